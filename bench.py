@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Benchmark of the GFORS hot path on one B300 (or N replicas).
+
+One step = one trigger period of Alg. 1 on the workload: k_int PDHG
+iterations (Alg. 2) + one round of k_b sampled candidates (Alg. 3) scored
+exactly on the original data + the on-device incumbent update.
+
+Default workload: max cut, dense Q = -L of G(n=4096, p=0.5) with +-1 edge
+weights, 8,192 candidates per round, k_int = 50.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload maxcut|setcover|knapsack|assign3d]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PDHG iters/s & candidates scored/s; time to ≤1% gap, learned+batched vs plain"
+L2_BYTES = 126 * 1024 * 1024
+
+WORKLOADS = {
+    # name: (builder, k_int, k_b, description)
+    "maxcut": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).max_cut(
+        n=4096, p=0.5, idx=r), 50, 8192,
+        "max cut G(4096,0.5) +-1 weights, Q=-L dense, 8192 candidates/round, k_int=50"),
+    "setcover": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).set_cover(
+        n=2000, m=200, density=0.05, idx=r), 50, 1024,
+        "set cover n=2000 m=200 Bernoulli(0.05), 1024 candidates/round, k_int=50"),
+    "knapsack": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).knapsack_batch(
+        ninst=512, idx=r), 50, 4096,
+        "512 knapsacks n_i~U[1e3,1e5], 4096 candidates/instance/round, k_int=50"),
+    "assign3d": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).assign3d(
+        I=64, idx=r), 50, 1024,
+        "axial 3D assignment I=64 (262,144 binaries), 1024 candidates/round, k_int=50"),
+}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2510_27117_b300 import gfors as G
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build, k_int, k_b, desc = WORKLOADS[args.workload]
+    inst = build(0)
+    insts = inst if isinstance(inst, list) else [inst]
+    stream = torch.cuda.Stream()
+    prm = G.default_params(k_int=k_int, k_b=k_b, seed=0x5EED0000 + 1, x0=-1.0,
+                           inst_base=rank * len(insts))
+    if args.workload in ("maxcut",):
+        prm.x0 = -1.0        # x = 0.5 is a stationary point of the max-cut relaxation
+    G.use_torch_allocator(True)
+    t_load0 = time.perf_counter()
+    H = G.load_batch(insts, prm, stream=stream)
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t_load0
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    round_id = [0]
+
+    def step():
+        H.pdhg_steps(k_int)
+        H.sample_eval(1, round_id[0], 0)
+        round_id[0] += 1
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        H.profile(True)
+        l0 = H.launch_count()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for q in range(args.steps):
+                flush.zero_()                       # L2 flushed between steps
+                evs[q][0].record(stream)
+                step()
+                evs[q][1].record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches = H.launch_count() - l0
+        prof = H.profile_read()
+        H.profile(False)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    cands = k_b * len(insts)
+    value = cands * args.steps * world / (ms / 1e3)
+    iters_s = k_int * args.steps / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = run_e2e(G, H, insts, k_int, k_b, stream, args, world)
+
+    # ---- roofline of the dominant kernel (phase timed with events on the stream)
+    peaks, src = load_peaks()
+    roof = roofline(args.workload, insts, k_int, k_b, prof, peaks, src, args.steps)
+    out = {
+        "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 PDHG / bf16 scoring / int64 evaluation", "data": "synthetic (seeded)",
+        "config": {"workload": desc, "global_batch": cands * world, "n": insts[0].n,
+                   "instances": len(insts), "k_int": k_int, "k_b": k_b,
+                   "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
+        "pdhg_iters_per_s": iters_s,
+        "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "e2e": e2e, "gpu_launches": int(launches), "load_s": t_load,
+        "wall_s": wall, "roofline": roof,
+    }
+    out["clocks"] = clk.summary()
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
+        print(json.dumps(out), flush=True)
+    H.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(G, H, insts, k_int, k_b, stream, args, world):
+    """The same metric through the public API per step: host->device copy of
+    the warm-start iterate from pinned memory (gfors_set_iterate), the step,
+    and the incumbent read back to the host (gfors_incumbent)."""
+    import torch
+    n = insts[0].n
+    x = torch.full((n,), 0.5, dtype=torch.float32).pin_memory().numpy()
+    steps = max(2, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rid = 10_000
+    for _ in range(steps):
+        for q in range(len(insts)):
+            H.set_iterate(q, x, x, None)
+        H.pdhg_steps(k_int)
+        H.sample_eval(1, rid, 0)
+        rid += 1
+        for q in range(len(insts)):
+            H.incumbent(q, want_x=True)
+    dt = time.perf_counter() - t0
+    bi = sum(2 * 4 * I.n for I in insts)
+    bo = sum(I.n + 8 + 8 + 8 for I in insts)
+    return {"value": k_b * len(insts) * steps * world / dt, "unit": "candidates/s",
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps}
+
+
+def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps):
+    if workload == "maxcut":
+        n = insts[0].n
+        ms, cnt = prof.get("dense_score", (0.0, 0))
+        flops = 2.0 * n * n * k_b
+        if cnt:
+            t = ms / cnt / 1e3
+            ach = flops / t / 1e12
+            peak = peaks.get("bf16_tflops", 1800.0)
+            pdhg_ms, pdhg_cnt = prof.get("pdhg", (0.0, 0))
+            return {"kernel": "dense Q.X scoring (EvalBest)", "bound": "tensor",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "peak_source": src,
+                    "algorithmic_per_launch": f"2*n*n*k_b = {flops:.3e} FLOP",
+                    "pdhg_iter_ms": pdhg_ms / max(pdhg_cnt, 1),
+                    "pdhg_gbs": (n * n * 2 + 12 * n) / (pdhg_ms / max(pdhg_cnt, 1) / 1e3) / 1e9
+                    if pdhg_cnt else None}
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(workload, budget_s=20.0):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of the
+    same workload; scaled to candidates/s of a full step."""
+    from oracle import oracle as O
+    build, k_int, k_b, desc = WORKLOADS[workload]
+    inst = build(0)
+    inst = inst[0] if isinstance(inst, list) else inst
+    P = O.Params(k_int=k_int, k_b=k_b, seed=0x5EED0000 + 1, x0=-1.0)
+    t0 = time.perf_counter()
+    sol = O.OracleSolver(inst, P)
+    t_pre = time.perf_counter() - t0
+    it = 0
+    t0 = time.perf_counter()
+    while it < k_int and (time.perf_counter() - t0) < budget_s * 0.4:
+        sol.step()
+        it += 1
+    t_iter = (time.perf_counter() - t0) / it
+    ns = 0
+    t0 = time.perf_counter()
+    p32 = sol.x.astype(np.float32)
+    while (time.perf_counter() - t0) < budget_s * 0.4:
+        X = O.sample(inst, p32, 8, P.seed, 0, 0)
+        O.Evaluator(inst)(X)
+        ns += 8
+        if ns >= k_b:
+            break
+    t_cand = (time.perf_counter() - t0) / ns
+    t_step = k_int * t_iter + k_b * t_cand
+    return {"value": k_b / t_step, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{it} PDHG iterations + {ns} candidates of the same workload, "
+                      f"extrapolated to {k_int} iterations + {k_b} candidates per step",
+            "s_per_iter": t_iter, "s_per_candidate": t_cand, "preprocess_s": t_pre}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    cb = None
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.workload, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)))
+        vals.append(cb["value"])
+    v = statistics.median(vals[args.warmup:]) if len(vals) > args.warmup else vals[-1]
+    build, k_int, k_b, desc = WORKLOADS[args.workload]
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "candidates/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": k_b / v * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+           "config": {"workload": desc, "k_int": k_int, "k_b": k_b},
+           "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": v, "unit": "candidates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "wall_s": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="maxcut", choices=list(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

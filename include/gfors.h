@@ -1,0 +1,303 @@
+/*
+ * gfors.h -- C ABI of the B300 (sm_103a) GFORS hot path.
+ *
+ * GFORS (arXiv 2510.27117) attacks the binary integer program of Eq. (1)
+ *
+ *     min  <x, Qx> + <c, x>   s.t.  A x >= b,  B x = d,  x in {0,1}^n
+ *
+ * by running the PDHG update of Alg. 2 on the penalised saddle form Eq. (2)
+ * (K = -[A;B], r = (b;d), y = (u,v), u >= 0, penalty rho <x, 1-x>) and, every
+ * k_int iterations, drawing k_r rounds of k_b binary candidates from the
+ * current iterate (Alg. 3 and the customised samplers of Section 2.4.2),
+ * scoring them on the original data and keeping the best feasible one
+ * (EvalBest of Alg. 1).
+ *
+ * Conventions shared by every call:
+ *  - Matrices cross the boundary as HOST CSR (int64 row pointers, int32
+ *    column indices, double values), borrowed for the duration of the call
+ *    and copied.  Duplicate entries are summed.
+ *  - A handle owns all device memory of one batch of instances.  Instances
+ *    are independent; they share one device launch per kernel (the batch is
+ *    laid out block-diagonally in HBM).
+ *  - Work is enqueued asynchronously on the handle's CUDA stream.  Calls that
+ *    return host data (gfors_incumbent, gfors_lp_stats, gfors_get_*,
+ *    gfors_eval_candidates, gfors_state_export, gfors_run) synchronise it.
+ *  - Errors are status codes; nothing throws across the ABI.  A CUDA error or
+ *    a device wait that ran out of time marks the handle failed: later calls
+ *    return GFORS_E_STATE until gfors_destroy.  gfors_last_error() explains.
+ *  - One handle per host thread at a time; handles are not thread-safe.
+ *  - The library never falls back to the CPU.  It needs an sm_103a device.
+ */
+#ifndef GFORS_H
+#define GFORS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GFORS_API __attribute__((visibility("default")))
+#else
+#define GFORS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfors_ctx* gfors_handle;
+
+typedef enum {
+  GFORS_OK = 0,
+  GFORS_E_ARG = 1,         /* bad argument or malformed / infeasible input   */
+  GFORS_E_CUDA = 2,        /* a CUDA runtime call failed                     */
+  GFORS_E_OOM = 3,         /* device allocation failed                       */
+  GFORS_E_TIMEOUT = 4,     /* a bounded device-side wait gave up             */
+  GFORS_E_STATE = 5,       /* handle failed earlier, or call out of order    */
+  GFORS_E_UNSUPPORTED = 6  /* valid input this build does not handle         */
+} gfors_status;
+
+/* Sparse matrix in CSR form, host memory, borrowed. */
+typedef struct {
+  int64_t rows, cols, nnz;
+  const int64_t* row_ptr; /* rows + 1 entries, row_ptr[0] = 0             */
+  const int32_t* col_idx; /* nnz entries in [0, cols)                      */
+  const double* val;      /* nnz entries                                   */
+} gfors_csr;
+
+/* Q of Eq. (1): kind 0 = none (Q = 0), 1 = dense row-major n x n host
+ * array, 2 = CSR.  Q need not be symmetric: the gradient uses (Q + Q^T)/2
+ * (Eq. 1 assumes symmetry without loss of generality); scoring uses x^T Q x. */
+typedef struct {
+  int32_t kind;
+  const double* dense_rowmajor;
+  gfors_csr sparse;
+} gfors_qmat;
+
+/* Parameters (Alg. 1, Section 3).  gfors_default_params() fills the
+ * defaults named in the comments. */
+typedef struct {
+  double sigma;        /* tau1 tau2 <= sigma after Preprocess (Sec. 3); 0.99 */
+  double rho_min;      /* UpdatePenalty (Sec. 3); 1e-3                      */
+  double rho_max;      /* 1.0                                               */
+  double T;            /* 20                                                */
+  double p;            /* 2                                                 */
+  double delta;        /* minimum increment; 0                              */
+  int32_t k_int;       /* sampling interval (Alg. 1); 50                    */
+  int32_t k_r;         /* sampling rounds per trigger; 1                    */
+  int32_t k_b;         /* candidates per round; 1024 (multiple of 32)       */
+  int32_t tau_cap_by_L;/* -1 auto (on iff Q != 0), 0 off, 1 on: tau1 <=
+                          1/(2L), L = 2(||Q||+rho) (Eq. 2, Prop. 2)          */
+  uint64_t seed;       /* Philox key                                        */
+  double x0;           /* start point: value in [0,1] = constant vector;
+                          negative = Philox uniform draws                   */
+  double halt_tol;     /* CheckHalt tolerance; 1e-4                         */
+  int32_t stall_window;/* CheckHalt stall window in triggers; 20            */
+  int32_t inst_base;   /* Philox instance id of the batch's first instance  */
+  int32_t sample_chunk;/* candidates evaluated per device pass (memory cap,
+                          the role Sec. 2.1 gives k_b); 0 = k_b              */
+  int32_t eval_mode;   /* 0 auto, 1 materialised bits, 2 fused sample+eval
+                          (single-row instances), 3 dense tensor-core
+                          scoring (dense +-small-integer Q)                 */
+  double power_tol;    /* power-iteration stop tolerance; 1e-12            */
+  int32_t power_maxit; /* power-iteration cap; 5000                         */
+  double wait_timeout_s;/* limit of every device-side wait; 2.0             */
+} gfors_params;
+
+GFORS_API void gfors_default_params(gfors_params* prm);
+GFORS_API const char* gfors_version(void);
+
+/* Device allocation hook (optional).  When set, every device buffer of a
+ * later gfors_load* comes from alloc(size, ctx) and returns via free(ptr,
+ * ctx); alloc returning NULL yields GFORS_E_OOM.  NULL functions restore
+ * cudaMalloc / cudaFree. */
+typedef void* (*gfors_alloc_fn)(size_t size, void* ctx);
+typedef void (*gfors_free_fn)(void* ptr, void* ctx);
+GFORS_API gfors_status gfors_set_allocator(gfors_alloc_fn alloc, gfors_free_fn free_fn,
+                                 void* ctx);
+
+/* Load one instance (Eq. 1) and run Preprocess (Section 3): K = -[A;B] rows
+ * divided by their 2-norms, Q and c divided by ||Q||_2 + ||c||_2, K and r
+ * divided by ||K||_2; the two spectral norms come from FP64 power
+ * iterations on the device.  A and/or B may be NULL (m1 = 0 / m2 = 0), Q may
+ * be NULL (Q = 0).  b has A->rows entries, d has B->rows, c has n.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Infeasible empty rows and malformed CSR give GFORS_E_ARG. */
+GFORS_API gfors_status gfors_load(const gfors_csr* A, const double* b, const gfors_csr* B,
+                        const double* d, const gfors_qmat* Q, const double* c,
+                        int64_t n, const gfors_params* prm, void* cuda_stream,
+                        gfors_handle* out);
+
+/* Batch of ninst independent instances in one handle (arrays of per-instance
+ * pointers; A[i]/B[i]/Q[i] entries may be NULL).  Instance i uses Philox
+ * instance id prm->inst_base + i, so a batch reproduces single-instance runs
+ * bit for bit. */
+GFORS_API gfors_status gfors_load_batch(int32_t ninst, const gfors_csr* const* A,
+                              const double* const* b, const gfors_csr* const* B,
+                              const double* const* d, const gfors_qmat* const* Q,
+                              const double* const* c, const int64_t* n,
+                              const gfors_params* prm, void* cuda_stream,
+                              gfors_handle* out);
+
+/* Customised sampling (Section 2.4.2) for instance inst.
+ * mode 0: plain Bernoulli (Alg. 3) for every variable.
+ * mode 1: one-hot groups -- ngroups disjoint groups (grp_ptr[ngroups+1]
+ *         offsets into grp_idx, variable indices) each receive exactly one 1
+ *         per candidate, drawn from p restricted to the group; the other
+ *         variables stay Bernoulli.
+ * mode 2: axial 3D assignment over n = I^3 variables x_ijk at (i I + j) I + k;
+ *         every candidate is a feasible assignment by construction.
+ * Groups are copied. */
+GFORS_API gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t mode,
+                              int64_t ngroups, const int64_t* grp_ptr,
+                              const int64_t* grp_idx, int32_t axial_I);
+
+/* Monotone relaxation with repair (Section 2.4.3) for instance inst: after
+ * sampling, rep_var[q] <- rep_var[q] OR (OR of rep_idx[rep_ptr[q] ..
+ * rep_ptr[q+1])).  Valid when the repaired variables have non-negative
+ * cost (facility opening). */
+GFORS_API gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t nrep,
+                               const int64_t* rep_var, const int64_t* rep_ptr,
+                               const int64_t* rep_idx);
+
+/* nsteps iterations of Alg. 1's loop body without sampling: k <- k+1;
+ * rho <- UpdatePenalty (the counter advances once per k_int iterations);
+ * FirstOrderStep (Alg. 2).  Asynchronous. */
+GFORS_API gfors_status gfors_pdhg_steps(gfors_handle h, int64_t nsteps);
+
+/* nrounds rounds of RandSampleStep + EvalBest (Alg. 1) on every instance,
+ * proposal p = x_k (proposal 0), the attached learned network (1) or half of
+ * each (2).  Round r uses Philox round id first_round_id + r.  Each round
+ * scores k_b candidates on the ORIGINAL data (violation count, objective)
+ * and updates the device incumbent.  Asynchronous. */
+GFORS_API gfors_status gfors_sample_eval(gfors_handle h, int32_t nrounds,
+                               uint32_t first_round_id, int32_t proposal);
+
+/* EvalBest(round(x_k)) of Alg. 1 (x_i = 1 iff x_i > 0.5), round id
+ * 0xFFFFFFFF.  Asynchronous. */
+GFORS_API gfors_status gfors_final_round(gfors_handle h);
+
+/* Alg. 1 end to end: iterate until CheckHalt (Section 3) holds for every
+ * instance, max_iters iterations, or time_budget_s seconds (<= 0: none);
+ * then the final rounding.  Sampling triggers every k_int iterations
+ * (k_r rounds each, proposal as in gfors_sample_eval).  *iters_out (may be
+ * NULL) receives the iteration count.  Synchronises. */
+GFORS_API gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time_budget_s,
+                       int32_t proposal, int64_t* iters_out);
+
+/* Incumbent of instance inst: *found = 0/1, objective on the original data
+ * (*obj_i exact for integer data, *obj_f always), the round id and sample
+ * index that produced it, and x_best as n bytes (0/1) into x_out (may be
+ * NULL).  Synchronises. */
+GFORS_API gfors_status gfors_incumbent(gfors_handle h, int32_t inst, int32_t* found,
+                             int64_t* obj_i, double* obj_f, uint32_t* round_id,
+                             int32_t* sample, uint8_t* x_out);
+
+/* Relaxation statistics of instance inst at the current iterate, FP64
+ * reductions on the preprocessed problem (CheckHalt indicators, Section 3):
+ * out[0] primal residual, out[1] gap (Q = 0: relative duality gap against
+ * the Lagrangian dual bound; else ||s^x|| of Thm. 2), out[2] binary gap,
+ * out[3] c^T x + x^T Q x (scaled), out[4] dual bound (NaN if Q != 0),
+ * out[5] ||s^x_k||, out[6] rho, out[7] k.  Synchronises. */
+GFORS_API gfors_status gfors_lp_stats(gfors_handle h, int32_t inst, double out[8]);
+
+/* Scales found by Preprocess for instance inst: out[0] ||Q_sym||_2,
+ * out[1] s_obj = ||Q||_2 + ||c||_2, out[2] ||K_rownormalised||_2, out[3]
+ * ||Q_hat||_2, out[4] power iterations for Q, out[5] for K, out[6] tau1,
+ * out[7] tau2 (current rho).  Synchronises. */
+GFORS_API gfors_status gfors_get_scales(gfors_handle h, int32_t inst, double out[8]);
+
+/* Iterate of instance inst as FP32 host arrays: x = x_k, xbar = xbar_k,
+ * x_prev = x_{k-1} (n entries each), y (m1+m2 entries).  Any pointer may be
+ * NULL.  Synchronises. */
+GFORS_API gfors_status gfors_get_iterate(gfors_handle h, int32_t inst, float* x,
+                               float* xbar, float* x_prev, float* y);
+
+/* Overwrite the iterate of instance inst (x_k, xbar_k, y_k; x_{k-1} set to
+ * x).  Any pointer may be NULL (left unchanged).  Asynchronous. */
+GFORS_API gfors_status gfors_set_iterate(gfors_handle h, int32_t inst, const float* x,
+                               const float* xbar, const float* y);
+
+/* Set the iteration counter k (all instances) and the penalty rho (rho < 0:
+ * keep the schedule's value); the penalty counter becomes floor(k/k_int).
+ * Asynchronous. */
+GFORS_API gfors_status gfors_set_counters(gfors_handle h, int64_t k, double rho);
+
+/* Score k explicit candidates X (k x n bytes, sample-major, 0/1) of
+ * instance inst on the original data with the same device evaluator that
+ * sampling uses: viol[k] violation counts, obj_i[k] exact objectives
+ * (integer data), obj_f[k] FP64 objectives.  The incumbent is untouched.
+ * Synchronises. */
+GFORS_API gfors_status gfors_eval_candidates(gfors_handle h, int32_t inst, int32_t k,
+                                   const uint8_t* X, int32_t* viol,
+                                   int64_t* obj_i, double* obj_f);
+
+/* Candidates and scores of the LAST sampled chunk of instance inst:
+ * X_out (chunk x n bytes, may be NULL), viol, obj_i (chunk entries, may be
+ * NULL); *count receives the chunk length.  Synchronises. */
+GFORS_API gfors_status gfors_get_samples(gfors_handle h, int32_t inst, uint8_t* X_out,
+                               int32_t* viol, int64_t* obj_i, int32_t* count);
+
+/* Learned proposal (an added pattern, no counterpart in the paper).
+ * Weights of the per-variable MLP  h1 = relu(W1 f + b1), h2 = relu(W2 h1 +
+ * b2), p = clip(sigmoid(w3 . h2 + b3), 1e-4, 1-1e-4), F = 8 features,
+ * H = 128 hidden units, packed as W1[H*F] b1[H] W2[H*H] b2[H] w3[H] b3[1]
+ * (FP32 masters; the kernels round weights to bf16).  nW must equal
+ * gfors_mlp_nparams(F, H). */
+GFORS_API int64_t gfors_mlp_nparams(int32_t F, int32_t H);
+GFORS_API gfors_status gfors_set_proposal(gfors_handle h, const float* W, int64_t nW);
+
+/* Features of the learned proposal at the current iterate, FP32 [n x 8]
+ * row-major into feat (host), for instance inst.  Synchronises. */
+GFORS_API gfors_status gfors_get_features(gfors_handle h, int32_t inst, float* feat);
+
+/* MLP kernels on caller DEVICE buffers (cuda_stream as in gfors_load):
+ * forward: feat [nv x F] -> z [nv] logits, p [nv] probabilities (p may be
+ * NULL); loss_grad: mean BCE on logits against label [nv] (0/1), gradient
+ * into grad [nparams] (overwritten), loss into *loss_dev (device double);
+ * adam: one Adam step (t >= 1) on W [nparams] with moments m, v [nparams]
+ * (FP32).  W is packed as in gfors_set_proposal. */
+GFORS_API gfors_status gfors_mlp_forward(int32_t F, int32_t H, const float* W_dev,
+                               int64_t nv, const float* feat_dev, float* z_dev,
+                               float* p_dev, void* cuda_stream);
+GFORS_API gfors_status gfors_mlp_loss_grad(int32_t F, int32_t H, const float* W_dev,
+                                 int64_t nv, const float* feat_dev,
+                                 const float* label_dev, float* grad_dev,
+                                 double* loss_dev, void* cuda_stream);
+GFORS_API gfors_status gfors_mlp_adam(int64_t nparams, float* W_dev, const float* grad_dev,
+                            float* m_dev, float* v_dev, int64_t t, double lr,
+                            double beta1, double beta2, double eps,
+                            void* cuda_stream);
+
+/* Checkpoint / resume of the whole solver state (iterates, counters,
+ * penalty, incumbents, halting trackers).  export: with buf == NULL only
+ * *len is set; otherwise *len must hold the buffer size.  A resumed handle
+ * (same instance data and parameters) continues bit-identically.
+ * Synchronises. */
+GFORS_API gfors_status gfors_state_export(gfors_handle h, void* buf, size_t* len);
+GFORS_API gfors_status gfors_state_import(gfors_handle h, const void* buf, size_t len);
+
+/* Phase timing with CUDA events recorded on the handle's stream (no
+ * counterpart in the paper; measurement support).  enable = 1 clears and
+ * starts recording, 0 stops.  gfors_profile_read synchronises and writes,
+ * for each of nphases phases, the summed milliseconds and the number of
+ * timed launches: 0 PDHG iterations (per captured pair or single step;
+ * counts iterations), 1 bit sampling, 2 sparse evaluation, 3 dense scoring,
+ * 4 incumbent update, 5 fused sample+evaluate, 6 CheckHalt statistics,
+ * 7 dense sampling. */
+GFORS_API gfors_status gfors_profile(gfors_handle h, int32_t enable);
+GFORS_API gfors_status gfors_profile_read(gfors_handle h, int32_t nphases, double* ms,
+                                          int64_t* counts);
+
+/* Kernel-launch counter of this handle (device kernels enqueued so far). */
+GFORS_API int64_t gfors_launch_count(gfors_handle h);
+
+/* Text of the last error on h (h == NULL: the calling thread's last load
+ * error).  Valid until the next call on the same handle / thread. */
+GFORS_API const char* gfors_last_error(gfors_handle h);
+
+GFORS_API void gfors_destroy(gfors_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFORS_H */

@@ -1,0 +1,868 @@
+// gfors_api.cu -- the GFORS loop (Alg. 1) around the device kernels, and
+// the state-access entry points of gfors.h.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+
+#include "internal.cuh"
+
+void gf_set_slot(GfCtx* h, int parity, double rho);
+cudaError_t gf_launch_dense_score(GfCtx* h, const GfDenseQ& dq, int s0, int len);
+
+#define GF_ENTER(h)                                                          \
+  do {                                                                       \
+    if (!(h)) return GFORS_E_ARG;                                            \
+    if ((h)->failed) return GFORS_E_STATE;                                   \
+  } while (0)
+
+namespace {
+
+// bytes (sample-major k x n) -> variable-major bits for one instance
+__global__ void k_pack_bits(const uint8_t* __restrict__ Xb, int k, int64_t n, int64_t v0,
+                            int kws, uint32_t* __restrict__ X) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int kwu = (k + 31) / 32;
+  if (gid >= n * kwu) return;
+  const int64_t i = gid / kwu;
+  const int w = (int)(gid % kwu);
+  uint32_t m = 0;
+  for (int t = 0; t < 32; ++t) {
+    const int s = 32 * w + t;
+    if (s < k && Xb[(int64_t)s * n + i]) m |= 1u << t;
+  }
+  X[(v0 + i) * kws + w] = m;
+}
+
+__global__ void k_unpack_bits(const uint32_t* __restrict__ X, int k, int64_t n, int64_t v0,
+                              int kws, uint8_t* __restrict__ Xb) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= n * (int64_t)k) return;
+  const int s = (int)(gid / n);
+  const int64_t i = gid % n;
+  Xb[gid] = (X[(v0 + i) * kws + (s >> 5)] >> (s & 31)) & 1u;
+}
+
+__global__ void k_pack_dense(const uint8_t* __restrict__ Xb, int k, int64_t n, int64_t ld,
+                             __nv_bfloat16* __restrict__ Xs) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)k * ld) return;
+  const int s = (int)(gid / ld);
+  const int64_t i = gid % ld;
+  Xs[gid] = __float2bfloat16((i < n && Xb[(int64_t)s * n + i]) ? 1.0f : 0.0f);
+}
+
+__global__ void k_unpack_dense(const __nv_bfloat16* __restrict__ Xs, int k, int64_t n,
+                               int64_t ld, uint8_t* __restrict__ Xb) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)k * n) return;
+  const int s = (int)(gid / n);
+  const int64_t i = gid % n;
+  Xb[gid] = __bfloat162float(Xs[(int64_t)s * ld + i]) != 0.0f;
+}
+
+// round(x_k) as candidate 0 (bits and dense operands)
+__global__ void k_round_bits(const float* __restrict__ x, const uint8_t* __restrict__ live,
+                             int64_t N, int kws, uint32_t* __restrict__ X) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  X[i * kws] = (live[i] && x[i] > 0.5f) ? 1u : 0u;
+}
+__global__ void k_round_dense(const float* __restrict__ x, int64_t v0, int64_t n, int64_t ld,
+                              __nv_bfloat16* __restrict__ Xs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ld) return;
+  Xs[i] = __float2bfloat16((i < n && x[v0 + i] > 0.5f) ? 1.0f : 0.0f);
+}
+__global__ void k_set_round(GfDState* st, unsigned v) { st->round_id = v; }
+
+__global__ void k_x0_random(float* __restrict__ x, const int32_t* __restrict__ var_inst,
+                            const int64_t* __restrict__ var_off, const uint8_t* __restrict__ live,
+                            int64_t N, uint64_t seed, int inst_base) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (!live[i]) { x[i] = 0.0f; return; }
+  const int b = var_inst[i];
+  const int64_t loc = i - var_off[b];
+  const uint4 u = gf::philox_call(seed, gf::kStreamX0, (uint32_t)(inst_base + b), 0u, 0u,
+                                  (uint64_t)(loc >> 2));
+  x[i] = (float)(gf::lane_of(u, (uint32_t)(loc & 3)) >> 8) * (1.0f / 16777216.0f);
+}
+
+}  // namespace
+
+cudaError_t gf_launch_x0_random(GfCtx* h) {
+  k_x0_random<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(
+      h->x[0], h->var_inst, h->var_off_d, h->var_live, h->N, h->prm.seed, h->prm.inst_base);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// phase profiling
+static cudaEvent_t prof_event(GfCtx* h) {
+  if (!h->prof_pool.empty()) {
+    cudaEvent_t e = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int gf_prof_begin(GfCtx* h, int phase) {
+  if (!h->prof) return -1;
+  GfCtx::ProfRec r{phase, 0, prof_event(h), prof_event(h)};
+  cudaEventRecord(r.a, h->stream);
+  h->prof_recs.push_back(r);
+  return (int)h->prof_recs.size() - 1;
+}
+
+void gf_prof_end(GfCtx* h, int idx, int count) {
+  if (idx < 0) return;
+  h->prof_recs[idx].count = count;
+  cudaEventRecord(h->prof_recs[idx].b, h->stream);
+}
+
+static void prof_clear(GfCtx* h) {
+  for (auto& r : h->prof_recs) {
+    h->prof_pool.push_back(r.a);
+    h->prof_pool.push_back(r.b);
+  }
+  h->prof_recs.clear();
+}
+
+extern "C" gfors_status gfors_profile(gfors_handle h, int32_t enable) {
+  GF_ENTER(h);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "profile sync");
+  prof_clear(h);
+  h->prof = enable != 0;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_profile_read(gfors_handle h, int32_t nphases, double* ms,
+                                           int64_t* counts) {
+  GF_ENTER(h);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "profile sync");
+  for (int q = 0; q < nphases; ++q) {
+    if (ms) ms[q] = 0.0;
+    if (counts) counts[q] = 0;
+  }
+  for (auto& r : h->prof_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { cudaGetLastError(); continue; }
+    if (r.phase < nphases) {
+      if (ms) ms[r.phase] += t;
+      if (counts) counts[r.phase] += r.count;
+    }
+  }
+  return GFORS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host mirror of UpdatePenalty (same recursion as the device)
+static void host_advance(GfCtx* h, long long it) {
+  const gfors_params& P = h->prm;
+  const int n_next = (int)(it / P.k_int);
+  while (h->n_rho_host < n_next) {
+    h->n_rho_host++;
+    double rt = P.rho_min * pow(1.0 + (double)h->n_rho_host / P.T, P.p);
+    double lo = h->rho_host + P.delta;
+    double v = rt < lo ? lo : rt;
+    h->rho_host = v > P.rho_max ? P.rho_max : v;
+  }
+}
+
+static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
+  cudaError_t e;
+  int64_t done = 0;
+  // replay a captured pair of iterations while at least two remain
+  while (h->use_graphs && nsteps - done >= 2) {
+    const int p = (int)((h->k_host + 1) & 1);   // parity of the first iteration
+    if (!h->g_iter2[p]) {
+      cudaGraph_t g;
+      if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal))) return e;
+      long long saved = h->launches;
+      cudaError_t e1 = gf_launch_pdhg_iter(h, p);
+      cudaError_t e2 = (e1 == cudaSuccess) ? gf_launch_pdhg_iter(h, 1 - p) : e1;
+      h->pair_launches = h->launches - saved;
+      h->launches = saved;
+      e = cudaStreamEndCapture(h->stream, &g);
+      if (e2 != cudaSuccess) return e2;
+      if (e) return e;
+      e = cudaGraphInstantiate(&h->g_iter2[p], g, 0);
+      cudaGraphDestroy(g);
+      if (e) return e;
+    }
+    const int pi = gf_prof_begin(h, 0);
+    if ((e = cudaGraphLaunch(h->g_iter2[p], h->stream))) return e;
+    gf_prof_end(h, pi, 2);
+    h->launches += h->pair_launches;
+    host_advance(h, h->k_host + 1);
+    host_advance(h, h->k_host + 2);
+    h->k_host += 2;
+    done += 2;
+  }
+  for (; done < nsteps; ++done) {
+    const long long it = h->k_host + 1;
+    const int pi = gf_prof_begin(h, 0);
+    if ((e = gf_launch_pdhg_iter(h, (int)(it & 1)))) return e;
+    gf_prof_end(h, pi, 1);
+    host_advance(h, it);
+    h->k_host = it;
+  }
+  return cudaSuccess;
+}
+
+extern "C" gfors_status gfors_pdhg_steps(gfors_handle h, int64_t nsteps) {
+  GF_ENTER(h);
+  if (nsteps < 0) return gf_fail(h, GFORS_E_ARG, "nsteps < 0");
+  cudaError_t e = enqueue_steps(h, nsteps);
+  if (e != cudaSuccess) return gf_cuda(h, e, "gfors_pdhg_steps");
+  return GFORS_OK;
+}
+
+// One round (k_b candidates, processed in chunks) from proposal p.
+static cudaError_t enqueue_round(GfCtx* h, const float* p) {
+  const int kb = h->prm.k_b;
+  cudaError_t e;
+  for (int s0 = 0; s0 < kb; s0 += h->chunk) {
+    const int len = std::min(h->chunk, kb - s0);
+    const bool last = (s0 + len >= kb);
+    h->last_p = p;
+    h->last_s0 = s0;
+    h->last_chunk_len = len;
+    h->last_round = h->host_round;
+    int pi;
+    if (h->fused_ok) {
+      pi = gf_prof_begin(h, 5);
+      if ((e = gf_launch_fused(h, p, s0, len))) return e;
+      gf_prof_end(h, pi, 1);
+      h->last_mode = 1;
+      pi = gf_prof_begin(h, 4);
+      if ((e = gf_launch_incumbent(h, s0, len, 1, last))) return e;
+      gf_prof_end(h, pi, 1);
+    } else {
+      pi = gf_prof_begin(h, 1);
+      if ((e = gf_launch_sample(h, p, s0, len, !h->dense.empty()))) return e;
+      gf_prof_end(h, pi, 1);
+      pi = gf_prof_begin(h, 2);
+      if ((e = gf_launch_eval(h, s0, len))) return e;
+      gf_prof_end(h, pi, 1);
+      for (const GfDenseQ& dq : h->dense) {
+        pi = gf_prof_begin(h, 3);
+        if ((e = gf_launch_dense_score(h, dq, s0, len))) return e;
+        gf_prof_end(h, pi, 1);
+      }
+      h->last_mode = 0;
+      pi = gf_prof_begin(h, 4);
+      if ((e = gf_launch_incumbent(h, s0, len, 0, last))) return e;
+      gf_prof_end(h, pi, 1);
+    }
+  }
+  return cudaSuccess;
+}
+
+static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal) {
+  if (!h->all_integral)
+    return gf_fail(h, GFORS_E_UNSUPPORTED,
+                   "exact evaluation needs integral data (|value| < 2^31)");
+  if (proposal != 0 && !h->mlp_W)
+    return gf_fail(h, GFORS_E_STATE, "learned proposal requested but none attached");
+  cudaError_t e;
+  const float* xk = h->x[h->k_host & 1];
+  for (int r = 0; r < nrounds; ++r) {
+    const float* p = xk;
+    if (proposal == 1 || (proposal == 2 && (r & 1))) {
+      if ((e = gf_launch_mlp_proposal(h))) return gf_cuda(h, e, "learned proposal");
+      p = h->p_learn;
+    }
+    if ((e = enqueue_round(h, p))) return gf_cuda(h, e, "sampling round");
+    h->host_round++;
+  }
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_sample_eval(gfors_handle h, int32_t nrounds,
+                                          uint32_t first_round_id, int32_t proposal) {
+  GF_ENTER(h);
+  if (nrounds < 0 || proposal < 0 || proposal > 2)
+    return gf_fail(h, GFORS_E_ARG, "bad nrounds / proposal");
+  k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, first_round_id);
+  h->launches++;
+  h->host_round = first_round_id;
+  return sample_rounds(h, nrounds, proposal);
+}
+
+static cudaError_t enqueue_final_round(GfCtx* h) {
+  cudaError_t e;
+  const float* xk = h->x[h->k_host & 1];
+  k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, 0xFFFFFFFFu);
+  h->last_round = 0xFFFFFFFFu;
+  k_round_bits<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(xk, h->var_live, h->N,
+                                                                     h->kw, h->X);
+  for (const GfDenseQ& dq : h->dense)
+    k_round_dense<<<(unsigned)((dq.ld + 255) / 256), 256, 0, h->stream>>>(
+        xk, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.Xs);
+  h->launches += 2 + (long long)h->dense.size();
+  if ((e = gf_launch_eval(h, 0, 1))) return e;
+  for (const GfDenseQ& dq : h->dense)
+    if ((e = gf_launch_dense_score(h, dq, 0, 1))) return e;
+  h->last_mode = 0;
+  h->last_s0 = 0;
+  h->last_chunk_len = 1;
+  if ((e = gf_launch_incumbent(h, 0, 1, 0, false))) return e;
+  k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, h->host_round);
+  return cudaGetLastError();
+}
+
+extern "C" gfors_status gfors_final_round(gfors_handle h) {
+  GF_ENTER(h);
+  if (!h->all_integral)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "exact evaluation needs integral data");
+  cudaError_t e = enqueue_final_round(h);
+  if (e) return gf_cuda(h, e, "gfors_final_round");
+  return GFORS_OK;
+}
+
+// CheckHalt (Section 3), host side, on the device's FP64 sums.
+static void stats_of(GfCtx* h, int b, const double* s1, const double* s2, double* out) {
+  const GfInstHost& I = h->ih[b];
+  const double pres = sqrt(s1[0]) / (1.0 + sqrt(s1[1]));
+  const double pobj = s2[3] + s2[4];
+  const double D = s1[2] + s2[6];
+  const double sx = sqrt(s2[7]);
+  out[0] = pres;
+  out[1] = (I.qkind == 0) ? fabs(pobj - D) / (1.0 + fabs(pobj) + fabs(D)) : sx;
+  out[2] = s2[5] / (double)I.n;
+  out[3] = pobj;
+  out[4] = (I.qkind == 0) ? D : NAN;
+  out[5] = sx;
+  out[6] = h->rho_host;
+  out[7] = (double)h->k_host;
+}
+
+static gfors_status fetch_stats(GfCtx* h, std::vector<double>& out) {
+  cudaError_t e = gf_launch_stats(h);
+  if (e) return gf_cuda(h, e, "stats");
+  std::vector<double> a(8 * h->ninst), b2(8 * h->ninst);
+  if ((e = cudaMemcpyAsync(a.data(), h->stats, sizeof(double) * 8 * h->ninst,
+                           cudaMemcpyDeviceToHost, h->stream)))
+    return gf_cuda(h, e, "stats copy");
+  if ((e = cudaMemcpyAsync(b2.data(), h->stats2, sizeof(double) * 8 * h->ninst,
+                           cudaMemcpyDeviceToHost, h->stream)))
+    return gf_cuda(h, e, "stats copy");
+  if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "stats sync");
+  out.assign(8 * h->ninst, 0.0);
+  for (int b = 0; b < h->ninst; ++b) stats_of(h, b, &a[8 * b], &b2[8 * b], &out[8 * b]);
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_lp_stats(gfors_handle h, int32_t inst, double out[8]) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst || !out) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  std::vector<double> v;
+  gfors_status st = fetch_stats(h, v);
+  if (st) return st;
+  memcpy(out, &v[8 * inst], sizeof(double) * 8);
+  return GFORS_OK;
+}
+
+// value-stalling detector: indicator q of instance b is done when <= tol or
+// its best value has not improved by 1e-3 (relative) for stall_window triggers
+static bool halt_update(GfCtx* h, const std::vector<double>& st) {
+  h->h_trig++;
+  bool all = true;
+  for (int b = 0; b < h->ninst; ++b) {
+    bool done = true;
+    for (int q = 0; q < 3; ++q) {
+      const double v = st[8 * b + q];
+      double& best = h->h_best[3 * b + q];
+      long long& last = h->h_last[3 * b + q];
+      if (std::isinf(best) || v < best * (1.0 - 1e-3)) { best = v; last = h->h_trig; }
+      done &= (v <= h->prm.halt_tol) || (h->h_trig - last >= h->prm.stall_window);
+    }
+    all &= done;
+  }
+  return all;
+}
+
+extern "C" gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time_budget_s,
+                                  int32_t proposal, int64_t* iters_out) {
+  GF_ENTER(h);
+  if (max_iters < 0 || proposal < 0 || proposal > 2)
+    return gf_fail(h, GFORS_E_ARG, "bad max_iters / proposal");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int kint = h->prm.k_int;
+  gfors_status st;
+  while (h->k_host < max_iters) {
+    int64_t to_trig = kint - (h->k_host % kint);
+    int64_t n = std::min<int64_t>(to_trig, max_iters - h->k_host);
+    cudaError_t e = enqueue_steps(h, n);
+    if (e) return gf_cuda(h, e, "gfors_run steps");
+    if (h->k_host % kint == 0) {
+      const long long trig = h->k_host / kint - 1;
+      if (proposal != 0 && (e = gf_launch_features(h))) return gf_cuda(h, e, "features");
+      k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, (unsigned)(trig * h->prm.k_r));
+      h->host_round = (unsigned)(trig * h->prm.k_r);
+      if ((st = sample_rounds(h, h->prm.k_r, proposal))) return st;
+      std::vector<double> sv;
+      if ((st = fetch_stats(h, sv))) return st;
+      if (halt_update(h, sv)) break;
+    }
+    if (time_budget_s > 0.0) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > time_budget_s) break;
+    }
+  }
+  if ((st = gfors_final_round(h))) return st;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "gfors_run sync");
+  if (iters_out) *iters_out = h->k_host;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_incumbent(gfors_handle h, int32_t inst, int32_t* found,
+                                        int64_t* obj_i, double* obj_f, uint32_t* round_id,
+                                        int32_t* sample, uint8_t* x_out) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  GfInc I;
+  cudaError_t e = cudaMemcpyAsync(&I, h->inc + inst, sizeof(GfInc), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e) return gf_cuda(h, e, "incumbent copy");
+  const GfInstHost& H = h->ih[inst];
+  if (x_out && (e = cudaMemcpyAsync(x_out, h->xbest + H.var_off, H.n, cudaMemcpyDeviceToHost,
+                                    h->stream)))
+    return gf_cuda(h, e, "incumbent copy");
+  if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "incumbent sync");
+  if (found) *found = I.found;
+  if (obj_i) *obj_i = I.obj;
+  if (obj_f) *obj_f = I.objf;
+  if (round_id) *round_id = I.round_id;
+  if (sample) *sample = I.sample;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_get_scales(gfors_handle h, int32_t inst, double out[8]) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst || !out) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  const GfInstHost& I = h->ih[inst];
+  GfIParam q;
+  cudaError_t e = cudaMemcpyAsync(&q, h->iprm + (size_t)((h->k_host + 1) & 1) * h->ninst + inst,
+                                  sizeof(q), cudaMemcpyDeviceToHost, h->stream);
+  if (e || (e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "scales");
+  out[0] = I.normQ_raw; out[1] = I.s_obj; out[2] = I.normK; out[3] = I.normQhat;
+  out[4] = I.itQ; out[5] = I.itK; out[6] = q.tau1d; out[7] = q.tau2d;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_get_iterate(gfors_handle h, int32_t inst, float* x, float* xbar,
+                                          float* x_prev, float* y) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  const GfInstHost& I = h->ih[inst];
+  const int par = (int)(h->k_host & 1);
+  cudaError_t e = cudaSuccess;
+  if (x && !e) e = cudaMemcpyAsync(x, h->x[par] + I.var_off, sizeof(float) * I.n,
+                                   cudaMemcpyDeviceToHost, h->stream);
+  if (xbar && !e) e = cudaMemcpyAsync(xbar, h->xbar + I.var_off, sizeof(float) * I.n,
+                                      cudaMemcpyDeviceToHost, h->stream);
+  if (x_prev && !e) e = cudaMemcpyAsync(x_prev, h->x[1 - par] + I.var_off, sizeof(float) * I.n,
+                                        cudaMemcpyDeviceToHost, h->stream);
+  if (y && I.m1 + I.m2 && !e)
+    e = cudaMemcpyAsync(y, h->y + I.row_off, sizeof(float) * (I.m1 + I.m2),
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "gfors_get_iterate");
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_set_iterate(gfors_handle h, int32_t inst, const float* x,
+                                          const float* xbar, const float* y) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  const GfInstHost& I = h->ih[inst];
+  const int par = (int)(h->k_host & 1);
+  cudaError_t e = cudaSuccess;
+  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice;
+  if (x) {
+    e = cudaMemcpyAsync(h->x[par] + I.var_off, x, sizeof(float) * I.n, H2D, h->stream);
+    if (!e) e = cudaMemcpyAsync(h->x[1 - par] + I.var_off, x, sizeof(float) * I.n, H2D,
+                                h->stream);
+  }
+  if (xbar && !e)
+    e = cudaMemcpyAsync(h->xbar + I.var_off, xbar, sizeof(float) * I.n, H2D, h->stream);
+  if (y && I.m1 + I.m2 && !e)
+    e = cudaMemcpyAsync(h->y + I.row_off, y, sizeof(float) * (I.m1 + I.m2), H2D, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "gfors_set_iterate");
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_set_counters(gfors_handle h, int64_t k, double rho) {
+  GF_ENTER(h);
+  if (k < 0) return gf_fail(h, GFORS_E_ARG, "k < 0");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "set_counters sync");
+  if ((k & 1) != (h->k_host & 1)) {       // keep x_k in x[k & 1]
+    std::swap(h->x[0], h->x[1]);
+    for (int q = 0; q < 2; ++q)
+      if (h->g_iter2[q]) { cudaGraphExecDestroy(h->g_iter2[q]); h->g_iter2[q] = nullptr; }
+  }
+  const gfors_params& P = h->prm;
+  h->n_rho_host = 0;
+  h->rho_host = std::min(P.rho_min, P.rho_max);
+  h->k_host = 0;
+  host_advance(h, k);
+  if (rho >= 0.0) h->rho_host = rho;
+  h->k_host = k;
+  GfDState ds;
+  if ((e = cudaMemcpy(&ds, h->dstate, sizeof(ds), cudaMemcpyDeviceToHost)))
+    return gf_cuda(h, e, "set_counters");
+  ds.k = k;
+  ds.n_rho = h->n_rho_host;
+  ds.rho = h->rho_host;
+  if ((e = cudaMemcpy(h->dstate, &ds, sizeof(ds), cudaMemcpyHostToDevice)))
+    return gf_cuda(h, e, "set_counters");
+  gf_set_slot(h, (int)((k + 1) & 1), h->rho_host);
+  gf_set_slot(h, (int)(k & 1), h->rho_host);
+  if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "set_counters");
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_eval_candidates(gfors_handle h, int32_t inst, int32_t k,
+                                              const uint8_t* X, int32_t* viol, int64_t* obj_i,
+                                              double* obj_f) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst || k < 0 || (k > 0 && !X))
+    return gf_fail(h, GFORS_E_ARG, "bad arguments");
+  if (!h->all_integral) return gf_fail(h, GFORS_E_UNSUPPORTED, "needs integral data");
+  const GfInstHost& I = h->ih[inst];
+  cudaError_t e;
+  uint8_t* Xd = gf_alloc_t<uint8_t>(h, (size_t)h->chunk * I.n);
+  if (!Xd) return gf_fail(h, GFORS_E_OOM, "eval_candidates buffer");
+  std::vector<int32_t> v(h->chunk);
+  std::vector<long long> o(h->chunk);
+  for (int s0 = 0; s0 < k; s0 += h->chunk) {
+    const int len = std::min(h->chunk, k - s0);
+    if ((e = cudaMemcpyAsync(Xd, X + (size_t)s0 * I.n, (size_t)len * I.n,
+                             cudaMemcpyHostToDevice, h->stream)))
+      return gf_cuda(h, e, "eval_candidates upload");
+    if (I.qkind == 1) {
+      const GfDenseQ& dq = h->dense[I.dense_idx];
+      k_pack_dense<<<(unsigned)(((int64_t)len * dq.ld + 255) / 256), 256, 0, h->stream>>>(
+          Xd, len, I.n, dq.ld, dq.Xs);
+    } else {
+      const int kwu = (len + 31) / 32;
+      k_pack_bits<<<(unsigned)((I.n * kwu + 255) / 256), 256, 0, h->stream>>>(Xd, len, I.n,
+                                                                              I.var_off, h->kw,
+                                                                              h->X);
+    }
+    if ((e = gf_launch_eval(h, 0, len))) return gf_cuda(h, e, "eval_candidates");
+    if (I.qkind == 1 && (e = gf_launch_dense_score(h, h->dense[I.dense_idx], 0, len)))
+      return gf_cuda(h, e, "eval_candidates dense");
+    if ((e = cudaMemcpyAsync(v.data(), h->viol + (size_t)inst * h->chunk, sizeof(int32_t) * len,
+                             cudaMemcpyDeviceToHost, h->stream)))
+      return gf_cuda(h, e, "eval_candidates copy");
+    if ((e = cudaMemcpyAsync(o.data(), h->obj + (size_t)inst * h->chunk,
+                             sizeof(long long) * len, cudaMemcpyDeviceToHost, h->stream)))
+      return gf_cuda(h, e, "eval_candidates copy");
+    if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "eval_candidates sync");
+    for (int t = 0; t < len; ++t) {
+      if (viol) viol[s0 + t] = v[t];
+      if (obj_i) obj_i[s0 + t] = o[t];
+      if (obj_f) obj_f[s0 + t] = (double)o[t];
+    }
+  }
+  gf_free_one(h, Xd);
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_get_samples(gfors_handle h, int32_t inst, uint8_t* X_out,
+                                          int32_t* viol, int64_t* obj_i, int32_t* count) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  const GfInstHost& I = h->ih[inst];
+  const int len = h->last_chunk_len;
+  cudaError_t e;
+  if (count) *count = len;
+  if (len == 0) return GFORS_OK;
+  if (X_out) {
+    uint8_t* Xd = gf_alloc_t<uint8_t>(h, (size_t)len * I.n);
+    if (!Xd) return gf_fail(h, GFORS_E_OOM, "get_samples buffer");
+    if (I.qkind == 1) {
+      const GfDenseQ& dq = h->dense[I.dense_idx];
+      k_unpack_dense<<<(unsigned)(((int64_t)len * I.n + 255) / 256), 256, 0, h->stream>>>(
+          dq.Xs, len, I.n, dq.ld, Xd);
+    } else {
+      if (h->last_mode == 1) {
+        // fused chunks are not materialised: regenerate the same draws
+        k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, h->last_round);
+        if ((e = gf_launch_sample(h, h->last_p, h->last_s0, len, false)))
+          return gf_cuda(h, e, "get_samples regenerate");
+        k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, h->host_round);
+      }
+      k_unpack_bits<<<(unsigned)(((int64_t)len * I.n + 255) / 256), 256, 0, h->stream>>>(
+          h->X, len, I.n, I.var_off, h->kw, Xd);
+    }
+    if ((e = cudaMemcpyAsync(X_out, Xd, (size_t)len * I.n, cudaMemcpyDeviceToHost, h->stream)))
+      return gf_cuda(h, e, "get_samples copy");
+    if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "get_samples sync");
+    gf_free_one(h, Xd);
+  }
+  std::vector<int32_t> v(len);
+  std::vector<long long> o(len);
+  if ((e = cudaMemcpyAsync(v.data(), h->viol + (size_t)inst * h->chunk, sizeof(int32_t) * len,
+                           cudaMemcpyDeviceToHost, h->stream)))
+    return gf_cuda(h, e, "get_samples copy");
+  if ((e = cudaMemcpyAsync(o.data(), h->obj + (size_t)inst * h->chunk, sizeof(long long) * len,
+                           cudaMemcpyDeviceToHost, h->stream)))
+    return gf_cuda(h, e, "get_samples copy");
+  if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "get_samples sync");
+  for (int t = 0; t < len; ++t) {
+    if (viol) viol[t] = v[t];
+    if (obj_i) obj_i[t] = o[t];
+  }
+  return GFORS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// groups and closure
+extern "C" gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t mode,
+                                         int64_t ngroups, const int64_t* grp_ptr,
+                                         const int64_t* grp_idx, int32_t axial_I) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  GfInstHost& I = h->ih[inst];
+  if (I.qkind == 1 && mode != 0)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "groups on a dense tensor-core instance");
+  if (h->fused_ok && mode != 0)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "groups on a fused single-row batch");
+  if (I.group_mode != 0) return gf_fail(h, GFORS_E_STATE, "groups already set");
+  cudaError_t e;
+  std::vector<uint8_t> grouped(I.npad, 0);
+  if (mode == 0) return GFORS_OK;
+  if (mode == 2) {
+    if (axial_I < 1 || axial_I > 256 || (int64_t)axial_I * axial_I * axial_I != I.n)
+      return gf_fail(h, GFORS_E_ARG, "axial mode needs n = I^3 with 1 <= I <= 256");
+    I.group_mode = 2;
+    I.axial_I = axial_I;
+    for (int64_t i = 0; i < I.n; ++i) grouped[i] = 1;
+  } else if (mode == 1) {
+    if (ngroups < 0 || (ngroups > 0 && (!grp_ptr || !grp_idx)) || (ngroups && grp_ptr[0] != 0))
+      return gf_fail(h, GFORS_E_ARG, "bad group arrays");
+    for (int64_t g = 0; g < ngroups; ++g) {
+      if (grp_ptr[g + 1] < grp_ptr[g]) return gf_fail(h, GFORS_E_ARG, "group ptr not monotone");
+      for (int64_t t = grp_ptr[g]; t < grp_ptr[g + 1]; ++t) {
+        const int64_t v = grp_idx[t];
+        if (v < 0 || v >= I.n) return gf_fail(h, GFORS_E_ARG, "group index out of range");
+        if (grouped[v]) return gf_fail(h, GFORS_E_ARG, "groups must be disjoint");
+        grouped[v] = 1;
+      }
+    }
+    I.group_mode = 1;
+    I.ngroups = ngroups;
+    const int64_t base = (int64_t)h->h_grp_idx.size();
+    if (h->h_grp_ptr.empty()) h->h_grp_ptr.push_back(0);
+    for (int64_t g = 0; g < ngroups; ++g) {
+      for (int64_t t = grp_ptr[g]; t < grp_ptr[g + 1]; ++t)
+        h->h_grp_idx.push_back(I.var_off + grp_idx[t]);
+      h->h_grp_ptr.push_back(base + grp_ptr[g + 1]);
+      h->h_grp_inst.push_back(inst);
+      h->h_grp_local.push_back((int32_t)g);
+    }
+    h->ngroups_tot = (int64_t)h->h_grp_inst.size();
+    // (re)upload the global group tables
+    h->grp_ptr = gf_alloc_t<int64_t>(h, h->h_grp_ptr.size());
+    h->grp_idx = gf_alloc_t<int64_t>(h, h->h_grp_idx.size());
+    h->grp_inst = gf_alloc_t<int32_t>(h, h->h_grp_inst.size());
+    h->grp_local = gf_alloc_t<int32_t>(h, h->h_grp_local.size());
+    h->grp_cw = gf_alloc_t<unsigned long long>(h, h->h_grp_idx.size());
+    if (!h->grp_ptr || !h->grp_idx || !h->grp_inst || !h->grp_local || !h->grp_cw)
+      return gf_fail(h, GFORS_E_OOM, "group tables");
+    if ((e = cudaMemcpy(h->grp_ptr, h->h_grp_ptr.data(), sizeof(int64_t) * h->h_grp_ptr.size(),
+                        cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(h->grp_idx, h->h_grp_idx.data(), sizeof(int64_t) * h->h_grp_idx.size(),
+                        cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(h->grp_inst, h->h_grp_inst.data(),
+                        sizeof(int32_t) * h->h_grp_inst.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(h->grp_local, h->h_grp_local.data(),
+                        sizeof(int32_t) * h->h_grp_local.size(), cudaMemcpyHostToDevice)))
+      return gf_cuda(h, e, "group upload");
+  } else {
+    return gf_fail(h, GFORS_E_ARG, "mode must be 0, 1 or 2");
+  }
+  if ((e = cudaMemcpy(h->var_grouped + I.var_off, grouped.data(), I.npad,
+                      cudaMemcpyHostToDevice)))
+    return gf_cuda(h, e, "group flags");
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t nrep,
+                                          const int64_t* rep_var, const int64_t* rep_ptr,
+                                          const int64_t* rep_idx) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  GfInstHost& I = h->ih[inst];
+  if (nrep <= 0) return GFORS_OK;
+  if (!rep_var || !rep_ptr || !rep_idx || rep_ptr[0] != 0)
+    return gf_fail(h, GFORS_E_ARG, "bad closure arrays");
+  if (I.qkind == 1 || h->fused_ok)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "closure on a dense / fused instance");
+  if (h->h_rep_ptr.empty()) h->h_rep_ptr.push_back(0);
+  const int64_t base = (int64_t)h->h_rep_idx.size();
+  for (int64_t q = 0; q < nrep; ++q) {
+    if (rep_var[q] < 0 || rep_var[q] >= I.n || rep_ptr[q + 1] < rep_ptr[q])
+      return gf_fail(h, GFORS_E_ARG, "closure index out of range");
+    h->h_rep_var.push_back(I.var_off + rep_var[q]);
+    for (int64_t t = rep_ptr[q]; t < rep_ptr[q + 1]; ++t) {
+      if (rep_idx[t] < 0 || rep_idx[t] >= I.n)
+        return gf_fail(h, GFORS_E_ARG, "closure index out of range");
+      h->h_rep_idx.push_back(I.var_off + rep_idx[t]);
+    }
+    h->h_rep_ptr.push_back(base + rep_ptr[q + 1]);
+  }
+  h->nrep_tot = (int64_t)h->h_rep_var.size();
+  h->rep_var = gf_alloc_t<int64_t>(h, h->h_rep_var.size());
+  h->rep_ptr = gf_alloc_t<int64_t>(h, h->h_rep_ptr.size());
+  h->rep_idx = gf_alloc_t<int64_t>(h, h->h_rep_idx.size());
+  if (!h->rep_var || !h->rep_ptr || !h->rep_idx) return gf_fail(h, GFORS_E_OOM, "closure");
+  cudaError_t e;
+  if ((e = cudaMemcpy(h->rep_var, h->h_rep_var.data(), sizeof(int64_t) * h->h_rep_var.size(),
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->rep_ptr, h->h_rep_ptr.data(), sizeof(int64_t) * h->h_rep_ptr.size(),
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->rep_idx, h->h_rep_idx.data(), sizeof(int64_t) * h->h_rep_idx.size(),
+                      cudaMemcpyHostToDevice)))
+    return gf_cuda(h, e, "closure upload");
+  return GFORS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume
+namespace {
+struct Blob {
+  std::vector<uint8_t> b;
+  template <class T> void put(const T& v) {
+    const uint8_t* p = reinterpret_cast<const uint8_t*>(&v);
+    b.insert(b.end(), p, p + sizeof(T));
+  }
+  void put_raw(const void* p, size_t n) {
+    const uint8_t* q = static_cast<const uint8_t*>(p);
+    b.insert(b.end(), q, q + n);
+  }
+};
+const uint64_t kMagic = 0x47464F5253303031ull;  // "GFORS001"
+}  // namespace
+
+static gfors_status export_blob(GfCtx* h, Blob& B) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "export sync");
+  const int64_t N = h->N, M = h->M;
+  std::vector<float> x0(N), x1(N), xb(N), y(std::max<int64_t>(M, 1));
+  std::vector<GfIParam> ip(2 * h->ninst);
+  std::vector<GfInc> inc(h->ninst);
+  std::vector<uint8_t> xbest(N);
+  GfDState ds;
+  if ((e = cudaMemcpy(x0.data(), h->x[0], sizeof(float) * N, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(x1.data(), h->x[1], sizeof(float) * N, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(xb.data(), h->xbar, sizeof(float) * N, cudaMemcpyDeviceToHost)) ||
+      (M && (e = cudaMemcpy(y.data(), h->y, sizeof(float) * M, cudaMemcpyDeviceToHost))) ||
+      (e = cudaMemcpy(ip.data(), h->iprm, sizeof(GfIParam) * 2 * h->ninst,
+                      cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(inc.data(), h->inc, sizeof(GfInc) * h->ninst, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(xbest.data(), h->xbest, N, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(&ds, h->dstate, sizeof(ds), cudaMemcpyDeviceToHost)))
+    return gf_cuda(h, e, "export copy");
+  B.put(kMagic);
+  B.put((int64_t)h->ninst);
+  B.put(N);
+  B.put(M);
+  B.put(h->k_host);
+  B.put(h->n_rho_host);
+  B.put(h->rho_host);
+  B.put(h->h_trig);
+  B.put(ds);
+  B.put_raw(x0.data(), sizeof(float) * N);
+  B.put_raw(x1.data(), sizeof(float) * N);
+  B.put_raw(xb.data(), sizeof(float) * N);
+  B.put_raw(y.data(), sizeof(float) * M);
+  B.put_raw(ip.data(), sizeof(GfIParam) * ip.size());
+  B.put_raw(inc.data(), sizeof(GfInc) * inc.size());
+  B.put_raw(xbest.data(), N);
+  B.put_raw(h->h_best.data(), sizeof(double) * h->h_best.size());
+  B.put_raw(h->h_last.data(), sizeof(long long) * h->h_last.size());
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_state_export(gfors_handle h, void* buf, size_t* len) {
+  GF_ENTER(h);
+  if (!len) return gf_fail(h, GFORS_E_ARG, "len is NULL");
+  Blob B;
+  gfors_status st = export_blob(h, B);
+  if (st) return st;
+  if (!buf) { *len = B.b.size(); return GFORS_OK; }
+  if (*len < B.b.size()) return gf_fail(h, GFORS_E_ARG, "buffer too small");
+  memcpy(buf, B.b.data(), B.b.size());
+  *len = B.b.size();
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_state_import(gfors_handle h, const void* buf, size_t len) {
+  GF_ENTER(h);
+  if (!buf) return gf_fail(h, GFORS_E_ARG, "buffer is NULL");
+  const uint8_t* p = static_cast<const uint8_t*>(buf);
+  size_t off = 0;
+  auto get = [&](void* dst, size_t n) -> bool {
+    if (off + n > len) return false;
+    memcpy(dst, p + off, n);
+    off += n;
+    return true;
+  };
+  uint64_t magic;
+  int64_t ninst, N, M;
+  long long k;
+  int nr;
+  double rho;
+  long long trig;
+  GfDState ds;
+  if (!get(&magic, 8) || magic != kMagic || !get(&ninst, 8) || !get(&N, 8) || !get(&M, 8) ||
+      ninst != h->ninst || N != h->N || M != h->M)
+    return gf_fail(h, GFORS_E_ARG, "checkpoint does not match this handle");
+  if (!get(&k, sizeof k) || !get(&nr, sizeof nr) || !get(&rho, sizeof rho) ||
+      !get(&trig, sizeof trig) || !get(&ds, sizeof ds))
+    return gf_fail(h, GFORS_E_ARG, "truncated checkpoint");
+  std::vector<float> x0(N), x1(N), xb(N), y(std::max<int64_t>(M, 1));
+  std::vector<GfIParam> ip(2 * h->ninst);
+  std::vector<GfInc> inc(h->ninst);
+  std::vector<uint8_t> xbest(N);
+  std::vector<double> best(h->h_best.size());
+  std::vector<long long> last(h->h_last.size());
+  if (!get(x0.data(), sizeof(float) * N) || !get(x1.data(), sizeof(float) * N) ||
+      !get(xb.data(), sizeof(float) * N) || !get(y.data(), sizeof(float) * M) ||
+      !get(ip.data(), sizeof(GfIParam) * ip.size()) || !get(inc.data(), sizeof(GfInc) * inc.size()) ||
+      !get(xbest.data(), N) || !get(best.data(), sizeof(double) * best.size()) ||
+      !get(last.data(), sizeof(long long) * last.size()))
+    return gf_fail(h, GFORS_E_ARG, "truncated checkpoint");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "import sync");
+  if ((e = cudaMemcpy(h->x[0], x0.data(), sizeof(float) * N, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->x[1], x1.data(), sizeof(float) * N, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->xbar, xb.data(), sizeof(float) * N, cudaMemcpyHostToDevice)) ||
+      (M && (e = cudaMemcpy(h->y, y.data(), sizeof(float) * M, cudaMemcpyHostToDevice))) ||
+      (e = cudaMemcpy(h->iprm, ip.data(), sizeof(GfIParam) * ip.size(), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->inc, inc.data(), sizeof(GfInc) * inc.size(), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->xbest, xbest.data(), N, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->dstate, &ds, sizeof ds, cudaMemcpyHostToDevice)))
+    return gf_cuda(h, e, "import copy");
+  h->k_host = k;
+  h->n_rho_host = nr;
+  h->rho_host = rho;
+  h->h_trig = trig;
+  h->h_best = best;
+  h->h_last = last;
+  return GFORS_OK;
+}

@@ -1,0 +1,1075 @@
+// gfors_load.cu -- loading a batch of instances and Preprocess (Section 3).
+//
+// Host (FP64): K = -[A;B] and r = (b;d) per instance (Eq. 2), duplicate
+// entries summed, every row divided by its 2-norm; Q symmetrised as
+// (Q + Q^T)/2 (Eq. 1); integer rows classified for exact evaluation;
+// the batch concatenated block-diagonally; K^T built as CSC.
+// Device (FP64): ||Q_sym||_2 and ||K_rownormalised||_2 by power iteration;
+// then s_obj = ||Q||_2 + ||c||_2, s_K = ||K||_2 and the FP32 scaled copies
+// Q/s_obj, c/s_obj, K/s_K, r/s_K used by the PDHG kernels.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <numeric>
+
+#include "internal.cuh"
+
+static thread_local std::string g_thread_err;
+static gfors_alloc_fn g_alloc = nullptr;
+static gfors_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+static std::mutex g_alloc_mu;
+
+extern cudaError_t gf_power_run(GfCtx* h, int which, const int64_t* Mp, const int32_t* Mc,
+                                const double* Mv, const int64_t* Tp, const int32_t* Tr,
+                                const double* Tv, int64_t mrows, const int32_t* rch,
+                                int64_t nrch, const int32_t* rptr,
+                                const double* const* dense_diag, double* norms, int* iters);
+extern cudaError_t gf_scale_to_f32(GfCtx* h, const double* Kd, const double* Td,
+                                   const double* rd, const double* cd, const double* Qd,
+                                   const double* sK, const double* sobj);
+void gf_set_slot(GfCtx* h, int parity, double rho);
+
+int64_t gf_round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+gfors_status gf_fail(GfCtx* h, gfors_status st, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (st == GFORS_E_CUDA || st == GFORS_E_TIMEOUT) h->failed = true;
+  } else {
+    g_thread_err = msg;
+  }
+  return st;
+}
+
+gfors_status gf_cuda(GfCtx* h, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return gf_fail(h, GFORS_E_OOM, std::string("out of device memory in ") + what);
+  }
+  return gf_fail(h, GFORS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* gf_alloc(GfCtx* h, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_alloc) {
+      p = g_alloc(bytes, g_alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (p) h->allocs.push_back(p);
+  return p;
+}
+
+void gf_free_one(GfCtx* h, void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  for (size_t q = 0; q < h->allocs.size(); ++q)
+    if (h->allocs[q] == p) {
+      h->allocs.erase(h->allocs.begin() + q);
+      if (g_free) g_free(p, g_alloc_ctx);
+      else cudaFree(p);
+      return;
+    }
+}
+
+void gf_free_all(GfCtx* h) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  for (void* p : h->allocs) {
+    if (g_free) g_free(p, g_alloc_ctx);
+    else cudaFree(p);
+  }
+  h->allocs.clear();
+}
+
+extern "C" void gfors_default_params(gfors_params* p) {
+  memset(p, 0, sizeof(*p));
+  p->sigma = 0.99;
+  p->rho_min = 1e-3;
+  p->rho_max = 1.0;
+  p->T = 20.0;
+  p->p = 2.0;
+  p->delta = 0.0;
+  p->k_int = 50;
+  p->k_r = 1;
+  p->k_b = 1024;
+  p->tau_cap_by_L = -1;
+  p->seed = 0x5EED0000ull;
+  p->x0 = 0.5;
+  p->halt_tol = 1e-4;
+  p->stall_window = 20;
+  p->inst_base = 0;
+  p->sample_chunk = 0;
+  p->eval_mode = 0;
+  p->power_tol = 1e-12;
+  p->power_maxit = 5000;
+  p->wait_timeout_s = 2.0;
+}
+
+extern "C" const char* gfors_version(void) { return "gfors-b300 0.1 (sm_103a)"; }
+
+extern "C" gfors_status gfors_set_allocator(gfors_alloc_fn a, gfors_free_fn f, void* ctx) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if ((a == nullptr) != (f == nullptr)) {
+    g_thread_err = "gfors_set_allocator: give both functions or neither";
+    return GFORS_E_ARG;
+  }
+  g_alloc = a;
+  g_free = f;
+  g_alloc_ctx = ctx;
+  return GFORS_OK;
+}
+
+extern "C" const char* gfors_last_error(gfors_handle h) {
+  return h ? h->err.c_str() : g_thread_err.c_str();
+}
+
+extern "C" int64_t gfors_launch_count(gfors_handle h) { return h ? h->launches : 0; }
+
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Row {                      // one merged row: sorted columns, summed values
+  std::vector<int32_t> col;
+  std::vector<double> val;
+};
+
+bool check_csr(const gfors_csr* M, int64_t ncols, std::string& why) {
+  if (!M) return true;
+  if (M->rows < 0 || M->nnz < 0 || M->cols != ncols) {
+    why = "CSR shape mismatch (cols must equal n)";
+    return false;
+  }
+  if (M->rows > 0 && !M->row_ptr) { why = "CSR row_ptr is NULL"; return false; }
+  if (M->rows > 0 && M->row_ptr[0] != 0) { why = "CSR row_ptr[0] != 0"; return false; }
+  for (int64_t r = 0; r < M->rows; ++r)
+    if (M->row_ptr[r + 1] < M->row_ptr[r]) { why = "CSR row_ptr not monotone"; return false; }
+  if (M->rows > 0 && M->row_ptr[M->rows] != M->nnz) { why = "CSR nnz mismatch"; return false; }
+  if (M->nnz > 0 && (!M->col_idx || !M->val)) { why = "CSR arrays NULL"; return false; }
+  for (int64_t t = 0; t < M->nnz; ++t) {
+    if (M->col_idx[t] < 0 || M->col_idx[t] >= ncols) { why = "CSR column out of range"; return false; }
+    if (!std::isfinite(M->val[t])) { why = "CSR value not finite"; return false; }
+  }
+  return true;
+}
+
+Row merged_row(const gfors_csr* M, int64_t r, double sign) {
+  std::vector<std::pair<int32_t, double>> e;
+  for (int64_t t = M->row_ptr[r]; t < M->row_ptr[r + 1]; ++t)
+    e.emplace_back(M->col_idx[t], sign * M->val[t]);
+  std::sort(e.begin(), e.end(),
+            [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+              return a.first < b.first;
+            });
+  Row out;
+  for (size_t q = 0; q < e.size();) {
+    size_t u = q;
+    double s = 0.0;
+    while (u < e.size() && e[u].first == e[q].first) s += e[u++].second;
+    if (s != 0.0) { out.col.push_back(e[q].first); out.val.push_back(s); }
+    q = u;
+  }
+  return out;
+}
+
+bool is_int31(double v) { return std::floor(v) == v && std::fabs(v) < 2147483648.0; }
+
+long long floor_div(long long a, long long b) {   // b != 0
+  long long q = a / b, r = a % b;
+  if (r != 0 && ((r < 0) != (b < 0))) --q;
+  return q;
+}
+long long ceil_div(long long a, long long b) { return -floor_div(-a, b); }
+
+// Host-side staging of one instance before concatenation.
+struct Stage {
+  std::vector<Row> K;             // rows of -[A;B], row-normalised later
+  std::vector<double> r;
+  std::vector<uint8_t> eq;
+  std::vector<double> rownorm;
+  // eval (original integer rows)
+  std::vector<Row> orig;          // A rows then B rows (original signs)
+  std::vector<long long> rhs;
+  // Q symmetric (sparse, FP64) and original (sparse, int)
+  std::vector<Row> Qsym;          // per variable (local columns)
+  std::vector<Row> Qorig;
+};
+
+}  // namespace
+
+void gf_set_slot(GfCtx* h, int parity, double rho) {
+  std::vector<GfIParam> v(h->ninst);
+  for (int b = 0; b < h->ninst; ++b) {
+    double t1 = sqrt(h->prm.sigma);
+    if (h->ih[b].cap) {
+      double L = 2.0 * (h->ih[b].normQhat + rho);
+      if (L > 0.0 && 1.0 / (2.0 * L) < t1) t1 = 1.0 / (2.0 * L);
+    }
+    double t2 = h->prm.sigma / t1;
+    GfIParam q;
+    q.tau1 = (float)t1; q.tau2 = (float)t2; q.rho = (float)rho; q.pad = 0.f;
+    q.tau1d = t1; q.tau2d = t2; q.rhod = rho; q.normQ = h->ih[b].normQhat;
+    v[b] = q;
+  }
+  cudaMemcpyAsync(h->iprm + (size_t)parity * h->ninst, v.data(), sizeof(GfIParam) * h->ninst,
+                  cudaMemcpyHostToDevice, h->stream);
+}
+
+static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A,
+                              const double* const* b, const gfors_csr* const* B,
+                              const double* const* d, const gfors_qmat* const* Q,
+                              const double* const* c, const int64_t* n) {
+  const gfors_params& P = h->prm;
+  if (ninst <= 0) return gf_fail(h, GFORS_E_ARG, "ninst must be positive");
+  if (P.k_int < 1 || P.k_r < 0 || P.k_b < 32 || P.k_b % 32 != 0)
+    return gf_fail(h, GFORS_E_ARG, "need k_int >= 1, k_r >= 0, k_b a positive multiple of 32");
+  if (!(P.sigma > 0.0) || !(P.sigma <= 1.0))
+    return gf_fail(h, GFORS_E_ARG, "sigma must lie in (0, 1]");
+  if (P.sample_chunk < 0 || P.sample_chunk % 32 != 0)
+    return gf_fail(h, GFORS_E_ARG, "sample_chunk must be a multiple of 32");
+  h->ninst = ninst;
+  h->ih.assign(ninst, GfInstHost());
+  std::vector<Stage> st(ninst);
+  std::vector<std::vector<double>> dense_diag(ninst);
+  std::vector<std::vector<__nv_bfloat16>> dense_w2(ninst);
+  std::string why;
+  int64_t voff = 0, roff = 0;
+  for (int q = 0; q < ninst; ++q) {
+    GfInstHost& I = h->ih[q];
+    Stage& S = st[q];
+    const gfors_csr* Aq = A ? A[q] : nullptr;
+    const gfors_csr* Bq = B ? B[q] : nullptr;
+    const gfors_qmat* Qq = Q ? Q[q] : nullptr;
+    if (!n || n[q] <= 0) return gf_fail(h, GFORS_E_ARG, "n must be positive");
+    if (n[q] >= (1ll << 30)) return gf_fail(h, GFORS_E_UNSUPPORTED, "n >= 2^30");
+    I.n = n[q];
+    I.npad = gf_round_up(I.n, 64);
+    if (!c || !c[q]) return gf_fail(h, GFORS_E_ARG, "c is NULL");
+    if (!check_csr(Aq, I.n, why) || !check_csr(Bq, I.n, why))
+      return gf_fail(h, GFORS_E_ARG, "instance " + std::to_string(q) + ": " + why);
+    I.m1 = Aq ? Aq->rows : 0;
+    I.m2 = Bq ? Bq->rows : 0;
+    if (I.m1 && (!b || !b[q])) return gf_fail(h, GFORS_E_ARG, "b is NULL");
+    if (I.m2 && (!d || !d[q])) return gf_fail(h, GFORS_E_ARG, "d is NULL");
+    I.var_off = voff;
+    I.row_off = roff;
+    voff += I.npad;
+    roff += I.m1 + I.m2;
+    bool integral = true;
+    for (int64_t i = 0; i < I.n; ++i) {
+      if (!std::isfinite(c[q][i])) return gf_fail(h, GFORS_E_ARG, "c not finite");
+      integral &= is_int31(c[q][i]);
+    }
+    // rows of K = -[A;B] (Eq. 2) and the original rows for evaluation
+    for (int part = 0; part < 2; ++part) {
+      const gfors_csr* M = part ? Bq : Aq;
+      const double* rhs = part ? (d ? d[q] : nullptr) : (b ? b[q] : nullptr);
+      if (!M) continue;
+      for (int64_t r = 0; r < M->rows; ++r) {
+        if (!std::isfinite(rhs[r])) return gf_fail(h, GFORS_E_ARG, "rhs not finite");
+        Row o = merged_row(M, r, 1.0);
+        Row k = o;
+        for (double& v : k.val) v = -v;
+        for (double v : o.val) integral &= is_int31(v);
+        integral &= is_int31(rhs[r]);
+        S.K.push_back(std::move(k));
+        S.r.push_back(rhs[r]);
+        S.eq.push_back((uint8_t)part);
+        S.orig.push_back(std::move(o));
+        S.rhs.push_back(is_int31(rhs[r]) ? (long long)rhs[r] : 0);
+      }
+    }
+    // Preprocess step 1: row 2-norms
+    S.rownorm.resize(S.K.size());
+    for (size_t j = 0; j < S.K.size(); ++j) {
+      double s = 0.0;
+      for (double v : S.K[j].val) s += v * v;
+      s = sqrt(s);
+      S.rownorm[j] = s;
+      if (s > 0.0) {
+        for (double& v : S.K[j].val) v /= s;
+        S.r[j] /= s;
+      } else if ((!S.eq[j] && S.r[j] > 0.0) || (S.eq[j] && S.r[j] != 0.0)) {
+        return gf_fail(h, GFORS_E_ARG, "instance " + std::to_string(q) + ": empty row " +
+                                           std::to_string(j) + " cannot be satisfied");
+      }
+    }
+    // Q
+    I.qkind = 0;
+    if (Qq && Qq->kind == 1) {
+      if (!Qq->dense_rowmajor) return gf_fail(h, GFORS_E_ARG, "dense Q pointer is NULL");
+      const double* Qd = Qq->dense_rowmajor;
+      bool qint = true;
+      long long w2max = 0;
+      for (int64_t i = 0; i < I.n && qint; ++i)
+        for (int64_t j = 0; j < I.n; ++j) {
+          const double v = Qd[i * I.n + j];
+          if (!std::isfinite(v)) return gf_fail(h, GFORS_E_ARG, "Q not finite");
+          if (!is_int31(v)) { qint = false; break; }
+          if (i != j) {
+            double w = v + Qd[j * I.n + i];
+            if (std::fabs(w) > (double)w2max) w2max = (long long)std::fabs(w);
+          }
+        }
+      const bool tc = qint && integral && I.m1 + I.m2 == 0 && w2max <= 256 &&
+                      (double)I.n * (double)w2max < 16777216.0 && P.eval_mode != 1 &&
+                      P.eval_mode != 2;
+      if (tc) {
+        I.qkind = 1;
+        GfDenseQ dq;
+        dq.inst = q;
+        dq.n = I.n;
+        dq.ld = gf_round_up(I.n, 64);
+        dq.w2max = w2max;
+        dq.tc_ok = true;
+        dense_w2[q].assign((size_t)I.n * dq.ld, __float2bfloat16(0.0f));
+        dense_diag[q].resize(I.n);
+        for (int64_t i = 0; i < I.n; ++i) {
+          for (int64_t j = 0; j < I.n; ++j)
+            if (i != j)
+              dense_w2[q][(size_t)i * dq.ld + j] =
+                  __float2bfloat16((float)(Qd[i * I.n + j] + Qd[j * I.n + i]));
+          dense_diag[q][i] = Qd[i * I.n + i];
+        }
+        I.dense_idx = (int)h->dense.size();
+        h->dense.push_back(dq);
+      } else {
+        I.qkind = 2;
+        S.Qsym.resize(I.n);
+        S.Qorig.resize(I.n);
+        for (int64_t i = 0; i < I.n; ++i)
+          for (int64_t j = 0; j < I.n; ++j) {
+            const double v = Qd[i * I.n + j];
+            if (v != 0.0) { S.Qorig[i].col.push_back((int32_t)j); S.Qorig[i].val.push_back(v); }
+            const double s = 0.5 * (v + Qd[j * I.n + i]);
+            if (s != 0.0) { S.Qsym[i].col.push_back((int32_t)j); S.Qsym[i].val.push_back(s); }
+            integral &= is_int31(v);
+          }
+      }
+    } else if (Qq && Qq->kind == 2) {
+      if (!check_csr(&Qq->sparse, I.n, why) || Qq->sparse.rows != I.n)
+        return gf_fail(h, GFORS_E_ARG, "Q: " + why);
+      I.qkind = 2;
+      S.Qorig.resize(I.n);
+      std::vector<std::vector<std::pair<int32_t, double>>> sym(I.n);
+      for (int64_t i = 0; i < I.n; ++i) {
+        S.Qorig[i] = merged_row(&Qq->sparse, i, 1.0);
+        for (size_t t = 0; t < S.Qorig[i].col.size(); ++t) {
+          const int32_t j = S.Qorig[i].col[t];
+          const double v = S.Qorig[i].val[t];
+          integral &= is_int31(v);
+          sym[i].emplace_back(j, 0.5 * v);
+          sym[j].emplace_back((int32_t)i, 0.5 * v);
+        }
+      }
+      S.Qsym.resize(I.n);
+      for (int64_t i = 0; i < I.n; ++i) {
+        auto& e = sym[i];
+        std::sort(e.begin(), e.end(),
+                  [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+                    return x.first < y.first;
+                  });
+        for (size_t u = 0; u < e.size();) {
+          size_t w = u;
+          double s = 0.0;
+          while (w < e.size() && e[w].first == e[u].first) s += e[w++].second;
+          if (s != 0.0) { S.Qsym[i].col.push_back(e[u].first); S.Qsym[i].val.push_back(s); }
+          u = w;
+        }
+      }
+      bool any = false;
+      for (auto& rw : S.Qsym) any |= !rw.col.empty();
+      if (!any) I.qkind = 0;
+    } else if (Qq && Qq->kind != 0) {
+      return gf_fail(h, GFORS_E_ARG, "Q.kind must be 0, 1 or 2");
+    }
+    I.integral = integral;
+    I.cap = (P.tau_cap_by_L < 0) ? (I.qkind != 0) : (P.tau_cap_by_L != 0);
+    I.single_row = (I.m1 == 1 && I.m2 == 0 && I.qkind == 0);
+    h->all_integral &= integral;
+  }
+  h->N = voff;
+  h->M = roff;
+  const int64_t N = h->N, M = h->M;
+  if (N >= (1ll << 31) - 64) return gf_fail(h, GFORS_E_UNSUPPORTED, "total variables >= 2^31");
+
+  // ---------------- concatenate K (FP64, global indices) and build CSC
+  std::vector<int64_t> Kp(M + 1, 0);
+  std::vector<int32_t> row_inst(M), Kc;
+  std::vector<double> Kd, rd(M);
+  std::vector<uint8_t> row_eq(M);
+  for (int q = 0; q < ninst; ++q) {
+    const GfInstHost& I = h->ih[q];
+    for (size_t j = 0; j < st[q].K.size(); ++j) {
+      const int64_t gj = I.row_off + (int64_t)j;
+      Kp[gj + 1] = (int64_t)st[q].K[j].col.size();
+      row_inst[gj] = q;
+      rd[gj] = st[q].r[j];
+      row_eq[gj] = st[q].eq[j];
+    }
+  }
+  for (int64_t j = 0; j < M; ++j) Kp[j + 1] += Kp[j];
+  h->nnzK = Kp[M];
+  if (h->nnzK >= (1ll << 31)) return gf_fail(h, GFORS_E_UNSUPPORTED, "nnz(K) >= 2^31");
+  Kc.resize(h->nnzK);
+  Kd.resize(h->nnzK);
+  for (int q = 0; q < ninst; ++q) {
+    const GfInstHost& I = h->ih[q];
+    for (size_t j = 0; j < st[q].K.size(); ++j) {
+      int64_t t = Kp[I.row_off + (int64_t)j];
+      for (size_t u = 0; u < st[q].K[j].col.size(); ++u, ++t) {
+        Kc[t] = (int32_t)(I.var_off + st[q].K[j].col[u]);
+        Kd[t] = st[q].K[j].val[u];
+      }
+    }
+  }
+  std::vector<int64_t> Tp(N + 1, 0);
+  for (int64_t t = 0; t < h->nnzK; ++t) Tp[Kc[t] + 1]++;
+  for (int64_t i = 0; i < N; ++i) Tp[i + 1] += Tp[i];
+  std::vector<int32_t> Tr(h->nnzK);
+  std::vector<double> Td(h->nnzK);
+  {
+    std::vector<int64_t> fill(Tp.begin(), Tp.end() - 1);
+    for (int64_t j = 0; j < M; ++j)
+      for (int64_t t = Kp[j]; t < Kp[j + 1]; ++t) {
+        const int64_t pos = fill[Kc[t]]++;
+        Tr[pos] = (int32_t)j;
+        Td[pos] = Kd[t];
+      }
+  }
+  // Q_sym (sparse instances), global indices
+  std::vector<int64_t> Qp(N + 1, 0);
+  std::vector<int32_t> Qc;
+  std::vector<double> Qd;
+  for (int q = 0; q < ninst; ++q) {
+    const GfInstHost& I = h->ih[q];
+    if (I.qkind != 2) continue;
+    for (int64_t i = 0; i < I.n; ++i) Qp[I.var_off + i + 1] = (int64_t)st[q].Qsym[i].col.size();
+  }
+  for (int64_t i = 0; i < N; ++i) Qp[i + 1] += Qp[i];
+  h->nnzQ = Qp[N];
+  Qc.resize(h->nnzQ);
+  Qd.resize(h->nnzQ);
+  for (int q = 0; q < ninst; ++q) {
+    const GfInstHost& I = h->ih[q];
+    if (I.qkind != 2) continue;
+    for (int64_t i = 0; i < I.n; ++i) {
+      int64_t t = Qp[I.var_off + i];
+      for (size_t u = 0; u < st[q].Qsym[i].col.size(); ++u, ++t) {
+        Qc[t] = (int32_t)(I.var_off + st[q].Qsym[i].col[u]);
+        Qd[t] = st[q].Qsym[i].val[u];
+      }
+    }
+  }
+  std::vector<int32_t> var_inst(N);
+  std::vector<uint8_t> live(N, 0);
+  std::vector<int64_t> var_off(ninst + 1);
+  std::vector<double> cd(N, 0.0);
+  std::vector<long long> cint(N, 0);
+  for (int q = 0; q < ninst; ++q) {
+    const GfInstHost& I = h->ih[q];
+    var_off[q] = I.var_off;
+    for (int64_t i = 0; i < I.npad; ++i) var_inst[I.var_off + i] = q;
+    for (int64_t i = 0; i < I.n; ++i) {
+      live[I.var_off + i] = 1;
+      cd[I.var_off + i] = c[q][i];
+      cint[I.var_off + i] = I.integral ? (long long)c[q][i] : 0;
+    }
+  }
+  var_off[ninst] = N;
+
+  // ---------------- device allocations
+  cudaStream_t s = h->stream;
+#define ALLOC(ptr, T, cnt)                                          \
+  do {                                                              \
+    ptr = gf_alloc_t<T>(h, (size_t)(cnt));                          \
+    if (!ptr) return gf_fail(h, GFORS_E_OOM, "allocating " #ptr);   \
+  } while (0)
+#define UP(dst, src, T, cnt) \
+  GF_CK(h, cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)(cnt), cudaMemcpyHostToDevice, s))
+
+  ALLOC(h->var_off_d, int64_t, ninst + 1);
+  ALLOC(h->var_inst, int32_t, N);
+  ALLOC(h->var_live, uint8_t, N);
+  ALLOC(h->row_inst, int32_t, M);
+  ALLOC(h->row_eq, uint8_t, M);
+  ALLOC(h->Kp, int64_t, M + 1);
+  ALLOC(h->Kc, int32_t, h->nnzK);
+  ALLOC(h->Kv, float, h->nnzK);
+  ALLOC(h->Tp, int64_t, N + 1);
+  ALLOC(h->Tr, int32_t, h->nnzK);
+  ALLOC(h->Tv, float, h->nnzK);
+  ALLOC(h->Qp, int64_t, N + 1);
+  ALLOC(h->Qc, int32_t, h->nnzQ);
+  ALLOC(h->Qv, float, h->nnzQ);
+  ALLOC(h->rhat, float, M);
+  ALLOC(h->chat, float, N);
+  UP(h->var_off_d, var_off.data(), int64_t, ninst + 1);
+  UP(h->var_inst, var_inst.data(), int32_t, N);
+  UP(h->var_live, live.data(), uint8_t, N);
+  UP(h->row_inst, row_inst.data(), int32_t, M);
+  UP(h->row_eq, row_eq.data(), uint8_t, M);
+  UP(h->Kp, Kp.data(), int64_t, M + 1);
+  UP(h->Kc, Kc.data(), int32_t, h->nnzK);
+  UP(h->Tp, Tp.data(), int64_t, N + 1);
+  UP(h->Tr, Tr.data(), int32_t, h->nnzK);
+  UP(h->Qp, Qp.data(), int64_t, N + 1);
+  UP(h->Qc, Qc.data(), int32_t, h->nnzQ);
+
+  // chunk tables for deterministic per-instance reductions
+  {
+    std::vector<int32_t> vch, vptr(ninst + 1), rch, rptr(ninst + 1);
+    for (int q = 0; q < ninst; ++q) {
+      const GfInstHost& I = h->ih[q];
+      vptr[q] = (int32_t)(vch.size() / 3);
+      for (int64_t a = 0; a < I.npad; a += 2048) {
+        vch.push_back(q);
+        vch.push_back((int32_t)(I.var_off + a));
+        vch.push_back((int32_t)(I.var_off + std::min<int64_t>(I.npad, a + 2048)));
+      }
+      rptr[q] = (int32_t)(rch.size() / 3);
+      for (int64_t a = 0; a < I.m1 + I.m2; a += 2048) {
+        rch.push_back(q);
+        rch.push_back((int32_t)(I.row_off + a));
+        rch.push_back((int32_t)(I.row_off + std::min<int64_t>(I.m1 + I.m2, a + 2048)));
+      }
+    }
+    vptr[ninst] = (int32_t)(vch.size() / 3);
+    rptr[ninst] = (int32_t)(rch.size() / 3);
+    h->nvchunk = (int64_t)vch.size() / 3;
+    h->nrchunk = (int64_t)rch.size() / 3;
+    ALLOC(h->vchunk, int32_t, vch.size());
+    ALLOC(h->rchunk, int32_t, rch.size() + 3);
+    ALLOC(h->vchunk_iptr, int32_t, ninst + 1);
+    ALLOC(h->rchunk_iptr, int32_t, ninst + 1);
+    UP(h->vchunk, vch.data(), int32_t, vch.size());
+    if (!rch.empty()) UP(h->rchunk, rch.data(), int32_t, rch.size());
+    UP(h->vchunk_iptr, vptr.data(), int32_t, ninst + 1);
+    UP(h->rchunk_iptr, rptr.data(), int32_t, ninst + 1);
+  }
+
+  // dense operands
+  std::vector<double*> ddiag(h->dense.size(), nullptr);
+  for (size_t u = 0; u < h->dense.size(); ++u) {
+    GfDenseQ& dq = h->dense[u];
+    ALLOC(dq.W2, __nv_bfloat16, dq.n * dq.ld);
+    ALLOC(dq.qdiag, float, dq.ld);
+    ALLOC(dq.lin, long long, dq.ld);
+    ALLOC(ddiag[u], double, dq.n);
+    UP(dq.W2, dense_w2[dq.inst].data(), __nv_bfloat16, dq.n * dq.ld);
+    UP(ddiag[u], dense_diag[dq.inst].data(), double, dq.n);
+    std::vector<long long> lin(dq.ld, 0);
+    for (int64_t i = 0; i < dq.n; ++i)
+      lin[i] = (long long)c[dq.inst][i] + (long long)dense_diag[dq.inst][i];
+    UP(dq.lin, lin.data(), long long, dq.ld);
+  }
+
+  // ---------------- Preprocess on the device: spectral norms (FP64)
+  double *Kd_d = nullptr, *Td_d = nullptr, *Qd_d = nullptr, *rd_d = nullptr, *cd_d = nullptr;
+  ALLOC(Kd_d, double, h->nnzK);
+  ALLOC(Td_d, double, h->nnzK);
+  ALLOC(Qd_d, double, h->nnzQ);
+  ALLOC(rd_d, double, M);
+  ALLOC(cd_d, double, N);
+  UP(Kd_d, Kd.data(), double, h->nnzK);
+  UP(Td_d, Td.data(), double, h->nnzK);
+  UP(Qd_d, Qd.data(), double, h->nnzQ);
+  UP(rd_d, rd.data(), double, M);
+  UP(cd_d, cd.data(), double, N);
+  GF_CK(h, cudaStreamSynchronize(s));
+  std::vector<double> nQ(ninst, 0.0), nK(ninst, 0.0);
+  std::vector<int> itQ(ninst, 0), itK(ninst, 0);
+  GF_CK(h, gf_power_run(h, 1, h->nnzQ ? h->Qp : nullptr, Qc.empty() ? nullptr : h->Qc, Qd_d,
+                        nullptr, nullptr, nullptr, N, nullptr, 0, nullptr, ddiag.data(),
+                        nQ.data(), itQ.data()));
+  if (M > 0)
+    GF_CK(h, gf_power_run(h, 0, h->Kp, h->Kc, Kd_d, h->Tp, h->Tr, Td_d, M, h->rchunk,
+                          h->nrchunk, h->rchunk_iptr, nullptr, nK.data(), itK.data()));
+  std::vector<double> sK(ninst), sobj(ninst), nQhat(ninst);
+  std::vector<int32_t> capv(ninst);
+  for (int q = 0; q < ninst; ++q) {
+    GfInstHost& I = h->ih[q];
+    double cn = 0.0;
+    for (int64_t i = 0; i < I.n; ++i) cn += c[q][i] * c[q][i];
+    I.normQ_raw = nQ[q];
+    I.s_obj = nQ[q] + sqrt(cn);
+    if (I.s_obj == 0.0) I.s_obj = 1.0;
+    I.normK = nK[q];
+    I.s_K = nK[q] > 0.0 ? nK[q] : 1.0;
+    I.normQhat = nQ[q] / I.s_obj;
+    I.itQ = itQ[q];
+    I.itK = itK[q];
+    sK[q] = I.s_K;
+    sobj[q] = I.s_obj;
+    nQhat[q] = I.normQhat;
+    capv[q] = I.cap;
+  }
+  double *sK_d = nullptr, *sobj_d = nullptr;
+  ALLOC(sK_d, double, ninst);
+  ALLOC(sobj_d, double, ninst);
+  ALLOC(h->normQhat_d, double, ninst);
+  ALLOC(h->cap_d, int32_t, ninst);
+  UP(sK_d, sK.data(), double, ninst);
+  UP(sobj_d, sobj.data(), double, ninst);
+  UP(h->normQhat_d, nQhat.data(), double, ninst);
+  UP(h->cap_d, capv.data(), int32_t, ninst);
+  GF_CK(h, gf_scale_to_f32(h, Kd_d, Td_d, rd_d, cd_d, Qd_d, sK_d, sobj_d));
+  for (GfDenseQ& dq : h->dense) {
+    const GfInstHost& I = h->ih[dq.inst];
+    std::vector<float> qd(dq.ld, 0.0f);
+    for (int64_t i = 0; i < dq.n; ++i) qd[i] = (float)(dense_diag[dq.inst][i] / I.s_obj);
+    UP(dq.qdiag, qd.data(), float, dq.ld);
+    dq.qscale = (float)(0.5 / I.s_obj);
+  }
+
+  // ---------------- PDHG work lists (length buckets, long chunks)
+  auto bucket_of = [](int64_t len) {
+    if (len <= 2) return 0;
+    if (len <= 8) return 1;
+    if (len <= 32) return 2;
+    if (len <= 128) return 3;
+    if (len <= kLongLen) return 4;
+    return 5;
+  };
+  static const int lanes_of[5] = {1, 4, 8, 16, 32};
+  {
+    std::vector<std::vector<int32_t>> rl(5);
+    std::vector<GfChunk> ch;
+    std::vector<int32_t> lid, lptr;
+    for (int64_t j = 0; j < M; ++j) {
+      const int64_t len = Kp[j + 1] - Kp[j];
+      const int bk = bucket_of(len);
+      if (bk < 5) {
+        rl[bk].push_back((int32_t)j);
+      } else {
+        lid.push_back((int32_t)j);
+        lptr.push_back((int32_t)ch.size());
+        for (int64_t t = Kp[j]; t < Kp[j + 1]; t += kChunkLen)
+          ch.push_back(GfChunk{(int32_t)j, 0, t, std::min(Kp[j + 1], t + kChunkLen)});
+      }
+    }
+    lptr.push_back((int32_t)ch.size());
+    for (int bk = 0; bk < 5; ++bk) {
+      GfBucket B;
+      B.lanes = lanes_of[bk];
+      B.count = (int32_t)rl[bk].size();
+      if (B.count) {
+        ALLOC(B.ids, int32_t, B.count);
+        UP(B.ids, rl[bk].data(), int32_t, B.count);
+      }
+      h->rb.push_back(B);
+    }
+    h->rlong.nlong = (int32_t)lid.size();
+    h->rlong.nchunks = (int32_t)ch.size();
+    if (!lid.empty()) {
+      ALLOC(h->rlong.ids, int32_t, lid.size());
+      ALLOC(h->rlong.chunk_ptr, int32_t, lptr.size());
+      ALLOC(h->rlong.chunks, GfChunk, ch.size());
+      ALLOC(h->rlong.partial, float2, ch.size());
+      UP(h->rlong.ids, lid.data(), int32_t, lid.size());
+      UP(h->rlong.chunk_ptr, lptr.data(), int32_t, lptr.size());
+      UP(h->rlong.chunks, ch.data(), GfChunk, ch.size());
+    }
+  }
+  {
+    std::vector<std::vector<int32_t>> cl(5);
+    std::vector<GfChunk> ch;
+    std::vector<int32_t> lid, lptr;
+    for (int q = 0; q < ninst; ++q) {
+      const GfInstHost& I = h->ih[q];
+      if (I.qkind == 1) continue;            // dense kernel handles these
+      for (int64_t i = I.var_off; i < I.var_off + I.n; ++i) {
+        const int64_t lt = Tp[i + 1] - Tp[i], lq = Qp[i + 1] - Qp[i];
+        const int bk = bucket_of(lt + lq);
+        if (bk < 5) {
+          cl[bk].push_back((int32_t)i);
+        } else {
+          lid.push_back((int32_t)i);
+          lptr.push_back((int32_t)ch.size());
+          for (int64_t t = Tp[i]; t < Tp[i + 1]; t += kChunkLen)
+            ch.push_back(GfChunk{(int32_t)i, 0, t, std::min(Tp[i + 1], t + kChunkLen)});
+          for (int64_t t = Qp[i]; t < Qp[i + 1]; t += kChunkLen)
+            ch.push_back(GfChunk{(int32_t)i, 1, t, std::min(Qp[i + 1], t + kChunkLen)});
+        }
+      }
+    }
+    lptr.push_back((int32_t)ch.size());
+    for (int bk = 0; bk < 5; ++bk) {
+      GfBucket B;
+      B.lanes = lanes_of[bk];
+      B.count = (int32_t)cl[bk].size();
+      if (B.count) {
+        ALLOC(B.ids, int32_t, B.count);
+        UP(B.ids, cl[bk].data(), int32_t, B.count);
+      }
+      h->cb.push_back(B);
+    }
+    h->clong.nlong = (int32_t)lid.size();
+    h->clong.nchunks = (int32_t)ch.size();
+    if (!lid.empty()) {
+      ALLOC(h->clong.ids, int32_t, lid.size());
+      ALLOC(h->clong.chunk_ptr, int32_t, lptr.size());
+      ALLOC(h->clong.chunks, GfChunk, ch.size());
+      ALLOC(h->clong.partial, float2, ch.size());
+      UP(h->clong.ids, lid.data(), int32_t, lid.size());
+      UP(h->clong.chunk_ptr, lptr.data(), int32_t, lptr.size());
+      UP(h->clong.chunks, ch.data(), GfChunk, ch.size());
+    }
+  }
+
+  // ---------------- evaluation structures (integer data)
+  {
+    std::vector<GfURow> ur;
+    std::vector<int32_t> ucols;
+    std::vector<GfPRow> pr;
+    std::vector<GfGRow> gr;
+    std::vector<int32_t> gcols, gvals;
+    std::vector<GfObjChunk> oc;
+    std::vector<GfQChunk> qc;
+    std::vector<int64_t> QIp(N + 1, 0);
+    std::vector<int32_t> QIc, QIv;
+    for (int q = 0; q < ninst; ++q) {
+      const GfInstHost& I = h->ih[q];
+      if (!I.integral) continue;
+      const Stage& S = st[q];
+      for (size_t j = 0; j < S.orig.size(); ++j) {
+        const Row& o = S.orig[j];
+        const long long rhs = S.rhs[j];
+        const bool eq = S.eq[j] != 0;
+        const int len = (int)o.col.size();
+        if (len <= 2) {
+          GfPRow R;
+          R.inst = q;
+          R.v1 = len >= 1 ? (int32_t)(I.var_off + o.col[0]) : 0;
+          R.v2 = len >= 2 ? (int32_t)(I.var_off + o.col[1]) : -1;
+          R.table = 0;
+          for (int m = 0; m < 4; ++m) {
+            const int x1 = m & 1, x2 = (m >> 1) & 1;
+            if (len < 1 && x1) continue;
+            if (len < 2 && x2) continue;
+            long long sum = (len >= 1 ? (long long)o.val[0] * x1 : 0) +
+                            (len >= 2 ? (long long)o.val[1] * x2 : 0);
+            const bool bad = eq ? (sum != rhs) : (sum < rhs);
+            if (bad) R.table |= 1u << m;
+          }
+          if (len == 0) R.v1 = (int32_t)I.var_off;    // read any word; table uses x1=0
+          if (len == 0 && R.table) {                    // constant violated row
+            R.table = 0xFu;
+          }
+          if (R.table) pr.push_back(R);
+          continue;
+        }
+        bool uni = len < 65536;
+        for (int t = 1; t < len && uni; ++t) uni = (o.val[t] == o.val[0]);
+        bool placed = false;
+        if (uni) {
+          const long long a = (long long)o.val[0];
+          long long L = 0, U = -1;
+          bool ok = true;
+          if (!eq) {
+            if (a > 0) { L = std::max(0ll, ceil_div(rhs, a)); U = -1; }
+            else { U = floor_div(rhs, a); L = 0; if (U < 0) ok = false; }
+            if (L > len) ok = false;
+          } else {
+            if (rhs % a != 0) ok = false;
+            else { L = U = rhs / a; if (L < 0 || L > len) ok = false; }
+          }
+          if (ok && U >= len) U = -1;
+          if (ok) {
+            if (L <= 0 && U < 0) { placed = true; }      // never violated
+            else if (L < 65536 && U < 65536) {
+              GfURow R;
+              R.inst = q;
+              R.len = len;
+              R.t0 = (int64_t)ucols.size();
+              R.L = (int32_t)L;
+              R.U = (int32_t)U;
+              for (int32_t col : o.col) ucols.push_back((int32_t)(I.var_off + col));
+              ur.push_back(R);
+              placed = true;
+            }
+          }
+        }
+        if (!placed) {
+          GfGRow R;
+          R.inst = q;
+          R.len = len;
+          R.t0 = (int64_t)gcols.size();
+          R.rhs = rhs;
+          R.eq = eq;
+          R.pad = 0;
+          for (int t = 0; t < len; ++t) {
+            gcols.push_back((int32_t)(I.var_off + o.col[t]));
+            gvals.push_back((int32_t)o.val[t]);
+          }
+          gr.push_back(R);
+        }
+      }
+      for (int64_t a = 0; a < I.n; a += 1024)
+        oc.push_back(GfObjChunk{q, (int32_t)(I.var_off + a),
+                                (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 1024)), 0});
+      if (I.qkind == 2) {
+        for (int64_t i = 0; i < I.n; ++i) QIp[I.var_off + i + 1] = (int64_t)S.Qorig[i].col.size();
+        for (int64_t a = 0; a < I.n; a += 64)
+          qc.push_back(GfQChunk{q, (int32_t)(I.var_off + a),
+                                (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 64)), 0});
+      }
+    }
+    for (int64_t i = 0; i < N; ++i) QIp[i + 1] += QIp[i];
+    QIc.resize(QIp[N]);
+    QIv.resize(QIp[N]);
+    for (int q = 0; q < ninst; ++q) {
+      const GfInstHost& I = h->ih[q];
+      if (!I.integral || I.qkind != 2) continue;
+      for (int64_t i = 0; i < I.n; ++i) {
+        int64_t t = QIp[I.var_off + i];
+        for (size_t u = 0; u < st[q].Qorig[i].col.size(); ++u, ++t) {
+          QIc[t] = (int32_t)(I.var_off + st[q].Qorig[i].col[u]);
+          QIv[t] = (int32_t)st[q].Qorig[i].val[u];
+        }
+      }
+    }
+    h->nurows = (int64_t)ur.size();
+    h->nprows = (int64_t)pr.size();
+    h->ngrows = (int64_t)gr.size();
+    h->nochunks = (int64_t)oc.size();
+    h->nqchunks = (int64_t)qc.size();
+    ALLOC(h->urows, GfURow, ur.size());
+    ALLOC(h->ucols, int32_t, ucols.size());
+    ALLOC(h->prows, GfPRow, pr.size());
+    ALLOC(h->grows, GfGRow, gr.size());
+    ALLOC(h->gcols, int32_t, gcols.size());
+    ALLOC(h->gvals, int32_t, gvals.size());
+    ALLOC(h->ochunks, GfObjChunk, oc.size());
+    ALLOC(h->qchunks, GfQChunk, qc.size());
+    ALLOC(h->QIp, int64_t, N + 1);
+    ALLOC(h->QIc, int32_t, QIc.size());
+    ALLOC(h->QIv, int32_t, QIv.size());
+    ALLOC(h->cint, long long, N);
+    if (!ur.empty()) UP(h->urows, ur.data(), GfURow, ur.size());
+    if (!ucols.empty()) UP(h->ucols, ucols.data(), int32_t, ucols.size());
+    if (!pr.empty()) UP(h->prows, pr.data(), GfPRow, pr.size());
+    if (!gr.empty()) UP(h->grows, gr.data(), GfGRow, gr.size());
+    if (!gcols.empty()) UP(h->gcols, gcols.data(), int32_t, gcols.size());
+    if (!gvals.empty()) UP(h->gvals, gvals.data(), int32_t, gvals.size());
+    if (!oc.empty()) UP(h->ochunks, oc.data(), GfObjChunk, oc.size());
+    if (!qc.empty()) UP(h->qchunks, qc.data(), GfQChunk, qc.size());
+    UP(h->QIp, QIp.data(), int64_t, N + 1);
+    if (!QIc.empty()) UP(h->QIc, QIc.data(), int32_t, QIc.size());
+    if (!QIv.empty()) UP(h->QIv, QIv.data(), int32_t, QIv.size());
+    UP(h->cint, cint.data(), long long, N);
+  }
+
+  // ---------------- fused single-row path (every instance one >= row, no Q)
+  {
+    bool ok = h->all_integral && P.eval_mode != 1 && P.eval_mode != 3;
+    for (int q = 0; q < ninst && ok; ++q) ok = h->ih[q].single_row;
+    long long worst = 0;
+    if (ok) {
+      for (int q = 0; q < ninst && ok; ++q) {
+        long long s = 0;
+        for (double v : st[q].orig[0].val) s += (long long)std::fabs(v);
+        worst = std::max(worst, s);
+      }
+    }
+    h->fused_ok = ok;
+    if (ok) {
+      std::vector<int32_t> w(N, 0), blk;
+      std::vector<long long> rhs(ninst);
+      for (int q = 0; q < ninst; ++q) {
+        const GfInstHost& I = h->ih[q];
+        const Row& o = st[q].orig[0];
+        for (size_t t = 0; t < o.col.size(); ++t) w[I.var_off + o.col[t]] = (int32_t)o.val[t];
+        rhs[q] = st[q].rhs[0];
+        for (int64_t a = 0; a < I.npad; a += 8192) {
+          blk.push_back(q);
+          blk.push_back((int32_t)(I.var_off + a));
+          blk.push_back((int32_t)(I.var_off + std::min<int64_t>(I.npad, a + 8192)));
+        }
+      }
+      // longest slices first (better tail)
+      h->nfblk = (int64_t)blk.size() / 3;
+      ALLOC(h->frow_w, int32_t, N);
+      ALLOC(h->frhs, long long, ninst);
+      ALLOC(h->fblk, int32_t, blk.size());
+      UP(h->frow_w, w.data(), int32_t, N);
+      UP(h->frhs, rhs.data(), long long, ninst);
+      UP(h->fblk, blk.data(), int32_t, blk.size());
+    }
+  }
+
+  // ---------------- iterate, state, sampling buffers
+  h->chunk = P.sample_chunk > 0 ? std::min(P.sample_chunk, P.k_b) : P.k_b;
+  h->kw = h->chunk / 32;
+  ALLOC(h->x[0], float, N);
+  ALLOC(h->x[1], float, N);
+  ALLOC(h->xbar, float, N);
+  ALLOC(h->y, float, M);
+  ALLOC(h->dlast, float, N);
+  ALLOC(h->qbuf, float, N);
+  ALLOC(h->qbuf2, float, N);
+  ALLOC(h->dxbuf, float, N);
+  ALLOC(h->dstate, GfDState, 1);
+  ALLOC(h->iprm, GfIParam, 2 * ninst);
+  ALLOC(h->sched_d, GfSched, 1);
+  ALLOC(h->X, uint32_t, (size_t)N * h->kw);
+  ALLOC(h->viol, int32_t, (size_t)ninst * h->chunk);
+  ALLOC(h->obj, long long, (size_t)ninst * h->chunk);
+  if (h->fused_ok) ALLOC(h->fsum, long long, (size_t)ninst * h->chunk);
+  ALLOC(h->inc, GfInc, ninst);
+  ALLOC(h->xbest, uint8_t, N);
+  ALLOC(h->var_grouped, uint8_t, N);
+  ALLOC(h->stats_part, double, 8 * (h->nrchunk + h->nvchunk + 1));
+  ALLOC(h->stats, double, 8 * ninst);
+  ALLOC(h->stats2, double, 8 * ninst);
+  ALLOC(h->inst_dense, uint8_t, ninst);
+  for (GfDenseQ& dq : h->dense) {
+    dq.chunk = h->chunk;
+    ALLOC(dq.Xs, __nv_bfloat16, (size_t)h->chunk * dq.ld);
+  }
+  {
+    std::vector<uint8_t> grouped(N, 0), idense(ninst, 0);
+    for (const GfDenseQ& dq : h->dense) {
+      idense[dq.inst] = 1;
+      const GfInstHost& I = h->ih[dq.inst];
+      for (int64_t i = 0; i < I.npad; ++i) grouped[I.var_off + i] = 1;  // no bit sampling
+    }
+    UP(h->var_grouped, grouped.data(), uint8_t, N);
+    UP(h->inst_dense, idense.data(), uint8_t, ninst);
+  }
+  GF_CK(h, cudaMemsetAsync(h->inc, 0, sizeof(GfInc) * ninst, s));
+  GF_CK(h, cudaMemsetAsync(h->xbest, 0, N, s));
+  GF_CK(h, cudaMemsetAsync(h->y, 0, sizeof(float) * std::max<int64_t>(M, 1), s));
+  GF_CK(h, cudaMemsetAsync(h->dlast, 0, sizeof(float) * N, s));
+  GF_CK(h, cudaMemsetAsync(h->qbuf, 0, sizeof(float) * N, s));
+  GF_CK(h, cudaMemsetAsync(h->qbuf2, 0, sizeof(float) * N, s));
+  // start point x_0 (Alg. 1): constant, or Philox uniforms (stream 5)
+  {
+    std::vector<float> x0(N, 0.0f);
+    for (int q = 0; q < ninst; ++q) {
+      const GfInstHost& I = h->ih[q];
+      if (P.x0 >= 0.0) {
+        const float v = (float)std::min(1.0, P.x0);
+        for (int64_t i = 0; i < I.n; ++i) x0[I.var_off + i] = v;
+      }
+    }
+    UP(h->x[0], x0.data(), float, N);
+    if (P.x0 < 0.0) {
+      extern cudaError_t gf_launch_x0_random(GfCtx * h);
+      GF_CK(h, gf_launch_x0_random(h));
+    }
+    GF_CK(h, cudaMemcpyAsync(h->x[1], h->x[0], sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+    GF_CK(h, cudaMemcpyAsync(h->xbar, h->x[0], sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+  }
+  h->sched = GfSched{P.sigma, P.rho_min, P.rho_max, P.T, P.p, P.delta, P.k_int, ninst};
+  UP(h->sched_d, &h->sched, GfSched, 1);
+  h->k_host = 0;
+  h->n_rho_host = 0;
+  h->rho_host = std::min(P.rho_min, P.rho_max);
+  GfDState ds;
+  memset(&ds, 0, sizeof(ds));
+  ds.k = 0;
+  ds.n_rho = 0;
+  ds.rho = h->rho_host;
+  ds.round_id = 0;
+  UP(h->dstate, &ds, GfDState, 1);
+  gf_set_slot(h, 1, h->rho_host);     // iteration 1 reads slot 1
+  GF_CK(h, cudaStreamSynchronize(s));
+  h->h_best.assign(3 * ninst, INFINITY);
+  h->h_last.assign(3 * ninst, 0);
+  h->h_trig = 0;
+  return GFORS_OK;
+#undef ALLOC
+#undef UP
+}
+
+static gfors_status make_ctx(const gfors_params* prm, void* stream, GfCtx** out) {
+  if (!out) { g_thread_err = "out handle is NULL"; return GFORS_E_ARG; }
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g_thread_err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return GFORS_E_CUDA;
+  }
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    g_thread_err = "cudaGetDeviceProperties failed";
+    return GFORS_E_CUDA;
+  }
+  if (!(pr.major == 10 && pr.minor == 3)) {
+    g_thread_err = "this build targets sm_103a (B300); device is sm_" + std::to_string(pr.major) +
+                   std::to_string(pr.minor);
+    return GFORS_E_UNSUPPORTED;
+  }
+  GfCtx* h = new GfCtx();
+  if (prm) h->prm = *prm; else gfors_default_params(&h->prm);
+  h->stream = (cudaStream_t)stream;
+  if (!h->stream) {          // own a stream: graph capture needs a non-legacy stream
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      g_thread_err = "cudaStreamCreate failed";
+      return GFORS_E_CUDA;
+    }
+    h->own_stream = true;
+  }
+  h->dev = dev;
+  *out = h;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_load_batch(int32_t ninst, const gfors_csr* const* A,
+                                         const double* const* b, const gfors_csr* const* B,
+                                         const double* const* d, const gfors_qmat* const* Q,
+                                         const double* const* c, const int64_t* n,
+                                         const gfors_params* prm, void* cuda_stream,
+                                         gfors_handle* out) {
+  GfCtx* h = nullptr;
+  gfors_status st = make_ctx(prm, cuda_stream, &h);
+  if (st != GFORS_OK) return st;
+  st = load_impl(h, ninst, A, b, B, d, Q, c, n);
+  if (st != GFORS_OK) {
+    g_thread_err = h->err;
+    cudaStreamSynchronize(h->stream);
+    gf_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_load(const gfors_csr* A, const double* b, const gfors_csr* B,
+                                   const double* d, const gfors_qmat* Q, const double* c,
+                                   int64_t n, const gfors_params* prm, void* cuda_stream,
+                                   gfors_handle* out) {
+  const gfors_csr* Aa[1] = {A};
+  const double* ba[1] = {b};
+  const gfors_csr* Ba[1] = {B};
+  const double* da[1] = {d};
+  const gfors_qmat* Qa[1] = {Q};
+  const double* ca[1] = {c};
+  int64_t na[1] = {n};
+  return gfors_load_batch(1, Aa, ba, Ba, da, Qa, ca, na, prm, cuda_stream, out);
+}
+
+extern "C" void gfors_destroy(gfors_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->g_pair) cudaGraphExecDestroy(h->g_pair);
+  for (int q = 0; q < 2; ++q)
+    if (h->g_iter2[q]) cudaGraphExecDestroy(h->g_iter2[q]);
+  gf_free_all(h);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}

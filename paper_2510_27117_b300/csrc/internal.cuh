@@ -1,0 +1,290 @@
+// internal.cuh -- host-side context of a GFORS handle and kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gfors.h"
+
+// ---------------------------------------------------------------------------
+// Work lists of the PDHG kernels.  Rows (dual step) and columns (primal
+// step) are bucketed by length; each bucket is processed by groups of
+// `lanes` threads; lengths above kLongLen are split into chunks whose
+// partial sums are combined in a fixed order by a finalising kernel.
+// ---------------------------------------------------------------------------
+constexpr int kLongLen = 2048;     // rows/cols longer than this are chunked
+constexpr int kChunkLen = 2048;    // nnz per partial-sum chunk
+
+struct GfChunk {                    // one partial-sum chunk of a long row/col
+  int32_t id;                       // row (dual) or column (primal)
+  int32_t part;                     // 0: K entries, 1: Q entries (primal)
+  int64_t t0, t1;                   // nnz range
+};
+
+struct GfBucket {
+  int lanes = 1;
+  int32_t* ids = nullptr;           // device row / column ids
+  int32_t count = 0;
+};
+
+struct GfLongSet {
+  GfChunk* chunks = nullptr;        // device
+  int32_t nchunks = 0;
+  int32_t* ids = nullptr;           // device: long row / column ids
+  int32_t* chunk_ptr = nullptr;     // device: nlong + 1 offsets into chunks
+  int32_t nlong = 0;
+  float2* partial = nullptr;        // device: (s, c) per chunk
+};
+
+// ---------------------------------------------------------------------------
+// Evaluation structures (original, unscaled, integer data).
+// ---------------------------------------------------------------------------
+struct GfURow {                     // all coefficients equal: count in [L, U]
+  int32_t inst;
+  int32_t len;
+  int64_t t0;                       // into ucols
+  int32_t L, U;                     // U < 0: no upper bound
+};
+struct GfPRow {                     // at most two nonzeros: truth table
+  int32_t inst;
+  int32_t v1, v2;                   // global variables (v2 = -1 if absent)
+  uint32_t table;                   // bit (x1 + 2 x2) set = violated
+};
+struct GfGRow {                     // general integer row
+  int32_t inst;
+  int32_t len;
+  int64_t t0;                       // into gcols / gvals
+  long long rhs;
+  int32_t eq;
+  int32_t pad;
+};
+struct GfObjChunk {                 // linear-objective chunk: vars [v0, v1)
+  int32_t inst;
+  int32_t v0, v1;
+  int32_t pad;
+};
+struct GfQChunk {                   // sparse-Q chunk: rows [r0, r1) of Q
+  int32_t inst;
+  int32_t r0, r1;
+  int32_t pad;
+};
+
+struct GfDenseQ {                   // dense +-small-integer Q (tensor-core path)
+  int inst = -1;
+  int64_t n = 0, ld = 0;            // ld: row stride in elements (mult. of 64)
+  __nv_bfloat16* W2 = nullptr;      // off-diagonal of Q + Q^T, n x ld
+  float* qdiag = nullptr;           // diag(Q_sym) / s_obj
+  float qscale = 0.f;               // 0.5 / s_obj
+  long long* lin = nullptr;         // c_i + Q_ii (original, integer)
+  __nv_bfloat16* Xs = nullptr;      // candidates, sample-major, chunk x ld
+  int chunk = 0;
+  bool tc_ok = false;               // tensor-core scoring exact (n max|W2| < 2^24)
+  long long w2max = 0;
+};
+
+struct GfInstHost {
+  int64_t n = 0, npad = 0, m1 = 0, m2 = 0;
+  int64_t var_off = 0, row_off = 0;
+  int qkind = 0;                    // 0 none, 1 dense tensor-core path, 2 sparse
+  bool integral = true;
+  double normQ_raw = 0, s_obj = 1, normK = 0, s_K = 1, normQhat = 0;
+  int itQ = 0, itK = 0;
+  int cap = 0;
+  int group_mode = 0;               // 0 Bernoulli, 1 one-hot groups, 2 axial
+  int axial_I = 0;
+  int64_t ngroups = 0;
+  int64_t grp_off = 0;              // offset into the group tables
+  int64_t nrep = 0, rep_off = 0;
+  bool single_row = false;          // eligible for fused sample+eval
+  int dense_idx = -1;
+};
+
+struct gfors_ctx {
+  gfors_params prm;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int dev = 0;
+  bool failed = false;
+  std::string err;
+  long long launches = 0;
+
+  int ninst = 0;
+  std::vector<GfInstHost> ih;
+  int64_t N = 0, M = 0, nnzK = 0, nnzQ = 0;
+
+  // allocation bookkeeping
+  std::vector<void*> allocs;
+
+  // instance tables (device)
+  int64_t* var_off_d = nullptr;     // ninst + 1
+  int32_t* var_inst = nullptr;      // N
+  int32_t* row_inst = nullptr;      // M
+  uint8_t* row_eq = nullptr;        // M
+
+  // scaled problem (FP32)
+  int64_t* Kp = nullptr; int32_t* Kc = nullptr; float* Kv = nullptr;
+  int64_t* Tp = nullptr; int32_t* Tr = nullptr; float* Tv = nullptr;
+  int64_t* Qp = nullptr; int32_t* Qc = nullptr; float* Qv = nullptr;
+  float* rhat = nullptr;
+  float* chat = nullptr;
+  uint8_t* var_live = nullptr;      // 1 for real variables, 0 for padding
+
+  // iterate
+  float* x[2] = {nullptr, nullptr}; // x_k lives in x[k & 1]
+  float* xbar = nullptr;
+  float* y = nullptr;
+  float* qbuf = nullptr;            // dense-Q products when K is present
+
+  // device state
+  GfDState* dstate = nullptr;
+  GfIParam* iprm = nullptr;         // [2][ninst]
+  GfSched sched;
+  GfSched* sched_d = nullptr;
+  double* normQhat_d = nullptr;     // ninst
+  int32_t* cap_d = nullptr;         // ninst
+  long long k_host = 0;             // mirrors dstate->k
+  int n_rho_host = 0;
+  double rho_host = 0;
+
+  // PDHG work lists
+  std::vector<GfBucket> rb, cb;     // row / column buckets
+  GfLongSet rlong, clong;
+  std::vector<GfDenseQ> dense;
+
+  // sampling
+  uint8_t* var_grouped = nullptr;   // N: 1 if drawn by a group sampler
+  int64_t ngroups_tot = 0;
+  int64_t* grp_ptr = nullptr;       // global groups (ngroups_tot + 1)
+  int64_t* grp_idx = nullptr;       // global variable ids
+  int32_t* grp_inst = nullptr;      // instance of each group
+  int32_t* grp_local = nullptr;     // group index within its instance
+  unsigned long long* grp_cw = nullptr;  // cumulative weights (per member)
+  std::vector<int64_t> h_grp_ptr, h_grp_idx;
+  std::vector<int32_t> h_grp_inst, h_grp_local;
+  bool groups_dirty = false;
+  int64_t nrep_tot = 0;
+  int64_t* rep_var = nullptr; int64_t* rep_ptr = nullptr; int64_t* rep_idx = nullptr;
+  std::vector<int64_t> h_rep_var, h_rep_ptr, h_rep_idx;
+  bool closure_dirty = false;
+  int chunk = 0;                    // candidates per pass (multiple of 32)
+  int kw = 0;                       // chunk / 32 words per variable
+  uint32_t* X = nullptr;            // variable-major bits, N x kw
+  int32_t* viol = nullptr;          // ninst x chunk
+  long long* obj = nullptr;         // ninst x chunk
+  int last_chunk_len = 0;
+  int last_mode = 0;                // how the last chunk was sampled
+  int last_s0 = 0;
+
+  // evaluation (integer data)
+  bool all_integral = true;
+  GfURow* urows = nullptr; int64_t nurows = 0; int32_t* ucols = nullptr;
+  GfPRow* prows = nullptr; int64_t nprows = 0;
+  GfGRow* grows = nullptr; int64_t ngrows = 0; int32_t* gcols = nullptr; int32_t* gvals = nullptr;
+  long long* cint = nullptr;        // N, original integer costs
+  GfObjChunk* ochunks = nullptr; int64_t nochunks = 0;
+  int64_t* QIp = nullptr; int32_t* QIc = nullptr; int32_t* QIv = nullptr;  // original Q (sparse)
+  GfQChunk* qchunks = nullptr; int64_t nqchunks = 0;
+  // fused single-row path
+  bool fused_ok = false;
+  int32_t* frow_w = nullptr;        // N: coefficient of the single row (0 for padding)
+  long long* frhs = nullptr;        // ninst
+  long long* fsum = nullptr;        // ninst x chunk row sums
+  int32_t* fblk = nullptr;          // fused work blocks: (inst, v0, v1) triples
+  int64_t nfblk = 0;
+
+  // incumbents
+  GfInc* inc = nullptr;             // ninst
+  uint8_t* xbest = nullptr;         // N (0/1 bytes)
+
+  // statistics
+  double* stats_part = nullptr;     // per stats chunk partials
+  double* stats = nullptr;          // ninst x 8 (row sums)
+  double* stats2 = nullptr;         // ninst x 8 (variable sums)
+  int32_t* vchunk = nullptr; int64_t nvchunk = 0;   // var chunks (inst, v0, v1)
+  int32_t* rchunk = nullptr; int64_t nrchunk = 0;   // row chunks (inst, r0, r1)
+  int32_t* vchunk_iptr = nullptr;   // ninst + 1
+  int32_t* rchunk_iptr = nullptr;   // ninst + 1
+  uint8_t* inst_dense = nullptr;    // ninst: 1 if dense tensor-core Q
+  float* qbuf2 = nullptr;           // N scratch (Q dx)
+  float* dxbuf = nullptr;           // N scratch (x - x_prev)
+  const float* last_p = nullptr;    // proposal of the last sampled chunk
+
+  // halting trackers (host)
+  std::vector<double> h_best;       // ninst x 3
+  std::vector<long long> h_last;    // ninst x 3
+  long long h_trig = 0;
+
+  // learned proposal
+  float* mlp_W = nullptr;
+  int64_t mlp_np = 0;
+  float* feat = nullptr;            // N x 8
+  float* x_hist = nullptr;          // N x 4 ring of trigger snapshots
+  float* x_trig_prev = nullptr;     // x at the previous trigger
+  int hist_count = 0;
+  float* p_learn = nullptr;         // N
+  float* dlast = nullptr;           // tau1 * delta of the last step (N)
+  float* degnorm = nullptr;         // column degree / max (N)
+  float* cstd = nullptr;            // standardised c (N)
+  float* grpmax = nullptr;          // N: max_{group} x (scratch)
+
+  // CUDA graphs of one PDHG iteration pair, by parity of its first iteration
+  cudaGraphExec_t g_pair = nullptr;
+  cudaGraphExec_t g_iter2[2] = {nullptr, nullptr};
+  long long pair_launches = 0;
+  bool use_graphs = true;
+  unsigned host_round = 0;          // round id of the next round (host mirror)
+  // phase profiling (CUDA events on the handle's stream)
+  bool prof = false;
+  struct ProfRec { int phase; int count; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  unsigned last_round = 0;          // round id of the last sampled chunk
+};
+
+typedef gfors_ctx GfCtx;
+
+// ---- error handling -------------------------------------------------------
+gfors_status gf_fail(GfCtx* h, gfors_status st, const std::string& msg);
+gfors_status gf_cuda(GfCtx* h, cudaError_t e, const char* what);
+#define GF_CK(h, call)                                        \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return gf_cuda((h), _e, #call);    \
+  } while (0)
+
+void* gf_alloc(GfCtx* h, size_t bytes);   // NULL on failure (status set)
+template <class T>
+T* gf_alloc_t(GfCtx* h, size_t count) {
+  return static_cast<T*>(gf_alloc(h, sizeof(T) * (count > 0 ? count : 1)));
+}
+void gf_free_all(GfCtx* h);
+void gf_free_one(GfCtx* h, void* p);
+
+// ---- launchers (each returns cudaGetLastError of its launch) --------------
+cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity);
+cudaError_t gf_launch_dense_gemv_q(GfCtx* h, const GfDenseQ& dq, const float* x,
+                                   float* out);   // out = Q_hat x (FP32)
+cudaError_t gf_launch_power(GfCtx* h, int which, const int64_t* Kp, const int32_t* Kc,
+                            const double* Kv, const int64_t* Tp, const int32_t* Tr,
+                            const double* Tv, int64_t mrows, double* norms, int* iters);
+cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense);
+cudaError_t gf_launch_eval(GfCtx* h, int s0, int len);
+cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len);
+cudaError_t gf_launch_dense_score(GfCtx* h, const GfDenseQ& dq, int s0, int len);
+cudaError_t gf_launch_incumbent(GfCtx* h, int s0, int len, int mode, bool last_chunk);
+cudaError_t gf_launch_stats(GfCtx* h);
+cudaError_t gf_launch_features(GfCtx* h);
+cudaError_t gf_launch_mlp_proposal(GfCtx* h);
+cudaError_t gf_launch_final_round(GfCtx* h);
+
+// phase profiling: returns an index to pass to gf_prof_end (or -1)
+int gf_prof_begin(GfCtx* h, int phase);
+void gf_prof_end(GfCtx* h, int idx, int count);
+
+// helpers used by several files
+int64_t gf_round_up(int64_t v, int64_t m);

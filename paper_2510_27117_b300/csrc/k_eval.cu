@@ -1,0 +1,459 @@
+// k_eval.cu -- EvalBest (Alg. 1, Section 3) on the device, on the ORIGINAL
+// integer data of Eq. (1):
+//   viol_s = #{j : A_j X_s < b_j} + #{j : B_j X_s != d_j},
+//   obj_s  = X_s^T Q X_s + c^T X_s,
+// exact (int64) for every candidate of a chunk, then the incumbent update:
+// the least objective among feasible candidates (earliest sample on ties)
+// replaces the incumbent only when strictly better.
+//
+// Rows are classified when the instance is loaded:
+//   U rows: all coefficients equal -> the count of chosen columns must lie
+//           in [L, U]; counted 32 candidates at a time in bit-sliced form.
+//   P rows: at most two nonzeros -> 4-entry violation truth table.
+//   G rows: anything else -> 32 per-candidate int64 accumulators.
+#include "internal.cuh"
+
+namespace {
+
+// Add per-candidate violation flags (one 32-bit mask per thread, all lanes
+// of the warp on the same word w) into viol[inst][32 w + t].
+__device__ void add_violations(uint32_t vmask, int inst, int w, int chunk,
+                               int32_t* __restrict__ viol, bool valid) {
+  const int lane = threadIdx.x & 31;
+  const unsigned act = __activemask();
+  const int lead_inst = __shfl_sync(act, inst, __ffs(act) - 1);
+  const int lead_w = __shfl_sync(act, w, __ffs(act) - 1);
+  const bool uniform = __all_sync(act, (!valid) || (inst == lead_inst && w == lead_w));
+  if (uniform) {
+    // lane t accumulates the count of candidate t over the warp's rows
+    int cnt = 0;
+    for (int t = 0; t < 32; ++t) {
+      const unsigned bal = __ballot_sync(act, valid && ((vmask >> t) & 1u));
+      if (lane == t) cnt = __popc(bal);
+    }
+    if (cnt && ((act >> lane) & 1u))
+      atomicAdd(&viol[(int64_t)lead_inst * chunk + 32 * lead_w + lane], cnt);
+  } else if (valid) {
+    while (vmask) {
+      const int t = __ffs(vmask) - 1;
+      vmask &= vmask - 1;
+      atomicAdd(&viol[(int64_t)inst * chunk + 32 * w + t], 1);
+    }
+  }
+}
+
+// U rows: bit-sliced counter of the chosen columns (up to 2^16 - 1), then
+// the bound test count in [L, U].  Fast paths: covering rows (L = 1, no U)
+// need only an OR; L = U = 1 (one-hot equality) uses ones/twos masks.
+__global__ void __launch_bounds__(256)
+k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
+             const int32_t* __restrict__ ucols, const uint32_t* __restrict__ X, int kws,
+             int kwu, int len, int chunk, int32_t* __restrict__ viol) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = (int)(gid / nrows);          // rows fastest: a warp shares w
+  const int64_t r = gid - (int64_t)w * nrows;
+  const bool valid = (w < kwu);
+  uint32_t vmask = 0;
+  int inst = 0;
+  if (valid) {
+    const GfURow R = rows[r];
+    inst = R.inst;
+    const int32_t* cols = ucols + R.t0;
+    const bool no_upper = (R.U < 0 || R.U >= R.len);
+    if (R.L <= 1 && no_upper) {
+      uint32_t any = 0;
+      for (int t = 0; t < R.len; ++t) any |= X[(int64_t)cols[t] * kws + w];
+      vmask = (R.L == 1) ? ~any : 0u;
+    } else if (R.U == 1 && R.L <= 1) {
+      uint32_t ones = 0, twos = 0;
+      for (int t = 0; t < R.len; ++t) {
+        const uint32_t m = X[(int64_t)cols[t] * kws + w];
+        twos |= ones & m;
+        ones |= m;
+      }
+      vmask = twos | (R.L == 1 ? ~ones : 0u);
+    } else {
+      uint32_t s[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) s[q] = 0u;
+      for (int t = 0; t < R.len; ++t) {
+        uint32_t c = X[(int64_t)cols[t] * kws + w];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const uint32_t carry = s[q] & c;
+          s[q] ^= c;
+          c = carry;
+        }
+      }
+      // ge = (count >= L), gt = (count > U), MSB-first bit-sliced compares
+      uint32_t eqL = 0xFFFFFFFFu, gtL = 0u, eqU = 0xFFFFFFFFu, gtU = 0u;
+      const uint32_t L = (uint32_t)max(R.L, 0), U = (uint32_t)max(R.U, 0);
+#pragma unroll
+      for (int q = 15; q >= 0; --q) {
+        if ((L >> q) & 1u) { eqL &= s[q]; } else { gtL |= eqL & s[q]; eqL &= ~s[q]; }
+        if ((U >> q) & 1u) { eqU &= s[q]; } else { gtU |= eqU & s[q]; eqU &= ~s[q]; }
+      }
+      const uint32_t ge = gtL | eqL;
+      vmask = ~ge;
+      if (!no_upper) vmask |= gtU;
+    }
+    const int nt = len - 32 * w;
+    if (nt < 32) vmask &= (1u << nt) - 1u;
+  }
+  add_violations(vmask, inst, w, chunk, viol, valid);
+}
+
+// P rows: at most two variables; `table` bit (x1 + 2 x2) marks a violation.
+__global__ void __launch_bounds__(256)
+k_eval_prows(const GfPRow* __restrict__ rows, int64_t nrows,
+             const uint32_t* __restrict__ X, int kws, int kwu, int len, int chunk,
+             int32_t* __restrict__ viol) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = (int)(gid / nrows);
+  const int64_t r = gid - (int64_t)w * nrows;
+  const bool valid = (w < kwu);
+  uint32_t vmask = 0;
+  int inst = 0;
+  if (valid) {
+    const GfPRow R = rows[r];
+    inst = R.inst;
+    const uint32_t a = X[(int64_t)R.v1 * kws + w];
+    const uint32_t b = (R.v2 >= 0) ? X[(int64_t)R.v2 * kws + w] : 0u;
+    const uint32_t T = R.table;
+    vmask = ((T & 1u) ? (~a & ~b) : 0u) | ((T & 2u) ? (a & ~b) : 0u) |
+            ((T & 4u) ? (~a & b) : 0u) | ((T & 8u) ? (a & b) : 0u);
+    const int nt = len - 32 * w;
+    if (nt < 32) vmask &= (1u << nt) - 1u;
+  }
+  add_violations(vmask, inst, w, chunk, viol, valid);
+}
+
+// G rows: 32 per-candidate accumulators.
+__global__ void __launch_bounds__(128)
+k_eval_grows(const GfGRow* __restrict__ rows, int64_t nrows,
+             const int32_t* __restrict__ gcols, const int32_t* __restrict__ gvals,
+             const uint32_t* __restrict__ X, int kws, int kwu, int len, int chunk,
+             int32_t* __restrict__ viol) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = (int)(gid / nrows);
+  const int64_t r = gid - (int64_t)w * nrows;
+  const bool valid = (w < kwu);
+  uint32_t vmask = 0;
+  int inst = 0;
+  if (valid) {
+    const GfGRow R = rows[r];
+    inst = R.inst;
+    long long acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0;
+    for (int q = 0; q < R.len; ++q) {
+      const uint32_t m = X[(int64_t)gcols[R.t0 + q] * kws + w];
+      if (!m) continue;
+      const long long a = gvals[R.t0 + q];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] += ((m >> t) & 1u) ? a : 0ll;
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const bool bad = R.eq ? (acc[t] != R.rhs) : (acc[t] < R.rhs);
+      vmask |= (uint32_t)bad << t;
+    }
+    const int nt = len - 32 * w;
+    if (nt < 32) vmask &= (1u << nt) - 1u;
+  }
+  add_violations(vmask, inst, w, chunk, viol, valid);
+}
+
+// Linear objective c^T X_s over a chunk of one instance's variables; block
+// of 32 x 8 threads: lane = candidate within word w, 8 warps split the
+// variables; partials reduced in shared memory, one atomic per candidate.
+__global__ void __launch_bounds__(256)
+k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
+               const long long* __restrict__ cint, const uint32_t* __restrict__ X,
+               int kws, int kwu, int len, int chunk, long long* __restrict__ obj) {
+  const int64_t c = blockIdx.x;
+  const int w = blockIdx.y;
+  if (c >= nch || w >= kwu) return;
+  const GfObjChunk C = ch[c];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long acc = 0;
+  for (int v = C.v0 + warp * 32; v < C.v1; v += 256) {
+    const int myv = v + lane;
+    const uint32_t mw = (myv < C.v1) ? X[(int64_t)myv * kws + w] : 0u;
+    const long long mc = (myv < C.v1) ? cint[myv] : 0ll;
+    unsigned nz = __ballot_sync(0xFFFFFFFFu, mw != 0u);
+    while (nz) {
+      const int src = __ffs(nz) - 1;
+      nz &= nz - 1;
+      const uint32_t word = __shfl_sync(0xFFFFFFFFu, mw, src);
+      const long long cv = __shfl_sync(0xFFFFFFFFu, mc, src);
+      if ((word >> lane) & 1u) acc += cv;
+    }
+  }
+  __shared__ long long red[8][32];
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    long long s = 0;
+    for (int q = 0; q < 8; ++q) s += red[q][lane];
+    if (s != 0 && 32 * w + lane < len)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)C.inst * chunk + 32 * w + lane]),
+                (unsigned long long)s);
+  }
+}
+
+// Sparse Q term X_s^T Q X_s over rows [r0, r1) of Q (original, integer).
+__global__ void __launch_bounds__(256)
+k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int64_t* __restrict__ Qp,
+             const int32_t* __restrict__ Qc, const int32_t* __restrict__ Qv,
+             const uint32_t* __restrict__ X, int kws, int kwu, int len, int chunk,
+             long long* __restrict__ obj) {
+  const int64_t c = blockIdx.x;
+  const int w = blockIdx.y;
+  if (c >= nch || w >= kwu) return;
+  const GfQChunk C = ch[c];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long acc = 0;
+  for (int i = C.r0 + warp; i < C.r1; i += 8) {
+    const uint32_t mi = X[(int64_t)i * kws + w];
+    if (!mi) continue;                         // warp-uniform
+    for (int64_t t0 = Qp[i]; t0 < Qp[i + 1]; t0 += 32) {
+      const int64_t t = t0 + lane;
+      uint32_t m = 0;
+      long long q = 0;
+      if (t < Qp[i + 1]) {
+        m = mi & X[(int64_t)Qc[t] * kws + w];
+        q = Qv[t];
+      }
+      unsigned nz = __ballot_sync(0xFFFFFFFFu, m != 0u);
+      while (nz) {
+        const int src = __ffs(nz) - 1;
+        nz &= nz - 1;
+        const uint32_t word = __shfl_sync(0xFFFFFFFFu, m, src);
+        const long long qv = __shfl_sync(0xFFFFFFFFu, q, src);
+        if ((word >> lane) & 1u) acc += qv;
+      }
+    }
+  }
+  __shared__ long long red[8][32];
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    long long s = 0;
+    for (int q = 0; q < 8; ++q) s += red[q][lane];
+    if (s != 0 && 32 * w + lane < len)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)C.inst * chunk + 32 * w + lane]),
+                (unsigned long long)s);
+  }
+}
+
+// Fused sampling + evaluation for single-row instances (knapsack form
+// -w^T x >= -cap): one thread per candidate, 128 candidates per block, the
+// block walks a slice [v0, v1) of one instance's variables four at a time
+// (one Philox call per four Bernoulli draws), accumulating the row sum and
+// the objective in int64; nothing is materialised.
+__global__ void __launch_bounds__(128)
+k_fused_single_row(const int32_t* __restrict__ blk, const float* __restrict__ p,
+                   const int32_t* __restrict__ wrow, const long long* __restrict__ cint,
+                   const int64_t* __restrict__ var_off, int s0, int len, int chunk,
+                   uint64_t seed, int inst_base, const GfDState* __restrict__ st,
+                   long long* __restrict__ fsum, long long* __restrict__ obj) {
+  const int b = blk[3 * blockIdx.x], v0 = blk[3 * blockIdx.x + 1], v1 = blk[3 * blockIdx.x + 2];
+  const int sidx = blockIdx.y * 128 + threadIdx.x;
+  if (sidx >= len) return;
+  const uint32_t s = (uint32_t)(s0 + sidx);
+  const uint32_t round = st->round_id;
+  const int64_t off = var_off[b];
+  long long rs = 0, ob = 0;
+  for (int v = v0; v < v1; v += 4) {
+    const float4 pp = *reinterpret_cast<const float4*>(p + v);
+    const int4 ww = *reinterpret_cast<const int4*>(wrow + v);
+    const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)(inst_base + b), round,
+                                    s, (uint64_t)((v - off) >> 2));
+    if ((u.x >> 8) < gf::prob_threshold(pp.x)) { rs += ww.x; ob += cint[v]; }
+    if ((u.y >> 8) < gf::prob_threshold(pp.y)) { rs += ww.y; ob += cint[v + 1]; }
+    if ((u.z >> 8) < gf::prob_threshold(pp.z)) { rs += ww.z; ob += cint[v + 2]; }
+    if ((u.w >> 8) < gf::prob_threshold(pp.w)) { rs += ww.w; ob += cint[v + 3]; }
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(&fsum[(int64_t)b * chunk + sidx]),
+            (unsigned long long)rs);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)b * chunk + sidx]),
+            (unsigned long long)ob);
+}
+
+__global__ void k_fused_viol(const long long* __restrict__ fsum, const long long* __restrict__ rhs,
+                             int ninst, int len, int chunk, int32_t* __restrict__ viol) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)ninst * len) return;
+  const int b = (int)(gid / len), s = (int)(gid % len);
+  viol[(int64_t)b * chunk + s] = (fsum[(int64_t)b * chunk + s] < rhs[b]) ? 1 : 0;
+}
+
+// Incumbent update of one instance per block: least feasible objective,
+// earliest candidate on ties; replaces only when strictly better.
+__global__ void __launch_bounds__(256)
+k_incumbent(const int32_t* __restrict__ viol, const long long* __restrict__ obj, int len,
+            int chunk, int s0, const GfDState* __restrict__ st, GfInc* __restrict__ inc) {
+  const int b = blockIdx.x;
+  long long best = 0;
+  int bs = -1;
+  for (int s = threadIdx.x; s < len; s += blockDim.x) {
+    if (viol[(int64_t)b * chunk + s] != 0) continue;
+    const long long o = obj[(int64_t)b * chunk + s];
+    if (bs < 0 || o < best) { best = o; bs = s; }
+  }
+  __shared__ long long sb[256];
+  __shared__ int ss[256];
+  sb[threadIdx.x] = best;
+  ss[threadIdx.x] = bs;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      const long long ob = sb[threadIdx.x + off];
+      const int os = ss[threadIdx.x + off];
+      const int ms = ss[threadIdx.x];
+      if (os >= 0 && (ms < 0 || ob < sb[threadIdx.x] || (ob == sb[threadIdx.x] && os < ms))) {
+        sb[threadIdx.x] = ob;
+        ss[threadIdx.x] = os;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    GfInc I = inc[b];
+    I.changed = 0;
+    if (ss[0] >= 0 && (!I.found || sb[0] < I.obj)) {
+      I.found = 1;
+      I.obj = sb[0];
+      I.objf = (double)sb[0];
+      I.round_id = st->round_id;
+      I.sample = s0 + ss[0];
+      I.changed = 1;
+    }
+    inc[b] = I;
+  }
+}
+
+// x_best extraction after an update (mode 0: bits, 1: Philox regeneration
+// of a fused candidate, dense instances read their bf16 operand).
+__global__ void __launch_bounds__(256)
+k_extract(const GfInc* __restrict__ inc, const int32_t* __restrict__ var_inst,
+          const int64_t* __restrict__ var_off, const uint8_t* __restrict__ live, int64_t N,
+          const uint32_t* __restrict__ X, int kws, int s0, int mode, const float* __restrict__ p,
+          uint64_t seed, int inst_base, uint8_t* __restrict__ xbest) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int b = var_inst[i];
+  const GfInc I = inc[b];
+  if (!I.changed) return;
+  if (!live[i]) { xbest[i] = 0; return; }
+  const int sl = I.sample - s0;
+  uint8_t bit;
+  if (mode == 1) {
+    const int64_t loc = i - var_off[b];
+    const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)(inst_base + b), I.round_id,
+                                    (uint32_t)I.sample, (uint64_t)(loc >> 2));
+    bit = (gf::lane_of(u, (uint32_t)(loc & 3)) >> 8) < gf::prob_threshold(p[i]);
+  } else {
+    bit = (X[i * kws + (sl >> 5)] >> (sl & 31)) & 1u;
+  }
+  xbest[i] = bit;
+}
+
+__global__ void k_extract_dense(const GfInc* __restrict__ inc, int b, int64_t v0, int64_t n,
+                                int64_t ld, const __nv_bfloat16* __restrict__ Xs, int s0,
+                                uint8_t* __restrict__ xbest) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const GfInc I = inc[b];
+  if (!I.changed) return;
+  const int sl = I.sample - s0;
+  xbest[v0 + i] = __bfloat162float(Xs[(int64_t)sl * ld + i]) != 0.0f;
+}
+
+__global__ void k_round_end(GfDState* st) { st->round_id += 1u; }
+
+}  // namespace
+
+// Exact evaluation of the materialised chunk (bits in h->X) of every
+// non-dense instance into viol / obj (zeroed here).
+cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
+  (void)s0;
+  cudaError_t e;
+  const int kwu = (len + 31) / 32;
+  if ((e = cudaMemsetAsync(h->viol, 0, sizeof(int32_t) * h->ninst * h->chunk, h->stream)))
+    return e;
+  if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
+    return e;
+  if (h->nurows) {
+    const int64_t th = h->nurows * kwu;
+    k_eval_urows<<<(unsigned)((th + 255) / 256), 256, 0, h->stream>>>(
+        h->urows, h->nurows, h->ucols, h->X, h->kw, kwu, len, h->chunk, h->viol);
+    h->launches++;
+  }
+  if (h->nprows) {
+    const int64_t th = h->nprows * kwu;
+    k_eval_prows<<<(unsigned)((th + 255) / 256), 256, 0, h->stream>>>(
+        h->prows, h->nprows, h->X, h->kw, kwu, len, h->chunk, h->viol);
+    h->launches++;
+  }
+  if (h->ngrows) {
+    const int64_t th = h->ngrows * kwu;
+    k_eval_grows<<<(unsigned)((th + 127) / 128), 128, 0, h->stream>>>(
+        h->grows, h->ngrows, h->gcols, h->gvals, h->X, h->kw, kwu, len, h->chunk, h->viol);
+    h->launches++;
+  }
+  if (h->nochunks) {
+    dim3 grid((unsigned)h->nochunks, (unsigned)kwu);
+    k_eval_obj_lin<<<grid, 256, 0, h->stream>>>(h->ochunks, h->nochunks, h->cint, h->X, h->kw,
+                                                kwu, len, h->chunk, h->obj);
+    h->launches++;
+  }
+  if (h->nqchunks) {
+    dim3 grid((unsigned)h->nqchunks, (unsigned)kwu);
+    k_eval_obj_q<<<grid, 256, 0, h->stream>>>(h->qchunks, h->nqchunks, h->QIp, h->QIc, h->QIv,
+                                              h->X, h->kw, kwu, len, h->chunk, h->obj);
+    h->launches++;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(h->fsum, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
+    return e;
+  if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
+    return e;
+  dim3 grid((unsigned)h->nfblk, (unsigned)((len + 127) / 128));
+  k_fused_single_row<<<grid, 128, 0, h->stream>>>(h->fblk, p, h->frow_w, h->cint, h->var_off_d,
+                                                 s0, len, h->chunk, h->prm.seed,
+                                                 h->prm.inst_base, h->dstate, h->fsum, h->obj);
+  const int64_t th = (int64_t)h->ninst * len;
+  k_fused_viol<<<(unsigned)((th + 255) / 256), 256, 0, h->stream>>>(h->fsum, h->frhs, h->ninst,
+                                                                   len, h->chunk, h->viol);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+// mode: 0 materialised bits, 1 fused (Philox regeneration), 2 dense.
+cudaError_t gf_launch_incumbent(GfCtx* h, int s0, int len, int mode, bool last_chunk) {
+  k_incumbent<<<h->ninst, 256, 0, h->stream>>>(h->viol, h->obj, len, h->chunk, s0, h->dstate,
+                                               h->inc);
+  h->launches++;
+  if (h->N > 0 && mode != 2) {
+    k_extract<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(
+        h->inc, h->var_inst, h->var_off_d, h->var_live, h->N, h->X, h->kw, s0, mode,
+        h->last_p, h->prm.seed, h->prm.inst_base, h->xbest);
+    h->launches++;
+  }
+  for (const GfDenseQ& dq : h->dense) {
+    k_extract_dense<<<(unsigned)((dq.n + 255) / 256), 256, 0, h->stream>>>(
+        h->inc, dq.inst, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.Xs, s0, h->xbest);
+    h->launches++;
+  }
+  if (last_chunk) {
+    k_round_end<<<1, 1, 0, h->stream>>>(h->dstate);
+    h->launches++;
+  }
+  return cudaGetLastError();
+}

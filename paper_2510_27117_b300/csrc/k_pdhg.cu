@@ -1,0 +1,398 @@
+// k_pdhg.cu -- FirstOrderStep (PDHG update, Alg. 2) on the preprocessed
+// problem of Eq. (2), FP32 storage with compensated FP32 accumulation:
+//   y_k    = Proj_{R+^{m1} x R^{m2}}( y_{k-1} + tau2 (K xbar_{k-1} + r) )
+//   delta  = c + rho + K^T y_k + 2 Q x_{k-1} - 2 rho x_{k-1}
+//   x_k    = Proj_{[0,1]^n}( x_{k-1} - tau1 delta ),   xbar_k = 2 x_k - x_{k-1}
+// The batch is block-diagonal: every row / column carries its instance id,
+// whose step sizes come from the iteration's parameter slot.  UpdatePenalty
+// (Section 3) for the NEXT iteration is folded into block 0 of the first
+// primal kernel of each iteration (it writes the other parity slot).
+#include "internal.cuh"
+
+namespace {
+
+using gf::CSum;
+
+// ---------------------------------------------------------------------------
+// UpdatePenalty for iteration k+1 (penalty counter advances once per k_int
+// iterations), then the per-instance step sizes (tau1 = sqrt(sigma), capped
+// at 1/(2L) with L = 2(||Q_hat|| + rho) when requested; tau2 = sigma/tau1).
+// Executed by all threads of one block; `next` is the slot to write.
+// ---------------------------------------------------------------------------
+__device__ void advance_penalty(GfDState* st, const GfSched* sc,
+                                const double* normQ, const int32_t* cap,
+                                GfIParam* next) {
+  __shared__ double rho_s;
+  if (threadIdx.x == 0) {
+    long long it = st->k + 1;               // the iteration now running
+    int n_next = (int)(it / sc->k_int);     // counter used by iteration it+1
+    double rho = st->rho;
+    while (st->n_rho < n_next) {
+      st->n_rho += 1;
+      double rt = sc->rho_min * pow(1.0 + (double)st->n_rho / sc->T, sc->p);
+      double lo = rho + sc->delta;
+      double v = rt < lo ? lo : rt;
+      rho = v > sc->rho_max ? sc->rho_max : v;
+    }
+    st->rho = rho;
+    st->k = it;
+    rho_s = rho;
+  }
+  __syncthreads();
+  const double rho = rho_s;
+  for (int b = threadIdx.x; b < sc->ninst; b += blockDim.x) {
+    double t1 = sqrt(sc->sigma);
+    if (cap[b]) {
+      double L = 2.0 * (normQ[b] + rho);
+      if (L > 0.0 && 1.0 / (2.0 * L) < t1) t1 = 1.0 / (2.0 * L);
+    }
+    double t2 = sc->sigma / t1;
+    GfIParam q;
+    q.tau1 = (float)t1; q.tau2 = (float)t2; q.rho = (float)rho; q.pad = 0.f;
+    q.tau1d = t1; q.tau2d = t2; q.rhod = rho; q.normQ = normQ[b];
+    next[b] = q;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dual step over a bucket of rows, `LANES` threads per row.
+// ---------------------------------------------------------------------------
+template <int LANES>
+__global__ void __launch_bounds__(256)
+k_dual_rows(const int32_t* __restrict__ rows, int32_t nrows,
+            const int64_t* __restrict__ Kp, const int32_t* __restrict__ Kc,
+            const float* __restrict__ Kv, const float* __restrict__ xbar,
+            const float* __restrict__ r, const uint8_t* __restrict__ row_eq,
+            const int32_t* __restrict__ row_inst,
+            const GfIParam* __restrict__ ip, float* __restrict__ y) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t grp = gid / LANES;
+  const int lane = (int)(gid % LANES);
+  if (grp >= nrows) return;                 // whole groups exit together
+  const int j = rows[grp];
+  const int64_t t0 = Kp[j], t1 = Kp[j + 1];
+  CSum acc;
+  for (int64_t t = t0 + lane; t < t1; t += LANES)
+    acc.add(__fmul_rn(Kv[t], xbar[Kc[t]]));
+  gf::csum_group_reduce<LANES>(acc);
+  if (lane == 0) {
+    const float tau2 = ip[row_inst[j]].tau2;
+    float v = y[j] + tau2 * (acc.value() + r[j]);
+    if (!row_eq[j] && v < 0.f) v = 0.f;
+    y[j] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Primal step over a bucket of columns (K^T in CSC and, optionally, sparse
+// symmetric Q rows), `LANES` threads per column, fused projection and
+// extrapolation.  Block 0 of the kernel flagged `advance` also runs
+// UpdatePenalty for the next iteration.
+// ---------------------------------------------------------------------------
+template <int LANES>
+__global__ void __launch_bounds__(256)
+k_primal_cols(const int32_t* __restrict__ cols, int32_t ncols,
+              const int64_t* __restrict__ Tp, const int32_t* __restrict__ Tr,
+              const float* __restrict__ Tv, const int64_t* __restrict__ Qp,
+              const int32_t* __restrict__ Qc, const float* __restrict__ Qv,
+              const float* __restrict__ y, const float* __restrict__ x_old,
+              const float* __restrict__ chat, const int32_t* __restrict__ var_inst,
+              const GfIParam* __restrict__ ip, float* __restrict__ x_new,
+              float* __restrict__ xbar, float* __restrict__ dlast, int advance,
+              GfDState* st, const GfSched* sc, const double* normQ,
+              const int32_t* cap, GfIParam* ip_next) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t grp = gid / LANES;
+  const int lane = (int)(gid % LANES);
+  if (grp < ncols) {
+    const int i = cols[grp];
+    CSum acc;
+    for (int64_t t = Tp[i] + lane; t < Tp[i + 1]; t += LANES)
+      acc.add(__fmul_rn(Tv[t], y[Tr[t]]));
+    if (Qp) {
+      for (int64_t t = Qp[i] + lane; t < Qp[i + 1]; t += LANES)
+        acc.add(2.0f * __fmul_rn(Qv[t], x_old[Qc[t]]));
+    }
+    gf::csum_group_reduce<LANES>(acc);
+    if (lane == 0) {
+      const GfIParam q = ip[var_inst[i]];
+      const float xo = x_old[i];
+      const float delta = chat[i] + q.rho + acc.value() - 2.0f * q.rho * xo;
+      float xn = xo - q.tau1 * delta;
+      xn = fminf(1.0f, fmaxf(0.0f, xn));
+      x_new[i] = xn;
+      xbar[i] = 2.0f * xn - xo;
+      if (dlast) dlast[i] = q.tau1 * delta;
+    }
+  }
+  if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip_next);
+}
+
+// ---------------------------------------------------------------------------
+// Long rows / columns: partial compensated sums of fixed chunks, combined in
+// chunk order by the finalising kernels (deterministic).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_long_partial(const GfChunk* __restrict__ ch, int32_t nch,
+               const int32_t* __restrict__ idx, const float* __restrict__ val,
+               const float* __restrict__ vec, const int32_t* __restrict__ Qc,
+               const float* __restrict__ Qv, const float* __restrict__ xq,
+               float2* __restrict__ partial) {
+  const int c = blockIdx.x;
+  if (c >= nch) return;
+  const GfChunk k = ch[c];
+  CSum acc;
+  if (k.part == 0) {
+    for (int64_t t = k.t0 + threadIdx.x; t < k.t1; t += blockDim.x)
+      acc.add(__fmul_rn(val[t], vec[idx[t]]));
+  } else {
+    for (int64_t t = k.t0 + threadIdx.x; t < k.t1; t += blockDim.x)
+      acc.add(2.0f * __fmul_rn(Qv[t], xq[Qc[t]]));
+  }
+  gf::csum_group_reduce<32>(acc);
+  __shared__ float ss[8], sc_[8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { ss[w] = acc.s; sc_[w] = acc.c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CSum tot;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot.merge(ss[q], sc_[q]);
+    partial[c] = make_float2(tot.s, tot.c);
+  }
+}
+
+__global__ void k_dual_long_final(const int32_t* __restrict__ ids,
+                                  const int32_t* __restrict__ cptr, int32_t nlong,
+                                  const float2* __restrict__ partial,
+                                  const float* __restrict__ r,
+                                  const uint8_t* __restrict__ row_eq,
+                                  const int32_t* __restrict__ row_inst,
+                                  const GfIParam* __restrict__ ip,
+                                  float* __restrict__ y) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nlong) return;
+  const int j = ids[q];
+  CSum acc;
+  for (int c = cptr[q]; c < cptr[q + 1]; ++c) acc.merge(partial[c].x, partial[c].y);
+  const float tau2 = ip[row_inst[j]].tau2;
+  float v = y[j] + tau2 * (acc.value() + r[j]);
+  if (!row_eq[j] && v < 0.f) v = 0.f;
+  y[j] = v;
+}
+
+__global__ void __launch_bounds__(256)
+k_primal_long_final(const int32_t* __restrict__ ids, const int32_t* __restrict__ cptr,
+                    int32_t nlong, const float2* __restrict__ partial,
+                    const float* __restrict__ x_old, const float* __restrict__ chat,
+                    const int32_t* __restrict__ var_inst,
+                    const GfIParam* __restrict__ ip, float* __restrict__ x_new,
+                    float* __restrict__ xbar, float* __restrict__ dlast, int advance,
+                    GfDState* st, const GfSched* sc, const double* normQ,
+                    const int32_t* cap, GfIParam* ip_next) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nlong) {
+    const int i = ids[q];
+    CSum acc;
+    for (int c = cptr[q]; c < cptr[q + 1]; ++c) acc.merge(partial[c].x, partial[c].y);
+    const GfIParam p = ip[var_inst[i]];
+    const float xo = x_old[i];
+    const float delta = chat[i] + p.rho + acc.value() - 2.0f * p.rho * xo;
+    float xn = fminf(1.0f, fmaxf(0.0f, xo - p.tau1 * delta));
+    x_new[i] = xn;
+    xbar[i] = 2.0f * xn - xo;
+    if (dlast) dlast[i] = p.tau1 * delta;
+  }
+  if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip_next);
+}
+
+// ---------------------------------------------------------------------------
+// Dense symmetric Q stored as W2 = offdiag(Q + Q^T) in bf16 (exact small
+// integers) plus diag(Q_sym): (Q_hat x)_i = qscale (W2 x)_i + qdiag_i x_i.
+// One warp per variable, x staged in shared memory, 16-byte bf16 loads,
+// 8-term plain FP32 chunks folded into a compensated accumulator.  Also sums
+// the column of K^T for the same variable, then applies the primal update.
+// mode 0: primal update; mode 1: out[i] = (Q_hat x)_i only.
+// ---------------------------------------------------------------------------
+constexpr int kDenseWarps = 16;
+
+__global__ void __launch_bounds__(kDenseWarps * 32)
+k_dense_primal(const __nv_bfloat16* __restrict__ W2, int64_t ld, int64_t n,
+               int64_t v0, const float* __restrict__ qdiag, float qscale,
+               const int64_t* __restrict__ Tp, const int32_t* __restrict__ Tr,
+               const float* __restrict__ Tv, const float* __restrict__ y,
+               const float* __restrict__ x_old, const float* __restrict__ chat,
+               const GfIParam* __restrict__ ip, int inst, float* __restrict__ x_new,
+               float* __restrict__ xbar, float* __restrict__ dlast, int mode,
+               float* __restrict__ out, int advance, GfDState* st,
+               const GfSched* sc, const double* normQ, const int32_t* cap,
+               GfIParam* ip_next) {
+  extern __shared__ float4 xs4[];
+  float* xs = reinterpret_cast<float*>(xs4);
+  for (int64_t j = threadIdx.x; j < ld; j += blockDim.x)
+    xs[j] = (j < n) ? x_old[v0 + j] : 0.0f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const GfIParam q = ip[inst];
+  for (int64_t i = (int64_t)blockIdx.x * kDenseWarps + warp; i < n;
+       i += (int64_t)gridDim.x * kDenseWarps) {
+    const uint4* row = reinterpret_cast<const uint4*>(W2 + i * ld);
+    CSum acc;
+    for (int64_t j8 = lane; j8 * 8 < ld; j8 += 32) {
+      const uint4 w = row[j8];
+      const float4 xa = xs4[2 * j8], xb = xs4[2 * j8 + 1];
+      const __nv_bfloat162* wp = reinterpret_cast<const __nv_bfloat162*>(&w);
+      float2 w0 = __bfloat1622float2(wp[0]), w1 = __bfloat1622float2(wp[1]);
+      float2 w2 = __bfloat1622float2(wp[2]), w3 = __bfloat1622float2(wp[3]);
+      float part = w0.x * xa.x;
+      part = fmaf(w0.y, xa.y, part);
+      part = fmaf(w1.x, xa.z, part);
+      part = fmaf(w1.y, xa.w, part);
+      part = fmaf(w2.x, xb.x, part);
+      part = fmaf(w2.y, xb.y, part);
+      part = fmaf(w3.x, xb.z, part);
+      part = fmaf(w3.y, xb.w, part);
+      acc.add(part);
+    }
+    // K^T column of this variable, folded in at the 1/(2 qscale) scale so a
+    // single compensated sum carries 2 (Q_hat x)_i + (K^T y)_i below.
+    gf::csum_group_reduce<32>(acc);
+    CSum g;
+    if (Tp) {
+      for (int64_t t = Tp[v0 + i] + lane; t < Tp[v0 + i + 1]; t += 32)
+        g.add(__fmul_rn(Tv[t], y[Tr[t]]));
+      gf::csum_group_reduce<32>(g);
+    }
+    if (lane == 0) {
+      const float xo = xs[i];
+      CSum s;                              // 2 (Q_hat x)_i + (K^T y)_i
+      s.merge(__fmul_rn(2.0f * qscale, acc.s), __fmul_rn(2.0f * qscale, acc.c));
+      s.add(__fmul_rn(2.0f * qdiag[i], xo));
+      s.merge(g.s, g.c);
+      if (mode == 1) {
+        out[i] = 0.5f * s.value();
+      } else {
+        const float delta = chat[v0 + i] + q.rho + s.value() - 2.0f * q.rho * xo;
+        float xn = fminf(1.0f, fmaxf(0.0f, xo - q.tau1 * delta));
+        x_new[v0 + i] = xn;
+        xbar[v0 + i] = 2.0f * xn - xo;
+        if (dlast) dlast[v0 + i] = q.tau1 * delta;
+      }
+    }
+  }
+  if (advance && blockIdx.x == 0) {
+    __syncthreads();
+    advance_penalty(st, sc, normQ, cap, ip_next);
+  }
+}
+
+template <int L>
+cudaError_t launch_dual(GfCtx* h, const GfBucket& b, const GfIParam* ip) {
+  int64_t threads = (int64_t)b.count * L;
+  int blocks = (int)((threads + 255) / 256);
+  k_dual_rows<L><<<blocks, 256, 0, h->stream>>>(b.ids, b.count, h->Kp, h->Kc, h->Kv,
+                                                h->xbar, h->rhat, h->row_eq, h->row_inst,
+                                                ip, h->y);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t launch_primal(GfCtx* h, const GfBucket& b, const GfIParam* ip,
+                          const float* xo, float* xn, int adv, GfIParam* ipn) {
+  int64_t threads = (int64_t)b.count * L;
+  int blocks = (int)((threads + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  k_primal_cols<L><<<blocks, 256, 0, h->stream>>>(
+      b.ids, b.count, h->Tp, h->Tr, h->Tv, h->nnzQ ? h->Qp : nullptr, h->Qc, h->Qv, h->y,
+      xo, h->chat, h->var_inst, ip, xn, h->xbar, h->dlast, adv, h->dstate, h->sched_d,
+      h->normQhat_d, h->cap_d, ipn);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gf_launch_dense_gemv_q(GfCtx* h, const GfDenseQ& dq, const float* x,
+                                   float* out) {
+  int blocks = (int)std::min<int64_t>((dq.n + kDenseWarps - 1) / kDenseWarps, 296);
+  size_t smem = sizeof(float) * (size_t)dq.ld;
+  k_dense_primal<<<blocks, kDenseWarps * 32, smem, h->stream>>>(
+      dq.W2, dq.ld, dq.n, h->ih[dq.inst].var_off, dq.qdiag, dq.qscale, nullptr, nullptr,
+      nullptr, nullptr, x, h->chat, h->iprm, dq.inst, nullptr, nullptr, nullptr, 1, out,
+      0, nullptr, nullptr, nullptr, nullptr, nullptr);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+// One PDHG iteration for every instance: dual buckets, long-row chunks,
+// primal buckets, long-column chunks, dense-Q instances.  x_{k-1} is read
+// from x[1-parity... ] -- iteration it = k+1 reads x[(it-1)&1], writes x[it&1].
+cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
+  const GfIParam* ip = h->iprm + (size_t)parity * h->ninst;
+  GfIParam* ipn = h->iprm + (size_t)(1 - parity) * h->ninst;
+  const float* xo = h->x[1 - parity];
+  float* xn = h->x[parity];
+  cudaError_t e;
+  // ---- dual
+  for (const GfBucket& b : h->rb) {
+    if (!b.count) continue;
+    switch (b.lanes) {
+      case 1: e = launch_dual<1>(h, b, ip); break;
+      case 4: e = launch_dual<4>(h, b, ip); break;
+      case 8: e = launch_dual<8>(h, b, ip); break;
+      case 16: e = launch_dual<16>(h, b, ip); break;
+      default: e = launch_dual<32>(h, b, ip); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (h->rlong.nlong) {
+    k_long_partial<<<h->rlong.nchunks, 256, 0, h->stream>>>(
+        h->rlong.chunks, h->rlong.nchunks, h->Kc, h->Kv, h->xbar, nullptr, nullptr,
+        nullptr, h->rlong.partial);
+    k_dual_long_final<<<(h->rlong.nlong + 127) / 128, 128, 0, h->stream>>>(
+        h->rlong.ids, h->rlong.chunk_ptr, h->rlong.nlong, h->rlong.partial, h->rhat,
+        h->row_eq, h->row_inst, ip, h->y);
+    h->launches += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // ---- primal (first launch advances the penalty state)
+  int adv = 1;
+  for (const GfDenseQ& dq : h->dense) {
+    int blocks = (int)std::min<int64_t>((dq.n + kDenseWarps - 1) / kDenseWarps, 296);
+    size_t smem = sizeof(float) * (size_t)dq.ld;
+    const GfInstHost& I = h->ih[dq.inst];
+    const bool hasK = (I.m1 + I.m2) > 0;
+    k_dense_primal<<<blocks, kDenseWarps * 32, smem, h->stream>>>(
+        dq.W2, dq.ld, dq.n, I.var_off, dq.qdiag, dq.qscale, hasK ? h->Tp : nullptr, h->Tr,
+        h->Tv, h->y, xo, h->chat, ip, dq.inst, xn, h->xbar, h->dlast, 0, nullptr, adv,
+        h->dstate, h->sched_d, h->normQhat_d, h->cap_d, ipn);
+    h->launches++;
+    adv = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  for (const GfBucket& b : h->cb) {
+    if (!b.count) continue;
+    switch (b.lanes) {
+      case 1: e = launch_primal<1>(h, b, ip, xo, xn, adv, ipn); break;
+      case 4: e = launch_primal<4>(h, b, ip, xo, xn, adv, ipn); break;
+      case 8: e = launch_primal<8>(h, b, ip, xo, xn, adv, ipn); break;
+      case 16: e = launch_primal<16>(h, b, ip, xo, xn, adv, ipn); break;
+      default: e = launch_primal<32>(h, b, ip, xo, xn, adv, ipn); break;
+    }
+    adv = 0;
+    if (e != cudaSuccess) return e;
+  }
+  if (h->clong.nlong) {
+    k_long_partial<<<h->clong.nchunks, 256, 0, h->stream>>>(
+        h->clong.chunks, h->clong.nchunks, h->Tr, h->Tv, h->y, h->Qc, h->Qv, xo,
+        h->clong.partial);
+    k_primal_long_final<<<(h->clong.nlong + 255) / 256, 256, 0, h->stream>>>(
+        h->clong.ids, h->clong.chunk_ptr, h->clong.nlong, h->clong.partial, xo, h->chat,
+        h->var_inst, ip, xn, h->xbar, h->dlast, adv, h->dstate, h->sched_d, h->normQhat_d,
+        h->cap_d, ipn);
+    h->launches += 2;
+    adv = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}

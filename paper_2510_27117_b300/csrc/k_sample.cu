@@ -1,0 +1,338 @@
+// k_sample.cu -- RandSampleStep (Alg. 3) and the customised samplers of
+// Section 2.4.2 / 2.4.3 on the device.  Candidates are stored
+// variable-major and bit-packed: word X[i * kw + w] holds samples
+// s0 + 32 w + t (bit t) of variable i.  Every draw comes from Philox4x32-10
+// with counter (local index >> 2, sample, round, instance | stream << 28).
+#include "internal.cuh"
+
+namespace {
+
+// Generic Bernoulli: X_si = [(u_si >> 8) < floor(p_i 2^24)].  One thread
+// per (4 consecutive variables, 32-sample word): 32 Philox calls fill four
+// words.  Grouped variables (drawn by a group sampler) and padding are
+// skipped / zeroed.
+__global__ void __launch_bounds__(256)
+k_bern_bits(const float* __restrict__ p, const int32_t* __restrict__ var_inst,
+            const int64_t* __restrict__ var_off, const uint8_t* __restrict__ grouped,
+            const uint8_t* __restrict__ live, int64_t N4, int kws, int kwu, int s0,
+            int len, uint64_t seed, int inst_base, const GfDState* __restrict__ st,
+            uint32_t* __restrict__ X) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= N4 * kwu) return;
+  const int64_t g4 = gid / kwu;
+  const int w = (int)(gid % kwu);
+  const int64_t i0 = g4 * 4;
+  const int b = var_inst[i0];
+  const int64_t loc4 = (i0 - var_off[b]) >> 2;
+  const uint32_t round = st->round_id;
+  uint32_t thr[4];
+  bool skip[4];
+  bool any = false;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    skip[l] = grouped[i0 + l] != 0;
+    thr[l] = live[i0 + l] ? gf::prob_threshold(p[i0 + l]) : 0u;
+    any |= (!skip[l] && thr[l] != 0u);
+  }
+  uint32_t word[4] = {0u, 0u, 0u, 0u};
+  if (any) {
+    const int nt = min(32, len - 32 * w);
+    for (int t = 0; t < nt; ++t) {
+      const uint32_t s = (uint32_t)(s0 + 32 * w + t);
+      const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)(inst_base + b),
+                                      round, s, (uint64_t)loc4);
+      word[0] |= (uint32_t)((u.x >> 8) < thr[0]) << t;
+      word[1] |= (uint32_t)((u.y >> 8) < thr[1]) << t;
+      word[2] |= (uint32_t)((u.z >> 8) < thr[2]) << t;
+      word[3] |= (uint32_t)((u.w >> 8) < thr[3]) << t;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+    if (!skip[l]) X[(i0 + l) * kws + w] = word[l];
+}
+
+// Cumulative weights floor(p 2^24) of each group's members (in list order),
+// one warp per group: warp-wide inclusive scans of 32-member slices.
+__global__ void k_group_cw(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
+                           int64_t ngroups, const float* __restrict__ p,
+                           unsigned long long* __restrict__ cw) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= ngroups) return;
+  unsigned long long carry = 0;
+  for (int64_t t0 = gp[g]; t0 < gp[g + 1]; t0 += 32) {
+    const int64_t t = t0 + lane;
+    unsigned long long v = (t < gp[g + 1]) ? gf::prob_threshold(p[gi[t]]) : 0ull;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, v, off);
+      if (lane >= off) v += o;
+    }
+    if (t < gp[g + 1]) cw[t] = carry + v;
+    carry += __shfl_sync(0xFFFFFFFFu, v, 31);
+  }
+}
+
+// One-hot group draw, one warp per (group, word): lane t draws sample
+// s0 + 32 w + t.  With W = total weight > 0 the pick is the first member
+// whose inclusive prefix exceeds floor(u W / 2^32) (exact 128-bit product,
+// binary search); with W = 0 it is member floor(u len / 2^32).  The warp
+// owns the group's words of column w: it zeroes them, then each distinct
+// pick is written once with the mask of lanes that chose it.
+__global__ void __launch_bounds__(256)
+k_group_pick(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
+             const int32_t* __restrict__ ginst, const int32_t* __restrict__ glocal,
+             int64_t ngroups, const unsigned long long* __restrict__ cw, int kws, int kwu,
+             int s0, int len, uint64_t seed, int inst_base,
+             const GfDState* __restrict__ st, uint32_t* __restrict__ X) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= ngroups * kwu) return;
+  const int64_t g = wid / kwu;
+  const int w = (int)(wid % kwu);
+  const int64_t a = gp[g], e = gp[g + 1];
+  const int64_t glen = e - a;
+  for (int64_t t = a + lane; t < e; t += 32) X[gi[t] * kws + w] = 0u;
+  __syncwarp();
+  if (glen <= 0) return;
+  const int sidx = 32 * w + lane;
+  int64_t pick = -1;
+  if (sidx < len) {
+    const uint32_t gl = (uint32_t)glocal[g];
+    const uint4 u4 = gf::philox_call(seed, gf::kStreamGroup, (uint32_t)(inst_base + ginst[g]),
+                                     st->round_id, (uint32_t)(s0 + sidx), gl >> 2);
+    const uint32_t u = gf::lane_of(u4, gl & 3u);
+    const unsigned long long W = cw[e - 1];
+    int64_t pos;
+    if (W == 0ull) {
+      pos = (int64_t)(((unsigned long long)u * (unsigned long long)glen) >> 32);
+    } else {
+      const unsigned long long lo = (unsigned long long)u * W;
+      const unsigned long long hi = __umul64hi((unsigned long long)u, W);
+      const unsigned long long r = (hi << 32) | (lo >> 32);
+      int64_t lo_i = 0, hi_i = glen - 1;      // first position with cw > r
+      while (lo_i < hi_i) {
+        const int64_t mid = (lo_i + hi_i) >> 1;
+        if (cw[a + mid] > r) hi_i = mid; else lo_i = mid + 1;
+      }
+      pos = lo_i;
+    }
+    pick = gi[a + pos];
+  }
+  const unsigned active = __ballot_sync(0xFFFFFFFFu, pick >= 0);
+  const unsigned same = __match_any_sync(0xFFFFFFFFu, pick);
+  if (pick >= 0 && lane == __ffs(same & active) - 1)
+    X[pick * kws + w] = same & active;
+}
+
+// Axial 3D assignment, one block per (instance, sample): for i = 0..I-1 the
+// pair (j,k) is drawn among pairs with j and k both unused by the rule of
+// k_group_pick over x_ijk in (j,k) row-major order (u: Philox stream 2,
+// index i).  Bits are OR-ed into X (zeroed beforehand).
+constexpr int kAxThreads = 256;
+__global__ void __launch_bounds__(kAxThreads)
+k_axial(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, int len,
+        int kw, uint64_t seed, int inst_base, const GfDState* __restrict__ st,
+        uint32_t* __restrict__ X) {
+  const int sidx = blockIdx.x;
+  if (sidx >= len) return;
+  const uint32_t s = (uint32_t)(s0 + sidx);
+  __shared__ uint8_t usedJ[256], usedK[256];
+  __shared__ unsigned long long wsum[kAxThreads / 32];
+  __shared__ unsigned long long sh_r, sh_W;
+  __shared__ int sh_pick;
+  for (int q = threadIdx.x; q < I; q += blockDim.x) { usedJ[q] = 0; usedK[q] = 0; }
+  __syncthreads();
+  const int P = I * I;
+  const int per = (P + kAxThreads - 1) / kAxThreads;
+  const int q0 = threadIdx.x * per, q1 = min(P, q0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < I; ++i) {
+    const float* pi = p + v0 + (int64_t)i * P;
+    unsigned long long mine = 0;
+    for (int q = q0; q < q1; ++q) {
+      const int j = q / I, k = q - j * I;
+      if (!usedJ[j] && !usedK[k]) mine += gf::prob_threshold(pi[q]);
+    }
+    // block exclusive scan of `mine`
+    unsigned long long v = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, v, off);
+      if (lane >= off) v += o;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    unsigned long long wbase = 0, tot = 0;
+    for (int q = 0; q < kAxThreads / 32; ++q) {
+      if (q < warp) wbase += wsum[q];
+      tot += wsum[q];
+    }
+    const unsigned long long excl = wbase + v - mine;
+    if (threadIdx.x == 0) {
+      const uint4 u4 = gf::philox_call(seed, gf::kStreamAxial, (uint32_t)(inst_base + inst),
+                                       st->round_id, s, (uint64_t)(i >> 2));
+      const uint32_t u = gf::lane_of(u4, (uint32_t)(i & 3));
+      sh_W = tot;
+      if (tot > 0) {
+        const unsigned long long lo = (unsigned long long)u * tot;
+        const unsigned long long hi = __umul64hi((unsigned long long)u, tot);
+        sh_r = (hi << 32) | (lo >> 32);
+      } else {
+        const int free = I - i;
+        sh_r = ((unsigned long long)u * (unsigned long long)(free * free)) >> 32;
+      }
+      sh_pick = -1;
+    }
+    __syncthreads();
+    const unsigned long long r = sh_r;
+    if (sh_W > 0) {
+      if (mine > 0 && excl <= r && r < excl + mine) {
+        unsigned long long acc = excl;
+        for (int q = q0; q < q1; ++q) {
+          const int j = q / I, k = q - j * I;
+          if (usedJ[j] || usedK[k]) continue;
+          acc += gf::prob_threshold(pi[q]);
+          if (acc > r) { sh_pick = q; break; }
+        }
+      }
+    } else if (threadIdx.x == 0) {
+      // r-th allowed pair in row-major order: (a-th free j, b-th free k)
+      const int free = I - i;
+      int a = (int)(r / free), bb = (int)(r % free), j = -1, k = -1;
+      for (int q = 0, c = 0; q < I; ++q) if (!usedJ[q]) { if (c == a) { j = q; break; } ++c; }
+      for (int q = 0, c = 0; q < I; ++q) if (!usedK[q]) { if (c == bb) { k = q; break; } ++c; }
+      sh_pick = j * I + k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int q = sh_pick;
+      const int j = q / I, k = q - j * I;
+      usedJ[j] = 1;
+      usedK[k] = 1;
+      const int64_t var = v0 + (int64_t)i * P + q;
+      atomicOr(&X[var * kw + (sidx >> 5)], 1u << (sidx & 31));
+    }
+    __syncthreads();
+  }
+}
+
+// Closure repair (Section 2.4.3): rep_var[q] |= OR of its list, per word.
+// One block per repaired variable; thread tid owns word tid % kw.
+__global__ void k_closure(const int64_t* __restrict__ rv, const int64_t* __restrict__ rp,
+                          const int64_t* __restrict__ ri, int64_t nrep, int kws,
+                          int kw, uint32_t* __restrict__ X) {
+  const int64_t q = blockIdx.x;
+  if (q >= nrep) return;
+  extern __shared__ uint32_t red[];
+  const int per = blockDim.x / kw;           // threads per word
+  const int w = threadIdx.x % kw;
+  const int slot = threadIdx.x / kw;
+  uint32_t acc = 0;
+  if (slot < per) {
+    const int64_t a = rp[q], e = rp[q + 1];
+    for (int64_t t = a + slot; t < e; t += per) acc |= X[ri[t] * kws + w];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < kw) {
+    uint32_t v = X[rv[q] * kws + threadIdx.x];
+    for (int s = 0; s < per; ++s) v |= red[s * kw + threadIdx.x];
+    X[rv[q] * kws + threadIdx.x] = v;
+  }
+}
+
+// Bernoulli draws of a dense-Q instance written sample-major as bf16 0/1
+// (the tensor-core operand), one thread per (sample, 4 variables).
+__global__ void __launch_bounds__(256)
+k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld, int len,
+            int s0, uint64_t seed, int inst, const GfDState* __restrict__ st,
+            __nv_bfloat16* __restrict__ Xs) {
+  const int64_t n4 = ld / 4;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= n4 * len) return;
+  const int sidx = (int)(gid / n4);
+  const int64_t g4 = gid % n4;
+  const int64_t i0 = g4 * 4;
+  uint32_t b[4] = {0, 0, 0, 0};
+  if (i0 < n) {
+    const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)inst, st->round_id,
+                                    (uint32_t)(s0 + sidx), (uint64_t)g4);
+    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      if (i0 + l < n) b[l] = (uu[l] >> 8) < gf::prob_threshold(p[v0 + i0 + l]);
+  }
+  // bf16 one = 0x3F80
+  uint2 out;
+  out.x = (b[0] ? 0x3F80u : 0u) | ((b[1] ? 0x3F80u : 0u) << 16);
+  out.y = (b[2] ? 0x3F80u : 0u) | ((b[3] ? 0x3F80u : 0u) << 16);
+  reinterpret_cast<uint2*>(Xs + (int64_t)sidx * ld)[g4] = out;
+}
+
+}  // namespace
+
+// Sample `len` candidates (samples s0 .. s0+len-1 of the current round) of
+// every instance from proposal p.  for_dense: dense-Q instances get their
+// bf16 sample-major operand instead of bits.
+cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense) {
+  const gfors_params& P = h->prm;
+  cudaError_t e;
+  const int kw = (len + 31) / 32;
+  // axial instances need zeroed words (bits are OR-ed in)
+  for (int b = 0; b < h->ninst; ++b) {
+    const GfInstHost& I = h->ih[b];
+    if (I.group_mode == 2) {
+      e = cudaMemsetAsync(h->X + I.var_off * h->kw, 0, sizeof(uint32_t) * I.npad * h->kw,
+                          h->stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (h->N > 0) {
+    const int64_t N4 = h->N / 4;
+    const int64_t threads = N4 * kw;
+    k_bern_bits<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(
+        p, h->var_inst, h->var_off_d, h->var_grouped, h->var_live, N4, h->kw, kw, s0, len,
+        P.seed, P.inst_base, h->dstate, h->X);
+    h->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (h->ngroups_tot > 0) {
+    k_group_cw<<<(unsigned)((h->ngroups_tot * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->grp_ptr, h->grp_idx, h->ngroups_tot, p, h->grp_cw);
+    const int64_t warps = h->ngroups_tot * kw;
+    k_group_pick<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->grp_ptr, h->grp_idx, h->grp_inst, h->grp_local, h->ngroups_tot, h->grp_cw, h->kw,
+        kw, s0, len, P.seed, P.inst_base, h->dstate, h->X);
+    h->launches += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  for (int b = 0; b < h->ninst; ++b) {
+    const GfInstHost& I = h->ih[b];
+    if (I.group_mode != 2) continue;
+    k_axial<<<len, kAxThreads, 0, h->stream>>>(p, I.var_off, I.axial_I, b, s0, len, h->kw,
+                                               P.seed, P.inst_base, h->dstate, h->X);
+    h->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (h->nrep_tot > 0) {
+    int per = std::max(1, 256 / kw);
+    int threads = per * kw;
+    k_closure<<<(unsigned)h->nrep_tot, threads, sizeof(uint32_t) * threads, h->stream>>>(
+        h->rep_var, h->rep_ptr, h->rep_idx, h->nrep_tot, h->kw, kw, h->X);
+    h->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (for_dense) {
+    for (const GfDenseQ& dq : h->dense) {
+      const int64_t threads = (dq.ld / 4) * len;
+      k_bern_bf16<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(
+          p, h->ih[dq.inst].var_off, dq.n, dq.ld, len, s0, P.seed, P.inst_base + dq.inst,
+          h->dstate, dq.Xs);
+      h->launches++;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}

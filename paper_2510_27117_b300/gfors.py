@@ -1,0 +1,366 @@
+"""Python binding of libgfors.so: argument marshalling only.
+
+Every call maps one-to-one onto an entry point of include/gfors.h; all
+computation runs in the library's CUDA kernels.  Importing this module fails
+loudly (ImportError) when the library has not been built, and every solver
+call fails (GforsError) on machines without an sm_103a GPU: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgfors.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libgfors.so not built ({LIB_PATH}); run paper_2510_27117_b300/build.py")
+_lib = C.CDLL(LIB_PATH)
+
+i32, i64, u32, u64, f64, vp = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double, C.c_void_p
+
+STATUS = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_OOM", 4: "E_TIMEOUT", 5: "E_STATE",
+          6: "E_UNSUPPORTED"}
+
+
+class GforsError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class Csr(C.Structure):
+    _fields_ = [("rows", i64), ("cols", i64), ("nnz", i64), ("row_ptr", vp),
+                ("col_idx", vp), ("val", vp)]
+
+
+class QMat(C.Structure):
+    _fields_ = [("kind", i32), ("dense_rowmajor", vp), ("sparse", Csr)]
+
+
+class Params(C.Structure):
+    _fields_ = [("sigma", f64), ("rho_min", f64), ("rho_max", f64), ("T", f64), ("p", f64),
+                ("delta", f64), ("k_int", i32), ("k_r", i32), ("k_b", i32),
+                ("tau_cap_by_L", i32), ("seed", u64), ("x0", f64), ("halt_tol", f64),
+                ("stall_window", i32), ("inst_base", i32), ("sample_chunk", i32),
+                ("eval_mode", i32), ("power_tol", f64), ("power_maxit", i32),
+                ("wait_timeout_s", f64)]
+
+
+_H = vp
+_P = C.POINTER
+_lib.gfors_default_params.argtypes = [_P(Params)]
+_lib.gfors_version.restype = C.c_char_p
+_lib.gfors_last_error.argtypes = [_H]
+_lib.gfors_last_error.restype = C.c_char_p
+ALLOC_FN = C.CFUNCTYPE(vp, C.c_size_t, vp)
+FREE_FN = C.CFUNCTYPE(None, vp, vp)
+_lib.gfors_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+_lib.gfors_load.argtypes = [_P(Csr), vp, _P(Csr), vp, _P(QMat), vp, i64, _P(Params), vp,
+                            _P(_H)]
+_lib.gfors_load_batch.argtypes = [i32, _P(_P(Csr)), _P(vp), _P(_P(Csr)), _P(vp),
+                                  _P(_P(QMat)), _P(vp), _P(i64), _P(Params), vp, _P(_H)]
+_lib.gfors_set_groups.argtypes = [_H, i32, i32, i64, vp, vp, i32]
+_lib.gfors_set_closure.argtypes = [_H, i32, i64, vp, vp, vp]
+_lib.gfors_pdhg_steps.argtypes = [_H, i64]
+_lib.gfors_sample_eval.argtypes = [_H, i32, u32, i32]
+_lib.gfors_final_round.argtypes = [_H]
+_lib.gfors_run.argtypes = [_H, i64, f64, i32, _P(i64)]
+_lib.gfors_incumbent.argtypes = [_H, i32, _P(i32), _P(i64), _P(f64), _P(u32), _P(i32), vp]
+_lib.gfors_lp_stats.argtypes = [_H, i32, vp]
+_lib.gfors_get_scales.argtypes = [_H, i32, vp]
+_lib.gfors_get_iterate.argtypes = [_H, i32, vp, vp, vp, vp]
+_lib.gfors_set_iterate.argtypes = [_H, i32, vp, vp, vp]
+_lib.gfors_set_counters.argtypes = [_H, i64, f64]
+_lib.gfors_eval_candidates.argtypes = [_H, i32, i32, vp, vp, vp, vp]
+_lib.gfors_get_samples.argtypes = [_H, i32, vp, vp, vp, _P(i32)]
+_lib.gfors_mlp_nparams.argtypes = [i32, i32]
+_lib.gfors_mlp_nparams.restype = i64
+_lib.gfors_set_proposal.argtypes = [_H, vp, i64]
+_lib.gfors_get_features.argtypes = [_H, i32, vp]
+_lib.gfors_mlp_forward.argtypes = [i32, i32, vp, i64, vp, vp, vp, vp]
+_lib.gfors_mlp_loss_grad.argtypes = [i32, i32, vp, i64, vp, vp, vp, vp, vp]
+_lib.gfors_mlp_adam.argtypes = [i64, vp, vp, vp, vp, i64, f64, f64, f64, f64, vp]
+_lib.gfors_state_export.argtypes = [_H, vp, _P(C.c_size_t)]
+_lib.gfors_state_import.argtypes = [_H, vp, C.c_size_t]
+_lib.gfors_profile.argtypes = [_H, i32]
+_lib.gfors_profile_read.argtypes = [_H, i32, vp, vp]
+_lib.gfors_launch_count.argtypes = [_H]
+_lib.gfors_launch_count.restype = i64
+_lib.gfors_destroy.argtypes = [_H]
+
+EXPORTS = [n for n in dir(_lib) if n.startswith("gfors_")]
+
+
+def version() -> str:
+    return _lib.gfors_version().decode()
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _lib.gfors_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _check(st, h=None):
+    if st != 0:
+        msg = _lib.gfors_last_error(h).decode(errors="replace")
+        raise GforsError(st, msg)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(vp)
+
+
+_alloc_keep = []
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through PyTorch's caching
+    allocator (device memory comes from torch; the kernels are the library's)."""
+    if not enable:
+        _check(_lib.gfors_set_allocator(ALLOC_FN(0), FREE_FN(0), None))
+        return
+    import torch
+
+    def _a(size, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size))
+        except Exception:
+            return None
+
+    def _f(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = ALLOC_FN(_a), FREE_FN(_f)
+    _alloc_keep[:] = [fa, ff]
+    _check(_lib.gfors_set_allocator(fa, ff, None))
+
+
+class _CsrHold:
+    """Keeps the numpy arrays of one CSR alive while the library copies it."""
+
+    def __init__(self, M, n):
+        import scipy.sparse as sp
+        M = sp.csr_matrix(M)
+        self.rp = np.ascontiguousarray(M.indptr, np.int64)
+        self.ci = np.ascontiguousarray(M.indices, np.int32)
+        self.v = np.ascontiguousarray(M.data, np.float64)
+        self.s = Csr(M.shape[0], n, self.v.size, _ptr(self.rp), _ptr(self.ci), _ptr(self.v))
+
+
+class _InstHold:
+    def __init__(self, inst):
+        self.n = inst.n
+        self.A = _CsrHold(inst.A, inst.n) if inst.A is not None else None
+        self.B = _CsrHold(inst.B, inst.n) if inst.B is not None else None
+        self.b = np.ascontiguousarray(inst.b, np.float64) if inst.A is not None else None
+        self.d = np.ascontiguousarray(inst.d, np.float64) if inst.B is not None else None
+        self.c = np.ascontiguousarray(inst.c, np.float64)
+        self.Q = None
+        self.Qd = None
+        self.Qs = None
+        if isinstance(inst.Q, np.ndarray):
+            self.Qd = np.ascontiguousarray(inst.Q, np.float64)
+            self.Q = QMat(1, _ptr(self.Qd), Csr())
+        elif inst.Q is not None:
+            self.Qs = _CsrHold(inst.Q, inst.n)
+            self.Q = QMat(2, None, self.Qs.s)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream      # torch.cuda.Stream
+
+
+class Handle:
+    """One loaded batch (gfors_handle)."""
+
+    def __init__(self, h, insts):
+        self.h = vp(h)
+        self.insts = insts
+
+    # --- Alg. 1 pieces
+    def pdhg_steps(self, nsteps):
+        _check(_lib.gfors_pdhg_steps(self.h, nsteps), self.h)
+
+    def sample_eval(self, nrounds, first_round_id, proposal=0):
+        _check(_lib.gfors_sample_eval(self.h, nrounds, first_round_id, proposal), self.h)
+
+    def final_round(self):
+        _check(_lib.gfors_final_round(self.h), self.h)
+
+    def run(self, max_iters, time_budget_s=0.0, proposal=0):
+        it = i64(0)
+        _check(_lib.gfors_run(self.h, max_iters, time_budget_s, proposal, C.byref(it)), self.h)
+        return it.value
+
+    # --- results and state
+    def incumbent(self, inst=0, want_x=True):
+        n = self.insts[inst].n
+        f, oi, of, rr, ss = i32(), i64(), f64(), u32(), i32()
+        x = np.zeros(n, np.uint8) if want_x else None
+        _check(_lib.gfors_incumbent(self.h, inst, C.byref(f), C.byref(oi), C.byref(of),
+                                    C.byref(rr), C.byref(ss), _ptr(x)), self.h)
+        return dict(found=f.value, obj=oi.value, objf=of.value, round=rr.value,
+                    sample=ss.value, x=x)
+
+    def lp_stats(self, inst=0):
+        out = np.zeros(8)
+        _check(_lib.gfors_lp_stats(self.h, inst, _ptr(out)), self.h)
+        return out
+
+    def get_scales(self, inst=0):
+        out = np.zeros(8)
+        _check(_lib.gfors_get_scales(self.h, inst, _ptr(out)), self.h)
+        return out
+
+    def get_iterate(self, inst=0):
+        I = self.insts[inst]
+        m = I.m1 + I.m2
+        x, xb, xp = (np.zeros(I.n, np.float32) for _ in range(3))
+        y = np.zeros(max(m, 1), np.float32)
+        _check(_lib.gfors_get_iterate(self.h, inst, _ptr(x), _ptr(xb), _ptr(xp), _ptr(y)),
+               self.h)
+        return x, xb, xp, y[:m]
+
+    def set_iterate(self, inst=0, x=None, xbar=None, y=None):
+        a = [None if v is None else np.ascontiguousarray(v, np.float32) for v in (x, xbar, y)]
+        _check(_lib.gfors_set_iterate(self.h, inst, *(_ptr(v) for v in a)), self.h)
+
+    def set_counters(self, k, rho=-1.0):
+        _check(_lib.gfors_set_counters(self.h, k, rho), self.h)
+
+    def eval_candidates(self, X, inst=0):
+        X = np.ascontiguousarray(X, np.uint8)
+        k = X.shape[0]
+        viol = np.zeros(k, np.int32)
+        oi = np.zeros(k, np.int64)
+        of = np.zeros(k, np.float64)
+        _check(_lib.gfors_eval_candidates(self.h, inst, k, _ptr(X), _ptr(viol), _ptr(oi),
+                                          _ptr(of)), self.h)
+        return viol, oi
+
+    def get_samples(self, inst=0, want_x=True):
+        n = self.insts[inst].n
+        cnt = i32()
+        _check(_lib.gfors_get_samples(self.h, inst, None, None, None, C.byref(cnt)), self.h)
+        k = cnt.value
+        X = np.zeros((k, n), np.uint8) if want_x else None
+        viol = np.zeros(k, np.int32)
+        oi = np.zeros(k, np.int64)
+        _check(_lib.gfors_get_samples(self.h, inst, _ptr(X), _ptr(viol), _ptr(oi),
+                                      C.byref(cnt)), self.h)
+        return X, viol, oi
+
+    def set_groups(self, inst=0, mode=1, groups=None, axial_I=0):
+        gp = gi = None
+        ng = 0
+        if groups is not None:
+            gp = np.ascontiguousarray(groups[0], np.int64)
+            gi = np.ascontiguousarray(groups[1], np.int64)
+            ng = gp.size - 1
+        _check(_lib.gfors_set_groups(self.h, inst, mode, ng, _ptr(gp), _ptr(gi), axial_I),
+               self.h)
+
+    def set_closure(self, inst, closure):
+        rv, rp, ri = (np.ascontiguousarray(a, np.int64) for a in closure)
+        _check(_lib.gfors_set_closure(self.h, inst, rv.size, _ptr(rv), _ptr(rp), _ptr(ri)),
+               self.h)
+
+    def set_proposal(self, W):
+        W = np.ascontiguousarray(W, np.float32)
+        _check(_lib.gfors_set_proposal(self.h, _ptr(W), W.size), self.h)
+
+    def get_features(self, inst=0):
+        n = self.insts[inst].n
+        f = np.zeros((n, 8), np.float32)
+        _check(_lib.gfors_get_features(self.h, inst, _ptr(f)), self.h)
+        return f
+
+    def state_export(self) -> bytes:
+        ln = C.c_size_t(0)
+        _check(_lib.gfors_state_export(self.h, None, C.byref(ln)), self.h)
+        buf = C.create_string_buffer(ln.value)
+        _check(_lib.gfors_state_export(self.h, buf, C.byref(ln)), self.h)
+        return buf.raw[:ln.value]
+
+    def state_import(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(_lib.gfors_state_import(self.h, buf, len(blob)), self.h)
+
+    PHASES = ("pdhg", "sample", "eval", "dense_score", "incumbent", "fused", "stats",
+              "dense_sample")
+
+    def profile(self, enable=True):
+        _check(_lib.gfors_profile(self.h, int(enable)), self.h)
+
+    def profile_read(self):
+        n = len(self.PHASES)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, np.int64)
+        _check(_lib.gfors_profile_read(self.h, n, _ptr(ms), _ptr(cnt)), self.h)
+        return {k: (float(ms[q]), int(cnt[q])) for q, k in enumerate(self.PHASES)}
+
+    def launch_count(self) -> int:
+        return _lib.gfors_launch_count(self.h)
+
+    def destroy(self):
+        if self.h:
+            _lib.gfors_destroy(self.h)
+            self.h = vp(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def load(inst, prm: Optional[Params] = None, stream=None, setup=True) -> Handle:
+    """gfors_load for one workloads.Instance (plus its groups / closure)."""
+    return load_batch([inst], prm, stream, setup)
+
+
+def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
+               setup=True) -> Handle:
+    """gfors_load_batch; with setup=True also gfors_set_groups / set_closure
+    from each instance's groups, axial size and closure lists."""
+    prm = default_params() if prm is None else prm
+    holds = [_InstHold(I) for I in insts]
+    nb = len(insts)
+    A = (_P(Csr) * nb)(*[C.pointer(hd.A.s) if hd.A else _P(Csr)() for hd in holds])
+    B = (_P(Csr) * nb)(*[C.pointer(hd.B.s) if hd.B else _P(Csr)() for hd in holds])
+    Q = (_P(QMat) * nb)(*[C.pointer(hd.Q) if hd.Q is not None else _P(QMat)() for hd in holds])
+    b = (vp * nb)(*[_ptr(hd.b) for hd in holds])
+    d = (vp * nb)(*[_ptr(hd.d) for hd in holds])
+    c = (vp * nb)(*[_ptr(hd.c) for hd in holds])
+    n = (i64 * nb)(*[hd.n for hd in holds])
+    h = _H()
+    st = _lib.gfors_load_batch(nb, A, b, B, d, Q, c, n, C.byref(prm), _stream_ptr(stream),
+                               C.byref(h))
+    _check(st, None)
+    H = Handle(h.value, list(insts))
+    if setup:
+        for q, I in enumerate(insts):
+            if I.axial_I:
+                H.set_groups(q, 2, None, I.axial_I)
+            elif I.groups is not None:
+                H.set_groups(q, 1, I.groups)
+            if I.closure is not None:
+                H.set_closure(q, I.closure)
+    return H
+
+
+def mlp_nparams(F=8, H=128) -> int:
+    return _lib.gfors_mlp_nparams(F, H)

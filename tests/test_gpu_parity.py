@@ -1,0 +1,254 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+identical seeded inputs.  Bit-exact for sampling, evaluation and the
+incumbent; 1e-6 of the absolute-sum scale per PDHG step; 1e-9 relative for
+the FP64 spectral norms; 1e-4 relative for LP limits."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import oracle as O
+from paper_2510_27117_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+G = pytest.importorskip("paper_2510_27117_b300.gfors")
+
+
+def _params(**kw):
+    base = dict(k_int=10, k_b=256, seed=0x5EED0000 + 7, x0=0.5)
+    base.update(kw)
+    return G.default_params(**base), O.Params(**{k: v for k, v in base.items()
+                                                  if k in O.Params.__dataclass_fields__})
+
+
+CASES = {
+    "setcover": lambda: W.set_cover(n=500, m=60, density=0.05, idx=3),
+    "knapsack": lambda: W.knapsack(3001, idx=5),
+    "tiny": lambda: W.tiny_bip(n=14, m1=4, m2=1, idx=2),
+    "maxcut": lambda: W.max_cut(n=300, idx=1),
+    "assign3d": lambda: W.assign3d(I=8, idx=1),
+    "facloc": lambda: W.facility_location(nf=12, nc=40, idx=2),
+}
+
+
+# ------------------------------------------------------------ Preprocess
+@pytest.mark.parametrize("name", list(CASES))
+def test_preprocess_norms(name):
+    inst = CASES[name]()
+    gp, op = _params()
+    H = G.load(inst, gp)
+    S = O.preprocess(inst, op.seed, 0)
+    sc = H.get_scales(0)
+    assert abs(sc[0] - S.normQ_raw) <= 1e-9 * max(S.normQ_raw, 1e-300)
+    assert abs(sc[1] - S.s_obj) <= 1e-9 * S.s_obj
+    if S.m:
+        nk = S.s_K
+        assert abs(sc[2] - nk) <= 1e-9 * nk
+    assert abs(sc[3] - S.normQ) <= 1e-9 * max(S.normQ, 1e-300)
+    H.destroy()
+
+
+# ------------------------------------------------------------ PDHG step
+def _step_tolerance(S, t1, t2, rho, x, xb, y, y1):
+    K = sp.csr_matrix((S.Kv, S.Kc, S.Kp), shape=(S.m, S.n))
+    Ka = abs(K)
+    if S.qkind == 1:
+        qa = np.abs(S.Qd) @ np.abs(x)
+    elif S.qkind == 2:
+        qa = abs(sp.csr_matrix((S.Qv, S.Qc, S.Qp), shape=(S.n, S.n))) @ np.abs(x)
+    else:
+        qa = np.zeros(S.n)
+    tol_y = 1e-6 * (np.abs(y) + t2 * (Ka @ np.abs(xb) + np.abs(S.r))) + 1e-7
+    tol_x = 1e-6 * (np.abs(x) + t1 * (np.abs(S.c) + rho + Ka.T @ np.abs(y1) + 2 * qa
+                                      + 2 * rho * np.abs(x))) + 1e-7
+    return tol_x, tol_y
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pdhg_single_step(name):
+    inst = CASES[name]()
+    gp, op = _params()
+    H = G.load(inst, gp)
+    S = O.preprocess(inst, op.seed, 0)
+    rng = np.random.default_rng(11)
+    x = rng.random(inst.n).astype(np.float32)
+    x[rng.random(inst.n) < 0.1] = 0.0
+    x[rng.random(inst.n) < 0.1] = 1.0
+    xb = (x + 0.3 * (rng.random(inst.n) - 0.5)).astype(np.float32)
+    y = (rng.random(S.m) * 0.5).astype(np.float32)
+    if S.m:
+        y[S.m1:] -= 0.25
+    k, rho = 7, 0.125
+    H.set_iterate(0, x, xb, y)
+    H.set_counters(k, rho)
+    H.pdhg_steps(1)
+    gx, gxb, gxp, gy = H.get_iterate(0)
+    cap = (S.qkind != 0)
+    t1, t2 = O.step_sizes(op.sigma, S.normQ, rho, cap)
+    ox, oxb, oy, _ = O.pdhg_step(S, t1, t2, rho, x.astype(np.float64), xb.astype(np.float64),
+                                 y.astype(np.float64))
+    tol_x, tol_y = _step_tolerance(S, t1, t2, rho, x.astype(np.float64),
+                                   xb.astype(np.float64), y.astype(np.float64), oy)
+    assert np.all(np.abs(gx - ox) <= tol_x)
+    assert np.all(np.abs(gxb - oxb) <= 2 * tol_x + 1e-7)
+    assert np.array_equal(gxp, x)
+    if S.m:
+        assert np.all(np.abs(gy - oy) <= tol_y)
+    assert gx.min() >= 0 and gx.max() <= 1
+    if S.m1:
+        assert gy[:S.m1].min() >= 0
+    H.destroy()
+
+
+# ------------------------------------------------------------ sampling + eval
+@pytest.mark.parametrize("name,mode", [("setcover", 0), ("knapsack", 1), ("knapsack", 2),
+                                       ("tiny", 0), ("maxcut", 0), ("assign3d", 0),
+                                       ("facloc", 0)])
+def test_sampling_and_evaluation_bit_exact(name, mode):
+    inst = CASES[name]()
+    gp, op = _params(eval_mode=mode, k_b=96 if name != "maxcut" else 128)
+    H = G.load(inst, gp)
+    rng = np.random.default_rng(5)
+    p = rng.random(inst.n).astype(np.float32)
+    p[rng.random(inst.n) < 0.05] = 0.0
+    p[rng.random(inst.n) < 0.05] = 1.0
+    H.set_iterate(0, p, p, None)
+    R = 13
+    H.sample_eval(1, R, 0)
+    X, viol, obj = H.get_samples(0)
+    Xo = O.sample(inst, p, gp.k_b, op.seed, 0, R)
+    assert X.shape == Xo.shape
+    assert np.array_equal(X, Xo)
+    vo, oo = O.Evaluator(inst)(Xo)
+    assert np.array_equal(viol, vo)
+    assert np.array_equal(obj, oo)
+    # incumbent = oracle's incumbent rule on the same scores
+    st = dict(found=0, obj=0, round=0, sample=-1)
+    O.incumbent_update(st, vo, oo, R)
+    inc = H.incumbent(0)
+    assert inc["found"] == st["found"]
+    if st["found"]:
+        assert inc["obj"] == st["obj"] and inc["round"] == R and inc["sample"] == st["sample"]
+        assert np.array_equal(inc["x"], Xo[st["sample"]])
+    H.destroy()
+
+
+@pytest.mark.parametrize("idx", range(3))
+def test_eval_candidates_brute_force(idx):
+    inst = W.tiny_bip(n=12, m1=4, m2=1, idx=40 + idx)
+    gp, op = _params(k_b=256)
+    H = G.load(inst, gp)
+    codes = np.arange(1 << inst.n, dtype=np.int64)
+    X = ((codes[:, None] >> np.arange(inst.n)[None, :]) & 1).astype(np.uint8)
+    viol, obj = H.eval_candidates(X)
+    ev = O.Evaluator(inst)
+    vo, oo = ev(X)
+    assert np.array_equal(viol, vo) and np.array_equal(obj, oo)
+    found, best, bx, nf = ev.brute_force()
+    feas = viol == 0
+    assert feas.sum() == nf
+    if found:
+        assert obj[feas].min() == best
+    H.destroy()
+
+
+def test_maxcut_scoring_is_minus_cut():
+    inst = W.max_cut(n=200, idx=4)
+    gp, _ = _params(k_b=64)
+    H = G.load(inst, gp)
+    rng = np.random.default_rng(1)
+    X = (rng.random((64, 200)) < 0.5).astype(np.uint8)
+    viol, obj = H.eval_candidates(X)
+    Wm = inst.meta["W"]
+    for s in range(64):
+        x = X[s].astype(np.float64)
+        cut = 0.5 * np.sum(Wm * (x[:, None] != x[None, :]))
+        assert obj[s] == -int(round(cut)) and viol[s] == 0
+    H.destroy()
+
+
+# ------------------------------------------------------------ LP limits
+def test_knapsack_lp_limit():
+    inst = W.knapsack(2000, idx=9)
+    gp, _ = _params(rho_min=0.0, rho_max=0.0, delta=0.0, k_int=1000000)
+    H = G.load(inst, gp)
+    H.pdhg_steps(30000)
+    x, _, _, _ = H.get_iterate(0)
+    v, _ = O.knapsack_lp(inst.meta["w"], inst.meta["p"], inst.meta["cap"])
+    got = float(inst.meta["p"] @ x.astype(np.float64))
+    assert abs(got - v) <= 1e-4 * abs(v)
+    st = H.lp_stats(0)
+    assert st[0] < 1e-4 and st[1] < 1e-4
+    H.destroy()
+
+
+def test_setcover_lp_limit_and_dual_bound():
+    import scipy.optimize as so
+    inst = W.set_cover(n=400, m=50, density=0.06, idx=4)
+    gp, op = _params(rho_min=0.0, rho_max=0.0, k_int=1000000)
+    H = G.load(inst, gp)
+    S = O.preprocess(inst, op.seed, 0)
+    K = sp.csr_matrix((S.Kv, S.Kc, S.Kp), shape=(S.m, S.n)).toarray()
+    res = so.linprog(S.c, A_ub=K, b_ub=-S.r, bounds=[(0, 1)] * S.n, method="highs")
+    H.pdhg_steps(40000)
+    st = H.lp_stats(0)
+    assert st[4] <= res.fun + 1e-6                    # weak duality (certificate)
+    assert abs(st[3] - res.fun) <= 1e-4 * abs(res.fun)
+    assert st[0] < 1e-4 and st[1] < 1e-4
+    H.destroy()
+
+
+# ------------------------------------------------------------ batching, checkpoint
+def test_batched_equals_single():
+    insts = [W.knapsack(n, idx=100 + q) for q, n in enumerate([1500, 4000, 777, 2600])]
+    gp, _ = _params(k_int=20, k_b=128)
+    HB = G.load_batch(insts, gp)
+    HB.run(100)
+    for q, I in enumerate(insts):
+        gq, _ = _params(k_int=20, k_b=128, inst_base=q)
+        H1 = G.load(I, gq)
+        H1.run(100)
+        a, b = HB.incumbent(q), H1.incumbent(0)
+        assert a["found"] == b["found"] and a["obj"] == b["obj"]
+        assert np.array_equal(a["x"], b["x"])
+        xa = HB.get_iterate(q)[0]
+        xb = H1.get_iterate(0)[0]
+        assert np.array_equal(xa, xb)
+        H1.destroy()
+    HB.destroy()
+
+
+def test_checkpoint_resume_bit_exact():
+    inst = W.set_cover(n=300, m=40, density=0.08, idx=6)
+    gp, _ = _params(k_int=10, k_b=64)
+    A = G.load(inst, gp)
+    A.run(60)
+    blob = A.state_export()
+    A.run(120)
+    B = G.load(inst, gp)
+    B.state_import(blob)
+    B.run(120)
+    for H in (A, B):
+        H.final_round()
+    a, b = A.incumbent(0), B.incumbent(0)
+    assert a["obj"] == b["obj"] and np.array_equal(a["x"], b["x"])
+    assert np.array_equal(A.get_iterate(0)[0], B.get_iterate(0)[0])
+    A.destroy()
+    B.destroy()
+
+
+# ------------------------------------------------------------ end to end
+@pytest.mark.parametrize("idx", range(3))
+def test_run_never_beats_brute_force(idx):
+    inst = W.tiny_bip(n=12, m1=3, m2=1, idx=30 + idx)
+    gp, _ = _params(k_int=10, k_b=256, seed=100 + idx)
+    H = G.load(inst, gp)
+    H.run(400)
+    inc = H.incumbent(0)
+    ev = O.Evaluator(inst)
+    found, best, bx, nf = ev.brute_force()
+    if inc["found"]:
+        assert found and inc["obj"] >= best
+        v, o = ev(inc["x"][None, :])
+        assert v[0] == 0 and o[0] == inc["obj"]
+    H.destroy()
