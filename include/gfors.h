@@ -97,7 +97,8 @@ typedef struct {
                           the role Sec. 2.1 gives k_b); 0 = k_b              */
   int32_t eval_mode;   /* 0 auto, 1 materialised bits, 2 fused sample+eval
                           (single-row instances), 3 dense tensor-core
-                          scoring (dense +-small-integer Q)                 */
+                          scoring (dense small-integer Q), 4 dense scoring
+                          on CUDA cores (checking)                          */
   double power_tol;    /* power-iteration stop tolerance; 1e-12            */
   int32_t power_maxit; /* power-iteration cap; 5000                         */
   double wait_timeout_s;/* limit of every device-side wait; 2.0             */

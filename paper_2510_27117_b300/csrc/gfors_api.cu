@@ -161,6 +161,16 @@ extern "C" gfors_status gfors_profile_read(gfors_handle h, int32_t nphases, doub
   return GFORS_OK;
 }
 
+// After a synchronisation: a device wait that ran out of time left an error
+// in the device state; the handle becomes failed.
+static gfors_status check_device_error(GfCtx* h) {
+  int err = 0;
+  cudaError_t e = cudaMemcpy(&err, &h->dstate->error, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) return gf_cuda(h, e, "device state");
+  if (err) return gf_fail(h, GFORS_E_TIMEOUT, "a bounded device-side wait gave up");
+  return GFORS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // host mirror of UpdatePenalty (same recursion as the device)
 static void host_advance(GfCtx* h, long long it) {
@@ -355,6 +365,7 @@ static gfors_status fetch_stats(GfCtx* h, std::vector<double>& out) {
                            cudaMemcpyDeviceToHost, h->stream)))
     return gf_cuda(h, e, "stats copy");
   if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "stats sync");
+  if (gfors_status ds = check_device_error(h)) return ds;
   out.assign(8 * h->ninst, 0.0);
   for (int b = 0; b < h->ninst; ++b) stats_of(h, b, &a[8 * b], &b2[8 * b], &out[8 * b]);
   return GFORS_OK;
@@ -438,6 +449,7 @@ extern "C" gfors_status gfors_incumbent(gfors_handle h, int32_t inst, int32_t* f
                                     h->stream)))
     return gf_cuda(h, e, "incumbent copy");
   if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "incumbent sync");
+  if (gfors_status ds = check_device_error(h)) return ds;
   if (found) *found = I.found;
   if (obj_i) *obj_i = I.obj;
   if (obj_f) *obj_f = I.objf;
@@ -571,6 +583,7 @@ extern "C" gfors_status gfors_eval_candidates(gfors_handle h, int32_t inst, int3
                              sizeof(long long) * len, cudaMemcpyDeviceToHost, h->stream)))
       return gf_cuda(h, e, "eval_candidates copy");
     if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "eval_candidates sync");
+    if (gfors_status ds = check_device_error(h)) return ds;
     for (int t = 0; t < len; ++t) {
       if (viol) viol[s0 + t] = v[t];
       if (obj_i) obj_i[s0 + t] = o[t];
@@ -622,6 +635,7 @@ extern "C" gfors_status gfors_get_samples(gfors_handle h, int32_t inst, uint8_t*
                            cudaMemcpyDeviceToHost, h->stream)))
     return gf_cuda(h, e, "get_samples copy");
   if ((e = cudaStreamSynchronize(h->stream))) return gf_cuda(h, e, "get_samples sync");
+  if (gfors_status ds = check_device_error(h)) return ds;
   for (int t = 0; t < len; ++t) {
     if (viol) viol[t] = v[t];
     if (obj_i) obj_i[t] = o[t];

@@ -328,7 +328,14 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
         dq.n = I.n;
         dq.ld = gf_round_up(I.n, 64);
         dq.w2max = w2max;
-        dq.tc_ok = true;
+        {
+          // tensor-core scoring keeps every per-tile partial in int32:
+          // 128 rows x (n max|W2| + 2 max|c_i + Q_ii|) < 2^31
+          double maxlin = 0.0;
+          for (int64_t i = 0; i < I.n; ++i)
+            maxlin = std::max(maxlin, std::fabs(c[q][i] + Qd[i * I.n + i]));
+          dq.tc_ok = 128.0 * ((double)I.n * (double)w2max + 2.0 * maxlin) < 2147483648.0;
+        }
         dense_w2[q].assign((size_t)I.n * dq.ld, __float2bfloat16(0.0f));
         dense_diag[q].resize(I.n);
         for (int64_t i = 0; i < I.n; ++i) {

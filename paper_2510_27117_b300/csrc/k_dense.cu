@@ -54,8 +54,10 @@ k_dense_score_simt(const __nv_bfloat16* __restrict__ W2, int64_t ld, int64_t n,
 
 }  // namespace
 
+cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int len);
+
 cudaError_t gf_launch_dense_score(GfCtx* h, const GfDenseQ& dq, int s0, int len) {
-  (void)s0;
+  if (dq.tc_ok && h->prm.eval_mode != 4) return gf_launch_dense_score_tc(h, dq, s0, len);
   long long* out = h->obj + (int64_t)dq.inst * h->chunk;
   k_dense_score_simt<<<len, 256, sizeof(uint32_t) * (dq.ld / 32), h->stream>>>(
       dq.W2, dq.ld, dq.n, dq.lin, dq.Xs, len, out);
