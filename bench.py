@@ -155,6 +155,8 @@ def run_ours(args, rank, world, local):
         l0 = H.launch_count()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
+        if args.profile_region:
+            torch.cuda.profiler.start()
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
             for q in range(args.steps):
@@ -164,6 +166,8 @@ def run_ours(args, rank, world, local):
                 evs[q][1].record(stream)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
+        if args.profile_region:
+            torch.cuda.profiler.stop()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -321,6 +325,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maxcut", choices=list(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--profile-region", action="store_true",
+                    help="cudaProfilerStart/Stop around the timed steps (for ncu "
+                         "--profile-from-start off)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
