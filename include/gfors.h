@@ -289,6 +289,36 @@ GFORS_API gfors_status gfors_profile(gfors_handle h, int32_t enable);
 GFORS_API gfors_status gfors_profile_read(gfors_handle h, int32_t nphases, double* ms,
                                           int64_t* counts);
 
+/* Allocation-free fused sampling + evaluation of one single-row instance
+ * (the knapsack form a.x >= rhs).  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they
+ * need the pass -- code running while a CUDA graph is captured on its
+ * thread, serving loops that never touch an allocator after start-up, hosts
+ * whose device memory all belongs to their own pool.  It draws the same
+ * candidates as gfors_sample_eval on a single-row handle and returns the
+ * same scores, without any allocation.
+ *   p_dev [n]   FP32 probabilities (device); a_dev [n] int32 row
+ *               coefficients; c_dev [n] int64 costs; rhs the row's bound
+ *   seed, inst_id, round_id, first_sample: the Philox key, instance id,
+ *               round id and first candidate index (as in gfors_sample_eval)
+ *   nsamples    candidates first_sample .. first_sample + nsamples - 1;
+ *               at most GFORS_NOALLOC_MAX_SAMPLES, else GFORS_E_ARG
+ *   viol_dev [nsamples] int32 out: 1 if a.x < rhs; obj_dev [nsamples]
+ *               int64 out: c.x  (device buffers owned by the caller)
+ * Enqueued on cuda_stream, asynchronous.  Its only scratch is a file-scope
+ * device array of GFORS_NOALLOC_MAX_SAMPLES int64 that every device using
+ * the library keeps until the process exits.  The first call on a device
+ * looks up that array's address and should come before any stream capture.
+ * Calls share the array (each clears what it uses first): calls that overlap
+ * on the GPU race. */
+#define GFORS_NOALLOC_MAX_SAMPLES 16384
+GFORS_API gfors_status gfors_fused_eval_noalloc(const float* p_dev, const int32_t* a_dev,
+                                                const int64_t* c_dev, int64_t n, int64_t rhs,
+                                                uint64_t seed, uint32_t inst_id,
+                                                uint32_t round_id, int32_t first_sample,
+                                                int32_t nsamples, int32_t* viol_dev,
+                                                int64_t* obj_dev, void* cuda_stream);
+
 /* Kernel-launch counter of this handle (device kernels enqueued so far). */
 GFORS_API int64_t gfors_launch_count(gfors_handle h);
 

@@ -362,5 +362,19 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
     return H
 
 
+NOALLOC_MAX_SAMPLES = 16384
+_lib.gfors_fused_eval_noalloc.argtypes = [vp, vp, vp, i64, i64, u64, u32, u32, i32, i32, vp,
+                                          vp, vp]
+
+
+def fused_eval_noalloc(p_dev, a_dev, c_dev, n, rhs, seed, inst_id, round_id, first_sample,
+                       nsamples, viol_dev, obj_dev, stream=None):
+    """gfors_fused_eval_noalloc on caller-owned device buffers (integer device
+    addresses, e.g. torch.Tensor.data_ptr()); allocates nothing."""
+    _check(_lib.gfors_fused_eval_noalloc(p_dev, a_dev, c_dev, n, rhs, seed, inst_id, round_id,
+                                         first_sample, nsamples, viol_dev, obj_dev,
+                                         _stream_ptr(stream)))
+
+
 def mlp_nparams(F=8, H=128) -> int:
     return _lib.gfors_mlp_nparams(F, H)
