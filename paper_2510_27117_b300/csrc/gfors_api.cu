@@ -234,12 +234,15 @@ extern "C" gfors_status gfors_pdhg_steps(gfors_handle h, int64_t nsteps) {
   return GFORS_OK;
 }
 
-// One round (k_b candidates, processed in chunks) from proposal p.
-static cudaError_t enqueue_round(GfCtx* h, const float* p) {
+// One round (k_b candidates, processed in chunks): candidates [0, split) are
+// drawn from p_a, [split, k_b) from p_b (split = k_b: a single proposal).
+static cudaError_t enqueue_round(GfCtx* h, const float* p_a, const float* p_b, int split) {
   const int kb = h->prm.k_b;
   cudaError_t e;
-  for (int s0 = 0; s0 < kb; s0 += h->chunk) {
-    const int len = std::min(h->chunk, kb - s0);
+  for (int s0 = 0; s0 < kb;) {
+    const int seg_end = (s0 < split) ? split : kb;
+    const float* p = (s0 < split) ? p_a : p_b;
+    const int len = std::min(h->chunk, seg_end - s0);
     const bool last = (s0 + len >= kb);
     h->last_p = p;
     h->last_s0 = s0;
@@ -271,6 +274,7 @@ static cudaError_t enqueue_round(GfCtx* h, const float* p) {
       if ((e = gf_launch_incumbent(h, s0, len, 0, last))) return e;
       gf_prof_end(h, pi, 1);
     }
+    s0 += len;
   }
   return cudaSuccess;
 }
@@ -283,13 +287,18 @@ static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal) {
     return gf_fail(h, GFORS_E_STATE, "learned proposal requested but none attached");
   cudaError_t e;
   const float* xk = h->x[h->k_host & 1];
+  if (proposal != 0 && nrounds > 0) {
+    // features of this trigger, then the network's probabilities
+    if ((e = gf_launch_features(h))) return gf_cuda(h, e, "features");
+    if ((e = gf_launch_mlp_proposal(h))) return gf_cuda(h, e, "learned proposal");
+  }
+  const int kb = h->prm.k_b;
+  // proposal 2: first half of every round from the network, second half
+  // from x_k (rounded to the 32-candidate word)
+  const int split = (proposal == 2) ? std::max(32, (kb / 2) / 32 * 32) : kb;
   for (int r = 0; r < nrounds; ++r) {
-    const float* p = xk;
-    if (proposal == 1 || (proposal == 2 && (r & 1))) {
-      if ((e = gf_launch_mlp_proposal(h))) return gf_cuda(h, e, "learned proposal");
-      p = h->p_learn;
-    }
-    if ((e = enqueue_round(h, p))) return gf_cuda(h, e, "sampling round");
+    const float* pa = (proposal == 0) ? xk : h->p_learn;
+    if ((e = enqueue_round(h, pa, xk, split))) return gf_cuda(h, e, "sampling round");
     h->host_round++;
   }
   return GFORS_OK;
@@ -415,7 +424,6 @@ extern "C" gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time
     if (e) return gf_cuda(h, e, "gfors_run steps");
     if (h->k_host % kint == 0) {
       const long long trig = h->k_host / kint - 1;
-      if (proposal != 0 && (e = gf_launch_features(h))) return gf_cuda(h, e, "features");
       k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, (unsigned)(trig * h->prm.k_r));
       h->host_round = (unsigned)(trig * h->prm.k_r);
       if ((st = sample_rounds(h, h->prm.k_r, proposal))) return st;
@@ -710,6 +718,8 @@ extern "C" gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t m
     return gf_fail(h, GFORS_E_ARG, "mode must be 0, 1 or 2");
   }
   if ((e = cudaMemcpy(h->var_grouped + I.var_off, grouped.data(), I.npad,
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->var_grouped_feat + I.var_off, grouped.data(), I.npad,
                       cudaMemcpyHostToDevice)))
     return gf_cuda(h, e, "group flags");
   return GFORS_OK;

@@ -567,6 +567,13 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   for (size_t u = 0; u < h->dense.size(); ++u) {
     GfDenseQ& dq = h->dense[u];
     ALLOC(dq.W2, __nv_bfloat16, dq.n * dq.ld);
+    if (dq.w2max <= 127) {             // int8 copy for the PDHG GEMV (exact)
+      ALLOC(dq.W2i8, int8_t, dq.n * dq.ld);
+      std::vector<int8_t> w8((size_t)dq.n * dq.ld);
+      const std::vector<__nv_bfloat16>& wb = dense_w2[dq.inst];
+      for (size_t t = 0; t < w8.size(); ++t) w8[t] = (int8_t)__bfloat162float(wb[t]);
+      UP(dq.W2i8, w8.data(), int8_t, w8.size());
+    }
     ALLOC(dq.qdiag, float, dq.ld);
     ALLOC(dq.lin, long long, dq.ld);
     ALLOC(ddiag[u], double, dq.n);
@@ -819,9 +826,11 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
           gr.push_back(R);
         }
       }
-      for (int64_t a = 0; a < I.n; a += 1024)
-        oc.push_back(GfObjChunk{q, (int32_t)(I.var_off + a),
-                                (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 1024)), 0});
+      // dense tensor-core instances: the scorer adds c + diag(Q) itself
+      if (I.qkind != 1)
+        for (int64_t a = 0; a < I.n; a += 1024)
+          oc.push_back(GfObjChunk{q, (int32_t)(I.var_off + a),
+                                  (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 1024)), 0});
       if (I.qkind == 2) {
         for (int64_t i = 0; i < I.n; ++i) QIp[I.var_off + i + 1] = (int64_t)S.Qorig[i].col.size();
         for (int64_t a = 0; a < I.n; a += 64)
@@ -933,6 +942,8 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   ALLOC(h->inc, GfInc, ninst);
   ALLOC(h->xbest, uint8_t, N);
   ALLOC(h->var_grouped, uint8_t, N);
+  ALLOC(h->var_grouped_feat, uint8_t, N);
+  GF_CK(h, cudaMemsetAsync(h->var_grouped_feat, 0, N, s));
   ALLOC(h->stats_part, double, 8 * (h->nrchunk + h->nvchunk + 1));
   ALLOC(h->stats, double, 8 * ninst);
   ALLOC(h->stats2, double, 8 * ninst);
@@ -1030,6 +1041,8 @@ static gfors_status make_ctx(const gfors_params* prm, void* stream, GfCtx** out)
     h->own_stream = true;
   }
   h->dev = dev;
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (h->num_sms <= 0) h->num_sms = 148;
   *out = h;
   return GFORS_OK;
 }

@@ -78,6 +78,7 @@ struct GfDenseQ {                   // dense +-small-integer Q (tensor-core path
   int inst = -1;
   int64_t n = 0, ld = 0;            // ld: row stride in elements (mult. of 64)
   __nv_bfloat16* W2 = nullptr;      // off-diagonal of Q + Q^T, n x ld
+  int8_t* W2i8 = nullptr;           // same as int8 when max|W2| <= 127 (PDHG GEMV)
   float* qdiag = nullptr;           // diag(Q_sym) / s_obj
   float qscale = 0.f;               // 0.5 / s_obj
   long long* lin = nullptr;         // c_i + Q_ii (original, integer)
@@ -109,6 +110,7 @@ struct gfors_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int dev = 0;
+  int num_sms = 148;
   bool failed = false;
   std::string err;
   long long launches = 0;
@@ -231,6 +233,9 @@ struct gfors_ctx {
   float* degnorm = nullptr;         // column degree / max (N)
   float* cstd = nullptr;            // standardised c (N)
   float* grpmax = nullptr;          // N: max_{group} x (scratch)
+  float* p_learn_z = nullptr;       // N: logits of the learned proposal
+  uint8_t* var_grouped_feat = nullptr;  // N: 1 if in a one-hot group / axial slab
+  int hist_ring = 0;                // triggers pushed into x_hist
 
   // CUDA graphs of one PDHG iteration pair, by parity of its first iteration
   cudaGraphExec_t g_pair = nullptr;

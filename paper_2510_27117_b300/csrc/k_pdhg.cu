@@ -236,25 +236,126 @@ k_dense_primal(const __nv_bfloat16* __restrict__ W2, int64_t ld, int64_t n,
   for (int64_t i = (int64_t)blockIdx.x * kDenseWarps + warp; i < n;
        i += (int64_t)gridDim.x * kDenseWarps) {
     const uint4* row = reinterpret_cast<const uint4*>(W2 + i * ld);
+    const int64_t n8 = ld / 8;                 // 16-byte words in the row
     CSum acc;
-    for (int64_t j8 = lane; j8 * 8 < ld; j8 += 32) {
-      const uint4 w = row[j8];
-      const float4 xa = xs4[2 * j8], xb = xs4[2 * j8 + 1];
-      const __nv_bfloat162* wp = reinterpret_cast<const __nv_bfloat162*>(&w);
-      float2 w0 = __bfloat1622float2(wp[0]), w1 = __bfloat1622float2(wp[1]);
-      float2 w2 = __bfloat1622float2(wp[2]), w3 = __bfloat1622float2(wp[3]);
-      float part = w0.x * xa.x;
-      part = fmaf(w0.y, xa.y, part);
-      part = fmaf(w1.x, xa.z, part);
-      part = fmaf(w1.y, xa.w, part);
-      part = fmaf(w2.x, xb.x, part);
-      part = fmaf(w2.y, xb.y, part);
-      part = fmaf(w3.x, xb.z, part);
-      part = fmaf(w3.y, xb.w, part);
-      acc.add(part);
+    // 8 independent 16-byte loads in flight per lane (memory-level
+    // parallelism), then 8-term plain FP32 chunks into the compensated sum
+    for (int64_t b8 = 0; b8 < n8; b8 += 8 * 32) {
+      uint4 w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j8 = b8 + lane + 32 * u;
+        w[u] = (j8 < n8) ? __ldg(row + j8) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j8 = b8 + lane + 32 * u;
+        if (j8 >= n8) break;
+        const float4 xa = xs4[2 * j8], xb = xs4[2 * j8 + 1];
+        const __nv_bfloat162* wp = reinterpret_cast<const __nv_bfloat162*>(&w[u]);
+        const float2 w0 = __bfloat1622float2(wp[0]), w1 = __bfloat1622float2(wp[1]);
+        const float2 w2 = __bfloat1622float2(wp[2]), w3 = __bfloat1622float2(wp[3]);
+        float part = w0.x * xa.x;
+        part = fmaf(w0.y, xa.y, part);
+        part = fmaf(w1.x, xa.z, part);
+        part = fmaf(w1.y, xa.w, part);
+        part = fmaf(w2.x, xb.x, part);
+        part = fmaf(w2.y, xb.y, part);
+        part = fmaf(w3.x, xb.z, part);
+        part = fmaf(w3.y, xb.w, part);
+        acc.add(part);
+      }
     }
     // K^T column of this variable, folded in at the 1/(2 qscale) scale so a
     // single compensated sum carries 2 (Q_hat x)_i + (K^T y)_i below.
+    gf::csum_group_reduce<32>(acc);
+    CSum g;
+    if (Tp) {
+      for (int64_t t = Tp[v0 + i] + lane; t < Tp[v0 + i + 1]; t += 32)
+        g.add(__fmul_rn(Tv[t], y[Tr[t]]));
+      gf::csum_group_reduce<32>(g);
+    }
+    if (lane == 0) {
+      const float xo = xs[i];
+      CSum s;                              // 2 (Q_hat x)_i + (K^T y)_i
+      s.merge(__fmul_rn(2.0f * qscale, acc.s), __fmul_rn(2.0f * qscale, acc.c));
+      s.add(__fmul_rn(2.0f * qdiag[i], xo));
+      s.merge(g.s, g.c);
+      if (mode == 1) {
+        out[i] = 0.5f * s.value();
+      } else {
+        const float delta = chat[v0 + i] + q.rho + s.value() - 2.0f * q.rho * xo;
+        float xn = fminf(1.0f, fmaxf(0.0f, xo - q.tau1 * delta));
+        x_new[v0 + i] = xn;
+        xbar[v0 + i] = 2.0f * xn - xo;
+        if (dlast) dlast[v0 + i] = q.tau1 * delta;
+      }
+    }
+  }
+  if (advance && blockIdx.x == 0) {
+    __syncthreads();
+    advance_penalty(st, sc, normQ, cap, ip_next);
+  }
+}
+
+// Same step with W2 stored as int8 (exact when max|W2| <= 127): 16 entries
+// per 16-byte load, one 1024-thread block per SM, each block a contiguous
+// range of rows, eight loads in flight per lane, 8-term plain chunks folded
+// into the compensated sum.
+constexpr int kI8Warps = 32;
+
+__global__ void __launch_bounds__(kI8Warps * 32, 1)
+k_dense_primal_i8(const int8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t v0,
+                  const float* __restrict__ qdiag, float qscale,
+                  const int64_t* __restrict__ Tp, const int32_t* __restrict__ Tr,
+                  const float* __restrict__ Tv, const float* __restrict__ y,
+                  const float* __restrict__ x_old, const float* __restrict__ chat,
+                  const GfIParam* __restrict__ ip, int inst, float* __restrict__ x_new,
+                  float* __restrict__ xbar, float* __restrict__ dlast, int mode,
+                  float* __restrict__ out, int advance, GfDState* st, const GfSched* sc,
+                  const double* normQ, const int32_t* cap, GfIParam* ip_next) {
+  extern __shared__ float4 xs4[];
+  float* xs = reinterpret_cast<float*>(xs4);
+  for (int64_t j = threadIdx.x; j < ld; j += blockDim.x) xs[j] = (j < n) ? x_old[v0 + j] : 0.0f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const GfIParam q = ip[inst];
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = (r0 + per < n) ? r0 + per : n;
+  const int64_t n16 = ld / 16;                // 16-byte words per row
+  for (int64_t i = r0 + warp; i < r1; i += kI8Warps) {
+    const uint4* row = reinterpret_cast<const uint4*>(W2 + i * ld);
+    CSum acc;
+    for (int64_t b16 = 0; b16 < n16; b16 += 8 * 32) {
+      uint4 w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j16 = b16 + lane + 32 * u;
+        w[u] = (j16 < n16) ? __ldg(row + j16) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j16 = b16 + lane + 32 * u;
+        if (j16 >= n16) break;
+        const float4* xv = xs4 + 4 * j16;
+        const uint32_t ww[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {           // two 8-term chunks
+          const float4 xa = xv[2 * h], xb = xv[2 * h + 1];
+          const uint32_t lo = ww[2 * h], hi = ww[2 * h + 1];
+          float part = (float)(int8_t)(lo) * xa.x;
+          part = fmaf((float)(int8_t)(lo >> 8), xa.y, part);
+          part = fmaf((float)(int8_t)(lo >> 16), xa.z, part);
+          part = fmaf((float)(int8_t)(lo >> 24), xa.w, part);
+          part = fmaf((float)(int8_t)(hi), xb.x, part);
+          part = fmaf((float)(int8_t)(hi >> 8), xb.y, part);
+          part = fmaf((float)(int8_t)(hi >> 16), xb.z, part);
+          part = fmaf((float)(int8_t)(hi >> 24), xb.w, part);
+          acc.add(part);
+        }
+      }
+    }
     gf::csum_group_reduce<32>(acc);
     CSum g;
     if (Tp) {
@@ -312,10 +413,30 @@ cudaError_t launch_primal(GfCtx* h, const GfBucket& b, const GfIParam* ip,
 
 }  // namespace
 
+static void dense_smem_attr(size_t smem) {
+  static size_t done = 48 * 1024;
+  if (smem > done) {
+    cudaFuncSetAttribute(k_dense_primal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_dense_primal_i8, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    done = smem;
+  }
+}
+
 cudaError_t gf_launch_dense_gemv_q(GfCtx* h, const GfDenseQ& dq, const float* x,
                                    float* out) {
-  int blocks = (int)std::min<int64_t>((dq.n + kDenseWarps - 1) / kDenseWarps, 296);
   size_t smem = sizeof(float) * (size_t)dq.ld;
+  dense_smem_attr(smem);
+  if (dq.W2i8) {
+    const int blocks = (int)std::min<int64_t>(h->num_sms, (dq.n + 7) / 8);
+    k_dense_primal_i8<<<blocks, kI8Warps * 32, smem, h->stream>>>(
+        dq.W2i8, dq.ld, dq.n, h->ih[dq.inst].var_off, dq.qdiag, dq.qscale, nullptr, nullptr,
+        nullptr, nullptr, x, h->chat, h->iprm, dq.inst, nullptr, nullptr, nullptr, 1, out, 0,
+        nullptr, nullptr, nullptr, nullptr, nullptr);
+    h->launches++;
+    return cudaGetLastError();
+  }
+  int blocks = (int)std::min<int64_t>((dq.n + kDenseWarps - 1) / kDenseWarps, 296);
   k_dense_primal<<<blocks, kDenseWarps * 32, smem, h->stream>>>(
       dq.W2, dq.ld, dq.n, h->ih[dq.inst].var_off, dq.qdiag, dq.qscale, nullptr, nullptr,
       nullptr, nullptr, x, h->chat, h->iprm, dq.inst, nullptr, nullptr, nullptr, 1, out,
@@ -358,10 +479,22 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
   // ---- primal (first launch advances the penalty state)
   int adv = 1;
   for (const GfDenseQ& dq : h->dense) {
-    int blocks = (int)std::min<int64_t>((dq.n + kDenseWarps - 1) / kDenseWarps, 296);
     size_t smem = sizeof(float) * (size_t)dq.ld;
+    dense_smem_attr(smem);
     const GfInstHost& I = h->ih[dq.inst];
     const bool hasK = (I.m1 + I.m2) > 0;
+    if (dq.W2i8) {
+      const int blocks = (int)std::min<int64_t>(h->num_sms, (dq.n + 7) / 8);
+      k_dense_primal_i8<<<blocks, kI8Warps * 32, smem, h->stream>>>(
+          dq.W2i8, dq.ld, dq.n, I.var_off, dq.qdiag, dq.qscale, hasK ? h->Tp : nullptr, h->Tr,
+          h->Tv, h->y, xo, h->chat, ip, dq.inst, xn, h->xbar, h->dlast, 0, nullptr, adv,
+          h->dstate, h->sched_d, h->normQhat_d, h->cap_d, ipn);
+      h->launches++;
+      adv = 0;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      continue;
+    }
+    int blocks = (int)std::min<int64_t>((dq.n + kDenseWarps - 1) / kDenseWarps, 296);
     k_dense_primal<<<blocks, kDenseWarps * 32, smem, h->stream>>>(
         dq.W2, dq.ld, dq.n, I.var_off, dq.qdiag, dq.qscale, hasK ? h->Tp : nullptr, h->Tr,
         h->Tv, h->y, xo, h->chat, ip, dq.inst, xn, h->xbar, h->dlast, 0, nullptr, adv,

@@ -378,3 +378,22 @@ def fused_eval_noalloc(p_dev, a_dev, c_dev, n, rhs, seed, inst_id, round_id, fir
 
 def mlp_nparams(F=8, H=128) -> int:
     return _lib.gfors_mlp_nparams(F, H)
+
+
+def mlp_forward(W_dev, nv, feat_dev, z_dev, p_dev=None, stream=None, F=8, H=128):
+    """gfors_mlp_forward on device addresses (e.g. tensor.data_ptr())."""
+    _check(_lib.gfors_mlp_forward(F, H, W_dev, nv, feat_dev, z_dev, p_dev, _stream_ptr(stream)))
+
+
+def mlp_loss_grad(W_dev, nv, feat_dev, label_dev, grad_dev, loss_dev=None, stream=None, F=8,
+                  H=128):
+    """gfors_mlp_loss_grad on device addresses."""
+    _check(_lib.gfors_mlp_loss_grad(F, H, W_dev, nv, feat_dev, label_dev, grad_dev, loss_dev,
+                                    _stream_ptr(stream)))
+
+
+def mlp_adam(np_, W_dev, grad_dev, m_dev, v_dev, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+             stream=None):
+    """gfors_mlp_adam on device addresses."""
+    _check(_lib.gfors_mlp_adam(np_, W_dev, grad_dev, m_dev, v_dev, t, lr, beta1, beta2, eps,
+                               _stream_ptr(stream)))

@@ -1,0 +1,151 @@
+"""Learned proposal: the CUDA MLP forward / gradient / Adam against the FP64
+oracle (same bf16 weight roundings), the feature kernel against its
+definitions on host-chosen inputs, and the ablation of the trained network
+against the plain sampler on held-out axial 3D-assignment instances."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2510_27117_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+G = pytest.importorskip("paper_2510_27117_b300.gfors")
+P = pytest.importorskip("paper_2510_27117_b300.proposal")
+
+KEYS = ("W1", "b1", "W2", "b2", "w3", "b3")
+SHAPES = {"W1": (128, 8), "b1": (128,), "W2": (128, 128), "b2": (128,), "w3": (128,),
+          "b3": (1,)}
+
+
+def _unpack(Wp):
+    out, o = {}, 0
+    for k in KEYS:
+        sz = int(np.prod(SHAPES[k]))
+        out[k] = Wp[o:o + sz].reshape(SHAPES[k]).astype(np.float32)
+        o += sz
+    return out
+
+
+def _data(nv, seed):
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((nv, 8)).astype(np.float32)
+    y = (rng.random(nv) < 0.3).astype(np.float32)
+    Wp = P.init_weights(seed)
+    Wp[1024:1152] = rng.standard_normal(128) * 0.1      # nonzero biases
+    Wp[-1] = 0.05
+    return f, y, Wp.astype(np.float32)
+
+
+def test_mlp_forward_matches_oracle():
+    import torch
+    f, y, Wp = _data(1000, 1)
+    z = torch.zeros(1000, device="cuda")
+    p = torch.zeros(1000, device="cuda")
+    Wd = torch.from_numpy(Wp).cuda()
+    fd = torch.from_numpy(f).cuda()
+    G.mlp_forward(Wd.data_ptr(), 1000, fd.data_ptr(), z.data_ptr(), p.data_ptr())
+    zo, po = O.mlp_forward(f, _unpack(Wp), rb=1)
+    zg = z.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(zg - zo) <= 1e-5 * (1 + np.abs(zo)))
+    assert np.all(np.abs(p.cpu().numpy() - po) <= 1e-5)
+
+
+def test_mlp_gradient_matches_oracle():
+    import torch
+    nv = 700                                   # several blocks and a ragged tail
+    f, y, Wp = _data(nv, 2)
+    Wd = torch.from_numpy(Wp).cuda()
+    fd = torch.from_numpy(f).cuda()
+    yd = torch.from_numpy(y).cuda()
+    g = torch.zeros_like(Wd)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.mlp_loss_grad(Wd.data_ptr(), nv, fd.data_ptr(), yd.data_ptr(), g.data_ptr(),
+                    loss.data_ptr())
+    lo, go = O.mlp_loss_grad(f, y, _unpack(Wp), rb=1)
+    assert abs(loss.item() - lo) <= 1e-6 * abs(lo)
+    gg = _unpack(g.cpu().numpy())
+    for k in KEYS:
+        scale = np.abs(go[k]).max() + 1e-12
+        assert np.all(np.abs(gg[k] - go[k]) <= 1e-4 * scale), k
+
+
+def test_adam_matches_oracle():
+    import torch
+    rng = np.random.default_rng(3)
+    n = G.mlp_nparams()
+    w = rng.standard_normal(n).astype(np.float32)
+    wd = torch.from_numpy(w.copy()).cuda()
+    m = torch.zeros_like(wd)
+    v = torch.zeros_like(wd)
+    mo, vo = np.zeros(n), np.zeros(n)
+    for t in range(1, 4):
+        g = rng.standard_normal(n).astype(np.float32)
+        gd = torch.from_numpy(g).cuda()
+        G.mlp_adam(n, wd.data_ptr(), gd.data_ptr(), m.data_ptr(), v.data_ptr(), t, lr=1e-2)
+        O.adam(w, g.astype(np.float64), mo, vo, t, lr=1e-2)
+    assert np.allclose(wd.cpu().numpy(), w, rtol=1e-5, atol=1e-6)
+
+
+def test_features_definitions():
+    inst = W.assign3d(I=6, idx=3)
+    prm = G.default_params(k_int=5, k_b=64, seed=3, x0=0.5)
+    H = G.load(inst, prm)
+    S = O.preprocess(inst, prm.seed, 0)
+    rng = np.random.default_rng(0)
+    x1 = rng.random(inst.n).astype(np.float32)
+    H.set_iterate(0, x1, x1, np.zeros(S.m, np.float32))
+    H.set_counters(3, 0.25)
+    H.set_proposal(P.init_weights(0))
+    f1 = H.get_features(0)                      # first push: history = {x1}
+    x2 = rng.random(inst.n).astype(np.float32)
+    H.set_iterate(0, x2, x2, None)
+    f2 = H.get_features(0)
+    cs = (S.c - S.c.mean()) / S.c.std()
+    assert np.allclose(f2[:, 0], cs, atol=1e-5)
+    assert np.allclose(f2[:, 1], 1.0)           # every column has 3 nonzeros
+    assert np.array_equal(f2[:, 2], x2)
+    assert np.allclose(f2[:, 3], x2 - x1, atol=1e-7)
+    assert np.allclose(f2[:, 4], 0.5 * (x1.astype(np.float64) + x2), atol=1e-6)
+    slab = x2.reshape(6, 36).max(axis=1).repeat(36)
+    assert np.allclose(f2[:, 5], x2 / slab, atol=1e-6)
+    assert np.allclose(f2[:, 7], 0.25)
+    # feature 7 = tau1 * delta of the last primal step
+    y = np.zeros(S.m, np.float32)
+    H.set_iterate(0, x2, x2, y)
+    H.set_counters(3, 0.25)
+    H.pdhg_steps(1)
+    f3 = H.get_features(0)
+    t1, t2 = O.step_sizes(0.99, S.normQ, 0.25, 0)
+    _, _, _, dl = O.pdhg_step(S, t1, t2, 0.25, x2.astype(np.float64), x2.astype(np.float64),
+                              y.astype(np.float64))
+    assert np.allclose(f3[:, 6], t1 * dl, atol=1e-6)
+    H.destroy()
+
+
+def test_learned_proposal_ablation(capsys):
+    """Train on plain runs of small axial 3D assignments, then compare the
+    learned / split proposals with the plain sampler on held-out instances
+    (same iteration budget).  Prints the gain; asserts that training
+    reduced the loss and that every proposal returns feasible incumbents."""
+    prm_kw = dict(k_b=256, seed=0x5EED0003, x0=0.5)
+    train_insts = [W.assign3d(I=10, idx=200 + q) for q in range(12)]
+    feat, lab = P.collect(train_insts, prm_kw, iters=400, k_int=20)
+    Wt, hist = P.train(feat, lab, epochs=6, batch=8192, lr=2e-3, seed=1)
+    assert hist[-1] < hist[0]
+    res = {0: [], 1: [], 2: []}
+    for q in range(4):
+        inst = W.assign3d(I=10, idx=900 + q)
+        for mode in (0, 1, 2):
+            H = G.load(inst, G.default_params(k_int=20, **prm_kw))
+            if mode:
+                H.set_proposal(Wt)
+            H.run(400, proposal=mode)
+            inc = H.incumbent(0)
+            assert inc["found"]
+            v, o = O.Evaluator(inst)(inc["x"][None, :])
+            assert v[0] == 0 and o[0] == inc["obj"]
+            res[mode].append(inc["obj"])
+            H.destroy()
+    with capsys.disabled():
+        print(f"\n[ablation] loss {hist[0]:.4f} -> {hist[-1]:.4f}; best objective per "
+              f"held-out instance: plain {res[0]}, learned {res[1]}, split {res[2]}")

@@ -54,3 +54,17 @@ def test_tc_full_size_round():
     xb = inc["x"].astype(bool)
     cut = Wm[np.ix_(xb, ~xb)].sum()
     assert inc["obj"] == -int(cut)
+
+
+@pytest.mark.parametrize("mode", [3, 4])
+def test_dense_scoring_with_linear_term(mode):
+    """Dense Q plus a nonzero linear term: objective counted once."""
+    inst = W.max_cut(n=257, idx=8)
+    inst.c = np.random.default_rng(2).integers(-9, 10, size=257).astype(np.float64)
+    prm = G.default_params(k_b=64, seed=5, eval_mode=mode)
+    H = G.load(inst, prm)
+    X = (np.random.default_rng(4).random((64, 257)) < 0.4).astype(np.uint8)
+    viol, obj = H.eval_candidates(X)
+    vo, oo = O.Evaluator(inst)(X)
+    assert np.array_equal(obj, oo) and np.all(viol == 0)
+    H.destroy()
