@@ -98,10 +98,15 @@ typedef struct {
   int32_t eval_mode;   /* 0 auto, 1 materialised bits, 2 fused sample+eval
                           (single-row instances), 3 dense tensor-core
                           scoring (dense small-integer Q), 4 dense scoring
-                          on CUDA cores (checking)                          */
+                          on CUDA cores (checking), 5 one-CTA tensor-core
+                          scoring instead of the two-CTA cluster kernel     */
   double power_tol;    /* power-iteration stop tolerance; 1e-12            */
   int32_t power_maxit; /* power-iteration cap; 5000                         */
   double wait_timeout_s;/* limit of every device-side wait; 2.0             */
+  int32_t pdhg_mode;   /* 0 auto (one persistent cooperative launch per call
+                          when a single dense instance fits; otherwise CUDA
+                          graphs of per-iteration launches), 1 per-iteration
+                          launches only                                     */
 } gfors_params;
 
 GFORS_API void gfors_default_params(gfors_params* prm);

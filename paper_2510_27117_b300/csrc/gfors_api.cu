@@ -185,9 +185,20 @@ static void host_advance(GfCtx* h, long long it) {
   }
 }
 
+cudaError_t gf_launch_persistent(GfCtx* h, int64_t nsteps);
+
 static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
   cudaError_t e;
   int64_t done = 0;
+  if (h->persist_ok && nsteps > 0) {
+    // one cooperative launch runs all nsteps iterations
+    const int pi = gf_prof_begin(h, 0);
+    if ((e = gf_launch_persistent(h, nsteps))) return e;
+    gf_prof_end(h, pi, (int)nsteps);
+    for (int64_t s = 0; s < nsteps; ++s) host_advance(h, h->k_host + 1 + s);
+    h->k_host += nsteps;
+    return cudaSuccess;
+  }
   // replay a captured pair of iterations while at least two remain
   while (h->use_graphs && nsteps - done >= 2) {
     const int p = (int)((h->k_host + 1) & 1);   // parity of the first iteration

@@ -111,6 +111,7 @@ extern "C" void gfors_default_params(gfors_params* p) {
   p->power_tol = 1e-12;
   p->power_maxit = 5000;
   p->wait_timeout_s = 2.0;
+  p->pdhg_mode = 0;
 }
 
 extern "C" const char* gfors_version(void) { return "gfors-b300 0.1 (sm_103a)"; }
@@ -999,6 +1000,10 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   ds.round_id = 0;
   UP(h->dstate, &ds, GfDState, 1);
   gf_set_slot(h, 1, h->rho_host);     // iteration 1 reads slot 1
+  {
+    extern bool gf_persistent_setup(GfCtx * h);
+    h->persist_ok = (P.pdhg_mode != 1) && gf_persistent_setup(h);
+  }
   GF_CK(h, cudaStreamSynchronize(s));
   h->h_best.assign(3 * ninst, INFINITY);
   h->h_last.assign(3 * ninst, 0);

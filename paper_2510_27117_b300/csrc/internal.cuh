@@ -242,6 +242,10 @@ struct gfors_ctx {
   cudaGraphExec_t g_iter2[2] = {nullptr, nullptr};
   long long pair_launches = 0;
   bool use_graphs = true;
+  // persistent cooperative PDHG launch (dense instance, matrix in smem)
+  bool persist_ok = false;
+  size_t persist_smem = 0;
+  unsigned* persist_bar = nullptr;
   unsigned host_round = 0;          // round id of the next round (host mirror)
   // phase profiling (CUDA events on the handle's stream)
   bool prof = false;

@@ -291,46 +291,75 @@ __global__ void k_fused_viol(const long long* __restrict__ fsum, const long long
 
 // Incumbent update of one instance per block: least feasible objective,
 // earliest candidate on ties; replaces only when strictly better.
-__global__ void __launch_bounds__(256)
+// (obj, sample) pair ordering: feasible first, then smaller objective, then
+// earlier sample.
+GF_DEV bool better(long long oa, int sa, long long ob, int sb) {
+  if (sb < 0) return false;
+  if (sa < 0) return true;
+  return ob < oa || (ob == oa && sb < sa);
+}
+
+constexpr int kIncThreads = 1024;
+
+__global__ void __launch_bounds__(kIncThreads)
 k_incumbent(const int32_t* __restrict__ viol, const long long* __restrict__ obj, int len,
             int chunk, int s0, const GfDState* __restrict__ st, GfInc* __restrict__ inc) {
   const int b = blockIdx.x;
+  const int32_t* vb = viol + (int64_t)b * chunk;
+  const long long* ob = obj + (int64_t)b * chunk;
   long long best = 0;
   int bs = -1;
-  for (int s = threadIdx.x; s < len; s += blockDim.x) {
-    if (viol[(int64_t)b * chunk + s] != 0) continue;
-    const long long o = obj[(int64_t)b * chunk + s];
-    if (bs < 0 || o < best) { best = o; bs = s; }
-  }
-  __shared__ long long sb[256];
-  __shared__ int ss[256];
-  sb[threadIdx.x] = best;
-  ss[threadIdx.x] = bs;
-  __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) {
-      const long long ob = sb[threadIdx.x + off];
-      const int os = ss[threadIdx.x + off];
-      const int ms = ss[threadIdx.x];
-      if (os >= 0 && (ms < 0 || ob < sb[threadIdx.x] || (ob == sb[threadIdx.x] && os < ms))) {
-        sb[threadIdx.x] = ob;
-        ss[threadIdx.x] = os;
+  // four independent loads in flight per thread
+  for (int s = threadIdx.x; s < len; s += 4 * kIncThreads) {
+    int vv[4];
+    long long oo[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int su = s + u * kIncThreads;
+      vv[u] = (su < len) ? vb[su] : 1;
+      oo[u] = (su < len) ? ob[su] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (vv[u] == 0 && better(best, bs, oo[u], s + u * kIncThreads)) {
+        best = oo[u];
+        bs = s + u * kIncThreads;
       }
-    }
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    GfInc I = inc[b];
-    I.changed = 0;
-    if (ss[0] >= 0 && (!I.found || sb[0] < I.obj)) {
-      I.found = 1;
-      I.obj = sb[0];
-      I.objf = (double)sb[0];
-      I.round_id = st->round_id;
-      I.sample = s0 + ss[0];
-      I.changed = 1;
+  // warp argmin by shuffles, then across the 32 warps
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long o2 = __shfl_down_sync(0xFFFFFFFFu, best, off);
+    const int s2 = __shfl_down_sync(0xFFFFFFFFu, bs, off);
+    if (better(best, bs, o2, s2)) { best = o2; bs = s2; }
+  }
+  __shared__ long long wb[32];
+  __shared__ int ws[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { wb[warp] = best; ws[warp] = bs; }
+  __syncthreads();
+  if (warp == 0) {
+    best = (lane < kIncThreads / 32) ? wb[lane] : 0;
+    bs = (lane < kIncThreads / 32) ? ws[lane] : -1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const long long o2 = __shfl_down_sync(0xFFFFFFFFu, best, off);
+      const int s2 = __shfl_down_sync(0xFFFFFFFFu, bs, off);
+      if (better(best, bs, o2, s2)) { best = o2; bs = s2; }
     }
-    inc[b] = I;
+    if (lane == 0) {
+      GfInc I = inc[b];
+      I.changed = 0;
+      if (bs >= 0 && (!I.found || best < I.obj)) {
+        I.found = 1;
+        I.obj = best;
+        I.objf = (double)best;
+        I.round_id = st->round_id;
+        I.sample = s0 + bs;
+        I.changed = 1;
+      }
+      inc[b] = I;
+    }
   }
 }
 
@@ -437,7 +466,7 @@ cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len) {
 
 // mode: 0 materialised bits, 1 fused (Philox regeneration), 2 dense.
 cudaError_t gf_launch_incumbent(GfCtx* h, int s0, int len, int mode, bool last_chunk) {
-  k_incumbent<<<h->ninst, 256, 0, h->stream>>>(h->viol, h->obj, len, h->chunk, s0, h->dstate,
+  k_incumbent<<<h->ninst, kIncThreads, 0, h->stream>>>(h->viol, h->obj, len, h->chunk, s0, h->dstate,
                                                h->inc);
   h->launches++;
   if (h->N > 0 && mode != 2) {

@@ -19,28 +19,39 @@ using gf::CSum;
 // at 1/(2L) with L = 2(||Q_hat|| + rho) when requested; tau2 = sigma/tau1).
 // Executed by all threads of one block; `next` is the slot to write.
 // ---------------------------------------------------------------------------
-__device__ void advance_penalty(GfDState* st, const GfSched* sc,
-                                const double* normQ, const int32_t* cap,
-                                GfIParam* next) {
+__device__ void advance_penalty(GfDState* st, const GfSched* sc, const double* normQ,
+                                const int32_t* cap, const GfIParam* cur, GfIParam* next) {
+  // The parameters of iteration it+1 equal those of iteration it unless the
+  // penalty counter advances (once per k_int iterations): only then are rho
+  // and the step sizes recomputed (FP64), otherwise the slot is copied.
   __shared__ double rho_s;
+  __shared__ int changed_s;
   if (threadIdx.x == 0) {
     long long it = st->k + 1;               // the iteration now running
     int n_next = (int)(it / sc->k_int);     // counter used by iteration it+1
     double rho = st->rho;
+    int changed = 0;
     while (st->n_rho < n_next) {
       st->n_rho += 1;
       double rt = sc->rho_min * pow(1.0 + (double)st->n_rho / sc->T, sc->p);
       double lo = rho + sc->delta;
       double v = rt < lo ? lo : rt;
       rho = v > sc->rho_max ? sc->rho_max : v;
+      changed = 1;
     }
     st->rho = rho;
     st->k = it;
     rho_s = rho;
+    changed_s = changed;
   }
   __syncthreads();
   const double rho = rho_s;
+  const int changed = changed_s;
   for (int b = threadIdx.x; b < sc->ninst; b += blockDim.x) {
+    if (!changed) {
+      next[b] = cur[b];
+      continue;
+    }
     double t1 = sqrt(sc->sigma);
     if (cap[b]) {
       double L = 2.0 * (normQ[b] + rho);
@@ -125,7 +136,7 @@ k_primal_cols(const int32_t* __restrict__ cols, int32_t ncols,
       if (dlast) dlast[i] = q.tau1 * delta;
     }
   }
-  if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip_next);
+  if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip, ip_next);
 }
 
 // ---------------------------------------------------------------------------
@@ -202,7 +213,7 @@ k_primal_long_final(const int32_t* __restrict__ ids, const int32_t* __restrict__
     xbar[i] = 2.0f * xn - xo;
     if (dlast) dlast[i] = p.tau1 * delta;
   }
-  if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip_next);
+  if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip, ip_next);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,7 +305,7 @@ k_dense_primal(const __nv_bfloat16* __restrict__ W2, int64_t ld, int64_t n,
   }
   if (advance && blockIdx.x == 0) {
     __syncthreads();
-    advance_penalty(st, sc, normQ, cap, ip_next);
+    advance_penalty(st, sc, normQ, cap, ip, ip_next);
   }
 }
 
@@ -382,7 +393,7 @@ k_dense_primal_i8(const int8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t 
   }
   if (advance && blockIdx.x == 0) {
     __syncthreads();
-    advance_penalty(st, sc, normQ, cap, ip_next);
+    advance_penalty(st, sc, normQ, cap, ip, ip_next);
   }
 }
 

@@ -132,10 +132,38 @@ GF_DEV void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// TMA load of one box, written to the same shared-memory offset of every
+// CTA in ctamask and completing on the same-offset mbarrier of each.
+GF_DEV void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                           uint16_t ctamask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(ctamask)
+      : "memory");
+}
+// MMA completion arriving on the same-offset mbarrier of every CTA in mask.
+GF_DEV void mma_commit_mc(uint32_t bar, uint16_t ctamask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"(ctamask)
+      : "memory");
+}
+GF_DEV void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 GF_DEV void named_bar(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// CL = 1: one CTA per tile.  CL = 2: a cluster of two CTAs computes the
+// tiles (2p, n) and (2p+1, n); each CTA loads its own W2 tile and HALF of the
+// shared candidate tile, multicast to both, so per-CTA operand traffic per
+// k-step drops from 48 KB to 32 KB; MMA completions are committed to both
+// CTAs' stage-release barriers (arrival count 2).
+template <int CL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            int n, int64_t ld, int len, int num_m, int num_n, int num_k,
@@ -162,7 +190,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     drain_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, CL);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
@@ -178,24 +206,37 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) cluster_sync();      // peers' barriers initialised
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
-  const int num_tiles = num_m * num_n;
+  uint32_t rank = 0;
+  if constexpr (CL == 2) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int num_mp = (num_m + CL - 1) / CL;    // tile rows handled per cluster step
+  const int num_tiles = num_mp * num_n;
+  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+  auto tile_m0 = [&](int t) { return (CL * (t % num_mp) + (int)rank) * BM; };
+  auto tile_n0 = [&](int t) { return (t / num_mp) * BN; };
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-        const int m0 = (t % num_m) * BM, n0 = (t / num_m) * BN;
+      for (int t = cid; t < num_tiles && ok; t += ncl) {
+        const int m0 = tile_m0(t), n0 = tile_n0(t);
         for (int kb = 0; kb < num_k && ok; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
           if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, limit_ns, &abort_flag))) break;
           mbar_arrive_expect_tx(full0 + 8 * s, STAGE_BYTES);
           tma_load_2d(smem_u32(stA + s * A_BYTES), &tmA, full0 + 8 * s, kb * BK, m0);
-          tma_load_2d(smem_u32(stB + s * B_BYTES), &tmB, full0 + 8 * s, kb * BK, n0);
+          if constexpr (CL == 2) {
+            // my half of the candidate tile, to both CTAs of the cluster
+            tma_load_2d_mc(smem_u32(stB + s * B_BYTES + rank * (B_BYTES / 2)), &tmB,
+                           full0 + 8 * s, kb * BK, n0 + (int)rank * (BN / 2), (uint16_t)0x3);
+          } else {
+            tma_load_2d(smem_u32(stB + s * B_BYTES), &tmB, full0 + 8 * s, kb * BK, n0);
+          }
         }
       }
       if (!ok) {
@@ -212,7 +253,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     if (lane == 0) {
       int it = 0, j = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++j) {
+      for (int t = cid; t < num_tiles && ok; t += ncl, ++j) {
         const int acc = j & 1;
         const uint32_t aph = (uint32_t)(j >> 1) & 1u;
         if (!(ok = mbar_wait(tempty0 + 8 * acc, aph ^ 1u, limit_ns, &abort_flag))) break;
@@ -228,7 +269,8 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           for (int k = 0; k < BK / 16; ++k)
             mma_bf16(d, sw128_desc(a0 + 32 * k), sw128_desc(b0 + 32 * k),
                      (kb | k) != 0 ? 1u : 0u);
-          mma_commit(empty0 + 8 * s);
+          if constexpr (CL == 2) mma_commit_mc(empty0 + 8 * s, (uint16_t)0x3);
+          else mma_commit(empty0 + 8 * s);
         }
         if (ok) mma_commit(tfull0 + 8 * acc);
       }
@@ -244,7 +286,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int et = threadIdx.x - 64;         // 0..127 within the epilogue group
     int j = 0;
-    for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++j) {
+    for (int t = cid; t < num_tiles; t += ncl, ++j) {
       const int acc = j & 1;
       const uint32_t aph = (uint32_t)(j >> 1) & 1u;
       bool ok = true;
@@ -255,7 +297,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       ok = ep_ok[0] && ep_ok[1] && ep_ok[2] && ep_ok[3];
       if (!ok) break;
       tc_fence_after();
-      const int m0 = (t % num_m) * BM, n0 = (t / num_m) * BN;
+      const int m0 = tile_m0(t), n0 = tile_n0(t);
       const int i = m0 + q * 32 + lane;
       const bool row_ok = i < n;
       const int lin2 = row_ok ? (int)(2 * lin[i]) : 0;
@@ -301,6 +343,9 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
   }
   __syncthreads();
+  // no CTA leaves while its peer may still multicast into it or arrive on
+  // its barriers (every wait above is bounded, so both CTAs get here)
+  if constexpr (CL == 2) cluster_sync();
   if (abort_flag && threadIdx.x == 0) atomicExch(&st->error, 1);
   if (warp == 1) {
     tc_fence_after();
@@ -344,8 +389,9 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, u
 struct TcCache {
   const void* W2 = nullptr;
   const void* Xs = nullptr;
-  CUtensorMap a, b;
+  CUtensorMap a, b, b2;
   int sms = 0;
+  int clusters2 = 0;                  // co-resident 2-CTA clusters (0: unusable)
   bool attr = false;
 };
 
@@ -353,6 +399,7 @@ struct TcCache {
 
 // Launch the tensor-core scorer for candidates [0, len) of the chunk;
 // obj (zeroed by the evaluation pass) receives the exact objectives.
+// eval_mode 5 forces the one-CTA variant (checking).
 cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int len) {
   (void)s0;
   static thread_local std::vector<TcCache> caches;
@@ -360,30 +407,79 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
   TcCache& C = caches[dq.inst % 64];
   if (C.W2 != dq.W2 || C.Xs != dq.Xs) {
     if (!make_map(&C.a, dq.W2, (uint64_t)dq.ld, (uint64_t)dq.n, (uint64_t)dq.ld, BK, BM) ||
-        !make_map(&C.b, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, BK, BN))
+        !make_map(&C.b, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, BK, BN) ||
+        !make_map(&C.b2, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, BK,
+                  BN / 2))
       return cudaErrorInvalidValue;
     C.W2 = dq.W2;
     C.Xs = dq.Xs;
   }
   if (!C.attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_score_tc<1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (!e) e = cudaFuncSetAttribute(k_score_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_BYTES);
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&C.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (C.sms / 2));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_score_tc<2>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      ncl = 0;
+    }
+    C.clusters2 = ncl;
     C.attr = true;
   }
   const int num_m = (int)((dq.n + BM - 1) / BM);
   const int num_n = (len + BN - 1) / BN;
   const int num_k = (int)(dq.ld / BK);
-  const int tiles = num_m * num_n;
-  const int grid = std::min(tiles, C.sms > 0 ? C.sms : 148);
   long long* out = h->obj + (int64_t)dq.inst * h->chunk;
+  unsigned long long* outu = reinterpret_cast<unsigned long long*>(out);
   const uint64_t limit = (uint64_t)(std::max(0.01, h->prm.wait_timeout_s) * 1e9);
-  k_score_tc<<<grid, kThreads, SMEM_BYTES, h->stream>>>(
-      C.a, C.b, (int)dq.n, dq.ld, len, num_m, num_n, num_k, dq.Xs, dq.lin,
-      reinterpret_cast<unsigned long long*>(out), limit, h->dstate);
+  const __nv_bfloat16* Xs = dq.Xs;
+  const long long* lin = dq.lin;
+  int nn = (int)dq.n, ll = len;
+  int64_t ld = dq.ld;
+  GfDState* st = h->dstate;
+  cudaError_t e;
+  if (C.clusters2 > 0 && h->prm.eval_mode != 5) {
+    const int tiles = ((num_m + 1) / 2) * num_n;
+    const int nclus = std::min(tiles, C.clusters2);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * nclus);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = h->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_score_tc<2>, C.a, C.b2, nn, ld, ll, num_m, num_n, num_k, Xs,
+                           lin, outu, limit, st);
+  } else {
+    const int tiles = num_m * num_n;
+    const int grid = std::min(tiles, C.sms > 0 ? C.sms : 148);
+    k_score_tc<1><<<grid, kThreads, SMEM_BYTES, h->stream>>>(C.a, C.b, nn, ld, ll, num_m,
+                                                             num_n, num_k, Xs, lin, outu,
+                                                             limit, st);
+    e = cudaGetLastError();
+  }
+  if (e) return e;
   k_halve<<<(len + 255) / 256, 256, 0, h->stream>>>(out, len);
   h->launches += 2;
   return cudaGetLastError();

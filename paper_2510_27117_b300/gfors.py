@@ -47,7 +47,7 @@ class Params(C.Structure):
                 ("tau_cap_by_L", i32), ("seed", u64), ("x0", f64), ("halt_tol", f64),
                 ("stall_window", i32), ("inst_base", i32), ("sample_chunk", i32),
                 ("eval_mode", i32), ("power_tol", f64), ("power_maxit", i32),
-                ("wait_timeout_s", f64)]
+                ("wait_timeout_s", f64), ("pdhg_mode", i32)]
 
 
 _H = vp

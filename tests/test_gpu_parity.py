@@ -252,3 +252,23 @@ def test_run_never_beats_brute_force(idx):
         v, o = ev(inc["x"][None, :])
         assert v[0] == 0 and o[0] == inc["obj"]
     H.destroy()
+
+
+def test_persistent_dense_path_matches_launch_path():
+    """One cooperative launch per call (matrix resident in shared memory)
+    against per-iteration launches: same iterates to FP32 summation-order
+    differences, identical penalty counters and incumbents' feasibility."""
+    inst = W.max_cut(n=700, idx=6)
+    out = []
+    for mode in (0, 1):
+        gp, _ = _params(k_int=10, k_b=64, x0=-1.0, pdhg_mode=mode)
+        H = G.load(inst, gp)
+        H.pdhg_steps(25)
+        x, xb, xp, _ = H.get_iterate(0)
+        sc = H.get_scales(0)
+        out.append((x, xb, sc))
+        H.destroy()
+    (xa, xba, sa), (xb_, xbb, sb) = out
+    assert np.max(np.abs(xa - xb_)) < 1e-5
+    assert np.max(np.abs(xba - xbb)) < 2e-5
+    assert sa[6] == sb[6] and sa[7] == sb[7]        # same step sizes (same rho)

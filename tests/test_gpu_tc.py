@@ -24,10 +24,12 @@ def _scores(inst, k_b, mode, R=5, seed=11):
     return p, X, viol, obj, inc
 
 
-@pytest.mark.parametrize("n,k_b", [(300, 96), (200, 512), (513, 288)])
-def test_tc_matches_simt_and_oracle_small(n, k_b):
+@pytest.mark.parametrize("n,k_b,mode", [(300, 96, 3), (200, 512, 3), (513, 288, 3),
+                                        (300, 96, 5), (513, 288, 5), (640, 1024, 3)])
+def test_tc_matches_simt_and_oracle_small(n, k_b, mode):
+    """mode 3: two-CTA cluster kernel with multicast; mode 5: one-CTA kernel."""
     inst = W.max_cut(n=n, idx=7)
-    p, X, viol, obj, inc = _scores(inst, k_b, 3)
+    p, X, viol, obj, inc = _scores(inst, k_b, mode)
     _, X2, viol2, obj2, inc2 = _scores(inst, k_b, 4)
     assert np.array_equal(X, X2)
     assert np.array_equal(obj, obj2) and np.all(viol == 0)
@@ -42,7 +44,8 @@ def test_tc_full_size_round():
     inst = W.max_cut(n=4096, idx=0)
     p, X, viol, obj, inc = _scores(inst, 8192, 3)
     _, X2, viol2, obj2, inc2 = _scores(inst, 8192, 4)
-    assert np.array_equal(obj, obj2)
+    _, X5, viol5, obj5, inc5 = _scores(inst, 8192, 5)
+    assert np.array_equal(obj, obj2) and np.array_equal(obj, obj5)
     assert inc["obj"] == inc2["obj"] and inc["sample"] == inc2["sample"]
     # sampled candidates scored by the oracle from its own draws
     Xo = O.sample(inst, p, 24, 11, 0, 5)
