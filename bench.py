@@ -76,8 +76,14 @@ class ClockSampler:
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
+            # start timing only once the sampler is producing lines
+            t0 = time.time()
+            while time.time() - t0 < 5.0:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -239,23 +245,39 @@ def run_e2e(G, H, insts, k_int, k_b, stream, args, world):
 
 
 def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps):
+    """Roofline of the dominant phase of the step (largest share of the
+    event-timed step), with the tensor-core scorer reported beside it."""
+    phases = {k: v for k, v in prof.items() if v[1]}
+    if not phases:
+        return None
+    dom = max(phases, key=lambda k: phases[k][0])
+    n = insts[0].n
+    fp32_tflops = 148 * 128 * 2 * 2.032e9 / 1e12      # FMA lanes x 2 x max SM clock
+    out = {"phase": dom, "share": phases[dom][0] / sum(v[0] for v in phases.values()),
+           "peak_source": src}
     if workload == "maxcut":
-        n = insts[0].n
-        ms, cnt = prof.get("dense_score", (0.0, 0))
-        flops = 2.0 * n * n * k_b
+        ms, cnt = phases.get("dense_score", (0.0, 0))
+        tc = None
         if cnt:
-            t = ms / cnt / 1e3
-            ach = flops / t / 1e12
-            peak = peaks.get("bf16_tflops", 1800.0)
-            pdhg_ms, pdhg_cnt = prof.get("pdhg", (0.0, 0))
-            return {"kernel": "dense Q.X scoring (EvalBest)", "bound": "tensor",
-                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None, "peak_source": src,
-                    "algorithmic_per_launch": f"2*n*n*k_b = {flops:.3e} FLOP",
-                    "pdhg_iter_ms": pdhg_ms / max(pdhg_cnt, 1),
-                    "pdhg_gbs": (n * n * 2 + 12 * n) / (pdhg_ms / max(pdhg_cnt, 1) / 1e3) / 1e9
-                    if pdhg_cnt else None}
-    return None
+            flops = 2.0 * n * n * k_b
+            ach = flops / (ms / cnt / 1e3) / 1e12
+            tc = {"kernel": "k_score_tc (tcgen05 W2.X^T + fused reduction)", "bound": "tensor",
+                  "achieved": ach, "peak": peaks.get("bf16_tflops", 1800.0), "unit": "TFLOP/s",
+                  "frac": ach / peaks.get("bf16_tflops", 1800.0), "traffic": None,
+                  "algorithmic_per_launch": f"2 n^2 k_b = {flops:.4e} FLOP"}
+        if dom == "pdhg":
+            ms, iters = phases["pdhg"]
+            flops = 2.0 * n * n * iters          # one n x n GEMV per iteration
+            ach = flops / (ms / 1e3) / 1e12
+            out.update({"kernel": "k_pdhg_dense_persistent (PDHG, Alg. 2, dense Q GEMV)",
+                        "bound": "alu", "achieved": ach, "peak": fp32_tflops,
+                        "unit": "TFLOP/s", "frac": ach / fp32_tflops, "traffic": None,
+                        "algorithmic_per_launch": f"k_int x 2 n^2 = {2.0 * n * n * k_int:.4e} FLOP",
+                        "us_per_iteration": ms / iters * 1e3, "scoring": tc})
+        elif dom == "dense_score" and tc:
+            out.update(tc)
+        return out
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -320,8 +342,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maxcut", choices=list(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=20.0)

@@ -90,6 +90,78 @@ GF_DEV void csum_group_reduce(CSum& a) {
 }
 
 // ---------------------------------------------------------------------------
+// Packed FP32 pair arithmetic (two IEEE round-to-nearest operations per
+// instruction) on 64-bit registers holding (lo, hi) floats.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+GF_DEV f32x2 f2_pack(uint32_t lo, uint32_t hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+GF_DEV f32x2 f2_add(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+GF_DEV f32x2 f2_mul(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+GF_DEV f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+GF_DEV float f2_sum(f32x2 a) {
+  return __fadd_rn(__uint_as_float((uint32_t)a), __uint_as_float((uint32_t)(a >> 32)));
+}
+// Signed bytes k, k+1 of a word as an exact float pair.  `wbias` is the word
+// with every byte's sign bit flipped (byte + 128): the biased byte becomes the
+// low mantissa bits of 2^23, and 2^23 + 128 is subtracted afterwards.
+GF_DEV f32x2 f2_i8pair(uint32_t wbias, int k) {
+  return f2_pack(__byte_perm(wbias, 0x4B000000u, 0x7650u + k),
+                 __byte_perm(wbias, 0x4B000000u, 0x7651u + k));
+}
+
+// One lane's share of an int8 row times an FP32 vector (the dense Q GEMV of
+// the primal step).  Lane l reads the 4-entry words l, l + 32, l + 64, ...
+// of the row; words (t, t + 32) form one 8-term chunk summed in plain FP32
+// (packed pairs).  Chunks starting at t = l + 128 j go to a first compensated
+// sum, chunks starting at t = l + 64 + 128 j to a second (two independent
+// dependency chains), merged at the end.  `row` may point to shared or global
+// memory; `x4` holds the vector as float4 words in shared memory.  Both PDHG
+// paths of a dense instance use this one routine, so their sums are
+// identical.
+GF_DEV f32x2 i8_chunk(const uint32_t* row, const ulonglong2* xv, int64_t t, int64_t nq,
+                      f32x2 bias) {
+  const uint32_t wa = row[t] ^ 0x80808080u;
+  const ulonglong2 xa = xv[t];
+  f32x2 pr = f2_mul(f2_add(f2_i8pair(wa, 0), bias), xa.x);
+  pr = f2_fma(f2_add(f2_i8pair(wa, 2), bias), xa.y, pr);
+  if (t + 32 < nq) {
+    const uint32_t wb = row[t + 32] ^ 0x80808080u;
+    const ulonglong2 xb = xv[t + 32];
+    pr = f2_fma(f2_add(f2_i8pair(wb, 0), bias), xb.x, pr);
+    pr = f2_fma(f2_add(f2_i8pair(wb, 2), bias), xb.y, pr);
+  }
+  return pr;
+}
+GF_DEV CSum i8_row_dot(const uint32_t* row, const float4* x4, int64_t nq, int lane) {
+  const f32x2 bias = f2_pack(__float_as_uint(-8388736.0f), __float_as_uint(-8388736.0f));
+  const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x4);
+  CSum acc, acc2;
+  for (int64_t t = lane; t < nq; t += 128) {
+    const f32x2 p1 = i8_chunk(row, xv, t, nq, bias);
+    if (t + 64 < nq) acc2.add(f2_sum(i8_chunk(row, xv, t + 64, nq, bias)));
+    acc.add(f2_sum(p1));
+  }
+  acc.merge(acc2.s, acc2.c);
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
 // Time source for bounded device waits.
 // ---------------------------------------------------------------------------
 GF_DEV uint64_t globaltimer_ns() {

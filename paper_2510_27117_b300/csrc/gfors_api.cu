@@ -192,11 +192,16 @@ static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
   int64_t done = 0;
   if (h->persist_ok && nsteps > 0) {
     // one cooperative launch runs all nsteps iterations
-    const int pi = gf_prof_begin(h, 0);
-    if ((e = gf_launch_persistent(h, nsteps))) return e;
-    gf_prof_end(h, pi, (int)nsteps);
-    for (int64_t s = 0; s < nsteps; ++s) host_advance(h, h->k_host + 1 + s);
-    h->k_host += nsteps;
+    // (at most 2^20 iterations per launch keeps the barrier counter in range)
+    while (done < nsteps) {
+      const int64_t cnt = std::min<int64_t>(nsteps - done, (int64_t)1 << 20);
+      const int pi = gf_prof_begin(h, 0);
+      if ((e = gf_launch_persistent(h, cnt))) return e;
+      gf_prof_end(h, pi, (int)cnt);
+      for (int64_t s = 0; s < cnt; ++s) host_advance(h, h->k_host + 1 + s);
+      h->k_host += cnt;
+      done += cnt;
+    }
     return cudaSuccess;
   }
   // replay a captured pair of iterations while at least two remain
@@ -334,8 +339,12 @@ static cudaError_t enqueue_final_round(GfCtx* h) {
   k_round_bits<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(xk, h->var_live, h->N,
                                                                      h->kw, h->X);
   for (const GfDenseQ& dq : h->dense)
+  {
     k_round_dense<<<(unsigned)((dq.ld + 255) / 256), 256, 0, h->stream>>>(
         xk, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.Xs);
+    k_dense_bits<<<(unsigned)((dq.ld / 32 + 255) / 256), 256, 0, h->stream>>>(dq.Xs, 1, dq.ld,
+                                                                               dq.Xb);
+  }
   h->launches += 2 + (long long)h->dense.size();
   if ((e = gf_launch_eval(h, 0, 1))) return e;
   for (const GfDenseQ& dq : h->dense)
@@ -586,6 +595,8 @@ extern "C" gfors_status gfors_eval_candidates(gfors_handle h, int32_t inst, int3
       const GfDenseQ& dq = h->dense[I.dense_idx];
       k_pack_dense<<<(unsigned)(((int64_t)len * dq.ld + 255) / 256), 256, 0, h->stream>>>(
           Xd, len, I.n, dq.ld, dq.Xs);
+      k_dense_bits<<<(unsigned)(((int64_t)len * (dq.ld / 32) + 255) / 256), 256, 0,
+                     h->stream>>>(dq.Xs, len, dq.ld, dq.Xb);
     } else {
       const int kwu = (len + 31) / 32;
       k_pack_bits<<<(unsigned)((I.n * kwu + 255) / 256), 256, 0, h->stream>>>(Xd, len, I.n,

@@ -83,6 +83,7 @@ struct GfDenseQ {                   // dense +-small-integer Q (tensor-core path
   float qscale = 0.f;               // 0.5 / s_obj
   long long* lin = nullptr;         // c_i + Q_ii (original, integer)
   __nv_bfloat16* Xs = nullptr;      // candidates, sample-major, chunk x ld
+  uint32_t* Xb = nullptr;           // same as bit words, chunk x ld/32
   int chunk = 0;
   bool tc_ok = false;               // tensor-core scoring exact (n max|W2| < 2^24)
   long long w2max = 0;
@@ -245,7 +246,9 @@ struct gfors_ctx {
   // persistent cooperative PDHG launch (dense instance, matrix in smem)
   bool persist_ok = false;
   size_t persist_smem = 0;
-  unsigned* persist_bar = nullptr;
+  int64_t persist_per = 0;          // rows per block
+  int persist_grid = 0;             // blocks (each owns >= 1 row)
+  unsigned* persist_bar = nullptr;  // grid-barrier counter
   unsigned host_round = 0;          // round id of the next round (host mirror)
   // phase profiling (CUDA events on the handle's stream)
   bool prof = false;
@@ -294,6 +297,10 @@ cudaError_t gf_launch_final_round(GfCtx* h);
 // phase profiling: returns an index to pass to gf_prof_end (or -1)
 int gf_prof_begin(GfCtx* h, int phase);
 void gf_prof_end(GfCtx* h, int idx, int count);
+
+// bit words of bf16 candidate rows (k_sample.cu)
+__global__ void k_dense_bits(const __nv_bfloat16* __restrict__ Xs, int len, int64_t ld,
+                             uint32_t* __restrict__ Xb);
 
 // helpers used by several files
 int64_t gf_round_up(int64_t v, int64_t m);

@@ -334,39 +334,9 @@ k_dense_primal_i8(const int8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t 
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * per;
   const int64_t r1 = (r0 + per < n) ? r0 + per : n;
-  const int64_t n16 = ld / 16;                // 16-byte words per row
+  const int64_t nq = ld / 4;                  // 4-entry words per row
   for (int64_t i = r0 + warp; i < r1; i += kI8Warps) {
-    const uint4* row = reinterpret_cast<const uint4*>(W2 + i * ld);
-    CSum acc;
-    for (int64_t b16 = 0; b16 < n16; b16 += 8 * 32) {
-      uint4 w[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t j16 = b16 + lane + 32 * u;
-        w[u] = (j16 < n16) ? __ldg(row + j16) : make_uint4(0u, 0u, 0u, 0u);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t j16 = b16 + lane + 32 * u;
-        if (j16 >= n16) break;
-        const float4* xv = xs4 + 4 * j16;
-        const uint32_t ww[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {           // two 8-term chunks
-          const float4 xa = xv[2 * h], xb = xv[2 * h + 1];
-          const uint32_t lo = ww[2 * h], hi = ww[2 * h + 1];
-          float part = (float)(int8_t)(lo) * xa.x;
-          part = fmaf((float)(int8_t)(lo >> 8), xa.y, part);
-          part = fmaf((float)(int8_t)(lo >> 16), xa.z, part);
-          part = fmaf((float)(int8_t)(lo >> 24), xa.w, part);
-          part = fmaf((float)(int8_t)(hi), xb.x, part);
-          part = fmaf((float)(int8_t)(hi >> 8), xb.y, part);
-          part = fmaf((float)(int8_t)(hi >> 16), xb.z, part);
-          part = fmaf((float)(int8_t)(hi >> 24), xb.w, part);
-          acc.add(part);
-        }
-      }
-    }
+    CSum acc = gf::i8_row_dot(reinterpret_cast<const uint32_t*>(W2 + i * ld), xs4, nq, lane);
     gf::csum_group_reduce<32>(acc);
     CSum g;
     if (Tp) {

@@ -244,32 +244,62 @@ __global__ void k_closure(const int64_t* __restrict__ rv, const int64_t* __restr
 }
 
 // Bernoulli draws of a dense-Q instance written sample-major as bf16 0/1
-// (the tensor-core operand), one thread per (sample, 4 variables).
+// (the tensor-core operand) and as bit words Xb[s * ld/32 + w] (bit t =
+// variable 32 w + t, read by the scorer's epilogue), one thread per
+// (sample = blockIdx.y, 4 variables); 8 consecutive lanes assemble one word.
 __global__ void __launch_bounds__(256)
-k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld, int len,
+k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld,
             int s0, uint64_t seed, int inst, const GfDState* __restrict__ st,
-            __nv_bfloat16* __restrict__ Xs) {
+            __nv_bfloat16* __restrict__ Xs, uint32_t* __restrict__ Xb) {
   const int64_t n4 = ld / 4;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= n4 * len) return;
-  const int sidx = (int)(gid / n4);
-  const int64_t g4 = gid % n4;
+  const int64_t g4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g4 >= n4) return;
+  const int sidx = (int)blockIdx.y;
   const int64_t i0 = g4 * 4;
   uint32_t b[4] = {0, 0, 0, 0};
   if (i0 < n) {
     const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)inst, st->round_id,
                                     (uint32_t)(s0 + sidx), (uint64_t)g4);
-    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-      if (i0 + l < n) b[l] = (uu[l] >> 8) < gf::prob_threshold(p[v0 + i0 + l]);
+    // v0 and i0 are multiples of 4; entries at or past n are padding
+    const float4 pv = __ldg(reinterpret_cast<const float4*>(p + v0 + i0));
+    b[0] = (u.x >> 8) < gf::prob_threshold(pv.x);
+    b[1] = (i0 + 1 < n) && (u.y >> 8) < gf::prob_threshold(pv.y);
+    b[2] = (i0 + 2 < n) && (u.z >> 8) < gf::prob_threshold(pv.z);
+    b[3] = (i0 + 3 < n) && (u.w >> 8) < gf::prob_threshold(pv.w);
   }
   // bf16 one = 0x3F80
   uint2 out;
   out.x = (b[0] ? 0x3F80u : 0u) | ((b[1] ? 0x3F80u : 0u) << 16);
   out.y = (b[2] ? 0x3F80u : 0u) | ((b[3] ? 0x3F80u : 0u) << 16);
   reinterpret_cast<uint2*>(Xs + (int64_t)sidx * ld)[g4] = out;
+  // ld/4 is a multiple of 16, so the 8 lanes holding one 32-variable word
+  // are always active together and belong to the same candidate
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned m8 = 0xFFu << (lane & ~7u);
+  uint32_t v = (b[0] | (b[1] << 1) | (b[2] << 2) | (b[3] << 3)) << (4 * (lane & 7u));
+  v |= __shfl_xor_sync(m8, v, 1, 8);
+  v |= __shfl_xor_sync(m8, v, 2, 8);
+  v |= __shfl_xor_sync(m8, v, 4, 8);
+  if ((lane & 7u) == 0) Xb[(int64_t)sidx * (ld / 32) + g4 / 8] = v;
 }
+
+}  // namespace
+
+// Bit words of bf16 candidate rows (for writers other than the sampler).
+__global__ void k_dense_bits(const __nv_bfloat16* __restrict__ Xs, int len, int64_t ld,
+                             uint32_t* __restrict__ Xb) {
+  const int64_t nw = ld / 32;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nw * len) return;
+  const int s = (int)(gid / nw);
+  const int64_t w = gid % nw;
+  const unsigned short* row = reinterpret_cast<const unsigned short*>(Xs + (int64_t)s * ld);
+  uint32_t m = 0;
+  for (int t = 0; t < 32; ++t) m |= (uint32_t)(row[32 * w + t] != 0) << t;
+  Xb[gid] = m;
+}
+
+namespace {
 
 }  // namespace
 
@@ -326,12 +356,16 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   }
   if (for_dense) {
     for (const GfDenseQ& dq : h->dense) {
-      const int64_t threads = (dq.ld / 4) * len;
-      k_bern_bf16<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(
-          p, h->ih[dq.inst].var_off, dq.n, dq.ld, len, s0, P.seed, P.inst_base + dq.inst,
-          h->dstate, dq.Xs);
-      h->launches++;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      // one block row per candidate, at most 32768 candidates per launch
+      for (int a = 0; a < len; a += 32768) {
+        const int cnt = std::min(32768, len - a);
+        const dim3 grid((unsigned)((dq.ld / 4 + 255) / 256), (unsigned)cnt);
+        k_bern_bf16<<<grid, 256, 0, h->stream>>>(
+            p, h->ih[dq.inst].var_off, dq.n, dq.ld, s0 + a, P.seed, P.inst_base + dq.inst,
+            h->dstate, dq.Xs + (int64_t)a * dq.ld, dq.Xb + (int64_t)a * (dq.ld / 32));
+        h->launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
     }
   }
   return cudaSuccess;

@@ -33,7 +33,7 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
 constexpr int TMEM_COLS = 512;                  // two 256-column accumulators
 constexpr int kThreads = 192;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 4 * BN * 4 /*partials*/ +
-                           256 /*barriers*/;
+                           4 * BN * 4 /*candidate bits*/ + 256 /*barriers*/;
 
 GF_DEV uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -167,7 +167,7 @@ template <int CL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            int n, int64_t ld, int len, int num_m, int num_n, int num_k,
-           const __nv_bfloat16* __restrict__ Xs, const long long* __restrict__ lin,
+           const uint32_t* __restrict__ Xb, const long long* __restrict__ lin,
            unsigned long long* __restrict__ obj, uint64_t limit_ns, GfDState* st) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
@@ -175,7 +175,8 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   uint8_t* stA = base;                                   // STAGES x 16 KB
   uint8_t* stB = base + STAGES * A_BYTES;                // STAGES x 32 KB
   int* partial = reinterpret_cast<int*>(base + STAGES * STAGE_BYTES);   // [4][BN]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(partial + 4 * BN);
+  uint32_t* xbits = reinterpret_cast<uint32_t*>(partial + 4 * BN);      // [BN][4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xbits + 4 * BN);
   // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
@@ -298,6 +299,16 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       if (!ok) break;
       tc_fence_after();
       const int m0 = tile_m0(t), n0 = tile_n0(t);
+      // the tile's candidate bits (256 candidates x the 4 words of rows
+      // m0..m0+127) into shared memory once; read back as broadcast words
+      {
+        const int ldw = (int)(ld / 32);
+        for (int e = et; e < BN * 4; e += 128) {
+          const int sl = e >> 2, w = m0 / 32 + (e & 3), s = n0 + sl;
+          xbits[e] = (s < len && w < ldw) ? Xb[(int64_t)s * ldw + w] : 0u;
+        }
+        named_bar(1, 128);
+      }
       const int i = m0 + q * 32 + lane;
       const bool row_ok = i < n;
       const int lin2 = row_ok ? (int)(2 * lin[i]) : 0;
@@ -308,10 +319,8 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         int v[32];
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
-          const int s = n0 + c * 32 + jj;
-          bool bit = false;
-          if (row_ok && s < len)
-            bit = reinterpret_cast<const unsigned short*>(Xs)[(int64_t)s * ld + i] != 0;
+          const uint32_t word = xbits[(c * 32 + jj) * 4 + q];
+          const bool bit = row_ok && ((word >> lane) & 1u);
           v[jj] = bit ? (__float2int_rn(__uint_as_float(r[jj])) + lin2) : 0;
         }
         // butterfly reduce-scatter: lane t ends with the sum of column t
@@ -448,7 +457,7 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
   long long* out = h->obj + (int64_t)dq.inst * h->chunk;
   unsigned long long* outu = reinterpret_cast<unsigned long long*>(out);
   const uint64_t limit = (uint64_t)(std::max(0.01, h->prm.wait_timeout_s) * 1e9);
-  const __nv_bfloat16* Xs = dq.Xs;
+  const uint32_t* Xb = dq.Xb;
   const long long* lin = dq.lin;
   int nn = (int)dq.n, ll = len;
   int64_t ld = dq.ld;
@@ -469,13 +478,13 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
     cfg.stream = h->stream;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_score_tc<2>, C.a, C.b2, nn, ld, ll, num_m, num_n, num_k, Xs,
+    e = cudaLaunchKernelEx(&cfg, k_score_tc<2>, C.a, C.b2, nn, ld, ll, num_m, num_n, num_k, Xb,
                            lin, outu, limit, st);
   } else {
     const int tiles = num_m * num_n;
     const int grid = std::min(tiles, C.sms > 0 ? C.sms : 148);
     k_score_tc<1><<<grid, kThreads, SMEM_BYTES, h->stream>>>(C.a, C.b, nn, ld, ll, num_m,
-                                                             num_n, num_k, Xs, lin, outu,
+                                                             num_n, num_k, Xb, lin, outu,
                                                              limit, st);
     e = cudaGetLastError();
   }
