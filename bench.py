@@ -42,8 +42,18 @@ WORKLOADS = {
         "512 knapsacks n_i~U[1e3,1e5], 4096 candidates/instance/round, k_int=50"),
     "assign3d": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).assign3d(
         I=64, idx=r), 50, 1024,
-        "axial 3D assignment I=64 (262,144 binaries), 1024 candidates/round, k_int=50"),
+        "axial 3D assignment I=64 (262,144 binaries), 1024 candidates/round, k_int=50, "
+        "learned proposal (MLP 8-128-128-1, random-init weights)"),
+    "facility": (lambda r: [__import__("paper_2510_27117_b300.workloads", fromlist=["x"])
+                            .facility_location(1000, 10000, idx=16 * r + q) for q in range(16)],
+                 50, 256,
+                 "16 facility-location instances 1000 x 10000 (10,001,000 binaries, 30M nnz "
+                 "each), 4 rounds x 256 candidates/instance, k_int=50, learned proposal "
+                 "(random-init weights)"),
 }
+# rounds per step and proposal (0 plain x_k, 1 learned) of each workload
+ROUNDS = {"maxcut": 1, "setcover": 1, "knapsack": 1, "assign3d": 1, "facility": 4}
+PROPOSAL = {"maxcut": 0, "setcover": 0, "knapsack": 0, "assign3d": 1, "facility": 1}
 
 
 def env_rank():
@@ -142,13 +152,23 @@ def run_ours(args, rank, world, local):
     H = G.load_batch(insts, prm, stream=stream)
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t_load0
+    tuned = None
+    if args.workload != "maxcut":           # lane counts of the bucket kernels
+        lanes, hit = H.autotune(os.environ.get("GFORS_TUNE_CACHE"))
+        tuned = {"lanes_rows": lanes[:5].tolist(), "lanes_cols": lanes[5:].tolist(),
+                 "cache_hit": hit}
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     round_id = [0]
 
+    nr, prop = ROUNDS[args.workload], PROPOSAL[args.workload]
+    if prop:
+        from paper_2510_27117_b300 import proposal as PR
+        H.set_proposal(PR.init_weights(seed=0))
+
     def step():
         H.pdhg_steps(k_int)
-        H.sample_eval(1, round_id[0], 0)
-        round_id[0] += 1
+        H.sample_eval(nr, round_id[0], prop)
+        round_id[0] += nr
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -186,24 +206,26 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_step = ms / args.steps
-    cands = k_b * len(insts)
+    cands = k_b * len(insts) * nr
     value = cands * args.steps * world / (ms / 1e3)
     iters_s = k_int * args.steps / (ms / 1e3)
 
     # ---- end to end through the public API with host buffers
-    e2e = run_e2e(G, H, insts, k_int, k_b, stream, args, world)
+    e2e = run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr, prop)
 
     # ---- roofline of the dominant kernel (phase timed with events on the stream)
     peaks, src = load_peaks()
-    roof = roofline(args.workload, insts, k_int, k_b, prof, peaks, src, args.steps)
+    roof = roofline(args.workload, insts, k_int, k_b * nr, prof, peaks, src, args.steps)
     out = {
         "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 PDHG / bf16 scoring / int64 evaluation", "data": "synthetic (seeded)",
         "config": {"workload": desc, "global_batch": cands * world, "n": insts[0].n,
-                   "instances": len(insts), "k_int": k_int, "k_b": k_b,
-                   "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
+                   "instances": len(insts), "k_int": k_int, "k_b": k_b, "k_r": nr,
+                   "proposal": ["plain", "learned"][prop],
+                   "parallelism": f"replicas x{world}", "l2": "flushed between steps",
+                   "autotune": tuned},
         "pdhg_iters_per_s": iters_s,
         "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "e2e": e2e, "gpu_launches": int(launches), "load_s": t_load,
@@ -211,36 +233,38 @@ def run_ours(args, rank, world, local):
     }
     out["clocks"] = clk.summary()
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = (cpu_baseline(args.workload, budget_s=args.cpu_budget)
+                               if args.cpu_budget > 0 else None)
         print(json.dumps(out), flush=True)
     H.destroy()
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_e2e(G, H, insts, k_int, k_b, stream, args, world):
+def run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr=1, prop=0):
     """The same metric through the public API per step: host->device copy of
     the warm-start iterate from pinned memory (gfors_set_iterate), the step,
     and the incumbent read back to the host (gfors_incumbent)."""
     import torch
-    n = insts[0].n
-    x = torch.full((n,), 0.5, dtype=torch.float32).pin_memory().numpy()
+    nmax = max(I.n for I in insts)
+    xall = torch.full((nmax,), 0.5, dtype=torch.float32).pin_memory().numpy()
+    xs = [xall[:I.n] for I in insts]
     steps = max(2, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rid = 10_000
     for _ in range(steps):
         for q in range(len(insts)):
-            H.set_iterate(q, x, x, None)
+            H.set_iterate(q, xs[q], xs[q], None)
         H.pdhg_steps(k_int)
-        H.sample_eval(1, rid, 0)
-        rid += 1
+        H.sample_eval(nr, rid, prop)
+        rid += nr
         for q in range(len(insts)):
             H.incumbent(q, want_x=True)
     dt = time.perf_counter() - t0
     bi = sum(2 * 4 * I.n for I in insts)
     bo = sum(I.n + 8 + 8 + 8 for I in insts)
-    return {"value": k_b * len(insts) * steps * world / dt, "unit": "candidates/s",
+    return {"value": k_b * nr * len(insts) * steps * world / dt, "unit": "candidates/s",
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps}
 
 
@@ -277,65 +301,125 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps):
         elif dom == "dense_score" and tc:
             out.update(tc)
         return out
+    # sparse instances: HBM-bound PDHG with the per-iteration algorithmic bytes
+    # of each workload; Philox-bound sampling against the integer-ALU rate
+    n = sum(I.n for I in insts)
+    nnz = sum(I.nnz() for I in insts)
+    m = sum(I.m1 + I.m2 for I in insts)
+    alg = {"setcover": (16 * nnz + 4 * (6 * n + 4 * m), "2 nnz (4+4) + 4 (6n + 4m)"),
+           "knapsack": (16 * n, "16 sum n_i (read x, w, c; write x)"),
+           "assign3d": (16 * nnz, "16 nnz"),
+           "facility": (16 * nnz + 24 * n + 16 * m, "2 nnz 8 + 24 n + 16 m")}[workload]
+    lanes_peak = 148 * 128 * 2.032e9 / 15.0      # Philox output lanes/s (15 INT32 ops/lane)
+    if dom == "pdhg":
+        ms, iters = phases["pdhg"]
+        ach = alg[0] * iters / (ms / 1e3) / 1e9
+        out.update({"kernel": "PDHG iteration (k_dual_rows / k_primal_cols / long-row chunks)",
+                    "bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs", 6400.0),
+                    "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6400.0), "traffic": None,
+                    "algorithmic_per_iteration": f"{alg[1]} = {alg[0]:.4e} B",
+                    "us_per_iteration": ms / iters * 1e3})
+    elif dom in ("fused", "sample"):
+        ms, cnt = phases[dom]
+        lanes = float(k_b) * n * steps
+        ach = lanes / (ms / 1e3)
+        out.update({"kernel": "Philox Bernoulli sampling" + (" + fused evaluation"
+                                                            if dom == "fused" else ""),
+                    "bound": "alu", "achieved": ach / 1e12, "peak": lanes_peak / 1e12,
+                    "unit": "T Philox lanes/s", "frac": ach / lanes_peak, "traffic": None,
+                    "algorithmic_per_step": f"k_b x sum n_i = {float(k_b) * n:.4e} lanes"})
+    else:
+        out.update({"kernel": dom, "bound": None, "achieved": None, "peak": None,
+                    "unit": None, "frac": None, "traffic": None})
     return out
 
 
 # ------------------------------------------------------------------ CPU oracle
+class OracleStep:
+    """The FP64 oracle as it stands, single thread, on a bounded sample of
+    the workload: Preprocess once, then per step some PDHG iterations and
+    some candidates of the first instance, extrapolated to one full step
+    (k_int iterations + k_b candidates of every instance, scaled by the
+    instances' total size for a batch)."""
+
+    def __init__(self, workload):
+        from oracle import oracle as O
+        self.O = O
+        build, self.k_int, self.k_b, self.desc = WORKLOADS[workload]
+        insts = build(0)
+        insts = insts if isinstance(insts, list) else [insts]
+        self.inst = insts[0]
+        self.scale = sum(I.n for I in insts) / self.inst.n
+        self.ninst = len(insts)
+        self.P = O.Params(k_int=self.k_int, k_b=self.k_b, seed=0x5EED0000 + 1, x0=-1.0)
+        t0 = time.perf_counter()
+        self.sol = O.OracleSolver(self.inst, self.P)
+        self.t_pre = time.perf_counter() - t0
+        self.ev = O.Evaluator(self.inst)
+        self.round = 0
+
+    def step(self, budget_s):
+        """One bounded sample; returns seconds of one full step."""
+        it, t0 = 0, time.perf_counter()
+        while it < 1 or (it < self.k_int and time.perf_counter() - t0 < 0.5 * budget_s):
+            self.sol.step()
+            it += 1
+        t_iter = (time.perf_counter() - t0) / it
+        p32 = self.sol.x.astype(np.float32)
+        ns, t0 = 0, time.perf_counter()
+        while ns < 8 or (ns < self.k_b and time.perf_counter() - t0 < 0.5 * budget_s):
+            X = self.O.sample(self.inst, p32, 8, self.P.seed, 0, self.round)
+            self.ev(X)
+            ns += 8
+        self.round += 1
+        t_cand = (time.perf_counter() - t0) / ns
+        self.last = (it, ns, t_iter, t_cand)
+        return self.scale * (self.k_int * t_iter + self.k_b * t_cand)
+
+    def sample_text(self):
+        it, ns, _, _ = self.last
+        txt = (f"{it} PDHG iterations + {ns} candidates of instance 0 per step, extrapolated "
+               f"to {self.k_int} iterations + {self.k_b} candidates")
+        if self.ninst > 1:
+            txt += f" of each of {self.ninst} instances (scaled by total size)"
+        return txt
+
+
 def cpu_baseline(workload, budget_s=20.0):
-    """The FP64 oracle as it stands, single thread, on a bounded sample of the
-    same workload; scaled to candidates/s of a full step."""
-    from oracle import oracle as O
-    build, k_int, k_b, desc = WORKLOADS[workload]
-    inst = build(0)
-    inst = inst[0] if isinstance(inst, list) else inst
-    P = O.Params(k_int=k_int, k_b=k_b, seed=0x5EED0000 + 1, x0=-1.0)
-    t0 = time.perf_counter()
-    sol = O.OracleSolver(inst, P)
-    t_pre = time.perf_counter() - t0
-    it = 0
-    t0 = time.perf_counter()
-    while it < k_int and (time.perf_counter() - t0) < budget_s * 0.4:
-        sol.step()
-        it += 1
-    t_iter = (time.perf_counter() - t0) / it
-    ns = 0
-    t0 = time.perf_counter()
-    p32 = sol.x.astype(np.float32)
-    while (time.perf_counter() - t0) < budget_s * 0.4:
-        X = O.sample(inst, p32, 8, P.seed, 0, 0)
-        O.Evaluator(inst)(X)
-        ns += 8
-        if ns >= k_b:
-            break
-    t_cand = (time.perf_counter() - t0) / ns
-    t_step = k_int * t_iter + k_b * t_cand
-    return {"value": k_b / t_step, "unit": "candidates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{it} PDHG iterations + {ns} candidates of the same workload, "
-                      f"extrapolated to {k_int} iterations + {k_b} candidates per step",
-            "s_per_iter": t_iter, "s_per_candidate": t_cand, "preprocess_s": t_pre}
+    ob = OracleStep(workload)
+    t_step = ob.step(budget_s)
+    it, ns, t_iter, t_cand = ob.last
+    return {"value": ob.k_b * ob.ninst / t_step, "unit": "candidates/s", "cores": 1,
+            "kind": "oracle", "sample": ob.sample_text(), "s_per_iter": t_iter,
+            "s_per_candidate": t_cand, "preprocess_s": ob.t_pre}
 
 
 def run_reference(args, rank, world):
+    """Reference arm: the oracle on the host cores, each step a bounded
+    sample; the whole run is sized to about two minutes."""
     if rank != 0:
         return
     t0 = time.perf_counter()
-    cb = None
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline(args.workload, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)))
-        vals.append(cb["value"])
-    v = statistics.median(vals[args.warmup:]) if len(vals) > args.warmup else vals[-1]
-    build, k_int, k_b, desc = WORKLOADS[args.workload]
+    ob = OracleStep(args.workload)
+    per_step = max(0.05, 120.0 / max(1, args.warmup + args.steps))
+    ts = []
+    for q in range(args.warmup + args.steps):
+        t = ob.step(per_step)
+        if q >= args.warmup:
+            ts.append(t)
+    t_step = statistics.median(ts) if ts else t
+    v = ob.k_b * ob.ninst / t_step
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "candidates/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": k_b / v * 1e3, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-           "config": {"workload": desc, "k_int": k_int, "k_b": k_b},
+           "config": {"workload": ob.desc, "k_int": ob.k_int, "k_b": ob.k_b,
+                      "instances": ob.ninst},
            "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": 1, "kind": "oracle",
-                            "sample": cb["sample"]},
+                            "sample": ob.sample_text()},
            "e2e": {"value": v, "unit": "candidates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0},
-           "wall_s": time.perf_counter() - t0}
+           "preprocess_s": ob.t_pre, "wall_s": time.perf_counter() - t0}
     print(json.dumps(out), flush=True)
 
 

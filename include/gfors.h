@@ -324,6 +324,43 @@ GFORS_API gfors_status gfors_fused_eval_noalloc(const float* p_dev, const int32_
                                                 int32_t nsamples, int32_t* viol_dev,
                                                 int64_t* obj_dev, void* cuda_stream);
 
+/* ---- Autotuner of the batched PDHG path (the batching pattern of the
+ * method's implementation; the paper itself prescribes no tuning).
+ * Rows (dual step, Alg. 2 line for y) and columns (primal step) are processed
+ * in five length buckets -- lengths <= 2, <= 8, <= 32, <= 128, <= 2048;
+ * longer ones are split into fixed chunks -- with `lanes` threads per row /
+ * column.  lanes[10] = rows' five buckets then columns' five, each 1, 2, 4,
+ * 8, 16 or 32.  A lane count changes only the FP32 summation order inside a
+ * row / column (results stay within the per-step tolerance of the FP64
+ * reference; a fixed choice is deterministic).
+ *
+ * gfors_autotune times every candidate lane count of every non-empty bucket
+ * on the device (scratch outputs: the solver state is untouched) and keeps
+ * the fastest.  cache_path (may be NULL) names a JSON file keyed by
+ * gfors_tune_key: on a hit the stored choice is applied without timing
+ * (*hit = 1), else the timed choice is stored (file created if absent).
+ * out_lanes (may be NULL) receives the choice.  Synchronises; drops captured
+ * CUDA graphs of the iteration.  Errors: GFORS_E_ARG (cache not writable),
+ * GFORS_E_CUDA. */
+GFORS_API gfors_status gfors_autotune(gfors_handle h, const char* cache_path,
+                                      int32_t out_lanes[10], int32_t* hit);
+/* Apply an explicit choice (GFORS_E_ARG if a value is not a lane count) /
+ * read the current one. */
+GFORS_API gfors_status gfors_set_lanes(gfors_handle h, const int32_t lanes[10]);
+GFORS_API gfors_status gfors_get_lanes(gfors_handle h, int32_t lanes[10]);
+/* Cache key of this handle: device name, then log2 classes of the total
+ * variables, rows and nonzeros and of every bucket's row / column count.
+ * GFORS_E_ARG if len is too small. */
+GFORS_API gfors_status gfors_tune_key(gfors_handle h, char* buf, size_t len);
+/* Host-only cache access (no device needed): look up key in the JSON file at
+ * path (*found = 0 when the file or key is absent), or insert / replace an
+ * entry (GFORS_E_ARG for invalid lanes, a key containing quotes, backslashes
+ * or control characters, or an unwritable path). */
+GFORS_API gfors_status gfors_tune_cache_lookup(const char* path, const char* key,
+                                               int32_t lanes[10], int32_t* found);
+GFORS_API gfors_status gfors_tune_cache_store(const char* path, const char* key,
+                                              const int32_t lanes[10]);
+
 /* Kernel-launch counter of this handle (device kernels enqueued so far). */
 GFORS_API int64_t gfors_launch_count(gfors_handle h);
 

@@ -187,9 +187,16 @@ static void host_advance(GfCtx* h, long long it) {
 
 cudaError_t gf_launch_persistent(GfCtx* h, int64_t nsteps);
 
+cudaError_t gf_single_init(GfCtx* h);
+
 static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
   cudaError_t e;
   int64_t done = 0;
+  if (h->single_ok && !h->sr_valid && nsteps > 0) {
+    // K xbar partials of the current state, read by the next dual step
+    if ((e = gf_single_init(h))) return e;
+    h->sr_valid = true;
+  }
   if (h->persist_ok && nsteps > 0) {
     // one cooperative launch runs all nsteps iterations
     // (at most 2^20 iterations per launch keeps the barrier counter in range)
@@ -523,6 +530,7 @@ extern "C" gfors_status gfors_get_iterate(gfors_handle h, int32_t inst, float* x
 extern "C" gfors_status gfors_set_iterate(gfors_handle h, int32_t inst, const float* x,
                                           const float* xbar, const float* y) {
   GF_ENTER(h);
+  h->sr_valid = false;                    // K xbar partials recomputed
   if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
   const GfInstHost& I = h->ih[inst];
   const int par = (int)(h->k_host & 1);
@@ -544,6 +552,7 @@ extern "C" gfors_status gfors_set_iterate(gfors_handle h, int32_t inst, const fl
 
 extern "C" gfors_status gfors_set_counters(gfors_handle h, int64_t k, double rho) {
   GF_ENTER(h);
+  h->sr_valid = false;                    // K xbar partials recomputed
   if (k < 0) return gf_fail(h, GFORS_E_ARG, "k < 0");
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e) return gf_cuda(h, e, "set_counters sync");
@@ -859,6 +868,7 @@ extern "C" gfors_status gfors_state_export(gfors_handle h, void* buf, size_t* le
 
 extern "C" gfors_status gfors_state_import(gfors_handle h, const void* buf, size_t len) {
   GF_ENTER(h);
+  h->sr_valid = false;                    // K xbar partials recomputed
   if (!buf) return gf_fail(h, GFORS_E_ARG, "buffer is NULL");
   const uint8_t* p = static_cast<const uint8_t*>(buf);
   size_t off = 0;

@@ -11,8 +11,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <numeric>
+#include <stdexcept>
+#include <thread>
 
 #include "internal.cuh"
 
@@ -137,9 +140,17 @@ extern "C" int64_t gfors_launch_count(gfors_handle h) { return h ? h->launches :
 // ---------------------------------------------------------------------------
 namespace {
 
-struct Row {                      // one merged row: sorted columns, summed values
+// Rows in flat CSR form: local columns ascending, no duplicates, no zeros.
+struct RowSet {
+  std::vector<int64_t> ptr{0};
   std::vector<int32_t> col;
   std::vector<double> val;
+  size_t size() const { return ptr.size() - 1; }
+  int64_t len(size_t j) const { return ptr[j + 1] - ptr[j]; }
+  const int32_t* c(size_t j) const { return col.data() + ptr[j]; }
+  const double* v(size_t j) const { return val.data() + ptr[j]; }
+  void add(int32_t cc, double vv) { col.push_back(cc); val.push_back(vv); }
+  void close() { ptr.push_back((int64_t)col.size()); }
 };
 
 bool check_csr(const gfors_csr* M, int64_t ncols, std::string& why) {
@@ -161,23 +172,32 @@ bool check_csr(const gfors_csr* M, int64_t ncols, std::string& why) {
   return true;
 }
 
-Row merged_row(const gfors_csr* M, int64_t r, double sign) {
-  std::vector<std::pair<int32_t, double>> e;
-  for (int64_t t = M->row_ptr[r]; t < M->row_ptr[r + 1]; ++t)
-    e.emplace_back(M->col_idx[t], sign * M->val[t]);
-  std::sort(e.begin(), e.end(),
-            [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
-              return a.first < b.first;
-            });
-  Row out;
-  for (size_t q = 0; q < e.size();) {
-    size_t u = q;
-    double s = 0.0;
-    while (u < e.size() && e[u].first == e[q].first) s += e[u++].second;
-    if (s != 0.0) { out.col.push_back(e[q].first); out.val.push_back(s); }
-    q = u;
+// Row r of M appended to R with duplicate columns summed (in input order),
+// columns ascending and zero sums dropped.
+void append_merged(RowSet& R, const gfors_csr* M, int64_t r,
+                   std::vector<std::pair<int32_t, double>>& e) {
+  const int64_t t0 = M->row_ptr[r], t1 = M->row_ptr[r + 1];
+  bool sorted = true;
+  for (int64_t t = t0 + 1; t < t1 && sorted; ++t) sorted = M->col_idx[t] > M->col_idx[t - 1];
+  if (sorted) {
+    for (int64_t t = t0; t < t1; ++t)
+      if (M->val[t] != 0.0) R.add(M->col_idx[t], M->val[t]);
+  } else {
+    e.clear();
+    for (int64_t t = t0; t < t1; ++t) e.emplace_back(M->col_idx[t], M->val[t]);
+    std::stable_sort(e.begin(), e.end(),
+                     [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+                       return x.first < y.first;
+                     });
+    for (size_t q = 0; q < e.size();) {
+      size_t u = q;
+      double sum = 0.0;
+      while (u < e.size() && e[u].first == e[q].first) sum += e[u++].second;
+      if (sum != 0.0) R.add(e[q].first, sum);
+      q = u;
+    }
   }
-  return out;
+  R.close();
 }
 
 bool is_int31(double v) { return std::floor(v) == v && std::fabs(v) < 2147483648.0; }
@@ -191,17 +211,280 @@ long long ceil_div(long long a, long long b) { return -floor_div(-a, b); }
 
 // Host-side staging of one instance before concatenation.
 struct Stage {
-  std::vector<Row> K;             // rows of -[A;B], row-normalised later
-  std::vector<double> r;
+  RowSet orig;                    // A rows then B rows, original values (merged)
+  std::vector<double> r;          // (b; d), divided by the row norms
   std::vector<uint8_t> eq;
-  std::vector<double> rownorm;
-  // eval (original integer rows)
-  std::vector<Row> orig;          // A rows then B rows (original signs)
-  std::vector<long long> rhs;
-  // Q symmetric (sparse, FP64) and original (sparse, int)
-  std::vector<Row> Qsym;          // per variable (local columns)
-  std::vector<Row> Qorig;
+  std::vector<double> rownorm;    // rows of K = -orig / rownorm
+  std::vector<long long> rhs;     // integer right-hand sides (evaluation)
+  RowSet Qsym;                    // (Q + Q^T)/2 per variable (sparse Q)
+  RowSet Qorig;                   // original Q rows (sparse Q)
+  bool dense = false;             // dense small-integer Q (tensor-core path)
+  GfDenseQ dq;
+  std::vector<double> dense_diag;
+  std::vector<__nv_bfloat16> dense_w2;
+  // evaluation rows of this instance (local offsets into ucols / gcols)
+  std::vector<GfURow> ur;
+  std::vector<int32_t> ucols;
+  std::vector<GfPRow> pr;
+  std::vector<GfGRow> gr;
+  std::vector<int32_t> gcols, gvals;
+  gfors_status status = GFORS_OK;
+  std::string err;
 };
+
+// Run f(q) for q in [0, count) on up to hardware_concurrency threads; an
+// exception in f(q) is returned as text (first failing q).
+template <class F>
+std::string parallel_for(int count, F&& f) {
+  const int nt = std::min<int>(count, std::max(1u, std::thread::hardware_concurrency()));
+  std::vector<std::string> errs(count);
+  auto run = [&](int q) {
+    try {
+      f(q);
+    } catch (const std::exception& ex) {
+      errs[q] = ex.what();
+    } catch (...) {
+      errs[q] = "unknown exception";
+    }
+  };
+  if (nt <= 1) {
+    for (int q = 0; q < count; ++q) run(q);
+  } else {
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back([&]() {
+        for (int q; (q = next.fetch_add(1)) < count;) run(q);
+      });
+    for (auto& x : th) x.join();
+  }
+  for (int q = 0; q < count; ++q)
+    if (!errs[q].empty()) return "instance " + std::to_string(q) + ": " + errs[q];
+  return std::string();
+}
+
+// Preprocess step 1 and the Q classification of one instance (host, FP64).
+void stage_instance(int q, GfInstHost& I, Stage& S, const gfors_params& P,
+                    const gfors_csr* Aq, const double* bq, const gfors_csr* Bq,
+                    const double* dq_rhs, const gfors_qmat* Qq, const double* cq) {
+  auto fail = [&](const std::string& why) {
+    S.status = GFORS_E_ARG;
+    S.err = "instance " + std::to_string(q) + ": " + why;
+  };
+  std::string why;
+  if (!check_csr(Aq, I.n, why) || !check_csr(Bq, I.n, why)) return fail(why);
+  bool integral = true;
+  for (int64_t i = 0; i < I.n; ++i) {
+    if (!std::isfinite(cq[i])) return fail("c not finite");
+    integral &= is_int31(cq[i]);
+  }
+  // rows of K = -[A;B] (Eq. 2) and the original rows for evaluation
+  std::vector<std::pair<int32_t, double>> scratch;
+  const int64_t nnz0 = (Aq ? Aq->nnz : 0) + (Bq ? Bq->nnz : 0);
+  S.orig.ptr.reserve(I.m1 + I.m2 + 1);
+  S.orig.col.reserve(nnz0);
+  S.orig.val.reserve(nnz0);
+  for (int part = 0; part < 2; ++part) {
+    const gfors_csr* M = part ? Bq : Aq;
+    const double* rhs = part ? dq_rhs : bq;
+    if (!M) continue;
+    for (int64_t r = 0; r < M->rows; ++r) {
+      if (!std::isfinite(rhs[r])) return fail("rhs not finite");
+      append_merged(S.orig, M, r, scratch);
+      const size_t j = S.orig.size() - 1;
+      for (int64_t u = 0; u < S.orig.len(j); ++u) integral &= is_int31(S.orig.v(j)[u]);
+      integral &= is_int31(rhs[r]);
+      S.r.push_back(rhs[r]);
+      S.eq.push_back((uint8_t)part);
+      S.rhs.push_back(is_int31(rhs[r]) ? (long long)rhs[r] : 0);
+    }
+  }
+  // Preprocess step 1: row 2-norms
+  S.rownorm.resize(S.orig.size());
+  for (size_t j = 0; j < S.orig.size(); ++j) {
+    double sq = 0.0;
+    for (int64_t u = 0; u < S.orig.len(j); ++u) sq += S.orig.v(j)[u] * S.orig.v(j)[u];
+    sq = sqrt(sq);
+    S.rownorm[j] = sq;
+    if (sq > 0.0) {
+      S.r[j] /= sq;
+    } else if ((!S.eq[j] && S.r[j] > 0.0) || (S.eq[j] && S.r[j] != 0.0)) {
+      return fail("empty row " + std::to_string(j) + " cannot be satisfied");
+    }
+  }
+  // Q
+  I.qkind = 0;
+  if (Qq && Qq->kind == 1) {
+    if (!Qq->dense_rowmajor) return fail("dense Q pointer is NULL");
+    const double* Qd = Qq->dense_rowmajor;
+    bool qint = true;
+    long long w2max = 0;
+    for (int64_t i = 0; i < I.n && qint; ++i)
+      for (int64_t j = 0; j < I.n; ++j) {
+        const double v = Qd[i * I.n + j];
+        if (!std::isfinite(v)) return fail("Q not finite");
+        if (!is_int31(v)) { qint = false; break; }
+        if (i != j) {
+          double w = v + Qd[j * I.n + i];
+          if (std::fabs(w) > (double)w2max) w2max = (long long)std::fabs(w);
+        }
+      }
+    const bool tc = qint && integral && I.m1 + I.m2 == 0 && w2max <= 256 &&
+                    (double)I.n * (double)w2max < 16777216.0 && P.eval_mode != 1 &&
+                    P.eval_mode != 2;
+    if (tc) {
+      I.qkind = 1;
+      GfDenseQ& dq = S.dq;
+      dq.inst = q;
+      dq.n = I.n;
+      dq.ld = gf_round_up(I.n, 64);
+      dq.w2max = w2max;
+      {
+        // tensor-core scoring keeps every per-tile partial in int32:
+        // 128 rows x (n max|W2| + 2 max|c_i + Q_ii|) < 2^31
+        double maxlin = 0.0;
+        for (int64_t i = 0; i < I.n; ++i)
+          maxlin = std::max(maxlin, std::fabs(cq[i] + Qd[i * I.n + i]));
+        dq.tc_ok = 128.0 * ((double)I.n * (double)w2max + 2.0 * maxlin) < 2147483648.0;
+      }
+      S.dense_w2.assign((size_t)I.n * dq.ld, __float2bfloat16(0.0f));
+      S.dense_diag.resize(I.n);
+      for (int64_t i = 0; i < I.n; ++i) {
+        for (int64_t j = 0; j < I.n; ++j)
+          if (i != j)
+            S.dense_w2[(size_t)i * dq.ld + j] =
+                __float2bfloat16((float)(Qd[i * I.n + j] + Qd[j * I.n + i]));
+        S.dense_diag[i] = Qd[i * I.n + i];
+      }
+      S.dense = true;
+    } else {
+      I.qkind = 2;
+      for (int64_t i = 0; i < I.n; ++i) {
+        for (int64_t j = 0; j < I.n; ++j) {
+          const double v = Qd[i * I.n + j];
+          if (v != 0.0) S.Qorig.add((int32_t)j, v);
+          const double sv = 0.5 * (v + Qd[j * I.n + i]);
+          if (sv != 0.0) S.Qsym.add((int32_t)j, sv);
+          integral &= is_int31(v);
+        }
+        S.Qorig.close();
+        S.Qsym.close();
+      }
+    }
+  } else if (Qq && Qq->kind == 2) {
+    if (!check_csr(&Qq->sparse, I.n, why) || Qq->sparse.rows != I.n) return fail("Q: " + why);
+    I.qkind = 2;
+    std::vector<std::vector<std::pair<int32_t, double>>> sym(I.n);
+    for (int64_t i = 0; i < I.n; ++i) {
+      append_merged(S.Qorig, &Qq->sparse, i, scratch);
+      for (int64_t t = 0; t < S.Qorig.len(i); ++t) {
+        const int32_t j = S.Qorig.c(i)[t];
+        const double v = S.Qorig.v(i)[t];
+        integral &= is_int31(v);
+        sym[i].emplace_back(j, 0.5 * v);
+        sym[j].emplace_back((int32_t)i, 0.5 * v);
+      }
+    }
+    bool any = false;
+    for (int64_t i = 0; i < I.n; ++i) {
+      auto& e = sym[i];
+      std::stable_sort(e.begin(), e.end(),
+                       [](const std::pair<int32_t, double>& x,
+                          const std::pair<int32_t, double>& y) { return x.first < y.first; });
+      for (size_t u = 0; u < e.size();) {
+        size_t w = u;
+        double sum = 0.0;
+        while (w < e.size() && e[w].first == e[u].first) sum += e[w++].second;
+        if (sum != 0.0) { S.Qsym.add(e[u].first, sum); any = true; }
+        u = w;
+      }
+      S.Qsym.close();
+    }
+    if (!any) I.qkind = 0;
+  } else if (Qq && Qq->kind != 0) {
+    return fail("Q.kind must be 0, 1 or 2");
+  }
+  I.integral = integral;
+  I.cap = (P.tau_cap_by_L < 0) ? (I.qkind != 0) : (P.tau_cap_by_L != 0);
+  I.single_row = (I.m1 == 1 && I.m2 == 0 && I.qkind == 0);
+}
+
+// Integer evaluation rows of one instance (original data): P rows (<= 2
+// nonzeros, truth table), U rows (equal coefficients: a count bound), G rows.
+void stage_eval_rows(int q, const GfInstHost& I, Stage& S) {
+  for (size_t j = 0; j < S.orig.size(); ++j) {
+    const int32_t* oc = S.orig.c(j);
+    const double* ov = S.orig.v(j);
+    const long long rhs = S.rhs[j];
+    const bool eq = S.eq[j] != 0;
+    const int len = (int)S.orig.len(j);
+    if (len <= 2) {
+      GfPRow R;
+      R.inst = q;
+      R.v1 = len >= 1 ? (int32_t)(I.var_off + oc[0]) : 0;
+      R.v2 = len >= 2 ? (int32_t)(I.var_off + oc[1]) : -1;
+      R.table = 0;
+      for (int m = 0; m < 4; ++m) {
+        const int x1 = m & 1, x2 = (m >> 1) & 1;
+        if (len < 1 && x1) continue;
+        if (len < 2 && x2) continue;
+        long long sum = (len >= 1 ? (long long)ov[0] * x1 : 0) +
+                        (len >= 2 ? (long long)ov[1] * x2 : 0);
+        const bool bad = eq ? (sum != rhs) : (sum < rhs);
+        if (bad) R.table |= 1u << m;
+      }
+      if (len == 0) R.v1 = (int32_t)I.var_off;      // read any word; table uses x1=0
+      if (len == 0 && R.table) R.table = 0xFu;      // constant violated row
+      if (R.table) S.pr.push_back(R);
+      continue;
+    }
+    bool uni = len < 65536;
+    for (int t = 1; t < len && uni; ++t) uni = (ov[t] == ov[0]);
+    bool placed = false;
+    if (uni) {
+      const long long a = (long long)ov[0];
+      long long L = 0, U = -1;
+      bool ok = true;
+      if (!eq) {
+        if (a > 0) { L = std::max(0ll, ceil_div(rhs, a)); U = -1; }
+        else { U = floor_div(rhs, a); L = 0; if (U < 0) ok = false; }
+        if (L > len) ok = false;
+      } else {
+        if (rhs % a != 0) ok = false;
+        else { L = U = rhs / a; if (L < 0 || L > len) ok = false; }
+      }
+      if (ok && U >= len) U = -1;
+      if (ok) {
+        if (L <= 0 && U < 0) { placed = true; }      // never violated
+        else if (L < 65536 && U < 65536) {
+          GfURow R;
+          R.inst = q;
+          R.len = len;
+          R.t0 = (int64_t)S.ucols.size();             // local; shifted on concatenation
+          R.L = (int32_t)L;
+          R.U = (int32_t)U;
+          for (int t = 0; t < len; ++t) S.ucols.push_back((int32_t)(I.var_off + oc[t]));
+          S.ur.push_back(R);
+          placed = true;
+        }
+      }
+    }
+    if (!placed) {
+      GfGRow R;
+      R.inst = q;
+      R.len = len;
+      R.t0 = (int64_t)S.gcols.size();                 // local; shifted on concatenation
+      R.rhs = rhs;
+      R.eq = eq;
+      R.pad = 0;
+      for (int t = 0; t < len; ++t) {
+        S.gcols.push_back((int32_t)(I.var_off + oc[t]));
+        S.gvals.push_back((int32_t)ov[t]);
+      }
+      S.gr.push_back(R);
+    }
+  }
+}
 
 }  // namespace
 
@@ -238,170 +521,40 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   h->ninst = ninst;
   h->ih.assign(ninst, GfInstHost());
   std::vector<Stage> st(ninst);
-  std::vector<std::vector<double>> dense_diag(ninst);
-  std::vector<std::vector<__nv_bfloat16>> dense_w2(ninst);
-  std::string why;
   int64_t voff = 0, roff = 0;
-  for (int q = 0; q < ninst; ++q) {
+  for (int q = 0; q < ninst; ++q) {          // sizes and offsets (serial)
     GfInstHost& I = h->ih[q];
-    Stage& S = st[q];
-    const gfors_csr* Aq = A ? A[q] : nullptr;
-    const gfors_csr* Bq = B ? B[q] : nullptr;
-    const gfors_qmat* Qq = Q ? Q[q] : nullptr;
     if (!n || n[q] <= 0) return gf_fail(h, GFORS_E_ARG, "n must be positive");
     if (n[q] >= (1ll << 30)) return gf_fail(h, GFORS_E_UNSUPPORTED, "n >= 2^30");
+    if (!c || !c[q]) return gf_fail(h, GFORS_E_ARG, "c is NULL");
+    const gfors_csr* Aq = A ? A[q] : nullptr;
+    const gfors_csr* Bq = B ? B[q] : nullptr;
     I.n = n[q];
     I.npad = gf_round_up(I.n, 64);
-    if (!c || !c[q]) return gf_fail(h, GFORS_E_ARG, "c is NULL");
-    if (!check_csr(Aq, I.n, why) || !check_csr(Bq, I.n, why))
-      return gf_fail(h, GFORS_E_ARG, "instance " + std::to_string(q) + ": " + why);
-    I.m1 = Aq ? Aq->rows : 0;
-    I.m2 = Bq ? Bq->rows : 0;
+    I.m1 = Aq ? std::max<int64_t>(0, Aq->rows) : 0;
+    I.m2 = Bq ? std::max<int64_t>(0, Bq->rows) : 0;
     if (I.m1 && (!b || !b[q])) return gf_fail(h, GFORS_E_ARG, "b is NULL");
     if (I.m2 && (!d || !d[q])) return gf_fail(h, GFORS_E_ARG, "d is NULL");
     I.var_off = voff;
     I.row_off = roff;
     voff += I.npad;
     roff += I.m1 + I.m2;
-    bool integral = true;
-    for (int64_t i = 0; i < I.n; ++i) {
-      if (!std::isfinite(c[q][i])) return gf_fail(h, GFORS_E_ARG, "c not finite");
-      integral &= is_int31(c[q][i]);
+  }
+  {
+    const std::string ex = parallel_for(ninst, [&](int q) {
+      stage_instance(q, h->ih[q], st[q], P, A ? A[q] : nullptr, b ? b[q] : nullptr,
+                     B ? B[q] : nullptr, d ? d[q] : nullptr, Q ? Q[q] : nullptr, c[q]);
+    });
+    if (!ex.empty()) return gf_fail(h, GFORS_E_OOM, "staging: " + ex);
+  }
+  for (int q = 0; q < ninst; ++q) {
+    if (st[q].status != GFORS_OK) return gf_fail(h, st[q].status, st[q].err);
+    GfInstHost& I = h->ih[q];
+    if (st[q].dense) {
+      I.dense_idx = (int)h->dense.size();
+      h->dense.push_back(st[q].dq);
     }
-    // rows of K = -[A;B] (Eq. 2) and the original rows for evaluation
-    for (int part = 0; part < 2; ++part) {
-      const gfors_csr* M = part ? Bq : Aq;
-      const double* rhs = part ? (d ? d[q] : nullptr) : (b ? b[q] : nullptr);
-      if (!M) continue;
-      for (int64_t r = 0; r < M->rows; ++r) {
-        if (!std::isfinite(rhs[r])) return gf_fail(h, GFORS_E_ARG, "rhs not finite");
-        Row o = merged_row(M, r, 1.0);
-        Row k = o;
-        for (double& v : k.val) v = -v;
-        for (double v : o.val) integral &= is_int31(v);
-        integral &= is_int31(rhs[r]);
-        S.K.push_back(std::move(k));
-        S.r.push_back(rhs[r]);
-        S.eq.push_back((uint8_t)part);
-        S.orig.push_back(std::move(o));
-        S.rhs.push_back(is_int31(rhs[r]) ? (long long)rhs[r] : 0);
-      }
-    }
-    // Preprocess step 1: row 2-norms
-    S.rownorm.resize(S.K.size());
-    for (size_t j = 0; j < S.K.size(); ++j) {
-      double s = 0.0;
-      for (double v : S.K[j].val) s += v * v;
-      s = sqrt(s);
-      S.rownorm[j] = s;
-      if (s > 0.0) {
-        for (double& v : S.K[j].val) v /= s;
-        S.r[j] /= s;
-      } else if ((!S.eq[j] && S.r[j] > 0.0) || (S.eq[j] && S.r[j] != 0.0)) {
-        return gf_fail(h, GFORS_E_ARG, "instance " + std::to_string(q) + ": empty row " +
-                                           std::to_string(j) + " cannot be satisfied");
-      }
-    }
-    // Q
-    I.qkind = 0;
-    if (Qq && Qq->kind == 1) {
-      if (!Qq->dense_rowmajor) return gf_fail(h, GFORS_E_ARG, "dense Q pointer is NULL");
-      const double* Qd = Qq->dense_rowmajor;
-      bool qint = true;
-      long long w2max = 0;
-      for (int64_t i = 0; i < I.n && qint; ++i)
-        for (int64_t j = 0; j < I.n; ++j) {
-          const double v = Qd[i * I.n + j];
-          if (!std::isfinite(v)) return gf_fail(h, GFORS_E_ARG, "Q not finite");
-          if (!is_int31(v)) { qint = false; break; }
-          if (i != j) {
-            double w = v + Qd[j * I.n + i];
-            if (std::fabs(w) > (double)w2max) w2max = (long long)std::fabs(w);
-          }
-        }
-      const bool tc = qint && integral && I.m1 + I.m2 == 0 && w2max <= 256 &&
-                      (double)I.n * (double)w2max < 16777216.0 && P.eval_mode != 1 &&
-                      P.eval_mode != 2;
-      if (tc) {
-        I.qkind = 1;
-        GfDenseQ dq;
-        dq.inst = q;
-        dq.n = I.n;
-        dq.ld = gf_round_up(I.n, 64);
-        dq.w2max = w2max;
-        {
-          // tensor-core scoring keeps every per-tile partial in int32:
-          // 128 rows x (n max|W2| + 2 max|c_i + Q_ii|) < 2^31
-          double maxlin = 0.0;
-          for (int64_t i = 0; i < I.n; ++i)
-            maxlin = std::max(maxlin, std::fabs(c[q][i] + Qd[i * I.n + i]));
-          dq.tc_ok = 128.0 * ((double)I.n * (double)w2max + 2.0 * maxlin) < 2147483648.0;
-        }
-        dense_w2[q].assign((size_t)I.n * dq.ld, __float2bfloat16(0.0f));
-        dense_diag[q].resize(I.n);
-        for (int64_t i = 0; i < I.n; ++i) {
-          for (int64_t j = 0; j < I.n; ++j)
-            if (i != j)
-              dense_w2[q][(size_t)i * dq.ld + j] =
-                  __float2bfloat16((float)(Qd[i * I.n + j] + Qd[j * I.n + i]));
-          dense_diag[q][i] = Qd[i * I.n + i];
-        }
-        I.dense_idx = (int)h->dense.size();
-        h->dense.push_back(dq);
-      } else {
-        I.qkind = 2;
-        S.Qsym.resize(I.n);
-        S.Qorig.resize(I.n);
-        for (int64_t i = 0; i < I.n; ++i)
-          for (int64_t j = 0; j < I.n; ++j) {
-            const double v = Qd[i * I.n + j];
-            if (v != 0.0) { S.Qorig[i].col.push_back((int32_t)j); S.Qorig[i].val.push_back(v); }
-            const double s = 0.5 * (v + Qd[j * I.n + i]);
-            if (s != 0.0) { S.Qsym[i].col.push_back((int32_t)j); S.Qsym[i].val.push_back(s); }
-            integral &= is_int31(v);
-          }
-      }
-    } else if (Qq && Qq->kind == 2) {
-      if (!check_csr(&Qq->sparse, I.n, why) || Qq->sparse.rows != I.n)
-        return gf_fail(h, GFORS_E_ARG, "Q: " + why);
-      I.qkind = 2;
-      S.Qorig.resize(I.n);
-      std::vector<std::vector<std::pair<int32_t, double>>> sym(I.n);
-      for (int64_t i = 0; i < I.n; ++i) {
-        S.Qorig[i] = merged_row(&Qq->sparse, i, 1.0);
-        for (size_t t = 0; t < S.Qorig[i].col.size(); ++t) {
-          const int32_t j = S.Qorig[i].col[t];
-          const double v = S.Qorig[i].val[t];
-          integral &= is_int31(v);
-          sym[i].emplace_back(j, 0.5 * v);
-          sym[j].emplace_back((int32_t)i, 0.5 * v);
-        }
-      }
-      S.Qsym.resize(I.n);
-      for (int64_t i = 0; i < I.n; ++i) {
-        auto& e = sym[i];
-        std::sort(e.begin(), e.end(),
-                  [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
-                    return x.first < y.first;
-                  });
-        for (size_t u = 0; u < e.size();) {
-          size_t w = u;
-          double s = 0.0;
-          while (w < e.size() && e[w].first == e[u].first) s += e[w++].second;
-          if (s != 0.0) { S.Qsym[i].col.push_back(e[u].first); S.Qsym[i].val.push_back(s); }
-          u = w;
-        }
-      }
-      bool any = false;
-      for (auto& rw : S.Qsym) any |= !rw.col.empty();
-      if (!any) I.qkind = 0;
-    } else if (Qq && Qq->kind != 0) {
-      return gf_fail(h, GFORS_E_ARG, "Q.kind must be 0, 1 or 2");
-    }
-    I.integral = integral;
-    I.cap = (P.tau_cap_by_L < 0) ? (I.qkind != 0) : (P.tau_cap_by_L != 0);
-    I.single_row = (I.m1 == 1 && I.m2 == 0 && I.qkind == 0);
-    h->all_integral &= integral;
+    h->all_integral &= I.integral;
   }
   h->N = voff;
   h->M = roff;
@@ -415,9 +568,9 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   std::vector<uint8_t> row_eq(M);
   for (int q = 0; q < ninst; ++q) {
     const GfInstHost& I = h->ih[q];
-    for (size_t j = 0; j < st[q].K.size(); ++j) {
+    for (size_t j = 0; j < st[q].orig.size(); ++j) {
       const int64_t gj = I.row_off + (int64_t)j;
-      Kp[gj + 1] = (int64_t)st[q].K[j].col.size();
+      Kp[gj + 1] = st[q].orig.len(j);
       row_inst[gj] = q;
       rd[gj] = st[q].r[j];
       row_eq[gj] = st[q].eq[j];
@@ -428,29 +581,39 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   if (h->nnzK >= (1ll << 31)) return gf_fail(h, GFORS_E_UNSUPPORTED, "nnz(K) >= 2^31");
   Kc.resize(h->nnzK);
   Kd.resize(h->nnzK);
-  for (int q = 0; q < ninst; ++q) {
-    const GfInstHost& I = h->ih[q];
-    for (size_t j = 0; j < st[q].K.size(); ++j) {
-      int64_t t = Kp[I.row_off + (int64_t)j];
-      for (size_t u = 0; u < st[q].K[j].col.size(); ++u, ++t) {
-        Kc[t] = (int32_t)(I.var_off + st[q].K[j].col[u]);
-        Kd[t] = st[q].K[j].val[u];
-      }
-    }
-  }
   std::vector<int64_t> Tp(N + 1, 0);
-  for (int64_t t = 0; t < h->nnzK; ++t) Tp[Kc[t] + 1]++;
-  for (int64_t i = 0; i < N; ++i) Tp[i + 1] += Tp[i];
   std::vector<int32_t> Tr(h->nnzK);
   std::vector<double> Td(h->nnzK);
   {
-    std::vector<int64_t> fill(Tp.begin(), Tp.end() - 1);
-    for (int64_t j = 0; j < M; ++j)
-      for (int64_t t = Kp[j]; t < Kp[j + 1]; ++t) {
-        const int64_t pos = fill[Kc[t]]++;
-        Tr[pos] = (int32_t)j;
-        Td[pos] = Kd[t];
+    // per instance (disjoint row, column and nnz ranges): K rows with global
+    // columns and values -a / ||a||, column counts, then the transpose
+    std::string ex = parallel_for(ninst, [&](int q) {
+      const GfInstHost& I = h->ih[q];
+      const Stage& S = st[q];
+      for (size_t j = 0; j < S.orig.size(); ++j) {
+        int64_t t = Kp[I.row_off + (int64_t)j];
+        const double nr = S.rownorm[j];
+        for (int64_t u = 0; u < S.orig.len(j); ++u, ++t) {
+          Kc[t] = (int32_t)(I.var_off + S.orig.c(j)[u]);
+          const double k = -S.orig.v(j)[u];
+          Kd[t] = nr > 0.0 ? k / nr : k;
+          Tp[Kc[t] + 1]++;
+        }
       }
+    });
+    if (!ex.empty()) return gf_fail(h, GFORS_E_OOM, "K: " + ex);
+    for (int64_t i = 0; i < N; ++i) Tp[i + 1] += Tp[i];
+    ex = parallel_for(ninst, [&](int q) {
+      const GfInstHost& I = h->ih[q];
+      std::vector<int64_t> fill(Tp.begin() + I.var_off, Tp.begin() + I.var_off + I.npad);
+      for (int64_t j = I.row_off; j < I.row_off + I.m1 + I.m2; ++j)
+        for (int64_t t = Kp[j]; t < Kp[j + 1]; ++t) {
+          const int64_t pos = fill[Kc[t] - I.var_off]++;
+          Tr[pos] = (int32_t)j;
+          Td[pos] = Kd[t];
+        }
+    });
+    if (!ex.empty()) return gf_fail(h, GFORS_E_OOM, "K^T: " + ex);
   }
   // Q_sym (sparse instances), global indices
   std::vector<int64_t> Qp(N + 1, 0);
@@ -459,7 +622,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   for (int q = 0; q < ninst; ++q) {
     const GfInstHost& I = h->ih[q];
     if (I.qkind != 2) continue;
-    for (int64_t i = 0; i < I.n; ++i) Qp[I.var_off + i + 1] = (int64_t)st[q].Qsym[i].col.size();
+    for (int64_t i = 0; i < I.n; ++i) Qp[I.var_off + i + 1] = st[q].Qsym.len(i);
   }
   for (int64_t i = 0; i < N; ++i) Qp[i + 1] += Qp[i];
   h->nnzQ = Qp[N];
@@ -470,9 +633,9 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     if (I.qkind != 2) continue;
     for (int64_t i = 0; i < I.n; ++i) {
       int64_t t = Qp[I.var_off + i];
-      for (size_t u = 0; u < st[q].Qsym[i].col.size(); ++u, ++t) {
-        Qc[t] = (int32_t)(I.var_off + st[q].Qsym[i].col[u]);
-        Qd[t] = st[q].Qsym[i].val[u];
+      for (int64_t u = 0; u < st[q].Qsym.len(i); ++u, ++t) {
+        Qc[t] = (int32_t)(I.var_off + st[q].Qsym.c(i)[u]);
+        Qd[t] = st[q].Qsym.v(i)[u];
       }
     }
   }
@@ -571,18 +734,18 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     if (dq.w2max <= 127) {             // int8 copy for the PDHG GEMV (exact)
       ALLOC(dq.W2i8, int8_t, dq.n * dq.ld);
       std::vector<int8_t> w8((size_t)dq.n * dq.ld);
-      const std::vector<__nv_bfloat16>& wb = dense_w2[dq.inst];
+      const std::vector<__nv_bfloat16>& wb = st[dq.inst].dense_w2;
       for (size_t t = 0; t < w8.size(); ++t) w8[t] = (int8_t)__bfloat162float(wb[t]);
       UP(dq.W2i8, w8.data(), int8_t, w8.size());
     }
     ALLOC(dq.qdiag, float, dq.ld);
     ALLOC(dq.lin, long long, dq.ld);
     ALLOC(ddiag[u], double, dq.n);
-    UP(dq.W2, dense_w2[dq.inst].data(), __nv_bfloat16, dq.n * dq.ld);
-    UP(ddiag[u], dense_diag[dq.inst].data(), double, dq.n);
+    UP(dq.W2, st[dq.inst].dense_w2.data(), __nv_bfloat16, dq.n * dq.ld);
+    UP(ddiag[u], st[dq.inst].dense_diag.data(), double, dq.n);
     std::vector<long long> lin(dq.ld, 0);
     for (int64_t i = 0; i < dq.n; ++i)
-      lin[i] = (long long)c[dq.inst][i] + (long long)dense_diag[dq.inst][i];
+      lin[i] = (long long)c[dq.inst][i] + (long long)st[dq.inst].dense_diag[i];
     UP(dq.lin, lin.data(), long long, dq.ld);
   }
 
@@ -639,7 +802,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   for (GfDenseQ& dq : h->dense) {
     const GfInstHost& I = h->ih[dq.inst];
     std::vector<float> qd(dq.ld, 0.0f);
-    for (int64_t i = 0; i < dq.n; ++i) qd[i] = (float)(dense_diag[dq.inst][i] / I.s_obj);
+    for (int64_t i = 0; i < dq.n; ++i) qd[i] = (float)(st[dq.inst].dense_diag[i] / I.s_obj);
     UP(dq.qdiag, qd.data(), float, dq.ld);
     dq.qscale = (float)(0.5 / I.s_obj);
   }
@@ -741,6 +904,12 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
 
   // ---------------- evaluation structures (integer data)
   {
+    {
+      const std::string ex = parallel_for(ninst, [&](int q) {
+        if (h->ih[q].integral) stage_eval_rows(q, h->ih[q], st[q]);
+      });
+      if (!ex.empty()) return gf_fail(h, GFORS_E_OOM, "evaluation rows: " + ex);
+    }
     std::vector<GfURow> ur;
     std::vector<int32_t> ucols;
     std::vector<GfPRow> pr;
@@ -753,87 +922,29 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     for (int q = 0; q < ninst; ++q) {
       const GfInstHost& I = h->ih[q];
       if (!I.integral) continue;
-      const Stage& S = st[q];
-      for (size_t j = 0; j < S.orig.size(); ++j) {
-        const Row& o = S.orig[j];
-        const long long rhs = S.rhs[j];
-        const bool eq = S.eq[j] != 0;
-        const int len = (int)o.col.size();
-        if (len <= 2) {
-          GfPRow R;
-          R.inst = q;
-          R.v1 = len >= 1 ? (int32_t)(I.var_off + o.col[0]) : 0;
-          R.v2 = len >= 2 ? (int32_t)(I.var_off + o.col[1]) : -1;
-          R.table = 0;
-          for (int m = 0; m < 4; ++m) {
-            const int x1 = m & 1, x2 = (m >> 1) & 1;
-            if (len < 1 && x1) continue;
-            if (len < 2 && x2) continue;
-            long long sum = (len >= 1 ? (long long)o.val[0] * x1 : 0) +
-                            (len >= 2 ? (long long)o.val[1] * x2 : 0);
-            const bool bad = eq ? (sum != rhs) : (sum < rhs);
-            if (bad) R.table |= 1u << m;
-          }
-          if (len == 0) R.v1 = (int32_t)I.var_off;    // read any word; table uses x1=0
-          if (len == 0 && R.table) {                    // constant violated row
-            R.table = 0xFu;
-          }
-          if (R.table) pr.push_back(R);
-          continue;
-        }
-        bool uni = len < 65536;
-        for (int t = 1; t < len && uni; ++t) uni = (o.val[t] == o.val[0]);
-        bool placed = false;
-        if (uni) {
-          const long long a = (long long)o.val[0];
-          long long L = 0, U = -1;
-          bool ok = true;
-          if (!eq) {
-            if (a > 0) { L = std::max(0ll, ceil_div(rhs, a)); U = -1; }
-            else { U = floor_div(rhs, a); L = 0; if (U < 0) ok = false; }
-            if (L > len) ok = false;
-          } else {
-            if (rhs % a != 0) ok = false;
-            else { L = U = rhs / a; if (L < 0 || L > len) ok = false; }
-          }
-          if (ok && U >= len) U = -1;
-          if (ok) {
-            if (L <= 0 && U < 0) { placed = true; }      // never violated
-            else if (L < 65536 && U < 65536) {
-              GfURow R;
-              R.inst = q;
-              R.len = len;
-              R.t0 = (int64_t)ucols.size();
-              R.L = (int32_t)L;
-              R.U = (int32_t)U;
-              for (int32_t col : o.col) ucols.push_back((int32_t)(I.var_off + col));
-              ur.push_back(R);
-              placed = true;
-            }
-          }
-        }
-        if (!placed) {
-          GfGRow R;
-          R.inst = q;
-          R.len = len;
-          R.t0 = (int64_t)gcols.size();
-          R.rhs = rhs;
-          R.eq = eq;
-          R.pad = 0;
-          for (int t = 0; t < len; ++t) {
-            gcols.push_back((int32_t)(I.var_off + o.col[t]));
-            gvals.push_back((int32_t)o.val[t]);
-          }
-          gr.push_back(R);
-        }
+      Stage& S = st[q];
+      for (GfURow R : S.ur) {
+        R.t0 += (int64_t)ucols.size();
+        ur.push_back(R);
       }
+      ucols.insert(ucols.end(), S.ucols.begin(), S.ucols.end());
+      pr.insert(pr.end(), S.pr.begin(), S.pr.end());
+      for (GfGRow R : S.gr) {
+        R.t0 += (int64_t)gcols.size();
+        gr.push_back(R);
+      }
+      gcols.insert(gcols.end(), S.gcols.begin(), S.gcols.end());
+      gvals.insert(gvals.end(), S.gvals.begin(), S.gvals.end());
+      std::vector<int32_t>().swap(S.ucols);
+      std::vector<int32_t>().swap(S.gcols);
+      std::vector<int32_t>().swap(S.gvals);
       // dense tensor-core instances: the scorer adds c + diag(Q) itself
       if (I.qkind != 1)
         for (int64_t a = 0; a < I.n; a += 1024)
           oc.push_back(GfObjChunk{q, (int32_t)(I.var_off + a),
                                   (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 1024)), 0});
       if (I.qkind == 2) {
-        for (int64_t i = 0; i < I.n; ++i) QIp[I.var_off + i + 1] = (int64_t)S.Qorig[i].col.size();
+        for (int64_t i = 0; i < I.n; ++i) QIp[I.var_off + i + 1] = S.Qorig.len(i);
         for (int64_t a = 0; a < I.n; a += 64)
           qc.push_back(GfQChunk{q, (int32_t)(I.var_off + a),
                                 (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 64)), 0});
@@ -847,9 +958,9 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       if (!I.integral || I.qkind != 2) continue;
       for (int64_t i = 0; i < I.n; ++i) {
         int64_t t = QIp[I.var_off + i];
-        for (size_t u = 0; u < st[q].Qorig[i].col.size(); ++u, ++t) {
-          QIc[t] = (int32_t)(I.var_off + st[q].Qorig[i].col[u]);
-          QIv[t] = (int32_t)st[q].Qorig[i].val[u];
+        for (int64_t u = 0; u < st[q].Qorig.len(i); ++u, ++t) {
+          QIc[t] = (int32_t)(I.var_off + st[q].Qorig.c(i)[u]);
+          QIv[t] = (int32_t)st[q].Qorig.v(i)[u];
         }
       }
     }
@@ -892,7 +1003,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     if (ok) {
       for (int q = 0; q < ninst && ok; ++q) {
         long long s = 0;
-        for (double v : st[q].orig[0].val) s += (long long)std::fabs(v);
+        for (int64_t u = 0; u < st[q].orig.len(0); ++u) s += (long long)std::fabs(st[q].orig.v(0)[u]);
         worst = std::max(worst, s);
       }
     }
@@ -902,8 +1013,8 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       std::vector<long long> rhs(ninst);
       for (int q = 0; q < ninst; ++q) {
         const GfInstHost& I = h->ih[q];
-        const Row& o = st[q].orig[0];
-        for (size_t t = 0; t < o.col.size(); ++t) w[I.var_off + o.col[t]] = (int32_t)o.val[t];
+        const RowSet& o = st[q].orig;
+        for (int64_t t = 0; t < o.len(0); ++t) w[I.var_off + o.c(0)[t]] = (int32_t)o.v(0)[t];
         rhs[q] = st[q].rhs[0];
         for (int64_t a = 0; a < I.npad; a += 8192) {
           blk.push_back(q);
@@ -1003,7 +1114,9 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   gf_set_slot(h, 1, h->rho_host);     // iteration 1 reads slot 1
   {
     extern bool gf_persistent_setup(GfCtx * h);
+    extern bool gf_single_setup(GfCtx * h);
     h->persist_ok = (P.pdhg_mode != 1) && gf_persistent_setup(h);
+    h->single_ok = gf_single_setup(h);
   }
   GF_CK(h, cudaStreamSynchronize(s));
   h->h_best.assign(3 * ninst, INFINITY);

@@ -243,6 +243,16 @@ struct gfors_ctx {
   cudaGraphExec_t g_iter2[2] = {nullptr, nullptr};
   long long pair_launches = 0;
   bool use_graphs = true;
+  // single-row batches (one constraint row per instance, no Q): fused
+  // primal step + K xbar partials, then a per-instance dual step
+  bool single_ok = false;
+  bool sr_valid = false;            // partials of K xbar match the state
+  int32_t* sr_chunk = nullptr;      // (inst, v0, v1) per chunk of <= 2048 variables
+  int64_t sr_nchunk = 0;
+  int32_t* sr_ciptr = nullptr;      // ninst + 1 offsets into the chunks
+  int64_t* sr_row = nullptr;        // global row of each instance
+  float* sr_kv = nullptr;           // K entry of every variable (0 if none)
+  float2* sr_part = nullptr;        // [2][sr_nchunk] compensated partial sums
   // persistent cooperative PDHG launch (dense instance, matrix in smem)
   bool persist_ok = false;
   size_t persist_smem = 0;

@@ -7,63 +7,14 @@
 // whose step sizes come from the iteration's parameter slot.  UpdatePenalty
 // (Section 3) for the NEXT iteration is folded into block 0 of the first
 // primal kernel of each iteration (it writes the other parity slot).
+#include <functional>
+
 #include "internal.cuh"
+#include "penalty.cuh"
 
 namespace {
 
 using gf::CSum;
-
-// ---------------------------------------------------------------------------
-// UpdatePenalty for iteration k+1 (penalty counter advances once per k_int
-// iterations), then the per-instance step sizes (tau1 = sqrt(sigma), capped
-// at 1/(2L) with L = 2(||Q_hat|| + rho) when requested; tau2 = sigma/tau1).
-// Executed by all threads of one block; `next` is the slot to write.
-// ---------------------------------------------------------------------------
-__device__ void advance_penalty(GfDState* st, const GfSched* sc, const double* normQ,
-                                const int32_t* cap, const GfIParam* cur, GfIParam* next) {
-  // The parameters of iteration it+1 equal those of iteration it unless the
-  // penalty counter advances (once per k_int iterations): only then are rho
-  // and the step sizes recomputed (FP64), otherwise the slot is copied.
-  __shared__ double rho_s;
-  __shared__ int changed_s;
-  if (threadIdx.x == 0) {
-    long long it = st->k + 1;               // the iteration now running
-    int n_next = (int)(it / sc->k_int);     // counter used by iteration it+1
-    double rho = st->rho;
-    int changed = 0;
-    while (st->n_rho < n_next) {
-      st->n_rho += 1;
-      double rt = sc->rho_min * pow(1.0 + (double)st->n_rho / sc->T, sc->p);
-      double lo = rho + sc->delta;
-      double v = rt < lo ? lo : rt;
-      rho = v > sc->rho_max ? sc->rho_max : v;
-      changed = 1;
-    }
-    st->rho = rho;
-    st->k = it;
-    rho_s = rho;
-    changed_s = changed;
-  }
-  __syncthreads();
-  const double rho = rho_s;
-  const int changed = changed_s;
-  for (int b = threadIdx.x; b < sc->ninst; b += blockDim.x) {
-    if (!changed) {
-      next[b] = cur[b];
-      continue;
-    }
-    double t1 = sqrt(sc->sigma);
-    if (cap[b]) {
-      double L = 2.0 * (normQ[b] + rho);
-      if (L > 0.0 && 1.0 / (2.0 * L) < t1) t1 = 1.0 / (2.0 * L);
-    }
-    double t2 = sc->sigma / t1;
-    GfIParam q;
-    q.tau1 = (float)t1; q.tau2 = (float)t2; q.rho = (float)rho; q.pad = 0.f;
-    q.tau1d = t1; q.tau2d = t2; q.rhod = rho; q.normQ = normQ[b];
-    next[b] = q;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Dual step over a bucket of rows, `LANES` threads per row.
@@ -368,28 +319,54 @@ k_dense_primal_i8(const int8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t 
 }
 
 template <int L>
-cudaError_t launch_dual(GfCtx* h, const GfBucket& b, const GfIParam* ip) {
+cudaError_t launch_dual(GfCtx* h, const GfBucket& b, const GfIParam* ip, float* y) {
   int64_t threads = (int64_t)b.count * L;
   int blocks = (int)((threads + 255) / 256);
   k_dual_rows<L><<<blocks, 256, 0, h->stream>>>(b.ids, b.count, h->Kp, h->Kc, h->Kv,
                                                 h->xbar, h->rhat, h->row_eq, h->row_inst,
-                                                ip, h->y);
+                                                ip, y);
   h->launches++;
   return cudaGetLastError();
 }
 
 template <int L>
 cudaError_t launch_primal(GfCtx* h, const GfBucket& b, const GfIParam* ip,
-                          const float* xo, float* xn, int adv, GfIParam* ipn) {
+                          const float* xo, float* xn, float* xbar, float* dlast, int adv,
+                          GfIParam* ipn) {
   int64_t threads = (int64_t)b.count * L;
   int blocks = (int)((threads + 255) / 256);
   if (blocks < 1) blocks = 1;
   k_primal_cols<L><<<blocks, 256, 0, h->stream>>>(
       b.ids, b.count, h->Tp, h->Tr, h->Tv, h->nnzQ ? h->Qp : nullptr, h->Qc, h->Qv, h->y,
-      xo, h->chat, h->var_inst, ip, xn, h->xbar, h->dlast, adv, h->dstate, h->sched_d,
+      xo, h->chat, h->var_inst, ip, xn, xbar, dlast, adv, h->dstate, h->sched_d,
       h->normQhat_d, h->cap_d, ipn);
   h->launches++;
   return cudaGetLastError();
+}
+
+// Bucket kernels with `lanes` threads per row / column (1, 2, 4, 8, 16, 32).
+cudaError_t dual_bucket(GfCtx* h, const GfBucket& b, int lanes, const GfIParam* ip,
+                        float* y) {
+  switch (lanes) {
+    case 1: return launch_dual<1>(h, b, ip, y);
+    case 2: return launch_dual<2>(h, b, ip, y);
+    case 4: return launch_dual<4>(h, b, ip, y);
+    case 8: return launch_dual<8>(h, b, ip, y);
+    case 16: return launch_dual<16>(h, b, ip, y);
+    default: return launch_dual<32>(h, b, ip, y);
+  }
+}
+cudaError_t primal_bucket(GfCtx* h, const GfBucket& b, int lanes, const GfIParam* ip,
+                          const float* xo, float* xn, float* xbar, float* dlast, int adv,
+                          GfIParam* ipn) {
+  switch (lanes) {
+    case 1: return launch_primal<1>(h, b, ip, xo, xn, xbar, dlast, adv, ipn);
+    case 2: return launch_primal<2>(h, b, ip, xo, xn, xbar, dlast, adv, ipn);
+    case 4: return launch_primal<4>(h, b, ip, xo, xn, xbar, dlast, adv, ipn);
+    case 8: return launch_primal<8>(h, b, ip, xo, xn, xbar, dlast, adv, ipn);
+    case 16: return launch_primal<16>(h, b, ip, xo, xn, xbar, dlast, adv, ipn);
+    default: return launch_primal<32>(h, b, ip, xo, xn, xbar, dlast, adv, ipn);
+  }
 }
 
 }  // namespace
@@ -429,7 +406,10 @@ cudaError_t gf_launch_dense_gemv_q(GfCtx* h, const GfDenseQ& dq, const float* x,
 // One PDHG iteration for every instance: dual buckets, long-row chunks,
 // primal buckets, long-column chunks, dense-Q instances.  x_{k-1} is read
 // from x[1-parity... ] -- iteration it = k+1 reads x[(it-1)&1], writes x[it&1].
+cudaError_t gf_single_iter(GfCtx* h, int p);
+
 cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
+  if (h->single_ok) return gf_single_iter(h, parity);
   const GfIParam* ip = h->iprm + (size_t)parity * h->ninst;
   GfIParam* ipn = h->iprm + (size_t)(1 - parity) * h->ninst;
   const float* xo = h->x[1 - parity];
@@ -438,14 +418,7 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
   // ---- dual
   for (const GfBucket& b : h->rb) {
     if (!b.count) continue;
-    switch (b.lanes) {
-      case 1: e = launch_dual<1>(h, b, ip); break;
-      case 4: e = launch_dual<4>(h, b, ip); break;
-      case 8: e = launch_dual<8>(h, b, ip); break;
-      case 16: e = launch_dual<16>(h, b, ip); break;
-      default: e = launch_dual<32>(h, b, ip); break;
-    }
-    if (e != cudaSuccess) return e;
+    if ((e = dual_bucket(h, b, b.lanes, ip, h->y)) != cudaSuccess) return e;
   }
   if (h->rlong.nlong) {
     k_long_partial<<<h->rlong.nchunks, 256, 0, h->stream>>>(
@@ -486,13 +459,7 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
   }
   for (const GfBucket& b : h->cb) {
     if (!b.count) continue;
-    switch (b.lanes) {
-      case 1: e = launch_primal<1>(h, b, ip, xo, xn, adv, ipn); break;
-      case 4: e = launch_primal<4>(h, b, ip, xo, xn, adv, ipn); break;
-      case 8: e = launch_primal<8>(h, b, ip, xo, xn, adv, ipn); break;
-      case 16: e = launch_primal<16>(h, b, ip, xo, xn, adv, ipn); break;
-      default: e = launch_primal<32>(h, b, ip, xo, xn, adv, ipn); break;
-    }
+    e = primal_bucket(h, b, b.lanes, ip, xo, xn, h->xbar, h->dlast, adv, ipn);
     adv = 0;
     if (e != cudaSuccess) return e;
   }
@@ -509,4 +476,79 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the bucket kernels: every (row or column) length bucket is run
+// with 1, 2, 4, 8, 16 and 32 lanes per row / column on scratch outputs (the
+// solver state is untouched) and the fastest lane count is kept.  The lane
+// count changes only the FP32 summation order within a row / column.
+// ---------------------------------------------------------------------------
+static float time_launches(GfCtx* h, const std::function<cudaError_t()>& f, cudaError_t* err) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  *err = f();                                    // warm-up
+  for (int rep = 0; rep < 3 && *err == cudaSuccess; ++rep) {
+    cudaEventRecord(a, h->stream);
+    *err = f();
+    cudaEventRecord(b, h->stream);
+    if (*err == cudaSuccess) *err = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (*err == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+cudaError_t gf_tune_lanes(GfCtx* h, int32_t lanes_out[10]) {
+  static const int cand[6] = {1, 2, 4, 8, 16, 32};
+  cudaError_t e = cudaSuccess;
+  float* ys = gf_alloc_t<float>(h, std::max<int64_t>(1, h->M));
+  float* xs = gf_alloc_t<float>(h, std::max<int64_t>(1, h->N));
+  float* xb = gf_alloc_t<float>(h, std::max<int64_t>(1, h->N));
+  if (!ys || !xs || !xb) {
+    gf_free_one(h, ys); gf_free_one(h, xs); gf_free_one(h, xb);
+    return cudaErrorMemoryAllocation;
+  }
+  if (h->M) e = cudaMemcpyAsync(ys, h->y, sizeof(float) * h->M, cudaMemcpyDeviceToDevice,
+                                h->stream);
+  const int p = (int)((h->k_host + 1) & 1);
+  const GfIParam* ip = h->iprm + (size_t)p * h->ninst;
+  const float* xo = h->x[1 - p];
+  const long long saved = h->launches;
+  // rows of bucket k are at most this long (bucket bounds of the loader)
+  static const int64_t maxlen[5] = {2, 8, 32, 128, kLongLen};
+  for (int side = 0; side < 2 && e == cudaSuccess; ++side) {
+    std::vector<GfBucket>& bs = side ? h->cb : h->rb;
+    for (size_t k = 0; k < bs.size() && e == cudaSuccess; ++k) {
+      GfBucket& b = bs[k];
+      if (!b.count) continue;
+      float best = 1e30f;
+      int pick = b.lanes;
+      for (int c : cand) {
+        if (c > 2 * maxlen[std::min<size_t>(k, 4)]) continue;
+        float ms = time_launches(h, [&]() {
+          return side ? primal_bucket(h, b, c, ip, xo, xs, xb, nullptr, 0, nullptr)
+                      : dual_bucket(h, b, c, ip, ys);
+        }, &e);
+        if (e != cudaSuccess) break;
+        if (ms < best) { best = ms; pick = c; }
+      }
+      b.lanes = pick;
+    }
+  }
+  h->launches = saved;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  gf_free_one(h, ys);
+  gf_free_one(h, xs);
+  gf_free_one(h, xb);
+  for (int k = 0; k < 5; ++k) {
+    lanes_out[k] = k < (int)h->rb.size() ? h->rb[k].lanes : 0;
+    lanes_out[5 + k] = k < (int)h->cb.size() ? h->cb[k].lanes : 0;
+  }
+  return e;
 }

@@ -312,6 +312,28 @@ class Handle:
         _check(_lib.gfors_profile_read(self.h, n, _ptr(ms), _ptr(cnt)), self.h)
         return {k: (float(ms[q]), int(cnt[q])) for q, k in enumerate(self.PHASES)}
 
+    def autotune(self, cache_path=None):
+        """gfors_autotune; returns (lanes[10], cache hit)."""
+        lanes = np.zeros(10, np.int32)
+        hit = i32()
+        _check(_lib.gfors_autotune(self.h, None if cache_path is None else str(cache_path).encode(),
+                                   _ptr(lanes), C.byref(hit)), self.h)
+        return lanes, bool(hit.value)
+
+    def set_lanes(self, lanes):
+        lanes = np.ascontiguousarray(lanes, np.int32)
+        _check(_lib.gfors_set_lanes(self.h, _ptr(lanes)), self.h)
+
+    def get_lanes(self):
+        lanes = np.zeros(10, np.int32)
+        _check(_lib.gfors_get_lanes(self.h, _ptr(lanes)), self.h)
+        return lanes
+
+    def tune_key(self):
+        buf = C.create_string_buffer(512)
+        _check(_lib.gfors_tune_key(self.h, buf, 512), self.h)
+        return buf.value.decode()
+
     def launch_count(self) -> int:
         return _lib.gfors_launch_count(self.h)
 
@@ -360,6 +382,28 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
             if I.closure is not None:
                 H.set_closure(q, I.closure)
     return H
+
+
+_lib.gfors_autotune.argtypes = [vp, C.c_char_p, vp, vp]
+_lib.gfors_set_lanes.argtypes = [vp, vp]
+_lib.gfors_get_lanes.argtypes = [vp, vp]
+_lib.gfors_tune_key.argtypes = [vp, C.c_char_p, C.c_size_t]
+_lib.gfors_tune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, vp, vp]
+_lib.gfors_tune_cache_store.argtypes = [C.c_char_p, C.c_char_p, vp]
+
+
+def tune_cache_lookup(path, key):
+    """Lanes stored for key in the tuning cache at path, or None."""
+    lanes = np.zeros(10, np.int32)
+    found = i32()
+    _check(_lib.gfors_tune_cache_lookup(str(path).encode(), key.encode(), _ptr(lanes),
+                                        C.byref(found)))
+    return lanes if found.value else None
+
+
+def tune_cache_store(path, key, lanes):
+    lanes = np.ascontiguousarray(lanes, np.int32)
+    _check(_lib.gfors_tune_cache_store(str(path).encode(), key.encode(), _ptr(lanes)))
 
 
 NOALLOC_MAX_SAMPLES = 16384

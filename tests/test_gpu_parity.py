@@ -276,3 +276,72 @@ def test_persistent_dense_path_matches_launch_path():
     assert np.array_equal(xa, xb_)
     assert np.array_equal(xba, xbb)
     assert sa[6] == sb[6] and sa[7] == sb[7]        # same step sizes (same rho)
+
+
+# ------------------------------------------------------------ autotuner
+def test_autotune_cache_and_parity(tmp_path):
+    """gfors_autotune picks lane counts from 1..32 per bucket, stores them
+    under the handle's key, and a second handle of the same shape class
+    takes them from the cache.  Every lane choice keeps a PDHG step within
+    the per-step tolerance of the FP64 oracle."""
+    inst = W.set_cover(n=3000, m=300, density=0.02, idx=4)
+    gp, op = _params()
+    cache = tmp_path / "tune.json"
+    H = G.load(inst, gp)
+    lanes, hit = H.autotune(cache)
+    assert not hit and set(lanes.tolist()) <= {1, 2, 4, 8, 16, 32}
+    assert np.array_equal(H.get_lanes(), lanes)
+    assert np.array_equal(G.tune_cache_lookup(cache, H.tune_key()), lanes)
+    H2 = G.load(inst, gp)
+    lanes2, hit2 = H2.autotune(cache)
+    assert hit2 and np.array_equal(lanes2, lanes)
+    H2.destroy()
+    # the tuner touched no state: iterates still those of the load
+    x0, xb0, _, y0 = H.get_iterate(0)
+    assert np.all(x0 == np.float32(0.5)) and np.all(y0 == 0)
+    S = O.preprocess(inst, op.seed, 0)
+    rng = np.random.default_rng(5)
+    x = rng.random(inst.n).astype(np.float32)
+    xb = (x + 0.2 * (rng.random(inst.n) - 0.5)).astype(np.float32)
+    y = (rng.random(S.m) * 0.5).astype(np.float32)
+    k, rho = 3, 0.25
+    t1, t2 = O.step_sizes(op.sigma, S.normQ, rho, False)
+    ox, oxb, oy, _ = O.pdhg_step(S, t1, t2, rho, x.astype(np.float64), xb.astype(np.float64),
+                                 y.astype(np.float64))
+    tol_x, tol_y = _step_tolerance(S, t1, t2, rho, x.astype(np.float64),
+                                   xb.astype(np.float64), y.astype(np.float64), oy)
+    for choice in (lanes, np.ones(10, np.int32), np.full(10, 32, np.int32),
+                   np.array([2, 4, 2, 32, 8, 16, 2, 1, 4, 2], np.int32)):
+        H.set_lanes(choice)
+        H.set_iterate(0, x, xb, y)
+        H.set_counters(k, rho)
+        H.pdhg_steps(1)
+        gx, gxb, _, gy = H.get_iterate(0)
+        assert np.all(np.abs(gx - ox) <= tol_x)
+        assert np.all(np.abs(gy - oy) <= tol_y)
+    H.destroy()
+
+
+def test_single_row_path_matches_generic_path():
+    """Batches of one-row instances (knapsack) take the fused single-row
+    iteration (primal step + K xbar partials, per-instance dual step); it
+    must follow the generic bucket / long-row path up to FP32 summation
+    order of K xbar, also across a set_iterate in the middle (partials
+    recomputed from the new state) and with uneven instance sizes."""
+    insts = [W.knapsack(n, idx=20 + q) for q, n in enumerate((3001, 777, 9000))]
+    rng = np.random.default_rng(9)
+    xs = [rng.random(I.n).astype(np.float32) for I in insts]
+    out = []
+    for mode in (0, 1):
+        gp, _ = _params(k_int=10, pdhg_mode=mode)
+        H = G.load_batch(insts, gp)
+        H.pdhg_steps(13)
+        for q, I in enumerate(insts):
+            H.set_iterate(q, xs[q], xs[q], None)
+        H.pdhg_steps(17)
+        out.append([H.get_iterate(q) for q in range(len(insts))])
+        H.destroy()
+    for (xa, xba, _, ya), (xb, xbb, _, yb) in zip(*out):
+        assert np.max(np.abs(xa - xb)) < 1e-5
+        assert np.max(np.abs(xba - xbb)) < 2e-5
+        assert np.max(np.abs(ya - yb)) <= 1e-5 * (1 + np.max(np.abs(yb)))
