@@ -139,14 +139,21 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2510_27117_b300 import shard as SH
     build, k_int, k_b, desc = WORKLOADS[args.workload]
-    inst = build(0)
+    # several ranks: a single instance splits every round by candidate index
+    # (each rank the same PDHG, its own candidate range, one all-gather of the
+    # incumbent key per step); a batch gives every rank its own seeded batch
+    single = args.workload == "maxcut"
+    inst = build(0 if single else rank)
     insts = inst if isinstance(inst, list) else [inst]
     stream = torch.cuda.Stream()
-    prm = G.default_params(k_int=k_int, k_b=k_b, seed=0x5EED0000 + 1, x0=-1.0,
-                           inst_base=rank * len(insts))
-    if args.workload in ("maxcut",):
-        prm.x0 = -1.0        # x = 0.5 is a stationary point of the max-cut relaxation
+    prm = G.default_params(k_int=k_int, k_b=k_b * (world if single else 1),
+                           seed=0x5EED0000 + 1, x0=-1.0,
+                           inst_base=0 if single else rank * len(insts))
+    if single and world > 1:
+        prm.sample_chunk = k_b                # buffers of one rank's range
+    s_begin, s_end = SH.sample_range(prm.k_b, world, rank) if single else (0, k_b)
     G.use_torch_allocator(True)
     t_load0 = time.perf_counter()
     H = G.load_batch(insts, prm, stream=stream)
@@ -165,9 +172,18 @@ def run_ours(args, rank, world, local):
         from paper_2510_27117_b300 import proposal as PR
         H.set_proposal(PR.init_weights(seed=0))
 
+    key = torch.zeros(3, dtype=torch.int64, device="cuda")
+    keys = torch.zeros(4 * world, dtype=torch.int64, device="cuda")
+    rank_t = torch.tensor([rank], dtype=torch.int64, device="cuda")
+
     def step():
         H.pdhg_steps(k_int)
-        H.sample_eval(nr, round_id[0], prop)
+        if single and world > 1:
+            H.sample_eval_range(nr, round_id[0], prop, s_begin, s_end)
+            H.incumbent_key_async(0, key.data_ptr())
+            dist.all_gather_into_tensor(keys, torch.cat([key, rank_t]))
+        else:
+            H.sample_eval(nr, round_id[0], prop)
         round_id[0] += nr
 
     with torch.cuda.stream(stream):
@@ -211,7 +227,8 @@ def run_ours(args, rank, world, local):
     iters_s = k_int * args.steps / (ms / 1e3)
 
     # ---- end to end through the public API with host buffers
-    e2e = run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr, prop)
+    e2e = run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr, prop,
+                  (s_begin, s_end) if single and world > 1 else None)
 
     # ---- roofline of the dominant kernel (phase timed with events on the stream)
     peaks, src = load_peaks()
@@ -241,7 +258,7 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr=1, prop=0):
+def run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr=1, prop=0, srange=None):
     """The same metric through the public API per step: host->device copy of
     the warm-start iterate from pinned memory (gfors_set_iterate), the step,
     and the incumbent read back to the host (gfors_incumbent)."""
@@ -257,7 +274,10 @@ def run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr=1, prop=0):
         for q in range(len(insts)):
             H.set_iterate(q, xs[q], xs[q], None)
         H.pdhg_steps(k_int)
-        H.sample_eval(nr, rid, prop)
+        if srange:
+            H.sample_eval_range(nr, rid, prop, *srange)
+        else:
+            H.sample_eval(nr, rid, prop)
         rid += nr
         for q in range(len(insts)):
             H.incumbent(q, want_x=True)
@@ -423,6 +443,135 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ time to gap
+def _dantzig_bound(I):
+    """Fractional-knapsack LP optimum (greedy by profit/weight), as the
+    minimisation objective -sum p x of the instance."""
+    w, pr, cap = I.meta["w"], I.meta["p"], I.meta["cap"]
+    order = np.argsort(-(pr / w), kind="stable")
+    left, val = cap, 0.0
+    for i in order:
+        if w[i] <= left:
+            left -= w[i]
+            val += pr[i]
+        else:
+            val += pr[i] * left / w[i]
+            break
+    return -val
+
+
+def _gap_ok(obj, zref):
+    return obj <= zref + 0.01 * max(1.0, abs(zref))
+
+
+def _run_until(G, H, insts, prm, proposal, zref, max_trig, tsync):
+    """Alg. 1 loop on handle H (all its instances): k_int PDHG iterations
+    then k_r sampling rounds per trigger; after each trigger the incumbents
+    are read.  Returns (seconds until every instance is within 1% of zref
+    (None if never), best objectives, per-trigger trace)."""
+    import torch
+    tsync()
+    t0 = time.perf_counter()
+    rid, hit_t, trace = 0, None, []
+    best = [None] * len(insts)
+    for trig in range(max_trig):
+        H.pdhg_steps(prm.k_int)
+        H.sample_eval(prm.k_r, rid, proposal)
+        rid += prm.k_r
+        for q in range(len(insts)):
+            inc = H.incumbent(q, want_x=False)
+            best[q] = inc["obj"] if inc["found"] else None
+        el = time.perf_counter() - t0
+        trace.append((el, list(best)))
+        if zref is not None and hit_t is None and all(
+                b is not None and _gap_ok(b, z) for b, z in zip(best, zref)):
+            hit_t = el
+            break
+    return hit_t, best, trace
+
+
+def time_to_gap(args):
+    """Wall time (Preprocess excluded) until the incumbent is within 1% of
+    the reference value: the plain form (p = x_k, one instance per handle,
+    instances one after another) against the batched form (all instances in
+    one handle) with the plain and with the learned proposal."""
+    import torch
+    from paper_2510_27117_b300 import gfors as G
+    from paper_2510_27117_b300 import proposal as PR
+    from paper_2510_27117_b300 import workloads as W
+    torch.cuda.set_device(0)
+    G.use_torch_allocator(True)
+    tsync = torch.cuda.synchronize
+    out = {"metric": "time to <=1% gap, learned+batched vs plain", "unit": "s",
+           "higher_is_better": False, "data": "synthetic (seeded)"}
+    train_info, Wt = None, None
+    if args.workload == "assign3d":
+        k_int, k_b, max_trig = 50, 1024, args.gap_triggers
+        insts = [W.assign3d(I=64, idx=q) for q in range(5)]
+        kw = dict(k_int=k_int, k_b=k_b, seed=0x5EED0003, x0=0.5)
+        # training data: plain runs on seeded I=32 instances (bounded time)
+        t0 = time.perf_counter()
+        feats, labels, ntr = [], [], 0
+        while ntr < args.train_instances and time.perf_counter() - t0 < args.train_budget:
+            batch = [W.assign3d(I=32, idx=20000 + ntr + q) for q in range(8)]
+            f, y = PR.collect(batch, dict(k_b=k_b, seed=0x5EED0003, x0=0.5), 500, k_int)
+            feats.append(f)
+            labels.append(y)
+            ntr += len(batch)
+        t_col = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        Wt, hist = PR.train(np.concatenate(feats), np.concatenate(labels), epochs=3)
+        train_info = {"instances": ntr, "rows": int(sum(len(y) for y in labels)),
+                      "collect_s": t_col, "train_s": time.perf_counter() - t0,
+                      "loss_per_epoch": hist,
+                      "source": "plain runs, 500 iterations each, axial I=32 seeds 20000+"}
+        zref = None                    # plain's best at its full budget (below)
+        desc = "axial 3D assignment I=64, seeds 0-4, k_int=50, k_b=1024"
+    else:
+        k_int, k_b, max_trig = 50, 4096, args.gap_triggers
+        insts = W.knapsack_batch(ninst=512)[:args.gap_instances]
+        kw = dict(k_int=k_int, k_b=k_b, seed=0x5EED0002, x0=0.5)
+        zref = [_dantzig_bound(I) for I in insts]
+        desc = (f"first {len(insts)} of the 512-knapsack batch, k_int=50, k_b=4096; "
+                "reference = fractional LP bound")
+    prm = G.default_params(**kw)
+    # plain form: one handle per instance, one after another
+    t_plain, best_plain, reached = 0.0, [], []
+    for q, I in enumerate(insts):
+        # Philox instance id q, as instance q of the batched handle: the
+        # batched plain form then draws the very same candidates
+        H = G.load(I, G.default_params(**kw, inst_base=q))
+        zq = None if zref is None else [zref[q]]
+        hit, best, trace = _run_until(G, H, [I], prm, 0, zq, max_trig, tsync)
+        H.destroy()
+        if zref is None:               # reference: plain's best at full budget
+            zb = best[0]
+            hit = next(el for el, b in trace if b[0] is not None and _gap_ok(b[0], zb))
+        best_plain.append(best[0])
+        reached.append(hit is not None)
+        t_plain += hit if hit is not None else trace[-1][0]
+    if zref is None:
+        zref = best_plain
+    res = {}
+    for name, prop in (("batched_plain", 0), ("learned_batched", 2)):
+        if prop and Wt is None:
+            continue
+        H = G.load_batch(insts, prm)
+        if prop:
+            H.set_proposal(Wt)
+        hit, best, trace = _run_until(G, H, insts, prm, prop, zref, max_trig, tsync)
+        H.destroy()
+        res[name] = {"s": hit, "reached": hit is not None, "best": best,
+                     "s_budget": trace[-1][0]}
+    out.update({"workload": desc, "instances": len(insts), "z_ref": zref,
+                "plain_s": t_plain, "plain_reached": reached, "plain_best": best_plain,
+                "max_triggers": max_trig, "training": train_info, **res})
+    lb = res.get("learned_batched", res.get("batched_plain"))
+    out["value"] = lb["s"]
+    out["speedup_vs_plain"] = (t_plain / lb["s"]) if lb["s"] else None
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,11 +580,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maxcut", choices=list(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--time-to-gap", action="store_true",
+                    help="measure time to <=1%% gap (plain vs batched / learned+batched) "
+                         "on --workload assign3d or knapsack instead of throughput")
+    ap.add_argument("--gap-triggers", type=int, default=100)
+    ap.add_argument("--gap-instances", type=int, default=32)
+    ap.add_argument("--train-instances", type=int, default=2000)
+    ap.add_argument("--train-budget", type=float, default=120.0)
     ap.add_argument("--profile-region", action="store_true",
                     help="cudaProfilerStart/Stop around the timed steps (for ncu "
                          "--profile-from-start off)")
     args = ap.parse_args()
     rank, world, local = env_rank()
+    if args.time_to_gap:
+        if rank == 0:
+            time_to_gap(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

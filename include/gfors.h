@@ -126,7 +126,8 @@ GFORS_API gfors_status gfors_set_allocator(gfors_alloc_fn alloc, gfors_free_fn f
  * divided by ||K||_2; the two spectral norms come from FP64 power
  * iterations on the device.  A and/or B may be NULL (m1 = 0 / m2 = 0), Q may
  * be NULL (Q = 0).  b has A->rows entries, d has B->rows, c has n.
- * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * cuda_stream: the cudaStream_t all of the handle's work is enqueued on
+ * (NULL: the handle creates and owns a non-blocking stream).
  * Infeasible empty rows and malformed CSR give GFORS_E_ARG. */
 GFORS_API gfors_status gfors_load(const gfors_csr* A, const double* b, const gfors_csr* B,
                         const double* d, const gfors_qmat* Q, const double* c,
@@ -360,6 +361,24 @@ GFORS_API gfors_status gfors_tune_cache_lookup(const char* path, const char* key
                                                int32_t lanes[10], int32_t* found);
 GFORS_API gfors_status gfors_tune_cache_store(const char* path, const char* key,
                                               const int32_t lanes[10]);
+
+/* ---- Several devices (Section 3's sampling rounds split by candidate).
+ * gfors_sample_eval_range: as gfors_sample_eval, but only candidates
+ * [s_begin, s_end) of every round (multiples of 32, within k_b).  Candidate
+ * indices stay global within the round (Philox counters as in Algorithm 3),
+ * so devices that each take a disjoint range of the same rounds from the same
+ * iterate draw together exactly the candidates of the whole round, and the
+ * lexicographic minimum of their incumbent keys is the one-device incumbent.
+ * Asynchronous. */
+GFORS_API gfors_status gfors_sample_eval_range(gfors_handle h, int32_t nrounds,
+                                               uint32_t first_round_id, int32_t proposal,
+                                               int32_t s_begin, int32_t s_end);
+/* Incumbent key of instance inst -- (objective, round id, candidate index);
+ * all three INT64_MAX when none was found -- written to key_dev[3] (DEVICE
+ * memory, caller-owned), enqueued on the handle's stream (asynchronous), for
+ * a min-reduction across devices without a host round trip. */
+GFORS_API gfors_status gfors_incumbent_key_async(gfors_handle h, int32_t inst,
+                                                 int64_t* key_dev);
 
 /* Kernel-launch counter of this handle (device kernels enqueued so far). */
 GFORS_API int64_t gfors_launch_count(gfors_handle h);

@@ -257,13 +257,17 @@ extern "C" gfors_status gfors_pdhg_steps(gfors_handle h, int64_t nsteps) {
   return GFORS_OK;
 }
 
-// One round (k_b candidates, processed in chunks): candidates [0, split) are
-// drawn from p_a, [split, k_b) from p_b (split = k_b: a single proposal).
-static cudaError_t enqueue_round(GfCtx* h, const float* p_a, const float* p_b, int split) {
-  const int kb = h->prm.k_b;
+// One round: candidates [sb, se) of the round's k_b (processed in chunks);
+// candidates below `split` are drawn from p_a, the others from p_b (split =
+// k_b: a single proposal).  Candidate indices are global within the round, so
+// disjoint ranges of one round (on several devices) draw exactly the
+// candidates of the whole round.
+static cudaError_t enqueue_round(GfCtx* h, const float* p_a, const float* p_b, int split,
+                                 int sb, int se) {
+  const int kb = se;
   cudaError_t e;
-  for (int s0 = 0; s0 < kb;) {
-    const int seg_end = (s0 < split) ? split : kb;
+  for (int s0 = sb; s0 < kb;) {
+    const int seg_end = (s0 < split) ? std::min(split, kb) : kb;
     const float* p = (s0 < split) ? p_a : p_b;
     const int len = std::min(h->chunk, seg_end - s0);
     const bool last = (s0 + len >= kb);
@@ -302,7 +306,8 @@ static cudaError_t enqueue_round(GfCtx* h, const float* p_a, const float* p_b, i
   return cudaSuccess;
 }
 
-static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal) {
+static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal, int sb,
+                                  int se) {
   if (!h->all_integral)
     return gf_fail(h, GFORS_E_UNSUPPORTED,
                    "exact evaluation needs integral data (|value| < 2^31)");
@@ -321,7 +326,7 @@ static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal) {
   const int split = (proposal == 2) ? std::max(32, (kb / 2) / 32 * 32) : kb;
   for (int r = 0; r < nrounds; ++r) {
     const float* pa = (proposal == 0) ? xk : h->p_learn;
-    if ((e = enqueue_round(h, pa, xk, split))) return gf_cuda(h, e, "sampling round");
+    if ((e = enqueue_round(h, pa, xk, split, sb, se))) return gf_cuda(h, e, "sampling round");
     h->host_round++;
   }
   return GFORS_OK;
@@ -335,7 +340,41 @@ extern "C" gfors_status gfors_sample_eval(gfors_handle h, int32_t nrounds,
   k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, first_round_id);
   h->launches++;
   h->host_round = first_round_id;
-  return sample_rounds(h, nrounds, proposal);
+  return sample_rounds(h, nrounds, proposal, 0, h->prm.k_b);
+}
+
+extern "C" gfors_status gfors_sample_eval_range(gfors_handle h, int32_t nrounds,
+                                                uint32_t first_round_id, int32_t proposal,
+                                                int32_t s_begin, int32_t s_end) {
+  GF_ENTER(h);
+  if (nrounds < 0 || proposal < 0 || proposal > 2)
+    return gf_fail(h, GFORS_E_ARG, "bad nrounds / proposal");
+  if (s_begin < 0 || s_end > h->prm.k_b || s_begin >= s_end || s_begin % 32 || s_end % 32)
+    return gf_fail(h, GFORS_E_ARG, "need 0 <= s_begin < s_end <= k_b, multiples of 32");
+  k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, first_round_id);
+  h->launches++;
+  h->host_round = first_round_id;
+  return sample_rounds(h, nrounds, proposal, s_begin, s_end);
+}
+
+namespace {
+__global__ void k_inc_key(const GfInc* __restrict__ inc, int q, long long* __restrict__ out) {
+  const GfInc v = inc[q];
+  out[0] = v.found ? v.obj : 0x7FFFFFFFFFFFFFFFll;
+  out[1] = v.found ? (long long)v.round_id : 0x7FFFFFFFFFFFFFFFll;
+  out[2] = v.found ? (long long)v.sample : 0x7FFFFFFFFFFFFFFFll;
+}
+}  // namespace
+
+extern "C" gfors_status gfors_incumbent_key_async(gfors_handle h, int32_t inst,
+                                                  int64_t* key_dev) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst || !key_dev) return gf_fail(h, GFORS_E_ARG, "bad inst / key");
+  k_inc_key<<<1, 1, 0, h->stream>>>(h->inc, inst, reinterpret_cast<long long*>(key_dev));
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e) return gf_cuda(h, e, "gfors_incumbent_key_async");
+  return GFORS_OK;
 }
 
 static cudaError_t enqueue_final_round(GfCtx* h) {
@@ -453,7 +492,7 @@ extern "C" gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time
       const long long trig = h->k_host / kint - 1;
       k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, (unsigned)(trig * h->prm.k_r));
       h->host_round = (unsigned)(trig * h->prm.k_r);
-      if ((st = sample_rounds(h, h->prm.k_r, proposal))) return st;
+      if ((st = sample_rounds(h, h->prm.k_r, proposal, 0, h->prm.k_b))) return st;
       std::vector<double> sv;
       if ((st = fetch_stats(h, sv))) return st;
       if (halt_update(h, sv)) break;

@@ -197,6 +197,15 @@ class Handle:
     def sample_eval(self, nrounds, first_round_id, proposal=0):
         _check(_lib.gfors_sample_eval(self.h, nrounds, first_round_id, proposal), self.h)
 
+    def sample_eval_range(self, nrounds, first_round_id, proposal, s_begin, s_end):
+        _check(_lib.gfors_sample_eval_range(self.h, nrounds, first_round_id, proposal,
+                                            s_begin, s_end), self.h)
+
+    def incumbent_key_async(self, inst, key_dev_ptr):
+        """Write (obj, round, sample) of instance inst to 3 int64 at a device
+        address (e.g. tensor.data_ptr()), on the handle's stream."""
+        _check(_lib.gfors_incumbent_key_async(self.h, inst, key_dev_ptr), self.h)
+
     def final_round(self):
         _check(_lib.gfors_final_round(self.h), self.h)
 
@@ -384,6 +393,8 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
     return H
 
 
+_lib.gfors_sample_eval_range.argtypes = [vp, i32, u32, i32, i32, i32]
+_lib.gfors_incumbent_key_async.argtypes = [vp, i32, vp]
 _lib.gfors_autotune.argtypes = [vp, C.c_char_p, vp, vp]
 _lib.gfors_set_lanes.argtypes = [vp, vp]
 _lib.gfors_get_lanes.argtypes = [vp, vp]

@@ -345,3 +345,33 @@ def test_single_row_path_matches_generic_path():
         assert np.max(np.abs(xa - xb)) < 1e-5
         assert np.max(np.abs(xba - xbb)) < 2e-5
         assert np.max(np.abs(ya - yb)) <= 1e-5 * (1 + np.max(np.abs(yb)))
+
+
+@pytest.mark.parametrize("name", ["setcover", "maxcut", "knapsack"])
+def test_candidate_ranges_reproduce_whole_round(name):
+    """Disjoint candidate ranges of the same rounds (as on several devices)
+    give, after the lexicographic min of their incumbent keys, the incumbent
+    of the whole rounds on one handle."""
+    import torch
+    from paper_2510_27117_b300 import shard as SH
+    inst = CASES[name]()
+    gp, _ = _params(k_b=256, x0=-1.0 if name == "maxcut" else 0.5)
+    keys = []
+    for rng_ in [(0, 256), (0, 96), (96, 256)]:
+        H = G.load(inst, gp)
+        H.pdhg_steps(10)
+        if rng_ == (0, 256):
+            H.sample_eval(3, 0, 0)
+        else:
+            H.sample_eval_range(3, 0, 0, *rng_)
+        k = torch.zeros(3, dtype=torch.int64, device="cuda")
+        H.incumbent_key_async(0, k.data_ptr())
+        torch.cuda.synchronize()
+        keys.append(k.cpu().numpy())
+        inc = H.incumbent(0, want_x=False)
+        if inc["found"]:
+            assert keys[-1].tolist() == [inc["obj"], inc["round"], inc["sample"]]
+        H.destroy()
+    whole = keys[0]
+    parts = np.stack([np.append(keys[1], 0), np.append(keys[2], 1)])
+    assert SH.min_key(parts)[:3].tolist() == whole.tolist()
