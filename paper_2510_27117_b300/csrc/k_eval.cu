@@ -42,47 +42,116 @@ __device__ void add_violations(uint32_t vmask, int inst, int w, int chunk,
   }
 }
 
-// U rows: bit-sliced counter of the chosen columns (up to 2^16 - 1), then
-// the bound test count in [L, U].  Fast paths: covering rows (L = 1, no U)
-// need only an OR; L = U = 1 (one-hot equality) uses ones/twos masks.
+// U rows: one warp per (row, group of up to 8 candidate words); the lanes
+// stride over the row's columns (consecutive lanes, consecutive columns) and
+// keep per-word state, combined across the warp at the end:
+//   covering rows (L <= 1, no upper bound): OR of the chosen columns;
+//   at-most/exactly-one rows (U == 1): ones / twos masks;
+//   others: a 16-slice bit-sliced counter per word (up to 2^16 - 1), summed
+//   across lanes by bit-sliced addition, then count in [L, U].
+constexpr int kUG = 8;                   // candidate words per warp task
+
+GF_DEV void load_words(const uint32_t* __restrict__ X, int64_t v, int kws, int w0, int nw,
+                       bool vec, uint32_t* m) {
+  const uint32_t* src = X + v * kws + w0;
+  if (vec && nw == kUG) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(src));
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(src) + 1);
+    m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
+    m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kUG; ++j) m[j] = (j < nw) ? __ldg(src + j) : 0u;
+  }
+}
+
+// Violations of one row for candidates of word w: lane t adds bit t.
+GF_DEV void add_row_violations(uint32_t vmask, int inst, int w, int len, int chunk,
+                               int32_t* __restrict__ viol) {
+  const int lane = threadIdx.x & 31;
+  const int nt = len - 32 * w;
+  if (nt < 32) vmask &= (1u << nt) - 1u;
+  if ((vmask >> lane) & 1u) atomicAdd(&viol[(int64_t)inst * chunk + 32 * w + lane], 1);
+}
+
 __global__ void __launch_bounds__(256)
 k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
              const int32_t* __restrict__ ucols, const uint32_t* __restrict__ X, int kws,
              int kwu, int len, int chunk, int32_t* __restrict__ viol) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int w = (int)(gid / nrows);          // rows fastest: a warp shares w
-  const int64_t r = gid - (int64_t)w * nrows;
-  const bool valid = (w < kwu);
-  uint32_t vmask = 0;
-  int inst = 0;
-  if (valid) {
-    const GfURow R = rows[r];
-    inst = R.inst;
-    const int32_t* cols = ucols + R.t0;
-    const bool no_upper = (R.U < 0 || R.U >= R.len);
-    if (R.L <= 1 && no_upper) {
-      uint32_t any = 0;
-      for (int t = 0; t < R.len; ++t) any |= X[(int64_t)cols[t] * kws + w];
-      vmask = (R.L == 1) ? ~any : 0u;
-    } else if (R.U == 1 && R.L <= 1) {
-      uint32_t ones = 0, twos = 0;
-      for (int t = 0; t < R.len; ++t) {
-        const uint32_t m = X[(int64_t)cols[t] * kws + w];
-        twos |= ones & m;
-        ones |= m;
-      }
-      vmask = twos | (R.L == 1 ? ~ones : 0u);
-    } else {
-      uint32_t s[16];
+  const int lane = threadIdx.x & 31;
+  const int ng = (kwu + kUG - 1) / kUG;
+  const int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (task >= nrows * ng) return;                 // whole warps exit together
+  const int64_t r = task / ng;
+  const int w0 = (int)(task - r * ng) * kUG;
+  const int nw = min(kUG, kwu - w0);
+  const bool vec = (kws % 4) == 0;
+  const GfURow R = rows[r];
+  const int32_t* cols = ucols + R.t0;
+  const bool no_upper = (R.U < 0 || R.U >= R.len);
+  uint32_t m[kUG];
+  if (R.L <= 1 && no_upper) {
+    uint32_t any[kUG] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = lane; t < R.len; t += 32) {
+      load_words(X, cols[t], kws, w0, nw, vec, m);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) s[q] = 0u;
-      for (int t = 0; t < R.len; ++t) {
-        uint32_t c = X[(int64_t)cols[t] * kws + w];
+      for (int j = 0; j < kUG; ++j) any[j] |= m[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kUG; ++j) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) any[j] |= __shfl_xor_sync(0xFFFFFFFFu, any[j], off);
+      if (j < nw && R.L == 1) add_row_violations(~any[j], R.inst, w0 + j, len, chunk, viol);
+    }
+  } else if (R.U == 1 && R.L <= 1) {
+    uint32_t ones[kUG] = {0, 0, 0, 0, 0, 0, 0, 0}, twos[kUG] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = lane; t < R.len; t += 32) {
+      load_words(X, cols[t], kws, w0, nw, vec, m);
+#pragma unroll
+      for (int j = 0; j < kUG; ++j) {
+        twos[j] |= ones[j] & m[j];
+        ones[j] |= m[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kUG; ++j) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, ones[j], off);
+        const uint32_t tw = __shfl_xor_sync(0xFFFFFFFFu, twos[j], off);
+        twos[j] |= tw | (ones[j] & o);
+        ones[j] |= o;
+      }
+      if (j < nw)
+        add_row_violations(twos[j] | (R.L == 1 ? ~ones[j] : 0u), R.inst, w0 + j, len, chunk,
+                           viol);
+    }
+  } else {
+    // general count bounds: one word at a time (16 slices per word)
+    for (int j = 0; j < nw; ++j) {
+      uint32_t sl[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sl[q] = 0u;
+      for (int t = lane; t < R.len; t += 32) {
+        uint32_t c = __ldg(X + (int64_t)cols[t] * kws + w0 + j);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const uint32_t carry = s[q] & c;
-          s[q] ^= c;
+          const uint32_t carry = sl[q] & c;
+          sl[q] ^= c;
           c = carry;
+        }
+      }
+      // bit-sliced sum across the warp (counts < 2^16: R.len < 65536)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        uint32_t carry = 0u;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, sl[q], off);
+          const uint32_t x = sl[q] ^ o;
+          const uint32_t nc = (sl[q] & o) | (carry & x);
+          sl[q] = x ^ carry;
+          carry = nc;
         }
       }
       // ge = (count >= L), gt = (count > U), MSB-first bit-sliced compares
@@ -90,42 +159,56 @@ k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
       const uint32_t L = (uint32_t)max(R.L, 0), U = (uint32_t)max(R.U, 0);
 #pragma unroll
       for (int q = 15; q >= 0; --q) {
-        if ((L >> q) & 1u) { eqL &= s[q]; } else { gtL |= eqL & s[q]; eqL &= ~s[q]; }
-        if ((U >> q) & 1u) { eqU &= s[q]; } else { gtU |= eqU & s[q]; eqU &= ~s[q]; }
+        if ((L >> q) & 1u) { eqL &= sl[q]; } else { gtL |= eqL & sl[q]; eqL &= ~sl[q]; }
+        if ((U >> q) & 1u) { eqU &= sl[q]; } else { gtU |= eqU & sl[q]; eqU &= ~sl[q]; }
       }
-      const uint32_t ge = gtL | eqL;
-      vmask = ~ge;
+      uint32_t vmask = ~(gtL | eqL);
       if (!no_upper) vmask |= gtU;
+      add_row_violations(vmask, R.inst, w0 + j, len, chunk, viol);
     }
-    const int nt = len - 32 * w;
-    if (nt < 32) vmask &= (1u << nt) - 1u;
   }
-  add_violations(vmask, inst, w, chunk, viol, valid);
 }
 
 // P rows: at most two variables; `table` bit (x1 + 2 x2) marks a violation.
+// One thread per row, all candidate words of the row in groups of 8 (16-byte
+// loads of the two variables' consecutive words), per-word warp aggregation.
 __global__ void __launch_bounds__(256)
 k_eval_prows(const GfPRow* __restrict__ rows, int64_t nrows,
              const uint32_t* __restrict__ X, int kws, int kwu, int len, int chunk,
              int32_t* __restrict__ viol) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int w = (int)(gid / nrows);
-  const int64_t r = gid - (int64_t)w * nrows;
-  const bool valid = (w < kwu);
-  uint32_t vmask = 0;
-  int inst = 0;
-  if (valid) {
-    const GfPRow R = rows[r];
-    inst = R.inst;
-    const uint32_t a = X[(int64_t)R.v1 * kws + w];
-    const uint32_t b = (R.v2 >= 0) ? X[(int64_t)R.v2 * kws + w] : 0u;
-    const uint32_t T = R.table;
-    vmask = ((T & 1u) ? (~a & ~b) : 0u) | ((T & 2u) ? (a & ~b) : 0u) |
-            ((T & 4u) ? (~a & b) : 0u) | ((T & 8u) ? (a & b) : 0u);
-    const int nt = len - 32 * w;
-    if (nt < 32) vmask &= (1u << nt) - 1u;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = r < nrows;
+  const bool vec = (kws % 4) == 0;
+  GfPRow R;
+  R.inst = 0; R.v1 = 0; R.v2 = -1; R.table = 0;
+  if (valid) R = rows[r];
+  for (int w0 = 0; w0 < kwu; w0 += kUG) {          // uniform across the warp
+    const int nw = min(kUG, kwu - w0);
+    uint32_t a[kUG], b[kUG];
+    if (valid) {
+      load_words(X, R.v1, kws, w0, nw, vec, a);
+      if (R.v2 >= 0) {
+        load_words(X, R.v2, kws, w0, nw, vec, b);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kUG; ++j) b[j] = 0u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kUG; ++j) {
+      if (j >= nw) break;
+      uint32_t vmask = 0u;
+      if (valid) {
+        const uint32_t T = R.table;
+        vmask = ((T & 1u) ? (~a[j] & ~b[j]) : 0u) | ((T & 2u) ? (a[j] & ~b[j]) : 0u) |
+                ((T & 4u) ? (~a[j] & b[j]) : 0u) | ((T & 8u) ? (a[j] & b[j]) : 0u);
+        const int nt = len - 32 * (w0 + j);
+        if (nt < 32) vmask &= (1u << nt) - 1u;
+      }
+      if (__any_sync(0xFFFFFFFFu, vmask != 0u))
+        add_violations(vmask, R.inst, w0 + j, chunk, viol, valid);
+    }
   }
-  add_violations(vmask, inst, w, chunk, viol, valid);
 }
 
 // G rows: 32 per-candidate accumulators.
@@ -165,40 +248,62 @@ k_eval_grows(const GfGRow* __restrict__ rows, int64_t nrows,
 }
 
 // Linear objective c^T X_s over a chunk of one instance's variables; block
-// of 32 x 8 threads: lane = candidate within word w, 8 warps split the
-// variables; partials reduced in shared memory, one atomic per candidate.
+// of 8 warps over the chunk's variables, candidate words in groups of 4
+// (16-byte loads; the chunk's words stay in L1 between groups).  Per word:
+// the warp's nonzero words are broadcast in turn and lane t adds the cost of
+// every variable whose bit t is set; partials reduced in shared memory, one
+// atomic per candidate.
 __global__ void __launch_bounds__(256)
 k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
                const long long* __restrict__ cint, const uint32_t* __restrict__ X,
                int kws, int kwu, int len, int chunk, long long* __restrict__ obj) {
   const int64_t c = blockIdx.x;
-  const int w = blockIdx.y;
-  if (c >= nch || w >= kwu) return;
+  if (c >= nch) return;
   const GfObjChunk C = ch[c];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long acc = 0;
-  for (int v = C.v0 + warp * 32; v < C.v1; v += 256) {
-    const int myv = v + lane;
-    const uint32_t mw = (myv < C.v1) ? X[(int64_t)myv * kws + w] : 0u;
-    const long long mc = (myv < C.v1) ? cint[myv] : 0ll;
-    unsigned nz = __ballot_sync(0xFFFFFFFFu, mw != 0u);
-    while (nz) {
-      const int src = __ffs(nz) - 1;
-      nz &= nz - 1;
-      const uint32_t word = __shfl_sync(0xFFFFFFFFu, mw, src);
-      const long long cv = __shfl_sync(0xFFFFFFFFu, mc, src);
-      if ((word >> lane) & 1u) acc += cv;
+  const bool vec = (kws % 4) == 0;
+  __shared__ long long red[8][4][32];
+  for (int w0 = 0; w0 < kwu; w0 += 4) {
+    const int nw = min(4, kwu - w0);
+    long long acc[4] = {0, 0, 0, 0};
+    for (int v = C.v0 + warp * 32; v < C.v1; v += 256) {
+      const int myv = v + lane;
+      uint32_t mw[4] = {0u, 0u, 0u, 0u};
+      long long mc = 0;
+      if (myv < C.v1) {
+        mc = cint[myv];
+        const uint32_t* src = X + (int64_t)myv * kws + w0;
+        if (vec && nw == 4) {
+          const uint4 q = __ldg(reinterpret_cast<const uint4*>(src));
+          mw[0] = q.x; mw[1] = q.y; mw[2] = q.z; mw[3] = q.w;
+        } else {
+          for (int j = 0; j < nw; ++j) mw[j] = __ldg(src + j);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        unsigned nz = __ballot_sync(0xFFFFFFFFu, mw[j] != 0u && mc != 0);
+        while (nz) {
+          const int src = __ffs(nz) - 1;
+          nz &= nz - 1;
+          const uint32_t word = __shfl_sync(0xFFFFFFFFu, mw[j], src);
+          const long long cv = __shfl_sync(0xFFFFFFFFu, mc, src);
+          if ((word >> lane) & 1u) acc[j] += cv;
+        }
+      }
     }
-  }
-  __shared__ long long red[8][32];
-  red[warp][lane] = acc;
-  __syncthreads();
-  if (warp == 0) {
-    long long s = 0;
-    for (int q = 0; q < 8; ++q) s += red[q][lane];
-    if (s != 0 && 32 * w + lane < len)
-      atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)C.inst * chunk + 32 * w + lane]),
-                (unsigned long long)s);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[warp][j][lane] = acc[j];
+    __syncthreads();
+    if (warp < 4 && warp < nw) {
+      long long s = 0;
+      for (int q = 0; q < 8; ++q) s += red[q][warp][lane];
+      const int cand = 32 * (w0 + warp) + lane;
+      if (s != 0 && cand < len)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)C.inst * chunk + cand]),
+                  (unsigned long long)s);
+    }
+    __syncthreads();
   }
 }
 
@@ -415,14 +520,13 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
   if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
     return e;
   if (h->nurows) {
-    const int64_t th = h->nurows * kwu;
-    k_eval_urows<<<(unsigned)((th + 255) / 256), 256, 0, h->stream>>>(
+    const int64_t warps = h->nurows * ((kwu + kUG - 1) / kUG);
+    k_eval_urows<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
         h->urows, h->nurows, h->ucols, h->X, h->kw, kwu, len, h->chunk, h->viol);
     h->launches++;
   }
   if (h->nprows) {
-    const int64_t th = h->nprows * kwu;
-    k_eval_prows<<<(unsigned)((th + 255) / 256), 256, 0, h->stream>>>(
+    k_eval_prows<<<(unsigned)((h->nprows + 255) / 256), 256, 0, h->stream>>>(
         h->prows, h->nprows, h->X, h->kw, kwu, len, h->chunk, h->viol);
     h->launches++;
   }
@@ -433,9 +537,8 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
     h->launches++;
   }
   if (h->nochunks) {
-    dim3 grid((unsigned)h->nochunks, (unsigned)kwu);
-    k_eval_obj_lin<<<grid, 256, 0, h->stream>>>(h->ochunks, h->nochunks, h->cint, h->X, h->kw,
-                                                kwu, len, h->chunk, h->obj);
+    k_eval_obj_lin<<<(unsigned)h->nochunks, 256, 0, h->stream>>>(
+        h->ochunks, h->nochunks, h->cint, h->X, h->kw, kwu, len, h->chunk, h->obj);
     h->launches++;
   }
   if (h->nqchunks) {
