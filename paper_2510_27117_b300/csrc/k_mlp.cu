@@ -9,12 +9,18 @@
 //   p  = clip(sigmoid(z), 1e-4, 1 - 1e-4).
 // Weights (not biases, not activations) are rounded to bf16 (round to
 // nearest even) when staged; arithmetic is FP32.  Gradients are taken with
-// respect to the FP32 masters, the rounding passed straight through.
+// respect to the FP32 masters, the rounding passed straight through.  The
+// forward pass used for sampling runs on the tensor cores (k_mlp_tc.cu)
+// with the same numerics; the gradient pass here recomputes its own forward.
 #include <math.h>
 #include <stddef.h>
 #include <string.h>
 
 #include "internal.cuh"
+
+cudaError_t gf_mlp_forward_tc(const float* W, int64_t nv, const float* feat, float* z,
+                              float* p, const uint8_t* live, uint64_t limit_ns, int* err,
+                              cudaStream_t s);
 
 namespace {
 
@@ -45,57 +51,6 @@ GF_DEV void stage_weights(MlpSmem& S, const float* __restrict__ W) {
   }
   if (threadIdx.x == 0) S.b3 = W[oB3];
   __syncthreads();
-}
-
-// Forward, one thread per variable: h1 in registers, h2 unit by unit with
-// the W2 row read from shared memory (broadcast across the warp).
-GF_DEV float mlp_logit(const MlpSmem& S, const float (&f)[kF], float (&h1)[kH]) {
-#pragma unroll
-  for (int a = 0; a < kH; ++a) {
-    float s = S.b1[a];
-#pragma unroll
-    for (int q = 0; q < kF; ++q) s = fmaf(S.W1[a * kF + q], f[q], s);
-    h1[a] = fmaxf(s, 0.0f);
-  }
-  float z = S.b3;
-  for (int a = 0; a < kH; ++a) {
-    const float4* w = reinterpret_cast<const float4*>(S.W2 + a * kH);
-    float s = S.b2[a];
-#pragma unroll
-    for (int q4 = 0; q4 < kH / 4; ++q4) {
-      const float4 ww = w[q4];
-      s = fmaf(ww.x, h1[4 * q4], s);
-      s = fmaf(ww.y, h1[4 * q4 + 1], s);
-      s = fmaf(ww.z, h1[4 * q4 + 2], s);
-      s = fmaf(ww.w, h1[4 * q4 + 3], s);
-    }
-    z = fmaf(S.w3[a], fmaxf(s, 0.0f), z);
-  }
-  return z;
-}
-
-GF_DEV float clip_sigmoid(float z) {
-  const float p = 1.0f / (1.0f + expf(-z));
-  return fminf(fmaxf(p, 1e-4f), 1.0f - 1e-4f);
-}
-
-__global__ void __launch_bounds__(128)
-k_mlp_fwd(const float* __restrict__ W, int64_t nv, const float* __restrict__ feat,
-          float* __restrict__ z_out, float* __restrict__ p_out,
-          const uint8_t* __restrict__ live) {
-  extern __shared__ float4 smem4[];
-  MlpSmem& S = *reinterpret_cast<MlpSmem*>(smem4);
-  stage_weights(S, W);
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    float f[kF];
-#pragma unroll
-    for (int q = 0; q < kF; ++q) f[q] = feat[v * kF + q];
-    float h1[kH];
-    const float z = mlp_logit(S, f, h1);
-    if (z_out) z_out[v] = z;
-    if (p_out) p_out[v] = (live && !live[v]) ? 0.0f : clip_sigmoid(z);
-  }
 }
 
 // Loss and gradient over a block of 128 variables (one per thread).  The
@@ -366,28 +321,23 @@ __global__ void k_features(int64_t N, const float* __restrict__ x, const float* 
 static_assert(offsetof(MlpSmem, W2) % 16 == 0, "W2 must be 16-byte aligned");
 static_assert(offsetof(GradSmem, H1) % 16 == 0 && offsetof(GradSmem, H2) % 16 == 0,
               "tiles must be 16-byte aligned");
-size_t fwd_smem() { return sizeof(MlpSmem) + 16; }
 size_t grad_smem() { return sizeof(GradSmem) + 16; }
 
 cudaError_t set_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fwd_smem());
-  if (!e) e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)grad_smem());
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)grad_smem());
   if (!e) done = true;
   return e;
 }
 
+// Forward pass on the tensor cores (k_mlp_tc.cu); err: device error word
+// of a handle, or NULL (outputs NaN if the tensor cores never answered).
 cudaError_t mlp_forward(const float* W, int64_t nv, const float* feat, float* z, float* p,
-                        const uint8_t* live, cudaStream_t s) {
-  cudaError_t e = set_attrs();
-  if (e) return e;
-  int blocks = (int)std::min<int64_t>((nv + 127) / 128, 148 * 8);
-  if (blocks < 1) blocks = 1;
-  k_mlp_fwd<<<blocks, 128, fwd_smem(), s>>>(W, nv, feat, z, p, live);
-  return cudaGetLastError();
+                        const uint8_t* live, cudaStream_t s, uint64_t limit_ns = 2000000000ull,
+                        int* err = nullptr) {
+  return gf_mlp_forward_tc(W, nv, feat, z, p, live, limit_ns, err, s);
 }
 
 }  // namespace
@@ -564,7 +514,9 @@ cudaError_t gf_launch_features(GfCtx* h) {
 cudaError_t gf_launch_mlp_proposal(GfCtx* h) {
   if (!h->mlp_W || !h->feat) return cudaErrorInvalidValue;
   h->launches++;
-  return mlp_forward(h->mlp_W, h->N, h->feat, h->p_learn_z, h->p_learn, h->var_live, h->stream);
+  const uint64_t limit = (uint64_t)(std::max(0.01, h->prm.wait_timeout_s) * 1e9);
+  return mlp_forward(h->mlp_W, h->N, h->feat, h->p_learn_z, h->p_learn, h->var_live, h->stream,
+                     limit, &h->dstate->error);
 }
 
 extern "C" gfors_status gfors_set_proposal(gfors_handle h, const float* W, int64_t nW) {

@@ -50,6 +50,29 @@ def test_mlp_forward_matches_oracle():
     assert np.all(np.abs(p.cpu().numpy() - po) <= 1e-5)
 
 
+def test_mlp_forward_many_tiles_matches_oracle():
+    """The tensor-core forward over many 128-variable tiles per CTA and a
+    ragged last tile: sampled rows against the FP64 oracle, p in range, the
+    live mask applied through a handle-free call (p for every row)."""
+    import torch
+    nv = 200_003
+    f, y, Wp = _data(nv, 7)
+    f *= np.float32(3.0)                        # larger activations
+    z = torch.zeros(nv, device="cuda")
+    p = torch.zeros(nv, device="cuda")
+    Wd = torch.from_numpy(Wp).cuda()
+    fd = torch.from_numpy(f).cuda()
+    G.mlp_forward(Wd.data_ptr(), nv, fd.data_ptr(), z.data_ptr(), p.data_ptr())
+    zg = z.cpu().numpy().astype(np.float64)
+    pg = p.cpu().numpy()
+    idx = np.unique(np.concatenate([np.random.default_rng(1).integers(0, nv, 1500),
+                                    np.arange(nv - 200, nv), np.arange(0, 200)]))
+    zo, po = O.mlp_forward(f[idx], _unpack(Wp), rb=1)
+    assert np.all(np.abs(zg[idx] - zo) <= 1e-5 * (1 + np.abs(zo)))
+    assert np.all(np.abs(pg[idx] - po) <= 1e-5)
+    assert np.all((pg >= 1e-4 - 1e-9) & (pg <= 1 - 1e-4 + 1e-9))
+
+
 def test_mlp_gradient_matches_oracle():
     import torch
     nv = 700                                   # several blocks and a ragged tail
