@@ -37,6 +37,11 @@ WORKLOADS = {
     "setcover": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).set_cover(
         n=2000, m=200, density=0.05, idx=r), 50, 1024,
         "set cover n=2000 m=200 Bernoulli(0.05), 1024 candidates/round, k_int=50"),
+    "setcover_batch": (lambda r: [__import__("paper_2510_27117_b300.workloads", fromlist=["x"])
+                                  .set_cover(n=2000, m=200, density=0.05, idx=1024 * r + q)
+                                  for q in range(1024)], 50, 1024,
+                       "1024 set-cover instances n=2000 m=200 Bernoulli(0.05), 1024 "
+                       "candidates/instance/round, k_int=50"),
     "knapsack": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).knapsack_batch(
         ninst=512, idx=r), 50, 4096,
         "512 knapsacks n_i~U[1e3,1e5], 4096 candidates/instance/round, k_int=50"),
@@ -52,8 +57,10 @@ WORKLOADS = {
                  "(random-init weights)"),
 }
 # rounds per step and proposal (0 plain x_k, 1 learned) of each workload
-ROUNDS = {"maxcut": 1, "setcover": 1, "knapsack": 1, "assign3d": 1, "facility": 4}
-PROPOSAL = {"maxcut": 0, "setcover": 0, "knapsack": 0, "assign3d": 1, "facility": 1}
+ROUNDS = {"maxcut": 1, "setcover": 1, "setcover_batch": 1, "knapsack": 1, "assign3d": 1,
+          "facility": 4}
+PROPOSAL = {"maxcut": 0, "setcover": 0, "setcover_batch": 0, "knapsack": 0, "assign3d": 1,
+            "facility": 1}
 
 
 def env_rank():
@@ -147,6 +154,8 @@ def run_ours(args, rank, world, local):
     single = args.workload == "maxcut"
     inst = build(0 if single else rank)
     insts = inst if isinstance(inst, list) else [inst]
+    if args.instances:                       # a smaller batch (profiling runs)
+        insts = insts[:args.instances]
     stream = torch.cuda.Stream()
     prm = G.default_params(k_int=k_int, k_b=k_b * (world if single else 1),
                            seed=0x5EED0000 + 1, x0=-1.0,
@@ -232,12 +241,16 @@ def run_ours(args, rank, world, local):
 
     # ---- roofline of the dominant kernel (phase timed with events on the stream)
     peaks, src = load_peaks()
-    roof = roofline(args.workload, insts, k_int, k_b * nr, prof, peaks, src, args.steps)
+    dinfo = H.dense_info(0)
+    roof = roofline(args.workload, insts, k_int, k_b * nr, prof, peaks, src, args.steps,
+                    fp8=dinfo["fp8"])
     out = {
         "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 PDHG / bf16 scoring / int64 evaluation", "data": "synthetic (seeded)",
+        "dtype": ("f32 PDHG / " + ("fp8 e4m3" if dinfo["fp8"] else "bf16") +
+                  " tensor-core scoring / int64 evaluation") if dinfo["dense"] else
+                 "f32 PDHG / int64 evaluation", "data": "synthetic (seeded)",
         "config": {"workload": desc, "global_batch": cands * world, "n": insts[0].n,
                    "instances": len(insts), "k_int": k_int, "k_b": k_b, "k_r": nr,
                    "proposal": ["plain", "learned"][prop],
@@ -288,7 +301,7 @@ def run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr=1, prop=0, srange=N
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps}
 
 
-def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps):
+def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False):
     """Roofline of the dominant phase of the step (largest share of the
     event-timed step), with the tensor-core scorer reported beside it."""
     phases = {k: v for k, v in prof.items() if v[1]}
@@ -305,9 +318,14 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps):
         if cnt:
             flops = 2.0 * n * n * k_b
             ach = flops / (ms / cnt / 1e3) / 1e12
+            # FP8 operands: the measured bf16 peak x the nominal fp8/bf16 ratio (2)
+            pk = peaks.get("bf16_tflops", 1800.0) * (2.0 if fp8 else 1.0)
             tc = {"kernel": "k_score_tc (tcgen05 W2.X^T + fused reduction)", "bound": "tensor",
-                  "achieved": ach, "peak": peaks.get("bf16_tflops", 1800.0), "unit": "TFLOP/s",
-                  "frac": ach / peaks.get("bf16_tflops", 1800.0), "traffic": None,
+                  "dtype": "fp8 e4m3" if fp8 else "bf16",
+                  "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                  "peak_note": ("measured bf16 burst x 2 (nominal fp8/bf16)" if fp8
+                                else "measured bf16 burst"),
+                  "traffic": None,
                   "algorithmic_per_launch": f"2 n^2 k_b = {flops:.4e} FLOP"}
         if dom == "pdhg":
             ms, iters = phases["pdhg"]
@@ -327,6 +345,7 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps):
     nnz = sum(I.nnz() for I in insts)
     m = sum(I.m1 + I.m2 for I in insts)
     alg = {"setcover": (16 * nnz + 4 * (6 * n + 4 * m), "2 nnz (4+4) + 4 (6n + 4m)"),
+           "setcover_batch": (16 * nnz + 4 * (6 * n + 4 * m), "2 nnz (4+4) + 4 (6n + 4m)"),
            "knapsack": (16 * n, "16 sum n_i (read x, w, c; write x)"),
            "assign3d": (16 * nnz, "16 nnz"),
            "facility": (16 * nnz + 24 * n + 16 * m, "2 nnz 8 + 24 n + 16 m")}[workload]
@@ -580,6 +599,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maxcut", choices=list(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--instances", type=int, default=0,
+                    help="use only the first N instances of a batch workload")
     ap.add_argument("--time-to-gap", action="store_true",
                     help="measure time to <=1%% gap (plain vs batched / learned+batched) "
                          "on --workload assign3d or knapsack instead of throughput")

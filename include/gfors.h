@@ -99,7 +99,10 @@ typedef struct {
                           (single-row instances), 3 dense tensor-core
                           scoring (dense small-integer Q), 4 dense scoring
                           on CUDA cores (checking), 5 one-CTA tensor-core
-                          scoring instead of the two-CTA cluster kernel     */
+                          scoring instead of the two-CTA cluster kernel,
+                          6 tensor-core scoring with bf16 operands (auto
+                          uses FP8 E4M3 operands when every entry of
+                          offdiag(Q+Q^T) is exact in E4M3)                  */
   double power_tol;    /* power-iteration stop tolerance; 1e-12            */
   int32_t power_maxit; /* power-iteration cap; 5000                         */
   double wait_timeout_s;/* limit of every device-side wait; 2.0             */
@@ -361,6 +364,13 @@ GFORS_API gfors_status gfors_tune_cache_lookup(const char* path, const char* key
                                                int32_t lanes[10], int32_t* found);
 GFORS_API gfors_status gfors_tune_cache_store(const char* path, const char* key,
                                               const int32_t lanes[10]);
+
+/* Dense-Q scoring of instance inst: out[0] = 1 if Q is held as a dense
+ * small-integer matrix, out[1] = 1 if the tensor-core scorer is exact for it
+ * (n max|W2| < 2^24 and int32 tile partials), out[2] = 1 if it scores with
+ * FP8 E4M3 operands (else bf16), out[3] = max|W2|, W2 = offdiag(Q + Q^T).
+ * Host only. */
+GFORS_API gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t out[4]);
 
 /* ---- Several devices (Section 3's sampling rounds split by candidate).
  * gfors_sample_eval_range: as gfors_sample_eval, but only candidates

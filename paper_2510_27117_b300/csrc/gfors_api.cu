@@ -43,22 +43,29 @@ __global__ void k_unpack_bits(const uint32_t* __restrict__ X, int k, int64_t n, 
   Xb[gid] = (X[(v0 + i) * kws + (s >> 5)] >> (s & 31)) & 1u;
 }
 
+// Dense-Q candidate operand element: bf16 1.0 = 0x3F80, FP8 E4M3 1.0 = 0x38.
+__device__ __forceinline__ void put_cand(void* Xs, int64_t idx, bool one, int f8) {
+  if (f8) reinterpret_cast<uint8_t*>(Xs)[idx] = one ? 0x38u : 0u;
+  else reinterpret_cast<uint16_t*>(Xs)[idx] = one ? 0x3F80u : 0u;
+}
+
 __global__ void k_pack_dense(const uint8_t* __restrict__ Xb, int k, int64_t n, int64_t ld,
-                             __nv_bfloat16* __restrict__ Xs) {
+                             void* __restrict__ Xs, int f8) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (int64_t)k * ld) return;
   const int s = (int)(gid / ld);
   const int64_t i = gid % ld;
-  Xs[gid] = __float2bfloat16((i < n && Xb[(int64_t)s * n + i]) ? 1.0f : 0.0f);
+  put_cand(Xs, gid, i < n && Xb[(int64_t)s * n + i], f8);
 }
 
-__global__ void k_unpack_dense(const __nv_bfloat16* __restrict__ Xs, int k, int64_t n,
-                               int64_t ld, uint8_t* __restrict__ Xb) {
+// candidate bytes from the bit words Xb[s * ld/32 + w]
+__global__ void k_unpack_dense(const uint32_t* __restrict__ Xw, int k, int64_t n, int64_t ld,
+                               uint8_t* __restrict__ Xb) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (int64_t)k * n) return;
   const int s = (int)(gid / n);
   const int64_t i = gid % n;
-  Xb[gid] = __bfloat162float(Xs[(int64_t)s * ld + i]) != 0.0f;
+  Xb[gid] = (Xw[(int64_t)s * (ld / 32) + i / 32] >> (i & 31)) & 1u;
 }
 
 // round(x_k) as candidate 0 (bits and dense operands)
@@ -69,10 +76,10 @@ __global__ void k_round_bits(const float* __restrict__ x, const uint8_t* __restr
   X[i * kws] = (live[i] && x[i] > 0.5f) ? 1u : 0u;
 }
 __global__ void k_round_dense(const float* __restrict__ x, int64_t v0, int64_t n, int64_t ld,
-                              __nv_bfloat16* __restrict__ Xs) {
+                              void* __restrict__ Xs, int f8) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ld) return;
-  Xs[i] = __float2bfloat16((i < n && x[v0 + i] > 0.5f) ? 1.0f : 0.0f);
+  put_cand(Xs, i, i < n && x[v0 + i] > 0.5f, f8);
 }
 __global__ void k_set_round(GfDState* st, unsigned v) { st->round_id = v; }
 
@@ -343,6 +350,20 @@ extern "C" gfors_status gfors_sample_eval(gfors_handle h, int32_t nrounds,
   return sample_rounds(h, nrounds, proposal, 0, h->prm.k_b);
 }
 
+extern "C" gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t out[4]) {
+  if (!h || !out || inst < 0 || inst >= h->ninst) return GFORS_E_ARG;
+  out[0] = out[1] = out[2] = out[3] = 0;
+  const GfInstHost& I = h->ih[inst];
+  if (I.qkind == 1) {
+    const GfDenseQ& dq = h->dense[I.dense_idx];
+    out[0] = 1;
+    out[1] = dq.tc_ok && h->prm.eval_mode != 4;
+    out[2] = dq.f8;
+    out[3] = dq.w2max;
+  }
+  return GFORS_OK;
+}
+
 extern "C" gfors_status gfors_sample_eval_range(gfors_handle h, int32_t nrounds,
                                                 uint32_t first_round_id, int32_t proposal,
                                                 int32_t s_begin, int32_t s_end) {
@@ -387,9 +408,9 @@ static cudaError_t enqueue_final_round(GfCtx* h) {
   for (const GfDenseQ& dq : h->dense)
   {
     k_round_dense<<<(unsigned)((dq.ld + 255) / 256), 256, 0, h->stream>>>(
-        xk, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.Xs);
+        xk, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.Xs, (int)dq.f8);
     k_dense_bits<<<(unsigned)((dq.ld / 32 + 255) / 256), 256, 0, h->stream>>>(dq.Xs, 1, dq.ld,
-                                                                               dq.Xb);
+                                                                               dq.Xb, (int)dq.f8);
   }
   h->launches += 2 + (long long)h->dense.size();
   if ((e = gf_launch_eval(h, 0, 1))) return e;
@@ -642,9 +663,9 @@ extern "C" gfors_status gfors_eval_candidates(gfors_handle h, int32_t inst, int3
     if (I.qkind == 1) {
       const GfDenseQ& dq = h->dense[I.dense_idx];
       k_pack_dense<<<(unsigned)(((int64_t)len * dq.ld + 255) / 256), 256, 0, h->stream>>>(
-          Xd, len, I.n, dq.ld, dq.Xs);
+          Xd, len, I.n, dq.ld, dq.Xs, (int)dq.f8);
       k_dense_bits<<<(unsigned)(((int64_t)len * (dq.ld / 32) + 255) / 256), 256, 0,
-                     h->stream>>>(dq.Xs, len, dq.ld, dq.Xb);
+                     h->stream>>>(dq.Xs, len, dq.ld, dq.Xb, (int)dq.f8);
     } else {
       const int kwu = (len + 31) / 32;
       k_pack_bits<<<(unsigned)((I.n * kwu + 255) / 256), 256, 0, h->stream>>>(Xd, len, I.n,
@@ -687,7 +708,7 @@ extern "C" gfors_status gfors_get_samples(gfors_handle h, int32_t inst, uint8_t*
     if (I.qkind == 1) {
       const GfDenseQ& dq = h->dense[I.dense_idx];
       k_unpack_dense<<<(unsigned)(((int64_t)len * I.n + 255) / 256), 256, 0, h->stream>>>(
-          dq.Xs, len, I.n, dq.ld, Xd);
+          dq.Xb, len, I.n, dq.ld, Xd);
     } else {
       if (h->last_mode == 1) {
         // fused chunks are not materialised: regenerate the same draws

@@ -17,6 +17,8 @@
 #include <stdexcept>
 #include <thread>
 
+#include <cuda_fp8.h>
+
 #include "internal.cuh"
 
 static thread_local std::string g_thread_err;
@@ -737,6 +739,25 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       const std::vector<__nv_bfloat16>& wb = st[dq.inst].dense_w2;
       for (size_t t = 0; t < w8.size(); ++t) w8[t] = (int8_t)__bfloat162float(wb[t]);
       UP(dq.W2i8, w8.data(), int8_t, w8.size());
+    }
+    // FP8 E4M3 copy for the tensor-core scorer when every entry of W2 is
+    // exactly representable in E4M3 (3 mantissa bits: all integers up to 16,
+    // even ones up to 32, ...); the 0/1 candidates always are
+    if (dq.tc_ok && P.eval_mode != 4 && P.eval_mode != 6) {
+      std::vector<uint8_t> w8((size_t)dq.n * dq.ld);
+      const std::vector<__nv_bfloat16>& wb = st[dq.inst].dense_w2;
+      bool exact = true;
+      for (size_t t = 0; t < w8.size() && exact; ++t) {
+        const float v = __bfloat162float(wb[t]);
+        const __nv_fp8_e4m3 q(v);
+        exact = (float)q == v;
+        w8[t] = q.__x;
+      }
+      if (exact) {
+        ALLOC(dq.W2f8, uint8_t, dq.n * dq.ld);
+        UP(dq.W2f8, w8.data(), uint8_t, w8.size());
+        dq.f8 = true;
+      }
     }
     ALLOC(dq.qdiag, float, dq.ld);
     ALLOC(dq.lin, long long, dq.ld);

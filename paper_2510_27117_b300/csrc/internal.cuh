@@ -82,10 +82,13 @@ struct GfDenseQ {                   // dense +-small-integer Q (tensor-core path
   float* qdiag = nullptr;           // diag(Q_sym) / s_obj
   float qscale = 0.f;               // 0.5 / s_obj
   long long* lin = nullptr;         // c_i + Q_ii (original, integer)
-  __nv_bfloat16* Xs = nullptr;      // candidates, sample-major, chunk x ld
+  uint8_t* W2f8 = nullptr;          // same as FP8 E4M3 when max|W2| <= 16 (scoring)
+  __nv_bfloat16* Xs = nullptr;      // candidates, sample-major, chunk x ld (bf16, or
+                                    // FP8 E4M3 bytes in the same buffer when f8)
   uint32_t* Xb = nullptr;           // same as bit words, chunk x ld/32
   int chunk = 0;
   bool tc_ok = false;               // tensor-core scoring exact (n max|W2| < 2^24)
+  bool f8 = false;                  // score with FP8 operands (exact, twice the rate)
   long long w2max = 0;
 };
 
@@ -309,8 +312,8 @@ int gf_prof_begin(GfCtx* h, int phase);
 void gf_prof_end(GfCtx* h, int idx, int count);
 
 // bit words of bf16 candidate rows (k_sample.cu)
-__global__ void k_dense_bits(const __nv_bfloat16* __restrict__ Xs, int len, int64_t ld,
-                             uint32_t* __restrict__ Xb);
+__global__ void k_dense_bits(const void* __restrict__ Xs, int len, int64_t ld,
+                             uint32_t* __restrict__ Xb, int f8);
 
 // helpers used by several files
 int64_t gf_round_up(int64_t v, int64_t m);

@@ -495,14 +495,14 @@ k_extract(const GfInc* __restrict__ inc, const int32_t* __restrict__ var_inst,
 }
 
 __global__ void k_extract_dense(const GfInc* __restrict__ inc, int b, int64_t v0, int64_t n,
-                                int64_t ld, const __nv_bfloat16* __restrict__ Xs, int s0,
+                                int64_t ld, const uint32_t* __restrict__ Xw, int s0,
                                 uint8_t* __restrict__ xbest) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const GfInc I = inc[b];
   if (!I.changed) return;
   const int sl = I.sample - s0;
-  xbest[v0 + i] = __bfloat162float(Xs[(int64_t)sl * ld + i]) != 0.0f;
+  xbest[v0 + i] = (Xw[(int64_t)sl * (ld / 32) + i / 32] >> (i & 31)) & 1u;
 }
 
 __global__ void k_round_end(GfDState* st) { st->round_id += 1u; }
@@ -580,7 +580,7 @@ cudaError_t gf_launch_incumbent(GfCtx* h, int s0, int len, int mode, bool last_c
   }
   for (const GfDenseQ& dq : h->dense) {
     k_extract_dense<<<(unsigned)((dq.n + 255) / 256), 256, 0, h->stream>>>(
-        h->inc, dq.inst, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.Xs, s0, h->xbest);
+        h->inc, dq.inst, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.Xb, s0, h->xbest);
     h->launches++;
   }
   if (last_chunk) {

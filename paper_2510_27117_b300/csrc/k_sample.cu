@@ -218,6 +218,106 @@ k_axial(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, int le
   }
 }
 
+// Same draw with the slab's weights staged in shared memory (I*I <= 4096):
+// per step i the block loads floor(p 2^24) of slab i once, coalesced, with
+// the used rows/columns already masked to 0 (bit masks of j and k), then
+// scans and picks from shared memory.  Identical picks to k_axial.
+constexpr int kAxMaxP = 4096;
+__global__ void __launch_bounds__(kAxThreads)
+k_axial_sm(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, int len,
+           int kw, uint64_t seed, int inst_base, const GfDState* __restrict__ st,
+           uint32_t* __restrict__ X) {
+  const int sidx = blockIdx.x;
+  if (sidx >= len) return;
+  const uint32_t s = (uint32_t)(s0 + sidx);
+  __shared__ uint32_t wt[kAxMaxP];
+  __shared__ unsigned long long wsum[kAxThreads / 32];
+  __shared__ unsigned long long sh_r, sh_W;
+  __shared__ int sh_pick;
+  __shared__ unsigned long long usedJ, usedK;          // bit j / k: already used
+  if (threadIdx.x == 0) { usedJ = 0ull; usedK = 0ull; }
+  const int P = I * I;
+  const int per = (P + kAxThreads - 1) / kAxThreads;
+  const int q0 = threadIdx.x * per, q1 = min(P, q0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int dj = kAxThreads / I, dk = kAxThreads % I;   // stride of q in (j, k)
+  const int j00 = threadIdx.x / I, k00 = threadIdx.x % I;
+  const uint32_t round = st->round_id;
+  __syncthreads();
+  for (int i = 0; i < I; ++i) {
+    const float* pi = p + v0 + (int64_t)i * P;
+    const unsigned long long uj = usedJ, uk = usedK;
+    int j = j00, k = k00;
+    for (int q = threadIdx.x; q < P; q += kAxThreads) {
+      const bool used = ((uj >> j) | (uk >> k)) & 1ull;
+      wt[q] = used ? 0u : gf::prob_threshold(__ldg(pi + q));
+      j += dj;
+      k += dk;
+      if (k >= I) { k -= I; ++j; }
+    }
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (int q = q0; q < q1; ++q) mine += wt[q];
+    unsigned long long v = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, v, off);
+      if (lane >= off) v += o;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    unsigned long long wbase = 0, tot = 0;
+    for (int q = 0; q < kAxThreads / 32; ++q) {
+      if (q < warp) wbase += wsum[q];
+      tot += wsum[q];
+    }
+    const unsigned long long excl = wbase + v - mine;
+    if (threadIdx.x == 0) {
+      const uint4 u4 = gf::philox_call(seed, gf::kStreamAxial, (uint32_t)(inst_base + inst),
+                                       round, s, (uint64_t)(i >> 2));
+      const uint32_t u = gf::lane_of(u4, (uint32_t)(i & 3));
+      sh_W = tot;
+      if (tot > 0) {
+        const unsigned long long lo = (unsigned long long)u * tot;
+        const unsigned long long hi = __umul64hi((unsigned long long)u, tot);
+        sh_r = (hi << 32) | (lo >> 32);
+      } else {
+        const int free = I - i;
+        sh_r = ((unsigned long long)u * (unsigned long long)(free * free)) >> 32;
+      }
+      sh_pick = -1;
+    }
+    __syncthreads();
+    const unsigned long long r = sh_r;
+    if (sh_W > 0) {
+      if (mine > 0 && excl <= r && r < excl + mine) {
+        unsigned long long acc = excl;
+        for (int q = q0; q < q1; ++q) {
+          acc += wt[q];
+          if (wt[q] && acc > r) { sh_pick = q; break; }
+        }
+      }
+    } else if (threadIdx.x == 0) {
+      // r-th allowed pair in row-major order: (a-th free j, b-th free k)
+      const int free = I - i;
+      int a = (int)(r / free), bb = (int)(r % free), jj = -1, kk = -1;
+      for (int q = 0, c = 0; q < I; ++q) if (!((uj >> q) & 1ull)) { if (c == a) { jj = q; break; } ++c; }
+      for (int q = 0, c = 0; q < I; ++q) if (!((uk >> q) & 1ull)) { if (c == bb) { kk = q; break; } ++c; }
+      sh_pick = jj * I + kk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int q = sh_pick;
+      const int jj = q / I, kk = q - jj * I;
+      usedJ |= 1ull << jj;
+      usedK |= 1ull << kk;
+      const int64_t var = v0 + (int64_t)i * P + q;
+      atomicOr(&X[var * kw + (sidx >> 5)], 1u << (sidx & 31));
+    }
+    __syncthreads();
+  }
+}
+
 // Closure repair (Section 2.4.3): rep_var[q] |= OR of its list, per word.
 // One block per repaired variable; thread tid owns word tid % kw.
 __global__ void k_closure(const int64_t* __restrict__ rv, const int64_t* __restrict__ rp,
@@ -250,7 +350,7 @@ __global__ void k_closure(const int64_t* __restrict__ rv, const int64_t* __restr
 __global__ void __launch_bounds__(256)
 k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld,
             int s0, uint64_t seed, int inst, const GfDState* __restrict__ st,
-            __nv_bfloat16* __restrict__ Xs, uint32_t* __restrict__ Xb) {
+            void* __restrict__ Xs, uint32_t* __restrict__ Xb, int f8) {
   const int64_t n4 = ld / 4;
   const int64_t g4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g4 >= n4) return;
@@ -267,11 +367,18 @@ k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld,
     b[2] = (i0 + 2 < n) && (u.z >> 8) < gf::prob_threshold(pv.z);
     b[3] = (i0 + 3 < n) && (u.w >> 8) < gf::prob_threshold(pv.w);
   }
-  // bf16 one = 0x3F80
-  uint2 out;
-  out.x = (b[0] ? 0x3F80u : 0u) | ((b[1] ? 0x3F80u : 0u) << 16);
-  out.y = (b[2] ? 0x3F80u : 0u) | ((b[3] ? 0x3F80u : 0u) << 16);
-  reinterpret_cast<uint2*>(Xs + (int64_t)sidx * ld)[g4] = out;
+  if (f8) {
+    // FP8 E4M3 one = 0x38
+    const uint32_t out = (b[0] ? 0x38u : 0u) | ((b[1] ? 0x38u : 0u) << 8) |
+                         ((b[2] ? 0x38u : 0u) << 16) | ((b[3] ? 0x38u : 0u) << 24);
+    reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(Xs) + (int64_t)sidx * ld)[g4] = out;
+  } else {
+    // bf16 one = 0x3F80
+    uint2 out;
+    out.x = (b[0] ? 0x3F80u : 0u) | ((b[1] ? 0x3F80u : 0u) << 16);
+    out.y = (b[2] ? 0x3F80u : 0u) | ((b[3] ? 0x3F80u : 0u) << 16);
+    reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(Xs) + (int64_t)sidx * ld)[g4] = out;
+  }
   // ld/4 is a multiple of 16, so the 8 lanes holding one 32-variable word
   // are always active together and belong to the same candidate
   const unsigned lane = threadIdx.x & 31u;
@@ -285,17 +392,22 @@ k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld,
 
 }  // namespace
 
-// Bit words of bf16 candidate rows (for writers other than the sampler).
-__global__ void k_dense_bits(const __nv_bfloat16* __restrict__ Xs, int len, int64_t ld,
-                             uint32_t* __restrict__ Xb) {
+// Bit words of bf16 / FP8 candidate rows (for writers other than the sampler).
+__global__ void k_dense_bits(const void* __restrict__ Xs, int len, int64_t ld,
+                             uint32_t* __restrict__ Xb, int f8) {
   const int64_t nw = ld / 32;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= nw * len) return;
   const int s = (int)(gid / nw);
   const int64_t w = gid % nw;
-  const unsigned short* row = reinterpret_cast<const unsigned short*>(Xs + (int64_t)s * ld);
   uint32_t m = 0;
-  for (int t = 0; t < 32; ++t) m |= (uint32_t)(row[32 * w + t] != 0) << t;
+  if (f8) {
+    const uint8_t* row = reinterpret_cast<const uint8_t*>(Xs) + (int64_t)s * ld;
+    for (int t = 0; t < 32; ++t) m |= (uint32_t)(row[32 * w + t] != 0) << t;
+  } else {
+    const uint16_t* row = reinterpret_cast<const uint16_t*>(Xs) + (int64_t)s * ld;
+    for (int t = 0; t < 32; ++t) m |= (uint32_t)(row[32 * w + t] != 0) << t;
+  }
   Xb[gid] = m;
 }
 
@@ -341,8 +453,12 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   for (int b = 0; b < h->ninst; ++b) {
     const GfInstHost& I = h->ih[b];
     if (I.group_mode != 2) continue;
-    k_axial<<<len, kAxThreads, 0, h->stream>>>(p, I.var_off, I.axial_I, b, s0, len, h->kw,
-                                               P.seed, P.inst_base, h->dstate, h->X);
+    if (I.axial_I <= 64 && I.axial_I * I.axial_I <= kAxMaxP)
+      k_axial_sm<<<len, kAxThreads, 0, h->stream>>>(p, I.var_off, I.axial_I, b, s0, len, h->kw,
+                                                    P.seed, P.inst_base, h->dstate, h->X);
+    else
+      k_axial<<<len, kAxThreads, 0, h->stream>>>(p, I.var_off, I.axial_I, b, s0, len, h->kw,
+                                                 P.seed, P.inst_base, h->dstate, h->X);
     h->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -362,7 +478,10 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
         const dim3 grid((unsigned)((dq.ld / 4 + 255) / 256), (unsigned)cnt);
         k_bern_bf16<<<grid, 256, 0, h->stream>>>(
             p, h->ih[dq.inst].var_off, dq.n, dq.ld, s0 + a, P.seed, P.inst_base + dq.inst,
-            h->dstate, dq.Xs + (int64_t)a * dq.ld, dq.Xb + (int64_t)a * (dq.ld / 32));
+            h->dstate,
+            dq.f8 ? (void*)(reinterpret_cast<uint8_t*>(dq.Xs) + (int64_t)a * dq.ld)
+                  : (void*)(dq.Xs + (int64_t)a * dq.ld),
+            dq.Xb + (int64_t)a * (dq.ld / 32), (int)dq.f8);
         h->launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
       }

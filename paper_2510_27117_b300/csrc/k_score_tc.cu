@@ -29,6 +29,8 @@ namespace {
 
 using namespace gf_tc;
 
+// BK: bf16 elements per 128-byte operand row of a stage (FP8 stages hold
+// 2 x BK elements in the same bytes)
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB
 constexpr int B_BYTES = BN * BK * 2;            // 32 KB
@@ -41,9 +43,14 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 4 * BN * 4 /*
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
 // N = 256, M = 128.
 constexpr uint32_t kIdesc = gf_tc::idesc_bf16(BM, BN);
+// FP8 (E4M3) operands: the same 128-byte rows hold 128 elements, every MMA
+// takes K = 32 (32 bytes of each row, as K = 16 in bf16).
+constexpr uint32_t kIdescF8 = gf_tc::idesc_e4m3(BM, BN);
 
-GF_DEV void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
-  gf_tc::mma_f16(d_tmem, a, b, kIdesc, accum);
+template <bool F8>
+GF_DEV void mma_op(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  if constexpr (F8) gf_tc::mma_f8f6f4(d_tmem, a, b, kIdescF8, accum);
+  else gf_tc::mma_f16(d_tmem, a, b, kIdesc, accum);
 }
 
 // CL = 1: one CTA per tile.  CL = 2: a cluster of two CTAs computes the
@@ -51,7 +58,7 @@ GF_DEV void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
 // shared candidate tile, multicast to both, so per-CTA operand traffic per
 // k-step drops from 48 KB to 32 KB; MMA completions are committed to both
 // CTAs' stage-release barriers (arrival count 2).
-template <int CL>
+template <int CL, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            int n, int64_t ld, int len, int num_m, int num_n, int num_k,
@@ -72,6 +79,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   __shared__ int ep_ok[4];                 // per-epilogue-warp wait results
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int KE = F8 ? 2 * BK : BK;     // K elements per stage (128-byte rows)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
   const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
   if (threadIdx.x == 0) {
@@ -118,13 +126,13 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
           if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, limit_ns, &abort_flag))) break;
           mbar_arrive_expect_tx(full0 + 8 * s, STAGE_BYTES);
-          tma_load_2d(smem_u32(stA + s * A_BYTES), &tmA, full0 + 8 * s, kb * BK, m0);
+          tma_load_2d(smem_u32(stA + s * A_BYTES), &tmA, full0 + 8 * s, kb * KE, m0);
           if constexpr (CL == 2) {
             // my half of the candidate tile, to both CTAs of the cluster
             tma_load_2d_mc(smem_u32(stB + s * B_BYTES + rank * (B_BYTES / 2)), &tmB,
-                           full0 + 8 * s, kb * BK, n0 + (int)rank * (BN / 2), (uint16_t)0x3);
+                           full0 + 8 * s, kb * KE, n0 + (int)rank * (BN / 2), (uint16_t)0x3);
           } else {
-            tma_load_2d(smem_u32(stB + s * B_BYTES), &tmB, full0 + 8 * s, kb * BK, n0);
+            tma_load_2d(smem_u32(stB + s * B_BYTES), &tmB, full0 + 8 * s, kb * KE, n0);
           }
         }
       }
@@ -156,8 +164,8 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           const uint32_t a0 = smem_u32(stA + s * A_BYTES), b0 = smem_u32(stB + s * B_BYTES);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
-            mma_bf16(d, sw128_desc(a0 + 32 * k), sw128_desc(b0 + 32 * k),
-                     (kb | k) != 0 ? 1u : 0u);
+            mma_op<F8>(d, sw128_desc(a0 + 32 * k), sw128_desc(b0 + 32 * k),
+                       (kb | k) != 0 ? 1u : 0u);
           if constexpr (CL == 2) mma_commit_mc(empty0 + 8 * s, (uint16_t)0x3);
           else mma_commit(empty0 + 8 * s);
         }
@@ -269,15 +277,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// 2-D tiled map over a row-major [rows x ld] operand of 2-byte (bf16) or
+// 1-byte (FP8) elements; boxes of box_inner x box_rows, 128-byte swizzle.
 bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
-              uint32_t box_inner, uint32_t box_rows) {
+              uint32_t box_inner, uint32_t box_rows, bool f8) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, rows};
-  cuuint64_t strides[1] = {ld * 2};
+  cuuint64_t strides[1] = {ld * (f8 ? 1 : 2)};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+  CUresult r = fn(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(base), dims, strides,
                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -302,20 +313,25 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
   static thread_local std::vector<TcCache> caches;
   if (caches.size() < 64) caches.resize(64);
   TcCache& C = caches[dq.inst % 64];
-  if (C.W2 != dq.W2 || C.Xs != dq.Xs) {
-    if (!make_map(&C.a, dq.W2, (uint64_t)dq.ld, (uint64_t)dq.n, (uint64_t)dq.ld, BK, BM) ||
-        !make_map(&C.b, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, BK, BN) ||
-        !make_map(&C.b2, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, BK,
-                  BN / 2))
+  const bool f8 = dq.f8;
+  const void* Wop = f8 ? (const void*)dq.W2f8 : (const void*)dq.W2;
+  const uint32_t ke = f8 ? 2 * BK : BK;      // elements in a 128-byte box row
+  if (C.W2 != Wop || C.Xs != dq.Xs) {
+    if (!make_map(&C.a, Wop, (uint64_t)dq.ld, (uint64_t)dq.n, (uint64_t)dq.ld, ke, BM, f8) ||
+        !make_map(&C.b, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, ke, BN,
+                  f8) ||
+        !make_map(&C.b2, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, ke,
+                  BN / 2, f8))
       return cudaErrorInvalidValue;
-    C.W2 = dq.W2;
+    C.W2 = Wop;
     C.Xs = dq.Xs;
   }
   if (!C.attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_score_tc<1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (!e) e = cudaFuncSetAttribute(k_score_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     SMEM_BYTES);
+    cudaError_t e = cudaSuccess;
+    for (const void* fn : {(const void*)k_score_tc<1, false>, (const void*)k_score_tc<2, false>,
+                           (const void*)k_score_tc<1, true>, (const void*)k_score_tc<2, true>})
+      if (!e) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES);
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -332,7 +348,7 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_score_tc<2>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_score_tc<2, false>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       ncl = 0;
     }
@@ -341,7 +357,7 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
   }
   const int num_m = (int)((dq.n + BM - 1) / BM);
   const int num_n = (len + BN - 1) / BN;
-  const int num_k = (int)(dq.ld / BK);
+  const int num_k = (int)((dq.ld + ke - 1) / ke);
   long long* out = h->obj + (int64_t)dq.inst * h->chunk;
   unsigned long long* outu = reinterpret_cast<unsigned long long*>(out);
   const uint64_t limit = (uint64_t)(std::max(0.01, h->prm.wait_timeout_s) * 1e9);
@@ -366,14 +382,21 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
     cfg.stream = h->stream;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_score_tc<2>, C.a, C.b2, nn, ld, ll, num_m, num_n, num_k, Xb,
-                           lin, outu, limit, st);
+    if (f8)
+      e = cudaLaunchKernelEx(&cfg, k_score_tc<2, true>, C.a, C.b2, nn, ld, ll, num_m, num_n,
+                             num_k, Xb, lin, outu, limit, st);
+    else
+      e = cudaLaunchKernelEx(&cfg, k_score_tc<2, false>, C.a, C.b2, nn, ld, ll, num_m, num_n,
+                             num_k, Xb, lin, outu, limit, st);
   } else {
     const int tiles = num_m * num_n;
     const int grid = std::min(tiles, C.sms > 0 ? C.sms : 148);
-    k_score_tc<1><<<grid, kThreads, SMEM_BYTES, h->stream>>>(C.a, C.b, nn, ld, ll, num_m,
-                                                             num_n, num_k, Xb, lin, outu,
-                                                             limit, st);
+    if (f8)
+      k_score_tc<1, true><<<grid, kThreads, SMEM_BYTES, h->stream>>>(
+          C.a, C.b, nn, ld, ll, num_m, num_n, num_k, Xb, lin, outu, limit, st);
+    else
+      k_score_tc<1, false><<<grid, kThreads, SMEM_BYTES, h->stream>>>(
+          C.a, C.b, nn, ld, ll, num_m, num_n, num_k, Xb, lin, outu, limit, st);
     e = cudaGetLastError();
   }
   if (e) return e;

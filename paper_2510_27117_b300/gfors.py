@@ -197,6 +197,12 @@ class Handle:
     def sample_eval(self, nrounds, first_round_id, proposal=0):
         _check(_lib.gfors_sample_eval(self.h, nrounds, first_round_id, proposal), self.h)
 
+    def dense_info(self, inst=0):
+        """(dense, tensor-core exact, fp8 operands, max|W2|) of instance inst."""
+        out = np.zeros(4, np.int64)
+        _check(_lib.gfors_dense_info(self.h, inst, _ptr(out)), self.h)
+        return dict(dense=bool(out[0]), tc=bool(out[1]), fp8=bool(out[2]), w2max=int(out[3]))
+
     def sample_eval_range(self, nrounds, first_round_id, proposal, s_begin, s_end):
         _check(_lib.gfors_sample_eval_range(self.h, nrounds, first_round_id, proposal,
                                             s_begin, s_end), self.h)
@@ -394,6 +400,7 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
 
 
 _lib.gfors_sample_eval_range.argtypes = [vp, i32, u32, i32, i32, i32]
+_lib.gfors_dense_info.argtypes = [vp, i32, vp]
 _lib.gfors_incumbent_key_async.argtypes = [vp, i32, vp]
 _lib.gfors_autotune.argtypes = [vp, C.c_char_p, vp, vp]
 _lib.gfors_set_lanes.argtypes = [vp, vp]

@@ -25,9 +25,12 @@ def _scores(inst, k_b, mode, R=5, seed=11):
 
 
 @pytest.mark.parametrize("n,k_b,mode", [(300, 96, 3), (200, 512, 3), (513, 288, 3),
-                                        (300, 96, 5), (513, 288, 5), (640, 1024, 3)])
+                                        (300, 96, 5), (513, 288, 5), (640, 1024, 3),
+                                        (513, 288, 6), (300, 96, 6)])
 def test_tc_matches_simt_and_oracle_small(n, k_b, mode):
-    """mode 3: two-CTA cluster kernel with multicast; mode 5: one-CTA kernel."""
+    """mode 3: two-CTA cluster kernel with multicast; mode 5: one-CTA kernel
+    (both with FP8 E4M3 operands for these +-1 graphs); mode 6: bf16
+    operands."""
     inst = W.max_cut(n=n, idx=7)
     p, X, viol, obj, inc = _scores(inst, k_b, mode)
     _, X2, viol2, obj2, inc2 = _scores(inst, k_b, 4)
@@ -45,7 +48,9 @@ def test_tc_full_size_round():
     p, X, viol, obj, inc = _scores(inst, 8192, 3)
     _, X2, viol2, obj2, inc2 = _scores(inst, 8192, 4)
     _, X5, viol5, obj5, inc5 = _scores(inst, 8192, 5)
+    _, X6, viol6, obj6, inc6 = _scores(inst, 8192, 6)
     assert np.array_equal(obj, obj2) and np.array_equal(obj, obj5)
+    assert np.array_equal(obj, obj6)
     assert inc["obj"] == inc2["obj"] and inc["sample"] == inc2["sample"]
     # sampled candidates scored by the oracle from its own draws
     Xo = O.sample(inst, p, 24, 11, 0, 5)
@@ -71,3 +76,17 @@ def test_dense_scoring_with_linear_term(mode):
     vo, oo = O.Evaluator(inst)(X)
     assert np.array_equal(obj, oo) and np.all(viol == 0)
     H.destroy()
+
+
+def test_tc_fp8_paper_weight_range():
+    """The paper's max-cut weights (integers in [-8, 10]): W2 = 2 w lies in
+    the even integers of [-16, 20], all exact in E4M3, so the FP8 scorer
+    runs; it must agree with bf16 tensor cores, CUDA cores and the oracle."""
+    inst = W.max_cut(n=700, idx=3, weights="int8_10")
+    p, X, viol, obj, inc = _scores(inst, 256, 3)
+    _, X6, _, obj6, _ = _scores(inst, 256, 6)
+    _, X4, _, obj4, _ = _scores(inst, 256, 4)
+    assert np.array_equal(X, X6) and np.array_equal(X, X4)
+    assert np.array_equal(obj, obj6) and np.array_equal(obj, obj4)
+    vo, oo = O.Evaluator(inst)(X)
+    assert np.array_equal(obj, oo)
