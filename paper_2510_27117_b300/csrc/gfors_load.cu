@@ -508,6 +508,32 @@ void gf_set_slot(GfCtx* h, int parity, double rho) {
                   cudaMemcpyHostToDevice, h->stream);
 }
 
+// Runs of a bucket's (ascending) ids: maximal stretches of consecutive ids of
+// one instance; uniform when all have the same length (ptr differences).
+// Used instead of the id list when there are at most kMaxRuns of them.
+constexpr int kMaxRuns = 4096;
+static bool make_runs(const std::vector<int32_t>& ids, const std::vector<int64_t>& ptr,
+                      const std::vector<int32_t>& inst_of, std::vector<GfRun>& runs,
+                      std::vector<int64_t>& run_ptr) {
+  runs.clear();
+  run_ptr.assign(1, 0);
+  for (size_t u = 0; u < ids.size(); ++u) {
+    const int32_t id = ids[u];
+    const int32_t len = (int32_t)(ptr[id + 1] - ptr[id]);
+    GfRun* R = runs.empty() ? nullptr : &runs.back();
+    if (R && id == R->first + R->count && inst_of[id] == R->inst) {
+      if (R->len != len) R->len = -1;
+      R->count++;
+    } else {
+      if ((int)runs.size() == kMaxRuns) return false;
+      runs.push_back(GfRun{id, ptr[id], 1, len, inst_of[id], 0});
+    }
+  }
+  int64_t acc = 0;
+  for (const GfRun& R : runs) run_ptr.push_back(acc += R.count);
+  return true;
+}
+
 static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A,
                               const double* const* b, const gfors_csr* const* B,
                               const double* const* d, const gfors_qmat* const* Q,
@@ -860,8 +886,18 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       B.lanes = lanes_of[bk];
       B.count = (int32_t)rl[bk].size();
       if (B.count) {
-        ALLOC(B.ids, int32_t, B.count);
-        UP(B.ids, rl[bk].data(), int32_t, B.count);
+        std::vector<GfRun> runs;
+        std::vector<int64_t> rptr;
+        if (make_runs(rl[bk], Kp, row_inst, runs, rptr)) {
+          B.nruns = (int32_t)runs.size();
+          ALLOC(B.runs, GfRun, runs.size());
+          ALLOC(B.run_ptr, int64_t, rptr.size());
+          UP(B.runs, runs.data(), GfRun, runs.size());
+          UP(B.run_ptr, rptr.data(), int64_t, rptr.size());
+        } else {
+          ALLOC(B.ids, int32_t, B.count);
+          UP(B.ids, rl[bk].data(), int32_t, B.count);
+        }
       }
       h->rb.push_back(B);
     }
@@ -905,8 +941,18 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       B.lanes = lanes_of[bk];
       B.count = (int32_t)cl[bk].size();
       if (B.count) {
-        ALLOC(B.ids, int32_t, B.count);
-        UP(B.ids, cl[bk].data(), int32_t, B.count);
+        std::vector<GfRun> runs;
+        std::vector<int64_t> rptr;
+        if (make_runs(cl[bk], Tp, var_inst, runs, rptr)) {
+          B.nruns = (int32_t)runs.size();
+          ALLOC(B.runs, GfRun, runs.size());
+          ALLOC(B.run_ptr, int64_t, rptr.size());
+          UP(B.runs, runs.data(), GfRun, runs.size());
+          UP(B.run_ptr, rptr.data(), int64_t, rptr.size());
+        } else {
+          ALLOC(B.ids, int32_t, B.count);
+          UP(B.ids, cl[bk].data(), int32_t, B.count);
+        }
       }
       h->cb.push_back(B);
     }

@@ -26,10 +26,23 @@ struct GfChunk {                    // one partial-sum chunk of a long row/col
   int64_t t0, t1;                   // nnz range
 };
 
+// Consecutive rows (columns) of one instance inside one length bucket.
+struct GfRun {
+  int64_t first;                    // first row / column id
+  int64_t nnz0;                     // offset of its first nonzero (uniform runs)
+  int32_t count;                    // rows / columns in the run
+  int32_t len;                      // common length, -1 if lengths differ
+  int32_t inst;
+  int32_t pad;
+};
+
 struct GfBucket {
   int lanes = 1;
-  int32_t* ids = nullptr;           // device row / column ids
+  int32_t* ids = nullptr;           // device row / column ids (when runs == nullptr)
   int32_t count = 0;
+  GfRun* runs = nullptr;            // device runs covering the bucket, in order
+  int64_t* run_ptr = nullptr;       // device prefix of run counts (nruns + 1)
+  int32_t nruns = 0;
 };
 
 struct GfLongSet {

@@ -11,11 +11,13 @@
 // tensor-core product w * piece is exact and the sums accumulate in FP32 in
 // TMEM -- the GEMMs carry FP32 activations, not bf16 ones.
 //
-// One persistent CTA per SM, tiles of 128 variables, 5 warps:
-//   warps 0-3  one thread per variable (TMEM lane = row): features ->
-//              pieces -> A1; TMEM D1 -> +b1, relu -> pieces -> A2; TMEM D2 ->
-//              +b2, relu, w3 dot -> z, p
-//   warp 4     MMA issuer (lane 0): layer 1 = 3 MMAs (M=N=128, K=16, one per
+// One persistent CTA per SM, tiles of 128 variables, 9 warps:
+//   warps 0-7  row warps: warp w serves TMEM lanes 32 (w mod 4) .. + 31 (one
+//              variable per lane) and hidden units 64 (w / 4) .. + 63: features
+//              -> pieces -> A1 (warps 0-3); TMEM D1 -> +b1, relu -> pieces ->
+//              A2; TMEM D2 -> +b2, relu, half of the w3 dot; the two halves of
+//              z meet in shared memory -> z, p
+//   warp 8     MMA issuer (lane 0): layer 1 = 3 MMAs (M=N=128, K=16, one per
 //              feature piece against W1 replicated at K offsets 0/16/32),
 //              layer 2 = 24 MMAs (3 pieces x 8 K-steps of 16) into D2
 // Operands are K-major, 128-byte swizzled, in shared memory; W1 and W2 are
@@ -30,7 +32,9 @@ namespace {
 using namespace gf_tc;
 
 constexpr int kF = 8, kH = 128, TM = 128;
-constexpr int kThreads = 160;
+constexpr int kThreads = 288;           // 8 row warps + 1 MMA warp
+constexpr int kRowThreads = 256;
+constexpr int kMmaWarp = 8;
 constexpr uint32_t kIdesc = idesc_bf16(128, 128);
 constexpr uint32_t TMEM_COLS = 256;          // D1 = columns [0, 128), D2 = [128, 256)
 constexpr int oW1 = 0, oB1 = kH * kF, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH,
@@ -42,7 +46,8 @@ constexpr int B1_OFF = A1_OFF + PANEL;       // W1 at K = 0, 16, 32
 constexpr int A2_OFF = B1_OFF + PANEL;       // h1: 3 pieces x 2 panels (K 0-63, 64-127)
 constexpr int B2_OFF = A2_OFF + 6 * PANEL;   // W2: 2 panels
 constexpr int VEC_OFF = B2_OFF + 2 * PANEL;  // b1, b2, w3 (FP32), b3
-constexpr int BAR_OFF = VEC_OFF + 3 * kH * 4 + 16;
+constexpr int ZP_OFF = VEC_OFF + 3 * kH * 4 + 16;   // z half sums [2][128]
+constexpr int BAR_OFF = ZP_OFF + 2 * 128 * 4;
 constexpr int SMEM_BYTES = BAR_OFF + 64 + 1024;
 
 // Byte offset of element (row r, k) of a K-major 128-byte-swizzled panel
@@ -101,6 +106,7 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
   float* b2s = b1s + kH;
   float* w3s = b2s + kH;
   float* b3s = w3s + kH;
+  float* zpart = reinterpret_cast<float*>(base + ZP_OFF);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + BAR_OFF);
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
@@ -141,7 +147,7 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
     mbar_init(mb2, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
                  "r"(TMEM_COLS));
@@ -157,6 +163,7 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
   int issued = 0;                             // commits issued (MMA warp)
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
     const uint32_t ph = (uint32_t)j & 1u;
+    const int qq = warp & 3, half = warp >> 2;  // TMEM lane quarter, hidden-unit half
     if (warp < 4) {
       // ---- features -> three bf16 pieces at K = 0, 16, 32 of A1
       const int r = threadIdx.x;
@@ -195,7 +202,7 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
     // A1 written (and the last tile's TMEM reads done); a wait that gave up
     // anywhere ends the loop for every thread alike
     if (named_bar_or(1, kThreads, abort_flag != 0)) break;
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
       if (lane == 0) {
         tc_fence_after();
 #pragma unroll
@@ -207,14 +214,15 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
       }
       __syncwarp();
     } else {
-      // ---- D1 -> +b1, relu -> three bf16 pieces of h1 into A2
-      const int r = threadIdx.x;
+      // ---- D1 -> +b1, relu -> three bf16 pieces of h1 into A2 (this warp's
+      // 64 hidden units = one K panel)
+      const int r = qq * 32 + lane;
       if (!mbar_wait(mb1, ph, limit_ns, &abort_flag)) abort_flag = 1;
       tc_fence_after();
 #pragma unroll 1
-      for (int c = 0; c < kH / 32; ++c) {
+      for (int c = 2 * half; c < 2 * half + 2; ++c) {
         uint32_t d[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), d);
+        tmem_ld32(tmem + ((uint32_t)(qq * 32) << 16) + (uint32_t)(c * 32), d);
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           float h[8];
@@ -231,7 +239,7 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
       tc_fence_before();
     }
     named_bar(2, kThreads);                   // A2 written, D1 read
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
       if (lane == 0) {
         tc_fence_after();
         const uint32_t d2 = tmem + 128u;
@@ -247,24 +255,27 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
       }
       __syncwarp();
     } else {
-      // ---- D2 -> +b2, relu, w3 dot -> z, p
-      const int r = threadIdx.x;
+      // ---- D2 -> +b2, relu, w3 dot over this warp's 64 units -> z, p
+      const int r = qq * 32 + lane;
       const int64_t v = t * TM + r;
       bool ok = mbar_wait(mb2, ph, limit_ns, &abort_flag);
       if (!ok) abort_flag = 1;
       tc_fence_after();
-      float z = b3s[0];
+      float zh = half ? 0.0f : b3s[0];
 #pragma unroll 1
-      for (int c = 0; c < kH / 32; ++c) {
+      for (int c = 2 * half; c < 2 * half + 2; ++c) {
         uint32_t d[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)(c * 32), d);
+        tmem_ld32(tmem + ((uint32_t)(qq * 32) << 16) + 128u + (uint32_t)(c * 32), d);
 #pragma unroll
         for (int q = 0; q < 32; ++q)
-          z = fmaf(w3s[32 * c + q],
-                   fmaxf(__fadd_rn(__uint_as_float(d[q]), b2s[32 * c + q]), 0.0f), z);
+          zh = fmaf(w3s[32 * c + q],
+                    fmaxf(__fadd_rn(__uint_as_float(d[q]), b2s[32 * c + q]), 0.0f), zh);
       }
       tc_fence_before();
-      if (v < nv) {
+      zpart[half * 128 + r] = zh;
+      named_bar(3, kRowThreads);              // both halves of z in shared memory
+      const float z = __fadd_rn(zpart[r], zpart[128 + r]);
+      if (half == 0 && v < nv) {
         if (!ok || abort_flag) {
           if (!err) {
             if (z_out) z_out[v] = __int_as_float(0x7FC00000);
@@ -278,7 +289,7 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
     }
   }
   __syncthreads();
-  if (warp == 4) {
+  if (warp == kMmaWarp) {
     // no MMA may still write TMEM when it is freed: wait (bounded) for the
     // last commit of each barrier
     if (lane == 0 && issued > 0) {
