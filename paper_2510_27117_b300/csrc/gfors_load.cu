@@ -1131,6 +1131,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     dq.chunk = h->chunk;
     ALLOC(dq.Xs, __nv_bfloat16, (size_t)h->chunk * dq.ld);
     ALLOC(dq.Xb, uint32_t, (size_t)h->chunk * (dq.ld / 32));
+    ALLOC(dq.thr, uint32_t, (size_t)dq.ld);
   }
   {
     std::vector<uint8_t> grouped(N, 0), idense(ninst, 0);

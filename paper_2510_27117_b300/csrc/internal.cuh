@@ -99,6 +99,7 @@ struct GfDenseQ {                   // dense +-small-integer Q (tensor-core path
   __nv_bfloat16* Xs = nullptr;      // candidates, sample-major, chunk x ld (bf16, or
                                     // FP8 E4M3 bytes in the same buffer when f8)
   uint32_t* Xb = nullptr;           // same as bit words, chunk x ld/32
+  uint32_t* thr = nullptr;          // Bernoulli thresholds of the current chunk (ld)
   int chunk = 0;
   bool tc_ok = false;               // tensor-core scoring exact (n max|W2| < 2^24)
   bool f8 = false;                  // score with FP8 operands (exact, twice the rate)

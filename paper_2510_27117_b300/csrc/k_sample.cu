@@ -218,103 +218,142 @@ k_axial(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, int le
   }
 }
 
-// Same draw with the slab's weights staged in shared memory (I*I <= 4096):
-// per step i the block loads floor(p 2^24) of slab i once, coalesced, with
-// the used rows/columns already masked to 0 (bit masks of j and k), then
-// scans and picks from shared memory.  Identical picks to k_axial.
+// Same draws as k_axial for I <= 64: a group of four warps (128 threads) per
+// candidate, four candidates per block.  Per step i the block stages
+// floor(p 2^24) of slab i once in shared memory; thread t of a group owns the
+// 32 pairs q in [32t, 32t + 32) (row-major; slots XOR-swizzled so that the
+// group reads them conflict-free).  When 32 divides I those pairs lie in one
+// row j, so the thread skips a used row at once and visits only the set bits
+// of its 32 available columns.  A scan across the group gives the prefixes and
+// the thread holding the crossing point finds the pick.  Identical picks to
+// k_axial (first pair, row-major, whose inclusive prefix exceeds r).
+GF_DEV void named_barrier(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 constexpr int kAxMaxP = 4096;
-__global__ void __launch_bounds__(kAxThreads)
-k_axial_sm(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, int len,
-           int kw, uint64_t seed, int inst_base, const GfDState* __restrict__ st,
-           uint32_t* __restrict__ X) {
-  const int sidx = blockIdx.x;
-  if (sidx >= len) return;
-  const uint32_t s = (uint32_t)(s0 + sidx);
+constexpr int kAxGroup = 128;                         // threads per candidate
+constexpr int kAxCands = 4;                           // candidates per block
+GF_DEV int ax_slot(int q) { return (q & ~31) | ((q & 31) ^ ((q >> 5) & 31)); }
+
+__global__ void __launch_bounds__(kAxGroup * kAxCands)
+k_axial_grp(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, int len,
+            int kw, uint64_t seed, int inst_base, const GfDState* __restrict__ st,
+            uint32_t* __restrict__ X) {
   __shared__ uint32_t wt[kAxMaxP];
-  __shared__ unsigned long long wsum[kAxThreads / 32];
-  __shared__ unsigned long long sh_r, sh_W;
-  __shared__ int sh_pick;
-  __shared__ unsigned long long usedJ, usedK;          // bit j / k: already used
-  if (threadIdx.x == 0) { usedJ = 0ull; usedK = 0ull; }
+  __shared__ unsigned long long gsum[kAxCands][kAxGroup / 32];
+  __shared__ unsigned long long sh_r[kAxCands];
+  __shared__ int sh_pick[kAxCands];
+  const int g = threadIdx.x / kAxGroup;               // candidate slot in the block
+  const int t = threadIdx.x % kAxGroup;               // thread in the group
+  const int lane = threadIdx.x & 31, gw = t >> 5;
+  const int sidx = blockIdx.x * kAxCands + g;
+  const bool active = sidx < len;
+  const uint32_t s = (uint32_t)(s0 + sidx);
   const int P = I * I;
-  const int per = (P + kAxThreads - 1) / kAxThreads;
-  const int q0 = threadIdx.x * per, q1 = min(P, q0 + per);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int dj = kAxThreads / I, dk = kAxThreads % I;   // stride of q in (j, k)
-  const int j00 = threadIdx.x / I, k00 = threadIdx.x % I;
   const uint32_t round = st->round_id;
-  __syncthreads();
+  unsigned long long usedJ = 0ull, usedK = 0ull;      // uniform in the group
+  const int qa = 32 * t;                              // first pair of this thread
+  const int ja = qa / I, ka = qa - (qa / I) * I;
+  const bool rowwise = (I % 32) == 0;                 // the 32 pairs share row ja
+  const int nq = max(0, min(32, P - qa));             // pairs of this thread
+  const int bar = 1 + g;                              // named barrier of the group
   for (int i = 0; i < I; ++i) {
     const float* pi = p + v0 + (int64_t)i * P;
-    const unsigned long long uj = usedJ, uk = usedK;
-    int j = j00, k = k00;
-    for (int q = threadIdx.x; q < P; q += kAxThreads) {
-      const bool used = ((uj >> j) | (uk >> k)) & 1ull;
-      wt[q] = used ? 0u : gf::prob_threshold(__ldg(pi + q));
-      j += dj;
-      k += dk;
-      if (k >= I) { k -= I; ++j; }
+    constexpr int kStage = kAxMaxP / (kAxGroup * kAxCands);
+    float pv[kStage];
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int q = threadIdx.x + u * kAxGroup * kAxCands;
+      pv[u] = q < P ? __ldg(pi + q) : 0.0f;
+    }
+    __syncthreads();                                  // previous step's reads done
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int q = threadIdx.x + u * kAxGroup * kAxCands;
+      wt[ax_slot(q)] = q < P ? gf::prob_threshold(pv[u]) : 0u;
     }
     __syncthreads();
+    if (!active) continue;                            // whole group alike
+    // available pairs of this thread as a bit mask (bit m: pair qa + m)
+    uint32_t avail = 0u;
+    if (nq > 0) {
+      if (rowwise) {
+        if (!((usedJ >> ja) & 1ull)) avail = ~(uint32_t)(usedK >> ka);
+      } else {
+        int j = ja, k = ka;
+        for (int m = 0; m < nq; ++m) {
+          if (!(((usedJ >> j) | (usedK >> k)) & 1ull)) avail |= 1u << m;
+          if (++k == I) { k = 0; ++j; }
+        }
+      }
+      if (nq < 32) avail &= (1u << nq) - 1u;
+    }
     unsigned long long mine = 0;
-    for (int q = q0; q < q1; ++q) mine += wt[q];
-    unsigned long long v = mine;
+    for (uint32_t a2 = avail; a2; a2 &= a2 - 1) mine += wt[ax_slot(qa + __ffs(a2) - 1)];
+    unsigned long long incl = mine;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, v, off);
-      if (lane >= off) v += o;
+      const unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+      if (lane >= off) incl += o;
     }
-    if (lane == 31) wsum[warp] = v;
-    __syncthreads();
-    unsigned long long wbase = 0, tot = 0;
-    for (int q = 0; q < kAxThreads / 32; ++q) {
-      if (q < warp) wbase += wsum[q];
-      tot += wsum[q];
+    if (lane == 31) gsum[g][gw] = incl;
+    named_barrier(bar, kAxGroup);
+    unsigned long long before = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < kAxGroup / 32; ++q) {
+      const unsigned long long v = gsum[g][q];
+      if (q < gw) before += v;
+      tot += v;
     }
-    const unsigned long long excl = wbase + v - mine;
-    if (threadIdx.x == 0) {
+    const unsigned long long excl = before + incl - mine;
+    if (t == 0) {
       const uint4 u4 = gf::philox_call(seed, gf::kStreamAxial, (uint32_t)(inst_base + inst),
                                        round, s, (uint64_t)(i >> 2));
       const uint32_t u = gf::lane_of(u4, (uint32_t)(i & 3));
-      sh_W = tot;
+      unsigned long long r;
       if (tot > 0) {
         const unsigned long long lo = (unsigned long long)u * tot;
         const unsigned long long hi = __umul64hi((unsigned long long)u, tot);
-        sh_r = (hi << 32) | (lo >> 32);
+        r = (hi << 32) | (lo >> 32);
       } else {
         const int free = I - i;
-        sh_r = ((unsigned long long)u * (unsigned long long)(free * free)) >> 32;
+        r = ((unsigned long long)u * (unsigned long long)(free * free)) >> 32;
       }
-      sh_pick = -1;
-    }
-    __syncthreads();
-    const unsigned long long r = sh_r;
-    if (sh_W > 0) {
-      if (mine > 0 && excl <= r && r < excl + mine) {
-        unsigned long long acc = excl;
-        for (int q = q0; q < q1; ++q) {
-          acc += wt[q];
-          if (wt[q] && acc > r) { sh_pick = q; break; }
-        }
+      sh_r[g] = r;
+      sh_pick[g] = -1;
+      if (tot == 0) {
+        // r-th allowed pair in row-major order: (a-th free j, b-th free k)
+        const int free = I - i;
+        const int a = (int)(r / free), bb = (int)(r % free);
+        int jj = -1, kk = -1;
+        for (int q = 0, c = 0; q < I; ++q)
+          if (!((usedJ >> q) & 1ull)) { if (c == a) { jj = q; break; } ++c; }
+        for (int q = 0, c = 0; q < I; ++q)
+          if (!((usedK >> q) & 1ull)) { if (c == bb) { kk = q; break; } ++c; }
+        sh_pick[g] = jj * I + kk;
       }
-    } else if (threadIdx.x == 0) {
-      // r-th allowed pair in row-major order: (a-th free j, b-th free k)
-      const int free = I - i;
-      int a = (int)(r / free), bb = (int)(r % free), jj = -1, kk = -1;
-      for (int q = 0, c = 0; q < I; ++q) if (!((uj >> q) & 1ull)) { if (c == a) { jj = q; break; } ++c; }
-      for (int q = 0, c = 0; q < I; ++q) if (!((uk >> q) & 1ull)) { if (c == bb) { kk = q; break; } ++c; }
-      sh_pick = jj * I + kk;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int q = sh_pick;
-      const int jj = q / I, kk = q - jj * I;
-      usedJ |= 1ull << jj;
-      usedK |= 1ull << kk;
-      const int64_t var = v0 + (int64_t)i * P + q;
+    named_barrier(bar, kAxGroup);
+    const unsigned long long r = sh_r[g];
+    if (tot > 0 && mine > 0 && excl <= r && r < excl + mine) {
+      unsigned long long acc = excl;
+      for (uint32_t a2 = avail; a2; a2 &= a2 - 1) {
+        const int m = __ffs(a2) - 1;
+        const uint32_t w = wt[ax_slot(qa + m)];
+        acc += w;
+        if (w && acc > r) { sh_pick[g] = qa + m; break; }
+      }
+    }
+    named_barrier(bar, kAxGroup);
+    const int pick = sh_pick[g];
+    if (pick < 0 || pick >= P) continue;              // unreachable: r < tot
+    const int jj = pick / I, kk = pick - jj * I;
+    usedJ |= 1ull << jj;
+    usedK |= 1ull << kk;
+    if (t == 0) {
+      const int64_t var = v0 + (int64_t)i * P + pick;
       atomicOr(&X[var * kw + (sidx >> 5)], 1u << (sidx & 31));
     }
-    __syncthreads();
   }
 }
 
@@ -343,12 +382,20 @@ __global__ void k_closure(const int64_t* __restrict__ rv, const int64_t* __restr
   }
 }
 
+// Bernoulli thresholds floor(p 2^24) of a dense instance's variables (0 past
+// n), computed once per chunk instead of once per draw.
+__global__ void k_thresholds(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld,
+                             uint32_t* __restrict__ thr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ld) thr[i] = i < n ? gf::prob_threshold(p[v0 + i]) : 0u;
+}
+
 // Bernoulli draws of a dense-Q instance written sample-major as bf16 0/1
 // (the tensor-core operand) and as bit words Xb[s * ld/32 + w] (bit t =
 // variable 32 w + t, read by the scorer's epilogue), one thread per
 // (sample = blockIdx.y, 4 variables); 8 consecutive lanes assemble one word.
 __global__ void __launch_bounds__(256)
-k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld,
+k_bern_bf16(const uint32_t* __restrict__ thr, int64_t n, int64_t ld,
             int s0, uint64_t seed, int inst, const GfDState* __restrict__ st,
             void* __restrict__ Xs, uint32_t* __restrict__ Xb, int f8) {
   const int64_t n4 = ld / 4;
@@ -360,12 +407,12 @@ k_bern_bf16(const float* __restrict__ p, int64_t v0, int64_t n, int64_t ld,
   if (i0 < n) {
     const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)inst, st->round_id,
                                     (uint32_t)(s0 + sidx), (uint64_t)g4);
-    // v0 and i0 are multiples of 4; entries at or past n are padding
-    const float4 pv = __ldg(reinterpret_cast<const float4*>(p + v0 + i0));
-    b[0] = (u.x >> 8) < gf::prob_threshold(pv.x);
-    b[1] = (i0 + 1 < n) && (u.y >> 8) < gf::prob_threshold(pv.y);
-    b[2] = (i0 + 2 < n) && (u.z >> 8) < gf::prob_threshold(pv.z);
-    b[3] = (i0 + 3 < n) && (u.w >> 8) < gf::prob_threshold(pv.w);
+    // thresholds floor(p 2^24) of the round (0 for padding entries)
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(thr) + g4);
+    b[0] = (u.x >> 8) < t.x;
+    b[1] = (u.y >> 8) < t.y;
+    b[2] = (u.z >> 8) < t.z;
+    b[3] = (u.w >> 8) < t.w;
   }
   if (f8) {
     // FP8 E4M3 one = 0x38
@@ -454,8 +501,8 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
     const GfInstHost& I = h->ih[b];
     if (I.group_mode != 2) continue;
     if (I.axial_I <= 64 && I.axial_I * I.axial_I <= kAxMaxP)
-      k_axial_sm<<<len, kAxThreads, 0, h->stream>>>(p, I.var_off, I.axial_I, b, s0, len, h->kw,
-                                                    P.seed, P.inst_base, h->dstate, h->X);
+      k_axial_grp<<<(len + kAxCands - 1) / kAxCands, kAxGroup * kAxCands, 0, h->stream>>>(
+          p, I.var_off, I.axial_I, b, s0, len, h->kw, P.seed, P.inst_base, h->dstate, h->X);
     else
       k_axial<<<len, kAxThreads, 0, h->stream>>>(p, I.var_off, I.axial_I, b, s0, len, h->kw,
                                                  P.seed, P.inst_base, h->dstate, h->X);
@@ -472,12 +519,15 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   }
   if (for_dense) {
     for (const GfDenseQ& dq : h->dense) {
+      k_thresholds<<<(unsigned)((dq.ld + 255) / 256), 256, 0, h->stream>>>(
+          p, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.thr);
+      h->launches++;
       // one block row per candidate, at most 32768 candidates per launch
       for (int a = 0; a < len; a += 32768) {
         const int cnt = std::min(32768, len - a);
         const dim3 grid((unsigned)((dq.ld / 4 + 255) / 256), (unsigned)cnt);
         k_bern_bf16<<<grid, 256, 0, h->stream>>>(
-            p, h->ih[dq.inst].var_off, dq.n, dq.ld, s0 + a, P.seed, P.inst_base + dq.inst,
+            dq.thr, dq.n, dq.ld, s0 + a, P.seed, P.inst_base + dq.inst,
             h->dstate,
             dq.f8 ? (void*)(reinterpret_cast<uint8_t*>(dq.Xs) + (int64_t)a * dq.ld)
                   : (void*)(dq.Xs + (int64_t)a * dq.ld),

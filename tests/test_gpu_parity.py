@@ -133,6 +133,29 @@ def test_sampling_and_evaluation_bit_exact(name, mode):
     H.destroy()
 
 
+@pytest.mark.parametrize("I,k_b", [(7, 64), (64, 96), (33, 160)])
+def test_axial_sampler_bit_exact(I, k_b):
+    """Axial 3D picks (one warp per candidate, slabs staged per step) against
+    the oracle: odd I (lanes with partial ranges), I = 64 (128 pairs per
+    lane) and a candidate count that leaves idle warps; proposals with zeros
+    so that some steps fall back to the uniform pick."""
+    inst = W.assign3d(I=I, idx=2)
+    gp, op = _params(k_b=k_b)
+    H = G.load(inst, gp)
+    rng = np.random.default_rng(I)
+    p = rng.random(inst.n).astype(np.float32) ** 3
+    p[rng.random(inst.n) < 0.3] = 0.0
+    if I == 7:
+        p[:] = 0.0                                   # every step uniform
+    H.set_iterate(0, p, p, None)
+    H.sample_eval(1, 4, 0)
+    X, viol, obj = H.get_samples(0)
+    Xo = O.sample(inst, p, k_b, op.seed, 0, 4)
+    assert np.array_equal(X, Xo)
+    assert np.all(viol == 0)                          # axial picks are feasible
+    H.destroy()
+
+
 @pytest.mark.parametrize("idx", range(3))
 def test_eval_candidates_brute_force(idx):
     inst = W.tiny_bip(n=12, m1=4, m2=1, idx=40 + idx)
