@@ -195,6 +195,7 @@ static void host_advance(GfCtx* h, long long it) {
 cudaError_t gf_launch_persistent(GfCtx* h, int64_t nsteps);
 
 cudaError_t gf_single_init(GfCtx* h);
+cudaError_t gf_launch_small(GfCtx* h, int64_t nsteps);
 
 static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
   cudaError_t e;
@@ -203,6 +204,19 @@ static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
     // K xbar partials of the current state, read by the next dual step
     if ((e = gf_single_init(h))) return e;
     h->sr_valid = true;
+  }
+  if (h->small_ok && nsteps > 0) {
+    // one launch: every instance's iterations in its own block
+    while (done < nsteps) {
+      const int64_t cnt = std::min<int64_t>(nsteps - done, (int64_t)1 << 20);
+      const int pi = gf_prof_begin(h, 0);
+      if ((e = gf_launch_small(h, cnt))) return e;
+      gf_prof_end(h, pi, (int)cnt);
+      for (int64_t s = 0; s < cnt; ++s) host_advance(h, h->k_host + 1 + s);
+      h->k_host += cnt;
+      done += cnt;
+    }
+    return cudaSuccess;
   }
   if (h->persist_ok && nsteps > 0) {
     // one cooperative launch runs all nsteps iterations

@@ -1185,6 +1185,18 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     extern bool gf_single_setup(GfCtx * h);
     h->persist_ok = (P.pdhg_mode != 1) && gf_persistent_setup(h);
     h->single_ok = gf_single_setup(h);
+    // rows with one common coefficient (the small path keeps one value per row)
+    extern bool gf_small_setup(GfCtx * h, const std::vector<uint8_t>& uniform,
+                               const std::vector<int64_t>& kp, const std::vector<int64_t>& tp);
+    std::vector<uint8_t> uniform(ninst, 1);
+    for (int q = 0; q < ninst; ++q) {
+      const RowSet& o = st[q].orig;
+      for (size_t j = 0; j < o.size() && uniform[q]; ++j)
+        for (int64_t u = 1; u < o.len(j); ++u)
+          if (o.v(j)[u] != o.v(j)[0]) { uniform[q] = 0; break; }
+    }
+    GF_CK(h, cudaStreamSynchronize(s));
+    h->small_ok = gf_small_setup(h, uniform, Kp, Tp);
   }
   GF_CK(h, cudaStreamSynchronize(s));
   h->h_best.assign(3 * ninst, INFINITY);

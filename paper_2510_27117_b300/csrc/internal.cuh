@@ -270,6 +270,10 @@ struct gfors_ctx {
   int64_t* sr_row = nullptr;        // global row of each instance
   float* sr_kv = nullptr;           // K entry of every variable (0 if none)
   float2* sr_part = nullptr;        // [2][sr_nchunk] compensated partial sums
+  // small instances: one block per instance, matrix in shared memory
+  bool small_ok = false;
+  struct GfSmallInst* small_tab = nullptr;
+  size_t small_smem = 0;
   // persistent cooperative PDHG launch (dense instance, matrix in smem)
   bool persist_ok = false;
   size_t persist_smem = 0;

@@ -12,6 +12,7 @@
 // update.  Arithmetic: the row dot product of gf::i8_row_dot (shared with
 // the per-iteration kernel of k_pdhg.cu), then the same projected update.
 #include "internal.cuh"
+#include "penalty.cuh"
 
 namespace {
 
@@ -20,21 +21,6 @@ using gf::CSum;
 constexpr int kWarps = 32;
 constexpr int kSchedThread = kWarps * 32 - 1;   // advances the penalty schedule
 constexpr int kMaxRows = 256;                   // rows per block (c_hat, diag cache)
-
-// Step sizes for penalty rho (tau1 = min(sqrt(sigma), 1/(2L)) when capped,
-// tau2 = sigma / tau1), as in k_pdhg.cu.
-GF_DEV GfIParam step_params(double sigma, double normQ, int cap, double rho) {
-  double t1 = sqrt(sigma);
-  if (cap) {
-    double L = 2.0 * (normQ + rho);
-    if (L > 0.0 && 1.0 / (2.0 * L) < t1) t1 = 1.0 / (2.0 * L);
-  }
-  double t2 = sigma / t1;
-  GfIParam q;
-  q.tau1 = (float)t1; q.tau2 = (float)t2; q.rho = (float)rho; q.pad = 0.f;
-  q.tau1d = t1; q.tau2d = t2; q.rhod = rho; q.normQ = normQ;
-  return q;
-}
 
 // Arrive at the grid barrier of step s and wait until all nb blocks arrived
 // (counter >= s * nb).  Called by one thread; false on timeout / error.

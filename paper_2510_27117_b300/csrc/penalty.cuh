@@ -52,3 +52,20 @@ __device__ __forceinline__ void advance_penalty(GfDState* st, const GfSched* sc,
     next[b] = q;
   }
 }
+
+// Step sizes of one instance for penalty rho (tau1 = min(sqrt(sigma), 1/(2L))
+// when capped, tau2 = sigma / tau1), the per-instance half of advance_penalty
+// for kernels that advance the schedule themselves.
+__device__ __forceinline__ GfIParam step_params(double sigma, double normQ, int cap,
+                                                double rho) {
+  double t1 = sqrt(sigma);
+  if (cap) {
+    double L = 2.0 * (normQ + rho);
+    if (L > 0.0 && 1.0 / (2.0 * L) < t1) t1 = 1.0 / (2.0 * L);
+  }
+  double t2 = sigma / t1;
+  GfIParam q;
+  q.tau1 = (float)t1; q.tau2 = (float)t2; q.rho = (float)rho; q.pad = 0.f;
+  q.tau1d = t1; q.tau2d = t2; q.rhod = rho; q.normQ = normQ;
+  return q;
+}
