@@ -27,6 +27,34 @@ GF_DEV uint4 philox(uint4 c, uint2 k) {
   return c;
 }
 
+// The same generator with the ten round keys computed once (they depend on
+// the seed only): for threads that draw many counters under one key.
+struct PhiloxKeys {
+  uint32_t kx[10], ky[10];
+};
+GF_DEV PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys K;
+  uint32_t kx = (uint32_t)seed, ky = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    K.kx[r] = kx;
+    K.ky[r] = ky;
+    kx += 0x9E3779B9u;
+    ky += 0xBB67AE85u;
+  }
+  return K;
+}
+GF_DEV uint4 philox_k(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a0 = 0xD2511F53u, a1 = 0xCD9E8D57u;
+    uint32_t lo0 = a0 * c.x, hi0 = __umulhi(a0, c.x);
+    uint32_t lo1 = a1 * c.z, hi1 = __umulhi(a1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ K.kx[r], lo1, hi0 ^ c.w ^ K.ky[r], lo0);
+  }
+  return c;
+}
+
 // Counter layout of every random draw: (idx >> 2, sample, round, inst |
 // stream << 28) under key (seed lo, seed hi); the draw for idx is lane idx&3.
 enum : uint32_t { kStreamBern = 0, kStreamGroup = 1, kStreamAxial = 2,

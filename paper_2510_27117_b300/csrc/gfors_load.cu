@@ -1097,6 +1097,20 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       UP(h->frow_w, w.data(), int32_t, N);
       UP(h->frhs, rhs.data(), long long, ninst);
       UP(h->fblk, blk.data(), int32_t, blk.size());
+      ALLOC(h->fthr, uint32_t, N);
+      // a block sums at most 8192 products of one instance: int32 partial
+      // sums are exact when every |coefficient| and |cost| is below 2^31/8192
+      long long maxw = 0, maxc = 0;
+      for (int64_t i = 0; i < N; ++i) {
+        maxw = std::max(maxw, std::llabs((long long)w[i]));
+        maxc = std::max(maxc, std::llabs(cint[i]));
+      }
+      if (maxw < (1ll << 31) / 8192 && maxc < (1ll << 31) / 8192) {
+        std::vector<int32_t> c32(N);
+        for (int64_t i = 0; i < N; ++i) c32[i] = (int32_t)cint[i];
+        ALLOC(h->f_c32, int32_t, N);
+        UP(h->f_c32, c32.data(), int32_t, N);
+      }
     }
   }
 

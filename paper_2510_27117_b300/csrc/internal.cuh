@@ -212,6 +212,8 @@ struct gfors_ctx {
   // fused single-row path
   bool fused_ok = false;
   int32_t* frow_w = nullptr;        // N: coefficient of the single row (0 for padding)
+  int32_t* f_c32 = nullptr;         // N: costs as int32 when every row / cost sum fits
+  uint32_t* fthr = nullptr;         // N: Bernoulli thresholds of the current chunk
   long long* frhs = nullptr;        // ninst
   long long* fsum = nullptr;        // ninst x chunk row sums
   int32_t* fblk = nullptr;          // fused work blocks: (inst, v0, v1) triples

@@ -357,33 +357,51 @@ k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int64_t* __rest
 // block walks a slice [v0, v1) of one instance's variables four at a time
 // (one Philox call per four Bernoulli draws), accumulating the row sum and
 // the objective in int64; nothing is materialised.
+template <typename Acc>
 __global__ void __launch_bounds__(128)
-k_fused_single_row(const int32_t* __restrict__ blk, const float* __restrict__ p,
+k_fused_single_row(const int32_t* __restrict__ blk, const uint32_t* __restrict__ thr,
                    const int32_t* __restrict__ wrow, const long long* __restrict__ cint,
-                   const int64_t* __restrict__ var_off, int s0, int len, int chunk,
-                   uint64_t seed, int inst_base, const GfDState* __restrict__ st,
-                   long long* __restrict__ fsum, long long* __restrict__ obj) {
+                   const int32_t* __restrict__ c32, const int64_t* __restrict__ var_off,
+                   int s0, int len, int chunk, uint64_t seed, int inst_base,
+                   const GfDState* __restrict__ st, long long* __restrict__ fsum,
+                   long long* __restrict__ obj) {
   const int b = blk[3 * blockIdx.x], v0 = blk[3 * blockIdx.x + 1], v1 = blk[3 * blockIdx.x + 2];
   const int sidx = blockIdx.y * 128 + threadIdx.x;
   if (sidx >= len) return;
   const uint32_t s = (uint32_t)(s0 + sidx);
   const uint32_t round = st->round_id;
   const int64_t off = var_off[b];
-  long long rs = 0, ob = 0;
+  const gf::PhiloxKeys K = gf::philox_keys(seed);
+  const uint32_t c3 = ((uint32_t)(inst_base + b) & 0x0FFFFFFFu) | (gf::kStreamBern << 28);
+  Acc rs = 0, ob = 0;                      // int32 when every sum provably fits
   for (int v = v0; v < v1; v += 4) {
-    const float4 pp = *reinterpret_cast<const float4*>(p + v);
+    const uint4 t = *reinterpret_cast<const uint4*>(thr + v);
     const int4 ww = *reinterpret_cast<const int4*>(wrow + v);
-    const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)(inst_base + b), round,
-                                    s, (uint64_t)((v - off) >> 2));
-    if ((u.x >> 8) < gf::prob_threshold(pp.x)) { rs += ww.x; ob += cint[v]; }
-    if ((u.y >> 8) < gf::prob_threshold(pp.y)) { rs += ww.y; ob += cint[v + 1]; }
-    if ((u.z >> 8) < gf::prob_threshold(pp.z)) { rs += ww.z; ob += cint[v + 2]; }
-    if ((u.w >> 8) < gf::prob_threshold(pp.w)) { rs += ww.w; ob += cint[v + 3]; }
+    const uint4 u = gf::philox_k(make_uint4((uint32_t)((v - off) >> 2), s, round, c3), K);
+    const bool b0 = (u.x >> 8) < t.x, b1 = (u.y >> 8) < t.y;
+    const bool b2 = (u.z >> 8) < t.z, b3 = (u.w >> 8) < t.w;
+    rs += (b0 ? ww.x : 0) + (b1 ? ww.y : 0) + (b2 ? ww.z : 0) + (b3 ? ww.w : 0);
+    if constexpr (sizeof(Acc) == 4) {
+      const int4 cc = *reinterpret_cast<const int4*>(c32 + v);
+      ob += (b0 ? cc.x : 0) + (b1 ? cc.y : 0) + (b2 ? cc.z : 0) + (b3 ? cc.w : 0);
+    } else {
+      if (b0) ob += cint[v];
+      if (b1) ob += cint[v + 1];
+      if (b2) ob += cint[v + 2];
+      if (b3) ob += cint[v + 3];
+    }
   }
   atomicAdd(reinterpret_cast<unsigned long long*>(&fsum[(int64_t)b * chunk + sidx]),
-            (unsigned long long)rs);
+            (unsigned long long)(long long)rs);
   atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)b * chunk + sidx]),
-            (unsigned long long)ob);
+            (unsigned long long)(long long)ob);
+}
+
+// Thresholds floor(p 2^24) of every variable (0 for padding), once per chunk.
+__global__ void k_thresholds_all(const float* __restrict__ p, const uint8_t* __restrict__ live,
+                                 int64_t N, uint32_t* __restrict__ thr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) thr[i] = live[i] ? gf::prob_threshold(p[i]) : 0u;
 }
 
 __global__ void k_fused_viol(const long long* __restrict__ fsum, const long long* __restrict__ rhs,
@@ -557,9 +575,17 @@ cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len) {
   if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
     return e;
   dim3 grid((unsigned)h->nfblk, (unsigned)((len + 127) / 128));
-  k_fused_single_row<<<grid, 128, 0, h->stream>>>(h->fblk, p, h->frow_w, h->cint, h->var_off_d,
-                                                 s0, len, h->chunk, h->prm.seed,
-                                                 h->prm.inst_base, h->dstate, h->fsum, h->obj);
+  k_thresholds_all<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(p, h->var_live, h->N,
+                                                                           h->fthr);
+  if (h->f_c32)
+    k_fused_single_row<int><<<grid, 128, 0, h->stream>>>(
+        h->fblk, h->fthr, h->frow_w, h->cint, h->f_c32, h->var_off_d, s0, len, h->chunk,
+        h->prm.seed, h->prm.inst_base, h->dstate, h->fsum, h->obj);
+  else
+    k_fused_single_row<long long><<<grid, 128, 0, h->stream>>>(
+        h->fblk, h->fthr, h->frow_w, h->cint, nullptr, h->var_off_d, s0, len, h->chunk,
+        h->prm.seed, h->prm.inst_base, h->dstate, h->fsum, h->obj);
+  h->launches++;
   const int64_t th = (int64_t)h->ninst * len;
   k_fused_viol<<<(unsigned)((th + 255) / 256), 256, 0, h->stream>>>(h->fsum, h->frhs, h->ninst,
                                                                    len, h->chunk, h->viol);

@@ -37,10 +37,11 @@ k_bern_bits(const float* __restrict__ p, const int32_t* __restrict__ var_inst,
   uint32_t word[4] = {0u, 0u, 0u, 0u};
   if (any) {
     const int nt = min(32, len - 32 * w);
+    const gf::PhiloxKeys K = gf::philox_keys(seed);
+    const uint32_t c3 = ((uint32_t)(inst_base + b) & 0x0FFFFFFFu) | (gf::kStreamBern << 28);
     for (int t = 0; t < nt; ++t) {
       const uint32_t s = (uint32_t)(s0 + 32 * w + t);
-      const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)(inst_base + b),
-                                      round, s, (uint64_t)loc4);
+      const uint4 u = gf::philox_k(make_uint4((uint32_t)loc4, s, round, c3), K);
       word[0] |= (uint32_t)((u.x >> 8) < thr[0]) << t;
       word[1] |= (uint32_t)((u.y >> 8) < thr[1]) << t;
       word[2] |= (uint32_t)((u.z >> 8) < thr[2]) << t;
