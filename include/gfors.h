@@ -106,10 +106,15 @@ typedef struct {
   double power_tol;    /* power-iteration stop tolerance; 1e-12            */
   int32_t power_maxit; /* power-iteration cap; 5000                         */
   double wait_timeout_s;/* limit of every device-side wait; 2.0             */
-  int32_t pdhg_mode;   /* 0 auto (one persistent cooperative launch per call
-                          when a single dense instance fits; otherwise CUDA
-                          graphs of per-iteration launches), 1 per-iteration
-                          launches only                                     */
+  int32_t pdhg_mode;   /* 0 auto: one persistent cooperative launch per call
+                          for a single dense instance that fits shared
+                          memory; one block per instance for instances whose
+                          matrix fits a block's shared memory; the fused
+                          one-row kernels for batches of one-row instances;
+                          otherwise CUDA graphs of per-iteration launches.
+                          1 per-iteration launches only.  2 as 0, plus one
+                          cooperative launch per call for sparse problems
+                          that fit the L2 cache                            */
 } gfors_params;
 
 GFORS_API void gfors_default_params(gfors_params* prm);

@@ -196,6 +196,7 @@ cudaError_t gf_launch_persistent(GfCtx* h, int64_t nsteps);
 
 cudaError_t gf_single_init(GfCtx* h);
 cudaError_t gf_launch_small(GfCtx* h, int64_t nsteps);
+cudaError_t gf_launch_coop(GfCtx* h, int64_t nsteps);
 
 static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
   cudaError_t e;
@@ -205,12 +206,13 @@ static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
     if ((e = gf_single_init(h))) return e;
     h->sr_valid = true;
   }
-  if (h->small_ok && nsteps > 0) {
-    // one launch: every instance's iterations in its own block
+  if ((h->small_ok || h->coop_ok) && nsteps > 0) {
+    // one launch: every instance's iterations in its own block (small), or
+    // the whole batch as one cooperative grid (L2-resident)
     while (done < nsteps) {
       const int64_t cnt = std::min<int64_t>(nsteps - done, (int64_t)1 << 20);
       const int pi = gf_prof_begin(h, 0);
-      if ((e = gf_launch_small(h, cnt))) return e;
+      if ((e = h->small_ok ? gf_launch_small(h, cnt) : gf_launch_coop(h, cnt))) return e;
       gf_prof_end(h, pi, (int)cnt);
       for (int64_t s = 0; s < cnt; ++s) host_advance(h, h->k_host + 1 + s);
       h->k_host += cnt;

@@ -1211,6 +1211,9 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     }
     GF_CK(h, cudaStreamSynchronize(s));
     h->small_ok = gf_small_setup(h, uniform, Kp, Tp);
+    extern bool gf_coop_setup(GfCtx * h, const std::vector<int64_t>& kp,
+                              const std::vector<int64_t>& tp);
+    h->coop_ok = gf_coop_setup(h, Kp, Tp);
   }
   GF_CK(h, cudaStreamSynchronize(s));
   h->h_best.assign(3 * ninst, INFINITY);

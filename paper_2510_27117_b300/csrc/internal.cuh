@@ -272,6 +272,12 @@ struct gfors_ctx {
   int64_t* sr_row = nullptr;        // global row of each instance
   float* sr_kv = nullptr;           // K entry of every variable (0 if none)
   float2* sr_part = nullptr;        // [2][sr_nchunk] compensated partial sums
+  // L2-resident sparse problems: one cooperative launch per call
+  bool coop_ok = false;
+  int32_t *coop_rblk = nullptr, *coop_rwarp = nullptr, *coop_cblk = nullptr,
+          *coop_cwarp = nullptr, *coop_cthr = nullptr;
+  int32_t coop_n[5] = {0, 0, 0, 0, 0};
+  unsigned* coop_bar = nullptr;
   // small instances: one block per instance, matrix in shared memory
   bool small_ok = false;
   struct GfSmallInst* small_tab = nullptr;

@@ -23,6 +23,9 @@ def _params(**kw):
 
 CASES = {
     "setcover": lambda: W.set_cover(n=500, m=60, density=0.05, idx=3),
+    # too large for one block's shared memory (bucketed launches; with
+    # pdhg_mode 2 the cooperative one-launch path)
+    "assign3d_l2": lambda: W.assign3d(I=24, idx=3),
     "knapsack": lambda: W.knapsack(3001, idx=5),
     "tiny": lambda: W.tiny_bip(n=14, m1=4, m2=1, idx=2),
     "maxcut": lambda: W.max_cut(n=300, idx=1),
@@ -64,10 +67,10 @@ def _step_tolerance(S, t1, t2, rho, x, xb, y, y1):
     return tol_x, tol_y
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_pdhg_single_step(name):
+@pytest.mark.parametrize("name,mode", [(c, 0) for c in CASES] + [("assign3d_l2", 2)])
+def test_pdhg_single_step(name, mode):
     inst = CASES[name]()
-    gp, op = _params()
+    gp, op = _params(pdhg_mode=mode)
     H = G.load(inst, gp)
     S = O.preprocess(inst, op.seed, 0)
     rng = np.random.default_rng(11)
@@ -398,3 +401,23 @@ def test_candidate_ranges_reproduce_whole_round(name):
     whole = keys[0]
     parts = np.stack([np.append(keys[1], 0), np.append(keys[2], 1)])
     assert SH.min_key(parts)[:3].tolist() == whole.tolist()
+
+
+def test_cooperative_path_matches_launch_path():
+    """L2-sized sparse problems run as one cooperative launch per call (dual
+    step, grid barrier, primal step, grid barrier); against per-iteration
+    launches over calls of uneven length, across penalty updates."""
+    inst = W.assign3d(I=24, idx=5)
+    out = []
+    for mode, pieces in ((2, (7, 13, 5)), (1, (25,))):
+        gp, _ = _params(k_int=10, pdhg_mode=mode)
+        H = G.load(inst, gp)
+        for k in pieces:
+            H.pdhg_steps(k)
+        out.append((H.get_iterate(0), H.get_scales(0)))
+        H.destroy()
+    (xa, xba, _, ya), sa = out[0]
+    (xb, xbb, _, yb), sb = out[1]
+    assert np.max(np.abs(xa - xb)) < 1e-5 and np.max(np.abs(xba - xbb)) < 2e-5
+    assert np.max(np.abs(ya - yb)) <= 1e-5 * (1 + np.max(np.abs(yb)))
+    assert sa[6] == sb[6] and sa[7] == sb[7]
