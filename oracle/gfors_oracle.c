@@ -388,6 +388,96 @@ void orc_axial3d(int32_t I, int32_t k, const float* p, uint64_t seed,
   free(cand); free(usedJ); free(usedK);
 }
 
+/* Algorithm 4 (customized sampling for the 3D assignment, Section 2.4.2):
+ * the largest gamma*I entries of p give a greedy partial assignment, every
+ * candidate completes it at random and improves it by L pairwise
+ * interchanges.  The paper fixes the outline only; readings used here:
+ *  (a) the gamma*I largest entries of p, ordered by p descending, then by
+ *      variable index ascending;
+ *  (b) greedy: an entry (i,j,k) is accepted when i, j and k are all unused;
+ *  (c) completion: the free j's and the free k's (each ascending) are
+ *      shuffled by Fisher-Yates (q = F-1 down to 1, r = floor(u (q+1) / 2^32)
+ *      with u the Philox lane of stream 6, index t for the t-th draw: the j's
+ *      first, then the k's) and handed in turn to the free i's (ascending);
+ *  (d) improvement: up to L steps, each applying the single best strictly
+ *      improving interchange between the triples of i = a and i = b (a < b):
+ *      type 0 exchanges their j, type 1 their k; exact integer costs; ties
+ *      to the smallest (a, b, type); a step without improvement ends it. */
+static int cmp_desc_pv(const void* x, const void* y) {
+  const double* a = (const double*)x;
+  const double* b = (const double*)y;
+  if (a[0] != b[0]) return a[0] > b[0] ? -1 : 1;      /* p descending */
+  return a[1] < b[1] ? -1 : (a[1] > b[1] ? 1 : 0);     /* index ascending */
+}
+
+void orc_assign3d_custom(int32_t I, int32_t gamma, int32_t L, int32_t k, const float* p,
+                         const int64_t* cost, uint64_t seed, uint32_t inst,
+                         uint32_t round_id, uint8_t* X) {
+  const int64_t n = (int64_t)I * I * I;
+  const int64_t K = (int64_t)gamma * I;
+  double* pv = malloc(sizeof(double) * 2 * (size_t)n);
+  for (int64_t v = 0; v < n; ++v) { pv[2 * v] = (double)p[v]; pv[2 * v + 1] = (double)v; }
+  qsort(pv, (size_t)n, 2 * sizeof(double), cmp_desc_pv);
+  int32_t* J0 = malloc(sizeof(int32_t) * (size_t)I);
+  int32_t* K0 = malloc(sizeof(int32_t) * (size_t)I);
+  uint8_t* uj = calloc((size_t)I, 1);
+  uint8_t* uk = calloc((size_t)I, 1);
+  for (int32_t i = 0; i < I; ++i) J0[i] = K0[i] = -1;
+  for (int64_t e = 0; e < K && e < n; ++e) {
+    const int64_t v = (int64_t)pv[2 * e + 1];
+    const int32_t i = (int32_t)(v / ((int64_t)I * I)), j = (int32_t)((v / I) % I),
+                  kk = (int32_t)(v % I);
+    if (J0[i] < 0 && !uj[j] && !uk[kk]) { J0[i] = j; K0[i] = kk; uj[j] = 1; uk[kk] = 1; }
+  }
+  int32_t* J = malloc(sizeof(int32_t) * (size_t)I);
+  int32_t* Kk = malloc(sizeof(int32_t) * (size_t)I);
+  int32_t* fi = malloc(sizeof(int32_t) * (size_t)I);
+  int32_t* fj = malloc(sizeof(int32_t) * (size_t)I);
+  int32_t* fk = malloc(sizeof(int32_t) * (size_t)I);
+#define C3(i, j, kk) cost[((int64_t)(i) * I + (j)) * I + (kk)]
+  for (int32_t s = 0; s < k; ++s) {
+    int32_t F = 0, Fj = 0, Fk = 0;
+    for (int32_t i = 0; i < I; ++i) {
+      J[i] = J0[i]; Kk[i] = K0[i];
+      if (J0[i] < 0) fi[F++] = i;
+      if (!uj[i]) fj[Fj++] = i;
+      if (!uk[i]) fk[Fk++] = i;
+    }
+    uint64_t t = 0;
+    for (int32_t q = F - 1; q >= 1; --q) {
+      const uint32_t u = orc_philox_lane(seed, 6u, inst, round_id, (uint32_t)s, t++);
+      const int32_t r = (int32_t)(((uint64_t)u * (uint64_t)(q + 1)) >> 32);
+      const int32_t tmp = fj[q]; fj[q] = fj[r]; fj[r] = tmp;
+    }
+    for (int32_t q = F - 1; q >= 1; --q) {
+      const uint32_t u = orc_philox_lane(seed, 6u, inst, round_id, (uint32_t)s, t++);
+      const int32_t r = (int32_t)(((uint64_t)u * (uint64_t)(q + 1)) >> 32);
+      const int32_t tmp = fk[q]; fk[q] = fk[r]; fk[r] = tmp;
+    }
+    for (int32_t e = 0; e < F; ++e) { J[fi[e]] = fj[e]; Kk[fi[e]] = fk[e]; }
+    for (int32_t step = 0; step < L; ++step) {
+      int64_t best = 0;
+      int32_t ba = -1, bb = -1, bt = -1;
+      for (int32_t a = 0; a < I; ++a)
+        for (int32_t b = a + 1; b < I; ++b) {
+          const int64_t old = C3(a, J[a], Kk[a]) + C3(b, J[b], Kk[b]);
+          const int64_t d0 = C3(a, J[b], Kk[a]) + C3(b, J[a], Kk[b]) - old;
+          const int64_t d1 = C3(a, J[a], Kk[b]) + C3(b, J[b], Kk[a]) - old;
+          if (d0 < best) { best = d0; ba = a; bb = b; bt = 0; }
+          if (d1 < best) { best = d1; ba = a; bb = b; bt = 1; }
+        }
+      if (ba < 0) break;
+      if (bt == 0) { const int32_t tmp = J[ba]; J[ba] = J[bb]; J[bb] = tmp; }
+      else { const int32_t tmp = Kk[ba]; Kk[ba] = Kk[bb]; Kk[bb] = tmp; }
+    }
+    memset(X + (int64_t)s * n, 0, (size_t)n);
+    for (int32_t i = 0; i < I; ++i) X[(int64_t)s * n + ((int64_t)i * I + J[i]) * I + Kk[i]] = 1;
+  }
+#undef C3
+  free(pv); free(J0); free(K0); free(uj); free(uk); free(J); free(Kk); free(fi); free(fj);
+  free(fk);
+}
+
 /* Monotone relaxation with repair (Section 2.4.3), facility-location form:
  * y <- y OR (OR of x_k over the repair list), valid because the opening
  * costs are non-negative. */

@@ -63,6 +63,8 @@ def lib():
         L.orc_bernoulli.argtypes = [i64, i32, F32P, u64, u32, u32, VP, U8P]
         L.orc_onehot.argtypes = [i64, i64, I64P, I64P, i32, F32P, u64, u32, u32, U8P]
         L.orc_axial3d.argtypes = [i32, i32, F32P, u64, u32, u32, U8P]
+        L.orc_assign3d_custom.argtypes = [i32, i32, i32, i32, F32P, I64P, u64, u32, u32,
+                                          U8P]
         L.orc_closure.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
         L.orc_eval_int.argtypes = [i64, i64, I64P, I32P, I64P, I64P, i64, I64P, I32P, I64P,
                                    I64P, i32, VP, VP, VP, VP, I64P, i32, U8P, I32P, I64P]
@@ -134,6 +136,17 @@ def axial3d(p32, I, k, seed, inst, round_id):
     p32 = np.ascontiguousarray(p32, np.float32)
     X = np.zeros((k, I ** 3), np.uint8)
     lib().orc_axial3d(I, k, p32, seed, inst, round_id, X)
+    return X
+
+
+def assign3d_custom(p32, cost, I, gamma, L, k, seed, inst, round_id):
+    """Algorithm 4: top gamma*I entries, greedy partial assignment, random
+    completion and L pairwise-interchange steps per candidate (readings in
+    orc_assign3d_custom)."""
+    p32 = np.ascontiguousarray(p32, np.float32)
+    cost = np.ascontiguousarray(cost, np.int64)
+    X = np.zeros((k, I ** 3), np.uint8)
+    lib().orc_assign3d_custom(I, gamma, L, k, p32, cost, seed, inst, round_id, X)
     return X
 
 

@@ -501,3 +501,96 @@ def test_adam_matches_torch():
         wt.grad = torch.from_numpy(g)
         opt.step()
     assert np.allclose(w, wt.detach().numpy(), rtol=1e-6, atol=1e-7)
+
+
+# ---------------------------------------------------------------- Algorithm 4
+def _assign_of(X, I):
+    """(i, j, k) triples of one candidate; None unless a 3D assignment."""
+    t = np.argwhere(X.reshape(I, I, I))
+    if len(t) != I or len(set(t[:, 0])) != I or len(set(t[:, 1])) != I or \
+            len(set(t[:, 2])) != I:
+        return None
+    return t
+
+
+def _cost3(t, C):
+    return int(sum(C[i, j, k] for i, j, k in t))
+
+
+def test_alg4_candidates_are_assignments_and_locally_optimal():
+    """Every candidate of Algorithm 4 is a 3D assignment; with enough steps
+    no pairwise interchange (swap of j or of k between two triples) improves
+    it -- checked by enumerating all interchanges here."""
+    I = 7
+    rng = np.random.default_rng(3)
+    p = (rng.random(I ** 3) ** 4).astype(np.float32)
+    C = rng.integers(1, 101, size=(I, I, I)).astype(np.int64)
+    X = O.assign3d_custom(p, C.ravel(), I, 1, I * I, 40, 11, 0, 2)
+    for s in range(40):
+        t = _assign_of(X[s], I)
+        assert t is not None
+        base = _cost3(t, C)
+        for a in range(I):
+            for b in range(a + 1, I):
+                for ax in (1, 2):
+                    u = t.copy()
+                    u[a, ax], u[b, ax] = t[b, ax], t[a, ax]
+                    assert _cost3(u, C) >= base
+
+
+def test_alg4_partial_assignment_from_top_entries():
+    """p concentrated on one assignment (plus noise below it): the top I
+    entries are exactly that assignment, the greedy partial assignment is
+    complete, and with L = 0 every candidate equals it."""
+    I = 6
+    rng = np.random.default_rng(4)
+    sj, sk = rng.permutation(I), rng.permutation(I)
+    p = (0.5 * rng.random(I ** 3)).astype(np.float32)
+    target = np.zeros(I ** 3, np.uint8)
+    for i in range(I):
+        v = (i * I + sj[i]) * I + sk[i]
+        p[v] = 0.9
+        target[v] = 1
+    C = rng.integers(1, 50, size=I ** 3).astype(np.int64)
+    X = O.assign3d_custom(p, C, I, 1, 0, 16, 5, 0, 0)
+    assert np.all(X == target[None, :])
+
+
+def test_alg4_random_completion_is_uniform():
+    """gamma = 0 (empty partial assignment) and L = 0: the completion pairs
+    the i's with two independent uniform permutations, so all (I!)^2 = 36
+    assignments of I = 3 appear equally often (chi-square, 36 cells)."""
+    I, k = 3, 7200
+    p = np.zeros(I ** 3, np.float32)
+    C = np.ones(I ** 3, np.int64)
+    X = O.assign3d_custom(p, C, I, 0, 0, k, 21, 0, 1)
+    counts = {}
+    for s in range(k):
+        t = _assign_of(X[s], I)
+        assert t is not None
+        key = tuple(t[:, 1]) + tuple(t[:, 2])
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 36
+    e = k / 36
+    chi2 = sum((c - e) ** 2 / e for c in counts.values())
+    assert chi2 < 80.0                      # 35 dof: p ~ 1e-5 above this
+
+
+def test_alg4_improvement_never_worsens_and_bounds_optimum():
+    """Same candidates with L = 0 and L = 12 (identical completions): the
+    improved cost is never higher, and never below the optimum found by
+    enumerating all (I!)^2 assignments of I = 4."""
+    import itertools
+    I = 4
+    rng = np.random.default_rng(8)
+    p = (rng.random(I ** 3) ** 3).astype(np.float32)
+    C = rng.integers(1, 101, size=(I, I, I)).astype(np.int64)
+    X0 = O.assign3d_custom(p, C.ravel(), I, 1, 0, 50, 9, 3, 7)
+    X1 = O.assign3d_custom(p, C.ravel(), I, 1, 12, 50, 9, 3, 7)
+    opt = min(sum(C[i, a[i], b[i]] for i in range(I))
+              for a in itertools.permutations(range(I))
+              for b in itertools.permutations(range(I)))
+    for s in range(50):
+        c0 = _cost3(_assign_of(X0[s], I), C)
+        c1 = _cost3(_assign_of(X1[s], I), C)
+        assert opt <= c1 <= c0
