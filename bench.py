@@ -49,6 +49,11 @@ WORKLOADS = {
         I=64, idx=r), 50, 1024,
         "axial 3D assignment I=64 (262,144 binaries), 1024 candidates/round, k_int=50, "
         "learned proposal (MLP 8-128-128-1, random-init weights)"),
+    "assign3d_alg4": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"])
+                      .assign3d(I=64, idx=r, sampler="alg4", gamma=1, L=64), 50, 1024,
+                      "axial 3D assignment I=64 with the customized sampler (Algorithm 4: "
+                      "top-I entries, greedy partial assignment, random completion, up to 64 "
+                      "best pairwise interchanges), 1024 candidates/round, k_int=50"),
     "facility": (lambda r: [__import__("paper_2510_27117_b300.workloads", fromlist=["x"])
                             .facility_location(1000, 10000, idx=16 * r + q) for q in range(16)],
                  50, 256,
@@ -58,9 +63,9 @@ WORKLOADS = {
 }
 # rounds per step and proposal (0 plain x_k, 1 learned) of each workload
 ROUNDS = {"maxcut": 1, "setcover": 1, "setcover_batch": 1, "knapsack": 1, "assign3d": 1,
-          "facility": 4}
+          "assign3d_alg4": 1, "facility": 4}
 PROPOSAL = {"maxcut": 0, "setcover": 0, "setcover_batch": 0, "knapsack": 0, "assign3d": 1,
-            "facility": 1}
+            "assign3d_alg4": 0, "facility": 1}
 
 
 def env_rank():
@@ -348,6 +353,7 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False):
            "setcover_batch": (16 * nnz + 4 * (6 * n + 4 * m), "2 nnz (4+4) + 4 (6n + 4m)"),
            "knapsack": (16 * n, "16 sum n_i (read x, w, c; write x)"),
            "assign3d": (16 * nnz, "16 nnz"),
+           "assign3d_alg4": (16 * nnz, "16 nnz"),
            "facility": (16 * nnz + 24 * n + 16 * m, "2 nnz 8 + 24 n + 16 m")}[workload]
     lanes_peak = 148 * 128 * 2.032e9 / 15.0      # Philox output lanes/s (15 INT32 ops/lane)
     if dom == "pdhg":
@@ -572,10 +578,15 @@ def time_to_gap(args):
     if zref is None:
         zref = best_plain
     res = {}
-    for name, prop in (("batched_plain", 0), ("learned_batched", 2)):
+    arms = [("batched_plain", 0, insts), ("learned_batched", 2, insts)]
+    if args.workload == "assign3d":
+        # the paper's own sampler (Algorithm 4) on the same instances, batched
+        arms.append(("alg4_batched", 0, [W.assign3d(I=64, idx=q, sampler="alg4")
+                                          for q in range(len(insts))]))
+    for name, prop, arm_insts in arms:
         if prop and Wt is None:
             continue
-        H = G.load_batch(insts, prm)
+        H = G.load_batch(arm_insts, prm)
         if prop:
             H.set_proposal(Wt)
         hit, best, trace = _run_until(G, H, insts, prm, prop, zref, max_trig, tsync)

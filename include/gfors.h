@@ -166,6 +166,18 @@ GFORS_API gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t mo
                               int64_t ngroups, const int64_t* grp_ptr,
                               const int64_t* grp_idx, int32_t axial_I);
 
+/* Algorithm 4 (customized sampling for the 3D assignment, Section 2.4.2)
+ * for instance inst, n = I^3 variables x_ijk at (i I + j) I + k, 1 <= I <= 64:
+ * the gamma*I largest entries of p (p descending, then index ascending) give
+ * a greedy conflict-free partial assignment; every candidate completes it with
+ * Fisher-Yates permutations of the free j's and k's (Philox stream 6) and
+ * applies up to L best strictly improving pairwise interchanges (exchange of
+ * j or of k between two triples; exact integer costs; ties to the smallest
+ * (a, b, type)).  Every candidate is a feasible assignment.  Needs integral
+ * costs, 0 <= gamma <= I, I * gamma * I <= 16384, L >= 0. */
+GFORS_API gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, int32_t I,
+                                                 int32_t gamma, int32_t L);
+
 /* Monotone relaxation with repair (Section 2.4.3) for instance inst: after
  * sampling, rep_var[q] <- rep_var[q] OR (OR of rep_idx[rep_ptr[q] ..
  * rep_ptr[q+1])).  Valid when the repaired variables have non-negative

@@ -161,9 +161,14 @@ def sample(inst, p32, k, seed, inst_id, round_id, mode=None):
     """RandSampleStep for an Instance: Bernoulli for ungrouped variables,
     one-hot groups (mode 1) or axial 3D picks (mode 2), then closure."""
     if mode is None:
-        mode = 2 if inst.axial_I else (1 if inst.groups is not None else 0)
+        mode = (3 if inst.meta.get("sampler") == "alg4" else 2) if inst.axial_I else \
+            (1 if inst.groups is not None else 0)
     n = inst.n
-    if mode == 2:
+    if mode == 3:
+        I = inst.axial_I
+        X = assign3d_custom(p32, np.asarray(inst.c, np.int64), I, inst.meta.get("gamma", 1),
+                            inst.meta.get("L", I), k, seed, inst_id, round_id)
+    elif mode == 2:
         X = axial3d(p32, inst.axial_I, k, seed, inst_id, round_id)
     else:
         mask = None

@@ -832,6 +832,41 @@ extern "C" gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t m
   return GFORS_OK;
 }
 
+extern "C" gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, int32_t I3,
+                                                  int32_t gamma, int32_t L) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  GfInstHost& I = h->ih[inst];
+  if (I.qkind == 1 || h->fused_ok)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "Algorithm 4 needs a sparse, sampled instance");
+  if (I.group_mode != 0) return gf_fail(h, GFORS_E_STATE, "groups already set");
+  if (I3 < 1 || I3 > 64 || (int64_t)I3 * I3 * I3 != I.n)
+    return gf_fail(h, GFORS_E_ARG, "Algorithm 4 needs n = I^3 with 1 <= I <= 64");
+  if (gamma < 0 || gamma > I3 || I3 * gamma * I3 > 16384 || L < 0)
+    return gf_fail(h, GFORS_E_ARG, "need 0 <= gamma <= I, I * gamma * I <= 16384, L >= 0");
+  if (!I.integral) return gf_fail(h, GFORS_E_UNSUPPORTED, "Algorithm 4 needs integral costs");
+  if (!h->a4_cand) {
+    h->a4_cand = gf_alloc_t<unsigned long long>(h, 16384);
+    h->a4_J0 = gf_alloc_t<int32_t>(h, 64);
+    h->a4_K0 = gf_alloc_t<int32_t>(h, 64);
+    if (!h->a4_cand || !h->a4_J0 || !h->a4_K0)
+      return gf_fail(h, GFORS_E_OOM, "Algorithm 4 scratch");
+  }
+  I.group_mode = 3;
+  I.axial_I = I3;
+  I.a4_gamma = gamma;
+  I.a4_L = L;
+  std::vector<uint8_t> grouped(I.npad, 0);
+  for (int64_t i = 0; i < I.n; ++i) grouped[i] = 1;
+  cudaError_t e;
+  if ((e = cudaMemcpy(h->var_grouped + I.var_off, grouped.data(), I.npad,
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->var_grouped_feat + I.var_off, grouped.data(), I.npad,
+                      cudaMemcpyHostToDevice)))
+    return gf_cuda(h, e, "group flags");
+  return GFORS_OK;
+}
+
 extern "C" gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t nrep,
                                           const int64_t* rep_var, const int64_t* rep_ptr,
                                           const int64_t* rep_idx) {

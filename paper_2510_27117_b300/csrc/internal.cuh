@@ -114,8 +114,10 @@ struct GfInstHost {
   double normQ_raw = 0, s_obj = 1, normK = 0, s_K = 1, normQhat = 0;
   int itQ = 0, itK = 0;
   int cap = 0;
-  int group_mode = 0;               // 0 Bernoulli, 1 one-hot groups, 2 axial
+  int group_mode = 0;               // 0 Bernoulli, 1 one-hot groups, 2 axial,
+                                    // 3 Algorithm 4 (customized 3D assignment)
   int axial_I = 0;
+  int a4_gamma = 1, a4_L = 0;       // Algorithm 4: entries gamma*I, steps L
   int64_t ngroups = 0;
   int64_t grp_off = 0;              // offset into the group tables
   int64_t nrep = 0, rep_off = 0;
@@ -272,6 +274,10 @@ struct gfors_ctx {
   int64_t* sr_row = nullptr;        // global row of each instance
   float* sr_kv = nullptr;           // K entry of every variable (0 if none)
   float2* sr_part = nullptr;        // [2][sr_nchunk] compensated partial sums
+  // Algorithm 4 scratch: slab top lists, partial assignment
+  unsigned long long* a4_cand = nullptr;   // up to 16384 keys
+  int32_t* a4_J0 = nullptr;                // 64
+  int32_t* a4_K0 = nullptr;                // 64
   // L2-resident sparse problems: one cooperative launch per call
   bool coop_ok = false;
   int32_t *coop_rblk = nullptr, *coop_rwarp = nullptr, *coop_cblk = nullptr,

@@ -1,0 +1,214 @@
+// k_assign.cu -- Algorithm 4 (customized sampling for the 3D assignment,
+// Section 2.4.2) on the device.  Readings (the paper gives the outline):
+//   (a) the gamma*I largest entries of p, ordered by p descending, then by
+//       variable index ascending;
+//   (b) greedy partial assignment: an entry (i,j,k) is accepted when i, j
+//       and k are all unused;
+//   (c) every candidate completes it: the free j's and the free k's (each
+//       ascending) are shuffled by Fisher-Yates (q = F-1 down to 1,
+//       r = floor(u (q+1) / 2^32), u = Philox lane of stream 6, index t of
+//       the t-th draw, j's first) and handed in turn to the free i's;
+//   (d) then up to L steps, each applying the single best strictly improving
+//       pairwise interchange between the triples of i = a < i = b (type 0:
+//       exchange j, type 1: exchange k; exact integer costs; ties to the
+//       smallest (a, b, type)); a step without improvement ends the search.
+// Kernels: per-slab top-K by a bitonic sort of 64-bit keys (p bits, then the
+// complemented index) in shared memory; one block merges the slab lists
+// (the global top K lie in the union of the slabs' top K) and runs (b);
+// one block per candidate runs (c) and (d).
+#include "internal.cuh"
+
+namespace {
+
+// Descending bitonic sort of N (power of two) keys in shared memory.
+GF_DEV void bitonic_desc(unsigned long long* key, int N) {
+  for (int k = 2; k <= N; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+        const int ixj = idx ^ j;
+        if (ixj > idx) {
+          const unsigned long long a = key[idx], b = key[ixj];
+          const bool desc = (idx & k) == 0;
+          if (desc ? (a < b) : (a > b)) { key[idx] = b; key[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+GF_DEV unsigned long long pkey(float p, uint32_t v) {
+  // p in [0, 1]: its IEEE bits order like its value (-0 and negatives as 0);
+  // ties by index ascending
+  return ((unsigned long long)__float_as_uint(p > 0.0f ? p : 0.0f) << 32) |
+         (unsigned long long)(0xFFFFFFFFu - v);
+}
+
+__global__ void __launch_bounds__(1024)
+k_a4_slabtop(const float* __restrict__ p, int64_t v0, int I, int K,
+             unsigned long long* __restrict__ out) {
+  extern __shared__ unsigned long long key[];
+  const int i = blockIdx.x;
+  const int P = I * I;
+  int N = 1;
+  while (N < P) N <<= 1;
+  for (int q = threadIdx.x; q < N; q += blockDim.x)
+    key[q] = q < P ? pkey(p[v0 + (int64_t)i * P + q], (uint32_t)(i * P + q)) : 0ull;
+  __syncthreads();
+  bitonic_desc(key, N);
+  for (int q = threadIdx.x; q < K; q += blockDim.x) out[(int64_t)i * K + q] = key[q];
+}
+
+__global__ void __launch_bounds__(1024)
+k_a4_partial(const unsigned long long* __restrict__ cand, int I, int K,
+             int32_t* __restrict__ J0, int32_t* __restrict__ K0) {
+  extern __shared__ unsigned long long key[];
+  const int total = I * K;
+  int N = 1;
+  while (N < total) N <<= 1;
+  for (int q = threadIdx.x; q < N; q += blockDim.x) key[q] = q < total ? cand[q] : 0ull;
+  __syncthreads();
+  bitonic_desc(key, N);
+  if (threadIdx.x == 0) {
+    unsigned long long uj = 0ull, uk = 0ull;
+    for (int a = 0; a < I; ++a) { J0[a] = -1; K0[a] = -1; }
+    for (int e = 0; e < K; ++e) {
+      const uint32_t v = 0xFFFFFFFFu - (uint32_t)(key[e] & 0xFFFFFFFFull);
+      const int i = (int)(v / (uint32_t)(I * I)), j = (int)((v / I) % I), k = (int)(v % I);
+      if (J0[i] < 0 && !((uj >> j) & 1ull) && !((uk >> k) & 1ull)) {
+        J0[i] = j;
+        K0[i] = k;
+        uj |= 1ull << j;
+        uk |= 1ull << k;
+      }
+    }
+  }
+}
+
+constexpr int kA4Threads = 256;
+
+__global__ void __launch_bounds__(kA4Threads)
+k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
+            const long long* __restrict__ cost, int64_t v0, int I, int L, int s0, int len,
+            uint64_t seed, int inst, const GfDState* __restrict__ st, int kw,
+            uint32_t* __restrict__ X) {
+  __shared__ int32_t J[64], Kk[64], fi[64], fj[64], fk[64];
+  __shared__ long long cold[64];
+  __shared__ long long wbest[kA4Threads / 32];
+  __shared__ int wcode[kA4Threads / 32];
+  __shared__ int go;
+  const int sidx = blockIdx.x;
+  if (sidx >= len) return;
+  const uint32_t s = (uint32_t)(s0 + sidx);
+  const uint32_t round = st->round_id;
+  const long long* c = cost + v0;
+  auto C3 = [&](int i, int j, int k) { return __ldg(c + ((int64_t)i * I + j) * I + k); };
+  if (threadIdx.x == 0) {
+    // (c) completion of the partial assignment
+    int F = 0, Fj = 0, Fk = 0;
+    unsigned long long uj = 0ull, uk = 0ull;
+    for (int a = 0; a < I; ++a) {
+      J[a] = J0[a];
+      Kk[a] = K0[a];
+      if (J0[a] < 0) fi[F++] = a;
+      else { uj |= 1ull << J0[a]; uk |= 1ull << K0[a]; }
+    }
+    for (int a = 0; a < I; ++a) {
+      if (!((uj >> a) & 1ull)) fj[Fj++] = a;
+      if (!((uk >> a) & 1ull)) fk[Fk++] = a;
+    }
+    uint64_t t = 0;
+    for (int q = F - 1; q >= 1; --q, ++t) {
+      const uint4 u4 = gf::philox_call(seed, 6u, (uint32_t)inst, round, s, t >> 2);
+      const uint32_t u = gf::lane_of(u4, (uint32_t)(t & 3));
+      const int r = (int)(((unsigned long long)u * (unsigned long long)(q + 1)) >> 32);
+      const int tmp = fj[q]; fj[q] = fj[r]; fj[r] = tmp;
+    }
+    for (int q = F - 1; q >= 1; --q, ++t) {
+      const uint4 u4 = gf::philox_call(seed, 6u, (uint32_t)inst, round, s, t >> 2);
+      const uint32_t u = gf::lane_of(u4, (uint32_t)(t & 3));
+      const int r = (int)(((unsigned long long)u * (unsigned long long)(q + 1)) >> 32);
+      const int tmp = fk[q]; fk[q] = fk[r]; fk[r] = tmp;
+    }
+    for (int e = 0; e < F; ++e) { J[fi[e]] = fj[e]; Kk[fi[e]] = fk[e]; }
+    go = 1;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < I; a += kA4Threads) cold[a] = C3(a, J[a], Kk[a]);
+  __syncthreads();
+  // (d) best-improvement pairwise interchanges
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int step = 0; step < L; ++step) {
+    long long best = 0;
+    int code = 0x7FFFFFFF;
+    for (int u = threadIdx.x; u < I * I; u += kA4Threads) {
+      const int a = u / I, b = u - a * I;
+      if (b <= a) continue;
+      const long long old = cold[a] + cold[b];
+      const long long d0 = C3(a, J[b], Kk[a]) + C3(b, J[a], Kk[b]) - old;
+      const long long d1 = C3(a, J[a], Kk[b]) + C3(b, J[b], Kk[a]) - old;
+      if (d0 < best || (d0 == best && d0 < 0 && 2 * u < code)) { best = d0; code = 2 * u; }
+      if (d1 < best || (d1 == best && d1 < 0 && 2 * u + 1 < code)) { best = d1; code = 2 * u + 1; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const long long ob = __shfl_down_sync(0xFFFFFFFFu, best, off);
+      const int oc = __shfl_down_sync(0xFFFFFFFFu, code, off);
+      if (ob < best || (ob == best && oc < code)) { best = ob; code = oc; }
+    }
+    if (lane == 0) { wbest[warp] = best; wcode[warp] = code; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long bb = 0;
+      int bc = 0x7FFFFFFF;
+      for (int w = 0; w < kA4Threads / 32; ++w)
+        if (wbest[w] < bb || (wbest[w] == bb && wcode[w] < bc)) { bb = wbest[w]; bc = wcode[w]; }
+      if (bb < 0) {
+        const int u = bc >> 1, type = bc & 1;
+        const int a = u / I, b = u - a * I;
+        if (type == 0) { const int tmp = J[a]; J[a] = J[b]; J[b] = tmp; }
+        else { const int tmp = Kk[a]; Kk[a] = Kk[b]; Kk[b] = tmp; }
+        cold[a] = C3(a, J[a], Kk[a]);
+        cold[b] = C3(b, J[b], Kk[b]);
+      } else {
+        go = 0;
+      }
+    }
+    __syncthreads();
+    if (!go) break;
+  }
+  for (int a = threadIdx.x; a < I; a += kA4Threads) {
+    const int64_t var = v0 + ((int64_t)a * I + J[a]) * I + Kk[a];
+    atomicOr(&X[var * kw + (sidx >> 5)], 1u << (sidx & 31));
+  }
+}
+
+}  // namespace
+
+// Candidates [s0, s0+len) of instance b drawn by Algorithm 4 from p.
+cudaError_t gf_launch_assign_custom(GfCtx* h, int b, const float* p, int s0, int len) {
+  const GfInstHost& I = h->ih[b];
+  const int n1 = I.axial_I, K = I.a4_gamma * n1, P = n1 * n1;
+  int N1 = 1;
+  while (N1 < P) N1 <<= 1;
+  int N2 = 1;
+  while (N2 < n1 * K) N2 <<= 1;
+  cudaError_t e;
+  if (K > 0) {
+    k_a4_slabtop<<<n1, 1024, sizeof(unsigned long long) * N1, h->stream>>>(p, I.var_off, n1, K,
+                                                                            h->a4_cand);
+    if ((e = cudaFuncSetAttribute(k_a4_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(unsigned long long) * N2))))
+      return e;
+    k_a4_partial<<<1, 1024, sizeof(unsigned long long) * N2, h->stream>>>(h->a4_cand, n1, K,
+                                                                          h->a4_J0, h->a4_K0);
+    h->launches += 2;
+  } else {
+    cudaMemsetAsync(h->a4_J0, 0xFF, sizeof(int32_t) * n1, h->stream);
+    cudaMemsetAsync(h->a4_K0, 0xFF, sizeof(int32_t) * n1, h->stream);
+  }
+  k_a4_sample<<<len, kA4Threads, 0, h->stream>>>(h->a4_J0, h->a4_K0, h->cint, I.var_off, n1,
+                                                 I.a4_L, s0, len, h->prm.seed,
+                                                 h->prm.inst_base + b, h->dstate, h->kw, h->X);
+  h->launches++;
+  return cudaGetLastError();
+}

@@ -498,7 +498,7 @@ cudaError_t gf_launch_features(GfCtx* h) {
     k_group_max<<<(unsigned)((h->ngroups_tot * 32 + 255) / 256), 256, 0, s>>>(
         h->grp_ptr, h->grp_idx, h->ngroups_tot, xk, h->grpmax);
   for (int b = 0; b < h->ninst; ++b)
-    if (h->ih[b].group_mode == 2)
+    if (h->ih[b].group_mode == 2 || h->ih[b].group_mode == 3)
       k_slab_max<<<h->ih[b].axial_I, 256, 0, s>>>(xk, h->ih[b].var_off, h->ih[b].axial_I,
                                                   h->grpmax);
   const float rf = (float)(h->prm.rho_max > 0 ? h->rho_host / h->prm.rho_max : 0.0);

@@ -473,7 +473,7 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   // axial instances need zeroed words (bits are OR-ed in)
   for (int b = 0; b < h->ninst; ++b) {
     const GfInstHost& I = h->ih[b];
-    if (I.group_mode == 2) {
+    if (I.group_mode == 2 || I.group_mode == 3) {
       e = cudaMemsetAsync(h->X + I.var_off * h->kw, 0, sizeof(uint32_t) * I.npad * h->kw,
                           h->stream);
       if (e != cudaSuccess) return e;
@@ -500,6 +500,12 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   }
   for (int b = 0; b < h->ninst; ++b) {
     const GfInstHost& I = h->ih[b];
+    if (I.group_mode == 3) {
+      extern cudaError_t gf_launch_assign_custom(GfCtx * h, int b, const float* p, int s0,
+                                                 int len);
+      if ((e = gf_launch_assign_custom(h, b, p, s0, len)) != cudaSuccess) return e;
+      continue;
+    }
     if (I.group_mode != 2) continue;
     if (I.axial_I <= 64 && I.axial_I * I.axial_I <= kAxMaxP)
       k_axial_grp<<<(len + kAxCands - 1) / kAxCands, kAxGroup * kAxCands, 0, h->stream>>>(

@@ -197,6 +197,11 @@ class Handle:
     def sample_eval(self, nrounds, first_round_id, proposal=0):
         _check(_lib.gfors_sample_eval(self.h, nrounds, first_round_id, proposal), self.h)
 
+    def set_assign3d_custom(self, inst, I, gamma=1, L=None):
+        """Algorithm 4 sampler for instance inst (L defaults to I steps)."""
+        _check(_lib.gfors_set_assign3d_custom(self.h, inst, I, gamma, I if L is None else L),
+               self.h)
+
     def dense_info(self, inst=0):
         """(dense, tensor-core exact, fp8 operands, max|W2|) of instance inst."""
         out = np.zeros(4, np.int64)
@@ -390,7 +395,10 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
     H = Handle(h.value, list(insts))
     if setup:
         for q, I in enumerate(insts):
-            if I.axial_I:
+            if I.axial_I and I.meta.get("sampler") == "alg4":
+                H.set_assign3d_custom(q, I.axial_I, I.meta.get("gamma", 1),
+                                      I.meta.get("L", I.axial_I))
+            elif I.axial_I:
                 H.set_groups(q, 2, None, I.axial_I)
             elif I.groups is not None:
                 H.set_groups(q, 1, I.groups)
@@ -400,6 +408,7 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
 
 
 _lib.gfors_sample_eval_range.argtypes = [vp, i32, u32, i32, i32, i32]
+_lib.gfors_set_assign3d_custom.argtypes = [vp, i32, i32, i32, i32]
 _lib.gfors_dense_info.argtypes = [vp, i32, vp]
 _lib.gfors_incumbent_key_async.argtypes = [vp, i32, vp]
 _lib.gfors_autotune.argtypes = [vp, C.c_char_p, vp, vp]

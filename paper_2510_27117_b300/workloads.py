@@ -150,7 +150,10 @@ def knapsack_batch(ninst: int = 512, nmin: int = 1000, nmax: int = 100000,
 # --------------------------------------------------------------------------
 # Axial 3D assignment (Eq. assign3d, Section 2.4.2).
 # --------------------------------------------------------------------------
-def assign3d(I: int = 64, idx: int = 0, family: int = A3D) -> Instance:
+def assign3d(I: int = 64, idx: int = 0, family: int = A3D, sampler: str = "axial",
+             gamma: int = 1, L: Optional[int] = None) -> Instance:
+    """Axial 3D assignment; sampler 'axial' (one (j,k) per i by p) or 'alg4'
+    (the paper's customized sampler with gamma*I entries and L steps)."""
     rng = _rng(family, idx)
     n = I ** 3
     c = rng.integers(1, 101, size=n).astype(np.float64)
@@ -161,8 +164,11 @@ def assign3d(I: int = 64, idx: int = 0, family: int = A3D) -> Instance:
     B = _csr(rows, cols, np.ones(3 * n), (3 * I, n))
     grp_ptr = np.arange(0, n + 1, I * I, dtype=np.int64)      # rows "per i"
     grp_idx = v.copy()
-    return Instance(f"assign3d_I{I}_s{idx}", n, c, B=B, d=np.ones(3 * I),
+    inst = Instance(f"assign3d_I{I}_s{idx}", n, c, B=B, d=np.ones(3 * I),
                     groups=(grp_ptr, grp_idx), axial_I=I)
+    if sampler == "alg4":
+        inst.meta.update(sampler="alg4", gamma=gamma, L=I if L is None else L)
+    return inst
 
 
 # --------------------------------------------------------------------------

@@ -421,3 +421,25 @@ def test_cooperative_path_matches_launch_path():
     assert np.max(np.abs(xa - xb)) < 1e-5 and np.max(np.abs(xba - xbb)) < 2e-5
     assert np.max(np.abs(ya - yb)) <= 1e-5 * (1 + np.max(np.abs(yb)))
     assert sa[6] == sb[6] and sa[7] == sb[7]
+
+
+@pytest.mark.parametrize("I,gamma,L,k_b", [(6, 1, 6, 64), (16, 2, 16, 96), (64, 1, 64, 128),
+                                           (9, 0, 3, 32), (12, 1, 0, 64)])
+def test_alg4_sampler_bit_exact(I, gamma, L, k_b):
+    """Algorithm 4 on the device against the oracle: identical candidates
+    (top entries with ties, greedy partial assignment, Philox completion,
+    best-improvement interchanges), all feasible, same objectives."""
+    inst = W.assign3d(I=I, idx=3, sampler="alg4", gamma=gamma, L=L)
+    gp, op = _params(k_b=k_b)
+    H = G.load(inst, gp)
+    rng = np.random.default_rng(I + gamma)
+    p = np.round(rng.random(inst.n) ** 3, 2).astype(np.float32)     # many ties
+    H.set_iterate(0, p, p, None)
+    H.sample_eval(1, 6, 0)
+    X, viol, obj = H.get_samples(0)
+    Xo = O.sample(inst, p, k_b, op.seed, 0, 6)
+    assert np.array_equal(X, Xo)
+    assert np.all(viol == 0)
+    vo, oo = O.Evaluator(inst)(Xo)
+    assert np.array_equal(obj, oo)
+    H.destroy()
