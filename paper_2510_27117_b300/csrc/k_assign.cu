@@ -85,24 +85,50 @@ k_a4_partial(const unsigned long long* __restrict__ cand, int I, int K,
 }
 
 constexpr int kA4Threads = 256;
+constexpr int kA4MaxPairs = 64 * 63 / 2;
 
+// Index of the pair (a, b), a < b, in lexicographic order.
+GF_DEV int pair_index(int a, int b, int I) { return a * (2 * I - a - 1) / 2 + (b - a - 1); }
+
+// One block per candidate.  The interchange search keeps the gain of every
+// (pair, type) in shared memory: an applied interchange at (a, b) changes
+// only the gains of pairs that contain a or b, so a step rescans the table
+// and recomputes those 4 (I - 1) entries instead of all 2 I (I - 1) / 2.
+// Gains are exact integers, so the chosen interchange is the same as with a
+// full recomputation.
 __global__ void __launch_bounds__(kA4Threads)
 k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
             const long long* __restrict__ cost, int64_t v0, int I, int L, int s0, int len,
             uint64_t seed, int inst, const GfDState* __restrict__ st, int kw,
             uint32_t* __restrict__ X) {
   __shared__ int32_t J[64], Kk[64], fi[64], fj[64], fk[64];
-  __shared__ long long cold[64];
+  __shared__ uint32_t ufy[128];                  // Fisher-Yates draws
+  __shared__ long long cold[64];                 // cost of the triple at each i
+  __shared__ long long gain[2 * kA4MaxPairs];    // [pair][type]
+  __shared__ uint8_t pa[kA4MaxPairs], pb[kA4MaxPairs];
   __shared__ long long wbest[kA4Threads / 32];
   __shared__ int wcode[kA4Threads / 32];
-  __shared__ int go;
+  __shared__ int sel;
   const int sidx = blockIdx.x;
   if (sidx >= len) return;
+  const int tid = threadIdx.x;
   const uint32_t s = (uint32_t)(s0 + sidx);
   const uint32_t round = st->round_id;
   const long long* c = cost + v0;
   auto C3 = [&](int i, int j, int k) { return __ldg(c + ((int64_t)i * I + j) * I + k); };
-  if (threadIdx.x == 0) {
+  const int np = I * (I - 1) / 2;
+  // draws t = 0 .. 2I-3 cover the j shuffle (t < F-1) and the k shuffle
+  for (int t = tid; t < 2 * I - 2; t += kA4Threads) {
+    const uint4 u4 = gf::philox_call(seed, 6u, (uint32_t)inst, round, s, (uint64_t)t >> 2);
+    ufy[t] = gf::lane_of(u4, (uint32_t)(t & 3));
+  }
+  for (int a = tid; a < I; a += kA4Threads)
+    for (int b = a + 1, q = pair_index(a, a + 1, I); b < I; ++b, ++q) {
+      pa[q] = (uint8_t)a;
+      pb[q] = (uint8_t)b;
+    }
+  __syncthreads();
+  if (tid == 0) {
     // (c) completion of the partial assignment
     int F = 0, Fj = 0, Fk = 0;
     unsigned long long uj = 0ull, uk = 0ull;
@@ -116,38 +142,35 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
       if (!((uj >> a) & 1ull)) fj[Fj++] = a;
       if (!((uk >> a) & 1ull)) fk[Fk++] = a;
     }
-    uint64_t t = 0;
+    int t = 0;
     for (int q = F - 1; q >= 1; --q, ++t) {
-      const uint4 u4 = gf::philox_call(seed, 6u, (uint32_t)inst, round, s, t >> 2);
-      const uint32_t u = gf::lane_of(u4, (uint32_t)(t & 3));
-      const int r = (int)(((unsigned long long)u * (unsigned long long)(q + 1)) >> 32);
+      const int r = (int)(((unsigned long long)ufy[t] * (unsigned long long)(q + 1)) >> 32);
       const int tmp = fj[q]; fj[q] = fj[r]; fj[r] = tmp;
     }
     for (int q = F - 1; q >= 1; --q, ++t) {
-      const uint4 u4 = gf::philox_call(seed, 6u, (uint32_t)inst, round, s, t >> 2);
-      const uint32_t u = gf::lane_of(u4, (uint32_t)(t & 3));
-      const int r = (int)(((unsigned long long)u * (unsigned long long)(q + 1)) >> 32);
+      const int r = (int)(((unsigned long long)ufy[t] * (unsigned long long)(q + 1)) >> 32);
       const int tmp = fk[q]; fk[q] = fk[r]; fk[r] = tmp;
     }
     for (int e = 0; e < F; ++e) { J[fi[e]] = fj[e]; Kk[fi[e]] = fk[e]; }
-    go = 1;
   }
   __syncthreads();
-  for (int a = threadIdx.x; a < I; a += kA4Threads) cold[a] = C3(a, J[a], Kk[a]);
+  for (int a = tid; a < I; a += kA4Threads) cold[a] = C3(a, J[a], Kk[a]);
+  __syncthreads();
+  auto pair_gains = [&](int q, int a, int b) {
+    const long long old = cold[a] + cold[b];
+    gain[2 * q] = C3(a, J[b], Kk[a]) + C3(b, J[a], Kk[b]) - old;       // exchange j
+    gain[2 * q + 1] = C3(a, J[a], Kk[b]) + C3(b, J[b], Kk[a]) - old;   // exchange k
+  };
+  for (int q = tid; q < np; q += kA4Threads) pair_gains(q, pa[q], pb[q]);
   __syncthreads();
   // (d) best-improvement pairwise interchanges
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = tid >> 5, lane = tid & 31;
   for (int step = 0; step < L; ++step) {
-    long long best = 0;
+    long long best = 0;                          // only strict improvements count
     int code = 0x7FFFFFFF;
-    for (int u = threadIdx.x; u < I * I; u += kA4Threads) {
-      const int a = u / I, b = u - a * I;
-      if (b <= a) continue;
-      const long long old = cold[a] + cold[b];
-      const long long d0 = C3(a, J[b], Kk[a]) + C3(b, J[a], Kk[b]) - old;
-      const long long d1 = C3(a, J[a], Kk[b]) + C3(b, J[b], Kk[a]) - old;
-      if (d0 < best || (d0 == best && d0 < 0 && 2 * u < code)) { best = d0; code = 2 * u; }
-      if (d1 < best || (d1 == best && d1 < 0 && 2 * u + 1 < code)) { best = d1; code = 2 * u + 1; }
+    for (int e = tid; e < 2 * np; e += kA4Threads) {
+      const long long g = gain[e];
+      if (g < best) { best = g; code = e; }      // ascending e: ties keep the first
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -157,26 +180,36 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
     }
     if (lane == 0) { wbest[warp] = best; wcode[warp] = code; }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       long long bb = 0;
       int bc = 0x7FFFFFFF;
       for (int w = 0; w < kA4Threads / 32; ++w)
         if (wbest[w] < bb || (wbest[w] == bb && wcode[w] < bc)) { bb = wbest[w]; bc = wcode[w]; }
       if (bb < 0) {
-        const int u = bc >> 1, type = bc & 1;
-        const int a = u / I, b = u - a * I;
-        if (type == 0) { const int tmp = J[a]; J[a] = J[b]; J[b] = tmp; }
+        const int q = bc >> 1, a = pa[q], b = pb[q];
+        if ((bc & 1) == 0) { const int tmp = J[a]; J[a] = J[b]; J[b] = tmp; }
         else { const int tmp = Kk[a]; Kk[a] = Kk[b]; Kk[b] = tmp; }
         cold[a] = C3(a, J[a], Kk[a]);
         cold[b] = C3(b, J[b], Kk[b]);
+        sel = q;
       } else {
-        go = 0;
+        sel = -1;
       }
     }
     __syncthreads();
-    if (!go) break;
+    const int q = sel;
+    if (q < 0) break;
+    const int a = pa[q], b = pb[q];
+    // pairs (a, x) for every x != a, then (b, x) for x not in {a, b}
+    for (int t = tid; t < 2 * I; t += kA4Threads) {
+      const int u = t < I ? a : b, x = t < I ? t : t - I;
+      if (x == u || (t >= I && x == a)) continue;
+      const int lo = u < x ? u : x, hi = u < x ? x : u;
+      pair_gains(pair_index(lo, hi, I), lo, hi);
+    }
+    __syncthreads();
   }
-  for (int a = threadIdx.x; a < I; a += kA4Threads) {
+  for (int a = tid; a < I; a += kA4Threads) {
     const int64_t var = v0 + ((int64_t)a * I + J[a]) * I + Kk[a];
     atomicOr(&X[var * kw + (sidx >> 5)], 1u << (sidx & 31));
   }

@@ -479,7 +479,14 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
       if (e != cudaSuccess) return e;
     }
   }
-  if (h->N > 0) {
+  // Bernoulli bits are needed unless every instance is drawn by a group
+  // sampler over all its variables or is a dense tensor-core instance
+  bool bits = false;
+  for (int b = 0; b < h->ninst; ++b) {
+    const GfInstHost& I = h->ih[b];
+    if (!(I.group_mode == 2 || I.group_mode == 3 || I.qkind == 1)) bits = true;
+  }
+  if (h->N > 0 && bits) {
     const int64_t N4 = h->N / 4;
     const int64_t threads = N4 * kw;
     k_bern_bits<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(
