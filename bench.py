@@ -34,6 +34,11 @@ WORKLOADS = {
     "maxcut": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).max_cut(
         n=4096, p=0.5, idx=r), 50, 8192,
         "max cut G(4096,0.5) +-1 weights, Q=-L dense, 8192 candidates/round, k_int=50"),
+    "maxcut_sparse": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"])
+                      .max_cut_sparse(n=65536, avg_deg=32.0, idx=r), 50, 8192,
+                      "max cut on a sparse random graph n=65,536, average degree 32, weights "
+                      "U{-8..10} (the paper's range), Q as CSR (sparse-Q path), 8192 "
+                      "candidates/round, k_int=50"),
     "setcover": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).set_cover(
         n=2000, m=200, density=0.05, idx=r), 50, 1024,
         "set cover n=2000 m=200 Bernoulli(0.05), 1024 candidates/round, k_int=50"),
@@ -62,9 +67,11 @@ WORKLOADS = {
                  "(random-init weights)"),
 }
 # rounds per step and proposal (0 plain x_k, 1 learned) of each workload
-ROUNDS = {"maxcut": 1, "setcover": 1, "setcover_batch": 1, "knapsack": 1, "assign3d": 1,
+ROUNDS = {"maxcut": 1, "maxcut_sparse": 1, "setcover": 1, "setcover_batch": 1, "knapsack": 1,
+          "assign3d": 1,
           "assign3d_alg4": 1, "facility": 4}
-PROPOSAL = {"maxcut": 0, "setcover": 0, "setcover_batch": 0, "knapsack": 0, "assign3d": 1,
+PROPOSAL = {"maxcut": 0, "maxcut_sparse": 0, "setcover": 0, "setcover_batch": 0, "knapsack": 0,
+            "assign3d": 1,
             "assign3d_alg4": 0, "facility": 1}
 
 
@@ -349,7 +356,8 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False):
     n = sum(I.n for I in insts)
     nnz = sum(I.nnz() for I in insts)
     m = sum(I.m1 + I.m2 for I in insts)
-    alg = {"setcover": (16 * nnz + 4 * (6 * n + 4 * m), "2 nnz (4+4) + 4 (6n + 4m)"),
+    alg = {"maxcut_sparse": (8 * nnz + 24 * n, "8 nnz(Q) + 24 n"),
+           "setcover": (16 * nnz + 4 * (6 * n + 4 * m), "2 nnz (4+4) + 4 (6n + 4m)"),
            "setcover_batch": (16 * nnz + 4 * (6 * n + 4 * m), "2 nnz (4+4) + 4 (6n + 4m)"),
            "knapsack": (16 * n, "16 sum n_i (read x, w, c; write x)"),
            "assign3d": (16 * nnz, "16 nnz"),

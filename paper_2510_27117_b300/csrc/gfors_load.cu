@@ -884,6 +884,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     for (int bk = 0; bk < 5; ++bk) {
       GfBucket B;
       B.lanes = lanes_of[bk];
+      B.short_ok = bk == 0;
       B.count = (int32_t)rl[bk].size();
       if (B.count) {
         std::vector<GfRun> runs;
@@ -939,6 +940,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     for (int bk = 0; bk < 5; ++bk) {
       GfBucket B;
       B.lanes = lanes_of[bk];
+      B.short_ok = bk == 0;
       B.count = (int32_t)cl[bk].size();
       if (B.count) {
         std::vector<GfRun> runs;
@@ -985,7 +987,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     std::vector<GfObjChunk> oc;
     std::vector<GfQChunk> qc;
     std::vector<int64_t> QIp(N + 1, 0);
-    std::vector<int32_t> QIc, QIv;
+    std::vector<int32_t> QIc;
     for (int q = 0; q < ninst; ++q) {
       const GfInstHost& I = h->ih[q];
       if (!I.integral) continue;
@@ -1011,24 +1013,97 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
           oc.push_back(GfObjChunk{q, (int32_t)(I.var_off + a),
                                   (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 1024)), 0});
       if (I.qkind == 2) {
-        for (int64_t i = 0; i < I.n; ++i) QIp[I.var_off + i + 1] = S.Qorig.len(i);
         for (int64_t a = 0; a < I.n; a += 64)
           qc.push_back(GfQChunk{q, (int32_t)(I.var_off + a),
                                 (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 64)), 0});
       }
     }
-    for (int64_t i = 0; i < N; ++i) QIp[i + 1] += QIp[i];
-    QIc.resize(QIp[N]);
-    QIv.resize(QIp[N]);
-    for (int q = 0; q < ninst; ++q) {
-      const GfInstHost& I = h->ih[q];
-      if (!I.integral || I.qkind != 2) continue;
-      for (int64_t i = 0; i < I.n; ++i) {
-        int64_t t = QIp[I.var_off + i];
-        for (int64_t u = 0; u < st[q].Qorig.len(i); ++u, ++t) {
-          QIc[t] = (int32_t)(I.var_off + st[q].Qorig.c(i)[u]);
-          QIv[t] = (int32_t)st[q].Qorig.v(i)[u];
+    // Sparse Q for evaluation: x^T Q x = sum_i q_ii x_i + sum_{i<j} w_ij x_i x_j
+    // with w_ij = q_ij + q_ji; the diagonal joins the linear costs (x_i^2 =
+    // x_i), the pairs are stored once, in row i = min, with per-row bias
+    // -min w and the bit width of max w - min w (bit-plane evaluation).
+    std::vector<long long> clin;
+    std::vector<long long> QIv;
+    std::vector<long long> QIb;
+    std::vector<uint8_t> QIw;
+    bool anyq = false;
+    for (int q = 0; q < ninst; ++q) anyq |= h->ih[q].integral && h->ih[q].qkind == 2;
+    if (anyq) {
+      clin = cint;
+      QIb.assign(N, 0);
+      QIw.assign(N, 0);
+      std::vector<std::vector<std::pair<int32_t, long long>>> pr2(ninst);
+      std::vector<std::vector<int64_t>> cnt(ninst);
+      const std::string ex = parallel_for(ninst, [&](int q) {
+        const GfInstHost& I = h->ih[q];
+        if (!I.integral || I.qkind != 2) return;
+        const RowSet& Qo = st[q].Qorig;
+        std::vector<int64_t>& pp = cnt[q];
+        pp.assign(I.n + 1, 0);
+        for (int64_t i = 0; i < I.n; ++i)
+          for (int64_t u = 0; u < Qo.len(i); ++u) {
+            const int64_t j = Qo.c(i)[u];
+            if (j != i) pp[std::min(i, j) + 1]++;
+          }
+        for (int64_t i = 0; i < I.n; ++i) pp[i + 1] += pp[i];
+        std::vector<std::pair<int32_t, long long>>& e = pr2[q];
+        e.resize(pp[I.n]);
+        std::vector<int64_t> fill(pp.begin(), pp.end() - 1);
+        for (int64_t i = 0; i < I.n; ++i)
+          for (int64_t u = 0; u < Qo.len(i); ++u) {
+            const int64_t j = Qo.c(i)[u];
+            const long long v = (long long)Qo.v(i)[u];
+            if (j == i) clin[I.var_off + i] += v;
+            else e[fill[std::min(i, j)]++] = {(int32_t)std::max(i, j), v};
+          }
+        // per row: sort by column, merge, drop zero sums; compact in place
+        int64_t outp = 0;
+        for (int64_t i = 0; i < I.n; ++i) {
+          const int64_t a = pp[i], b = pp[i + 1];
+          std::sort(e.begin() + a, e.begin() + b);
+          const int64_t start = outp;
+          for (int64_t u = a; u < b;) {
+            int64_t w = u;
+            long long sum = 0;
+            while (w < b && e[w].first == e[u].first) sum += e[w++].second;
+            if (sum != 0) e[outp++] = {e[u].first, sum};
+            u = w;
+          }
+          pp[i] = start;
         }
+        pp[I.n] = outp;
+        e.resize(outp);
+        for (int64_t i = 0; i < I.n; ++i) {
+          long long lo = 0, hi = 0;
+          for (int64_t u = pp[i]; u < pp[i + 1]; ++u) {
+            if (u == pp[i] || e[u].second < lo) lo = e[u].second;
+            if (u == pp[i] || e[u].second > hi) hi = e[u].second;
+          }
+          const unsigned long long span = (unsigned long long)(hi - lo);
+          int bits = 0;
+          while (bits < 64 && (span >> bits) != 0ull) ++bits;
+          QIb[I.var_off + i] = -lo;
+          QIw[I.var_off + i] = (uint8_t)bits;
+        }
+      });
+      if (!ex.empty()) return gf_fail(h, GFORS_E_OOM, "sparse Q pairs: " + ex);
+      for (int q = 0; q < ninst; ++q) {
+        const GfInstHost& I = h->ih[q];
+        if (cnt[q].empty()) continue;
+        for (int64_t i = 0; i < I.n; ++i) QIp[I.var_off + i + 1] = cnt[q][i + 1] - cnt[q][i];
+      }
+      for (int64_t i = 0; i < N; ++i) QIp[i + 1] += QIp[i];
+      QIc.resize(QIp[N]);
+      QIv.resize(QIp[N]);
+      for (int q = 0; q < ninst; ++q) {
+        const GfInstHost& I = h->ih[q];
+        if (cnt[q].empty()) continue;
+        int64_t t = QIp[I.var_off];
+        for (const auto& pe : pr2[q]) {
+          QIc[t] = (int32_t)(I.var_off + pe.first);
+          QIv[t++] = pe.second;
+        }
+        std::vector<std::pair<int32_t, long long>>().swap(pr2[q]);
       }
     }
     h->nurows = (int64_t)ur.size();
@@ -1046,7 +1121,12 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     ALLOC(h->qchunks, GfQChunk, qc.size());
     ALLOC(h->QIp, int64_t, N + 1);
     ALLOC(h->QIc, int32_t, QIc.size());
-    ALLOC(h->QIv, int32_t, QIv.size());
+    ALLOC(h->QIv, long long, QIv.size());
+    if (anyq) {
+      ALLOC(h->QIb, long long, N);
+      ALLOC(h->QIw, uint8_t, N);
+      ALLOC(h->clin, long long, N);
+    }
     ALLOC(h->cint, long long, N);
     if (!ur.empty()) UP(h->urows, ur.data(), GfURow, ur.size());
     if (!ucols.empty()) UP(h->ucols, ucols.data(), int32_t, ucols.size());
@@ -1058,7 +1138,12 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     if (!qc.empty()) UP(h->qchunks, qc.data(), GfQChunk, qc.size());
     UP(h->QIp, QIp.data(), int64_t, N + 1);
     if (!QIc.empty()) UP(h->QIc, QIc.data(), int32_t, QIc.size());
-    if (!QIv.empty()) UP(h->QIv, QIv.data(), int32_t, QIv.size());
+    if (!QIv.empty()) UP(h->QIv, QIv.data(), long long, QIv.size());
+    if (anyq) {
+      UP(h->QIb, QIb.data(), long long, N);
+      UP(h->QIw, QIw.data(), uint8_t, N);
+      UP(h->clin, clin.data(), long long, N);
+    }
     UP(h->cint, cint.data(), long long, N);
   }
 

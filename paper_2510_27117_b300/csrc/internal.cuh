@@ -43,6 +43,7 @@ struct GfBucket {
   GfRun* runs = nullptr;            // device runs covering the bucket, in order
   int64_t* run_ptr = nullptr;       // device prefix of run counts (nruns + 1)
   int32_t nruns = 0;
+  bool short_ok = false;            // every member has <= 2 nonzeros
 };
 
 struct GfLongSet {
@@ -209,7 +210,11 @@ struct gfors_ctx {
   GfGRow* grows = nullptr; int64_t ngrows = 0; int32_t* gcols = nullptr; int32_t* gvals = nullptr;
   long long* cint = nullptr;        // N, original integer costs
   GfObjChunk* ochunks = nullptr; int64_t nochunks = 0;
-  int64_t* QIp = nullptr; int32_t* QIc = nullptr; int32_t* QIv = nullptr;  // original Q (sparse)
+  // sparse Q for evaluation: pairs i < j (row i) with w_ij = q_ij + q_ji,
+  // per-row bias (-min w) and bit width of the weight span; clin = c +
+  // diag(Q) (null when no instance has a sparse Q)
+  int64_t* QIp = nullptr; int32_t* QIc = nullptr; long long* QIv = nullptr;
+  long long* QIb = nullptr; uint8_t* QIw = nullptr; long long* clin = nullptr;
   GfQChunk* qchunks = nullptr; int64_t nqchunks = 0;
   // fused single-row path
   bool fused_ok = false;

@@ -307,48 +307,116 @@ k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
   }
 }
 
-// Sparse Q term X_s^T Q X_s over rows [r0, r1) of Q (original, integer).
+// 32 x 32 bit transpose across a warp: lane l holds word A_l; afterwards
+// lane b holds the word whose bit l is bit b of A_l (five block-swap stages).
+GF_DEV uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+    const bool low = (lane & j) == 0;
+    const uint32_t t = (low ? ((x >> j) ^ y) : ((y >> j) ^ x)) & masks[k];
+    x ^= low ? (t << j) : t;
+  }
+  return x;
+}
+
+// Sparse Q term: for a row i and a candidate s with x_i = 1, the sum of the
+// pair weights w_ij (j > i, w_ij = q_ij + q_ji) over the j with x_j = 1.  A
+// warp takes one row and kQW candidate words.  Per block of 32 pairs, lane l
+// holds m_l = X_i & X_j (pair l), a bit transpose hands lane b the word T
+// whose bit l says that candidate b takes pair l, and with the weights
+// shifted to u_l = w_l + bias >= 0 (bit planes by ballot) the candidate's
+// sum is  sum_p 2^p popc(T & plane_p) - bias popc(T).  Rows whose weights
+// span more than kQPlanes bits add pair by pair instead.
+constexpr int kQW = 4;
+constexpr int kQPlanes = 12;
+
 __global__ void __launch_bounds__(256)
-k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int64_t* __restrict__ Qp,
-             const int32_t* __restrict__ Qc, const int32_t* __restrict__ Qv,
+k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int64_t* __restrict__ Pp,
+             const int32_t* __restrict__ Pc, const long long* __restrict__ Pv,
+             const long long* __restrict__ Pb, const uint8_t* __restrict__ Pw,
              const uint32_t* __restrict__ X, int kws, int kwu, int len, int chunk,
              long long* __restrict__ obj) {
   const int64_t c = blockIdx.x;
-  const int w = blockIdx.y;
-  if (c >= nch || w >= kwu) return;
+  const int w0 = blockIdx.y * kQW;
+  if (c >= nch || w0 >= kwu) return;
   const GfQChunk C = ch[c];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long acc = 0;
+  const int nw = min(kQW, kwu - w0);
+  const bool vec = (kws % 4) == 0;
+  long long acc[kQW] = {0, 0, 0, 0};
   for (int i = C.r0 + warp; i < C.r1; i += 8) {
-    const uint32_t mi = X[(int64_t)i * kws + w];
-    if (!mi) continue;                         // warp-uniform
-    for (int64_t t0 = Qp[i]; t0 < Qp[i + 1]; t0 += 32) {
+    uint32_t mi[kQW];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kQW; ++k) {
+      mi[k] = k < nw ? __ldg(X + (int64_t)i * kws + w0 + k) : 0u;
+      any |= mi[k] != 0u;
+    }
+    if (!any) continue;                          // warp-uniform
+    const int64_t p0 = Pp[i], p1 = Pp[i + 1];
+    const int P = Pw[i];
+    const long long bias = Pb[i];
+    for (int64_t t0 = p0; t0 < p1; t0 += 32) {
       const int64_t t = t0 + lane;
-      uint32_t m = 0;
-      long long q = 0;
-      if (t < Qp[i + 1]) {
-        m = mi & X[(int64_t)Qc[t] * kws + w];
-        q = Qv[t];
+      const bool valid = t < p1;
+      const int64_t j = valid ? Pc[t] : 0;
+      const long long wv = valid ? Pv[t] : 0;
+      uint32_t xj[kQW] = {0u, 0u, 0u, 0u};
+      if (valid) {
+        const uint32_t* src = X + j * kws + w0;
+        if (vec && nw == kQW) {
+          const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(src));
+          xj[0] = q4.x; xj[1] = q4.y; xj[2] = q4.z; xj[3] = q4.w;
+        } else {
+          for (int k = 0; k < nw; ++k) xj[k] = __ldg(src + k);
+        }
       }
-      unsigned nz = __ballot_sync(0xFFFFFFFFu, m != 0u);
-      while (nz) {
-        const int src = __ffs(nz) - 1;
-        nz &= nz - 1;
-        const uint32_t word = __shfl_sync(0xFFFFFFFFu, m, src);
-        const long long qv = __shfl_sync(0xFFFFFFFFu, q, src);
-        if ((word >> lane) & 1u) acc += qv;
+      if (P <= kQPlanes) {
+        const uint32_t u = (uint32_t)(wv + bias);
+        uint32_t plane[kQPlanes];
+#pragma unroll
+        for (int q = 0; q < kQPlanes; ++q)
+          plane[q] = q < P ? __ballot_sync(0xFFFFFFFFu, (u >> q) & 1u) : 0u;
+#pragma unroll
+        for (int k = 0; k < kQW; ++k) {
+          if (!mi[k]) continue;                  // warp-uniform
+          const uint32_t T = warp_transpose32(mi[k] & xj[k], lane);
+          long long sum = -bias * (long long)__popc(T);
+#pragma unroll
+          for (int q = 0; q < kQPlanes; ++q)
+            if (q < P) sum += (long long)__popc(T & plane[q]) << q;
+          acc[k] += sum;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kQW; ++k) {
+          const uint32_t m = mi[k] & xj[k];
+          unsigned nz = __ballot_sync(0xFFFFFFFFu, m != 0u);
+          while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t word = __shfl_sync(0xFFFFFFFFu, m, src);
+            const long long qv = __shfl_sync(0xFFFFFFFFu, wv, src);
+            if ((word >> lane) & 1u) acc[k] += qv;
+          }
+        }
       }
     }
   }
-  __shared__ long long red[8][32];
-  red[warp][lane] = acc;
+  __shared__ long long red[8][kQW][32];
+#pragma unroll
+  for (int k = 0; k < kQW; ++k) red[warp][k][lane] = acc[k];
   __syncthreads();
-  if (warp == 0) {
-    long long s = 0;
-    for (int q = 0; q < 8; ++q) s += red[q][lane];
-    if (s != 0 && 32 * w + lane < len)
-      atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)C.inst * chunk + 32 * w + lane]),
-                (unsigned long long)s);
+  if (warp < nw) {
+    long long sm = 0;
+    for (int q = 0; q < 8; ++q) sm += red[q][warp][lane];
+    const int s = 32 * (w0 + warp) + lane;
+    if (sm != 0 && s < len)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)C.inst * chunk + s]),
+                (unsigned long long)sm);
   }
 }
 
@@ -556,13 +624,15 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
   }
   if (h->nochunks) {
     k_eval_obj_lin<<<(unsigned)h->nochunks, 256, 0, h->stream>>>(
-        h->ochunks, h->nochunks, h->cint, h->X, h->kw, kwu, len, h->chunk, h->obj);
+        h->ochunks, h->nochunks, h->clin ? h->clin : h->cint, h->X, h->kw, kwu, len, h->chunk,
+        h->obj);
     h->launches++;
   }
   if (h->nqchunks) {
-    dim3 grid((unsigned)h->nqchunks, (unsigned)kwu);
+    dim3 grid((unsigned)h->nqchunks, (unsigned)((kwu + kQW - 1) / kQW));
     k_eval_obj_q<<<grid, 256, 0, h->stream>>>(h->qchunks, h->nqchunks, h->QIp, h->QIc, h->QIv,
-                                              h->X, h->kw, kwu, len, h->chunk, h->obj);
+                                              h->QIb, h->QIw, h->X, h->kw, kwu, len, h->chunk,
+                                              h->obj);
     h->launches++;
   }
   return cudaGetLastError();

@@ -90,6 +90,135 @@ k_dual_runs(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr,
 }
 
 // ---------------------------------------------------------------------------
+// Rows / columns with at most two nonzeros (the length bucket <= 2), given as
+// runs: kShortRpt of them per thread, kShortRpt * 256 consecutive ones per
+// block, so that a thread issues the loads of all its rows before it uses
+// any (several independent gathers in flight instead of one dependent
+// chain).  Sums as in the one-lane run kernels: the same two compensated
+// adds in the same order, so the results are identical.
+// ---------------------------------------------------------------------------
+constexpr int kShortRpt = 4;
+
+struct ShortRow {
+  int64_t id, t0;
+  int n, inst;                    // n = -1: no row
+};
+
+GF_DEV void short_rows(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr,
+                       int nruns, int64_t count, const int64_t* __restrict__ ptr,
+                       ShortRow (&w)[kShortRpt]) {
+  const int64_t base = (int64_t)blockIdx.x * (256 * kShortRpt) + threadIdx.x;
+  int64_t lo = 0, hi = -1;
+  GfRun R{};
+#pragma unroll
+  for (int u = 0; u < kShortRpt; ++u) {
+    const int64_t g = base + (int64_t)u * 256;
+    w[u].n = -1;
+    if (g >= count) continue;
+    if (g >= hi) {
+      const int q = nruns == 1 ? 0 : run_of(run_ptr, nruns, g);
+      R = runs[q];
+      lo = __ldg(run_ptr + q);
+      hi = __ldg(run_ptr + q + 1);
+    }
+    const int64_t off = g - lo;
+    w[u].id = R.first + off;
+    w[u].inst = R.inst;
+    if (R.len >= 0) {
+      w[u].t0 = R.nnz0 + off * R.len;
+      w[u].n = R.len;
+    } else {
+      w[u].t0 = ptr[w[u].id];
+      w[u].n = (int)(ptr[w[u].id + 1] - w[u].t0);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_dual_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr, int nruns,
+             int64_t nrows, const int64_t* __restrict__ Kp, const int32_t* __restrict__ Kc,
+             const float* __restrict__ Kv, const float* __restrict__ xbar,
+             const float* __restrict__ r, const uint8_t* __restrict__ row_eq,
+             const GfIParam* __restrict__ ip, float* __restrict__ y) {
+  ShortRow w[kShortRpt];
+  short_rows(runs, run_ptr, nruns, nrows, Kp, w);
+  int c0[kShortRpt], c1[kShortRpt];
+  float v0[kShortRpt], v1[kShortRpt], yo[kShortRpt], rr[kShortRpt];
+  float xa[kShortRpt], xb[kShortRpt];
+#pragma unroll
+  for (int u = 0; u < kShortRpt; ++u) {
+    c0[u] = w[u].n >= 1 ? Kc[w[u].t0] : 0;
+    v0[u] = w[u].n >= 1 ? Kv[w[u].t0] : 0.f;
+    c1[u] = w[u].n >= 2 ? Kc[w[u].t0 + 1] : 0;
+    v1[u] = w[u].n >= 2 ? Kv[w[u].t0 + 1] : 0.f;
+    yo[u] = w[u].n >= 0 ? y[w[u].id] : 0.f;
+    rr[u] = w[u].n >= 0 ? r[w[u].id] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kShortRpt; ++u) {
+    xa[u] = w[u].n >= 1 ? xbar[c0[u]] : 0.f;
+    xb[u] = w[u].n >= 2 ? xbar[c1[u]] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kShortRpt; ++u) {
+    if (w[u].n < 0) continue;
+    CSum acc;
+    if (w[u].n >= 1) acc.add(__fmul_rn(v0[u], xa[u]));
+    if (w[u].n >= 2) acc.add(__fmul_rn(v1[u], xb[u]));
+    const float tau2 = ip[w[u].inst].tau2;
+    float v = yo[u] + tau2 * (acc.value() + rr[u]);
+    if (!row_eq[w[u].id] && v < 0.f) v = 0.f;
+    y[w[u].id] = v;
+  }
+}
+
+// Columns with at most two K^T entries and no Q entries.
+__global__ void __launch_bounds__(256)
+k_primal_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr, int nruns,
+               int64_t ncols, const int64_t* __restrict__ Tp, const int32_t* __restrict__ Tr,
+               const float* __restrict__ Tv, const float* __restrict__ y,
+               const float* __restrict__ x_old, const float* __restrict__ chat,
+               const GfIParam* __restrict__ ip, float* __restrict__ x_new,
+               float* __restrict__ xbar, float* __restrict__ dlast, int advance,
+               GfDState* st, const GfSched* sc, const double* normQ, const int32_t* cap,
+               GfIParam* ip_next) {
+  ShortRow w[kShortRpt];
+  short_rows(runs, run_ptr, nruns, ncols, Tp, w);
+  int c0[kShortRpt], c1[kShortRpt];
+  float v0[kShortRpt], v1[kShortRpt], xo[kShortRpt], ch[kShortRpt];
+  float ya[kShortRpt], yb[kShortRpt];
+#pragma unroll
+  for (int u = 0; u < kShortRpt; ++u) {
+    c0[u] = w[u].n >= 1 ? Tr[w[u].t0] : 0;
+    v0[u] = w[u].n >= 1 ? Tv[w[u].t0] : 0.f;
+    c1[u] = w[u].n >= 2 ? Tr[w[u].t0 + 1] : 0;
+    v1[u] = w[u].n >= 2 ? Tv[w[u].t0 + 1] : 0.f;
+    xo[u] = w[u].n >= 0 ? x_old[w[u].id] : 0.f;
+    ch[u] = w[u].n >= 0 ? chat[w[u].id] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kShortRpt; ++u) {
+    ya[u] = w[u].n >= 1 ? y[c0[u]] : 0.f;
+    yb[u] = w[u].n >= 2 ? y[c1[u]] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kShortRpt; ++u) {
+    if (w[u].n < 0) continue;
+    CSum acc;
+    if (w[u].n >= 1) acc.add(__fmul_rn(v0[u], ya[u]));
+    if (w[u].n >= 2) acc.add(__fmul_rn(v1[u], yb[u]));
+    const GfIParam p = ip[w[u].inst];
+    const float delta = ch[u] + p.rho + acc.value() - 2.0f * p.rho * xo[u];
+    float xn = xo[u] - p.tau1 * delta;
+    xn = fminf(1.0f, fmaxf(0.0f, xn));
+    x_new[w[u].id] = xn;
+    xbar[w[u].id] = 2.0f * xn - xo[u];
+    if (dlast) dlast[w[u].id] = p.tau1 * delta;
+  }
+  if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip, ip_next);
+}
+
+// ---------------------------------------------------------------------------
 // Primal step over a bucket of columns (K^T in CSC and, optionally, sparse
 // symmetric Q rows), `LANES` threads per column, fused projection and
 // extrapolation.  Block 0 of the kernel flagged `advance` also runs
@@ -412,7 +541,11 @@ template <int L>
 cudaError_t launch_dual(GfCtx* h, const GfBucket& b, const GfIParam* ip, float* y) {
   int64_t threads = (int64_t)b.count * L;
   int blocks = (int)((threads + 255) / 256);
-  if (b.runs)
+  if (L == 1 && b.runs && b.short_ok) {
+    k_dual_short<<<(unsigned)((b.count + 256 * kShortRpt - 1) / (256 * kShortRpt)), 256, 0,
+                   h->stream>>>(b.runs, b.run_ptr, b.nruns, b.count, h->Kp, h->Kc, h->Kv,
+                                h->xbar, h->rhat, h->row_eq, ip, y);
+  } else if (b.runs)
     k_dual_runs<L><<<blocks, 256, 0, h->stream>>>(b.runs, b.run_ptr, b.nruns, b.count, h->Kp,
                                                   h->Kc, h->Kv, h->xbar, h->rhat, h->row_eq,
                                                   ip, y);
@@ -431,7 +564,13 @@ cudaError_t launch_primal(GfCtx* h, const GfBucket& b, const GfIParam* ip,
   int64_t threads = (int64_t)b.count * L;
   int blocks = (int)((threads + 255) / 256);
   if (blocks < 1) blocks = 1;
-  if (b.runs)
+  if (L == 1 && b.runs && b.short_ok && !h->nnzQ) {
+    const unsigned sb = (unsigned)std::max<int64_t>(
+        1, (b.count + 256 * kShortRpt - 1) / (256 * kShortRpt));
+    k_primal_short<<<sb, 256, 0, h->stream>>>(
+        b.runs, b.run_ptr, b.nruns, b.count, h->Tp, h->Tr, h->Tv, h->y, xo, h->chat, ip, xn,
+        xbar, dlast, adv, h->dstate, h->sched_d, h->normQhat_d, h->cap_d, ipn);
+  } else if (b.runs)
     k_primal_runs<L><<<blocks, 256, 0, h->stream>>>(
         b.runs, b.run_ptr, b.nruns, b.count, h->Tp, h->Tr, h->Tv, h->nnzQ ? h->Qp : nullptr,
         h->Qc, h->Qv, h->y, xo, h->chat, ip, xn, xbar, dlast, adv, h->dstate, h->sched_d,

@@ -104,9 +104,10 @@ def set_cover(n: int = 2000, m: int = 200, density: float = 0.05,
 # Max cut, QP form (Section 4.2.3) with Q = -L, so x^T Q x = -cut(x).
 # --------------------------------------------------------------------------
 def max_cut(n: int = 4096, p: float = 0.5, idx: int = 0,
-            family: int = MC, weights: str = "pm1") -> Instance:
+            family: int = MC, weights: str = "pm1", sparse: bool = False) -> Instance:
     """Erdos-Renyi G(n,p); weights +-1 equiprobable ('pm1') or integers
-    uniform on [-8, 10] ('int8_10', the paper's range).  Q = W - diag(W 1)."""
+    uniform on [-8, 10] ('int8_10', the paper's range).  Q = W - diag(W 1);
+    sparse=True hands Q over as CSR (the sparse-Q path) instead of dense."""
     rng = _rng(family, idx)
     iu = np.triu_indices(n, 1)
     edge = rng.random(iu[0].size) < p
@@ -119,7 +120,39 @@ def max_cut(n: int = 4096, p: float = 0.5, idx: int = 0,
     W[iu] = w
     W += W.T
     Q = W - np.diag(W.sum(axis=1))
-    inst = Instance(f"maxcut_n{n}_s{idx}", n, np.zeros(n), Q=Q)
+    if sparse:
+        Q = sp.csr_matrix(Q)
+    inst = Instance(f"maxcut_n{n}_s{idx}" + ("_csr" if sparse else ""), n, np.zeros(n), Q=Q)
+    inst.meta["W"] = W
+    return inst
+
+
+def max_cut_sparse(n: int = 65536, avg_deg: float = 32.0, idx: int = 0,
+                   family: int = MC, weights: str = "int8_10") -> Instance:
+    """Sparse random graph for the sparse-Q path: n * avg_deg / 2 edges drawn
+    as uniform pairs i < j (duplicates dropped, zero weights dropped), weights
+    as in max_cut.  Q = W - diag(W 1) as CSR; meta["W"] holds W (CSR)."""
+    rng = _rng(family, 500 + idx)
+    m = int(n * avg_deg / 2)
+    i = rng.integers(0, n, size=m)
+    j = rng.integers(0, n, size=m)
+    keep = i != j
+    lo, hi = np.minimum(i, j)[keep], np.maximum(i, j)[keep]
+    key = np.unique(lo.astype(np.int64) * n + hi)
+    lo, hi = key // n, key % n
+    if weights == "pm1":
+        w = np.where(rng.random(key.size) < 0.5, -1.0, 1.0)
+    else:
+        w = rng.integers(-8, 11, size=key.size).astype(np.float64)
+    nz = w != 0
+    lo, hi, w = lo[nz], hi[nz], w[nz]
+    W = sp.csr_matrix((np.concatenate([w, w]), (np.concatenate([lo, hi]),
+                                                  np.concatenate([hi, lo]))), shape=(n, n))
+    deg = np.asarray(W.sum(axis=1)).ravel()
+    Q = (W - sp.diags(deg)).tocsr()
+    Q.sum_duplicates()
+    Q.sort_indices()
+    inst = Instance(f"maxcut_sparse_n{n}_s{idx}", n, np.zeros(n), Q=Q)
     inst.meta["W"] = W
     return inst
 

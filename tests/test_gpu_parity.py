@@ -29,6 +29,10 @@ CASES = {
     "knapsack": lambda: W.knapsack(3001, idx=5),
     "tiny": lambda: W.tiny_bip(n=14, m1=4, m2=1, idx=2),
     "maxcut": lambda: W.max_cut(n=300, idx=1),
+    # the paper's weight range on the sparse-Q path: a dense graph handed
+    # over as CSR, and a sparse random graph
+    "maxcut_csr": lambda: W.max_cut(n=300, idx=1, weights="int8_10", sparse=True),
+    "maxcut_sparse": lambda: W.max_cut_sparse(n=3000, avg_deg=12.0, idx=1),
     "assign3d": lambda: W.assign3d(I=8, idx=1),
     "facloc": lambda: W.facility_location(nf=12, nc=40, idx=2),
 }
@@ -106,7 +110,8 @@ def test_pdhg_single_step(name, mode):
 # ------------------------------------------------------------ sampling + eval
 @pytest.mark.parametrize("name,mode", [("setcover", 0), ("knapsack", 1), ("knapsack", 2),
                                        ("tiny", 0), ("maxcut", 0), ("assign3d", 0),
-                                       ("facloc", 0)])
+                                       ("facloc", 0), ("maxcut_csr", 0),
+                                       ("maxcut_sparse", 0)])
 def test_sampling_and_evaluation_bit_exact(name, mode):
     inst = CASES[name]()
     gp, op = _params(eval_mode=mode, k_b=96 if name != "maxcut" else 128)
@@ -178,14 +183,20 @@ def test_eval_candidates_brute_force(idx):
     H.destroy()
 
 
-def test_maxcut_scoring_is_minus_cut():
-    inst = W.max_cut(n=200, idx=4)
+@pytest.mark.parametrize("form", ["dense", "csr", "sparse"])
+def test_maxcut_scoring_is_minus_cut(form):
+    if form == "sparse":
+        inst = W.max_cut_sparse(n=200, avg_deg=20.0, idx=4)
+    else:
+        inst = W.max_cut(n=200, idx=4, weights="int8_10" if form == "csr" else "pm1",
+                         sparse=form == "csr")
     gp, _ = _params(k_b=64)
     H = G.load(inst, gp)
     rng = np.random.default_rng(1)
     X = (rng.random((64, 200)) < 0.5).astype(np.uint8)
     viol, obj = H.eval_candidates(X)
     Wm = inst.meta["W"]
+    Wm = Wm.toarray() if sp.issparse(Wm) else Wm
     for s in range(64):
         x = X[s].astype(np.float64)
         cut = 0.5 * np.sum(Wm * (x[:, None] != x[None, :]))
