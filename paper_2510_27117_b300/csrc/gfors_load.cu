@@ -512,6 +512,8 @@ void gf_set_slot(GfCtx* h, int parity, double rho) {
 // one instance; uniform when all have the same length (ptr differences).
 // Used instead of the id list when there are at most kMaxRuns of them.
 constexpr int kMaxRuns = 4096;
+// Blocks of 32 sparse-Q pairs per evaluation chunk (one CUDA block of 8 warps).
+constexpr int kQChunkBlocks = 64;
 static bool make_runs(const std::vector<int32_t>& ids, const std::vector<int64_t>& ptr,
                       const std::vector<int32_t>& inst_of, std::vector<GfRun>& runs,
                       std::vector<int64_t>& run_ptr) {
@@ -986,8 +988,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     std::vector<int32_t> gcols, gvals;
     std::vector<GfObjChunk> oc;
     std::vector<GfQChunk> qc;
-    std::vector<int64_t> QIp(N + 1, 0);
-    std::vector<int32_t> QIc;
+    std::vector<int32_t> QIi, QIc;
     for (int q = 0; q < ninst; ++q) {
       const GfInstHost& I = h->ih[q];
       if (!I.integral) continue;
@@ -1012,16 +1013,12 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
         for (int64_t a = 0; a < I.n; a += 1024)
           oc.push_back(GfObjChunk{q, (int32_t)(I.var_off + a),
                                   (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 1024)), 0});
-      if (I.qkind == 2) {
-        for (int64_t a = 0; a < I.n; a += 64)
-          qc.push_back(GfQChunk{q, (int32_t)(I.var_off + a),
-                                (int32_t)(I.var_off + std::min<int64_t>(I.n, a + 64)), 0});
-      }
     }
     // Sparse Q for evaluation: x^T Q x = sum_i q_ii x_i + sum_{i<j} w_ij x_i x_j
     // with w_ij = q_ij + q_ji; the diagonal joins the linear costs (x_i^2 =
-    // x_i), the pairs are stored once, in row i = min, with per-row bias
-    // -min w and the bit width of max w - min w (bit-plane evaluation).
+    // x_i), every pair (i < j) is stored once, in blocks of 32 with the
+    // block's bias -min w and the bit width of max w - min w (bit-plane
+    // evaluation).
     std::vector<long long> clin;
     std::vector<long long> QIv;
     std::vector<long long> QIb;
@@ -1030,8 +1027,6 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     for (int q = 0; q < ninst; ++q) anyq |= h->ih[q].integral && h->ih[q].qkind == 2;
     if (anyq) {
       clin = cint;
-      QIb.assign(N, 0);
-      QIw.assign(N, 0);
       std::vector<std::vector<std::pair<int32_t, long long>>> pr2(ninst);
       std::vector<std::vector<int64_t>> cnt(ninst);
       const std::string ex = parallel_for(ninst, [&](int q) {
@@ -1073,36 +1068,42 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
         }
         pp[I.n] = outp;
         e.resize(outp);
-        for (int64_t i = 0; i < I.n; ++i) {
-          long long lo = 0, hi = 0;
-          for (int64_t u = pp[i]; u < pp[i + 1]; ++u) {
-            if (u == pp[i] || e[u].second < lo) lo = e[u].second;
-            if (u == pp[i] || e[u].second > hi) hi = e[u].second;
+      });
+      if (!ex.empty()) return gf_fail(h, GFORS_E_OOM, "sparse Q pairs: " + ex);
+      // flat pair list, each instance padded to whole blocks of 32 with
+      // weight-0 pairs; per block the bias -min w and the span's bit width
+      for (int q = 0; q < ninst; ++q) {
+        const GfInstHost& I = h->ih[q];
+        if (cnt[q].empty()) continue;
+        const int64_t np = (int64_t)pr2[q].size();
+        const int64_t nb = (np + 31) / 32;
+        const int64_t pb0 = (int64_t)QIi.size() / 32;
+        for (int64_t i = 0; i < I.n; ++i)
+          for (int64_t u = cnt[q][i]; u < cnt[q][i + 1]; ++u) {
+            QIi.push_back((int32_t)(I.var_off + i));
+            QIc.push_back((int32_t)(I.var_off + pr2[q][u].first));
+            QIv.push_back(pr2[q][u].second);
+          }
+        while ((int64_t)QIi.size() % 32) {
+          QIi.push_back((int32_t)I.var_off);
+          QIc.push_back((int32_t)I.var_off);
+          QIv.push_back(0);
+        }
+        for (int64_t bk = 0; bk < nb; ++bk) {
+          long long lo = QIv[(pb0 + bk) * 32], hi = lo;
+          for (int l = 1; l < 32; ++l) {
+            lo = std::min(lo, QIv[(pb0 + bk) * 32 + l]);
+            hi = std::max(hi, QIv[(pb0 + bk) * 32 + l]);
           }
           const unsigned long long span = (unsigned long long)(hi - lo);
           int bits = 0;
           while (bits < 64 && (span >> bits) != 0ull) ++bits;
-          QIb[I.var_off + i] = -lo;
-          QIw[I.var_off + i] = (uint8_t)bits;
+          QIb.push_back(-lo);
+          QIw.push_back((uint8_t)bits);
         }
-      });
-      if (!ex.empty()) return gf_fail(h, GFORS_E_OOM, "sparse Q pairs: " + ex);
-      for (int q = 0; q < ninst; ++q) {
-        const GfInstHost& I = h->ih[q];
-        if (cnt[q].empty()) continue;
-        for (int64_t i = 0; i < I.n; ++i) QIp[I.var_off + i + 1] = cnt[q][i + 1] - cnt[q][i];
-      }
-      for (int64_t i = 0; i < N; ++i) QIp[i + 1] += QIp[i];
-      QIc.resize(QIp[N]);
-      QIv.resize(QIp[N]);
-      for (int q = 0; q < ninst; ++q) {
-        const GfInstHost& I = h->ih[q];
-        if (cnt[q].empty()) continue;
-        int64_t t = QIp[I.var_off];
-        for (const auto& pe : pr2[q]) {
-          QIc[t] = (int32_t)(I.var_off + pe.first);
-          QIv[t++] = pe.second;
-        }
+        for (int64_t bk = 0; bk < nb; bk += kQChunkBlocks)
+          qc.push_back(GfQChunk{q, (int32_t)(pb0 + bk),
+                                (int32_t)(pb0 + std::min<int64_t>(nb, bk + kQChunkBlocks)), 0});
         std::vector<std::pair<int32_t, long long>>().swap(pr2[q]);
       }
     }
@@ -1118,15 +1119,35 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     ALLOC(h->gcols, int32_t, gcols.size());
     ALLOC(h->gvals, int32_t, gvals.size());
     ALLOC(h->ochunks, GfObjChunk, oc.size());
+    // cost bit planes per 32-variable group (linear-objective evaluation)
+    std::vector<long long> cgb(N / 32);
+    std::vector<uint8_t> cgp(N / 32);
+    {
+      const std::vector<long long>& cl = anyq ? clin : cint;
+      for (int64_t g = 0; g < N / 32; ++g) {
+        long long lo = cl[32 * g], hi = lo;
+        for (int l = 1; l < 32; ++l) {
+          lo = std::min(lo, cl[32 * g + l]);
+          hi = std::max(hi, cl[32 * g + l]);
+        }
+        const unsigned long long span = (unsigned long long)(hi - lo);
+        int bits = 0;
+        while (bits < 64 && (span >> bits) != 0ull) ++bits;
+        cgb[g] = -lo;
+        cgp[g] = (uint8_t)bits;
+      }
+    }
+    ALLOC(h->cgbias, long long, N / 32);
+    ALLOC(h->cgP, uint8_t, N / 32);
+    UP(h->cgbias, cgb.data(), long long, N / 32);
+    UP(h->cgP, cgp.data(), uint8_t, N / 32);
     ALLOC(h->qchunks, GfQChunk, qc.size());
-    ALLOC(h->QIp, int64_t, N + 1);
+    ALLOC(h->QIi, int32_t, QIi.size());
     ALLOC(h->QIc, int32_t, QIc.size());
     ALLOC(h->QIv, long long, QIv.size());
-    if (anyq) {
-      ALLOC(h->QIb, long long, N);
-      ALLOC(h->QIw, uint8_t, N);
-      ALLOC(h->clin, long long, N);
-    }
+    ALLOC(h->QIb, long long, QIb.size());
+    ALLOC(h->QIw, uint8_t, QIw.size());
+    if (anyq) ALLOC(h->clin, long long, N);
     ALLOC(h->cint, long long, N);
     if (!ur.empty()) UP(h->urows, ur.data(), GfURow, ur.size());
     if (!ucols.empty()) UP(h->ucols, ucols.data(), int32_t, ucols.size());
@@ -1136,14 +1157,12 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     if (!gvals.empty()) UP(h->gvals, gvals.data(), int32_t, gvals.size());
     if (!oc.empty()) UP(h->ochunks, oc.data(), GfObjChunk, oc.size());
     if (!qc.empty()) UP(h->qchunks, qc.data(), GfQChunk, qc.size());
-    UP(h->QIp, QIp.data(), int64_t, N + 1);
+    if (!QIi.empty()) UP(h->QIi, QIi.data(), int32_t, QIi.size());
     if (!QIc.empty()) UP(h->QIc, QIc.data(), int32_t, QIc.size());
     if (!QIv.empty()) UP(h->QIv, QIv.data(), long long, QIv.size());
-    if (anyq) {
-      UP(h->QIb, QIb.data(), long long, N);
-      UP(h->QIw, QIw.data(), uint8_t, N);
-      UP(h->clin, clin.data(), long long, N);
-    }
+    if (!QIb.empty()) UP(h->QIb, QIb.data(), long long, QIb.size());
+    if (!QIw.empty()) UP(h->QIw, QIw.data(), uint8_t, QIw.size());
+    if (anyq) UP(h->clin, clin.data(), long long, N);
     UP(h->cint, cint.data(), long long, N);
   }
 

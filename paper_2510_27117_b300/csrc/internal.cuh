@@ -82,7 +82,7 @@ struct GfObjChunk {                 // linear-objective chunk: vars [v0, v1)
   int32_t v0, v1;
   int32_t pad;
 };
-struct GfQChunk {                   // sparse-Q chunk: rows [r0, r1) of Q
+struct GfQChunk {                   // sparse-Q chunk: pair blocks [r0, r1)
   int32_t inst;
   int32_t r0, r1;
   int32_t pad;
@@ -210,11 +210,15 @@ struct gfors_ctx {
   GfGRow* grows = nullptr; int64_t ngrows = 0; int32_t* gcols = nullptr; int32_t* gvals = nullptr;
   long long* cint = nullptr;        // N, original integer costs
   GfObjChunk* ochunks = nullptr; int64_t nochunks = 0;
-  // sparse Q for evaluation: pairs i < j (row i) with w_ij = q_ij + q_ji,
-  // per-row bias (-min w) and bit width of the weight span; clin = c +
-  // diag(Q) (null when no instance has a sparse Q)
-  int64_t* QIp = nullptr; int32_t* QIc = nullptr; long long* QIv = nullptr;
+  // sparse Q for evaluation: pairs (QIi < QIc) with w = q_ij + q_ji in
+  // blocks of 32 (each instance padded with weight-0 pairs), per block the
+  // bias -min w and the bit width of the weight span; clin = c + diag(Q)
+  // (null when no instance has a sparse Q)
+  int32_t* QIi = nullptr; int32_t* QIc = nullptr; long long* QIv = nullptr;
   long long* QIb = nullptr; uint8_t* QIw = nullptr; long long* clin = nullptr;
+  // per 32-variable group of the linear costs used in evaluation: bias
+  // -min c and bit width of the cost span
+  long long* cgbias = nullptr; uint8_t* cgP = nullptr;
   GfQChunk* qchunks = nullptr; int64_t nqchunks = 0;
   // fused single-row path
   bool fused_ok = false;

@@ -108,7 +108,6 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
   __shared__ uint8_t pa[kA4MaxPairs], pb[kA4MaxPairs];
   __shared__ long long wbest[kA4Threads / 32];
   __shared__ int wcode[kA4Threads / 32];
-  __shared__ int sel;
   const int sidx = blockIdx.x;
   if (sidx >= len) return;
   const int tid = threadIdx.x;
@@ -163,7 +162,11 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
   };
   for (int q = tid; q < np; q += kA4Threads) pair_gains(q, pa[q], pb[q]);
   __syncthreads();
-  // (d) best-improvement pairwise interchanges
+  // (d) best-improvement pairwise interchanges.  Two barriers per step:
+  // after the scan (every thread then reduces the warp winners itself and
+  // reads the chosen triples), and after the gain updates (then thread 0
+  // stores the new triples, which nobody reads before the next scan's
+  // barrier).
   const int warp = tid >> 5, lane = tid & 31;
   for (int step = 0; step < L; ++step) {
     long long best = 0;                          // only strict improvements count
@@ -180,35 +183,44 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
     }
     if (lane == 0) { wbest[warp] = best; wcode[warp] = code; }
     __syncthreads();
-    if (tid == 0) {
-      long long bb = 0;
-      int bc = 0x7FFFFFFF;
-      for (int w = 0; w < kA4Threads / 32; ++w)
-        if (wbest[w] < bb || (wbest[w] == bb && wcode[w] < bc)) { bb = wbest[w]; bc = wcode[w]; }
-      if (bb < 0) {
-        const int q = bc >> 1, a = pa[q], b = pb[q];
-        if ((bc & 1) == 0) { const int tmp = J[a]; J[a] = J[b]; J[b] = tmp; }
-        else { const int tmp = Kk[a]; Kk[a] = Kk[b]; Kk[b] = tmp; }
-        cold[a] = C3(a, J[a], Kk[a]);
-        cold[b] = C3(b, J[b], Kk[b]);
-        sel = q;
-      } else {
-        sel = -1;
-      }
-    }
-    __syncthreads();
-    const int q = sel;
-    if (q < 0) break;
-    const int a = pa[q], b = pb[q];
-    // pairs (a, x) for every x != a, then (b, x) for x not in {a, b}
+    long long bb = 0;
+    int bc = 0x7FFFFFFF;
+#pragma unroll
+    for (int w = 0; w < kA4Threads / 32; ++w)
+      if (wbest[w] < bb || (wbest[w] == bb && wcode[w] < bc)) { bb = wbest[w]; bc = wcode[w]; }
+    if (bb >= 0) break;                          // no strict improvement (uniform)
+    const int q = bc >> 1, a = pa[q], b = pb[q];
+    int Ja = J[a], Jb = J[b], Ka = Kk[a], Kb = Kk[b];
+    if ((bc & 1) == 0) { const int tmp = Ja; Ja = Jb; Jb = tmp; }
+    else { const int tmp = Ka; Ka = Kb; Kb = tmp; }
+    // gains of the pairs (a, x) for every x != a, then (b, x), x not in {a, b}
     for (int t = tid; t < 2 * I; t += kA4Threads) {
-      const int u = t < I ? a : b, x = t < I ? t : t - I;
-      if (x == u || (t >= I && x == a)) continue;
+      const bool first = t < I;
+      const int x = first ? t : t - I;
+      if (first ? x == a : (x == a || x == b)) continue;
+      const int u = first ? a : b;
+      const int Ju = first ? Ja : Jb, Ku = first ? Ka : Kb;
+      const long long cu = C3(u, Ju, Ku);
+      int Jx, Kx;
+      long long cx;
+      if (x == b) { Jx = Jb; Kx = Kb; cx = C3(b, Jb, Kb); }
+      else { Jx = J[x]; Kx = Kk[x]; cx = cold[x]; }
       const int lo = u < x ? u : x, hi = u < x ? x : u;
-      pair_gains(pair_index(lo, hi, I), lo, hi);
+      const int Jl = u < x ? Ju : Jx, Kl = u < x ? Ku : Kx;
+      const int Jh = u < x ? Jx : Ju, Kh = u < x ? Kx : Ku;
+      const long long old = cu + cx;
+      const int pq = pair_index(lo, hi, I);
+      gain[2 * pq] = C3(lo, Jh, Kl) + C3(hi, Jl, Kh) - old;       // exchange j
+      gain[2 * pq + 1] = C3(lo, Jl, Kh) + C3(hi, Jh, Kl) - old;   // exchange k
     }
     __syncthreads();
+    if (tid == 0) {
+      J[a] = Ja; J[b] = Jb; Kk[a] = Ka; Kk[b] = Kb;
+      cold[a] = C3(a, Ja, Ka);
+      cold[b] = C3(b, Jb, Kb);
+    }
   }
+  __syncthreads();
   for (int a = tid; a < I; a += kA4Threads) {
     const int64_t var = v0 + ((int64_t)a * I + J[a]) * I + Kk[a];
     atomicOr(&X[var * kw + (sidx >> 5)], 1u << (sidx & 31));

@@ -247,55 +247,155 @@ k_eval_grows(const GfGRow* __restrict__ rows, int64_t nrows,
   add_violations(vmask, inst, w, chunk, viol, valid);
 }
 
-// Linear objective c^T X_s over a chunk of one instance's variables; block
-// of 8 warps over the chunk's variables, candidate words in groups of 4
-// (16-byte loads; the chunk's words stay in L1 between groups).  Per word:
-// the warp's nonzero words are broadcast in turn and lane t adds the cost of
-// every variable whose bit t is set; partials reduced in shared memory, one
-// atomic per candidate.
+// 32 x 32 bit transpose across a warp: lane l holds word A_l; afterwards
+// lane b holds the word whose bit l is bit b of A_l.  Five block-swap
+// stages; in the stage of distance j a lane keeps its own bits outside the
+// mask M and takes its partner's word rotated by j (lower lane) or 32 - j
+// (upper lane) inside it.  The per-lane rotations and masks depend on the
+// lane only (TransposeLane, computed once).
+struct TransposeLane {
+  uint32_t rot[5], mask[5];
+};
+GF_DEV TransposeLane transpose_lane(int lane) {
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+  TransposeLane t;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const bool low = (lane & j) == 0;
+    t.rot[k] = low ? (uint32_t)j : (uint32_t)(32 - j);
+    t.mask[k] = low ? (m[k] << j) : m[k];
+  }
+  return t;
+}
+GF_DEV uint32_t warp_transpose32(uint32_t x, const TransposeLane& t) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, 16 >> k);
+    const uint32_t r = __funnelshift_l(y, y, t.rot[k]);
+    x = (x & ~t.mask[k]) | (r & t.mask[k]);
+  }
+  return x;
+}
+
+constexpr int kQW = 4;
+
+// Weighted counts of a warp's 32 items for the 32 candidates of each of kQW
+// words: acc[k] of lane b gains sum_l w_l * bit b of m_l[k] (lane l: item
+// l's weight w_l and candidate words m_l).  A bit transpose hands lane b the
+// word T of its candidate; with the weights shifted to u_l = w_l + bias >= 0
+// (P bit planes by ballot) the sum is sum_p 2^p popc(T & plane_p) -
+// bias popc(T).
+template <int P>
+GF_DEV void weighted_counts(const uint32_t (&m)[kQW], uint32_t u, long long bias, int nw,
+                            const TransposeLane& tl, long long (&acc)[kQW]) {
+  uint32_t plane[P > 0 ? P : 1];
+#pragma unroll
+  for (int q = 0; q < P; ++q) plane[q] = __ballot_sync(0xFFFFFFFFu, (u >> q) & 1u);
+#pragma unroll
+  for (int k = 0; k < kQW; ++k) {
+    if (k >= nw) break;
+    const uint32_t T = warp_transpose32(m[k], tl);
+    int sum = 0;                                 // <= 32 (2^P - 1) < 2^18
+#pragma unroll
+    for (int q = 0; q < P; ++q) sum += __popc(T & plane[q]) * (1 << q);
+    acc[k] += (long long)sum - bias * (long long)__popc(T);
+  }
+}
+
+// The same sums item by item (broadcast of each nonzero word and its
+// weight): cheaper when few items have a nonzero word, and the form for
+// weight spans wider than the bit-plane kernels take.
+GF_DEV void weighted_counts_sparse(const uint32_t (&m)[kQW], long long w, int nw, int lane,
+                                   long long (&acc)[kQW]) {
+#pragma unroll
+  for (int k = 0; k < kQW; ++k) {
+    if (k >= nw) break;
+    unsigned nz = __ballot_sync(0xFFFFFFFFu, m[k] != 0u && w != 0);
+    while (nz) {
+      const int src = __ffs(nz) - 1;
+      nz &= nz - 1;
+      const uint32_t word = __shfl_sync(0xFFFFFFFFu, m[k], src);
+      const long long wv = __shfl_sync(0xFFFFFFFFu, w, src);
+      if ((word >> lane) & 1u) acc[k] += wv;
+    }
+  }
+}
+
+// Bit-plane form for P <= 12 planes (uniform across the warp), else item by
+// item.
+GF_DEV void weighted_counts_p(int P, const uint32_t (&m)[kQW], long long w, long long bias,
+                              int nw, int lane, const TransposeLane& tl,
+                              long long (&acc)[kQW]) {
+  const uint32_t u = (uint32_t)(w + bias);
+  switch (P) {
+    case 0: weighted_counts<0>(m, u, bias, nw, tl, acc); break;
+    case 1: weighted_counts<1>(m, u, bias, nw, tl, acc); break;
+    case 2: weighted_counts<2>(m, u, bias, nw, tl, acc); break;
+    case 3: weighted_counts<3>(m, u, bias, nw, tl, acc); break;
+    case 4: weighted_counts<4>(m, u, bias, nw, tl, acc); break;
+    case 5: weighted_counts<5>(m, u, bias, nw, tl, acc); break;
+    case 6: weighted_counts<6>(m, u, bias, nw, tl, acc); break;
+    case 7: weighted_counts<7>(m, u, bias, nw, tl, acc); break;
+    case 8: weighted_counts<8>(m, u, bias, nw, tl, acc); break;
+    case 9: weighted_counts<9>(m, u, bias, nw, tl, acc); break;
+    case 10: weighted_counts<10>(m, u, bias, nw, tl, acc); break;
+    case 11: weighted_counts<11>(m, u, bias, nw, tl, acc); break;
+    case 12: weighted_counts<12>(m, u, bias, nw, tl, acc); break;
+    default: weighted_counts_sparse(m, w, nw, lane, acc); break;
+  }
+}
+
+constexpr int kSparseLanes = 16;
+
+// Linear objective c^T x_s of every candidate: a warp takes 32 variables
+// (lane = variable; 32-variable groups never straddle instances, whose
+// offsets are multiples of 64) and kQW candidate words; per group the bias
+// -min c and the bit width P of the cost span are precomputed.  Block sums
+// go to obj with one atomic per candidate.
 __global__ void __launch_bounds__(256)
 k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
-               const long long* __restrict__ cint, const uint32_t* __restrict__ X,
-               int kws, int kwu, int len, int chunk, long long* __restrict__ obj) {
+               const long long* __restrict__ cint, const long long* __restrict__ gbias,
+               const uint8_t* __restrict__ gP, const uint32_t* __restrict__ X, int kws,
+               int kwu, int len, int chunk, long long* __restrict__ obj) {
   const int64_t c = blockIdx.x;
   if (c >= nch) return;
   const GfObjChunk C = ch[c];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool vec = (kws % 4) == 0;
-  __shared__ long long red[8][4][32];
-  for (int w0 = 0; w0 < kwu; w0 += 4) {
-    const int nw = min(4, kwu - w0);
-    long long acc[4] = {0, 0, 0, 0};
+  const TransposeLane tl = transpose_lane(lane);
+  __shared__ long long red[8][kQW][32];
+  for (int w0 = 0; w0 < kwu; w0 += kQW) {
+    const int nw = min(kQW, kwu - w0);
+    const bool vec = (kws % 4) == 0 && nw == kQW;
+    long long acc[kQW] = {0, 0, 0, 0};
     for (int v = C.v0 + warp * 32; v < C.v1; v += 256) {
       const int myv = v + lane;
-      uint32_t mw[4] = {0u, 0u, 0u, 0u};
+      uint32_t mw[kQW] = {0u, 0u, 0u, 0u};
       long long mc = 0;
       if (myv < C.v1) {
         mc = cint[myv];
         const uint32_t* src = X + (int64_t)myv * kws + w0;
-        if (vec && nw == 4) {
+        if (vec) {
           const uint4 q = __ldg(reinterpret_cast<const uint4*>(src));
           mw[0] = q.x; mw[1] = q.y; mw[2] = q.z; mw[3] = q.w;
         } else {
-          for (int j = 0; j < nw; ++j) mw[j] = __ldg(src + j);
-        }
-      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        unsigned nz = __ballot_sync(0xFFFFFFFFu, mw[j] != 0u && mc != 0);
-        while (nz) {
-          const int src = __ffs(nz) - 1;
-          nz &= nz - 1;
-          const uint32_t word = __shfl_sync(0xFFFFFFFFu, mw[j], src);
-          const long long cv = __shfl_sync(0xFFFFFFFFu, mc, src);
-          if ((word >> lane) & 1u) acc[j] += cv;
+          for (int j = 0; j < kQW; ++j)
+            if (j < nw) mw[j] = __ldg(src + j);
         }
       }
+      // item by item when at most kSparseLanes (variable, word) pairs of the
+      // four words are nonzero (sparse candidates, e.g. one-hot groups)
+      int dense = 0;
+#pragma unroll
+      for (int j = 0; j < kQW; ++j) dense += __popc(__ballot_sync(0xFFFFFFFFu, mw[j] != 0u));
+      if (dense <= kSparseLanes) weighted_counts_sparse(mw, mc, nw, lane, acc);
+      else weighted_counts_p(gP[v >> 5], mw, mc, gbias[v >> 5], nw, lane, tl, acc);
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) red[warp][j][lane] = acc[j];
+    for (int j = 0; j < kQW; ++j) red[warp][j][lane] = acc[j];
     __syncthreads();
-    if (warp < 4 && warp < nw) {
+    if (warp < nw) {
       long long s = 0;
       for (int q = 0; q < 8; ++q) s += red[q][warp][lane];
       const int cand = 32 * (w0 + warp) + lane;
@@ -307,35 +407,13 @@ k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
   }
 }
 
-// 32 x 32 bit transpose across a warp: lane l holds word A_l; afterwards
-// lane b holds the word whose bit l is bit b of A_l (five block-swap stages).
-GF_DEV uint32_t warp_transpose32(uint32_t x, int lane) {
-  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int j = 16 >> k;
-    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-    const bool low = (lane & j) == 0;
-    const uint32_t t = (low ? ((x >> j) ^ y) : ((y >> j) ^ x)) & masks[k];
-    x ^= low ? (t << j) : t;
-  }
-  return x;
-}
-
-// Sparse Q term: for a row i and a candidate s with x_i = 1, the sum of the
-// pair weights w_ij (j > i, w_ij = q_ij + q_ji) over the j with x_j = 1.  A
-// warp takes one row and kQW candidate words.  Per block of 32 pairs, lane l
-// holds m_l = X_i & X_j (pair l), a bit transpose hands lane b the word T
-// whose bit l says that candidate b takes pair l, and with the weights
-// shifted to u_l = w_l + bias >= 0 (bit planes by ballot) the candidate's
-// sum is  sum_p 2^p popc(T & plane_p) - bias popc(T).  Rows whose weights
-// span more than kQPlanes bits add pair by pair instead.
-constexpr int kQW = 4;
-constexpr int kQPlanes = 12;
-
+// Sparse Q term: sum over the pairs (i < j) of w_ij x_i x_j per candidate
+// (w_ij = q_ij + q_ji).  A warp takes a block of 32 pairs (lane l: m_l =
+// X_i & X_j of pair l, weight w_l) and kQW candidate words; the block's
+// bias -min w and bit width P of the weight span are precomputed.
 __global__ void __launch_bounds__(256)
-k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int64_t* __restrict__ Pp,
-             const int32_t* __restrict__ Pc, const long long* __restrict__ Pv,
+k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int32_t* __restrict__ Pi,
+             const int32_t* __restrict__ Pj, const long long* __restrict__ Pv,
              const long long* __restrict__ Pb, const uint8_t* __restrict__ Pw,
              const uint32_t* __restrict__ X, int kws, int kwu, int len, int chunk,
              long long* __restrict__ obj) {
@@ -345,66 +423,27 @@ k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int64_t* __rest
   const GfQChunk C = ch[c];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = min(kQW, kwu - w0);
-  const bool vec = (kws % 4) == 0;
+  const bool vec = (kws % 4) == 0 && nw == kQW;
+  const TransposeLane tl = transpose_lane(lane);
   long long acc[kQW] = {0, 0, 0, 0};
-  for (int i = C.r0 + warp; i < C.r1; i += 8) {
-    uint32_t mi[kQW];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < kQW; ++k) {
-      mi[k] = k < nw ? __ldg(X + (int64_t)i * kws + w0 + k) : 0u;
-      any |= mi[k] != 0u;
-    }
-    if (!any) continue;                          // warp-uniform
-    const int64_t p0 = Pp[i], p1 = Pp[i + 1];
-    const int P = Pw[i];
-    const long long bias = Pb[i];
-    for (int64_t t0 = p0; t0 < p1; t0 += 32) {
-      const int64_t t = t0 + lane;
-      const bool valid = t < p1;
-      const int64_t j = valid ? Pc[t] : 0;
-      const long long wv = valid ? Pv[t] : 0;
-      uint32_t xj[kQW] = {0u, 0u, 0u, 0u};
-      if (valid) {
-        const uint32_t* src = X + j * kws + w0;
-        if (vec && nw == kQW) {
-          const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(src));
-          xj[0] = q4.x; xj[1] = q4.y; xj[2] = q4.z; xj[3] = q4.w;
-        } else {
-          for (int k = 0; k < nw; ++k) xj[k] = __ldg(src + k);
-        }
-      }
-      if (P <= kQPlanes) {
-        const uint32_t u = (uint32_t)(wv + bias);
-        uint32_t plane[kQPlanes];
-#pragma unroll
-        for (int q = 0; q < kQPlanes; ++q)
-          plane[q] = q < P ? __ballot_sync(0xFFFFFFFFu, (u >> q) & 1u) : 0u;
-#pragma unroll
-        for (int k = 0; k < kQW; ++k) {
-          if (!mi[k]) continue;                  // warp-uniform
-          const uint32_t T = warp_transpose32(mi[k] & xj[k], lane);
-          long long sum = -bias * (long long)__popc(T);
-#pragma unroll
-          for (int q = 0; q < kQPlanes; ++q)
-            if (q < P) sum += (long long)__popc(T & plane[q]) << q;
-          acc[k] += sum;
-        }
+  for (int pb = C.r0 + warp; pb < C.r1; pb += 8) {
+    const int64_t t = (int64_t)pb * 32 + lane;
+    const int64_t i = Pi[t], j = Pj[t];
+    uint32_t m[kQW] = {0u, 0u, 0u, 0u};
+    {
+      const uint32_t* si = X + i * kws + w0;
+      const uint32_t* sj = X + j * kws + w0;
+      if (vec) {
+        const uint4 a4 = __ldg(reinterpret_cast<const uint4*>(si));
+        const uint4 b4 = __ldg(reinterpret_cast<const uint4*>(sj));
+        m[0] = a4.x & b4.x; m[1] = a4.y & b4.y; m[2] = a4.z & b4.z; m[3] = a4.w & b4.w;
       } else {
 #pragma unroll
-        for (int k = 0; k < kQW; ++k) {
-          const uint32_t m = mi[k] & xj[k];
-          unsigned nz = __ballot_sync(0xFFFFFFFFu, m != 0u);
-          while (nz) {
-            const int src = __ffs(nz) - 1;
-            nz &= nz - 1;
-            const uint32_t word = __shfl_sync(0xFFFFFFFFu, m, src);
-            const long long qv = __shfl_sync(0xFFFFFFFFu, wv, src);
-            if ((word >> lane) & 1u) acc[k] += qv;
-          }
-        }
+        for (int k = 0; k < kQW; ++k)
+          if (k < nw) m[k] = __ldg(si + k) & __ldg(sj + k);
       }
     }
+    weighted_counts_p(Pw[pb], m, Pv[t], Pb[pb], nw, lane, tl, acc);
   }
   __shared__ long long red[8][kQW][32];
 #pragma unroll
@@ -624,13 +663,13 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
   }
   if (h->nochunks) {
     k_eval_obj_lin<<<(unsigned)h->nochunks, 256, 0, h->stream>>>(
-        h->ochunks, h->nochunks, h->clin ? h->clin : h->cint, h->X, h->kw, kwu, len, h->chunk,
-        h->obj);
+        h->ochunks, h->nochunks, h->clin ? h->clin : h->cint, h->cgbias, h->cgP, h->X, h->kw,
+        kwu, len, h->chunk, h->obj);
     h->launches++;
   }
   if (h->nqchunks) {
     dim3 grid((unsigned)h->nqchunks, (unsigned)((kwu + kQW - 1) / kQW));
-    k_eval_obj_q<<<grid, 256, 0, h->stream>>>(h->qchunks, h->nqchunks, h->QIp, h->QIc, h->QIv,
+    k_eval_obj_q<<<grid, 256, 0, h->stream>>>(h->qchunks, h->nqchunks, h->QIi, h->QIc, h->QIv,
                                               h->QIb, h->QIw, h->X, h->kw, kwu, len, h->chunk,
                                               h->obj);
     h->launches++;
