@@ -145,15 +145,16 @@ GF_DEV f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
 GF_DEV float f2_sum(f32x2 a) {
   return __fadd_rn(__uint_as_float((uint32_t)a), __uint_as_float((uint32_t)(a >> 32)));
 }
-// Signed bytes k, k+1 of a word as an exact float pair.  `wbias` is the word
-// with every byte's sign bit flipped (byte + 128): the biased byte becomes the
+// Signed bytes k, k+1 of a word as an exact float pair.  `wbias` holds the
+// bytes biased by +128 (as the matrix is stored): the biased byte becomes the
 // low mantissa bits of 2^23, and 2^23 + 128 is subtracted afterwards.
 GF_DEV f32x2 f2_i8pair(uint32_t wbias, int k) {
   return f2_pack(__byte_perm(wbias, 0x4B000000u, 0x7650u + k),
                  __byte_perm(wbias, 0x4B000000u, 0x7651u + k));
 }
 
-// One lane's share of an int8 row times an FP32 vector (the dense Q GEMV of
+// One lane's share of an int8 row (stored as biased bytes, w + 128) times an
+// FP32 vector (the dense Q GEMV of
 // the primal step).  Lane l reads the 4-entry words l, l + 32, l + 64, ...
 // of the row; words (t, t + 32) form one 8-term chunk summed in plain FP32
 // (packed pairs).  Chunks starting at t = l + 128 j go to a first compensated
@@ -162,23 +163,44 @@ GF_DEV f32x2 f2_i8pair(uint32_t wbias, int k) {
 // memory; `x4` holds the vector as float4 words in shared memory.  Both PDHG
 // paths of a dense instance use this one routine, so their sums are
 // identical.
-GF_DEV f32x2 i8_chunk(const uint32_t* row, const ulonglong2* xv, int64_t t, int64_t nq,
-                      f32x2 bias) {
-  const uint32_t wa = row[t] ^ 0x80808080u;
-  const ulonglong2 xa = xv[t];
+GF_DEV f32x2 i8_chunk_x(const uint32_t* row, int64_t t, bool has_b, ulonglong2 xa,
+                        ulonglong2 xb, f32x2 bias) {
+  const uint32_t wa = row[t];
   f32x2 pr = f2_mul(f2_add(f2_i8pair(wa, 0), bias), xa.x);
   pr = f2_fma(f2_add(f2_i8pair(wa, 2), bias), xa.y, pr);
-  if (t + 32 < nq) {
-    const uint32_t wb = row[t + 32] ^ 0x80808080u;
-    const ulonglong2 xb = xv[t + 32];
+  if (has_b) {
+    const uint32_t wb = row[t + 32];
     pr = f2_fma(f2_add(f2_i8pair(wb, 0), bias), xb.x, pr);
     pr = f2_fma(f2_add(f2_i8pair(wb, 2), bias), xb.y, pr);
   }
   return pr;
 }
+GF_DEV f32x2 i8_chunk(const uint32_t* row, const ulonglong2* xv, int64_t t, int64_t nq,
+                      f32x2 bias) {
+  const bool has_b = t + 32 < nq;
+  return i8_chunk_x(row, t, has_b, xv[t], has_b ? xv[t + 32] : make_ulonglong2(0, 0), bias);
+}
+// Rows whose word count is a multiple of 128: the same chunks, chains and
+// order as the general loop below, without its bounds tests and with
+// 32-bit offsets (so the two give identical sums).
+GF_DEV CSum i8_row_dot_full(const uint32_t* row, const ulonglong2* xv, int nq, int lane,
+                            f32x2 bias) {
+  CSum acc, acc2;
+  const uint32_t* r = row + lane;
+  const ulonglong2* xp = xv + lane;
+  for (int it = nq >> 7; it > 0; --it, r += 128, xp += 128) {
+    const f32x2 pa = i8_chunk_x(r, 0, true, xp[0], xp[32], bias);
+    const f32x2 pb = i8_chunk_x(r, 64, true, xp[64], xp[96], bias);
+    acc2.add(f2_sum(pb));
+    acc.add(f2_sum(pa));
+  }
+  acc.merge(acc2.s, acc2.c);
+  return acc;
+}
 GF_DEV CSum i8_row_dot(const uint32_t* row, const float4* x4, int64_t nq, int lane) {
   const f32x2 bias = f2_pack(__float_as_uint(-8388736.0f), __float_as_uint(-8388736.0f));
   const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x4);
+  if ((nq & 127) == 0 && nq < (1ll << 30)) return i8_row_dot_full(row, xv, (int)nq, lane, bias);
   CSum acc, acc2;
   for (int64_t t = lane; t < nq; t += 128) {
     const f32x2 p1 = i8_chunk(row, xv, t, nq, bias);

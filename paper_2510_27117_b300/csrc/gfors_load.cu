@@ -761,12 +761,13 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   for (size_t u = 0; u < h->dense.size(); ++u) {
     GfDenseQ& dq = h->dense[u];
     ALLOC(dq.W2, __nv_bfloat16, dq.n * dq.ld);
-    if (dq.w2max <= 127) {             // int8 copy for the PDHG GEMV (exact)
-      ALLOC(dq.W2i8, int8_t, dq.n * dq.ld);
-      std::vector<int8_t> w8((size_t)dq.n * dq.ld);
+    if (dq.w2max <= 127) {             // biased byte copy for the PDHG GEMV (exact)
+      ALLOC(dq.W2i8, uint8_t, dq.n * dq.ld);
+      std::vector<uint8_t> w8((size_t)dq.n * dq.ld);
       const std::vector<__nv_bfloat16>& wb = st[dq.inst].dense_w2;
-      for (size_t t = 0; t < w8.size(); ++t) w8[t] = (int8_t)__bfloat162float(wb[t]);
-      UP(dq.W2i8, w8.data(), int8_t, w8.size());
+      for (size_t t = 0; t < w8.size(); ++t)
+        w8[t] = (uint8_t)((int)__bfloat162float(wb[t]) + 128);
+      UP(dq.W2i8, w8.data(), uint8_t, w8.size());
     }
     // FP8 E4M3 copy for the tensor-core scorer when every entry of W2 is
     // exactly representable in E4M3 (3 mantissa bits: all integers up to 16,

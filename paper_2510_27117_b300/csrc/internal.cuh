@@ -92,7 +92,7 @@ struct GfDenseQ {                   // dense +-small-integer Q (tensor-core path
   int inst = -1;
   int64_t n = 0, ld = 0;            // ld: row stride in elements (mult. of 64)
   __nv_bfloat16* W2 = nullptr;      // off-diagonal of Q + Q^T, n x ld
-  int8_t* W2i8 = nullptr;           // same as int8 when max|W2| <= 127 (PDHG GEMV)
+  uint8_t* W2i8 = nullptr;          // W2 + 128 as bytes when max|W2| <= 127 (PDHG GEMV)
   float* qdiag = nullptr;           // diag(Q_sym) / s_obj
   float qscale = 0.f;               // 0.5 / s_obj
   long long* lin = nullptr;         // c_i + Q_ii (original, integer)

@@ -486,7 +486,7 @@ k_dense_primal(const __nv_bfloat16* __restrict__ W2, int64_t ld, int64_t n,
 constexpr int kI8Warps = 32;
 
 __global__ void __launch_bounds__(kI8Warps * 32, 1)
-k_dense_primal_i8(const int8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t v0,
+k_dense_primal_i8(const uint8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t v0,
                   const float* __restrict__ qdiag, float qscale,
                   const int64_t* __restrict__ Tp, const int32_t* __restrict__ Tr,
                   const float* __restrict__ Tv, const float* __restrict__ y,

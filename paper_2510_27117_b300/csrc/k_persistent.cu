@@ -43,7 +43,7 @@ GF_DEV bool grid_arrive_wait(unsigned* bar, unsigned target, int* err, uint64_t 
 }
 
 __global__ void __launch_bounds__(kWarps * 32, 1)
-k_pdhg_dense_persistent(const int8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t v0,
+k_pdhg_dense_persistent(const uint8_t* __restrict__ W2, int64_t ld, int64_t n, int64_t v0,
                         int64_t per, const float* __restrict__ qdiag, float qscale, float* x0,
                         float* x1, float* __restrict__ xbar, const float* __restrict__ chat,
                         float* __restrict__ dlast, GfIParam* iprm, int inst, int ninst,
@@ -185,7 +185,7 @@ cudaError_t gf_launch_persistent(GfCtx* h, int64_t nsteps) {
   const GfInstHost& I = h->ih[dq.inst];
   cudaError_t e = cudaMemsetAsync(h->persist_bar, 0, sizeof(unsigned), h->stream);
   if (e) return e;
-  const int8_t* W2 = dq.W2i8;
+  const uint8_t* W2 = dq.W2i8;
   int64_t ld = dq.ld, n = dq.n, v0 = I.var_off, per = h->persist_per;
   const float* qdiag = dq.qdiag;
   float qscale = dq.qscale;
