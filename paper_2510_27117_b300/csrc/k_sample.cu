@@ -391,51 +391,62 @@ __global__ void k_thresholds(const float* __restrict__ p, int64_t v0, int64_t n,
   if (i < ld) thr[i] = i < n ? gf::prob_threshold(p[v0 + i]) : 0u;
 }
 
-// Bernoulli draws of a dense-Q instance written sample-major as bf16 0/1
-// (the tensor-core operand) and as bit words Xb[s * ld/32 + w] (bit t =
-// variable 32 w + t, read by the scorer's epilogue), one thread per
-// (sample = blockIdx.y, 4 variables); 8 consecutive lanes assemble one word.
+// Bernoulli draws of a dense-Q instance written sample-major as FP8 / bf16
+// 0/1 (the tensor-core operand) and as bit words Xb[s * ld/32 + w] (bit t =
+// variable 32 w + t, read by the scorer's epilogue).  A thread takes 4
+// variables and kBernCands consecutive samples (round keys and thresholds
+// loaded once); 8 consecutive lanes assemble one word.
+constexpr int kBernCands = 8;
+
 __global__ void __launch_bounds__(256)
 k_bern_bf16(const uint32_t* __restrict__ thr, int64_t n, int64_t ld,
-            int s0, uint64_t seed, int inst, const GfDState* __restrict__ st,
+            int s0, int len, uint64_t seed, int inst, const GfDState* __restrict__ st,
             void* __restrict__ Xs, uint32_t* __restrict__ Xb, int f8) {
   const int64_t n4 = ld / 4;
   const int64_t g4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g4 >= n4) return;
-  const int sidx = (int)blockIdx.y;
   const int64_t i0 = g4 * 4;
-  uint32_t b[4] = {0, 0, 0, 0};
-  if (i0 < n) {
-    const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)inst, st->round_id,
-                                    (uint32_t)(s0 + sidx), (uint64_t)g4);
-    // thresholds floor(p 2^24) of the round (0 for padding entries)
-    const uint4 t = __ldg(reinterpret_cast<const uint4*>(thr) + g4);
-    b[0] = (u.x >> 8) < t.x;
-    b[1] = (u.y >> 8) < t.y;
-    b[2] = (u.z >> 8) < t.z;
-    b[3] = (u.w >> 8) < t.w;
-  }
-  if (f8) {
-    // FP8 E4M3 one = 0x38
-    const uint32_t out = (b[0] ? 0x38u : 0u) | ((b[1] ? 0x38u : 0u) << 8) |
-                         ((b[2] ? 0x38u : 0u) << 16) | ((b[3] ? 0x38u : 0u) << 24);
-    reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(Xs) + (int64_t)sidx * ld)[g4] = out;
-  } else {
-    // bf16 one = 0x3F80
-    uint2 out;
-    out.x = (b[0] ? 0x3F80u : 0u) | ((b[1] ? 0x3F80u : 0u) << 16);
-    out.y = (b[2] ? 0x3F80u : 0u) | ((b[3] ? 0x3F80u : 0u) << 16);
-    reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(Xs) + (int64_t)sidx * ld)[g4] = out;
-  }
+  const bool live = i0 < n;
+  // thresholds floor(p 2^24) of the round (0 for padding entries)
+  const uint4 t = live ? __ldg(reinterpret_cast<const uint4*>(thr) + g4) : make_uint4(0, 0, 0, 0);
+  const gf::PhiloxKeys K = gf::philox_keys(seed);
+  const uint32_t round = st->round_id;
+  const uint32_t c3 = ((uint32_t)inst & 0x0FFFFFFFu) | (gf::kStreamBern << 28);
   // ld/4 is a multiple of 16, so the 8 lanes holding one 32-variable word
   // are always active together and belong to the same candidate
   const unsigned lane = threadIdx.x & 31u;
   const unsigned m8 = 0xFFu << (lane & ~7u);
-  uint32_t v = (b[0] | (b[1] << 1) | (b[2] << 2) | (b[3] << 3)) << (4 * (lane & 7u));
-  v |= __shfl_xor_sync(m8, v, 1, 8);
-  v |= __shfl_xor_sync(m8, v, 2, 8);
-  v |= __shfl_xor_sync(m8, v, 4, 8);
-  if ((lane & 7u) == 0) Xb[(int64_t)sidx * (ld / 32) + g4 / 8] = v;
+  const int c0 = blockIdx.y * kBernCands;
+#pragma unroll 2
+  for (int c = 0; c < kBernCands; ++c) {
+    const int sidx = c0 + c;
+    if (sidx >= len) break;
+    uint32_t b[4] = {0, 0, 0, 0};
+    if (live) {
+      const uint4 u = gf::philox_k(make_uint4((uint32_t)g4, (uint32_t)(s0 + sidx), round, c3), K);
+      b[0] = (u.x >> 8) < t.x;
+      b[1] = (u.y >> 8) < t.y;
+      b[2] = (u.z >> 8) < t.z;
+      b[3] = (u.w >> 8) < t.w;
+    }
+    if (f8) {
+      // FP8 E4M3 one = 0x38
+      const uint32_t out = (b[0] ? 0x38u : 0u) | ((b[1] ? 0x38u : 0u) << 8) |
+                           ((b[2] ? 0x38u : 0u) << 16) | ((b[3] ? 0x38u : 0u) << 24);
+      reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(Xs) + (int64_t)sidx * ld)[g4] = out;
+    } else {
+      // bf16 one = 0x3F80
+      uint2 out;
+      out.x = (b[0] ? 0x3F80u : 0u) | ((b[1] ? 0x3F80u : 0u) << 16);
+      out.y = (b[2] ? 0x3F80u : 0u) | ((b[3] ? 0x3F80u : 0u) << 16);
+      reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(Xs) + (int64_t)sidx * ld)[g4] = out;
+    }
+    uint32_t v = (b[0] | (b[1] << 1) | (b[2] << 2) | (b[3] << 3)) << (4 * (lane & 7u));
+    v |= __shfl_xor_sync(m8, v, 1, 8);
+    v |= __shfl_xor_sync(m8, v, 2, 8);
+    v |= __shfl_xor_sync(m8, v, 4, 8);
+    if ((lane & 7u) == 0) Xb[(int64_t)sidx * (ld / 32) + g4 / 8] = v;
+  }
 }
 
 }  // namespace
@@ -536,12 +547,13 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
       k_thresholds<<<(unsigned)((dq.ld + 255) / 256), 256, 0, h->stream>>>(
           p, h->ih[dq.inst].var_off, dq.n, dq.ld, dq.thr);
       h->launches++;
-      // one block row per candidate, at most 32768 candidates per launch
-      for (int a = 0; a < len; a += 32768) {
-        const int cnt = std::min(32768, len - a);
-        const dim3 grid((unsigned)((dq.ld / 4 + 255) / 256), (unsigned)cnt);
+      // kBernCands candidates per block row, at most 32768 block rows per launch
+      for (int a = 0; a < len; a += 32768 * kBernCands) {
+        const int cnt = std::min(32768 * kBernCands, len - a);
+        const dim3 grid((unsigned)((dq.ld / 4 + 255) / 256),
+                        (unsigned)((cnt + kBernCands - 1) / kBernCands));
         k_bern_bf16<<<grid, 256, 0, h->stream>>>(
-            dq.thr, dq.n, dq.ld, s0 + a, P.seed, P.inst_base + dq.inst,
+            dq.thr, dq.n, dq.ld, s0 + a, cnt, P.seed, P.inst_base + dq.inst,
             h->dstate,
             dq.f8 ? (void*)(reinterpret_cast<uint8_t*>(dq.Xs) + (int64_t)a * dq.ld)
                   : (void*)(dq.Xs + (int64_t)a * dq.ld),
