@@ -255,7 +255,7 @@ def run_ours(args, rank, world, local):
     peaks, src = load_peaks()
     dinfo = H.dense_info(0)
     roof = roofline(args.workload, insts, k_int, k_b * nr, prof, peaks, src, args.steps,
-                    fp8=dinfo["fp8"])
+                    fp8=dinfo["fp8"], path=H.pdhg_path())
     out = {
         "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -313,10 +313,27 @@ def run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr=1, prop=0, srange=N
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps}
 
 
-def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False):
+# DRAM bytes per launch of the roofline kernel from one ncu capture of the
+# current kernel (dram__bytes_read.sum + dram__bytes_write.sum), with the
+# summary that records it; None where no capture of the current code exists.
+TRAFFIC = {
+    "maxcut": (16.875776e6 + 0.011264e6,
+               "profiles/k_pdhg_dense_persistent_maxcut_n4096.md (one launch = 50 iterations; "
+               "the one-time copy of W2 into shared memory)"),
+}
+PDHG_KERNELS = {
+    "buckets": "PDHG iteration (bucketed k_dual_* / k_primal_* kernels, long-row chunks)",
+    "one_row": "PDHG iteration (k_single_primal + k_single_dual, one-row batches)",
+    "small": "PDHG iterations (k_pdhg_small, one block per instance)",
+    "cooperative": "PDHG iterations (k_pdhg_coop, one cooperative launch)",
+    "persistent": "k_pdhg_dense_persistent (PDHG, Alg. 2, dense Q GEMV)",
+}
+
+
+def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False, path="buckets"):
     """Roofline of the dominant phase of the step (largest share of the
     event-timed step), with the tensor-core scorer reported beside it."""
-    phases = {k: v for k, v in prof.items() if v[1]}
+    phases = {k: v for k, v in prof.items() if v[1] and k != "eval_q"}
     if not phases:
         return None
     dom = max(phases, key=lambda k: phases[k][0])
@@ -343,9 +360,12 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False):
             ms, iters = phases["pdhg"]
             flops = 2.0 * n * n * iters          # one n x n GEMV per iteration
             ach = flops / (ms / 1e3) / 1e12
-            out.update({"kernel": "k_pdhg_dense_persistent (PDHG, Alg. 2, dense Q GEMV)",
+            tr = TRAFFIC.get(workload)
+            out.update({"kernel": PDHG_KERNELS[path],
                         "bound": "alu", "achieved": ach, "peak": fp32_tflops,
-                        "unit": "TFLOP/s", "frac": ach / fp32_tflops, "traffic": None,
+                        "unit": "TFLOP/s", "frac": ach / fp32_tflops,
+                        "traffic": tr[0] if tr else None,
+                        "traffic_source": tr[1] if tr else None,
                         "algorithmic_per_launch": f"k_int x 2 n^2 = {2.0 * n * n * k_int:.4e} FLOP",
                         "us_per_iteration": ms / iters * 1e3, "scoring": tc})
         elif dom == "dense_score" and tc:
@@ -367,11 +387,33 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False):
     if dom == "pdhg":
         ms, iters = phases["pdhg"]
         ach = alg[0] * iters / (ms / 1e3) / 1e9
-        out.update({"kernel": "PDHG iteration (k_dual_rows / k_primal_cols / long-row chunks)",
+        out.update({"kernel": PDHG_KERNELS[path],
                     "bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs", 6400.0),
                     "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6400.0), "traffic": None,
                     "algorithmic_per_iteration": f"{alg[1]} = {alg[0]:.4e} B",
                     "us_per_iteration": ms / iters * 1e3})
+    elif dom == "eval" and workload == "maxcut_sparse":
+        # bit-plane evaluation of the pair sums: per block of 32 pairs and
+        # 32 candidates, P + 1 popc (16 per clock per SM) bound the work;
+        # P = bit width of the pair-weight span
+        import scipy.sparse as sp
+        ms, cnt = prof["eval_q"]                 # k_eval_obj_q alone (events around it)
+        Q = insts[0].Q
+        off = Q - sp.diags(Q.diagonal())
+        w = (off + off.T).tocsr()
+        wu = sp.triu(w, 1).tocoo()
+        npairs = wu.nnz
+        span = int(wu.data.max() - wu.data.min()) if npairs else 0
+        P = max(span, 0).bit_length()
+        pc_per_s = float(npairs) * k_b * cnt / (ms / 1e3)
+        pk = 148 * 2.032e9 * 1024 * 16 / 32.0 / (P + 1)
+        out.update({"kernel": "k_eval_obj_q (sparse-Q pair sums by bit transpose and weight "
+                              "bit planes)", "bound": "alu", "achieved": pc_per_s / 1e12,
+                    "peak": pk / 1e12, "unit": "T pair-candidates/s", "frac": pc_per_s / pk,
+                    "traffic": None,
+                    "peak_note": f"148 SMs x 2.032 GHz x 16 popc/clk, P + 1 = {P + 1} popc per "
+                                 "32 pairs x 32 candidates",
+                    "algorithmic_per_step": f"{npairs} pairs x {k_b} candidates"})
     elif dom in ("fused", "sample"):
         ms, cnt = phases[dom]
         lanes = float(k_b) * n * steps

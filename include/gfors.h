@@ -310,7 +310,7 @@ GFORS_API gfors_status gfors_state_import(gfors_handle h, const void* buf, size_
  * timed launches: 0 PDHG iterations (per captured pair or single step;
  * counts iterations), 1 bit sampling, 2 sparse evaluation, 3 dense scoring,
  * 4 incumbent update, 5 fused sample+evaluate, 6 CheckHalt statistics,
- * 7 dense sampling. */
+ * 7 dense sampling, 8 the sparse-Q objective kernel (also inside 2). */
 GFORS_API gfors_status gfors_profile(gfors_handle h, int32_t enable);
 GFORS_API gfors_status gfors_profile_read(gfors_handle h, int32_t nphases, double* ms,
                                           int64_t* counts);
@@ -388,6 +388,20 @@ GFORS_API gfors_status gfors_tune_cache_store(const char* path, const char* key,
  * FP8 E4M3 operands (else bf16), out[3] = max|W2|, W2 = offdiag(Q + Q^T).
  * Host only. */
 GFORS_API gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t out[4]);
+
+/* Which kernels run the PDHG iterations (Alg. 2) of this handle, fixed at
+ * load: bucketed row / column kernels with CUDA-graph replay, the one-row
+ * streaming kernels (every instance one row, no Q), one block per instance
+ * (instances that fit shared memory), one cooperative launch per call
+ * (pdhg_mode 2), or the persistent dense-Q launch.  Host only. */
+enum {
+  GFORS_PATH_BUCKETS = 0,
+  GFORS_PATH_ONE_ROW = 1,
+  GFORS_PATH_SMALL = 2,
+  GFORS_PATH_COOPERATIVE = 3,
+  GFORS_PATH_PERSISTENT = 4
+};
+GFORS_API gfors_status gfors_pdhg_path(gfors_handle h, int32_t* path);
 
 /* ---- Several devices (Section 3's sampling rounds split by candidate).
  * gfors_sample_eval_range: as gfors_sample_eval, but only candidates

@@ -234,6 +234,35 @@ static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
     }
     return cudaSuccess;
   }
+  // light pairs while more than two iterations remain
+  while (h->use_graphs && nsteps - done >= 3) {
+    const int p = (int)((h->k_host + 1) & 1);
+    if (!h->g_light2[p]) {
+      cudaGraph_t g;
+      if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal))) return e;
+      long long saved = h->launches;
+      h->light_iter = true;
+      cudaError_t e1 = gf_launch_pdhg_iter(h, p);
+      cudaError_t e2 = (e1 == cudaSuccess) ? gf_launch_pdhg_iter(h, 1 - p) : e1;
+      h->light_iter = false;
+      h->pair_launches = h->launches - saved;
+      h->launches = saved;
+      e = cudaStreamEndCapture(h->stream, &g);
+      if (e2 != cudaSuccess) return e2;
+      if (e) return e;
+      e = cudaGraphInstantiate(&h->g_light2[p], g, 0);
+      cudaGraphDestroy(g);
+      if (e) return e;
+    }
+    const int pi = gf_prof_begin(h, 0);
+    if ((e = cudaGraphLaunch(h->g_light2[p], h->stream))) return e;
+    gf_prof_end(h, pi, 2);
+    h->launches += h->pair_launches;
+    host_advance(h, h->k_host + 1);
+    host_advance(h, h->k_host + 2);
+    h->k_host += 2;
+    done += 2;
+  }
   // replay a captured pair of iterations while at least two remain
   while (h->use_graphs && nsteps - done >= 2) {
     const int p = (int)((h->k_host + 1) & 1);   // parity of the first iteration
@@ -377,6 +406,16 @@ extern "C" gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t o
     out[2] = dq.f8;
     out[3] = dq.w2max;
   }
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_pdhg_path(gfors_handle h, int32_t* path) {
+  if (!h || !path) return GFORS_E_ARG;
+  *path = h->persist_ok ? GFORS_PATH_PERSISTENT
+        : h->small_ok   ? GFORS_PATH_SMALL
+        : h->coop_ok    ? GFORS_PATH_COOPERATIVE
+        : h->single_ok  ? GFORS_PATH_ONE_ROW
+                        : GFORS_PATH_BUCKETS;
   return GFORS_OK;
 }
 
@@ -636,6 +675,8 @@ extern "C" gfors_status gfors_set_counters(gfors_handle h, int64_t k, double rho
     std::swap(h->x[0], h->x[1]);
     for (int q = 0; q < 2; ++q)
       if (h->g_iter2[q]) { cudaGraphExecDestroy(h->g_iter2[q]); h->g_iter2[q] = nullptr; }
+    for (int q = 0; q < 2; ++q)
+      if (h->g_light2[q]) { cudaGraphExecDestroy(h->g_light2[q]); h->g_light2[q] = nullptr; }
   }
   const gfors_params& P = h->prm;
   h->n_rho_host = 0;

@@ -1408,8 +1408,10 @@ extern "C" void gfors_destroy(gfors_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   if (h->g_pair) cudaGraphExecDestroy(h->g_pair);
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < 2; ++q) {
     if (h->g_iter2[q]) cudaGraphExecDestroy(h->g_iter2[q]);
+    if (h->g_light2[q]) cudaGraphExecDestroy(h->g_light2[q]);
+  }
   gf_free_all(h);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;

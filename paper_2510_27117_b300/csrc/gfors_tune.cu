@@ -94,11 +94,16 @@ std::string shape_key(GfCtx* h) {
 }
 
 void drop_graphs(GfCtx* h) {
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < 2; ++q) {
     if (h->g_iter2[q]) {
       cudaGraphExecDestroy(h->g_iter2[q]);
       h->g_iter2[q] = nullptr;
     }
+    if (h->g_light2[q]) {
+      cudaGraphExecDestroy(h->g_light2[q]);
+      h->g_light2[q] = nullptr;
+    }
+  }
 }
 
 void apply_lanes(GfCtx* h, const int32_t* l) {

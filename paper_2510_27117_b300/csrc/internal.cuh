@@ -271,6 +271,12 @@ struct gfors_ctx {
   // CUDA graphs of one PDHG iteration pair, by parity of its first iteration
   cudaGraphExec_t g_pair = nullptr;
   cudaGraphExec_t g_iter2[2] = {nullptr, nullptr};
+  // pairs of "light" iterations: they do not store tau1 delta (a feature of
+  // the learned proposal) and, in one-row batches, not xbar either (only the
+  // K xbar partials the next dual step reads); every call's last two
+  // iterations run in full, so both are current between calls
+  cudaGraphExec_t g_light2[2] = {nullptr, nullptr};
+  bool light_iter = false;
   long long pair_launches = 0;
   bool use_graphs = true;
   // single-row batches (one constraint row per instance, no Q): fused

@@ -669,9 +669,11 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
   }
   if (h->nqchunks) {
     dim3 grid((unsigned)h->nqchunks, (unsigned)((kwu + kQW - 1) / kQW));
+    const int pq = gf_prof_begin(h, 8);         // inside phase 2
     k_eval_obj_q<<<grid, 256, 0, h->stream>>>(h->qchunks, h->nqchunks, h->QIi, h->QIc, h->QIv,
                                               h->QIb, h->QIw, h->X, h->kw, kwu, len, h->chunk,
                                               h->obj);
+    gf_prof_end(h, pq, 1);
     h->launches++;
   }
   return cudaGetLastError();

@@ -134,7 +134,7 @@ GF_DEV void short_rows(const GfRun* __restrict__ runs, const int64_t* __restrict
   }
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_dual_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr, int nruns,
              int64_t nrows, const int64_t* __restrict__ Kp, const int32_t* __restrict__ Kc,
              const float* __restrict__ Kv, const float* __restrict__ xbar,
@@ -173,7 +173,7 @@ k_dual_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr
 }
 
 // Columns with at most two K^T entries and no Q entries.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_primal_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr, int nruns,
                int64_t ncols, const int64_t* __restrict__ Tp, const int32_t* __restrict__ Tr,
                const float* __restrict__ Tv, const float* __restrict__ y,
@@ -654,6 +654,7 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
   GfIParam* ipn = h->iprm + (size_t)(1 - parity) * h->ninst;
   const float* xo = h->x[1 - parity];
   float* xn = h->x[parity];
+  float* dl = h->light_iter ? nullptr : h->dlast;   // tau1 delta: full iterations only
   cudaError_t e;
   // ---- dual
   for (const GfBucket& b : h->rb) {
@@ -681,7 +682,7 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
       const int blocks = (int)std::min<int64_t>(h->num_sms, (dq.n + 7) / 8);
       k_dense_primal_i8<<<blocks, kI8Warps * 32, smem, h->stream>>>(
           dq.W2i8, dq.ld, dq.n, I.var_off, dq.qdiag, dq.qscale, hasK ? h->Tp : nullptr, h->Tr,
-          h->Tv, h->y, xo, h->chat, ip, dq.inst, xn, h->xbar, h->dlast, 0, nullptr, adv,
+          h->Tv, h->y, xo, h->chat, ip, dq.inst, xn, h->xbar, dl, 0, nullptr, adv,
           h->dstate, h->sched_d, h->normQhat_d, h->cap_d, ipn);
       h->launches++;
       adv = 0;
@@ -691,7 +692,7 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
     int blocks = (int)std::min<int64_t>((dq.n + kDenseWarps - 1) / kDenseWarps, 296);
     k_dense_primal<<<blocks, kDenseWarps * 32, smem, h->stream>>>(
         dq.W2, dq.ld, dq.n, I.var_off, dq.qdiag, dq.qscale, hasK ? h->Tp : nullptr, h->Tr,
-        h->Tv, h->y, xo, h->chat, ip, dq.inst, xn, h->xbar, h->dlast, 0, nullptr, adv,
+        h->Tv, h->y, xo, h->chat, ip, dq.inst, xn, h->xbar, dl, 0, nullptr, adv,
         h->dstate, h->sched_d, h->normQhat_d, h->cap_d, ipn);
     h->launches++;
     adv = 0;
@@ -699,7 +700,7 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
   }
   for (const GfBucket& b : h->cb) {
     if (!b.count) continue;
-    e = primal_bucket(h, b, b.lanes, ip, xo, xn, h->xbar, h->dlast, adv, ipn);
+    e = primal_bucket(h, b, b.lanes, ip, xo, xn, h->xbar, dl, adv, ipn);
     adv = 0;
     if (e != cudaSuccess) return e;
   }
@@ -709,7 +710,7 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
         h->clong.partial);
     k_primal_long_final<<<(h->clong.nlong + 255) / 256, 256, 0, h->stream>>>(
         h->clong.ids, h->clong.chunk_ptr, h->clong.nlong, h->clong.partial, xo, h->chat,
-        h->var_inst, ip, xn, h->xbar, h->dlast, adv, h->dstate, h->sched_d, h->normQhat_d,
+        h->var_inst, ip, xn, h->xbar, dl, adv, h->dstate, h->sched_d, h->normQhat_d,
         h->cap_d, ipn);
     h->launches += 2;
     adv = 0;

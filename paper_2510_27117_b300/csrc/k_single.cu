@@ -7,7 +7,9 @@
 // fixed chunks of 2048 variables (compensated, deterministic order); a tiny
 // kernel folds an instance's chunk partials in chunk order into the next dual
 // step.  Per variable and iteration the kernels read x_{k-1}, k_i, c_hat_i
-// and write x_k, xbar_k and tau1 delta_i -- the row is never re-read.
+// and write x_k (16 bytes, the algorithmic minimum); xbar_k and tau1 delta_i
+// are stored only by the last two iterations of a call -- the row is never
+// re-read.
 //
 // Partial sums are double-buffered by iteration parity: iteration `it`
 // (parity p = it & 1) reads part[1 - p] (K xbar_{it-1}) in its dual step and
@@ -70,6 +72,8 @@ k_single_partials(const int32_t* __restrict__ ch, const float* __restrict__ kv,
 }
 
 // Primal step of a chunk of variables, fused with the chunk's K xbar partial.
+// FULL = false stores only x_k (xbar_k enters the partial directly).
+template <bool FULL>
 __global__ void __launch_bounds__(kThreads)
 k_single_primal(const int32_t* __restrict__ ch, const float* __restrict__ kv,
                 const float* __restrict__ x_old, const float* __restrict__ chat,
@@ -90,8 +94,10 @@ k_single_primal(const int32_t* __restrict__ ch, const float* __restrict__ kv,
     const float xn = fminf(1.0f, fmaxf(0.0f, xo - p.tau1 * delta));
     const float xb = 2.0f * xn - xo;
     x_new[i] = xn;
-    xbar[i] = xb;
-    if (dlast) dlast[i] = p.tau1 * delta;
+    if (FULL) {
+      xbar[i] = xb;
+      if (dlast) dlast[i] = p.tau1 * delta;
+    }
     acc.add(__fmul_rn(k, xb));
   }
   CSum tot = block_csum(acc);
@@ -117,7 +123,8 @@ cudaError_t gf_single_iter(GfCtx* h, int p) {
   k_single_dual<<<(unsigned)((h->ninst * 32 + 255) / 256), 256, 0, h->stream>>>(
       h->sr_ciptr, h->ninst, h->sr_part + (size_t)(1 - p) * h->sr_nchunk, h->rhat, h->row_eq,
       h->sr_row, ip, h->y);
-  k_single_primal<<<(unsigned)h->sr_nchunk, kThreads, 0, h->stream>>>(
+  auto kern = h->light_iter ? k_single_primal<false> : k_single_primal<true>;
+  kern<<<(unsigned)h->sr_nchunk, kThreads, 0, h->stream>>>(
       h->sr_chunk, h->sr_kv, h->x[1 - p], h->chat, h->y, h->sr_row, ip, h->x[p], h->xbar,
       h->dlast, h->sr_part + (size_t)p * h->sr_nchunk, 1, h->dstate, h->sched_d,
       h->normQhat_d, h->cap_d, ipn);

@@ -208,6 +208,12 @@ class Handle:
         _check(_lib.gfors_dense_info(self.h, inst, _ptr(out)), self.h)
         return dict(dense=bool(out[0]), tc=bool(out[1]), fp8=bool(out[2]), w2max=int(out[3]))
 
+    def pdhg_path(self):
+        """Name of the kernels that run this handle's PDHG iterations."""
+        v = C.c_int32(0)
+        _check(_lib.gfors_pdhg_path(self.h, C.byref(v)), self.h)
+        return ("buckets", "one_row", "small", "cooperative", "persistent")[v.value]
+
     def sample_eval_range(self, nrounds, first_round_id, proposal, s_begin, s_end):
         _check(_lib.gfors_sample_eval_range(self.h, nrounds, first_round_id, proposal,
                                             s_begin, s_end), self.h)
@@ -319,8 +325,9 @@ class Handle:
         buf = C.create_string_buffer(blob, len(blob))
         _check(_lib.gfors_state_import(self.h, buf, len(blob)), self.h)
 
+    # "eval_q" (the sparse-Q objective kernel) is also counted inside "eval"
     PHASES = ("pdhg", "sample", "eval", "dense_score", "incumbent", "fused", "stats",
-              "dense_sample")
+              "dense_sample", "eval_q")
 
     def profile(self, enable=True):
         _check(_lib.gfors_profile(self.h, int(enable)), self.h)
@@ -410,6 +417,7 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
 _lib.gfors_sample_eval_range.argtypes = [vp, i32, u32, i32, i32, i32]
 _lib.gfors_set_assign3d_custom.argtypes = [vp, i32, i32, i32, i32]
 _lib.gfors_dense_info.argtypes = [vp, i32, vp]
+_lib.gfors_pdhg_path.argtypes = [vp, vp]
 _lib.gfors_incumbent_key_async.argtypes = [vp, i32, vp]
 _lib.gfors_autotune.argtypes = [vp, C.c_char_p, vp, vp]
 _lib.gfors_set_lanes.argtypes = [vp, vp]
