@@ -865,6 +865,7 @@ extern "C" gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t m
   } else {
     return gf_fail(h, GFORS_E_ARG, "mode must be 0, 1 or 2");
   }
+  h->n_bit_g4 = -1;                      // Bernoulli group list rebuilt
   if ((e = cudaMemcpy(h->var_grouped + I.var_off, grouped.data(), I.npad,
                       cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->var_grouped_feat + I.var_off, grouped.data(), I.npad,
@@ -900,6 +901,7 @@ extern "C" gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, 
   std::vector<uint8_t> grouped(I.npad, 0);
   for (int64_t i = 0; i < I.n; ++i) grouped[i] = 1;
   cudaError_t e;
+  h->n_bit_g4 = -1;                      // Bernoulli group list rebuilt
   if ((e = cudaMemcpy(h->var_grouped + I.var_off, grouped.data(), I.npad,
                       cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->var_grouped_feat + I.var_off, grouped.data(), I.npad,

@@ -1240,6 +1240,9 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   ALLOC(h->inc, GfInc, ninst);
   ALLOC(h->xbest, uint8_t, N);
   ALLOC(h->var_grouped, uint8_t, N);
+  ALLOC(h->bit_g4, int32_t, N / 4 + 1);
+  ALLOC(h->bit_count, int32_t, 1);
+  h->n_bit_g4 = -1;
   ALLOC(h->var_grouped_feat, uint8_t, N);
   GF_CK(h, cudaMemsetAsync(h->var_grouped_feat, 0, N, s));
   ALLOC(h->stats_part, double, 8 * (h->nrchunk + h->nvchunk + 1));

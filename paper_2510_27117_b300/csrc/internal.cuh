@@ -181,6 +181,12 @@ struct gfors_ctx {
 
   // sampling
   uint8_t* var_grouped = nullptr;   // N: 1 if drawn by a group sampler
+  // 4-variable groups with a variable the Bernoulli sampler draws (any
+  // variable not drawn by a group sampler, padding included), built on the
+  // device when stale (n_bit_g4 < 0)
+  int32_t* bit_g4 = nullptr;
+  int32_t* bit_count = nullptr;
+  int64_t n_bit_g4 = -1;
   int64_t ngroups_tot = 0;
   int64_t* grp_ptr = nullptr;       // global groups (ngroups_tot + 1)
   int64_t* grp_idx = nullptr;       // global variable ids

@@ -7,6 +7,16 @@
 
 namespace {
 
+// Indices of the 4-variable groups holding a variable that no group sampler
+// draws (order irrelevant: every entry writes its own words).
+__global__ void k_bit_list(const uint8_t* __restrict__ grouped, int64_t N4,
+                           int32_t* __restrict__ list, int32_t* __restrict__ count) {
+  const int64_t g4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g4 >= N4) return;
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(grouped + 4 * g4);
+  if (w != 0x01010101u) list[atomicAdd(count, 1)] = (int32_t)g4;
+}
+
 // Generic Bernoulli: X_si = [(u_si >> 8) < floor(p_i 2^24)].  One thread
 // per (4 consecutive variables, 32-sample word): 32 Philox calls fill four
 // words.  Grouped variables (drawn by a group sampler) and padding are
@@ -14,12 +24,12 @@ namespace {
 __global__ void __launch_bounds__(256)
 k_bern_bits(const float* __restrict__ p, const int32_t* __restrict__ var_inst,
             const int64_t* __restrict__ var_off, const uint8_t* __restrict__ grouped,
-            const uint8_t* __restrict__ live, int64_t N4, int kws, int kwu, int s0,
-            int len, uint64_t seed, int inst_base, const GfDState* __restrict__ st,
-            uint32_t* __restrict__ X) {
+            const uint8_t* __restrict__ live, const int32_t* __restrict__ g4list, int64_t N4,
+            int kws, int kwu, int s0, int len, uint64_t seed, int inst_base,
+            const GfDState* __restrict__ st, uint32_t* __restrict__ X) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= N4 * kwu) return;
-  const int64_t g4 = gid / kwu;
+  const int64_t g4 = g4list[gid / kwu];
   const int w = (int)(gid % kwu);
   const int64_t i0 = g4 * 4;
   const int b = var_inst[i0];
@@ -78,9 +88,10 @@ __global__ void k_group_cw(const int64_t* __restrict__ gp, const int64_t* __rest
 // One-hot group draw, one warp per (group, word): lane t draws sample
 // s0 + 32 w + t.  With W = total weight > 0 the pick is the first member
 // whose inclusive prefix exceeds floor(u W / 2^32) (exact 128-bit product,
-// binary search); with W = 0 it is member floor(u len / 2^32).  The warp
-// owns the group's words of column w: it zeroes them, then each distinct
-// pick is written once with the mask of lanes that chose it.
+// binary search); with W = 0 it is member floor(u len / 2^32).  The
+// group's words start zeroed (one memset of the instance's range per
+// chunk); each distinct pick is written once with the mask of lanes that
+// chose it.
 __global__ void __launch_bounds__(256)
 k_group_pick(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
              const int32_t* __restrict__ ginst, const int32_t* __restrict__ glocal,
@@ -94,8 +105,6 @@ k_group_pick(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
   const int w = (int)(wid % kwu);
   const int64_t a = gp[g], e = gp[g + 1];
   const int64_t glen = e - a;
-  for (int64_t t = a + lane; t < e; t += 32) X[gi[t] * kws + w] = 0u;
-  __syncwarp();
   if (glen <= 0) return;
   const int sidx = 32 * w + lane;
   int64_t pick = -1;
@@ -481,28 +490,37 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   const gfors_params& P = h->prm;
   cudaError_t e;
   const int kw = (len + 31) / 32;
-  // axial instances need zeroed words (bits are OR-ed in)
+  // group-sampled instances start from zeroed words (axial picks are OR-ed
+  // in; one-hot picks write only the chosen members' words); the Bernoulli
+  // sampler then overwrites the words of the other variables
   for (int b = 0; b < h->ninst; ++b) {
     const GfInstHost& I = h->ih[b];
-    if (I.group_mode == 2 || I.group_mode == 3) {
+    if (I.group_mode == 1 || I.group_mode == 2 || I.group_mode == 3) {
       e = cudaMemsetAsync(h->X + I.var_off * h->kw, 0, sizeof(uint32_t) * I.npad * h->kw,
                           h->stream);
       if (e != cudaSuccess) return e;
     }
   }
-  // Bernoulli bits are needed unless every instance is drawn by a group
-  // sampler over all its variables or is a dense tensor-core instance
-  bool bits = false;
-  for (int b = 0; b < h->ninst; ++b) {
-    const GfInstHost& I = h->ih[b];
-    if (!(I.group_mode == 2 || I.group_mode == 3 || I.qkind == 1)) bits = true;
-  }
-  if (h->N > 0 && bits) {
+  // Bernoulli bits only for the 4-variable groups that hold a variable no
+  // group sampler draws (the list is rebuilt after the groups change)
+  if (h->n_bit_g4 < 0) {
     const int64_t N4 = h->N / 4;
+    if ((e = cudaMemsetAsync(h->bit_count, 0, sizeof(int32_t), h->stream))) return e;
+    k_bit_list<<<(unsigned)((N4 + 255) / 256), 256, 0, h->stream>>>(h->var_grouped, N4,
+                                                                     h->bit_g4, h->bit_count);
+    int32_t cnt = 0;
+    if ((e = cudaMemcpyAsync(&cnt, h->bit_count, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+      return e;
+    h->n_bit_g4 = cnt;
+  }
+  if (h->n_bit_g4 > 0) {
+    const int64_t N4 = h->n_bit_g4;
     const int64_t threads = N4 * kw;
     k_bern_bits<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(
-        p, h->var_inst, h->var_off_d, h->var_grouped, h->var_live, N4, h->kw, kw, s0, len,
-        P.seed, P.inst_base, h->dstate, h->X);
+        p, h->var_inst, h->var_off_d, h->var_grouped, h->var_live, h->bit_g4, N4, h->kw, kw,
+        s0, len, P.seed, P.inst_base, h->dstate, h->X);
     h->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
