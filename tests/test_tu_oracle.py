@@ -1,0 +1,94 @@
+"""Pins of the oracle's TU reformulation (Thm. 5) against brute force: on
+small instances whose equality rows J are totally unimodular, the
+reformulated problem over x_Ibar has the same optimum (plus the constant
+c0') and its feasible points map one to one onto the original feasible
+points with equal objectives.  No GPU needed."""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import oracle as O
+from oracle import tu as T
+from paper_2510_27117_b300 import workloads as W
+
+
+def _assignment2d(n, idx):
+    """min c^T x over n x n permutation matrices: rows sum_j x_ij = 1 and
+    columns sum_i x_ij = 1 (bipartite incidence matrix, TU)."""
+    rng = np.random.default_rng(100 + idx)
+    N = n * n
+    rows, cols = [], []
+    for i in range(n):
+        for j in range(n):
+            v = i * n + j
+            rows += [i, n + j]
+            cols += [v, v]
+    B = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(2 * n, N))
+    c = rng.integers(-5, 10, size=N).astype(np.float64)
+    return W.Instance(f"assign2d_{n}_{idx}", N, c, B=B, d=np.ones(2 * n))
+
+
+def _all_points(inst):
+    """Every binary point with its (viol, obj) under the oracle evaluator."""
+    X = np.array(list(itertools.product([0, 1], repeat=inst.n)), np.uint8)
+    v, o = O.Evaluator(inst)(X)
+    return X, v, o
+
+
+def _check_equivalent(inst, J, I):
+    R, info = T.tu_reformulate(inst, J, I)
+    X, v, o = _all_points(inst)
+    Xr, vr, orr = _all_points(R)
+    feas = {tuple(x): val for x, val, vv in zip(X, o, v) if vv == 0}
+    feas_r = [(x, val) for x, val, vv in zip(Xr, orr, vr) if vv == 0]
+    assert len(feas_r) == len(feas) > 0
+    mapped = T.tu_recover(info, np.array([x for x, _ in feas_r]))
+    c0 = info["c0"]
+    assert float(c0).is_integer()
+    for (xr, val), x in zip(feas_r, mapped):
+        assert tuple(x) in feas                       # maps onto a feasible point
+        assert feas[tuple(x)] == val + int(c0)        # with the same objective
+    assert min(feas.values()) == min(val for _, val in feas_r) + int(c0)
+    return R, info
+
+
+@pytest.mark.parametrize("idx", range(3))
+def test_tu_assignment_spanning_tree(idx):
+    """J = all rows but the last column row, I = the tree x_00..x_0(n-1),
+    x_10, x_20 (B_JI invertible but not a permutation)."""
+    n = 3
+    inst = _assignment2d(n, idx)
+    J = [0, 1, 2, 3, 4]
+    I = [0, 1, 2, 3, 6]
+    R, info = _check_equivalent(inst, J, I)
+    assert R.n == 4 and R.m2 == 1
+
+
+@pytest.mark.parametrize("idx", range(2))
+def test_tu_facility_location_pivots(idx):
+    """Customer rows sum_i x_ij = 1 with one pivot x_i0j each (B_JI = I)."""
+    inst = W.facility_location(nf=3, nc=3, idx=idx)
+    nf = 3
+    J = list(range(3))
+    # x index nf + j*nf + i; pivot i0 = j mod nf
+    I = [nf + j * nf + (j % nf) for j in range(3)]
+    R, info = _check_equivalent(inst, J, I)
+    assert R.m2 == 0
+
+
+@pytest.mark.parametrize("idx", range(3))
+def test_tu_with_quadratic_term(idx):
+    """A non-symmetric integer Q, general rows A x >= b and one equality
+    sum_{k < 4} x_k = 1 eliminated through x_2 (a wrong Q', c' or c0' term
+    changes some feasible objective)."""
+    rng = np.random.default_rng(200 + idx)
+    n = 9
+    Q = rng.integers(-4, 5, size=(n, n)).astype(np.float64)
+    A = sp.csr_matrix(rng.integers(-2, 3, size=(2, n)).astype(np.float64))
+    b = np.array([-3.0, -2.0])
+    B = sp.csr_matrix((np.ones(4), ([0, 0, 0, 0], [0, 1, 2, 3])), shape=(1, n))
+    c = rng.integers(-6, 7, size=n).astype(np.float64)
+    inst = W.Instance(f"tuq_{idx}", n, c, A=A, b=b, B=B, d=np.ones(1), Q=Q)
+    _check_equivalent(inst, [0], [2])
