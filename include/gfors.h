@@ -389,6 +389,49 @@ GFORS_API gfors_status gfors_tune_cache_store(const char* path, const char* key,
  * Host only. */
 GFORS_API gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t out[4]);
 
+/* ---- TU reformulation (Thm. 5, Section 2.4.1), host only, no GPU needed.
+ * Removes the equality rows J of B by x_I = s + S x_Ibar (s = B_JI^-1 d_J,
+ * S = -B_JI^-1 B_JIbar) for the case in which B_JI is a signed permutation:
+ * every row J[k] has exactly one entry, +1 or -1, in the columns I, and
+ * every column of I has its entry in exactly one of those rows (I[k] need
+ * not be the pivot of J[k]).  The new problem is over x_Ibar, Ibar = the
+ * other columns in ascending order:
+ *   A' = [A_.I S + A_.Ibar; S; -S],  b' = [b - A_.I s; -s; s - 1],
+ *   B' = B_JbarI S + B_JbarIbar (rows of B outside J, ascending),
+ *   d' = d_Jbar - B_JbarI s,  Q' = S^T Q_II S + S^T Q_IIbar + Q_IbarI S +
+ *   Q_IbarIbar,  c' = S^T (Q_II + Q_II^T) s + Q_IIbar^T s + Q_IbarI s +
+ *   S^T c_I + c_Ibar,  objective constant c0' = s^T Q_II s + c_I^T s.
+ * Q is used as given (not symmetrised).  Exactness needs B_J totally
+ * unimodular; that is the caller's claim, not checked.
+ * gfors_tu_reformulate: n, A, b, B, d, Q, c as in gfors_load (A, Q may be
+ *   NULL); J, I: nJ row / column indices.  *out receives an object owned by
+ *   the caller (gfors_tu_free).  GFORS_E_ARG for malformed input or
+ *   repeated / out-of-range indices, GFORS_E_UNSUPPORTED when B_JI is not a
+ *   signed permutation (the LU form of a general B_JI is not built).
+ * gfors_tu_sizes: out[0] = n', out[1] = rows of A', out[2] = nnz(A'),
+ *   out[3] = rows of B', out[4] = nnz(B'), out[5] = 1 if Q' exists,
+ *   out[6] = nnz(Q'), out[7] = |I|.
+ * gfors_tu_copy: copies the CSR arrays (row_ptr, col_idx, val; sized from
+ *   gfors_tu_sizes), b', d', c' (n'), c0' and Ibar (n') into caller buffers;
+ *   any pointer may be NULL to skip that array.
+ * gfors_tu_recover: k candidates over x_Ibar (k x n' bytes, row-major) to
+ *   candidates of the original problem (k x n bytes); GFORS_E_ARG if some
+ *   x_I falls outside {0, 1} (that candidate violates the bounds rows). */
+typedef struct gfors_tu_s* gfors_tu;
+GFORS_API gfors_status gfors_tu_reformulate(int64_t n, const gfors_csr* A, const double* b,
+                                            const gfors_csr* B, const double* d,
+                                            const gfors_qmat* Q, const double* c,
+                                            int64_t nJ, const int64_t* J, const int64_t* I,
+                                            gfors_tu* out);
+GFORS_API gfors_status gfors_tu_sizes(gfors_tu t, int64_t out[8]);
+GFORS_API gfors_status gfors_tu_copy(gfors_tu t, int64_t* Ap, int32_t* Ac, double* Av,
+                                     double* b, int64_t* Bp, int32_t* Bc, double* Bv,
+                                     double* d, int64_t* Qp, int32_t* Qc, double* Qv,
+                                     double* c, double* c0, int64_t* Ibar);
+GFORS_API gfors_status gfors_tu_recover(gfors_tu t, int64_t k, const uint8_t* Xbar,
+                                        uint8_t* X);
+GFORS_API void gfors_tu_free(gfors_tu t);
+
 /* Which kernels run the PDHG iterations (Alg. 2) of this handle, fixed at
  * load: bucketed row / column kernels with CUDA-graph replay, the one-row
  * streaming kernels (every instance one row, no Q), one block per instance

@@ -1,0 +1,290 @@
+// gfors_tu.cu -- TU reformulation (Thm. 5, Section 2.4.1) on the host, for
+// the case in which B_JI is a signed permutation: every row j of J has
+// exactly one entry, +1 or -1, in the columns I, and every column of I has
+// its entry in exactly one row of J.  Then B_JI^-1 is the transposed signed
+// permutation, and for the row j whose pivot is I_k (sign sigma)
+//
+//   x_{I_k} = s_k + S_k x_Ibar,   s_k = sigma d_j,   S_k = -sigma B_{j,Ibar},
+//
+// so S is as sparse as B_JIbar (the paper's remark keeps an LU factor of a
+// general B_JI instead; that form is not built here).  The new problem over
+// x_Ibar (Ibar ascending) is
+//
+//   Q'  = S^T Q_II S + S^T Q_IIbar + Q_IbarI S + Q_IbarIbar
+//   c'  = S^T (Q_II + Q_II^T) s + Q_IIbar^T s + Q_IbarI s + S^T c_I + c_Ibar
+//   c0' = s^T Q_II s + c_I^T s
+//   A'  = [A_.I S + A_.Ibar ;  S ; -S],   b' = [b - A_.I s ; -s ; s - 1]
+//   B'  = B_JbarI S + B_JbarIbar,         d' = d_Jbar - B_JbarI s
+//
+// Q is used as given (not symmetrised), so integral data stay integral.  The
+// theorem needs B_J to be totally unimodular; that is the caller's claim.
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+struct SpRows {                       // rows as (column, value) lists
+  std::vector<int64_t> ptr{0};
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  // append a row from unsorted (column, value) pairs: sum duplicates, drop 0
+  void add_row(std::vector<std::pair<int32_t, double>>& e) {
+    std::sort(e.begin(), e.end(),
+              [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                return a.first < b.first;
+              });
+    for (size_t u = 0; u < e.size();) {
+      size_t w = u;
+      double s = 0.0;
+      while (w < e.size() && e[w].first == e[u].first) s += e[w++].second;
+      if (s != 0.0) {
+        col.push_back(e[u].first);
+        val.push_back(s);
+      }
+      u = w;
+    }
+    ptr.push_back((int64_t)col.size());
+  }
+  int64_t rows() const { return (int64_t)ptr.size() - 1; }
+};
+
+}  // namespace
+
+struct gfors_tu_s {
+  int64_t n = 0, nbar = 0;
+  std::vector<int64_t> I, Ibar;       // pivot columns (given order), the rest
+  std::vector<int64_t> pos;           // n: index in Ibar, or -1 - k for pivot k
+  std::vector<double> s;              // |I|
+  SpRows S;                           // |I| rows over Ibar indices
+  SpRows A, B, Q;                     // reformulated data
+  std::vector<double> b, d, c;
+  double c0 = 0.0;
+  bool hasQ = false;
+};
+
+static bool csr_ok(const gfors_csr* M, int64_t n) {
+  if (!M) return true;
+  if (M->rows < 0 || M->cols != n || M->nnz < 0) return false;
+  if (M->rows > 0 && (!M->row_ptr || M->row_ptr[0] != 0 || M->row_ptr[M->rows] != M->nnz))
+    return false;
+  if (M->nnz > 0 && (!M->col_idx || !M->val)) return false;
+  for (int64_t r = 0; r < M->rows; ++r)
+    if (M->row_ptr[r + 1] < M->row_ptr[r]) return false;
+  for (int64_t t = 0; t < M->nnz; ++t)
+    if (M->col_idx[t] < 0 || M->col_idx[t] >= n) return false;
+  return true;
+}
+
+extern "C" gfors_status gfors_tu_reformulate(int64_t n, const gfors_csr* A, const double* b,
+                                             const gfors_csr* B, const double* d,
+                                             const gfors_qmat* Q, const double* c, int64_t nJ,
+                                             const int64_t* J, const int64_t* I,
+                                             gfors_tu* out) {
+  if (!out) return GFORS_E_ARG;
+  *out = nullptr;
+  if (n <= 0 || n >= (1ll << 30) || !c || !B || !d || nJ <= 0 || !J || !I) return GFORS_E_ARG;
+  if (!csr_ok(A, n) || !csr_ok(B, n) || (A && A->rows > 0 && !b)) return GFORS_E_ARG;
+  if (nJ > B->rows || nJ >= n) return GFORS_E_ARG;
+  if (Q && Q->kind == 1 && !Q->dense_rowmajor) return GFORS_E_ARG;
+  if (Q && Q->kind == 2 && (!csr_ok(&Q->sparse, n) || Q->sparse.rows != n)) return GFORS_E_ARG;
+  gfors_tu_s* t = new gfors_tu_s();
+  t->n = n;
+  t->pos.assign(n, 0);
+  std::vector<int64_t> rowJ(B->rows, -1);          // row of B -> k (pivot index)
+  for (int64_t k = 0; k < nJ; ++k) {
+    if (J[k] < 0 || J[k] >= B->rows || rowJ[J[k]] >= 0 || I[k] < 0 || I[k] >= n ||
+        t->pos[I[k]] != 0) {
+      delete t;
+      return GFORS_E_ARG;
+    }
+    rowJ[J[k]] = k;
+    t->pos[I[k]] = -1 - k;
+  }
+  t->I.assign(I, I + nJ);
+  for (int64_t i = 0; i < n; ++i)
+    if (t->pos[i] == 0) {
+      t->pos[i] = (int64_t)t->Ibar.size();
+      t->Ibar.push_back(i);
+    }
+  t->nbar = (int64_t)t->Ibar.size();
+  // B_JI must be a signed permutation: row J[k] has one pivot entry +-1
+  // (in any column of I); pivot of row J[k] is matched to the column it hits
+  std::vector<int64_t> row_of_pivot(nJ, -1);
+  std::vector<double> sigma(nJ, 0.0);
+  for (int64_t k = 0; k < nJ; ++k) {
+    const int64_t j = J[k];
+    int hits = 0;
+    for (int64_t u = B->row_ptr[j]; u < B->row_ptr[j + 1]; ++u) {
+      const int64_t p = t->pos[B->col_idx[u]];
+      if (p >= 0 || B->val[u] == 0.0) continue;
+      const int64_t kk = -1 - p;
+      ++hits;
+      if ((B->val[u] != 1.0 && B->val[u] != -1.0) || row_of_pivot[kk] >= 0) hits = 99;
+      row_of_pivot[kk] = j;
+      sigma[kk] = B->val[u];
+    }
+    if (hits != 1) {
+      delete t;
+      return GFORS_E_UNSUPPORTED;       // B_JI is not a signed permutation
+    }
+  }
+  // s and S (row k of S belongs to pivot column I[k])
+  t->s.assign(nJ, 0.0);
+  for (int64_t k = 0; k < nJ; ++k) {
+    const int64_t j = row_of_pivot[k];
+    t->s[k] = sigma[k] * d[j];
+    std::vector<std::pair<int32_t, double>> e;
+    for (int64_t u = B->row_ptr[j]; u < B->row_ptr[j + 1]; ++u) {
+      const int64_t p = t->pos[B->col_idx[u]];
+      if (p >= 0) e.emplace_back((int32_t)p, -sigma[k] * B->val[u]);
+    }
+    t->S.add_row(e);
+  }
+  auto add_srow = [&](std::vector<std::pair<int32_t, double>>& e, int64_t k, double a) {
+    for (int64_t u = t->S.ptr[k]; u < t->S.ptr[k + 1]; ++u)
+      e.emplace_back(t->S.col[u], a * t->S.val[u]);
+  };
+  // A' = [A_.I S + A_.Ibar ; S ; -S]
+  std::vector<std::pair<int32_t, double>> e;
+  const int64_t m1 = A ? A->rows : 0;
+  for (int64_t r = 0; r < m1; ++r) {
+    e.clear();
+    double rhs = b[r];
+    for (int64_t u = A->row_ptr[r]; u < A->row_ptr[r + 1]; ++u) {
+      const int64_t p = t->pos[A->col_idx[u]];
+      if (p >= 0) e.emplace_back((int32_t)p, A->val[u]);
+      else { add_srow(e, -1 - p, A->val[u]); rhs -= A->val[u] * t->s[-1 - p]; }
+    }
+    t->A.add_row(e);
+    t->b.push_back(rhs);
+  }
+  for (int sign = 1; sign >= -1; sign -= 2)
+    for (int64_t k = 0; k < nJ; ++k) {
+      e.clear();
+      add_srow(e, k, (double)sign);
+      t->A.add_row(e);
+      t->b.push_back(sign > 0 ? -t->s[k] : t->s[k] - 1.0);
+    }
+  // B' = B_JbarI S + B_JbarIbar over the rows of B outside J
+  for (int64_t r = 0; r < B->rows; ++r) {
+    if (rowJ[r] >= 0) continue;
+    e.clear();
+    double rhs = d[r];
+    for (int64_t u = B->row_ptr[r]; u < B->row_ptr[r + 1]; ++u) {
+      const int64_t p = t->pos[B->col_idx[u]];
+      if (p >= 0) e.emplace_back((int32_t)p, B->val[u]);
+      else { add_srow(e, -1 - p, B->val[u]); rhs -= B->val[u] * t->s[-1 - p]; }
+    }
+    t->B.add_row(e);
+    t->d.push_back(rhs);
+  }
+  // linear part: c' = S^T c_I + c_Ibar, c0' = c_I^T s
+  t->c.assign(t->nbar, 0.0);
+  for (int64_t q = 0; q < t->nbar; ++q) t->c[q] = c[t->Ibar[q]];
+  for (int64_t k = 0; k < nJ; ++k) {
+    const double ck = c[t->I[k]];
+    t->c0 += ck * t->s[k];
+    for (int64_t u = t->S.ptr[k]; u < t->S.ptr[k + 1]; ++u) t->c[t->S.col[u]] += ck * t->S.val[u];
+  }
+  // quadratic part, entry by entry of Q (x_a q x_b with x_I = s + S x_Ibar)
+  if (Q && Q->kind != 0) {
+    t->hasQ = true;
+    std::vector<std::vector<std::pair<int32_t, double>>> qr(t->nbar);
+    auto entry = [&](int64_t a, int64_t bb, double q) {
+      if (q == 0.0) return;
+      const int64_t pa = t->pos[a], pb = t->pos[bb];
+      if (pa >= 0 && pb >= 0) {
+        qr[pa].emplace_back((int32_t)pb, q);
+      } else if (pa < 0 && pb >= 0) {          // (s_k + S_k x) q x_b
+        const int64_t k = -1 - pa;
+        t->c[pb] += t->s[k] * q;
+        for (int64_t u = t->S.ptr[k]; u < t->S.ptr[k + 1]; ++u)
+          qr[t->S.col[u]].emplace_back((int32_t)pb, t->S.val[u] * q);
+      } else if (pa >= 0 && pb < 0) {          // x_a q (s_k + S_k x)
+        const int64_t k = -1 - pb;
+        t->c[pa] += q * t->s[k];
+        for (int64_t u = t->S.ptr[k]; u < t->S.ptr[k + 1]; ++u)
+          qr[pa].emplace_back(t->S.col[u], q * t->S.val[u]);
+      } else {                                 // (s_k1 + S_k1 x) q (s_k2 + S_k2 x)
+        const int64_t k1 = -1 - pa, k2 = -1 - pb;
+        t->c0 += t->s[k1] * q * t->s[k2];
+        for (int64_t u = t->S.ptr[k1]; u < t->S.ptr[k1 + 1]; ++u)
+          t->c[t->S.col[u]] += t->S.val[u] * q * t->s[k2];
+        for (int64_t u = t->S.ptr[k2]; u < t->S.ptr[k2 + 1]; ++u)
+          t->c[t->S.col[u]] += t->s[k1] * q * t->S.val[u];
+        for (int64_t u = t->S.ptr[k1]; u < t->S.ptr[k1 + 1]; ++u)
+          for (int64_t w = t->S.ptr[k2]; w < t->S.ptr[k2 + 1]; ++w)
+            qr[t->S.col[u]].emplace_back(t->S.col[w], t->S.val[u] * q * t->S.val[w]);
+      }
+    };
+    if (Q->kind == 1) {
+      for (int64_t a = 0; a < n; ++a)
+        for (int64_t bb = 0; bb < n; ++bb) entry(a, bb, Q->dense_rowmajor[a * n + bb]);
+    } else {
+      for (int64_t a = 0; a < n; ++a)
+        for (int64_t u = Q->sparse.row_ptr[a]; u < Q->sparse.row_ptr[a + 1]; ++u)
+          entry(a, Q->sparse.col_idx[u], Q->sparse.val[u]);
+    }
+    for (int64_t q = 0; q < t->nbar; ++q) t->Q.add_row(qr[q]);
+  }
+  *out = t;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_tu_sizes(gfors_tu t, int64_t out[8]) {
+  if (!t || !out) return GFORS_E_ARG;
+  out[0] = t->nbar;
+  out[1] = t->A.rows();
+  out[2] = (int64_t)t->A.col.size();
+  out[3] = t->B.rows();
+  out[4] = (int64_t)t->B.col.size();
+  out[5] = t->hasQ ? 1 : 0;
+  out[6] = t->hasQ ? (int64_t)t->Q.col.size() : 0;
+  out[7] = (int64_t)t->I.size();
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_tu_copy(gfors_tu t, int64_t* Ap, int32_t* Ac, double* Av,
+                                      double* b, int64_t* Bp, int32_t* Bc, double* Bv,
+                                      double* d, int64_t* Qp, int32_t* Qc, double* Qv,
+                                      double* c, double* c0, int64_t* Ibar) {
+  if (!t) return GFORS_E_ARG;
+  auto cp = [](const SpRows& M, int64_t* p, int32_t* cc, double* v) {
+    if (p) std::copy(M.ptr.begin(), M.ptr.end(), p);
+    if (cc) std::copy(M.col.begin(), M.col.end(), cc);
+    if (v) std::copy(M.val.begin(), M.val.end(), v);
+  };
+  cp(t->A, Ap, Ac, Av);
+  cp(t->B, Bp, Bc, Bv);
+  if (t->hasQ) cp(t->Q, Qp, Qc, Qv);
+  if (b) std::copy(t->b.begin(), t->b.end(), b);
+  if (d) std::copy(t->d.begin(), t->d.end(), d);
+  if (c) std::copy(t->c.begin(), t->c.end(), c);
+  if (c0) *c0 = t->c0;
+  if (Ibar) std::copy(t->Ibar.begin(), t->Ibar.end(), Ibar);
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_tu_recover(gfors_tu t, int64_t k, const uint8_t* Xbar,
+                                         uint8_t* X) {
+  if (!t || k < 0 || (k > 0 && (!Xbar || !X))) return GFORS_E_ARG;
+  bool in_range = true;
+  for (int64_t r = 0; r < k; ++r) {
+    const uint8_t* xb = Xbar + r * t->nbar;
+    uint8_t* x = X + r * t->n;
+    for (int64_t q = 0; q < t->nbar; ++q) x[t->Ibar[q]] = xb[q] ? 1 : 0;
+    for (size_t kk = 0; kk < t->I.size(); ++kk) {
+      double v = t->s[kk];
+      for (int64_t u = t->S.ptr[kk]; u < t->S.ptr[kk + 1]; ++u)
+        if (xb[t->S.col[u]]) v += t->S.val[u];
+      in_range &= (v == 0.0 || v == 1.0);
+      x[t->I[kk]] = v == 1.0 ? 1 : 0;
+    }
+  }
+  return in_range ? GFORS_OK : GFORS_E_ARG;
+}
+
+extern "C" void gfors_tu_free(gfors_tu t) { delete t; }

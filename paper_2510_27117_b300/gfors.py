@@ -418,6 +418,12 @@ _lib.gfors_sample_eval_range.argtypes = [vp, i32, u32, i32, i32, i32]
 _lib.gfors_set_assign3d_custom.argtypes = [vp, i32, i32, i32, i32]
 _lib.gfors_dense_info.argtypes = [vp, i32, vp]
 _lib.gfors_pdhg_path.argtypes = [vp, vp]
+_lib.gfors_tu_reformulate.argtypes = [i64, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
+_lib.gfors_tu_sizes.argtypes = [vp, vp]
+_lib.gfors_tu_copy.argtypes = [vp] + [vp] * 14
+_lib.gfors_tu_recover.argtypes = [vp, i64, vp, vp]
+_lib.gfors_tu_free.argtypes = [vp]
+_lib.gfors_tu_free.restype = None
 _lib.gfors_incumbent_key_async.argtypes = [vp, i32, vp]
 _lib.gfors_autotune.argtypes = [vp, C.c_char_p, vp, vp]
 _lib.gfors_set_lanes.argtypes = [vp, vp]
@@ -425,6 +431,62 @@ _lib.gfors_get_lanes.argtypes = [vp, vp]
 _lib.gfors_tune_key.argtypes = [vp, C.c_char_p, C.c_size_t]
 _lib.gfors_tune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, vp, vp]
 _lib.gfors_tune_cache_store.argtypes = [C.c_char_p, C.c_char_p, vp]
+
+
+class TuReformulation:
+    """gfors_tu: a TU-reformulated problem (Thm. 5) and the map back."""
+
+    def __init__(self, t, n, nbar, c0, Ibar):
+        self.t = t if isinstance(t, vp) else vp(t)
+        self.n, self.nbar, self.c0, self.Ibar = n, nbar, c0, Ibar
+
+    def recover(self, Xbar):
+        """Original candidates (k x n uint8) from candidates over x_Ibar."""
+        Xbar = np.ascontiguousarray(Xbar, np.uint8).reshape(-1, self.nbar)
+        X = np.zeros((Xbar.shape[0], self.n), np.uint8)
+        _check(_lib.gfors_tu_recover(self.t, Xbar.shape[0], _ptr(Xbar), _ptr(X)))
+        return X
+
+    def __del__(self):
+        if getattr(self, "t", None) is not None and self.t.value:
+            _lib.gfors_tu_free(self.t)
+            self.t = None
+
+
+def tu_reformulate(inst, J, I):
+    """gfors_tu_reformulate on an Instance: returns (Instance over x_Ibar,
+    TuReformulation).  The new instance's meta holds the objective constant
+    c0' ("tu_c0"); groups, closure and axial marks do not carry over."""
+    import scipy.sparse as sp
+    from .workloads import Instance
+    hd = _InstHold(inst)
+    J = np.ascontiguousarray(J, np.int64)
+    I = np.ascontiguousarray(I, np.int64)
+    out = vp()
+    _check(_lib.gfors_tu_reformulate(
+        inst.n, C.byref(hd.A.s) if hd.A else None, _ptr(hd.b) if hd.b is not None else None,
+        C.byref(hd.B.s) if hd.B else None, _ptr(hd.d) if hd.d is not None else None,
+        C.byref(hd.Q) if hd.Q is not None else None, _ptr(hd.c), J.size, _ptr(J), _ptr(I),
+        C.byref(out)))
+    sz = np.zeros(8, np.int64)
+    _check(_lib.gfors_tu_sizes(out, _ptr(sz)))
+    nbar, m1, nnzA, m2, nnzB, hasQ, nnzQ = (int(v) for v in sz[:7])
+    Ap, Ac, Av = np.zeros(m1 + 1, np.int64), np.zeros(max(nnzA, 1), np.int32), np.zeros(max(nnzA, 1))
+    Bp, Bc, Bv = np.zeros(m2 + 1, np.int64), np.zeros(max(nnzB, 1), np.int32), np.zeros(max(nnzB, 1))
+    Qp, Qc, Qv = np.zeros(nbar + 1, np.int64), np.zeros(max(nnzQ, 1), np.int32), np.zeros(max(nnzQ, 1))
+    b, d, c = np.zeros(max(m1, 1)), np.zeros(max(m2, 1)), np.zeros(nbar)
+    c0 = C.c_double(0.0)
+    Ibar = np.zeros(nbar, np.int64)
+    _check(_lib.gfors_tu_copy(out, _ptr(Ap), _ptr(Ac), _ptr(Av), _ptr(b), _ptr(Bp), _ptr(Bc),
+                              _ptr(Bv), _ptr(d), _ptr(Qp), _ptr(Qc), _ptr(Qv), _ptr(c),
+                              C.byref(c0), _ptr(Ibar)))
+    A = sp.csr_matrix((Av[:nnzA], Ac[:nnzA], Ap), shape=(m1, nbar)) if m1 else None
+    B = sp.csr_matrix((Bv[:nnzB], Bc[:nnzB], Bp), shape=(m2, nbar)) if m2 else None
+    Q = sp.csr_matrix((Qv[:nnzQ], Qc[:nnzQ], Qp), shape=(nbar, nbar)) if hasQ else None
+    new = Instance(inst.name + "_tu", nbar, c, A=A, b=b[:m1] if m1 else None, B=B,
+                   d=d[:m2] if m2 else None, Q=Q)
+    new.meta["tu_c0"] = c0.value
+    return new, TuReformulation(out, inst.n, nbar, c0.value, Ibar)
 
 
 def tune_cache_lookup(path, key):

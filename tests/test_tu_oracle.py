@@ -92,3 +92,75 @@ def test_tu_with_quadratic_term(idx):
     c = rng.integers(-6, 7, size=n).astype(np.float64)
     inst = W.Instance(f"tuq_{idx}", n, c, A=A, b=b, B=B, d=np.ones(1), Q=Q)
     _check_equivalent(inst, [0], [2])
+
+
+# ------------------------------------------------ library transform vs oracle
+def _as_dense(M, shape):
+    if M is None:
+        return np.zeros(shape)
+    return M.toarray() if sp.issparse(M) else np.asarray(M, np.float64)
+
+
+def _same_problem(L, R):
+    """The library's reformulation equals the oracle's exactly (integral data;
+    empty rows and zero entries compared as dense arrays)."""
+    assert L.n == R.n
+    assert np.array_equal(L.c, R.c)
+    assert np.array_equal(_as_dense(L.A, (L.m1, L.n)), _as_dense(R.A, (R.m1, R.n)))
+    assert np.array_equal(np.asarray(L.b), np.asarray(R.b))
+    assert L.m2 == R.m2
+    if L.m2:
+        assert np.array_equal(_as_dense(L.B, (L.m2, L.n)), _as_dense(R.B, (R.m2, R.n)))
+        assert np.array_equal(np.asarray(L.d), np.asarray(R.d))
+    assert (L.Q is None) == (R.Q is None)
+    if L.Q is not None:
+        assert np.array_equal(_as_dense(L.Q, (L.n, L.n)), _as_dense(R.Q, (R.n, R.n)))
+
+
+@pytest.mark.parametrize("idx", range(2))
+def test_library_tu_matches_oracle_facility(idx):
+    from paper_2510_27117_b300 import gfors as G
+    inst = W.facility_location(nf=4, nc=5, idx=idx)
+    nf = 4
+    J = list(range(5))
+    I = [nf + j * nf + ((3 * j) % nf) for j in range(5)]
+    L, t = G.tu_reformulate(inst, J, I)
+    R, info = T.tu_reformulate(inst, J, I)
+    _same_problem(L, R)
+    assert L.meta["tu_c0"] == info["c0"]
+    # recovery agrees with the oracle's on every feasible reformulated point
+    Xr = np.array(list(itertools.product([0, 1], repeat=min(L.n, 14))), np.uint8)
+    Xr = np.hstack([Xr, np.zeros((Xr.shape[0], L.n - Xr.shape[1]), np.uint8)])
+    v, _ = O.Evaluator(R)(Xr)
+    ok = Xr[v == 0]
+    assert np.array_equal(t.recover(ok), T.tu_recover(info, ok))
+
+
+@pytest.mark.parametrize("idx", range(3))
+def test_library_tu_matches_oracle_quadratic(idx):
+    from paper_2510_27117_b300 import gfors as G
+    rng = np.random.default_rng(300 + idx)
+    n = 11
+    Q = rng.integers(-4, 5, size=(n, n)).astype(np.float64)
+    A = sp.csr_matrix(rng.integers(-2, 3, size=(3, n)).astype(np.float64))
+    b = np.array([-3.0, -2.0, -4.0])
+    # two equality rows with pivots x_2 (sign -1) and x_7 (+1); a third row kept
+    Bd = np.zeros((3, n))
+    Bd[0, [0, 1, 2, 3]] = [1, 1, -1, 1]
+    Bd[1, [4, 5, 7]] = [1, -1, 1]
+    Bd[2, [2, 7, 9]] = [1, 1, 1]
+    inst = W.Instance(f"tuql_{idx}", n, rng.integers(-6, 7, size=n).astype(np.float64),
+                      A=A, b=b, B=sp.csr_matrix(Bd), d=np.array([0.0, 1.0, 1.0]),
+                      Q=sp.csr_matrix(Q) if idx % 2 else Q)
+    L, t = G.tu_reformulate(inst, [1, 0], [7, 2])
+    R, info = T.tu_reformulate(inst, [1, 0], [7, 2])
+    _same_problem(L, R)
+    assert L.meta["tu_c0"] == info["c0"]
+
+
+def test_library_tu_general_pivots_unsupported():
+    from paper_2510_27117_b300 import gfors as G
+    inst = _assignment2d(3, 0)
+    with pytest.raises(G.GforsError) as e:
+        G.tu_reformulate(inst, [0, 1, 2, 3, 4], [0, 1, 2, 3, 6])
+    assert e.value.status == 6                      # GFORS_E_UNSUPPORTED
