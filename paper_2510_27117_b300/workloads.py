@@ -254,6 +254,17 @@ def facility_location(nf: int = 1000, nc: int = 10000, idx: int = 0,
 # Tiny random BIPs for brute force (n <= 20): mixed >= rows, one equality
 # row, symmetric integer Q, integer c.
 # --------------------------------------------------------------------------
+def facility_tu_pivots(inst: Instance, nf: int, nc: int):
+    """Row and column index sets (J, I) for the TU reformulation (Thm. 5) of
+    a facility-location instance: every customer row sum_i x_ij = 1 with the
+    customer's cheapest x_ij as its pivot (B_JI is the identity)."""
+    cx = np.asarray(inst.c[nf:], np.float64).reshape(nc, nf)
+    i0 = cx.argmin(axis=1)
+    J = np.arange(nc, dtype=np.int64)
+    I = nf + np.arange(nc, dtype=np.int64) * nf + i0
+    return J, I
+
+
 def tiny_bip(n: int = 12, m1: int = 4, m2: int = 1, idx: int = 0,
              with_Q: bool = True, family: int = 9) -> Instance:
     rng = _rng(family, idx)

@@ -35,6 +35,10 @@ CASES = {
     "maxcut_sparse": lambda: W.max_cut_sparse(n=3000, avg_deg=12.0, idx=1),
     "assign3d": lambda: W.assign3d(I=8, idx=1),
     "facloc": lambda: W.facility_location(nf=12, nc=40, idx=2),
+    # the same shape after the library's TU reformulation (Thm. 5)
+    "facloc_tu": lambda: G.tu_reformulate(
+        W.facility_location(nf=12, nc=40, idx=2),
+        *W.facility_tu_pivots(W.facility_location(nf=12, nc=40, idx=2), 12, 40))[0],
 }
 
 
@@ -111,7 +115,7 @@ def test_pdhg_single_step(name, mode):
 @pytest.mark.parametrize("name,mode", [("setcover", 0), ("knapsack", 1), ("knapsack", 2),
                                        ("tiny", 0), ("maxcut", 0), ("assign3d", 0),
                                        ("facloc", 0), ("maxcut_csr", 0),
-                                       ("maxcut_sparse", 0)])
+                                       ("maxcut_sparse", 0), ("facloc_tu", 0)])
 def test_sampling_and_evaluation_bit_exact(name, mode):
     inst = CASES[name]()
     gp, op = _params(eval_mode=mode, k_b=96 if name != "maxcut" else 128)
@@ -454,3 +458,23 @@ def test_alg4_sampler_bit_exact(I, gamma, L, k_b):
     vo, oo = O.Evaluator(inst)(Xo)
     assert np.array_equal(obj, oo)
     H.destroy()
+
+
+def test_tu_incumbent_maps_back():
+    """GFORS on a TU-reformulated facility-location instance: the incumbent,
+    mapped back by x_I = s + S x_Ibar, is feasible for the original problem
+    with objective = reformulated objective + c0' (Thm. 5)."""
+    inst = W.facility_location(nf=12, nc=40, idx=5)
+    J, I = W.facility_tu_pivots(inst, 12, 40)
+    R, tu = G.tu_reformulate(inst, J, I)
+    gp, _ = _params(k_b=1024, k_int=50)
+    H = G.load(R, gp)
+    for r in range(20):
+        H.pdhg_steps(50)
+        H.sample_eval(1, r, 0)
+    inc = H.incumbent(0)
+    H.destroy()
+    assert inc["found"]
+    X = tu.recover(inc["x"][None, :])
+    v, o = O.Evaluator(inst)(X)
+    assert v[0] == 0 and o[0] == inc["obj"] + int(tu.c0)
