@@ -396,7 +396,8 @@ GFORS_API gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t ou
  * every column of I has its entry in exactly one of those rows (I[k] need
  * not be the pivot of J[k]).  The new problem is over x_Ibar, Ibar = the
  * other columns in ascending order:
- *   A' = [A_.I S + A_.Ibar; S; -S],  b' = [b - A_.I s; -s; s - 1],
+ *   A' = [A_.I S + A_.Ibar; S; -S],  b' = [b - A_.I s; -s; s - 1] (a
+ *   bounds row that every x in [0, 1] satisfies is left out),
  *   B' = B_JbarI S + B_JbarIbar (rows of B outside J, ascending),
  *   d' = d_Jbar - B_JbarI s,  Q' = S^T Q_II S + S^T Q_IIbar + Q_IbarI S +
  *   Q_IbarIbar,  c' = S^T (Q_II + Q_II^T) s + Q_IIbar^T s + Q_IbarI s +

@@ -15,7 +15,9 @@ the order the theorem defines them:
     B'  = B_JbarI S + B_JbarIbar,      d' = d_Jbar - B_JbarI s
     c'  = S^T (Q_II + Q_II^T) s + Q_IIbar^T s + Q_IbarI s + S^T c_I + c_Ibar
     c0' = s^T Q_II s + c_I^T s
-    S x >= -s,   -S x >= s - 1          (x_I within [0, 1])
+    S x >= -s,   -S x >= s - 1          (x_I within [0, 1]; a bounds row
+                                         that every x in [0, 1] satisfies is
+                                         left out)
 
 Q is used as given (not symmetrised), so integral data stay integral; for a
 symmetric Q the linear terms reduce to the theorem's 2 S^T Q_II s + 2 Q_IIbar^T s.
@@ -72,10 +74,13 @@ def tu_reformulate(inst, J, I):
         A = _dense(inst.A, (inst.m1, n))
         rowsA.append(A[:, I] @ S + A[:, Ibar])
         rhsA.append(np.asarray(inst.b, np.float64) - A[:, I] @ s)
-    rowsA.append(S)
-    rhsA.append(-s)
-    rowsA.append(-S)
-    rhsA.append(s - 1.0)
+    # bounds rows of x_I, except those every x in [0, 1] satisfies (the
+    # row's minimum over the box, sum of its negative coefficients, is at
+    # least its right-hand side)
+    for M, r in ((S, -s), (-S, s - 1.0)):
+        keep = np.minimum(M, 0.0).sum(axis=1) < r
+        rowsA.append(M[keep])
+        rhsA.append(r[keep])
     A_new = np.vstack(rowsA)
     b_new = np.concatenate(rhsA)
     B_new = d_new = None

@@ -14,6 +14,7 @@
 //   c'  = S^T (Q_II + Q_II^T) s + Q_IIbar^T s + Q_IbarI s + S^T c_I + c_Ibar
 //   c0' = s^T Q_II s + c_I^T s
 //   A'  = [A_.I S + A_.Ibar ;  S ; -S],   b' = [b - A_.I s ; -s ; s - 1]
+//         (a bounds row that every x in [0, 1] satisfies is left out)
 //   B'  = B_JbarI S + B_JbarIbar,         d' = d_Jbar - B_JbarI s
 //
 // Q is used as given (not symmetrised), so integral data stay integral.  The
@@ -161,12 +162,19 @@ extern "C" gfors_status gfors_tu_reformulate(int64_t n, const gfors_csr* A, cons
     t->A.add_row(e);
     t->b.push_back(rhs);
   }
+  // bounds rows of x_I, except those every x in [0, 1] satisfies (sum of
+  // the negative coefficients at least the right-hand side)
   for (int sign = 1; sign >= -1; sign -= 2)
     for (int64_t k = 0; k < nJ; ++k) {
+      const double rhs = sign > 0 ? -t->s[k] : t->s[k] - 1.0;
+      double lo = 0.0;
+      for (int64_t u = t->S.ptr[k]; u < t->S.ptr[k + 1]; ++u)
+        lo += std::min(0.0, sign * t->S.val[u]);
+      if (lo >= rhs) continue;
       e.clear();
       add_srow(e, k, (double)sign);
       t->A.add_row(e);
-      t->b.push_back(sign > 0 ? -t->s[k] : t->s[k] - 1.0);
+      t->b.push_back(rhs);
     }
   // B' = B_JbarI S + B_JbarIbar over the rows of B outside J
   for (int64_t r = 0; r < B->rows; ++r) {

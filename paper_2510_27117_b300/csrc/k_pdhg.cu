@@ -781,16 +781,19 @@ cudaError_t gf_tune_lanes(GfCtx* h, int32_t lanes_out[10]) {
     for (size_t k = 0; k < bs.size() && e == cudaSuccess; ++k) {
       GfBucket& b = bs[k];
       if (!b.count) continue;
+      // candidates in ascending lane count; a wider choice must beat the
+      // best narrower one by 3% (timings of L2-resident buckets are close,
+      // and the narrow form keeps more rows in flight when data are cold)
       float best = 1e30f;
       int pick = b.lanes;
       for (int c : cand) {
-        if (c > 2 * maxlen[std::min<size_t>(k, 4)]) continue;
+        if (c > maxlen[std::min<size_t>(k, 4)]) continue;
         float ms = time_launches(h, [&]() {
           return side ? primal_bucket(h, b, c, ip, xo, xs, xb, nullptr, 0, nullptr)
                       : dual_bucket(h, b, c, ip, ys);
         }, &e);
         if (e != cudaSuccess) break;
-        if (ms < best) { best = ms; pick = c; }
+        if (ms < 0.97f * best) { best = ms; pick = c; }
       }
       b.lanes = pick;
     }

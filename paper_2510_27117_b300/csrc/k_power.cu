@@ -317,11 +317,18 @@ extern "C++" cudaError_t gf_power_run(GfCtx* h, int which, const int64_t* Mp,
   }
   const int maxit = h->prm.power_maxit > 0 ? h->prm.power_maxit : 5000;
   const double tol = h->prm.power_tol > 0 ? h->prm.power_tol : 1e-12;
+  // lanes per row of M from its mean row length (rows of two nonzeros get
+  // one thread, rows of hundreds a warp)
+  const double mean_len = mrows > 0 ? (double)h->nnzK / (double)mrows : 0.0;
+  const int rl = mean_len <= 4 ? 1 : mean_len <= 16 ? 4 : mean_len <= 64 ? 8 : 32;
   auto product = [&](const double* in, double* out, bool transpose) {
     if (which == 0) {
       if (!transpose) {
-        k_spmv64<32><<<(unsigned)((mrows * 32 + 255) / 256), 256, 0, s>>>(Mp, Mc, Mv, in, mrows,
-                                                                          out);
+        const unsigned nblk = (unsigned)((mrows * rl + 255) / 256);
+        if (rl == 1) k_spmv64<1><<<nblk, 256, 0, s>>>(Mp, Mc, Mv, in, mrows, out);
+        else if (rl == 4) k_spmv64<4><<<nblk, 256, 0, s>>>(Mp, Mc, Mv, in, mrows, out);
+        else if (rl == 8) k_spmv64<8><<<nblk, 256, 0, s>>>(Mp, Mc, Mv, in, mrows, out);
+        else k_spmv64<32><<<nblk, 256, 0, s>>>(Mp, Mc, Mv, in, mrows, out);
       } else {
         k_spmv64<4><<<(unsigned)((N * 4 + 255) / 256), 256, 0, s>>>(Tp, Tr, Tv, in, N, out);
       }
