@@ -491,6 +491,26 @@ void orc_closure(int64_t n, int64_t nrep, const int64_t* rv, const int64_t* rp,
     }
 }
 
+/* Repair after a monotone relaxation (Section 2.4.3): an equality group
+ * sum_{k in G} x_k = 1 relaxed to sum >= 1 lets a candidate select several
+ * members; the repair keeps the selected member of least cost c_k (ties to
+ * the member listed first) and clears the others, so the candidate meets
+ * the equality again whenever it selected any member.  Valid when dropping
+ * a member can violate no other constraint (the caller's claim). */
+void orc_repair_min(int64_t n, int64_t ng, const int64_t* gp, const int64_t* gi,
+                    const int64_t* cost, int32_t k, uint8_t* X) {
+  for (int32_t s = 0; s < k; ++s) {
+    uint8_t* x = X + (int64_t)s * n;
+    for (int64_t g = 0; g < ng; ++g) {
+      int64_t keep = -1;
+      for (int64_t t = gp[g]; t < gp[g + 1]; ++t)
+        if (x[gi[t]] && (keep < 0 || cost[gi[t]] < cost[keep])) keep = gi[t];
+      for (int64_t t = gp[g]; t < gp[g + 1]; ++t)
+        if (gi[t] != keep) x[gi[t]] = 0;
+    }
+  }
+}
+
 /* ======================================================================
  * EvalBest, evaluation half (Section 3 and Eq. 1), on the ORIGINAL data:
  *   viol_s = #{j : A_j X_s < b_j} + #{j : B_j X_s != d_j}

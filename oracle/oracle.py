@@ -45,6 +45,7 @@ def lib():
         L.orc_philox4x32_10.argtypes = [U32P, U32P, U32P]
         L.orc_philox_lane.argtypes = [u64, u32, u32, u32, u32, u64]
         L.orc_philox_lane.restype = u32
+        L.orc_repair_min.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
         L.orc_philox_lanes.argtypes = [u64, u32, u32, u32, u32, i64, U32P]
         L.orc_row_normalize.argtypes = [i64, i64, I64P, F64P, F64P, F64P]
         L.orc_row_normalize.restype = i64
@@ -150,6 +151,16 @@ def assign3d_custom(p32, cost, I, gamma, L, k, seed, inst, round_id):
     return X
 
 
+def repair_min(X, groups, cost):
+    """Monotone-relaxation repair: per relaxed group keep the selected member
+    of least cost (ties to the first listed), clear the others."""
+    gp, gi = (np.ascontiguousarray(a, np.int64) for a in groups)
+    cost = np.ascontiguousarray(cost, np.int64)
+    k, n = X.shape
+    lib().orc_repair_min(n, gp.size - 1, gp, gi, cost, k, X)
+    return X
+
+
 def closure(X, clos):
     rv, rp, ri = (np.ascontiguousarray(a, np.int64) for a in clos)
     k, n = X.shape
@@ -178,6 +189,8 @@ def sample(inst, p32, k, seed, inst_id, round_id, mode=None):
         X = bernoulli(p32, k, seed, inst_id, round_id, mask)
         if mode == 1 and inst.groups is not None:
             onehot(p32, inst.groups, k, seed, inst_id, round_id, X)
+    if inst.repair is not None:
+        repair_min(X, inst.repair, np.asarray(inst.c, np.int64))
     if inst.closure is not None:
         closure(X, inst.closure)
     return X

@@ -32,7 +32,9 @@ class Instance:
     feasible point) as (grp_ptr, grp_idx); ``axial_I`` > 0 marks an axial 3D
     assignment over I^3 variables x_ijk at index (i*I + j)*I + k;
     ``closure`` = (rep_var, rep_ptr, rep_idx) lists monotone repairs
-    y <- y OR x_k for k in the list (the facility-location closure).
+    y <- y OR x_k for k in the list (the facility-location closure);
+    ``repair`` = (grp_ptr, grp_idx) lists equality groups relaxed to
+    "sum >= 1" whose candidates keep only their least-cost selected member.
     """
 
     name: str
@@ -46,6 +48,7 @@ class Instance:
     groups: Optional[Tuple[np.ndarray, np.ndarray]] = None
     axial_I: int = 0
     closure: Optional[Tuple[np.ndarray, np.ndarray, np.ndarray]] = None
+    repair: Optional[Tuple[np.ndarray, np.ndarray]] = None
     meta: dict = field(default_factory=dict)
 
     @property
@@ -210,7 +213,12 @@ def assign3d(I: int = 64, idx: int = 0, family: int = A3D, sampler: str = "axial
 # at index nf + j*nf + i.  Rows: sum_i x_ij = 1 (equalities), y_i - x_ij >= 0.
 # --------------------------------------------------------------------------
 def facility_location(nf: int = 1000, nc: int = 10000, idx: int = 0,
-                      family: int = FL) -> Instance:
+                      family: int = FL, relaxed: bool = False) -> Instance:
+    """relaxed=True: the monotone relaxation of Section 2.4.3 (costs are
+    nonnegative): the customer rows sum_i x_ij = 1 become sum_i x_ij >= 1
+    (appended to A), candidates come from plain Bernoulli draws, and each
+    customer's selected facilities are cut to the cheapest one by the repair
+    groups before the closure."""
     rng = _rng(family, idx)
     fac = rng.random((nf, 2))
     cus = rng.random((nc, 2))
@@ -243,9 +251,15 @@ def facility_location(nf: int = 1000, nc: int = 10000, idx: int = 0,
     rep_ptr = np.arange(0, nf * nc + 1, nc, dtype=np.int64)
     rep_idx = (nf + np.arange(nc, dtype=np.int64)[None, :] * nf
                + np.arange(nf, dtype=np.int64)[:, None]).reshape(-1)
-    inst = Instance(f"facloc_nf{nf}_nc{nc}_s{idx}", n, c, A=A, b=np.zeros(m1),
-                    B=B, d=np.ones(nc), groups=(grp_ptr, grp_idx),
-                    closure=(rep_var, rep_ptr, rep_idx))
+    if relaxed:
+        A = sp.vstack([A, B]).tocsr()
+        inst = Instance(f"facloc_rel_nf{nf}_nc{nc}_s{idx}", n, c, A=A,
+                        b=np.concatenate([np.zeros(m1), np.ones(nc)]),
+                        repair=(grp_ptr, grp_idx), closure=(rep_var, rep_ptr, rep_idx))
+    else:
+        inst = Instance(f"facloc_nf{nf}_nc{nc}_s{idx}", n, c, A=A, b=np.zeros(m1),
+                        B=B, d=np.ones(nc), groups=(grp_ptr, grp_idx),
+                        closure=(rep_var, rep_ptr, rep_idx))
     inst.meta.update(nf=nf, nc=nc)
     return inst
 
