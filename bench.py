@@ -64,6 +64,13 @@ WORKLOADS = {
                     "(Thm. 5, cheapest facility of each customer as pivot: 9,991,000 "
                     "binaries, 5.0e7 nnz each, no equalities), 4 rounds x 256 Bernoulli "
                     "candidates/instance, k_int=50, plain proposal"),
+    "facility_relaxed": (lambda r: [__import__("paper_2510_27117_b300.workloads", fromlist=["x"])
+                                    .facility_location(1000, 10000, idx=16 * r + q, relaxed=True)
+                                    for q in range(16)], 50, 256,
+                         "16 facility-location instances 1000 x 10000 under the monotone "
+                         "relaxation (customer rows >= 1, Bernoulli draws, least-cost repair "
+                         "per customer, closure), 4 rounds x 256 candidates/instance, k_int=50, "
+                         "plain proposal"),
     "facility": (lambda r: [__import__("paper_2510_27117_b300.workloads", fromlist=["x"])
                             .facility_location(1000, 10000, idx=16 * r + q) for q in range(16)],
                  50, 256,
@@ -93,10 +100,10 @@ TU_SECONDS = [0.0]
 # rounds per step and proposal (0 plain x_k, 1 learned) of each workload
 ROUNDS = {"maxcut": 1, "maxcut_sparse": 1, "setcover": 1, "setcover_batch": 1, "knapsack": 1,
           "assign3d": 1,
-          "assign3d_alg4": 1, "facility": 4, "facility_tu": 4}
+          "assign3d_alg4": 1, "facility": 4, "facility_tu": 4, "facility_relaxed": 4}
 PROPOSAL = {"maxcut": 0, "maxcut_sparse": 0, "setcover": 0, "setcover_batch": 0, "knapsack": 0,
             "assign3d": 1,
-            "assign3d_alg4": 0, "facility": 1, "facility_tu": 0}
+            "assign3d_alg4": 0, "facility": 1, "facility_tu": 0, "facility_relaxed": 0}
 
 
 def env_rank():
@@ -408,7 +415,8 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False, pa
            "assign3d": (16 * nnz, "16 nnz"),
            "assign3d_alg4": (16 * nnz, "16 nnz"),
            "facility": (16 * nnz + 24 * n + 16 * m, "2 nnz 8 + 24 n + 16 m"),
-           "facility_tu": (16 * nnz + 24 * n + 16 * m, "2 nnz 8 + 24 n + 16 m")}[workload]
+           "facility_tu": (16 * nnz + 24 * n + 16 * m, "2 nnz 8 + 24 n + 16 m"),
+           "facility_relaxed": (16 * nnz + 24 * n + 16 * m, "2 nnz 8 + 24 n + 16 m")}[workload]
     lanes_peak = 148 * 128 * 2.032e9 / 15.0      # Philox output lanes/s (15 INT32 ops/lane)
     if dom == "pdhg":
         ms, iters = phases["pdhg"]

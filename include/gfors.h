@@ -178,6 +178,18 @@ GFORS_API gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t mo
 GFORS_API gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, int32_t I,
                                                  int32_t gamma, int32_t L);
 
+/* Monotone relaxation (Section 2.4.3), group repair for instance inst: the
+ * caller has relaxed equality groups sum_{k in G} x_k = 1 to sum >= 1 (rows
+ * of A; valid when costs are non-negative); after sampling, every candidate
+ * keeps, in each group, its selected member of least cost c_k (ties to the
+ * member listed first) and clears the others, before the closure below.
+ * Dropping a member must not be able to violate any other row (the caller's
+ * claim).  grp_ptr (ngroups + 1, grp_ptr[0] = 0) / grp_idx: disjoint groups
+ * of local variable indices.  Needs integral costs; GFORS_E_UNSUPPORTED on
+ * a dense-Q or fused single-row batch. */
+GFORS_API gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, int64_t ngroups,
+                                               const int64_t* grp_ptr, const int64_t* grp_idx);
+
 /* Monotone relaxation with repair (Section 2.4.3) for instance inst: after
  * sampling, rep_var[q] <- rep_var[q] OR (OR of rep_idx[rep_ptr[q] ..
  * rep_ptr[q+1])).  Valid when the repaired variables have non-negative

@@ -212,6 +212,38 @@ GF_DEV CSum i8_row_dot(const uint32_t* row, const float4* x4, int64_t nq, int la
 }
 
 // ---------------------------------------------------------------------------
+// 32 x 32 bit transpose across a warp: lane l holds word A_l; afterwards
+// lane b holds the word whose bit l is bit b of A_l.  Five block-swap
+// stages; in the stage of distance j a lane keeps its own bits outside the
+// mask M and takes its partner's word rotated by j (lower lane) or 32 - j
+// (upper lane) inside it.  The per-lane rotations and masks depend on the
+// lane only (TransposeLane, computed once).
+struct TransposeLane {
+  uint32_t rot[5], mask[5];
+};
+GF_DEV TransposeLane transpose_lane(int lane) {
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+  TransposeLane t;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const bool low = (lane & j) == 0;
+    t.rot[k] = low ? (uint32_t)j : (uint32_t)(32 - j);
+    t.mask[k] = low ? (m[k] << j) : m[k];
+  }
+  return t;
+}
+GF_DEV uint32_t warp_transpose32(uint32_t x, const TransposeLane& t) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, 16 >> k);
+    const uint32_t r = __funnelshift_l(y, y, t.rot[k]);
+    x = (x & ~t.mask[k]) | (r & t.mask[k]);
+  }
+  return x;
+}
+
+// ---------------------------------------------------------------------------
 // Time source for bounded device waits.
 // ---------------------------------------------------------------------------
 GF_DEV uint64_t globaltimer_ns() {

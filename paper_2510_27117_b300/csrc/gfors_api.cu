@@ -910,6 +910,43 @@ extern "C" gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, 
   return GFORS_OK;
 }
 
+extern "C" gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, int64_t ngroups,
+                                                const int64_t* grp_ptr, const int64_t* grp_idx) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  const GfInstHost& I = h->ih[inst];
+  if (ngroups <= 0) return GFORS_OK;
+  if (!grp_ptr || !grp_idx || grp_ptr[0] != 0) return gf_fail(h, GFORS_E_ARG, "bad group arrays");
+  if (I.qkind == 1 || h->fused_ok)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "repair groups on a dense / fused instance");
+  if (!I.integral) return gf_fail(h, GFORS_E_UNSUPPORTED, "repair groups need integral costs");
+  std::vector<uint8_t> seen(I.n, 0);
+  if (h->h_rg_ptr.empty()) h->h_rg_ptr.push_back(0);
+  const int64_t base = (int64_t)h->h_rg_idx.size();
+  for (int64_t g = 0; g < ngroups; ++g) {
+    if (grp_ptr[g + 1] < grp_ptr[g]) return gf_fail(h, GFORS_E_ARG, "group ptr not monotone");
+    for (int64_t t = grp_ptr[g]; t < grp_ptr[g + 1]; ++t) {
+      const int64_t v = grp_idx[t];
+      if (v < 0 || v >= I.n) return gf_fail(h, GFORS_E_ARG, "group index out of range");
+      if (seen[v]) return gf_fail(h, GFORS_E_ARG, "groups must be disjoint");
+      seen[v] = 1;
+      h->h_rg_idx.push_back(I.var_off + v);
+    }
+    h->h_rg_ptr.push_back(base + grp_ptr[g + 1]);
+  }
+  h->nrg = (int64_t)h->h_rg_ptr.size() - 1;
+  h->rg_ptr = gf_alloc_t<int64_t>(h, h->h_rg_ptr.size());
+  h->rg_idx = gf_alloc_t<int64_t>(h, std::max<size_t>(1, h->h_rg_idx.size()));
+  if (!h->rg_ptr || !h->rg_idx) return gf_fail(h, GFORS_E_OOM, "repair groups");
+  cudaError_t e;
+  if ((e = cudaMemcpy(h->rg_ptr, h->h_rg_ptr.data(), sizeof(int64_t) * h->h_rg_ptr.size(),
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->rg_idx, h->h_rg_idx.data(), sizeof(int64_t) * h->h_rg_idx.size(),
+                      cudaMemcpyHostToDevice)))
+    return gf_cuda(h, e, "repair group upload");
+  return GFORS_OK;
+}
+
 extern "C" gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t nrep,
                                           const int64_t* rep_var, const int64_t* rep_ptr,
                                           const int64_t* rep_idx) {

@@ -184,6 +184,11 @@ struct gfors_ctx {
   // 4-variable groups with a variable the Bernoulli sampler draws (any
   // variable not drawn by a group sampler, padding included), built on the
   // device when stale (n_bit_g4 < 0)
+  // monotone-relaxation repair groups (Section 2.4.3), global variable ids
+  std::vector<int64_t> h_rg_ptr, h_rg_idx;
+  int64_t* rg_ptr = nullptr;
+  int64_t* rg_idx = nullptr;
+  int64_t nrg = 0;
   int32_t* bit_g4 = nullptr;
   int32_t* bit_count = nullptr;
   int64_t n_bit_g4 = -1;

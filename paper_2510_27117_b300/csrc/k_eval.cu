@@ -247,37 +247,6 @@ k_eval_grows(const GfGRow* __restrict__ rows, int64_t nrows,
   add_violations(vmask, inst, w, chunk, viol, valid);
 }
 
-// 32 x 32 bit transpose across a warp: lane l holds word A_l; afterwards
-// lane b holds the word whose bit l is bit b of A_l.  Five block-swap
-// stages; in the stage of distance j a lane keeps its own bits outside the
-// mask M and takes its partner's word rotated by j (lower lane) or 32 - j
-// (upper lane) inside it.  The per-lane rotations and masks depend on the
-// lane only (TransposeLane, computed once).
-struct TransposeLane {
-  uint32_t rot[5], mask[5];
-};
-GF_DEV TransposeLane transpose_lane(int lane) {
-  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-  TransposeLane t;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int j = 16 >> k;
-    const bool low = (lane & j) == 0;
-    t.rot[k] = low ? (uint32_t)j : (uint32_t)(32 - j);
-    t.mask[k] = low ? (m[k] << j) : m[k];
-  }
-  return t;
-}
-GF_DEV uint32_t warp_transpose32(uint32_t x, const TransposeLane& t) {
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, 16 >> k);
-    const uint32_t r = __funnelshift_l(y, y, t.rot[k]);
-    x = (x & ~t.mask[k]) | (r & t.mask[k]);
-  }
-  return x;
-}
-
 constexpr int kQW = 4;
 
 // Weighted counts of a warp's 32 items for the 32 candidates of each of kQW
@@ -288,14 +257,14 @@ constexpr int kQW = 4;
 // bias popc(T).
 template <int P>
 GF_DEV void weighted_counts(const uint32_t (&m)[kQW], uint32_t u, long long bias, int nw,
-                            const TransposeLane& tl, long long (&acc)[kQW]) {
+                            const gf::TransposeLane& tl, long long (&acc)[kQW]) {
   uint32_t plane[P > 0 ? P : 1];
 #pragma unroll
   for (int q = 0; q < P; ++q) plane[q] = __ballot_sync(0xFFFFFFFFu, (u >> q) & 1u);
 #pragma unroll
   for (int k = 0; k < kQW; ++k) {
     if (k >= nw) break;
-    const uint32_t T = warp_transpose32(m[k], tl);
+    const uint32_t T = gf::warp_transpose32(m[k], tl);
     int sum = 0;                                 // <= 32 (2^P - 1) < 2^18
 #pragma unroll
     for (int q = 0; q < P; ++q) sum += __popc(T & plane[q]) * (1 << q);
@@ -325,7 +294,7 @@ GF_DEV void weighted_counts_sparse(const uint32_t (&m)[kQW], long long w, int nw
 // Bit-plane form for P <= 12 planes (uniform across the warp), else item by
 // item.
 GF_DEV void weighted_counts_p(int P, const uint32_t (&m)[kQW], long long w, long long bias,
-                              int nw, int lane, const TransposeLane& tl,
+                              int nw, int lane, const gf::TransposeLane& tl,
                               long long (&acc)[kQW]) {
   const uint32_t u = (uint32_t)(w + bias);
   switch (P) {
@@ -362,7 +331,7 @@ k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
   if (c >= nch) return;
   const GfObjChunk C = ch[c];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TransposeLane tl = transpose_lane(lane);
+  const gf::TransposeLane tl = gf::transpose_lane(lane);
   __shared__ long long red[8][kQW][32];
   for (int w0 = 0; w0 < kwu; w0 += kQW) {
     const int nw = min(kQW, kwu - w0);
@@ -424,7 +393,7 @@ k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int32_t* __rest
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = min(kQW, kwu - w0);
   const bool vec = (kws % 4) == 0 && nw == kQW;
-  const TransposeLane tl = transpose_lane(lane);
+  const gf::TransposeLane tl = gf::transpose_lane(lane);
   long long acc[kQW] = {0, 0, 0, 0};
   for (int pb = C.r0 + warp; pb < C.r1; pb += 8) {
     const int64_t t = (int64_t)pb * 32 + lane;

@@ -7,6 +7,54 @@
 
 namespace {
 
+// Repair after the monotone relaxation (Section 2.4.3): an equality group
+// relaxed to "sum >= 1" may hold several selected members; each candidate
+// keeps its selected member of least cost (ties to the member listed first).
+// One warp per (group, word): pass 1 transposes 32 members' words so that
+// lane b sees candidate b's selections among them and keeps the best; pass 2
+// transposes the chosen bits back and writes each member's word.
+__global__ void __launch_bounds__(256)
+k_repair_min(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi, int64_t ng,
+             const long long* __restrict__ cost, int kws, int kwu, uint32_t* __restrict__ X) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= ng * kwu) return;                       // whole warps
+  const int64_t g = wid / kwu;
+  const int w = (int)(wid % kwu);
+  const int64_t a = gp[g], e = gp[g + 1];
+  const gf::TransposeLane tl = gf::transpose_lane(lane);
+  long long bc = 0;
+  int64_t bt = -1;                                   // position of the kept member
+  for (int64_t t0 = a; t0 < e; t0 += 32) {
+    const int64_t t = t0 + lane;
+    const bool valid = t < e;
+    const int64_t m = valid ? gi[t] : 0;
+    const uint32_t word = valid ? X[m * kws + w] : 0u;
+    const long long c = valid ? cost[m] : 0;
+    unsigned any = __ballot_sync(0xFFFFFFFFu, word != 0u);
+    if (!any) continue;
+    const uint32_t T = gf::warp_transpose32(word, tl);
+    while (any) {
+      const int l = __ffs(any) - 1;
+      any &= any - 1;
+      const long long cl = __shfl_sync(0xFFFFFFFFu, c, l);
+      if (((T >> l) & 1u) && (bt < 0 || cl < bc)) {
+        bc = cl;
+        bt = t0 + l;
+      }
+    }
+  }
+  for (int64_t t0 = a; t0 < e; t0 += 32) {
+    const uint32_t mine = (bt >= t0 && bt < t0 + 32) ? (1u << (uint32_t)(bt - t0)) : 0u;
+    const uint32_t keep = gf::warp_transpose32(mine, tl);
+    const int64_t t = t0 + lane;
+    if (t < e) {
+      uint32_t* p = X + gi[t] * kws + w;
+      if (*p != keep) *p = keep;
+    }
+  }
+}
+
 // Indices of the 4-variable groups holding a variable that no group sampler
 // draws (order irrelevant: every entry writes its own words).
 __global__ void k_bit_list(const uint8_t* __restrict__ grouped, int64_t N4,
@@ -549,6 +597,13 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
     else
       k_axial<<<len, kAxThreads, 0, h->stream>>>(p, I.var_off, I.axial_I, b, s0, len, h->kw,
                                                  P.seed, P.inst_base, h->dstate, h->X);
+    h->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (h->nrg > 0) {
+    const int64_t warps = h->nrg * kw;
+    k_repair_min<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->rg_ptr, h->rg_idx, h->nrg, h->cint, h->kw, kw, h->X);
     h->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -65,6 +65,7 @@ _lib.gfors_load_batch.argtypes = [i32, _P(_P(Csr)), _P(vp), _P(_P(Csr)), _P(vp),
                                   _P(_P(QMat)), _P(vp), _P(i64), _P(Params), vp, _P(_H)]
 _lib.gfors_set_groups.argtypes = [_H, i32, i32, i64, vp, vp, i32]
 _lib.gfors_set_closure.argtypes = [_H, i32, i64, vp, vp, vp]
+_lib.gfors_set_repair_groups.argtypes = [_H, i32, i64, vp, vp]
 _lib.gfors_pdhg_steps.argtypes = [_H, i64]
 _lib.gfors_sample_eval.argtypes = [_H, i32, u32, i32]
 _lib.gfors_final_round.argtypes = [_H]
@@ -299,6 +300,11 @@ class Handle:
         _check(_lib.gfors_set_groups(self.h, inst, mode, ng, _ptr(gp), _ptr(gi), axial_I),
                self.h)
 
+    def set_repair_groups(self, inst, groups):
+        gp, gi = (np.ascontiguousarray(a, np.int64) for a in groups)
+        _check(_lib.gfors_set_repair_groups(self.h, inst, gp.size - 1, _ptr(gp), _ptr(gi)),
+               self.h)
+
     def set_closure(self, inst, closure):
         rv, rp, ri = (np.ascontiguousarray(a, np.int64) for a in closure)
         _check(_lib.gfors_set_closure(self.h, inst, rv.size, _ptr(rv), _ptr(rp), _ptr(ri)),
@@ -409,6 +415,8 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
                 H.set_groups(q, 2, None, I.axial_I)
             elif I.groups is not None:
                 H.set_groups(q, 1, I.groups)
+            if getattr(I, "repair", None) is not None:
+                H.set_repair_groups(q, I.repair)
             if I.closure is not None:
                 H.set_closure(q, I.closure)
     return H

@@ -35,6 +35,8 @@ CASES = {
     "maxcut_sparse": lambda: W.max_cut_sparse(n=3000, avg_deg=12.0, idx=1),
     "assign3d": lambda: W.assign3d(I=8, idx=1),
     "facloc": lambda: W.facility_location(nf=12, nc=40, idx=2),
+    # the monotone relaxation: customer rows >= 1, Bernoulli draws, repair
+    "facloc_rel": lambda: W.facility_location(nf=12, nc=40, idx=2, relaxed=True),
     # the same shape after the library's TU reformulation (Thm. 5)
     "facloc_tu": lambda: G.tu_reformulate(
         W.facility_location(nf=12, nc=40, idx=2),
@@ -115,7 +117,8 @@ def test_pdhg_single_step(name, mode):
 @pytest.mark.parametrize("name,mode", [("setcover", 0), ("knapsack", 1), ("knapsack", 2),
                                        ("tiny", 0), ("maxcut", 0), ("assign3d", 0),
                                        ("facloc", 0), ("maxcut_csr", 0),
-                                       ("maxcut_sparse", 0), ("facloc_tu", 0)])
+                                       ("maxcut_sparse", 0), ("facloc_tu", 0),
+                                       ("facloc_rel", 0)])
 def test_sampling_and_evaluation_bit_exact(name, mode):
     inst = CASES[name]()
     gp, op = _params(eval_mode=mode, k_b=96 if name != "maxcut" else 128)
@@ -478,3 +481,25 @@ def test_tu_incumbent_maps_back():
     X = tu.recover(inc["x"][None, :])
     v, o = O.Evaluator(inst)(X)
     assert v[0] == 0 and o[0] == inc["obj"] + int(tu.c0)
+
+
+@pytest.mark.parametrize("k_b", [96, 2048])
+def test_repair_groups_bit_exact(k_b):
+    """Monotone-relaxation repair on the device against the oracle: groups
+    longer than a warp (nf = 70), dense draws (p near 1) so that many members
+    compete, and a candidate count that leaves a partial word."""
+    inst = W.facility_location(nf=70, nc=9, idx=4, relaxed=True)
+    gp, op = _params(k_b=k_b)
+    H = G.load(inst, gp)
+    rng = np.random.default_rng(k_b)
+    p = (0.5 + 0.5 * rng.random(inst.n)).astype(np.float32)
+    H.set_iterate(0, p, p, None)
+    H.sample_eval(1, 3, 0)
+    X, viol, obj = H.get_samples(0)
+    H.destroy()
+    Xo = O.sample(inst, p, k_b, op.seed, 0, 3)
+    assert np.array_equal(X, Xo)
+    vo, oo = O.Evaluator(inst)(Xo)
+    assert np.array_equal(viol, vo) and np.array_equal(obj, oo)
+    # every customer keeps at most one facility
+    assert X[:, 70:].reshape(k_b, 9, 70).sum(-1).max() <= 1
