@@ -403,11 +403,12 @@ GFORS_API gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t ou
 
 /* ---- TU reformulation (Thm. 5, Section 2.4.1), host only, no GPU needed.
  * Removes the equality rows J of B by x_I = s + S x_Ibar (s = B_JI^-1 d_J,
- * S = -B_JI^-1 B_JIbar) for the case in which B_JI is a signed permutation:
- * every row J[k] has exactly one entry, +1 or -1, in the columns I, and
- * every column of I has its entry in exactly one of those rows (I[k] need
- * not be the pivot of J[k]).  The new problem is over x_Ibar, Ibar = the
- * other columns in ascending order:
+ * S = -B_JI^-1 B_JIbar).  A signed-permutation B_JI (every row J[k] has
+ * exactly one entry +-1 in the columns I, every column of I has its entry in
+ * exactly one of those rows) is used directly; any other B_JI is inverted by
+ * Gauss-Jordan elimination in exact integer arithmetic, S stored explicitly.
+ * The new problem is over x_Ibar, Ibar = the other columns in ascending
+ * order:
  *   A' = [A_.I S + A_.Ibar; S; -S],  b' = [b - A_.I s; -s; s - 1] (a
  *   bounds row that every x in [0, 1] satisfies is left out),
  *   B' = B_JbarI S + B_JbarIbar (rows of B outside J, ascending),
@@ -419,8 +420,10 @@ GFORS_API gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t ou
  * gfors_tu_reformulate: n, A, b, B, d, Q, c as in gfors_load (A, Q may be
  *   NULL); J, I: nJ row / column indices.  *out receives an object owned by
  *   the caller (gfors_tu_free).  GFORS_E_ARG for malformed input or
- *   repeated / out-of-range indices, GFORS_E_UNSUPPORTED when B_JI is not a
- *   signed permutation (the LU form of a general B_JI is not built).
+ *   repeated / out-of-range indices, a singular B_JI or non-integral B_J,
+ *   d_J; GFORS_E_UNSUPPORTED when the elimination meets a pivot other than
+ *   +-1 or an entry outside {-1, 0, 1} (B_J not TU) or S would exceed 2^28
+ *   entries (the paper keeps an LU factor instead; not built).
  * gfors_tu_sizes: out[0] = n', out[1] = rows of A', out[2] = nnz(A'),
  *   out[3] = rows of B', out[4] = nnz(B'), out[5] = 1 if Q' exists,
  *   out[6] = nnz(Q'), out[7] = |I|.

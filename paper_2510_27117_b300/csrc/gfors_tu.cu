@@ -1,13 +1,17 @@
-// gfors_tu.cu -- TU reformulation (Thm. 5, Section 2.4.1) on the host, for
-// the case in which B_JI is a signed permutation: every row j of J has
-// exactly one entry, +1 or -1, in the columns I, and every column of I has
-// its entry in exactly one row of J.  Then B_JI^-1 is the transposed signed
-// permutation, and for the row j whose pivot is I_k (sign sigma)
+// gfors_tu.cu -- TU reformulation (Thm. 5, Section 2.4.1) on the host.
+// When B_JI is a signed permutation (every row j of J has exactly one entry,
+// +1 or -1, in the columns I, and every column of I has its entry in exactly
+// one row of J), B_JI^-1 is the transposed permutation and for the row j
+// whose pivot is I_k (sign sigma)
 //
 //   x_{I_k} = s_k + S_k x_Ibar,   s_k = sigma d_j,   S_k = -sigma B_{j,Ibar},
 //
-// so S is as sparse as B_JIbar (the paper's remark keeps an LU factor of a
-// general B_JI instead; that form is not built here).  The new problem over
+// so S is as sparse as B_JIbar.  Any other invertible B_JI goes through
+// Gauss-Jordan elimination of the rows J on the columns I in exact integer
+// arithmetic (every pivot is +-1 and every entry stays in {-1, 0, 1} when
+// B_J is totally unimodular), and S is stored explicitly (the paper's remark
+// keeps an LU factor instead, to save memory when S fills in; here a fill
+// above 2^28 entries is reported as unsupported).  The new problem over
 // x_Ibar (Ibar ascending) is
 //
 //   Q'  = S^T Q_II S + S^T Q_IIbar + Q_IbarI S + Q_IbarIbar
@@ -20,7 +24,8 @@
 // Q is used as given (not symmetrised), so integral data stay integral.  The
 // theorem needs B_J to be totally unimodular; that is the caller's claim.
 #include <algorithm>
-#include <unordered_map>
+#include <climits>
+#include <cmath>
 #include <vector>
 
 #include "internal.cuh"
@@ -111,11 +116,12 @@ extern "C" gfors_status gfors_tu_reformulate(int64_t n, const gfors_csr* A, cons
       t->Ibar.push_back(i);
     }
   t->nbar = (int64_t)t->Ibar.size();
-  // B_JI must be a signed permutation: row J[k] has one pivot entry +-1
-  // (in any column of I); pivot of row J[k] is matched to the column it hits
+  // Fast path: B_JI a signed permutation (row J[k] has one entry +-1 in
+  // the columns I, every column of I in exactly one of those rows).
   std::vector<int64_t> row_of_pivot(nJ, -1);
   std::vector<double> sigma(nJ, 0.0);
-  for (int64_t k = 0; k < nJ; ++k) {
+  bool perm = true;
+  for (int64_t k = 0; k < nJ && perm; ++k) {
     const int64_t j = J[k];
     int hits = 0;
     for (int64_t u = B->row_ptr[j]; u < B->row_ptr[j + 1]; ++u) {
@@ -127,22 +133,133 @@ extern "C" gfors_status gfors_tu_reformulate(int64_t n, const gfors_csr* A, cons
       row_of_pivot[kk] = j;
       sigma[kk] = B->val[u];
     }
-    if (hits != 1) {
-      delete t;
-      return GFORS_E_UNSUPPORTED;       // B_JI is not a signed permutation
-    }
+    perm = hits == 1;
   }
-  // s and S (row k of S belongs to pivot column I[k])
   t->s.assign(nJ, 0.0);
-  for (int64_t k = 0; k < nJ; ++k) {
-    const int64_t j = row_of_pivot[k];
-    t->s[k] = sigma[k] * d[j];
-    std::vector<std::pair<int32_t, double>> e;
-    for (int64_t u = B->row_ptr[j]; u < B->row_ptr[j + 1]; ++u) {
-      const int64_t p = t->pos[B->col_idx[u]];
-      if (p >= 0) e.emplace_back((int32_t)p, -sigma[k] * B->val[u]);
+  if (perm) {
+    // s and S (row k of S belongs to pivot column I[k])
+    for (int64_t k = 0; k < nJ; ++k) {
+      const int64_t j = row_of_pivot[k];
+      t->s[k] = sigma[k] * d[j];
+      std::vector<std::pair<int32_t, double>> e;
+      for (int64_t u = B->row_ptr[j]; u < B->row_ptr[j + 1]; ++u) {
+        const int64_t p = t->pos[B->col_idx[u]];
+        if (p >= 0) e.emplace_back((int32_t)p, -sigma[k] * B->val[u]);
+      }
+      t->S.add_row(e);
     }
-    t->S.add_row(e);
+  } else {
+    // General B_JI: Gauss-Jordan elimination of the rows J on the pivot
+    // columns I in exact integer arithmetic.  For a totally unimodular B_J
+    // every pivot is +-1 and every entry stays in {-1, 0, 1}; a pivot of
+    // another size means B_J is not TU (unsupported), a missing one that
+    // B_JI is singular (bad argument).  Columns are kept in one index space:
+    // pivot k as -1 - k, Ibar columns as their position.
+    typedef std::vector<std::pair<int64_t, long long>> Row;   // sorted by key
+    std::vector<Row> R(nJ);
+    std::vector<long long> rhs(nJ);
+    std::vector<std::vector<int64_t>> rows_with(nJ);     // pivot k -> rows holding it
+    for (int64_t r = 0; r < nJ; ++r) {
+      const int64_t j = J[r];
+      for (int64_t u = B->row_ptr[j]; u < B->row_ptr[j + 1]; ++u) {
+        const double v = B->val[u];
+        if (v == 0.0) continue;
+        if (v != std::floor(v) || std::fabs(v) > 1e15 || d[j] != std::floor(d[j])) {
+          delete t;
+          return GFORS_E_ARG;                       // B_J, d_J must be integral
+        }
+        R[r].emplace_back(t->pos[B->col_idx[u]], (long long)v);
+      }
+      std::sort(R[r].begin(), R[r].end());
+      // merge duplicates
+      Row m;
+      for (const auto& e2 : R[r]) {
+        if (!m.empty() && m.back().first == e2.first) m.back().second += e2.second;
+        else m.push_back(e2);
+      }
+      m.erase(std::remove_if(m.begin(), m.end(), [](const std::pair<int64_t, long long>& e2) {
+                return e2.second == 0;
+              }), m.end());
+      R[r].swap(m);
+      rhs[r] = (long long)d[j];
+      for (const auto& e2 : R[r])
+        if (e2.first < 0) rows_with[-1 - e2.first].push_back(r);
+    }
+    auto coef = [](const Row& row, int64_t kk) -> long long {
+      auto it = std::lower_bound(row.begin(), row.end(), std::make_pair(kk, LLONG_MIN));
+      return (it != row.end() && it->first == kk) ? it->second : 0;
+    };
+    std::vector<int64_t> piv_row(nJ, -1);
+    std::vector<uint8_t> used(nJ, 0);
+    int64_t fill = 0;
+    for (int64_t r = 0; r < nJ; ++r) fill += (int64_t)R[r].size();
+    for (int64_t k = 0; k < nJ; ++k) {
+      const int64_t kk = -1 - k;
+      int64_t pr = -1;
+      for (int64_t r : rows_with[k])
+        if (!used[r] && coef(R[r], kk) != 0) { pr = r; break; }
+      if (pr < 0) {
+        delete t;
+        return GFORS_E_ARG;                         // B_JI singular
+      }
+      const long long pv = coef(R[pr], kk);
+      if (pv != 1 && pv != -1) {
+        delete t;
+        return GFORS_E_UNSUPPORTED;                 // B_J not totally unimodular
+      }
+      used[pr] = 1;
+      piv_row[k] = pr;
+      if (pv == -1) {
+        for (auto& e2 : R[pr]) e2.second = -e2.second;
+        rhs[pr] = -rhs[pr];
+      }
+      // eliminate pivot k from every other row that holds it
+      const std::vector<int64_t> holders = rows_with[k];
+      for (int64_t r : holders) {
+        if (r == pr) continue;
+        const long long f = coef(R[r], kk);
+        if (f == 0) continue;
+        Row out;
+        out.reserve(R[r].size() + R[pr].size());
+        size_t a1 = 0, b1 = 0;
+        while (a1 < R[r].size() || b1 < R[pr].size()) {
+          if (b1 == R[pr].size() || (a1 < R[r].size() && R[r][a1].first < R[pr][b1].first)) {
+            out.push_back(R[r][a1++]);
+          } else if (a1 == R[r].size() || R[pr][b1].first < R[r][a1].first) {
+            const long long v = -f * R[pr][b1].second;
+            const int64_t c2 = R[pr][b1++].first;
+            out.emplace_back(c2, v);
+            if (c2 < 0) rows_with[-1 - c2].push_back(r);
+          } else {
+            const long long v = R[r][a1].second - f * R[pr][b1].second;
+            if (v != 0) out.emplace_back(R[r][a1].first, v);
+            ++a1;
+            ++b1;
+          }
+        }
+        for (const auto& e2 : out)
+          if (e2.second > 1 || e2.second < -1) {
+            delete t;
+            return GFORS_E_UNSUPPORTED;             // B_J not totally unimodular
+          }
+        fill += (int64_t)out.size() - (int64_t)R[r].size();
+        R[r].swap(out);
+        rhs[r] -= f * rhs[pr];
+      }
+      if (fill > (1ll << 28)) {
+        delete t;
+        return GFORS_E_UNSUPPORTED;                 // S too dense to hold
+      }
+    }
+    // row piv_row[k] now reads x_{I_k} + sum_Ibar a x = rhs
+    for (int64_t k = 0; k < nJ; ++k) {
+      const int64_t r = piv_row[k];
+      t->s[k] = (double)rhs[r];
+      std::vector<std::pair<int32_t, double>> e;
+      for (const auto& e2 : R[r])
+        if (e2.first >= 0) e.emplace_back((int32_t)e2.first, -(double)e2.second);
+      t->S.add_row(e);
+    }
   }
   auto add_srow = [&](std::vector<std::pair<int32_t, double>>& e, int64_t k, double a) {
     for (int64_t u = t->S.ptr[k]; u < t->S.ptr[k + 1]; ++u)

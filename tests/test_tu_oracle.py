@@ -158,9 +158,39 @@ def test_library_tu_matches_oracle_quadratic(idx):
     assert L.meta["tu_c0"] == info["c0"]
 
 
-def test_library_tu_general_pivots_unsupported():
+def _spanning_tree(n):
+    """Rows J: all n row sums and the first n-1 column sums of the n x n
+    assignment; columns I: x_0j for every j and x_i0 for i >= 1 (a spanning
+    tree of the bipartite graph, B_JI invertible, not a permutation)."""
+    J = list(range(2 * n - 1))
+    I = [j for j in range(n)] + [i * n for i in range(1, n)]
+    return J, I
+
+
+@pytest.mark.parametrize("n,idx", [(3, 0), (3, 1), (6, 2), (9, 3)])
+def test_library_tu_general_pivots_match_oracle(n, idx):
+    """A general B_JI goes through exact Gauss-Jordan elimination and gives
+    the oracle's reformulation entry by entry."""
     from paper_2510_27117_b300 import gfors as G
-    inst = _assignment2d(3, 0)
+    inst = _assignment2d(n, idx)
+    J, I = _spanning_tree(n)
+    L, t = G.tu_reformulate(inst, J, I)
+    R, info = T.tu_reformulate(inst, J, I)
+    _same_problem(L, R)
+    assert L.meta["tu_c0"] == info["c0"]
+
+
+def test_library_tu_rejects_non_tu_and_singular():
+    from paper_2510_27117_b300 import gfors as G
+    # a 2 x 2 block with determinant 2 on the pivot columns: not TU
+    Bd = np.array([[1.0, 1.0, 0.0, 1.0], [1.0, -1.0, 1.0, 0.0]])
+    inst = W.Instance("nontu", 4, np.ones(4), B=sp.csr_matrix(Bd), d=np.array([1.0, 0.0]))
     with pytest.raises(G.GforsError) as e:
-        G.tu_reformulate(inst, [0, 1, 2, 3, 4], [0, 1, 2, 3, 6])
+        G.tu_reformulate(inst, [0, 1], [0, 1])
     assert e.value.status == 6                      # GFORS_E_UNSUPPORTED
+    # two equal rows on the pivot columns: B_JI singular
+    Bd = np.array([[1.0, 1.0, 1.0, 0.0], [1.0, 1.0, 0.0, 1.0]])
+    inst = W.Instance("sing", 4, np.ones(4), B=sp.csr_matrix(Bd), d=np.array([1.0, 1.0]))
+    with pytest.raises(G.GforsError) as e:
+        G.tu_reformulate(inst, [0, 1], [0, 1])
+    assert e.value.status == 1                      # GFORS_E_ARG
