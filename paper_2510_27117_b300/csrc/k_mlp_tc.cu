@@ -161,23 +161,29 @@ k_mlp_fwd_tc(const float* __restrict__ W, int64_t nv, const float* __restrict__ 
   const int64_t ntiles = (nv + TM - 1) / TM;
   int j = 0;                                  // tiles done by this CTA
   int issued = 0;                             // commits issued (MMA warp)
+  // features of the next tile, loaded one tile ahead by warps 0-3 so that
+  // their global-memory latency overlaps the current tile
+  float4 fn0 = make_float4(0.f, 0.f, 0.f, 0.f), fn1 = fn0;
+  auto load_feat = [&](int64_t tile) {
+    const int64_t v = tile * TM + threadIdx.x;
+    if (tile < ntiles && v < nv) {
+      fn0 = __ldg(reinterpret_cast<const float4*>(feat + v * kF));
+      fn1 = __ldg(reinterpret_cast<const float4*>(feat + v * kF) + 1);
+    } else {
+      fn0 = fn1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (warp < 4) load_feat(blockIdx.x);
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
     const uint32_t ph = (uint32_t)j & 1u;
     const int qq = warp & 3, half = warp >> 2;  // TMEM lane quarter, hidden-unit half
     if (warp < 4) {
       // ---- features -> three bf16 pieces at K = 0, 16, 32 of A1
       const int r = threadIdx.x;
-      const int64_t v = t * TM + r;
       float f[kF];
-      if (v < nv) {
-        const float4 f0 = __ldg(reinterpret_cast<const float4*>(feat + v * kF));
-        const float4 f1 = __ldg(reinterpret_cast<const float4*>(feat + v * kF) + 1);
-        f[0] = f0.x; f[1] = f0.y; f[2] = f0.z; f[3] = f0.w;
-        f[4] = f1.x; f[5] = f1.y; f[6] = f1.z; f[7] = f1.w;
-      } else {
-#pragma unroll
-        for (int q = 0; q < kF; ++q) f[q] = 0.0f;
-      }
+      f[0] = fn0.x; f[1] = fn0.y; f[2] = fn0.z; f[3] = fn0.w;
+      f[4] = fn1.x; f[5] = fn1.y; f[6] = fn1.z; f[7] = fn1.w;
+      load_feat(t + gridDim.x);
       // the three pieces share one panel: hi at K 0, mid at K 16, lo at K 32
       {
         uint32_t hi[4], mid[4], lo[4];
