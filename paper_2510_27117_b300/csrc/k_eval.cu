@@ -450,16 +450,25 @@ k_fused_single_row(const int32_t* __restrict__ blk, const uint32_t* __restrict__
   const gf::PhiloxKeys K = gf::philox_keys(seed);
   const uint32_t c3 = ((uint32_t)(inst_base + b) & 0x0FFFFFFFu) | (gf::kStreamBern << 28);
   Acc rs = 0, ob = 0;                      // int32 when every sum provably fits
-  for (int v = v0; v < v1; v += 4) {
-    const uint4 t = *reinterpret_cast<const uint4*>(thr + v);
-    const int4 ww = *reinterpret_cast<const int4*>(wrow + v);
-    const uint4 u = gf::philox_k(make_uint4((uint32_t)((v - off) >> 2), s, round, c3), K);
-    const bool b0 = (u.x >> 8) < t.x, b1 = (u.y >> 8) < t.y;
-    const bool b2 = (u.z >> 8) < t.z, b3 = (u.w >> 8) < t.w;
-    rs += (b0 ? ww.x : 0) + (b1 ? ww.y : 0) + (b2 ? ww.z : 0) + (b3 ? ww.w : 0);
+  // pointers advance by increments (no per-load index multiply), and the
+  // selected terms are masked in with logic ops: the integer multiply pipe
+  // is left to the generator, which bounds this kernel
+  const uint4* tp = reinterpret_cast<const uint4*>(thr + v0);
+  const int4* wp = reinterpret_cast<const int4*>(wrow + v0);
+  // (the int64 form reads cint instead; cp then walks wrow unused)
+  const int4* cp = reinterpret_cast<const int4*>((sizeof(Acc) == 4 ? c32 : wrow) + v0);
+  uint32_t q4 = (uint32_t)((v0 - off) >> 2);
+  for (int v = v0; v < v1; v += 4, ++tp, ++wp, ++cp, ++q4) {
+    const uint4 t = *tp;
+    const int4 ww = *wp;
+    const uint4 u = gf::philox_k(make_uint4(q4, s, round, c3), K);
+    const int m0 = -(int)((u.x >> 8) < t.x), m1 = -(int)((u.y >> 8) < t.y);
+    const int m2 = -(int)((u.z >> 8) < t.z), m3 = -(int)((u.w >> 8) < t.w);
+    const bool b0 = m0 != 0, b1 = m1 != 0, b2 = m2 != 0, b3 = m3 != 0;
+    rs += (ww.x & m0) + (ww.y & m1) + (ww.z & m2) + (ww.w & m3);
     if constexpr (sizeof(Acc) == 4) {
-      const int4 cc = *reinterpret_cast<const int4*>(c32 + v);
-      ob += (b0 ? cc.x : 0) + (b1 ? cc.y : 0) + (b2 ? cc.z : 0) + (b3 ? cc.w : 0);
+      const int4 cc = *cp;
+      ob += (cc.x & m0) + (cc.y & m1) + (cc.z & m2) + (cc.w & m3);
     } else {
       if (b0) ob += cint[v];
       if (b1) ob += cint[v + 1];
