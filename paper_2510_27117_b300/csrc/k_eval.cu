@@ -429,10 +429,14 @@ k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int32_t* __rest
 }
 
 // Fused sampling + evaluation for single-row instances (knapsack form
-// -w^T x >= -cap): one thread per candidate, 128 candidates per block, the
-// block walks a slice [v0, v1) of one instance's variables four at a time
-// (one Philox call per four Bernoulli draws), accumulating the row sum and
-// the objective in int64; nothing is materialised.
+// -w^T x >= -cap): a thread takes kFusedCpt candidates (128 threads, 128 kFusedCpt
+// candidates per block), the block walks a slice [v0, v1) of one instance's
+// variables four at a time (one Philox call per four Bernoulli draws of one
+// candidate; the thresholds and row data are loaded once for all of a
+// thread's candidates), accumulating the row sum and the objective;
+// nothing is materialised.
+constexpr int kFusedCpt = 2;
+
 template <typename Acc>
 __global__ void __launch_bounds__(128)
 k_fused_single_row(const int32_t* __restrict__ blk, const uint32_t* __restrict__ thr,
@@ -442,14 +446,22 @@ k_fused_single_row(const int32_t* __restrict__ blk, const uint32_t* __restrict__
                    const GfDState* __restrict__ st, long long* __restrict__ fsum,
                    long long* __restrict__ obj) {
   const int b = blk[3 * blockIdx.x], v0 = blk[3 * blockIdx.x + 1], v1 = blk[3 * blockIdx.x + 2];
-  const int sidx = blockIdx.y * 128 + threadIdx.x;
-  if (sidx >= len) return;
-  const uint32_t s = (uint32_t)(s0 + sidx);
+  const int sbase = blockIdx.y * (128 * kFusedCpt) + threadIdx.x;
+  if (sbase >= len) return;
+  uint32_t s[kFusedCpt];
+  bool on[kFusedCpt];
+#pragma unroll
+  for (int q = 0; q < kFusedCpt; ++q) {
+    on[q] = sbase + 128 * q < len;
+    s[q] = (uint32_t)(s0 + sbase + 128 * q);
+  }
   const uint32_t round = st->round_id;
   const int64_t off = var_off[b];
   const gf::PhiloxKeys K = gf::philox_keys(seed);
   const uint32_t c3 = ((uint32_t)(inst_base + b) & 0x0FFFFFFFu) | (gf::kStreamBern << 28);
-  Acc rs = 0, ob = 0;                      // int32 when every sum provably fits
+  Acc rs[kFusedCpt], ob[kFusedCpt];       // int32 when every sum provably fits
+#pragma unroll
+  for (int q = 0; q < kFusedCpt; ++q) rs[q] = ob[q] = 0;
   // pointers advance by increments (no per-load index multiply), and the
   // selected terms are masked in with logic ops: the integer multiply pipe
   // is left to the generator, which bounds this kernel
@@ -461,25 +473,34 @@ k_fused_single_row(const int32_t* __restrict__ blk, const uint32_t* __restrict__
   for (int v = v0; v < v1; v += 4, ++tp, ++wp, ++cp, ++q4) {
     const uint4 t = *tp;
     const int4 ww = *wp;
-    const uint4 u = gf::philox_k(make_uint4(q4, s, round, c3), K);
-    const int m0 = -(int)((u.x >> 8) < t.x), m1 = -(int)((u.y >> 8) < t.y);
-    const int m2 = -(int)((u.z >> 8) < t.z), m3 = -(int)((u.w >> 8) < t.w);
-    const bool b0 = m0 != 0, b1 = m1 != 0, b2 = m2 != 0, b3 = m3 != 0;
-    rs += (ww.x & m0) + (ww.y & m1) + (ww.z & m2) + (ww.w & m3);
-    if constexpr (sizeof(Acc) == 4) {
-      const int4 cc = *cp;
-      ob += (cc.x & m0) + (cc.y & m1) + (cc.z & m2) + (cc.w & m3);
-    } else {
-      if (b0) ob += cint[v];
-      if (b1) ob += cint[v + 1];
-      if (b2) ob += cint[v + 2];
-      if (b3) ob += cint[v + 3];
+    int4 cc = make_int4(0, 0, 0, 0);
+    if constexpr (sizeof(Acc) == 4) cc = *cp;
+#pragma unroll
+    for (int q = 0; q < kFusedCpt; ++q) {
+      if (!on[q]) continue;                      // warp-uniform (len: whole words)
+      const uint4 u = gf::philox_k(make_uint4(q4, s[q], round, c3), K);
+      const int m0 = -(int)((u.x >> 8) < t.x), m1 = -(int)((u.y >> 8) < t.y);
+      const int m2 = -(int)((u.z >> 8) < t.z), m3 = -(int)((u.w >> 8) < t.w);
+      rs[q] += (ww.x & m0) + (ww.y & m1) + (ww.z & m2) + (ww.w & m3);
+      if constexpr (sizeof(Acc) == 4) {
+        ob[q] += (cc.x & m0) + (cc.y & m1) + (cc.z & m2) + (cc.w & m3);
+      } else {
+        if (m0) ob[q] += cint[v];
+        if (m1) ob[q] += cint[v + 1];
+        if (m2) ob[q] += cint[v + 2];
+        if (m3) ob[q] += cint[v + 3];
+      }
     }
   }
-  atomicAdd(reinterpret_cast<unsigned long long*>(&fsum[(int64_t)b * chunk + sidx]),
-            (unsigned long long)(long long)rs);
-  atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)b * chunk + sidx]),
-            (unsigned long long)(long long)ob);
+#pragma unroll
+  for (int q = 0; q < kFusedCpt; ++q) {
+    if (!on[q]) continue;
+    const int sidx = sbase + 128 * q;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&fsum[(int64_t)b * chunk + sidx]),
+              (unsigned long long)(long long)rs[q]);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&obj[(int64_t)b * chunk + sidx]),
+              (unsigned long long)(long long)ob[q]);
+  }
 }
 
 // Thresholds floor(p 2^24) of every variable (0 for padding), once per chunk.
@@ -663,7 +684,7 @@ cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len) {
     return e;
   if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
     return e;
-  dim3 grid((unsigned)h->nfblk, (unsigned)((len + 127) / 128));
+  dim3 grid((unsigned)h->nfblk, (unsigned)((len + 128 * kFusedCpt - 1) / (128 * kFusedCpt)));
   k_thresholds_all<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(p, h->var_live, h->N,
                                                                            h->fthr);
   if (h->f_c32)
