@@ -435,7 +435,7 @@ k_eval_obj_q(const GfQChunk* __restrict__ ch, int64_t nch, const int32_t* __rest
 // candidate; the thresholds and row data are loaded once for all of a
 // thread's candidates), accumulating the row sum and the objective;
 // nothing is materialised.
-constexpr int kFusedCpt = 2;
+constexpr int kFusedCpt = 4;
 
 template <typename Acc>
 __global__ void __launch_bounds__(128)
