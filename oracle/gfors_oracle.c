@@ -305,16 +305,23 @@ static uint32_t prob_threshold(float p) {
   return (uint32_t)floor((double)p * 16777216.0);
 }
 
+/* Candidates first .. first+k-1 of a round (row s - first of X). */
+void orc_bernoulli_from(int64_t n, int32_t first, int32_t k, const float* p, uint64_t seed,
+                        uint32_t inst, uint32_t round_id, const uint8_t* mask,
+                        uint8_t* X) {
+  for (int32_t r = 0; r < k; ++r)
+    for (int64_t i = 0; i < n; ++i) {
+      if (mask && mask[i]) continue;
+      uint32_t u = orc_philox_lane(seed, 0u, inst, round_id, (uint32_t)(first + r),
+                                   (uint64_t)i);
+      X[(int64_t)r * n + i] = ((u >> 8) < prob_threshold(p[i])) ? 1 : 0;
+    }
+}
+
 void orc_bernoulli(int64_t n, int32_t k, const float* p, uint64_t seed,
                    uint32_t inst, uint32_t round_id, const uint8_t* mask,
                    uint8_t* X) {
-  for (int32_t s = 0; s < k; ++s)
-    for (int64_t i = 0; i < n; ++i) {
-      if (mask && mask[i]) continue;
-      uint32_t u = orc_philox_lane(seed, 0u, inst, round_id, (uint32_t)s,
-                                   (uint64_t)i);
-      X[(int64_t)s * n + i] = ((u >> 8) < prob_threshold(p[i])) ? 1 : 0;
-    }
+  orc_bernoulli_from(n, 0, k, p, seed, inst, round_id, mask, X);
 }
 
 /* Categorical pick over a list of candidate variables (customized sampling,

@@ -46,6 +46,7 @@ def lib():
         L.orc_philox_lane.argtypes = [u64, u32, u32, u32, u32, u64]
         L.orc_philox_lane.restype = u32
         L.orc_repair_min.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
+        L.orc_bernoulli_from.argtypes = [i64, i32, i32, F32P, u64, u32, u32, VP, U8P]
         L.orc_philox_lanes.argtypes = [u64, u32, u32, u32, u32, i64, U32P]
         L.orc_row_normalize.argtypes = [i64, i64, I64P, F64P, F64P, F64P]
         L.orc_row_normalize.restype = i64
@@ -114,12 +115,13 @@ def philox_lanes(seed, stream, inst, round_id, s, count):
     return out
 
 
-def bernoulli(p32, k, seed, inst, round_id, mask=None):
+def bernoulli(p32, k, seed, inst, round_id, mask=None, first=0):
+    """Bernoulli draws of candidates first .. first+k-1 of a round (Alg. 3)."""
     p32 = np.ascontiguousarray(p32, np.float32)
     n = p32.size
     X = np.zeros((k, n), np.uint8)
     m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
-    lib().orc_bernoulli(n, k, p32, seed, inst, round_id, _ptr(m), X)
+    lib().orc_bernoulli_from(n, first, k, p32, seed, inst, round_id, _ptr(m), X)
     return X
 
 
