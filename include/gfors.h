@@ -473,6 +473,21 @@ GFORS_API gfors_status gfors_pdhg_path(gfors_handle h, int32_t* path);
 GFORS_API gfors_status gfors_sample_eval_range(gfors_handle h, int32_t nrounds,
                                                uint32_t first_round_id, int32_t proposal,
                                                int32_t s_begin, int32_t s_end);
+/* ---- Asynchronous host I/O (serving loops: one synchronisation per batch
+ * of steps instead of one per call).
+ * gfors_set_iterate_async: as gfors_set_iterate, but only enqueued on the
+ *   handle's stream; the host arrays must stay valid and unchanged until the
+ *   stream has passed the copies (pinned memory makes them asynchronous).
+ * gfors_incumbent_async: enqueues the copy of instance inst's incumbent key
+ *   (objective, round id, candidate index; all INT64_MAX when none) into
+ *   key_host[3] (host memory, pinned for asynchrony); valid after
+ *   gfors_synchronize or any synchronisation of the stream.
+ * gfors_synchronize: waits for everything enqueued on the handle's stream. */
+GFORS_API gfors_status gfors_set_iterate_async(gfors_handle h, int32_t inst, const float* x,
+                                               const float* xbar, const float* y);
+GFORS_API gfors_status gfors_incumbent_async(gfors_handle h, int32_t inst, int64_t* key_host);
+GFORS_API gfors_status gfors_synchronize(gfors_handle h);
+
 /* Incumbent key of instance inst -- (objective, round id, candidate index);
  * all three INT64_MAX when none was found -- written to key_dev[3] (DEVICE
  * memory, caller-owned), enqueued on the handle's stream (asynchronous), for

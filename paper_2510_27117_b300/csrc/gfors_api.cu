@@ -453,6 +453,30 @@ extern "C" gfors_status gfors_incumbent_key_async(gfors_handle h, int32_t inst,
   return GFORS_OK;
 }
 
+extern "C" gfors_status gfors_incumbent_async(gfors_handle h, int32_t inst, int64_t* key_host) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst || !key_host) return gf_fail(h, GFORS_E_ARG, "bad inst / key");
+  if (!h->key_stage) {
+    h->key_stage = gf_alloc_t<long long>(h, 3 * (size_t)h->ninst);
+    if (!h->key_stage) return gf_fail(h, GFORS_E_OOM, "key staging");
+  }
+  long long* kd = h->key_stage + 3 * (size_t)inst;
+  k_inc_key<<<1, 1, 0, h->stream>>>(h->inc, inst, kd);
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = cudaMemcpyAsync(key_host, kd, 3 * sizeof(long long), cudaMemcpyDeviceToHost,
+                              h->stream);
+  if (e) return gf_cuda(h, e, "gfors_incumbent_async");
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_synchronize(gfors_handle h) {
+  GF_ENTER(h);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return gf_cuda(h, e, "gfors_synchronize");
+  return GFORS_OK;
+}
+
 static cudaError_t enqueue_final_round(GfCtx* h) {
   cudaError_t e;
   const float* xk = h->x[h->k_host & 1];
@@ -642,8 +666,21 @@ extern "C" gfors_status gfors_get_iterate(gfors_handle h, int32_t inst, float* x
   return GFORS_OK;
 }
 
+static gfors_status set_iterate_impl(gfors_handle h, int32_t inst, const float* x,
+                                     const float* xbar, const float* y, bool sync);
+
 extern "C" gfors_status gfors_set_iterate(gfors_handle h, int32_t inst, const float* x,
                                           const float* xbar, const float* y) {
+  return set_iterate_impl(h, inst, x, xbar, y, true);
+}
+
+extern "C" gfors_status gfors_set_iterate_async(gfors_handle h, int32_t inst, const float* x,
+                                                const float* xbar, const float* y) {
+  return set_iterate_impl(h, inst, x, xbar, y, false);
+}
+
+static gfors_status set_iterate_impl(gfors_handle h, int32_t inst, const float* x,
+                                     const float* xbar, const float* y, bool sync) {
   GF_ENTER(h);
   h->sr_valid = false;                    // K xbar partials recomputed
   if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
@@ -660,7 +697,7 @@ extern "C" gfors_status gfors_set_iterate(gfors_handle h, int32_t inst, const fl
     e = cudaMemcpyAsync(h->xbar + I.var_off, xbar, sizeof(float) * I.n, H2D, h->stream);
   if (y && I.m1 + I.m2 && !e)
     e = cudaMemcpyAsync(h->y + I.row_off, y, sizeof(float) * (I.m1 + I.m2), H2D, h->stream);
-  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (!e && sync) e = cudaStreamSynchronize(h->stream);
   if (e) return gf_cuda(h, e, "gfors_set_iterate");
   return GFORS_OK;
 }

@@ -189,6 +189,7 @@ struct gfors_ctx {
   int64_t* rg_ptr = nullptr;
   int64_t* rg_idx = nullptr;
   int64_t nrg = 0;
+  long long* key_stage = nullptr;    // 3 per instance: gfors_incumbent_async
   int32_t* bit_g4 = nullptr;
   int32_t* bit_count = nullptr;
   int64_t n_bit_g4 = -1;

@@ -219,6 +219,19 @@ class Handle:
         _check(_lib.gfors_sample_eval_range(self.h, nrounds, first_round_id, proposal,
                                             s_begin, s_end), self.h)
 
+    def set_iterate_async(self, inst, x, xbar=None, y=None):
+        """Enqueue the iterate copies; the arrays must stay alive and unchanged
+        until the stream passes them (pinned memory: truly asynchronous)."""
+        _check(_lib.gfors_set_iterate_async(self.h, inst, _ptr(x), _ptr(xbar), _ptr(y)), self.h)
+
+    def incumbent_async(self, inst, key_host):
+        """Enqueue the copy of (obj, round, sample) into key_host (int64[3],
+        pinned); valid after synchronize()."""
+        _check(_lib.gfors_incumbent_async(self.h, inst, _ptr(key_host)), self.h)
+
+    def synchronize(self):
+        _check(_lib.gfors_synchronize(self.h), self.h)
+
     def incumbent_key_async(self, inst, key_dev_ptr):
         """Write (obj, round, sample) of instance inst to 3 int64 at a device
         address (e.g. tensor.data_ptr()), on the handle's stream."""
@@ -426,6 +439,9 @@ _lib.gfors_sample_eval_range.argtypes = [vp, i32, u32, i32, i32, i32]
 _lib.gfors_set_assign3d_custom.argtypes = [vp, i32, i32, i32, i32]
 _lib.gfors_dense_info.argtypes = [vp, i32, vp]
 _lib.gfors_pdhg_path.argtypes = [vp, vp]
+_lib.gfors_set_iterate_async.argtypes = [vp, i32, vp, vp, vp]
+_lib.gfors_incumbent_async.argtypes = [vp, i32, vp]
+_lib.gfors_synchronize.argtypes = [vp]
 _lib.gfors_tu_reformulate.argtypes = [i64, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
 _lib.gfors_tu_sizes.argtypes = [vp, vp]
 _lib.gfors_tu_copy.argtypes = [vp] + [vp] * 14

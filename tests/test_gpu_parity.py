@@ -503,3 +503,33 @@ def test_repair_groups_bit_exact(k_b):
     assert np.array_equal(viol, vo) and np.array_equal(obj, oo)
     # every customer keeps at most one facility
     assert X[:, 70:].reshape(k_b, 9, 70).sum(-1).max() <= 1
+
+
+def test_async_io_matches_sync():
+    """gfors_set_iterate_async / gfors_incumbent_async / gfors_synchronize give
+    the results of the synchronous calls."""
+    inst = CASES["setcover"]()
+    gp, _ = _params(k_b=256)
+    rng = np.random.default_rng(3)
+    x = rng.random(inst.n).astype(np.float32)
+    keys = []
+    for asyn in (False, True):
+        H = G.load(inst, gp)
+        if asyn:
+            H.set_iterate_async(0, x, x, None)
+        else:
+            H.set_iterate(0, x, x, None)
+        H.pdhg_steps(20)
+        H.sample_eval(1, 5, 0)
+        if asyn:
+            k = np.zeros(3, np.int64)
+            H.incumbent_async(0, k)
+            H.synchronize()
+        else:
+            inc = H.incumbent(0, want_x=False)
+            big = np.iinfo(np.int64).max
+            k = np.array([inc["obj"], inc["round"], inc["sample"]] if inc["found"]
+                         else [big, big, big], np.int64)
+        keys.append(k)
+        H.destroy()
+    assert np.array_equal(keys[0], keys[1])
