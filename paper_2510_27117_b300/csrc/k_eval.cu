@@ -92,7 +92,17 @@ k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
   uint32_t m[kUG];
   if (R.L <= 1 && no_upper) {
     uint32_t any[kUG] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = lane; t < R.len; t += 32) {
+    // two columns per lane and step, both loads issued before either is used
+    int t = lane;
+    for (; t + 32 < R.len; t += 64) {
+      const int32_t ca = cols[t], cb = cols[t + 32];
+      uint32_t m2[kUG];
+      load_words(X, ca, kws, w0, nw, vec, m);
+      load_words(X, cb, kws, w0, nw, vec, m2);
+#pragma unroll
+      for (int j = 0; j < kUG; ++j) any[j] |= m[j] | m2[j];
+    }
+    if (t < R.len) {
       load_words(X, cols[t], kws, w0, nw, vec, m);
 #pragma unroll
       for (int j = 0; j < kUG; ++j) any[j] |= m[j];
@@ -105,7 +115,20 @@ k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
     }
   } else if (R.U == 1 && R.L <= 1) {
     uint32_t ones[kUG] = {0, 0, 0, 0, 0, 0, 0, 0}, twos[kUG] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = lane; t < R.len; t += 32) {
+    // two columns per lane and step, both loads issued before either is used
+    int t = lane;
+    for (; t + 32 < R.len; t += 64) {
+      const int32_t ca = cols[t], cb = cols[t + 32];
+      uint32_t m2[kUG];
+      load_words(X, ca, kws, w0, nw, vec, m);
+      load_words(X, cb, kws, w0, nw, vec, m2);
+#pragma unroll
+      for (int j = 0; j < kUG; ++j) {
+        twos[j] |= (ones[j] & m[j]) | (m[j] & m2[j]) | (ones[j] & m2[j]);
+        ones[j] |= m[j] | m2[j];
+      }
+    }
+    if (t < R.len) {
       load_words(X, cols[t], kws, w0, nw, vec, m);
 #pragma unroll
       for (int j = 0; j < kUG; ++j) {
