@@ -300,8 +300,8 @@ def test_run_never_beats_brute_force(idx):
 
 def test_persistent_dense_path_matches_launch_path():
     """One cooperative launch per call (matrix resident in shared memory,
-    blocks exchanging x through tagged words) against per-iteration
-    launches.  Both paths sum each row with the same routine, so the iterates
+    blocks meeting at a grid barrier between iterations) against
+    per-iteration launches.  Both paths sum each row with the same routine, so the iterates
     must agree exactly; the persistent path is called in uneven pieces so that
     penalty updates (every k_int = 10 iterations) fall inside a launch and
     between launches."""
