@@ -134,17 +134,72 @@ GF_DEV void short_rows(const GfRun* __restrict__ runs, const int64_t* __restrict
   }
 }
 
+// The block's rows, when they all lie in one run of two-entry rows whose
+// nonzeros start at an even offset (nearly every block of a large bucket):
+// row ids and nonzero offsets are then affine in the thread index, and each
+// (index, value) pair is one 8-byte load.  Otherwise (run boundaries, the
+// last block, other lengths) the general per-row bookkeeping of short_rows.
+struct ShortBlock {
+  GfRun R;
+  int64_t off0;      // offset in the run of this thread's first row
+  bool fast;
+};
+GF_DEV ShortBlock short_block(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr,
+                              int nruns) {
+  const int64_t b0 = (int64_t)blockIdx.x * (256 * kShortRpt);
+  const int q = nruns == 1 ? 0 : run_of(run_ptr, nruns, b0);
+  ShortBlock B;
+  B.R = runs[q];
+  const int64_t lo = __ldg(run_ptr + q), hi = __ldg(run_ptr + q + 1);
+  B.off0 = b0 - lo + threadIdx.x;
+  B.fast = B.R.len == 2 && !(B.R.nnz0 & 1) && b0 + 256 * kShortRpt <= hi;
+  return B;
+}
+
 __global__ void __launch_bounds__(256, 4)
 k_dual_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr, int nruns,
              int64_t nrows, const int64_t* __restrict__ Kp, const int32_t* __restrict__ Kc,
              const float* __restrict__ Kv, const float* __restrict__ xbar,
              const float* __restrict__ r, const uint8_t* __restrict__ row_eq,
              const GfIParam* __restrict__ ip, float* __restrict__ y) {
+  const ShortBlock B = short_block(runs, run_ptr, nruns);
+  if (B.fast) {
+    const float tau2 = ip[B.R.inst].tau2;
+    int2 c[kShortRpt];
+    float2 v[kShortRpt];
+    float yo[kShortRpt], rr[kShortRpt], xa[kShortRpt], xb[kShortRpt];
+    uint8_t eq[kShortRpt];
+#pragma unroll
+    for (int u = 0; u < kShortRpt; ++u) {
+      const int64_t off = B.off0 + u * 256, j = B.R.first + off, t = B.R.nnz0 + 2 * off;
+      c[u] = *reinterpret_cast<const int2*>(Kc + t);
+      v[u] = *reinterpret_cast<const float2*>(Kv + t);
+      yo[u] = y[j];
+      rr[u] = r[j];
+      eq[u] = row_eq[j];
+    }
+#pragma unroll
+    for (int u = 0; u < kShortRpt; ++u) {
+      xa[u] = xbar[c[u].x];
+      xb[u] = xbar[c[u].y];
+    }
+#pragma unroll
+    for (int u = 0; u < kShortRpt; ++u) {
+      CSum acc;
+      acc.add(__fmul_rn(v[u].x, xa[u]));
+      acc.add(__fmul_rn(v[u].y, xb[u]));
+      float val = yo[u] + tau2 * (acc.value() + rr[u]);
+      if (!eq[u] && val < 0.f) val = 0.f;
+      y[B.R.first + B.off0 + u * 256] = val;
+    }
+    return;
+  }
   ShortRow w[kShortRpt];
   short_rows(runs, run_ptr, nruns, nrows, Kp, w);
   int c0[kShortRpt], c1[kShortRpt];
   float v0[kShortRpt], v1[kShortRpt], yo[kShortRpt], rr[kShortRpt];
   float xa[kShortRpt], xb[kShortRpt];
+  uint8_t eq[kShortRpt];
 #pragma unroll
   for (int u = 0; u < kShortRpt; ++u) {
     c0[u] = w[u].n >= 1 ? Kc[w[u].t0] : 0;
@@ -153,6 +208,7 @@ k_dual_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr
     v1[u] = w[u].n >= 2 ? Kv[w[u].t0 + 1] : 0.f;
     yo[u] = w[u].n >= 0 ? y[w[u].id] : 0.f;
     rr[u] = w[u].n >= 0 ? r[w[u].id] : 0.f;
+    eq[u] = w[u].n >= 0 ? row_eq[w[u].id] : 1;
   }
 #pragma unroll
   for (int u = 0; u < kShortRpt; ++u) {
@@ -167,7 +223,7 @@ k_dual_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr
     if (w[u].n >= 2) acc.add(__fmul_rn(v1[u], xb[u]));
     const float tau2 = ip[w[u].inst].tau2;
     float v = yo[u] + tau2 * (acc.value() + rr[u]);
-    if (!row_eq[w[u].id] && v < 0.f) v = 0.f;
+    if (!eq[u] && v < 0.f) v = 0.f;
     y[w[u].id] = v;
   }
 }
@@ -182,38 +238,72 @@ k_primal_short(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_p
                float* __restrict__ xbar, float* __restrict__ dlast, int advance,
                GfDState* st, const GfSched* sc, const double* normQ, const int32_t* cap,
                GfIParam* ip_next) {
-  ShortRow w[kShortRpt];
-  short_rows(runs, run_ptr, nruns, ncols, Tp, w);
-  int c0[kShortRpt], c1[kShortRpt];
-  float v0[kShortRpt], v1[kShortRpt], xo[kShortRpt], ch[kShortRpt];
-  float ya[kShortRpt], yb[kShortRpt];
+  const ShortBlock B = short_block(runs, run_ptr, nruns);
+  if (B.fast) {
+    const GfIParam p = ip[B.R.inst];
+    int2 c[kShortRpt];
+    float2 v[kShortRpt];
+    float xo[kShortRpt], ch[kShortRpt], ya[kShortRpt], yb[kShortRpt];
 #pragma unroll
-  for (int u = 0; u < kShortRpt; ++u) {
-    c0[u] = w[u].n >= 1 ? Tr[w[u].t0] : 0;
-    v0[u] = w[u].n >= 1 ? Tv[w[u].t0] : 0.f;
-    c1[u] = w[u].n >= 2 ? Tr[w[u].t0 + 1] : 0;
-    v1[u] = w[u].n >= 2 ? Tv[w[u].t0 + 1] : 0.f;
-    xo[u] = w[u].n >= 0 ? x_old[w[u].id] : 0.f;
-    ch[u] = w[u].n >= 0 ? chat[w[u].id] : 0.f;
-  }
+    for (int u = 0; u < kShortRpt; ++u) {
+      const int64_t off = B.off0 + u * 256, i = B.R.first + off, t = B.R.nnz0 + 2 * off;
+      c[u] = *reinterpret_cast<const int2*>(Tr + t);
+      v[u] = *reinterpret_cast<const float2*>(Tv + t);
+      xo[u] = x_old[i];
+      ch[u] = chat[i];
+    }
 #pragma unroll
-  for (int u = 0; u < kShortRpt; ++u) {
-    ya[u] = w[u].n >= 1 ? y[c0[u]] : 0.f;
-    yb[u] = w[u].n >= 2 ? y[c1[u]] : 0.f;
-  }
+    for (int u = 0; u < kShortRpt; ++u) {
+      ya[u] = y[c[u].x];
+      yb[u] = y[c[u].y];
+    }
 #pragma unroll
-  for (int u = 0; u < kShortRpt; ++u) {
-    if (w[u].n < 0) continue;
-    CSum acc;
-    if (w[u].n >= 1) acc.add(__fmul_rn(v0[u], ya[u]));
-    if (w[u].n >= 2) acc.add(__fmul_rn(v1[u], yb[u]));
-    const GfIParam p = ip[w[u].inst];
-    const float delta = ch[u] + p.rho + acc.value() - 2.0f * p.rho * xo[u];
-    float xn = xo[u] - p.tau1 * delta;
-    xn = fminf(1.0f, fmaxf(0.0f, xn));
-    x_new[w[u].id] = xn;
-    xbar[w[u].id] = 2.0f * xn - xo[u];
-    if (dlast) dlast[w[u].id] = p.tau1 * delta;
+    for (int u = 0; u < kShortRpt; ++u) {
+      CSum acc;
+      acc.add(__fmul_rn(v[u].x, ya[u]));
+      acc.add(__fmul_rn(v[u].y, yb[u]));
+      const float delta = ch[u] + p.rho + acc.value() - 2.0f * p.rho * xo[u];
+      float xn = xo[u] - p.tau1 * delta;
+      xn = fminf(1.0f, fmaxf(0.0f, xn));
+      const int64_t i = B.R.first + B.off0 + u * 256;
+      x_new[i] = xn;
+      xbar[i] = 2.0f * xn - xo[u];
+      if (dlast) dlast[i] = p.tau1 * delta;
+    }
+  } else {
+    ShortRow w[kShortRpt];
+    short_rows(runs, run_ptr, nruns, ncols, Tp, w);
+    int c0[kShortRpt], c1[kShortRpt];
+    float v0[kShortRpt], v1[kShortRpt], xo[kShortRpt], ch[kShortRpt];
+    float ya[kShortRpt], yb[kShortRpt];
+#pragma unroll
+    for (int u = 0; u < kShortRpt; ++u) {
+      c0[u] = w[u].n >= 1 ? Tr[w[u].t0] : 0;
+      v0[u] = w[u].n >= 1 ? Tv[w[u].t0] : 0.f;
+      c1[u] = w[u].n >= 2 ? Tr[w[u].t0 + 1] : 0;
+      v1[u] = w[u].n >= 2 ? Tv[w[u].t0 + 1] : 0.f;
+      xo[u] = w[u].n >= 0 ? x_old[w[u].id] : 0.f;
+      ch[u] = w[u].n >= 0 ? chat[w[u].id] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kShortRpt; ++u) {
+      ya[u] = w[u].n >= 1 ? y[c0[u]] : 0.f;
+      yb[u] = w[u].n >= 2 ? y[c1[u]] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kShortRpt; ++u) {
+      if (w[u].n < 0) continue;
+      CSum acc;
+      if (w[u].n >= 1) acc.add(__fmul_rn(v0[u], ya[u]));
+      if (w[u].n >= 2) acc.add(__fmul_rn(v1[u], yb[u]));
+      const GfIParam p = ip[w[u].inst];
+      const float delta = ch[u] + p.rho + acc.value() - 2.0f * p.rho * xo[u];
+      float xn = xo[u] - p.tau1 * delta;
+      xn = fminf(1.0f, fmaxf(0.0f, xn));
+      x_new[w[u].id] = xn;
+      xbar[w[u].id] = 2.0f * xn - xo[u];
+      if (dlast) dlast[w[u].id] = p.tau1 * delta;
+    }
   }
   if (advance && blockIdx.x == 0) advance_penalty(st, sc, normQ, cap, ip, ip_next);
 }
