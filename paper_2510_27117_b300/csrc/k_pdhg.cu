@@ -33,14 +33,22 @@ k_dual_rows(const int32_t* __restrict__ rows, int32_t nrows,
   if (grp >= nrows) return;                 // whole groups exit together
   const int j = rows[grp];
   const int64_t t0 = Kp[j], t1 = Kp[j + 1];
+  // the update's own operands, loaded before the row's gathers
+  float yo = 0.f, rj = 0.f, tau2 = 0.f;
+  uint8_t eq = 1;
+  if (lane == 0) {
+    yo = y[j];
+    rj = r[j];
+    eq = row_eq[j];
+    tau2 = ip[row_inst[j]].tau2;
+  }
   CSum acc;
   for (int64_t t = t0 + lane; t < t1; t += LANES)
     acc.add(__fmul_rn(Kv[t], xbar[Kc[t]]));
   gf::csum_group_reduce<LANES>(acc);
   if (lane == 0) {
-    const float tau2 = ip[row_inst[j]].tau2;
-    float v = y[j] + tau2 * (acc.value() + r[j]);
-    if (!row_eq[j] && v < 0.f) v = 0.f;
+    float v = yo + tau2 * (acc.value() + rj);
+    if (!eq && v < 0.f) v = 0.f;
     y[j] = v;
   }
 }
@@ -77,14 +85,21 @@ k_dual_runs(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr,
   const int64_t j = R.first + off;
   const int64_t t0 = R.len >= 0 ? R.nnz0 + off * R.len : Kp[j];
   const int64_t t1 = R.len >= 0 ? t0 + R.len : Kp[j + 1];
+  float yo = 0.f, rj = 0.f;                 // loaded before the row's gathers
+  uint8_t eq = 1;
+  if (lane == 0) {
+    yo = y[j];
+    rj = r[j];
+    eq = row_eq[j];
+  }
   CSum acc;
   for (int64_t t = t0 + lane; t < t1; t += LANES)
     acc.add(__fmul_rn(Kv[t], xbar[Kc[t]]));
   gf::csum_group_reduce<LANES>(acc);
   if (lane == 0) {
     const float tau2 = ip[R.inst].tau2;
-    float v = y[j] + tau2 * (acc.value() + r[j]);
-    if (!row_eq[j] && v < 0.f) v = 0.f;
+    float v = yo + tau2 * (acc.value() + rj);
+    if (!eq && v < 0.f) v = 0.f;
     y[j] = v;
   }
 }
@@ -331,6 +346,11 @@ k_primal_cols(const int32_t* __restrict__ cols, int32_t ncols,
   const int lane = (int)(gid % LANES);
   if (grp < ncols) {
     const int i = cols[grp];
+    float xo = 0.f, ch = 0.f;               // loaded before the column's gathers
+    if (lane == 0) {
+      xo = x_old[i];
+      ch = chat[i];
+    }
     CSum acc;
     for (int64_t t = Tp[i] + lane; t < Tp[i + 1]; t += LANES)
       acc.add(__fmul_rn(Tv[t], y[Tr[t]]));
@@ -341,8 +361,7 @@ k_primal_cols(const int32_t* __restrict__ cols, int32_t ncols,
     gf::csum_group_reduce<LANES>(acc);
     if (lane == 0) {
       const GfIParam q = ip[var_inst[i]];
-      const float xo = x_old[i];
-      const float delta = chat[i] + q.rho + acc.value() - 2.0f * q.rho * xo;
+      const float delta = ch + q.rho + acc.value() - 2.0f * q.rho * xo;
       float xn = xo - q.tau1 * delta;
       xn = fminf(1.0f, fmaxf(0.0f, xn));
       x_new[i] = xn;
@@ -377,6 +396,11 @@ k_primal_runs(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_pt
     const int64_t i = R.first + off;
     const int64_t t0 = R.len >= 0 ? R.nnz0 + off * R.len : Tp[i];
     const int64_t t1 = R.len >= 0 ? t0 + R.len : Tp[i + 1];
+    float xo = 0.f, ch = 0.f;               // loaded before the column's gathers
+    if (lane == 0) {
+      xo = x_old[i];
+      ch = chat[i];
+    }
     CSum acc;
     for (int64_t t = t0 + lane; t < t1; t += LANES)
       acc.add(__fmul_rn(Tv[t], y[Tr[t]]));
@@ -387,8 +411,7 @@ k_primal_runs(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_pt
     gf::csum_group_reduce<LANES>(acc);
     if (lane == 0) {
       const GfIParam p = ip[R.inst];
-      const float xo = x_old[i];
-      const float delta = chat[i] + p.rho + acc.value() - 2.0f * p.rho * xo;
+      const float delta = ch + p.rho + acc.value() - 2.0f * p.rho * xo;
       float xn = xo - p.tau1 * delta;
       xn = fminf(1.0f, fmaxf(0.0f, xn));
       x_new[i] = xn;
