@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 
 #include "internal.cuh"
@@ -957,6 +958,12 @@ extern "C" gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, in
   if (I.qkind == 1 || h->fused_ok)
     return gf_fail(h, GFORS_E_UNSUPPORTED, "repair groups on a dense / fused instance");
   if (!I.integral) return gf_fail(h, GFORS_E_UNSUPPORTED, "repair groups need integral costs");
+  // the instance's integer costs: members are stored in (cost, listing
+  // position) order, so the repair kernel keeps the first selected member
+  std::vector<long long> cost((size_t)I.n);
+  if (cudaError_t e0 = cudaMemcpy(cost.data(), h->cint + I.var_off, sizeof(long long) * I.n,
+                                  cudaMemcpyDeviceToHost))
+    return gf_cuda(h, e0, "repair group costs");
   std::vector<uint8_t> seen(I.n, 0);
   if (h->h_rg_ptr.empty()) h->h_rg_ptr.push_back(0);
   const int64_t base = (int64_t)h->h_rg_idx.size();
@@ -969,6 +976,10 @@ extern "C" gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, in
       seen[v] = 1;
       h->h_rg_idx.push_back(I.var_off + v);
     }
+    std::stable_sort(h->h_rg_idx.begin() + base + grp_ptr[g], h->h_rg_idx.end(),
+                     [&](int64_t x, int64_t y) {
+                       return cost[x - I.var_off] < cost[y - I.var_off];
+                     });
     h->h_rg_ptr.push_back(base + grp_ptr[g + 1]);
   }
   h->nrg = (int64_t)h->h_rg_ptr.size() - 1;

@@ -10,12 +10,18 @@ namespace {
 // Repair after the monotone relaxation (Section 2.4.3): an equality group
 // relaxed to "sum >= 1" may hold several selected members; each candidate
 // keeps its selected member of least cost (ties to the member listed first).
-// One warp per (group, word): pass 1 transposes 32 members' words so that
-// lane b sees candidate b's selections among them and keeps the best; pass 2
-// transposes the chosen bits back and writes each member's word.
+// The members of every group are stored in (cost, listing position) order,
+// so that member is simply the first one selected in storage order.  One
+// warp per (group, word), kRepairU chunks of 32 members per step with all
+// their loads in flight: pass 1 transposes each chunk's words so that lane b
+// sees candidate b's selections and keeps the first, stopping once every
+// candidate has one; pass 2 transposes the kept bits back and rewrites the
+// members' words that change.
+constexpr int kRepairU = 4;
+
 __global__ void __launch_bounds__(256)
 k_repair_min(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi, int64_t ng,
-             const long long* __restrict__ cost, int kws, int kwu, uint32_t* __restrict__ X) {
+             int kws, int kwu, uint32_t* __restrict__ X) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= ng * kwu) return;                       // whole warps
@@ -23,34 +29,37 @@ k_repair_min(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi, int
   const int w = (int)(wid % kwu);
   const int64_t a = gp[g], e = gp[g + 1];
   const gf::TransposeLane tl = gf::transpose_lane(lane);
-  long long bc = 0;
-  int64_t bt = -1;                                   // position of the kept member
-  for (int64_t t0 = a; t0 < e; t0 += 32) {
-    const int64_t t = t0 + lane;
-    const bool valid = t < e;
-    const int64_t m = valid ? gi[t] : 0;
-    const uint32_t word = valid ? X[m * kws + w] : 0u;
-    const long long c = valid ? cost[m] : 0;
-    unsigned any = __ballot_sync(0xFFFFFFFFu, word != 0u);
-    if (!any) continue;
-    const uint32_t T = gf::warp_transpose32(word, tl);
-    while (any) {
-      const int l = __ffs(any) - 1;
-      any &= any - 1;
-      const long long cl = __shfl_sync(0xFFFFFFFFu, c, l);
-      if (((T >> l) & 1u) && (bt < 0 || cl < bc)) {
-        bc = cl;
-        bt = t0 + l;
-      }
+  int64_t bt = -1;                                   // storage position of the kept member
+  for (int64_t t0 = a; t0 < e; t0 += 32 * kRepairU) {
+    uint32_t word[kRepairU];
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) {
+      const int64_t t = t0 + 32 * u + lane;
+      word[u] = t < e ? X[gi[t] * kws + w] : 0u;
     }
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) {
+      const uint32_t T = gf::warp_transpose32(word[u], tl);
+      if (bt < 0 && T) bt = t0 + 32 * u + (__ffs(T) - 1);
+    }
+    if (__all_sync(0xFFFFFFFFu, bt >= 0)) break;
   }
-  for (int64_t t0 = a; t0 < e; t0 += 32) {
-    const uint32_t mine = (bt >= t0 && bt < t0 + 32) ? (1u << (uint32_t)(bt - t0)) : 0u;
-    const uint32_t keep = gf::warp_transpose32(mine, tl);
-    const int64_t t = t0 + lane;
-    if (t < e) {
-      uint32_t* p = X + gi[t] * kws + w;
-      if (*p != keep) *p = keep;
+  for (int64_t t0 = a; t0 < e; t0 += 32 * kRepairU) {
+    int64_t m[kRepairU];
+    uint32_t cur[kRepairU];
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) {
+      const int64_t t = t0 + 32 * u + lane;
+      m[u] = t < e ? gi[t] : -1;
+      cur[u] = t < e ? X[m[u] * kws + w] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) {
+      const int64_t c0 = t0 + 32 * u;
+      const uint32_t mine = (bt >= c0 && bt < c0 + 32) ? (1u << (uint32_t)(bt - c0)) : 0u;
+      const uint32_t keep =
+          __any_sync(0xFFFFFFFFu, mine != 0u) ? gf::warp_transpose32(mine, tl) : 0u;
+      if (m[u] >= 0 && cur[u] != keep) X[m[u] * kws + w] = keep;
     }
   }
 }
@@ -603,7 +612,7 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   if (h->nrg > 0) {
     const int64_t warps = h->nrg * kw;
     k_repair_min<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
-        h->rg_ptr, h->rg_idx, h->nrg, h->cint, h->kw, kw, h->X);
+        h->rg_ptr, h->rg_idx, h->nrg, h->kw, kw, h->X);
     h->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
