@@ -1108,6 +1108,18 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
         std::vector<std::pair<int32_t, long long>>().swap(pr2[q]);
       }
     }
+    // uniform rows grouped by evaluation class (any-of, at-most-one with at
+    // least one, general count), one kernel instance per class
+    {
+      auto cls = [](const GfURow& R) {
+        const bool no_upper = R.U < 0 || R.U >= R.len;
+        return (R.L <= 1 && no_upper) ? 0 : (R.U == 1 && R.L <= 1) ? 1 : 2;
+      };
+      std::stable_sort(ur.begin(), ur.end(),
+                       [&](const GfURow& a, const GfURow& b) { return cls(a) < cls(b); });
+      for (int c = 0; c < 3; ++c) h->nurows_cls[c] = 0;
+      for (const GfURow& R : ur) ++h->nurows_cls[cls(R)];
+    }
     h->nurows = (int64_t)ur.size();
     h->nprows = (int64_t)pr.size();
     h->ngrows = (int64_t)gr.size();

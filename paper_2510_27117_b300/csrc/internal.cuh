@@ -218,6 +218,7 @@ struct gfors_ctx {
   // evaluation (integer data)
   bool all_integral = true;
   GfURow* urows = nullptr; int64_t nurows = 0; int32_t* ucols = nullptr;
+  int64_t nurows_cls[3] = {0, 0, 0};  // urows of each class, stored in class order
   GfPRow* prows = nullptr; int64_t nprows = 0;
   GfGRow* grows = nullptr; int64_t ngrows = 0; int32_t* gcols = nullptr; int32_t* gvals = nullptr;
   long long* cint = nullptr;        // N, original integer costs

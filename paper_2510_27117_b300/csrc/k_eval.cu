@@ -74,6 +74,10 @@ GF_DEV void add_row_violations(uint32_t vmask, int inst, int w, int len, int chu
   if ((vmask >> lane) & 1u) atomicAdd(&viol[(int64_t)inst * chunk + 32 * w + lane], 1);
 }
 
+// CLS: the rows' class (0: L <= 1 without upper bound, an OR; 1: U = 1,
+// L <= 1, ones and twos; 2: general bounds), so that each class compiles to
+// its own register budget.
+template <int CLS>
 __global__ void __launch_bounds__(256)
 k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
              const int32_t* __restrict__ ucols, const uint32_t* __restrict__ X, int kws,
@@ -90,7 +94,7 @@ k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
   const int32_t* cols = ucols + R.t0;
   const bool no_upper = (R.U < 0 || R.U >= R.len);
   uint32_t m[kUG];
-  if (R.L <= 1 && no_upper) {
+  if (CLS == 0) {
     uint32_t any[kUG] = {0, 0, 0, 0, 0, 0, 0, 0};
     // two columns per lane and step, both loads issued before either is used
     int t = lane;
@@ -113,7 +117,7 @@ k_eval_urows(const GfURow* __restrict__ rows, int64_t nrows,
       for (int off = 16; off > 0; off >>= 1) any[j] |= __shfl_xor_sync(0xFFFFFFFFu, any[j], off);
       if (j < nw && R.L == 1) add_row_violations(~any[j], R.inst, w0 + j, len, chunk, viol);
     }
-  } else if (R.U == 1 && R.L <= 1) {
+  } else if (CLS == 1) {
     uint32_t ones[kUG] = {0, 0, 0, 0, 0, 0, 0, 0}, twos[kUG] = {0, 0, 0, 0, 0, 0, 0, 0};
     // two columns per lane and step, both loads issued before either is used
     int t = lane;
@@ -666,10 +670,21 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
     return e;
   if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
     return e;
-  if (h->nurows) {
-    const int64_t warps = h->nurows * ((kwu + kUG - 1) / kUG);
-    k_eval_urows<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
-        h->urows, h->nurows, h->ucols, h->X, h->kw, kwu, len, h->chunk, h->viol);
+  for (int c = 0, r0 = 0; c < 3; r0 += (int)h->nurows_cls[c], ++c) {
+    const int64_t nr = h->nurows_cls[c];
+    if (!nr) continue;
+    const int64_t warps = nr * ((kwu + kUG - 1) / kUG);
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    const GfURow* rows = h->urows + r0;
+    if (c == 0)
+      k_eval_urows<0><<<blocks, 256, 0, h->stream>>>(rows, nr, h->ucols, h->X, h->kw, kwu, len,
+                                                     h->chunk, h->viol);
+    else if (c == 1)
+      k_eval_urows<1><<<blocks, 256, 0, h->stream>>>(rows, nr, h->ucols, h->X, h->kw, kwu, len,
+                                                     h->chunk, h->viol);
+    else
+      k_eval_urows<2><<<blocks, 256, 0, h->stream>>>(rows, nr, h->ucols, h->X, h->kw, kwu, len,
+                                                     h->chunk, h->viol);
     h->launches++;
   }
   if (h->nprows) {
