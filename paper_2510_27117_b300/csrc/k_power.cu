@@ -137,7 +137,8 @@ __global__ void k_pw_step(PwState* __restrict__ ps, const double* __restrict__ l
   ps[b] = S;
 }
 
-__global__ void k_pw_normalize(double* __restrict__ v, const double* __restrict__ z,
+// v = z / |z| per instance; v and z may be the same vector (in-place start)
+__global__ void k_pw_normalize(double* v, const double* z,
                                const double* __restrict__ zn2,
                                const int32_t* __restrict__ var_inst,
                                const PwState* __restrict__ ps, int64_t N) {
