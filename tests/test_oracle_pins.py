@@ -366,6 +366,28 @@ def test_maxcut_objective_is_minus_cut():
         assert obj[s] == -cut and viol[s] == 0
 
 
+@pytest.mark.parametrize("form", ["csr_dense_graph", "sparse_graph"])
+def test_maxcut_csr_objective_is_minus_cut(form):
+    """The CSR (sparse-Q) objective path gives minus the cut weight, counted
+    edge by edge, with the paper's weights U{-8..10} (negative weights and a
+    diagonal that is not zero)."""
+    if form == "csr_dense_graph":
+        inst = W.max_cut(n=36, idx=4, weights="paper", sparse=True)
+        Wm = np.asarray(inst.meta["W"], np.int64)
+    else:
+        inst = W.max_cut_sparse(n=60, avg_deg=6.0, idx=2)
+        Wm = inst.meta["W"].toarray().astype(np.int64)
+    n = inst.n
+    rng = np.random.default_rng(7)
+    X = (rng.random((25, n)) < 0.5).astype(np.uint8)
+    viol, obj = O.Evaluator(inst)(X)
+    iu, ju = np.nonzero(np.triu(Wm, 1))
+    assert len(iu) > 0 and (Wm[iu, ju] < 0).any()
+    for s in range(25):
+        cut = sum(int(Wm[i, j]) for i, j in zip(iu, ju) if X[s, i] != X[s, j])
+        assert obj[s] == -cut and viol[s] == 0
+
+
 def test_eval_setcover_and_knapsack_semantics():
     inst = W.set_cover(n=50, m=10, density=0.2, idx=5)
     rng = np.random.default_rng(3)
