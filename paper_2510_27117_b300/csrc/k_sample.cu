@@ -302,7 +302,7 @@ constexpr int kAxGroup = 128;                         // threads per candidate
 constexpr int kAxCands = 4;                           // candidates per block
 GF_DEV int ax_slot(int q) { return (q & ~31) | ((q & 31) ^ ((q >> 5) & 31)); }
 
-__global__ void __launch_bounds__(kAxGroup * kAxCands)
+__global__ void __launch_bounds__(kAxGroup * kAxCands, 2)
 k_axial_grp(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, int len,
             int kw, uint64_t seed, int inst_base, const GfDState* __restrict__ st,
             uint32_t* __restrict__ X) {
