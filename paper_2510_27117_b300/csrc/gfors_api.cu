@@ -932,6 +932,17 @@ extern "C" gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, 
     if (!h->a4_cand || !h->a4_J0 || !h->a4_K0)
       return gf_fail(h, GFORS_E_OOM, "Algorithm 4 scratch");
   }
+  {
+    // gains are differences of two pairs of costs: int32 holds them when
+    // 4 max|c| < 2^31
+    std::vector<long long> cost((size_t)I.n);
+    if (cudaError_t e0 = cudaMemcpy(cost.data(), h->cint + I.var_off, sizeof(long long) * I.n,
+                                    cudaMemcpyDeviceToHost))
+      return gf_cuda(h, e0, "Algorithm 4 costs");
+    long long cmax = 0;
+    for (long long v : cost) cmax = std::max(cmax, v < 0 ? -v : v);
+    I.a4_gain32 = cmax < (1ll << 29);
+  }
   I.group_mode = 3;
   I.axial_I = I3;
   I.a4_gamma = gamma;

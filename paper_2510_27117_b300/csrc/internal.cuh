@@ -119,6 +119,7 @@ struct GfInstHost {
                                     // 3 Algorithm 4 (customized 3D assignment)
   int axial_I = 0;
   int a4_gamma = 1, a4_L = 0;       // Algorithm 4: entries gamma*I, steps L
+  bool a4_gain32 = false;           // Algorithm 4 gains fit in int32 (4 max|c| < 2^31)
   int64_t ngroups = 0;
   int64_t grp_off = 0;              // offset into the group tables
   int64_t nrep = 0, rep_off = 0;

@@ -96,7 +96,11 @@ GF_DEV int pair_index(int a, int b, int I) { return a * (2 * I - a - 1) / 2 + (b
 // and recomputes those 4 (I - 1) entries instead of all 2 I (I - 1) / 2.
 // Gains are exact integers, so the chosen interchange is the same as with a
 // full recomputation.
-__global__ void __launch_bounds__(kA4Threads)
+// G: the gain type.  int when every gain fits (4 max|c| < 2^31; gains are
+// differences of two pairs of costs), which halves the gain table and lets
+// seven candidates' blocks share an SM, so a round of 1,024 runs in one wave.
+template <typename G>
+__global__ void __launch_bounds__(kA4Threads, sizeof(G) == 4 ? 7 : 1)
 k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
             const long long* __restrict__ cost, int64_t v0, int I, int L, int s0, int len,
             uint64_t seed, int inst, const GfDState* __restrict__ st, int kw,
@@ -104,9 +108,9 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
   __shared__ int32_t J[64], Kk[64], fi[64], fj[64], fk[64];
   __shared__ uint32_t ufy[128];                  // Fisher-Yates draws
   __shared__ long long cold[64];                 // cost of the triple at each i
-  __shared__ long long gain[2 * kA4MaxPairs];    // [pair][type]
+  __shared__ G gain[2 * kA4MaxPairs];            // [pair][type]
   __shared__ uint8_t pa[kA4MaxPairs], pb[kA4MaxPairs];
-  __shared__ long long wbest[kA4Threads / 32];
+  __shared__ G wbest[kA4Threads / 32];
   __shared__ int wcode[kA4Threads / 32];
   const int sidx = blockIdx.x;
   if (sidx >= len) return;
@@ -157,8 +161,8 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
   __syncthreads();
   auto pair_gains = [&](int q, int a, int b) {
     const long long old = cold[a] + cold[b];
-    gain[2 * q] = C3(a, J[b], Kk[a]) + C3(b, J[a], Kk[b]) - old;       // exchange j
-    gain[2 * q + 1] = C3(a, J[a], Kk[b]) + C3(b, J[b], Kk[a]) - old;   // exchange k
+    gain[2 * q] = (G)(C3(a, J[b], Kk[a]) + C3(b, J[a], Kk[b]) - old);       // exchange j
+    gain[2 * q + 1] = (G)(C3(a, J[a], Kk[b]) + C3(b, J[b], Kk[a]) - old);   // exchange k
   };
   for (int q = tid; q < np; q += kA4Threads) pair_gains(q, pa[q], pb[q]);
   __syncthreads();
@@ -169,21 +173,21 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
   // barrier).
   const int warp = tid >> 5, lane = tid & 31;
   for (int step = 0; step < L; ++step) {
-    long long best = 0;                          // only strict improvements count
+    G best = 0;                                  // only strict improvements count
     int code = 0x7FFFFFFF;
     for (int e = tid; e < 2 * np; e += kA4Threads) {
-      const long long g = gain[e];
+      const G g = gain[e];
       if (g < best) { best = g; code = e; }      // ascending e: ties keep the first
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const long long ob = __shfl_down_sync(0xFFFFFFFFu, best, off);
+      const G ob = __shfl_down_sync(0xFFFFFFFFu, best, off);
       const int oc = __shfl_down_sync(0xFFFFFFFFu, code, off);
       if (ob < best || (ob == best && oc < code)) { best = ob; code = oc; }
     }
     if (lane == 0) { wbest[warp] = best; wcode[warp] = code; }
     __syncthreads();
-    long long bb = 0;
+    G bb = 0;
     int bc = 0x7FFFFFFF;
 #pragma unroll
     for (int w = 0; w < kA4Threads / 32; ++w)
@@ -210,8 +214,8 @@ k_a4_sample(const int32_t* __restrict__ J0, const int32_t* __restrict__ K0,
       const int Jh = u < x ? Jx : Ju, Kh = u < x ? Kx : Ku;
       const long long old = cu + cx;
       const int pq = pair_index(lo, hi, I);
-      gain[2 * pq] = C3(lo, Jh, Kl) + C3(hi, Jl, Kh) - old;       // exchange j
-      gain[2 * pq + 1] = C3(lo, Jl, Kh) + C3(hi, Jh, Kl) - old;   // exchange k
+      gain[2 * pq] = (G)(C3(lo, Jh, Kl) + C3(hi, Jl, Kh) - old);       // exchange j
+      gain[2 * pq + 1] = (G)(C3(lo, Jl, Kh) + C3(hi, Jh, Kl) - old);   // exchange k
     }
     __syncthreads();
     if (tid == 0) {
@@ -251,9 +255,14 @@ cudaError_t gf_launch_assign_custom(GfCtx* h, int b, const float* p, int s0, int
     cudaMemsetAsync(h->a4_J0, 0xFF, sizeof(int32_t) * n1, h->stream);
     cudaMemsetAsync(h->a4_K0, 0xFF, sizeof(int32_t) * n1, h->stream);
   }
-  k_a4_sample<<<len, kA4Threads, 0, h->stream>>>(h->a4_J0, h->a4_K0, h->cint, I.var_off, n1,
-                                                 I.a4_L, s0, len, h->prm.seed,
-                                                 h->prm.inst_base + b, h->dstate, h->kw, h->X);
+  if (I.a4_gain32)
+    k_a4_sample<int><<<len, kA4Threads, 0, h->stream>>>(
+        h->a4_J0, h->a4_K0, h->cint, I.var_off, n1, I.a4_L, s0, len, h->prm.seed,
+        h->prm.inst_base + b, h->dstate, h->kw, h->X);
+  else
+    k_a4_sample<long long><<<len, kA4Threads, 0, h->stream>>>(
+        h->a4_J0, h->a4_K0, h->cint, I.var_off, n1, I.a4_L, s0, len, h->prm.seed,
+        h->prm.inst_base + b, h->dstate, h->kw, h->X);
   h->launches++;
   return cudaGetLastError();
 }
