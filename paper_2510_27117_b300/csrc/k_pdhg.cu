@@ -402,8 +402,25 @@ k_primal_runs(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_pt
       ch = chat[i];
     }
     CSum acc;
-    for (int64_t t = t0 + lane; t < t1; t += LANES)
-      acc.add(__fmul_rn(Tv[t], y[Tr[t]]));
+    if (LANES == 1 && (R.len == 3 || R.len == 4)) {
+      // one lane, three or four entries: every index and value load first,
+      // then the gathers, then the adds in entry order (the loop's sum)
+      int c[4];
+      float v[4], g[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        c[e] = e < R.len ? Tr[t0 + e] : 0;
+        v[e] = e < R.len ? Tv[t0 + e] : 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) g[e] = e < R.len ? y[c[e]] : 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (e < R.len) acc.add(__fmul_rn(v[e], g[e]));
+    } else {
+      for (int64_t t = t0 + lane; t < t1; t += LANES)
+        acc.add(__fmul_rn(Tv[t], y[Tr[t]]));
+    }
     if (Qp) {
       for (int64_t t = Qp[i] + lane; t < Qp[i + 1]; t += LANES)
         acc.add(2.0f * __fmul_rn(Qv[t], x_old[Qc[t]]));
