@@ -316,6 +316,7 @@ struct gfors_ctx {
   // small instances: one block per instance, matrix in shared memory
   bool small_ok = false;
   struct GfSmallInst* small_tab = nullptr;
+  uint16_t* small_perm = nullptr;   // N: each instance's columns by decreasing length
   size_t small_smem = 0;
   // persistent cooperative PDHG launch (dense instance, matrix in smem)
   bool persist_ok = false;

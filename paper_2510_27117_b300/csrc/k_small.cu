@@ -11,6 +11,8 @@
 // The penalty schedule advances inside every block from the same FP64 state.
 // Arithmetic: 4-term plain FP32 chunks folded into compensated sums (8
 // lanes per row, a thread per column), then the projected updates of Alg. 2.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "penalty.cuh"
 
@@ -33,7 +35,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_pdhg_small(const GfSmallInst* __restrict__ insts, const int64_t* __restrict__ Kp,
              const int32_t* __restrict__ Kc, const float* __restrict__ Kv,
              const int64_t* __restrict__ Tp, const int32_t* __restrict__ Tr,
-             const float* __restrict__ Tv, const float* __restrict__ rhat,
+             const float* __restrict__ Tv, const uint16_t* __restrict__ perm_g,
+             const float* __restrict__ rhat,
              const uint8_t* __restrict__ row_eq, const float* __restrict__ chat, float* x0,
              float* x1, float* __restrict__ xbar_g, float* __restrict__ y_g,
              float* __restrict__ dlast, GfIParam* iprm, int ninst, long long k0,
@@ -59,6 +62,7 @@ k_pdhg_small(const GfSmallInst* __restrict__ insts, const int64_t* __restrict__ 
   float* tval = reinterpret_cast<float*>(take(I.uniform ? 0 : 4 * (size_t)nnz));
   uint16_t* kcol = reinterpret_cast<uint16_t*>(take(2 * (size_t)nnz));
   uint16_t* trow = reinterpret_cast<uint16_t*>(take(2 * (size_t)nnz));
+  uint16_t* perm = reinterpret_cast<uint16_t*>(take(2 * (size_t)n));   // columns by length
   uint8_t* eq = take((size_t)m);
   __shared__ GfIParam qsm[2];
   __shared__ double rho_s;
@@ -68,6 +72,7 @@ k_pdhg_small(const GfSmallInst* __restrict__ insts, const int64_t* __restrict__ 
   const float* xo_g = (it0 & 1) ? x0 : x1;        // x_{k0} in x[k0 & 1]
   for (int j = threadIdx.x; j <= m; j += kThreads) rp[j] = (int32_t)(Kp[I.r0 + j] - I.k0);
   for (int i = threadIdx.x; i <= n; i += kThreads) cp[i] = (int32_t)(Tp[I.v0 + i] - I.t0);
+  for (int i = threadIdx.x; i < n; i += kThreads) perm[i] = perm_g[I.v0 + i];
   for (int t = threadIdx.x; t < nnz; t += kThreads) {
     kcol[t] = (uint16_t)(Kc[I.k0 + t] - I.v0);
     trow[t] = (uint16_t)(Tr[I.t0 + t] - I.r0);
@@ -126,9 +131,12 @@ k_pdhg_small(const GfSmallInst* __restrict__ insts, const int64_t* __restrict__ 
       }
     }
     __syncthreads();
-    // primal step: a thread per column, chunks of 4 products
+    // primal step: a thread per column, chunks of 4 products; columns are
+    // taken in order of decreasing length, so the 32 columns of a warp have
+    // nearly equal lengths and few lanes idle in the chunk loop
     const bool last = (s + 1 == nsteps);
-    for (int i = threadIdx.x; i < n; i += kThreads) {
+    for (int ii = threadIdx.x; ii < n; ii += kThreads) {
+      const int i = perm[ii];
       CSum acc;
       const int te = cp[i + 1];
       for (int t = cp[i]; t < te; t += 4) {
@@ -200,7 +208,7 @@ size_t small_smem(int64_t n, int64_t m, int64_t nnz, bool uniform) {
   auto a16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
   size_t b = a16(4 * (m + 1)) + a16(4 * (n + 1)) + 4 * a16(4 * n) + 2 * a16(4 * m);
   b += uniform ? a16(4 * m) : 2 * a16(4 * nnz);
-  b += 2 * a16(2 * nnz) + a16(m);
+  b += 2 * a16(2 * nnz) + a16(2 * n) + a16(m);
   return b;
 }
 
@@ -233,6 +241,24 @@ bool gf_small_setup(GfCtx* h, const std::vector<uint8_t>& uniform,
     smem = std::max(smem, small_smem(S.n, S.m, S.nnz, S.uniform != 0));
   }
   if (smem > 200 * 1024) return false;
+  // each instance's columns by decreasing length (ties in index order)
+  std::vector<uint16_t> perm((size_t)h->N, 0);
+  for (int q = 0; q < h->ninst; ++q) {
+    const GfSmallInst& S = tab[q];
+    std::vector<int32_t> ord(S.n);
+    for (int32_t i = 0; i < S.n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) {
+      return tp[S.v0 + a + 1] - tp[S.v0 + a] > tp[S.v0 + c + 1] - tp[S.v0 + c];
+    });
+    for (int32_t i = 0; i < S.n; ++i) perm[S.v0 + i] = (uint16_t)ord[i];
+  }
+  h->small_perm = gf_alloc_t<uint16_t>(h, perm.size());
+  if (!h->small_perm) return false;
+  if (cudaMemcpy(h->small_perm, perm.data(), sizeof(uint16_t) * perm.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   if (cudaFuncSetAttribute(k_pdhg_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -253,7 +279,8 @@ bool gf_small_setup(GfCtx* h, const std::vector<uint8_t>& uniform,
 // nsteps iterations of every instance after iteration h->k_host (one launch).
 cudaError_t gf_launch_small(GfCtx* h, int64_t nsteps) {
   k_pdhg_small<<<h->ninst, kThreads, h->small_smem, h->stream>>>(
-      h->small_tab, h->Kp, h->Kc, h->Kv, h->Tp, h->Tr, h->Tv, h->rhat, h->row_eq, h->chat,
+      h->small_tab, h->Kp, h->Kc, h->Kv, h->Tp, h->Tr, h->Tv, h->small_perm, h->rhat,
+      h->row_eq, h->chat,
       h->x[0], h->x[1], h->xbar, h->y, h->dlast, h->iprm, h->ninst, h->k_host, nsteps,
       h->dstate, h->sched_d, h->normQhat_d, h->cap_d);
   h->launches++;
