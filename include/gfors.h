@@ -98,8 +98,7 @@ typedef struct {
   int32_t eval_mode;   /* 0 auto, 1 materialised bits, 2 fused sample+eval
                           (single-row instances), 3 dense tensor-core
                           scoring (dense small-integer Q), 4 dense scoring
-                          on CUDA cores (checking), 5 one-CTA tensor-core
-                          scoring instead of the two-CTA cluster kernel,
+                          on CUDA cores (checking), 5 the same as 3,
                           6 tensor-core scoring with bf16 operands (auto
                           uses FP8 E4M3 operands when every entry of
                           offdiag(Q+Q^T) is exact in E4M3)                  */
@@ -340,14 +339,16 @@ GFORS_API gfors_status gfors_profile_read(gfors_handle h, int32_t nphases, doubl
  *   seed, inst_id, round_id, first_sample: the Philox key, instance id,
  *               round id and first candidate index (as in gfors_sample_eval)
  *   nsamples    candidates first_sample .. first_sample + nsamples - 1;
- *               at most GFORS_NOALLOC_MAX_SAMPLES, else GFORS_E_ARG
+ *               at most GFORS_NOALLOC_MAX_SAMPLES, and first_sample +
+ *               nsamples at most INT32_MAX, else GFORS_E_ARG
  *   viol_dev [nsamples] int32 out: 1 if a.x < rhs; obj_dev [nsamples]
  *               int64 out: c.x  (device buffers owned by the caller)
  * Enqueued on cuda_stream, asynchronous.  Its only scratch is a file-scope
  * device array of GFORS_NOALLOC_MAX_SAMPLES int64 that every device using
  * the library keeps until the process exits.  The first call on a device
- * looks up that array's address and should come before any stream capture.
- * Calls share the array (each clears what it uses first): calls that overlap
+ * looks up that array's address and should come before any stream capture;
+ * the address is cached for the process, so do not call this after a
+ * cudaDeviceReset.  Calls share the array (each clears what it uses first): calls that overlap
  * on the GPU race. */
 #define GFORS_NOALLOC_MAX_SAMPLES 16384
 GFORS_API gfors_status gfors_fused_eval_noalloc(const float* p_dev, const int32_t* a_dev,

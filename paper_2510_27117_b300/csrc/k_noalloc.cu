@@ -12,7 +12,9 @@
 //
 // Set-up: the first call on a device looks the array's device address up
 // (cudaGetSymbolAddress, with that device current) and caches it; make
-// that first call before any stream capture.  Every device that loads the
+// that first call before any stream capture.  The cached address belongs
+// to the device's primary context: after cudaDeviceReset it is stale, so
+// this entry point must not be used after a reset in the same process.  Every device that loads the
 // library holds the array (GFORS_NOALLOC_MAX_SAMPLES x 8 bytes) until the
 // process exits.  All calls share it: each call clears the part it uses
 // first, and calls whose work overlaps on the GPU (different streams, no
@@ -92,6 +94,12 @@ extern "C" gfors_status gfors_fused_eval_noalloc(const float* p_dev, const int32
   if (n < 0 || first_sample < 0 || (n > 0 && (!p_dev || !a_dev || !c_dev)) ||
       (nsamples > 0 && (!viol_dev || !obj_dev))) {
     gf_fail(nullptr, GFORS_E_ARG, "gfors_fused_eval_noalloc: bad pointer or size");
+    return GFORS_E_ARG;
+  }
+  // candidate indices first_sample + s must stay within int32
+  if (first_sample > INT32_MAX - nsamples) {
+    gf_fail(nullptr, GFORS_E_ARG,
+            "gfors_fused_eval_noalloc: first_sample + nsamples exceeds INT32_MAX");
     return GFORS_E_ARG;
   }
   if (nsamples == 0) return GFORS_OK;

@@ -53,12 +53,8 @@ GF_DEV void mma_op(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
   else gf_tc::mma_f16(d_tmem, a, b, kIdesc, accum);
 }
 
-// CL = 1: one CTA per tile.  CL = 2: a cluster of two CTAs computes the
-// tiles (2p, n) and (2p+1, n); each CTA loads its own W2 tile and HALF of the
-// shared candidate tile, multicast to both, so per-CTA operand traffic per
-// k-step drops from 48 KB to 32 KB; MMA completions are committed to both
-// CTAs' stage-release barriers (arrival count 2).
-template <int CL, bool F8>
+// One CTA per 128 x 256 output tile; every CTA loads its own operand tiles.
+template <bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            int n, int64_t ld, int len, int num_m, int num_n, int num_k,
@@ -87,7 +83,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     drain_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, CL);
+      mbar_init(empty0 + 8 * s, 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
@@ -103,16 +99,12 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL == 2) cluster_sync();      // peers' barriers initialised
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
-  uint32_t rank = 0;
-  if constexpr (CL == 2) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  const int num_mp = (num_m + CL - 1) / CL;    // tile rows handled per cluster step
-  const int num_tiles = num_mp * num_n;
-  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-  auto tile_m0 = [&](int t) { return (CL * (t % num_mp) + (int)rank) * BM; };
-  auto tile_n0 = [&](int t) { return (t / num_mp) * BN; };
+  const int num_tiles = num_m * num_n;
+  const int cid = blockIdx.x, ncl = gridDim.x;
+  auto tile_m0 = [&](int t) { return (t % num_m) * BM; };
+  auto tile_n0 = [&](int t) { return (t / num_m) * BN; };
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -127,13 +119,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, limit_ns, &abort_flag))) break;
           mbar_arrive_expect_tx(full0 + 8 * s, STAGE_BYTES);
           tma_load_2d(smem_u32(stA + s * A_BYTES), &tmA, full0 + 8 * s, kb * KE, m0);
-          if constexpr (CL == 2) {
-            // my half of the candidate tile, to both CTAs of the cluster
-            tma_load_2d_mc(smem_u32(stB + s * B_BYTES + rank * (B_BYTES / 2)), &tmB,
-                           full0 + 8 * s, kb * KE, n0 + (int)rank * (BN / 2), (uint16_t)0x3);
-          } else {
-            tma_load_2d(smem_u32(stB + s * B_BYTES), &tmB, full0 + 8 * s, kb * KE, n0);
-          }
+          tma_load_2d(smem_u32(stB + s * B_BYTES), &tmB, full0 + 8 * s, kb * KE, n0);
         }
       }
       if (!ok) {
@@ -166,8 +152,7 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
           for (int k = 0; k < BK / 16; ++k)
             mma_op<F8>(d, sw128_desc(a0 + 32 * k), sw128_desc(b0 + 32 * k),
                        (kb | k) != 0 ? 1u : 0u);
-          if constexpr (CL == 2) mma_commit_mc(empty0 + 8 * s, (uint16_t)0x3);
-          else mma_commit(empty0 + 8 * s);
+          mma_commit(empty0 + 8 * s);
         }
         if (ok) mma_commit(tfull0 + 8 * acc);
       }
@@ -248,9 +233,6 @@ k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
   }
   __syncthreads();
-  // no CTA leaves while its peer may still multicast into it or arrive on
-  // its barriers (every wait above is bounded, so both CTAs get here)
-  if constexpr (CL == 2) cluster_sync();
   if (abort_flag && threadIdx.x == 0) atomicExch(&st->error, 1);
   if (warp == 1) {
     tc_fence_after();
@@ -297,9 +279,8 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, u
 struct TcCache {
   const void* W2 = nullptr;
   const void* Xs = nullptr;
-  CUtensorMap a, b, b2;
+  CUtensorMap a, b;
   int sms = 0;
-  int clusters2 = 0;                  // co-resident 2-CTA clusters (0: unusable)
   bool attr = false;
 };
 
@@ -307,7 +288,6 @@ struct TcCache {
 
 // Launch the tensor-core scorer for candidates [0, len) of the chunk;
 // obj (zeroed by the evaluation pass) receives the exact objectives.
-// eval_mode 5 forces the one-CTA variant (checking).
 cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int len) {
   (void)s0;
   static thread_local std::vector<TcCache> caches;
@@ -319,40 +299,20 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
   if (C.W2 != Wop || C.Xs != dq.Xs) {
     if (!make_map(&C.a, Wop, (uint64_t)dq.ld, (uint64_t)dq.n, (uint64_t)dq.ld, ke, BM, f8) ||
         !make_map(&C.b, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, ke, BN,
-                  f8) ||
-        !make_map(&C.b2, dq.Xs, (uint64_t)dq.ld, (uint64_t)dq.chunk, (uint64_t)dq.ld, ke,
-                  BN / 2, f8))
+                  f8))
       return cudaErrorInvalidValue;
     C.W2 = Wop;
     C.Xs = dq.Xs;
   }
   if (!C.attr) {
     cudaError_t e = cudaSuccess;
-    for (const void* fn : {(const void*)k_score_tc<1, false>, (const void*)k_score_tc<2, false>,
-                           (const void*)k_score_tc<1, true>, (const void*)k_score_tc<2, true>})
+    for (const void* fn : {(const void*)k_score_tc<false>, (const void*)k_score_tc<true>})
       if (!e) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        SMEM_BYTES);
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&C.sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(2 * (C.sms / 2));
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_score_tc<2, false>, &cfg) != cudaSuccess) {
-      cudaGetLastError();
-      ncl = 0;
-    }
-    C.clusters2 = ncl;
     C.attr = true;
   }
   const int num_m = (int)((dq.n + BM - 1) / BM);
@@ -366,39 +326,15 @@ cudaError_t gf_launch_dense_score_tc(GfCtx* h, const GfDenseQ& dq, int s0, int l
   int nn = (int)dq.n, ll = len;
   int64_t ld = dq.ld;
   GfDState* st = h->dstate;
-  cudaError_t e;
-  if (C.clusters2 > 0 && h->prm.eval_mode != 5) {
-    const int tiles = ((num_m + 1) / 2) * num_n;
-    const int nclus = std::min(tiles, C.clusters2);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(2 * nclus);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.stream = h->stream;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if (f8)
-      e = cudaLaunchKernelEx(&cfg, k_score_tc<2, true>, C.a, C.b2, nn, ld, ll, num_m, num_n,
-                             num_k, Xb, lin, outu, limit, st);
-    else
-      e = cudaLaunchKernelEx(&cfg, k_score_tc<2, false>, C.a, C.b2, nn, ld, ll, num_m, num_n,
-                             num_k, Xb, lin, outu, limit, st);
-  } else {
-    const int tiles = num_m * num_n;
-    const int grid = std::min(tiles, C.sms > 0 ? C.sms : 148);
-    if (f8)
-      k_score_tc<1, true><<<grid, kThreads, SMEM_BYTES, h->stream>>>(
-          C.a, C.b, nn, ld, ll, num_m, num_n, num_k, Xb, lin, outu, limit, st);
-    else
-      k_score_tc<1, false><<<grid, kThreads, SMEM_BYTES, h->stream>>>(
-          C.a, C.b, nn, ld, ll, num_m, num_n, num_k, Xb, lin, outu, limit, st);
-    e = cudaGetLastError();
-  }
+  const int tiles = num_m * num_n;
+  const int grid = std::min(tiles, C.sms > 0 ? C.sms : 148);
+  if (f8)
+    k_score_tc<true><<<grid, kThreads, SMEM_BYTES, h->stream>>>(
+        C.a, C.b, nn, ld, ll, num_m, num_n, num_k, Xb, lin, outu, limit, st);
+  else
+    k_score_tc<false><<<grid, kThreads, SMEM_BYTES, h->stream>>>(
+        C.a, C.b, nn, ld, ll, num_m, num_n, num_k, Xb, lin, outu, limit, st);
+  cudaError_t e = cudaGetLastError();
   if (e) return e;
   k_halve<<<(len + 255) / 256, 256, 0, h->stream>>>(out, len);
   h->launches += 2;

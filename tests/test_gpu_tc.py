@@ -25,12 +25,11 @@ def _scores(inst, k_b, mode, R=5, seed=11):
 
 
 @pytest.mark.parametrize("n,k_b,mode", [(300, 96, 3), (200, 512, 3), (513, 288, 3),
-                                        (300, 96, 5), (513, 288, 5), (640, 1024, 3),
+                                        (640, 1024, 3), (1100, 520, 3),
                                         (513, 288, 6), (300, 96, 6)])
 def test_tc_matches_simt_and_oracle_small(n, k_b, mode):
-    """mode 3: two-CTA cluster kernel with multicast; mode 5: one-CTA kernel
-    (both with FP8 E4M3 operands for these +-1 graphs); mode 6: bf16
-    operands."""
+    """mode 3: the tcgen05 scorer with FP8 E4M3 operands (exact for these
+    +-1 graphs); mode 6: bf16 operands."""
     inst = W.max_cut(n=n, idx=7)
     p, X, viol, obj, inc = _scores(inst, k_b, mode)
     _, X2, viol2, obj2, inc2 = _scores(inst, k_b, 4)
@@ -47,9 +46,8 @@ def test_tc_full_size_round():
     inst = W.max_cut(n=4096, idx=0)
     p, X, viol, obj, inc = _scores(inst, 8192, 3)
     _, X2, viol2, obj2, inc2 = _scores(inst, 8192, 4)
-    _, X5, viol5, obj5, inc5 = _scores(inst, 8192, 5)
     _, X6, viol6, obj6, inc6 = _scores(inst, 8192, 6)
-    assert np.array_equal(obj, obj2) and np.array_equal(obj, obj5)
+    assert np.array_equal(obj, obj2)
     assert np.array_equal(obj, obj6)
     assert inc["obj"] == inc2["obj"] and inc["sample"] == inc2["sample"]
     # sampled candidates scored by the oracle from its own draws

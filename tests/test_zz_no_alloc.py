@@ -46,3 +46,15 @@ def test_noalloc_matches_handle_path_twice():
 def test_noalloc_rejects_oversize():
     with pytest.raises(G.GforsError):
         G.fused_eval_noalloc(0, 0, 0, 10, 0, 1, 0, 0, 0, G.NOALLOC_MAX_SAMPLES + 1, 0, 0, None)
+
+
+def test_noalloc_rejects_index_overflow():
+    """Candidate indices first_sample + s must stay within int32.  Real
+    device buffers are passed, so the call would be harmless even if the
+    check were missing; the error text shows which check fired."""
+    import torch
+    viol_t = torch.zeros(200, dtype=torch.int32, device="cuda")
+    obj_t = torch.zeros(200, dtype=torch.int64, device="cuda")
+    with pytest.raises(G.GforsError, match="INT32_MAX"):
+        G.fused_eval_noalloc(0, 0, 0, 0, 0, 1, 0, 0, 2**31 - 100, 200, viol_t.data_ptr(),
+                             obj_t.data_ptr(), None)
