@@ -41,6 +41,12 @@ CASES = {
     "facloc_tu": lambda: G.tu_reformulate(
         W.facility_location(nf=12, nc=40, idx=2),
         *W.facility_tu_pivots(W.facility_location(nf=12, nc=40, idx=2), 12, 40))[0],
+    # the full-size max-cut instance: 4,096 int8 entries per row (1,024 words,
+    # a multiple of 128) take the bounds-free row loop of the dense GEMV
+    "maxcut_4096": lambda: W.max_cut(n=4096, idx=0),
+    # more than 2,048 customers: every facility column y_i is a long CSC
+    # column (chunked partial sums plus a finalising pass)
+    "facloc_long": lambda: W.facility_location(nf=6, nc=3000, idx=2),
 }
 
 
@@ -77,7 +83,9 @@ def _step_tolerance(S, t1, t2, rho, x, xb, y, y1):
     return tol_x, tol_y
 
 
-@pytest.mark.parametrize("name,mode", [(c, 0) for c in CASES] + [("assign3d_l2", 2)])
+@pytest.mark.parametrize("name,mode", [(c, 0) for c in CASES] +
+                         [("assign3d_l2", 2), ("maxcut_4096", 1), ("facloc_long", 1),
+                          ("facloc_long", 2)])
 def test_pdhg_single_step(name, mode):
     inst = CASES[name]()
     gp, op = _params(pdhg_mode=mode)
@@ -298,14 +306,16 @@ def test_run_never_beats_brute_force(idx):
     H.destroy()
 
 
-def test_persistent_dense_path_matches_launch_path():
+@pytest.mark.parametrize("n", [700, 1024])
+def test_persistent_dense_path_matches_launch_path(n):
     """One cooperative launch per call (matrix resident in shared memory,
     blocks meeting at a grid barrier between iterations) against
     per-iteration launches.  Both paths sum each row with the same routine, so the iterates
     must agree exactly; the persistent path is called in uneven pieces so that
     penalty updates (every k_int = 10 iterations) fall inside a launch and
-    between launches."""
-    inst = W.max_cut(n=700, idx=6)
+    between launches.  n = 1024 gives rows of 256 words, which take the
+    bounds-free row loop; n = 700 the general one."""
+    inst = W.max_cut(n=n, idx=6)
     out = []
     for mode, pieces in ((0, (7, 7, 11)), (1, (25,))):
         gp, _ = _params(k_int=10, k_b=64, x0=-1.0, pdhg_mode=mode)
@@ -533,3 +543,117 @@ def test_async_io_matches_sync():
         keys.append(k)
         H.destroy()
     assert np.array_equal(keys[0], keys[1])
+
+
+# ------------------------------------------------------------ penalty schedule
+@pytest.mark.parametrize("kind,delta", [("maxcut", 0.35), ("maxcut", 0.2), ("setcover", 0.35),
+                                        ("knapsack", 0.2)])
+def test_penalty_schedule_matches_oracle(kind, delta):
+    """UpdatePenalty (Section 3) as the device advances it, across several
+    sampling triggers, against orc_rho_update: rho_n = clip(rho_min (1 +
+    n/T)^p, rho_{n-1} + delta, rho_max), the counter advancing once per k_int
+    iterations.  With the step-size cap on, tau1 = min(sqrt(sigma),
+    1/(4 (||Q_hat|| + rho))) pins the device's rho; delta = 0.35 makes the
+    minimum increment win at n = 1, 2, 3 and rho_max cap n = 4, delta = 0.2
+    lets the growth law win first.  Max cut runs the persistent dense kernel
+    (every block advances the schedule), set cover the small-instance kernel,
+    knapsack the one-row kernels."""
+    inst = {"maxcut": lambda: W.max_cut(n=300, idx=1), "setcover": CASES["setcover"],
+            "knapsack": CASES["knapsack"]}[kind]()
+    sched = dict(rho_min=0.3, rho_max=1.5, T=3.0, p=2.0, delta=delta)
+    gp, op = _params(k_int=10, tau_cap_by_L=1, x0=-1.0 if kind == "maxcut" else 0.5, **sched)
+    H = G.load(inst, gp)
+    S = O.preprocess(inst, op.seed, 0)
+    args = (sched["rho_min"], sched["rho_max"], sched["T"], sched["p"], sched["delta"])
+    rhos = [O.rho_update(0, 0.0, *args)]
+    k = 0
+    seen = set()
+    for piece in (7, 16, 12, 10, 20):
+        H.pdhg_steps(piece)
+        k += piece
+        n_next = k // 10                         # counter of iteration k + 1
+        while len(rhos) <= n_next:
+            rhos.append(O.rho_update(len(rhos), rhos[-1], *args))
+        want = rhos[n_next]
+        seen.add(want)
+        t1, t2 = O.step_sizes(op.sigma, S.normQ, want, True)
+        sc = H.get_scales(0)
+        assert abs(sc[6] - t1) <= 1e-9 * t1 and abs(sc[7] - t2) <= 1e-9 * t2, (k, want)
+        st = H.lp_stats(0)
+        assert st[6] == want and st[7] == k
+    assert len(seen) >= 4 and 1.5 in seen
+    H.destroy()
+
+
+# ------------------------------------------------------------ CheckHalt sums
+def _f32(a):
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["setcover", "knapsack", "tiny", "facloc", "assign3d",
+                                  "maxcut", "maxcut_sparse"])
+def test_lp_stats_match_oracle(name):
+    """gfors_lp_stats (FP64 device reductions) entry by entry against
+    orc_halt_stats on the same iterate.  The device reduces over its FP32
+    copy of the scaled data, so the oracle is given that data rounded to FP32
+    as well; what remains is FP64 summation order plus, rarely, a one-ulp
+    difference of an FP32 entry where the two FP64 norm estimates straddle a
+    rounding boundary (<= 6e-8 of one term), hence 1e-8 of each quantity's
+    absolute-sum scale.  With Q != 0 the Q x and Q dx terms come from the
+    FP32 GEMV of the PDHG kernels (<= ~6 eps of the absolute sum, as in the
+    single-step tolerance), hence 1e-6 of the scale for those."""
+    inst = CASES[name]()
+    gp, op = _params()
+    H = G.load(inst, gp)
+    S = O.preprocess(inst, op.seed, 0)
+    rng = np.random.default_rng(21)
+    x = rng.random(inst.n).astype(np.float32)
+    x[rng.random(inst.n) < 0.1] = 0.0
+    x[rng.random(inst.n) < 0.1] = 1.0
+    y = (rng.random(S.m) * 0.5).astype(np.float32)
+    if S.m:
+        y[S.m1:] -= 0.25
+    rho = 0.125
+    H.set_iterate(0, x, x, y)
+    H.set_counters(7, rho)
+    H.pdhg_steps(1)
+    gx, _, gxp, gy = (v.astype(np.float64) for v in H.get_iterate(0))
+    st = H.lp_stats(0)
+    H.destroy()
+    S32 = O.Scaled(**{f: getattr(S, f) for f in S.__dataclass_fields__})
+    S32.Kv, S32.r, S32.c = _f32(S.Kv), _f32(S.r), _f32(S.c)
+    if S.qkind == 2:
+        S32.Qv = _f32(S.Qv)
+    t1, _ = O.step_sizes(op.sigma, S.normQ, rho, S.qkind != 0)
+    hs = O.halt_stats(S32, t1, rho, gx, gxp, gy)
+    K = abs(sp.csr_matrix((S.Kv, S.Kc, S.Kp), shape=(S.m, S.n)))
+    if S.qkind == 1:
+        Qa = np.abs(S.Qd)
+    elif S.qkind == 2:
+        Qa = abs(sp.csr_matrix((S.Qv, S.Qc, S.Qp), shape=(S.n, S.n)))
+    else:
+        Qa = None
+    ax, adx = np.abs(gx), np.abs(gx - gxp)
+    qtol = 1e-6 if S.qkind == 1 else 1e-8
+    tol = 1e-8
+    # [0] primal residual
+    sc0 = np.linalg.norm(K @ ax + np.abs(S.r)) / (1 + np.linalg.norm(S.r)) if S.m else 0.0
+    assert abs(st[0] - hs[0]) <= tol * sc0 + 1e-15
+    # [2] binary gap, [6] rho, [7] k
+    assert abs(st[2] - hs[2]) <= 1e-13
+    assert st[6] == rho and st[7] == 8
+    # [3] c^T x + x^T Q x
+    sc3 = np.abs(S.c) @ ax + (ax @ (Qa @ ax) if Qa is not None else 0.0)
+    assert abs(st[3] - hs[3]) <= qtol * sc3 + 1e-15
+    # [5] ||s^x|| (Thm. 2)
+    sc5 = np.linalg.norm(adx / t1 + 2 * rho * adx + (2 * (Qa @ adx) if Qa is not None else 0))
+    assert abs(st[5] - hs[5]) <= qtol * sc5 + 1e-15
+    if S.qkind == 0:
+        # [4] Lagrangian dual bound, [1] relative gap against it
+        sc4 = np.abs(S.r) @ np.abs(gy) + np.sum(np.abs(S.c) + K.T @ np.abs(gy))
+        assert abs(st[4] - hs[4]) <= tol * sc4 + 1e-15
+        den = 1 + abs(hs[3]) + abs(hs[4])
+        assert abs(st[1] - hs[1]) <= 2 * tol * (sc3 + sc4) / den + 1e-15
+    else:
+        assert np.isnan(st[4]) and st[1] == st[5]
+        assert abs(hs[1] - hs[5]) == 0.0

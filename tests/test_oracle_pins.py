@@ -616,3 +616,134 @@ def test_alg4_improvement_never_worsens_and_bounds_optimum():
         c0 = _cost3(_assign_of(X0[s], I), C)
         c1 = _cost3(_assign_of(X1[s], I), C)
         assert opt <= c1 <= c0
+
+
+# ---------------------------------------------------------------- CheckHalt
+@pytest.mark.parametrize("with_Q", [True, False])
+def test_sx_is_thm2_primal_residual(with_Q):
+    """||s^x_k|| of orc_halt_stats against Thm. 2's definition, with the two
+    gradients of L_hat (Eq. 2) taken by central differences of the scalar
+    Lagrangian: s^x = (x_{k-1} - x_k)/tau1 + grad_x L(x_k, y_k) -
+    grad_x L(x_{k-1}, y_k).  With Q != 0 the Gap indicator is ||s^x||."""
+    inst = W.tiny_bip(n=12, m1=4, m2=1, idx=17, with_Q=with_Q)
+    S = O.preprocess(inst, 3)
+    assert (S.qkind != 0) == with_Q
+    rng = np.random.default_rng(4)
+    xp = rng.random(S.n)
+    xb = rng.random(S.n)
+    y = rng.random(S.m)
+    rho, t1, t2 = 0.29, 0.13, 0.4
+    x, _, y1, _ = O.pdhg_step(S, t1, t2, rho, xp, xb, y)
+    h = 1e-6
+
+    def grad(z):
+        g = np.zeros(S.n)
+        for i in range(S.n):
+            e = np.zeros(S.n)
+            e[i] = h
+            g[i] = (_lagrangian(S, rho, z + e, y1) - _lagrangian(S, rho, z - e, y1)) / (2 * h)
+        return g
+
+    sx = (xp - x) / t1 + grad(x) - grad(xp)
+    hs = O.halt_stats(S, t1, rho, x, xp, y1)
+    assert np.linalg.norm(x - xp) > 0.1
+    assert abs(hs[5] - np.linalg.norm(sx)) <= 1e-6 * np.linalg.norm(sx)
+    if with_Q:
+        assert hs[1] == hs[5] and math.isnan(hs[4])
+
+
+def test_halt_tracker_stall_rule():
+    """The value-stalling half of CheckHalt on a hand-built sequence: an
+    indicator is done when <= tol, or when its best value has not improved
+    by more than 1e-3 (relative) for `window` triggers.  Expected decisions
+    worked out by hand from that rule."""
+    hT = O.HaltTracker(1e-4, 3)
+    seq = [(1.0, 5e-5, 0.5),       # t=1: every best set; ind1 <= tol
+           (0.9, 5e-5, 0.4996),    # t=2: ind0 improves; ind2 by 0.08% only
+           (0.9, 1e-3, 0.4996),    # t=3: ind1 above tol, last improved t=1
+           (0.9, 1e-3, 0.4996),    # t=4: ind1, ind2 stalled 3 triggers; ind0 2
+           (0.9, 1e-3, 0.4996)]    # t=5: ind0 stalled 3 triggers -> halt
+    got = [hT.update(v) for v in seq]
+    assert got == [False, False, False, False, True]
+    # improvement is measured against the best value so far: 0.2% per
+    # trigger resets every trigger, 0.05% every third (0.9995^3 < 0.999), so
+    # neither stalls with window 5; 0.01% needs 11 triggers, so the
+    # indicators stall at t = 6, five triggers after the best set at t = 1
+    for rate, halt_at in ((0.998, None), (0.9995, None), (0.9999, 5)):
+        hT = O.HaltTracker(1e-12, 5)
+        halted = [hT.update((rate ** t, rate ** t, rate ** t)) for t in range(1, 40)]
+        assert (halted.index(True) if any(halted) else None) == halt_at
+
+
+# ---------------------------------------------------------------- sampling
+def test_axial3d_pick_frequencies():
+    """Axial 3D picks at I = 3 against the categorical rule: step i = 0 picks
+    (j, k) with probability w_0jk / sum w_0 (w = floor(p 2^24)); given that
+    pick, step i = 1 picks among the pairs with unused j and k with
+    probability proportional to w_1jk; step i = 2 is forced."""
+    I, k = 3, 40000
+    rng = np.random.default_rng(8)
+    p = (0.05 + rng.random(I ** 3)).astype(np.float32)
+    w = np.floor(p.astype(np.float64) * 2.0 ** 24).reshape(I, I, I)
+    X = O.axial3d(p, I, k, 77, 1, 2).reshape(k, I, I, I)
+    first = X[:, 0].reshape(k, I * I)
+    f0 = first.mean(axis=0)
+    want0 = (w[0] / w[0].sum()).reshape(-1)
+    assert np.all(np.abs(f0 - want0) <= 5 * np.sqrt(want0 * (1 - want0) / k))
+    j0, k0 = np.unravel_index(np.argmax(want0), (I, I))
+    sel = X[first[:, j0 * I + k0] == 1]
+    ks = sel.shape[0]
+    free = [(j, kk) for j in range(I) for kk in range(I) if j != j0 and kk != k0]
+    wf = np.array([w[1, j, kk] for j, kk in free])
+    for (j, kk), q in zip(free, wf / wf.sum()):
+        f = sel[:, 1, j, kk].mean()
+        assert abs(f - q) <= 5 * math.sqrt(q * (1 - q) / ks)
+    # every sample is an axial assignment, so step 2 takes the last pair
+    assert np.all(X.sum(axis=(2, 3)) == 1) and np.all(X.sum(axis=(1, 3)) == 1)
+
+
+def test_random_start_vector_from_philox_stream5():
+    """x0 < 0: x_0,i = (u_i >> 8) 2^-24 with u_i lane i & 3 of
+    Philox4x32-10(counter = (i >> 2, 0, 0, inst | 5 << 28), key = seed),
+    built here from explicit generator calls (the generator itself is pinned
+    by its published known-answer vectors)."""
+    seed, inst_id, n = 0x0123456789ABCDEF, 3, 11
+    x0 = O.x0_vector(n, -1.0, seed, inst_id)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    want = np.zeros(n)
+    for i in range(n):
+        u = O.philox4x32_10([i >> 2, 0, 0, inst_id | (5 << 28)], key)[i & 3]
+        want[i] = (int(u) >> 8) * 2.0 ** -24
+    assert np.array_equal(x0, want)
+    assert np.all((x0 >= 0) & (x0 < 1))
+    assert np.all(O.x0_vector(5, 0.25, seed, inst_id) == 0.25)
+
+
+def test_fp64_evaluator_on_fractional_data():
+    """The FP64 evaluator (non-integral data): objective = c^T x + x^T Q x
+    (checked against a brute-force sum for every point of {0,1}^8), and a
+    row is violated only when it misses its right-hand side by more than
+    1e-9 (1 + |rhs|)."""
+    n = 8
+    rng = np.random.default_rng(6)
+    A = sp.csr_matrix(np.array([[0.5, 0.25, 0, 0, 0, 0, 0, 1.0],
+                                [0, 0, 1.0, 1.0, 0, 0, 0, 0]]))
+    Qd = rng.integers(-3, 4, size=(n, n)).astype(np.float64) * 0.5
+    c = rng.random(n) - 0.5
+    codes = np.arange(1 << n)
+    X = ((codes[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
+    for eps, kind in ((0.0, "exact"), (0.5e-9, "inside"), (2e-9, "outside")):
+        b = np.array([0.75 + eps * 1.75, 1.0])
+        inst = W.Instance("frac", n, c, A=A, b=b, Q=Qd)
+        ev = O.Evaluator(inst)
+        assert not ev.integral
+        viol, obj = ev(X)
+        xf = X.astype(np.float64)
+        assert np.allclose(obj, xf @ c + np.einsum("si,ij,sj->s", xf, Qd, xf), rtol=0,
+                           atol=1e-12)
+        ax = xf @ A.toarray().T
+        want = (ax[:, 0] < 0.75 - 1e-12).astype(int) + (ax[:, 1] < 1.0).astype(int)
+        hit = np.isclose(ax[:, 0], 0.75)          # rows exactly at the old rhs
+        if kind == "outside":
+            want = want + hit
+        assert np.array_equal(viol, want)
