@@ -326,6 +326,20 @@ GFORS_API gfors_status gfors_profile(gfors_handle h, int32_t enable);
 GFORS_API gfors_status gfors_profile_read(gfors_handle h, int32_t nphases, double* ms,
                                           int64_t* counts);
 
+/* Failure injection for tests of the bounded device-side waits (failure
+ * detection of this library; the paper has no counterpart).  kind 1: in
+ * the next launch of the persistent dense PDHG kernel (pdhg_mode 0, one
+ * dense instance) or of the cooperative sparse kernel (pdhg_mode 2), block
+ * `block` waits at its first grid barrier without arriving there.  The
+ * other blocks' waits, bounded by wait_timeout_s, run out; every block
+ * then leaves the kernel, the next synchronising call returns
+ * GFORS_E_TIMEOUT and the handle is failed (later calls GFORS_E_STATE until
+ * gfors_destroy).  Nothing faults and the CUDA context stays usable.  A
+ * block index beyond the grid injects nothing.  kind 0 clears a pending
+ * injection.  One launch consumes it.  GFORS_E_ARG for another kind or a
+ * negative block. */
+GFORS_API gfors_status gfors_debug_inject(gfors_handle h, int32_t kind, int32_t block);
+
 /* Allocation-free fused sampling + evaluation of one single-row instance
  * (the knapsack form a.x >= rhs).  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they

@@ -471,6 +471,17 @@ extern "C" gfors_status gfors_incumbent_async(gfors_handle h, int32_t inst, int6
   return GFORS_OK;
 }
 
+extern "C" gfors_status gfors_debug_inject(gfors_handle h, int32_t kind, int32_t block) {
+  GF_ENTER(h);
+  if (kind == 0) {
+    h->inject_skip_block = -1;
+    return GFORS_OK;
+  }
+  if (kind != 1 || block < 0) return gf_fail(h, GFORS_E_ARG, "gfors_debug_inject: bad kind/block");
+  h->inject_skip_block = block;
+  return GFORS_OK;
+}
+
 extern "C" gfors_status gfors_synchronize(gfors_handle h) {
   GF_ENTER(h);
   cudaError_t e = cudaStreamSynchronize(h->stream);

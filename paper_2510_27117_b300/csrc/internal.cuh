@@ -136,6 +136,9 @@ struct gfors_ctx {
   bool failed = false;
   std::string err;
   long long launches = 0;
+  // test injection (gfors_debug_inject): this block of the next persistent
+  // or cooperative PDHG launch skips its first grid-barrier arrival; -1 none
+  int inject_skip_block = -1;
 
   int ninst = 0;
   std::vector<GfInstHost> ih;

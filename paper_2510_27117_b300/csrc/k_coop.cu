@@ -19,12 +19,15 @@ using gf::CSum;
 constexpr int kThreads = 1024;
 constexpr int kMaxStagedY = 8192;                // y staged when it has <= this many rows
 
-GF_DEV bool coop_barrier(unsigned* bar, unsigned target, int* err, uint64_t limit_ns) {
+// arrive = false (test injection only) waits without arriving, so every
+// block's bounded wait runs out.
+GF_DEV bool coop_barrier(unsigned* bar, unsigned target, int* err, uint64_t limit_ns,
+                         bool arrive = true) {
   __syncthreads();
   __shared__ int ok_s;
   if (threadIdx.x == 0) {
     bool ok = true;
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     uint64_t t0 = 0;
     while (true) {
       unsigned v;
@@ -84,7 +87,8 @@ k_pdhg_coop(CoopLists L, const int64_t* __restrict__ Kp, const int32_t* __restri
             const float* __restrict__ chat, float* x0, float* x1, float* xbar, float* y,
             float* __restrict__ dlast, GfIParam* iprm, int ninst, long long k0,
             long long nsteps, GfDState* st, const GfSched* sc, const double* normQ,
-            const int32_t* cap, unsigned* bar, uint64_t limit_ns, int stage_y) {
+            const int32_t* cap, unsigned* bar, uint64_t limit_ns, int stage_y,
+            int skip_block) {
   extern __shared__ float ysm[];                // y staged for the primal step
   __shared__ double rho_s;                      // schedule state (block 0)
   __shared__ int n_rho_s, changed_s;
@@ -125,7 +129,9 @@ k_pdhg_coop(CoopLists L, const int64_t* __restrict__ Kp, const int32_t* __restri
       if (lane == 0)
         y[j] = dual_update(y[j], ip[row_inst[j]].tau2, acc.value(), rhat[j], row_eq[j] != 0);
     }
-    if (!coop_barrier(bar, (unsigned)(2 * s + 1) * nb, &st->error, limit_ns)) break;
+    if (!coop_barrier(bar, (unsigned)(2 * s + 1) * nb, &st->error, limit_ns,
+                      !(s == 0 && (int)blockIdx.x == skip_block)))
+      break;
     // ---- primal step, Alg. 2 (y of this iteration staged in shared memory)
     const float* yv = y;
     if (M > 0) {
@@ -271,9 +277,11 @@ cudaError_t gf_launch_coop(GfCtx* h, int64_t nsteps) {
   unsigned* bar = h->coop_bar;
   uint64_t limit = (uint64_t)(std::max(0.01, h->prm.wait_timeout_s) * 1e9);
   int stage_y = h->M <= kMaxStagedY ? (int)h->M : 0;
+  int skip = h->inject_skip_block;
+  h->inject_skip_block = -1;
   void* args[] = {&L, &Kp, &Kc, &Kv, &Tp, &Tr, &Tv, &rhat, &req, &ri, &vi, &chat, &x0, &x1,
                   &xbar, &y, &dlast, &iprm, &ninst, &k0, &ns, &st, &sc, &nq, &cap, &bar,
-                  &limit, &stage_y};
+                  &limit, &stage_y, &skip};
   e = cudaLaunchCooperativeKernel((const void*)k_pdhg_coop, dim3(h->num_sms), dim3(kThreads),
                                   args, sizeof(float) * (size_t)stage_y, h->stream);
   h->launches += 2;

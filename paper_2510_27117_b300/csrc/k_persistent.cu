@@ -24,8 +24,11 @@ constexpr int kMaxRows = 256;                   // rows per block (c_hat, diag c
 
 // Arrive at the grid barrier of step s and wait until all nb blocks arrived
 // (counter >= s * nb).  Called by one thread; false on timeout / error.
-GF_DEV bool grid_arrive_wait(unsigned* bar, unsigned target, int* err, uint64_t limit_ns) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+// arrive = false (test injection only) waits without arriving, so every
+// block's bounded wait runs out.
+GF_DEV bool grid_arrive_wait(unsigned* bar, unsigned target, int* err, uint64_t limit_ns,
+                             bool arrive) {
+  if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
   uint64_t t0 = 0;
   while (true) {
     unsigned v;
@@ -49,7 +52,7 @@ k_pdhg_dense_persistent(const uint8_t* __restrict__ W2, int64_t ld, int64_t n, i
                         float* __restrict__ dlast, GfIParam* iprm, int inst, int ninst,
                         long long k0, long long nsteps, GfDState* st, const GfSched* sc,
                         const double* normQ, const int32_t* cap, unsigned* bar,
-                        uint64_t limit_ns) {
+                        uint64_t limit_ns, int skip_block) {
   extern __shared__ float4 sm4[];
   float* xs = reinterpret_cast<float*>(sm4);                          // [2][ld]
   const uint32_t* Ws = reinterpret_cast<const uint32_t*>(xs + 2 * ld);  // my rows, int8
@@ -86,7 +89,8 @@ k_pdhg_dense_persistent(const uint8_t* __restrict__ W2, int64_t ld, int64_t n, i
     if (s > 0) {
       __syncthreads();                            // this block's rows of step s-1 written
       if (threadIdx.x == 0)
-        ok = grid_arrive_wait(bar, (unsigned)s * nb, &st->error, limit_ns);
+        ok = grid_arrive_wait(bar, (unsigned)s * nb, &st->error, limit_ns,
+                              !(s == 1 && (int)blockIdx.x == skip_block));
     }
     if (__syncthreads_or(!ok)) break;
     // x_{it-1} into shared memory (padding entries are zero, never written)
@@ -203,8 +207,10 @@ cudaError_t gf_launch_persistent(GfCtx* h, int64_t nsteps) {
   const int32_t* cap = h->cap_d;
   unsigned* bar = h->persist_bar;
   uint64_t limit = (uint64_t)(std::max(0.01, h->prm.wait_timeout_s) * 1e9);
+  int skip = h->inject_skip_block;
+  h->inject_skip_block = -1;
   void* args[] = {&W2, &ld, &n, &v0, &per, &qdiag, &qscale, &x0, &x1, &xbar, &chat, &dlast,
-                  &iprm, &inst, &ninst, &k0, &ns, &st, &sc, &nq, &cap, &bar, &limit};
+                  &iprm, &inst, &ninst, &k0, &ns, &st, &sc, &nq, &cap, &bar, &limit, &skip};
   e = cudaLaunchCooperativeKernel((const void*)k_pdhg_dense_persistent, dim3(h->persist_grid),
                                   dim3(kWarps * 32), args, h->persist_smem, h->stream);
   h->launches += 2;

@@ -88,6 +88,7 @@ _lib.gfors_mlp_adam.argtypes = [i64, vp, vp, vp, vp, i64, f64, f64, f64, f64, vp
 _lib.gfors_state_export.argtypes = [_H, vp, _P(C.c_size_t)]
 _lib.gfors_state_import.argtypes = [_H, vp, C.c_size_t]
 _lib.gfors_profile.argtypes = [_H, i32]
+_lib.gfors_debug_inject.argtypes = [_H, i32, i32]
 _lib.gfors_profile_read.argtypes = [_H, i32, vp, vp]
 _lib.gfors_launch_count.argtypes = [_H]
 _lib.gfors_launch_count.restype = i64
@@ -121,6 +122,19 @@ def _ptr(a: Optional[np.ndarray]):
 
 
 _alloc_keep = []
+
+
+def set_allocator(alloc=None, free=None):
+    """gfors_set_allocator with Python callables alloc(size) -> int device
+    address or None, free(ptr); both None restores cudaMalloc / cudaFree."""
+    if alloc is None and free is None:
+        _alloc_keep[:] = []
+        _check(_lib.gfors_set_allocator(ALLOC_FN(0), FREE_FN(0), None))
+        return
+    fa = ALLOC_FN(lambda size, ctx: alloc(int(size)))
+    ff = FREE_FN(lambda ptr, ctx: free(ptr))
+    _alloc_keep[:] = [fa, ff]
+    _check(_lib.gfors_set_allocator(fa, ff, None))
 
 
 def use_torch_allocator(enable: bool = True):
@@ -350,6 +364,12 @@ class Handle:
 
     def profile(self, enable=True):
         _check(_lib.gfors_profile(self.h, int(enable)), self.h)
+
+    def debug_inject(self, kind, block=0):
+        """gfors_debug_inject: kind 1 makes one block of the next cooperative
+        PDHG launch skip its first grid-barrier arrival (tests of the
+        bounded waits); kind 0 clears it."""
+        _check(_lib.gfors_debug_inject(self.h, kind, block), self.h)
 
     def profile_read(self):
         n = len(self.PHASES)
