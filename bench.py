@@ -5,11 +5,14 @@ One step = one trigger period of Alg. 1 on the workload: k_int PDHG
 iterations (Alg. 2) + one round of k_b sampled candidates (Alg. 3) scored
 exactly on the original data + the on-device incumbent update.
 
-Default workload: max cut, dense Q = -L of G(n=4096, p=0.5) with +-1 edge
-weights, 8,192 candidates per round, k_int = 50.  Prints ONE JSON line.
+Default workload: the largest single-GPU configuration, 16 facility-location
+instances of 1,000 facilities x 10,000 customers (10,001,000 binaries and
+30M nonzeros each) in one batch, 4 rounds x 256 candidates per instance per
+step, k_int = 50, with the learned proposal trained in the same run by the
+library's own kernels.  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload maxcut|setcover|knapsack|assign3d]
+                  [--workload facility|maxcut|setcover|knapsack|assign3d|...]
 """
 from __future__ import annotations
 
@@ -54,7 +57,8 @@ WORKLOADS = {
     "assign3d": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"]).assign3d(
         I=64, idx=r), 50, 1024,
         "axial 3D assignment I=64 (262,144 binaries), 1024 candidates/round, k_int=50, "
-        "learned proposal (MLP 8-128-128-1, random-init weights)"),
+        "plain + learned proposal (MLP 8-128-128-1, trained in this run): 1024 candidates "
+        "from x_k and 1024 from the network per round"),
     "assign3d_alg4": (lambda r: __import__("paper_2510_27117_b300.workloads", fromlist=["x"])
                       .assign3d(I=64, idx=r, sampler="alg4", gamma=1, L=64), 50, 1024,
                       "axial 3D assignment I=64 with the customized sampler (Algorithm 4: "
@@ -76,8 +80,8 @@ WORKLOADS = {
                             .facility_location(1000, 10000, idx=16 * r + q) for q in range(16)],
                  50, 256,
                  "16 facility-location instances 1000 x 10000 (10,001,000 binaries, 30M nnz "
-                 "each), 4 rounds x 256 candidates/instance, k_int=50, learned proposal "
-                 "(random-init weights)"),
+                 "each), k_int=50, 4 rounds per step, each 256 candidates/instance from x_k "
+                 "plus 256 from the learned proposal (MLP 8-128-128-1, trained in this run)"),
 }
 def _facility_tu(r):
     """The facility batch reformulated through the library (host transform);
@@ -102,9 +106,15 @@ TU_SECONDS = [0.0]
 ROUNDS = {"maxcut": 1, "maxcut_sparse": 1, "setcover": 1, "setcover_batch": 1, "knapsack": 1,
           "assign3d": 1,
           "assign3d_alg4": 1, "facility": 4, "facility_tu": 4, "facility_relaxed": 4}
+# 2 = split rounds: the first half of every round from the network, the
+# second half from x_k (the plain sampler stays in every round);
+# 3 = plain + learned: k_b candidates from x_k (those of the plain form)
+# and k_b more from the network per round
 PROPOSAL = {"maxcut": 0, "maxcut_sparse": 0, "setcover": 0, "setcover_batch": 0, "knapsack": 0,
-            "assign3d": 1,
-            "assign3d_alg4": 0, "facility": 1, "facility_tu": 0, "facility_relaxed": 0}
+            "assign3d": 3,
+            "assign3d_alg4": 0, "facility": 3, "facility_tu": 0, "facility_relaxed": 0}
+PROPOSAL_NAMES = ["plain", "learned", "learned (split rounds)",
+                  "plain + learned (k_b from x_k and k_b from the network per round)"]
 
 
 def env_rank():
@@ -208,6 +218,14 @@ def run_ours(args, rank, world, local):
         prm.sample_chunk = k_b                # buffers of one rank's range
     s_begin, s_end = SH.sample_range(prm.k_b, world, rank) if single else (0, k_b)
     G.use_torch_allocator(True)
+    nr, prop = ROUNDS[args.workload], PROPOSAL[args.workload]
+    Wt, train_info = None, None
+    if prop:
+        # the learned proposal, trained here on small seeded instances of the
+        # same family by the library's forward / backward / Adam kernels
+        from paper_2510_27117_b300 import proposal as PR
+        Wt, train_info = PR.train_for(args.workload, args.train_instances_bench,
+                                      args.train_budget_bench)
     t_load0 = time.perf_counter()
     H = G.load_batch(insts, prm, stream=stream)
     torch.cuda.synchronize()
@@ -220,10 +238,8 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     round_id = [0]
 
-    nr, prop = ROUNDS[args.workload], PROPOSAL[args.workload]
     if prop:
-        from paper_2510_27117_b300 import proposal as PR
-        H.set_proposal(PR.init_weights(seed=0))
+        H.set_proposal(Wt)
 
     key = torch.zeros(3, dtype=torch.int64, device="cuda")
     keys = torch.zeros(4 * world, dtype=torch.int64, device="cuda")
@@ -275,7 +291,8 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_step = ms / args.steps
-    cands = k_b * len(insts) * nr
+    per_round = k_b * (2 if prop == 3 else 1)     # proposal 3: plain + learned draws
+    cands = per_round * len(insts) * nr
     value = cands * args.steps * world / (ms / 1e3)
     iters_s = k_int * args.steps / (ms / 1e3)
 
@@ -286,8 +303,10 @@ def run_ours(args, rank, world, local):
     # ---- roofline of the dominant kernel (phase timed with events on the stream)
     peaks, src = load_peaks()
     dinfo = H.dense_info(0)
-    roof = roofline(args.workload, insts, k_int, k_b * nr, prof, peaks, src, args.steps,
+    roof = roofline(args.workload, insts, k_int, per_round * nr, prof, peaks, src, args.steps,
                     fp8=dinfo["fp8"], path=H.pdhg_path())
+    if args.workload == "maxcut" and roof is not None:
+        roof["scoring_bf16"] = bf16_scorer(G, insts[0], k_b, stream, peaks)
     out = {
         "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -297,18 +316,20 @@ def run_ours(args, rank, world, local):
                  "f32 PDHG / int64 evaluation", "data": "synthetic (seeded)",
         "config": {"workload": desc, "global_batch": cands * world, "n": insts[0].n,
                    "instances": len(insts), "k_int": k_int, "k_b": k_b, "k_r": nr,
-                   "proposal": ["plain", "learned"][prop],
+                   "proposal": PROPOSAL_NAMES[prop],
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps",
                    "autotune": tuned},
         "pdhg_iters_per_s": iters_s,
         "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "e2e": e2e, "gpu_launches": int(launches), "load_s": t_load,
+        **({"proposal_training": train_info} if train_info else {}),
         **({"tu_reformulate_s": TU_SECONDS[0]} if args.workload == "facility_tu" else {}),
         "wall_s": wall, "roofline": roof,
     }
     out["clocks"] = clk.summary()
     if rank == 0:
-        out["cpu_baseline"] = (cpu_baseline(args.workload, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = (cpu_baseline(args.workload, budget_s=args.cpu_budget,
+                                            insts=insts if not single else None)
                                if args.cpu_budget > 0 else None)
         print(json.dumps(out), flush=True)
     H.destroy()
@@ -348,7 +369,8 @@ def run_e2e(G, H, insts, k_int, k_b, stream, args, world, nr=1, prop=0, srange=N
     bi = sum(2 * 4 * I.n for I in insts)
     bo = 3 * 8 * len(insts)
     found = int((keys[-1, :, 0] != np.iinfo(np.int64).max).sum())
-    return {"value": k_b * nr * len(insts) * steps * world / dt, "unit": "candidates/s",
+    per_round = k_b * (2 if prop == 3 else 1)
+    return {"value": per_round * nr * len(insts) * steps * world / dt, "unit": "candidates/s",
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps,
             "incumbents_found_last_step": found}
 
@@ -399,15 +421,26 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False, pa
         if dom == "pdhg":
             ms, iters = phases["pdhg"]
             flops = 2.0 * n * n * iters          # one n x n GEMV per iteration
-            ach = flops / (ms / 1e3) / 1e12
+            gemv_b = 2.0 * n * n * iters         # its n^2 x 2 B (bf16 Q) per iteration
+            ach = gemv_b / (ms / 1e3) / 1e9
+            hbm = peaks.get("hbm_gbs", 6400.0)
             tr = TRAFFIC.get(workload)
             out.update({"kernel": PDHG_KERNELS[path],
-                        "bound": "alu", "achieved": ach, "peak": fp32_tflops,
-                        "unit": "TFLOP/s", "frac": ach / fp32_tflops,
+                        "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm,
+                        "notional": "n^2 x 2 B per iteration, the dense GEMV 2Qx as the scope "
+                                    "table counts it (bf16 Q streamed once per iteration); the "
+                                    "kernel keeps Q as int8 in shared memory for the whole "
+                                    "launch, so DRAM moves only `traffic` bytes per launch",
                         "traffic": tr[0] if tr else None,
                         "traffic_source": tr[1] if tr else None,
-                        "algorithmic_per_launch": f"k_int x 2 n^2 = {2.0 * n * n * k_int:.4e} FLOP",
-                        "us_per_iteration": ms / iters * 1e3, "scoring": tc})
+                        "algorithmic_per_launch": f"k_int x 2 n^2 = {2.0 * n * n * k_int:.4e} B",
+                        "us_per_iteration": ms / iters * 1e3,
+                        "alu_view": {"achieved": flops / (ms / 1e3) / 1e12,
+                                     "peak": fp32_tflops, "unit": "TFLOP/s",
+                                     "frac": flops / (ms / 1e3) / 1e12 / fp32_tflops,
+                                     "peak_note": "148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"},
+                        "scoring": tc})
         elif dom == "dense_score" and tc:
             out.update(tc)
         return out
@@ -471,6 +504,53 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False, pa
     return out
 
 
+def bf16_scorer(G, inst, k_b, stream, peaks, rounds=20):
+    """The dense scoring round of the max-cut workload with bf16 operands
+    (eval_mode 6) instead of FP8, timed by the library's phase events with
+    L2 flushed before every round, against the measured bf16 peak."""
+    import torch
+    prm = G.default_params(k_int=50, k_b=k_b, seed=0x5EED0000 + 1, x0=-1.0, eval_mode=6)
+    H = G.load(inst, prm, stream=stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        H.pdhg_steps(50)
+        for r in range(3):
+            H.sample_eval(1, r, 0)
+        torch.cuda.synchronize()
+        H.profile(True)
+        for r in range(3, 3 + rounds):
+            flush.zero_()
+            H.sample_eval(1, r, 0)
+        prof = H.profile_read()
+        H.profile(False)
+    info = H.dense_info(0)
+    H.destroy()
+    ms, cnt = prof["dense_score"]
+    n = inst.n
+    flops = 2.0 * n * n * k_b
+    ach = flops / (ms / cnt / 1e3) / 1e12
+    pk = peaks.get("bf16_tflops", 1800.0)
+    return {"kernel": "k_score_tc (tcgen05, bf16 operands)", "bound": "tensor",
+            "dtype": "fp8 e4m3" if info["fp8"] else "bf16", "achieved": ach, "peak": pk,
+            "unit": "TFLOP/s", "frac": ach / pk, "peak_note": "measured bf16 burst",
+            "ms_per_round": ms / cnt, "rounds": cnt,
+            "algorithmic_per_launch": f"2 n^2 k_b = {flops:.4e} FLOP"}
+
+
+def host_info():
+    """Host cores the process may use, all cores, and the CPU model."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"host_cores": len(os.sched_getaffinity(0)), "cpu_count": os.cpu_count(),
+            "cpu_model": model}
+
+
 # ------------------------------------------------------------------ CPU oracle
 class OracleStep:
     """The FP64 oracle as it stands, single thread, on a bounded sample of
@@ -479,12 +559,16 @@ class OracleStep:
     (k_int iterations + k_b candidates of every instance, scaled by the
     instances' total size for a batch)."""
 
-    def __init__(self, workload):
+    def __init__(self, workload, insts=None):
         from oracle import oracle as O
         self.O = O
         build, self.k_int, self.k_b, self.desc = WORKLOADS[workload]
-        insts = build(0)
-        insts = insts if isinstance(insts, list) else [insts]
+        # candidates per step as the GPU draws them (proposal 3: two draws per round)
+        self.k_b *= ROUNDS[workload] * (2 if PROPOSAL[workload] == 3 else 1)
+        if insts is None:
+            insts = build(0)
+            insts = insts if isinstance(insts, list) else [insts]
+        self.threads = O.use_threads(True)       # Preprocess on every host core
         self.inst = insts[0]
         self.scale = sum(I.n for I in insts) / self.inst.n
         self.ninst = len(insts)
@@ -495,8 +579,11 @@ class OracleStep:
         self.ev = O.Evaluator(self.inst)
         self.round = 0
 
-    def step(self, budget_s):
-        """One bounded sample; returns seconds of one full step."""
+    def step(self, budget_s, threads=False):
+        """One bounded sample with the single-thread reference build or the
+        multi-core build (identical results); returns seconds of one full
+        step."""
+        self.O.use_threads(threads)
         it, t0 = 0, time.perf_counter()
         while it < 1 or (it < self.k_int and time.perf_counter() - t0 < 0.5 * budget_s):
             self.sol.step()
@@ -527,16 +614,25 @@ NO_ORACLE = {"facility_tu": "the oracle's TU reformulation is dense (exact inver
                            "untransformed facility batch is the comparable figure"}
 
 
-def cpu_baseline(workload, budget_s=20.0):
+def cpu_baseline(workload, budget_s=20.0, insts=None):
+    """The oracle on a bounded sample of the workload: first the
+    single-thread reference build, then the same source built with OpenMP
+    over rows and samples on every host core; `value` and `cores` are the
+    multi-core leg's."""
     if workload in NO_ORACLE:
         return {"value": None, "unit": "candidates/s", "cores": 1, "kind": "oracle",
-                "sample": "not run: " + NO_ORACLE[workload]}
-    ob = OracleStep(workload)
-    t_step = ob.step(budget_s)
+                "sample": "not run: " + NO_ORACLE[workload], **host_info()}
+    ob = OracleStep(workload, insts)
+    t1 = ob.step(budget_s / 2, threads=False)
+    it1, ns1, ti1, tc1 = ob.last
+    single = {"value": ob.k_b * ob.ninst / t1, "cores": 1, "s_per_iter": ti1,
+              "s_per_candidate": tc1, "sample": ob.sample_text()}
+    tm = ob.step(budget_s / 2, threads=True)
     it, ns, t_iter, t_cand = ob.last
-    return {"value": ob.k_b * ob.ninst / t_step, "unit": "candidates/s", "cores": 1,
+    return {"value": ob.k_b * ob.ninst / tm, "unit": "candidates/s", "cores": ob.threads,
             "kind": "oracle", "sample": ob.sample_text(), "s_per_iter": t_iter,
-            "s_per_candidate": t_cand, "preprocess_s": ob.t_pre}
+            "s_per_candidate": t_cand, "preprocess_s": ob.t_pre, "single_core": single,
+            **host_info()}
 
 
 def run_reference(args, rank, world):
@@ -552,7 +648,7 @@ def run_reference(args, rank, world):
     per_step = max(0.05, 120.0 / max(1, args.warmup + args.steps))
     ts = []
     for q in range(args.warmup + args.steps):
-        t = ob.step(per_step)
+        t = ob.step(per_step, threads=True)
         if q >= args.warmup:
             ts.append(t)
     t_step = statistics.median(ts) if ts else t
@@ -563,8 +659,8 @@ def run_reference(args, rank, world):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
            "config": {"workload": ob.desc, "k_int": ob.k_int, "k_b": ob.k_b,
                       "instances": ob.ninst},
-           "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": 1, "kind": "oracle",
-                            "sample": ob.sample_text()},
+           "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": ob.threads,
+                            "kind": "oracle", "sample": ob.sample_text(), **host_info()},
            "e2e": {"value": v, "unit": "candidates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0},
            "preprocess_s": ob.t_pre, "wall_s": time.perf_counter() - t0}
@@ -637,24 +733,17 @@ def time_to_gap(args):
         k_int, k_b, max_trig = 50, 1024, args.gap_triggers
         insts = [W.assign3d(I=64, idx=q) for q in range(5)]
         kw = dict(k_int=k_int, k_b=k_b, seed=0x5EED0003, x0=0.5)
-        # training data: plain runs on seeded I=32 instances (bounded time)
-        t0 = time.perf_counter()
-        feats, labels, ntr = [], [], 0
-        while ntr < args.train_instances and time.perf_counter() - t0 < args.train_budget:
-            batch = [W.assign3d(I=32, idx=20000 + ntr + q) for q in range(8)]
-            f, y = PR.collect(batch, dict(k_b=k_b, seed=0x5EED0003, x0=0.5), 500, k_int)
-            feats.append(f)
-            labels.append(y)
-            ntr += len(batch)
-        t_col = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        Wt, hist = PR.train(np.concatenate(feats), np.concatenate(labels), epochs=3)
-        train_info = {"instances": ntr, "rows": int(sum(len(y) for y in labels)),
-                      "collect_s": t_col, "train_s": time.perf_counter() - t0,
-                      "loss_per_epoch": hist,
-                      "source": "plain runs, 500 iterations each, axial I=32 seeds 20000+"}
+        Wt, train_info = PR.train_for("assign3d", args.train_instances, args.train_budget)
         zref = None                    # plain's best at its full budget (below)
         desc = "axial 3D assignment I=64, seeds 0-4, k_int=50, k_b=1024"
+    elif args.workload == "facility":
+        k_int, k_b, max_trig = 50, 256, args.gap_triggers
+        insts = [W.facility_location(1000, 10000, idx=q) for q in range(16)]
+        kw = dict(k_int=k_int, k_b=k_b, k_r=4, seed=0x5EED0004, x0=0.5)
+        Wt, train_info = PR.train_for("facility", args.train_instances, args.train_budget)
+        zref = None
+        desc = ("16 facility-location instances 1000 x 10000, seeds 0-15, k_int=50, "
+                "4 rounds x 256 candidates")
     else:
         k_int, k_b, max_trig = 50, 4096, args.gap_triggers
         insts = W.knapsack_batch(ninst=512)[:args.gap_instances]
@@ -681,7 +770,11 @@ def time_to_gap(args):
     if zref is None:
         zref = best_plain
     res = {}
-    arms = [("batched_plain", 0, insts), ("learned_batched", 2, insts)]
+    # the learned form: every round draws the plain form's candidates from
+    # x_k and as many again from the network (proposal 3); split rounds
+    # (proposal 2, half of each) are reported beside it
+    arms = [("batched_plain", 0, insts), ("learned_batched", 3, insts),
+            ("learned_split_batched", 2, insts)]
     if args.workload == "assign3d":
         # the paper's own sampler (Algorithm 4) on the same instances, batched
         arms.append(("alg4_batched", 0, [W.assign3d(I=64, idx=q, sampler="alg4")
@@ -711,7 +804,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="maxcut", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="facility", choices=list(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--instances", type=int, default=0,
                     help="use only the first N instances of a batch workload")
@@ -721,7 +814,10 @@ def main():
     ap.add_argument("--gap-triggers", type=int, default=100)
     ap.add_argument("--gap-instances", type=int, default=32)
     ap.add_argument("--train-instances", type=int, default=2000)
-    ap.add_argument("--train-budget", type=float, default=120.0)
+    ap.add_argument("--train-budget", type=float, default=400.0)
+    ap.add_argument("--train-instances-bench", type=int, default=64,
+                    help="training instances of the learned proposal in a throughput run")
+    ap.add_argument("--train-budget-bench", type=float, default=30.0)
     ap.add_argument("--profile-region", action="store_true",
                     help="cudaProfilerStart/Stop around the timed steps (for ncu "
                          "--profile-from-start off)")

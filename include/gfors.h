@@ -203,10 +203,13 @@ GFORS_API gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t n
 GFORS_API gfors_status gfors_pdhg_steps(gfors_handle h, int64_t nsteps);
 
 /* nrounds rounds of RandSampleStep + EvalBest (Alg. 1) on every instance,
- * proposal p = x_k (proposal 0), the attached learned network (1) or half of
- * each (2).  Round r uses Philox round id first_round_id + r.  Each round
- * scores k_b candidates on the ORIGINAL data (violation count, objective)
- * and updates the device incumbent.  Asynchronous. */
+ * proposal p = x_k (proposal 0), the attached learned network (1), half of
+ * each (2: the first half of every round from the network), or both (3:
+ * every round draws k_b candidates from x_k -- exactly those of proposal 0
+ * -- and then k_b from the network under round id | 2^31).  Round r uses
+ * Philox round id first_round_id + r.  Each round scores its candidates on
+ * the ORIGINAL data (violation count, objective) and updates the device
+ * incumbent.  Asynchronous. */
 GFORS_API gfors_status gfors_sample_eval(gfors_handle h, int32_t nrounds,
                                uint32_t first_round_id, int32_t proposal);
 
@@ -277,7 +280,8 @@ GFORS_API gfors_status gfors_get_samples(gfors_handle h, int32_t inst, uint8_t* 
 
 /* Learned proposal (an added pattern, no counterpart in the paper).
  * Weights of the per-variable MLP  h1 = relu(W1 f + b1), h2 = relu(W2 h1 +
- * b2), p = clip(sigmoid(w3 . h2 + b3), 1e-4, 1-1e-4), F = 8 features,
+ * b2), p = clip(sigmoid(w3 . h2 + b3), 2^-24, 1 - 2^-24) (the sampler's
+ * resolution: every variable keeps a draw weight floor(p 2^24) >= 1), F = 8 features,
  * H = 128 hidden units, packed as W1[H*F] b1[H] W2[H*H] b2[H] w3[H] b3[1]
  * (FP32 masters; the kernels round weights to bf16).  nW must equal
  * gfors_mlp_nparams(F, H). */
@@ -285,7 +289,13 @@ GFORS_API int64_t gfors_mlp_nparams(int32_t F, int32_t H);
 GFORS_API gfors_status gfors_set_proposal(gfors_handle h, const float* W, int64_t nW);
 
 /* Features of the learned proposal at the current iterate, FP32 [n x 8]
- * row-major into feat (host), for instance inst.  Synchronises. */
+ * row-major into feat (host), for instance inst: 1 standardised cost over
+ * the instance, 2 column degree / max degree, 3 x_k, 4 x_k - x at the
+ * previous call, 5 feature 1 minus its minimum over the variable's group
+ * (one-hot group or axial slab; the instance when ungrouped), 6 x_k / max of
+ * x_k over the group (x_k when ungrouped), 7 tau1 delta of the last primal
+ * step, 8 rho / rho_max.  Each call (and each learned sampling round)
+ * advances the previous-trigger snapshot of feature 4.  Synchronises. */
 GFORS_API gfors_status gfors_get_features(gfors_handle h, int32_t inst, float* feat);
 
 /* MLP kernels on caller DEVICE buffers (cuda_stream as in gfors_load):

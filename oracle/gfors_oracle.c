@@ -26,6 +26,26 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Multi-core build (test infrastructure: the CPU baseline's multi-core leg).
+ * Compiled with -fopenmp, the loops marked ORC_PAR_FOR run their iterations
+ * on all host threads.  Each marked loop writes disjoint outputs per
+ * iteration (one row, one sample) with unchanged per-element arithmetic,
+ * so both builds give identical results. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PAR_FOR
+#endif
+
+int32_t orc_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* ======================================================================
  * Philox4x32-10 counter-based generator, written from its published
  * definition (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
@@ -85,6 +105,7 @@ void orc_philox_lanes(uint64_t seed, uint32_t stream, uint32_t inst,
  * ====================================================================== */
 static void csr_mv(int64_t m, const int64_t* rp, const int32_t* ci,
                    const double* v, const double* x, double* out) {
+  ORC_PAR_FOR
   for (int64_t j = 0; j < m; ++j) {
     double s = 0.0;
     for (int64_t t = rp[j]; t < rp[j + 1]; ++t) s += v[t] * x[ci[t]];
@@ -104,6 +125,7 @@ static void q_mv(int qkind, int64_t n, const double* Qd, const int64_t* Qp,
                  const int32_t* Qc, const double* Qv, const double* x,
                  double* out) {
   if (qkind == 1) {
+    ORC_PAR_FOR
     for (int64_t i = 0; i < n; ++i) {
       double s = 0.0;
       for (int64_t j = 0; j < n; ++j) s += Qd[i * n + j] * x[j];
@@ -272,6 +294,7 @@ void orc_pdhg_step(int64_t n, int64_t m, int64_t m1, const int64_t* Kp,
   double* KTy = malloc(sizeof(double) * (n > 0 ? n : 1));
   double* Qx = malloc(sizeof(double) * (n > 0 ? n : 1));
   csr_mv(m, Kp, Kc, Kv, xbar_prev, Kx);
+  ORC_PAR_FOR
   for (int64_t j = 0; j < m; ++j) {
     double yj = y[j] + tau2 * (Kx[j] + r[j]);
     if (j < m1 && yj < 0.0) yj = 0.0;
@@ -279,6 +302,7 @@ void orc_pdhg_step(int64_t n, int64_t m, int64_t m1, const int64_t* Kp,
   }
   csr_mtv(m, n, Kp, Kc, Kv, y, KTy);
   q_mv(qkind, n, Qd, Qp, Qc, Qv, x_prev, Qx);
+  ORC_PAR_FOR
   for (int64_t i = 0; i < n; ++i) {
     double delta = c[i] + rho + KTy[i] + 2.0 * Qx[i] - 2.0 * rho * x_prev[i];
     double xi = x_prev[i] - tau1 * delta;
@@ -309,6 +333,7 @@ static uint32_t prob_threshold(float p) {
 void orc_bernoulli_from(int64_t n, int32_t first, int32_t k, const float* p, uint64_t seed,
                         uint32_t inst, uint32_t round_id, const uint8_t* mask,
                         uint8_t* X) {
+  ORC_PAR_FOR
   for (int32_t r = 0; r < k; ++r)
     for (int64_t i = 0; i < n; ++i) {
       if (mask && mask[i]) continue;
@@ -350,6 +375,7 @@ static int64_t categorical_pick(int64_t len, const int64_t* idx, const float* p,
 void orc_onehot(int64_t n, int64_t ngroups, const int64_t* gp,
                 const int64_t* gi, int32_t k, const float* p, uint64_t seed,
                 uint32_t inst, uint32_t round_id, uint8_t* X) {
+  ORC_PAR_FOR
   for (int32_t s = 0; s < k; ++s)
     for (int64_t g = 0; g < ngroups; ++g) {
       int64_t len = gp[g + 1] - gp[g];
@@ -490,6 +516,7 @@ void orc_assign3d_custom(int32_t I, int32_t gamma, int32_t L, int32_t k, const f
  * costs are non-negative. */
 void orc_closure(int64_t n, int64_t nrep, const int64_t* rv, const int64_t* rp,
                  const int64_t* ri, int32_t k, uint8_t* X) {
+  ORC_PAR_FOR
   for (int32_t s = 0; s < k; ++s)
     for (int64_t q = 0; q < nrep; ++q) {
       uint8_t v = X[(int64_t)s * n + rv[q]];
@@ -506,6 +533,7 @@ void orc_closure(int64_t n, int64_t nrep, const int64_t* rv, const int64_t* rp,
  * a member can violate no other constraint (the caller's claim). */
 void orc_repair_min(int64_t n, int64_t ng, const int64_t* gp, const int64_t* gi,
                     const int64_t* cost, int32_t k, uint8_t* X) {
+  ORC_PAR_FOR
   for (int32_t s = 0; s < k; ++s) {
     uint8_t* x = X + (int64_t)s * n;
     for (int64_t g = 0; g < ng; ++g) {
@@ -532,6 +560,7 @@ void orc_eval_int(int64_t n, int64_t m1, const int64_t* Ap, const int32_t* Ac,
                   const int64_t* Qp, const int32_t* Qc, const int64_t* Qv,
                   const int64_t* c, int32_t k, const uint8_t* X, int32_t* viol,
                   int64_t* obj) {
+  ORC_PAR_FOR
   for (int32_t s = 0; s < k; ++s) {
     const uint8_t* x = X + (int64_t)s * n;
     int32_t v = 0;
@@ -572,6 +601,7 @@ void orc_eval_f64(int64_t n, int64_t m1, const int64_t* Ap, const int32_t* Ac,
                   const int64_t* Qp, const int32_t* Qc, const double* Qv,
                   const double* c, int32_t k, const uint8_t* X, int32_t* viol,
                   double* obj) {
+  ORC_PAR_FOR
   for (int32_t s = 0; s < k; ++s) {
     const uint8_t* x = X + (int64_t)s * n;
     int32_t v = 0;
@@ -766,7 +796,9 @@ double orc_knapsack_lp(int64_t n, const double* w, const double* p, double cap,
 /* ======================================================================
  * Learned proposal (an added pattern; the paper has none): per-variable MLP
  *   h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), z = w3 . h2 + b3,
- *   p  = clip(sigmoid(z), 1e-4, 1 - 1e-4)
+ *   p  = clip(sigmoid(z), 2^-24, 1 - 2^-24)
+ * (the clip bounds are the Bernoulli / categorical threshold's resolution:
+ * every probability keeps a weight floor(p 2^24) of at least 1)
  * with F inputs, H hidden units; weights (not biases, not activations)
  * rounded to bf16 by round-to-nearest-even when round_bf16 != 0, computed
  * in FP64.  Weight layout: W1 [H x F] row-major, W2 [H x H] row-major.
@@ -814,8 +846,8 @@ void orc_mlp_forward(int64_t nv, int32_t F, int32_t H, const float* feat,
     double z = b3[0];
     for (int32_t a = 0; a < H; ++a) z += wq(w3, a, rb) * h2[a];
     double p = 1.0 / (1.0 + exp(-z));
-    if (p < 1e-4) p = 1e-4;
-    if (p > 1.0 - 1e-4) p = 1.0 - 1e-4;
+    if (p < 0x1p-24) p = 0x1p-24;
+    if (p > 1.0 - 0x1p-24) p = 1.0 - 0x1p-24;
     z_out[v] = z;
     p_out[v] = p;
     if (h1_out) memcpy(h1_out + v * H, h1, sizeof(double) * H);

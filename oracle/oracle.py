@@ -1,8 +1,10 @@
 """ctypes front end of the FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
 
 Only tests/, the smoke check and the benchmark's CPU-baseline leg import this
-module.  It loads oracle/liboracle.so (plain C, FP64, single thread) and
-strings its routines together in the order of Alg. 1:
+module.  It loads oracle/liboracle.so (plain C, FP64, single thread; or,
+after use_threads(True), the same source built with OpenMP over rows and
+samples, which gives identical results) and strings its routines together in
+the order of Alg. 1:
 
     Preprocess (Section 3) -> loop { UpdatePenalty; FirstOrderStep (Alg. 2);
     every k_int iterations k_r rounds of RandSampleStep (Alg. 3 or the
@@ -26,6 +28,7 @@ import scipy.sparse as sp
 from . import build as _build
 
 _lib = None
+_libs = {}
 
 F64P = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 F32P = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
@@ -37,63 +40,77 @@ VP = C.c_void_p
 i64, i32, u32, u64, f64 = C.c_int64, C.c_int32, C.c_uint32, C.c_uint64, C.c_double
 
 
-def lib():
+def use_threads(on: bool) -> int:
+    """Select the multi-core build (all host threads, identical results)
+    or the single-thread reference build for later calls; returns the
+    number of threads the selected build uses."""
     global _lib
+    if (on, ) not in _libs:
+        _libs[(on, )] = _load(_build.build(omp=on))
+    _lib = _libs[(on, )]
+    return int(_lib.orc_threads())
+
+
+def lib():
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        L.orc_philox4x32_10.argtypes = [U32P, U32P, U32P]
-        L.orc_philox_lane.argtypes = [u64, u32, u32, u32, u32, u64]
-        L.orc_philox_lane.restype = u32
-        L.orc_repair_min.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
-        L.orc_bernoulli_from.argtypes = [i64, i32, i32, F32P, u64, u32, u32, VP, U8P]
-        L.orc_philox_lanes.argtypes = [u64, u32, u32, u32, u32, i64, U32P]
-        L.orc_row_normalize.argtypes = [i64, i64, I64P, F64P, F64P, F64P]
-        L.orc_row_normalize.restype = i64
-        L.orc_power_norm_K.argtypes = [i64, i64, I64P, I32P, F64P, u64, u32, f64, i32,
-                                       C.POINTER(i32)]
-        L.orc_power_norm_K.restype = f64
-        L.orc_power_norm_Q.argtypes = [i32, i64, VP, VP, VP, VP, u64, u32, f64, i32,
-                                       C.POINTER(i32)]
-        L.orc_power_norm_Q.restype = f64
-        L.orc_step_sizes.argtypes = [f64, f64, f64, i32, C.POINTER(f64), C.POINTER(f64)]
-        L.orc_rho_update.argtypes = [i64, f64, f64, f64, f64, f64, f64]
-        L.orc_rho_update.restype = f64
-        L.orc_pdhg_step.argtypes = [i64, i64, i64, I64P, I32P, F64P, F64P, i32, VP, VP,
-                                    VP, VP, F64P, f64, f64, f64, F64P, F64P, F64P, F64P,
-                                    F64P, VP]
-        L.orc_bernoulli.argtypes = [i64, i32, F32P, u64, u32, u32, VP, U8P]
-        L.orc_onehot.argtypes = [i64, i64, I64P, I64P, i32, F32P, u64, u32, u32, U8P]
-        L.orc_axial3d.argtypes = [i32, i32, F32P, u64, u32, u32, U8P]
-        L.orc_assign3d_custom.argtypes = [i32, i32, i32, i32, F32P, I64P, u64, u32, u32,
-                                          U8P]
-        L.orc_closure.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
-        L.orc_eval_int.argtypes = [i64, i64, I64P, I32P, I64P, I64P, i64, I64P, I32P, I64P,
-                                   I64P, i32, VP, VP, VP, VP, I64P, i32, U8P, I32P, I64P]
-        L.orc_eval_f64.argtypes = [i64, i64, I64P, I32P, F64P, F64P, i64, I64P, I32P, F64P,
-                                   F64P, i32, VP, VP, VP, VP, F64P, i32, U8P, I32P, F64P]
-        L.orc_incumbent_update.argtypes = [i32, I32P, I64P, u32, C.POINTER(i32),
-                                           C.POINTER(i64), C.POINTER(u32), C.POINTER(i32)]
-        L.orc_incumbent_update.restype = i32
-        L.orc_round.argtypes = [i64, F64P, U8P]
-        L.orc_halt_stats.argtypes = [i64, i64, i64, I64P, I32P, F64P, F64P, i32, VP, VP, VP,
-                                     VP, F64P, f64, f64, F64P, F64P, F64P, F64P]
-        L.orc_brute_force.argtypes = [i64, i64, I64P, I32P, I64P, I64P, i64, I64P, I32P,
-                                      I64P, I64P, i32, VP, VP, VP, VP, I64P,
-                                      C.POINTER(i64), U8P, C.POINTER(i64)]
-        L.orc_brute_force.restype = i32
-        L.orc_knapsack_lp.argtypes = [i64, F64P, F64P, f64, F64P]
-        L.orc_knapsack_lp.restype = f64
-        L.orc_bf16_round.argtypes = [C.c_float]
-        L.orc_bf16_round.restype = C.c_float
-        L.orc_mlp_forward.argtypes = [i64, i32, i32, F32P, F32P, F32P, F32P, F32P, F32P,
-                                      F32P, i32, F64P, F64P, VP, VP]
-        L.orc_mlp_loss_grad.argtypes = [i64, i32, i32, F32P, F32P, F32P, F32P, F32P, F32P,
-                                        F32P, F32P, i32, F64P, F64P, F64P, F64P, F64P, F64P]
-        L.orc_mlp_loss_grad.restype = f64
-        L.orc_adam.argtypes = [i64, F32P, F64P, F64P, F64P, i64, f64, f64, f64, f64]
-        _lib = L
+        use_threads(False)
     return _lib
+
+
+def _load(path):
+    L = C.CDLL(path)
+    L.orc_threads.restype = i32
+    L.orc_philox4x32_10.argtypes = [U32P, U32P, U32P]
+    L.orc_philox_lane.argtypes = [u64, u32, u32, u32, u32, u64]
+    L.orc_philox_lane.restype = u32
+    L.orc_repair_min.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
+    L.orc_bernoulli_from.argtypes = [i64, i32, i32, F32P, u64, u32, u32, VP, U8P]
+    L.orc_philox_lanes.argtypes = [u64, u32, u32, u32, u32, i64, U32P]
+    L.orc_row_normalize.argtypes = [i64, i64, I64P, F64P, F64P, F64P]
+    L.orc_row_normalize.restype = i64
+    L.orc_power_norm_K.argtypes = [i64, i64, I64P, I32P, F64P, u64, u32, f64, i32,
+                                   C.POINTER(i32)]
+    L.orc_power_norm_K.restype = f64
+    L.orc_power_norm_Q.argtypes = [i32, i64, VP, VP, VP, VP, u64, u32, f64, i32,
+                                   C.POINTER(i32)]
+    L.orc_power_norm_Q.restype = f64
+    L.orc_step_sizes.argtypes = [f64, f64, f64, i32, C.POINTER(f64), C.POINTER(f64)]
+    L.orc_rho_update.argtypes = [i64, f64, f64, f64, f64, f64, f64]
+    L.orc_rho_update.restype = f64
+    L.orc_pdhg_step.argtypes = [i64, i64, i64, I64P, I32P, F64P, F64P, i32, VP, VP,
+                                VP, VP, F64P, f64, f64, f64, F64P, F64P, F64P, F64P,
+                                F64P, VP]
+    L.orc_bernoulli.argtypes = [i64, i32, F32P, u64, u32, u32, VP, U8P]
+    L.orc_onehot.argtypes = [i64, i64, I64P, I64P, i32, F32P, u64, u32, u32, U8P]
+    L.orc_axial3d.argtypes = [i32, i32, F32P, u64, u32, u32, U8P]
+    L.orc_assign3d_custom.argtypes = [i32, i32, i32, i32, F32P, I64P, u64, u32, u32,
+                                      U8P]
+    L.orc_closure.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
+    L.orc_eval_int.argtypes = [i64, i64, I64P, I32P, I64P, I64P, i64, I64P, I32P, I64P,
+                               I64P, i32, VP, VP, VP, VP, I64P, i32, U8P, I32P, I64P]
+    L.orc_eval_f64.argtypes = [i64, i64, I64P, I32P, F64P, F64P, i64, I64P, I32P, F64P,
+                               F64P, i32, VP, VP, VP, VP, F64P, i32, U8P, I32P, F64P]
+    L.orc_incumbent_update.argtypes = [i32, I32P, I64P, u32, C.POINTER(i32),
+                                       C.POINTER(i64), C.POINTER(u32), C.POINTER(i32)]
+    L.orc_incumbent_update.restype = i32
+    L.orc_round.argtypes = [i64, F64P, U8P]
+    L.orc_halt_stats.argtypes = [i64, i64, i64, I64P, I32P, F64P, F64P, i32, VP, VP, VP,
+                                 VP, F64P, f64, f64, F64P, F64P, F64P, F64P]
+    L.orc_brute_force.argtypes = [i64, i64, I64P, I32P, I64P, I64P, i64, I64P, I32P,
+                                  I64P, I64P, i32, VP, VP, VP, VP, I64P,
+                                  C.POINTER(i64), U8P, C.POINTER(i64)]
+    L.orc_brute_force.restype = i32
+    L.orc_knapsack_lp.argtypes = [i64, F64P, F64P, f64, F64P]
+    L.orc_knapsack_lp.restype = f64
+    L.orc_bf16_round.argtypes = [C.c_float]
+    L.orc_bf16_round.restype = C.c_float
+    L.orc_mlp_forward.argtypes = [i64, i32, i32, F32P, F32P, F32P, F32P, F32P, F32P,
+                                  F32P, i32, F64P, F64P, VP, VP]
+    L.orc_mlp_loss_grad.argtypes = [i64, i32, i32, F32P, F32P, F32P, F32P, F32P, F32P,
+                                    F32P, F32P, i32, F64P, F64P, F64P, F64P, F64P, F64P]
+    L.orc_mlp_loss_grad.restype = f64
+    L.orc_adam.argtypes = [i64, F32P, F64P, F64P, F64P, i64, f64, f64, f64, f64]
+    return L
 
 
 def _ptr(a):

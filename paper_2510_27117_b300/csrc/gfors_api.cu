@@ -374,6 +374,23 @@ static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal, i
     if ((e = gf_launch_mlp_proposal(h))) return gf_cuda(h, e, "learned proposal");
   }
   const int kb = h->prm.k_b;
+  if (proposal == 3) {
+    // every round twice: from x_k under its own id (the candidates of
+    // proposal 0), then from the network under id | 2^31 (disjoint Philox
+    // counters); the plain sampler stays complete in every round
+    for (int r = 0; r < nrounds; ++r) {
+      const unsigned rid = h->host_round;
+      if ((e = enqueue_round(h, xk, xk, kb, sb, se))) return gf_cuda(h, e, "sampling round");
+      k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, rid | 0x80000000u);
+      h->host_round = rid | 0x80000000u;
+      if ((e = enqueue_round(h, h->p_learn, xk, kb, sb, se)))
+        return gf_cuda(h, e, "sampling round");
+      k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, rid + 1);
+      h->host_round = rid + 1;
+      h->launches += 2;
+    }
+    return GFORS_OK;
+  }
   // proposal 2: first half of every round from the network, second half
   // from x_k (rounded to the 32-candidate word)
   const int split = (proposal == 2) ? std::max(32, (kb / 2) / 32 * 32) : kb;
@@ -388,7 +405,7 @@ static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal, i
 extern "C" gfors_status gfors_sample_eval(gfors_handle h, int32_t nrounds,
                                           uint32_t first_round_id, int32_t proposal) {
   GF_ENTER(h);
-  if (nrounds < 0 || proposal < 0 || proposal > 2)
+  if (nrounds < 0 || proposal < 0 || proposal > 3)
     return gf_fail(h, GFORS_E_ARG, "bad nrounds / proposal");
   k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, first_round_id);
   h->launches++;
@@ -424,7 +441,7 @@ extern "C" gfors_status gfors_sample_eval_range(gfors_handle h, int32_t nrounds,
                                                 uint32_t first_round_id, int32_t proposal,
                                                 int32_t s_begin, int32_t s_end) {
   GF_ENTER(h);
-  if (nrounds < 0 || proposal < 0 || proposal > 2)
+  if (nrounds < 0 || proposal < 0 || proposal > 3)
     return gf_fail(h, GFORS_E_ARG, "bad nrounds / proposal");
   if (s_begin < 0 || s_end > h->prm.k_b || s_begin >= s_end || s_begin % 32 || s_end % 32)
     return gf_fail(h, GFORS_E_ARG, "need 0 <= s_begin < s_end <= k_b, multiples of 32");
@@ -590,7 +607,7 @@ static bool halt_update(GfCtx* h, const std::vector<double>& st) {
 extern "C" gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time_budget_s,
                                   int32_t proposal, int64_t* iters_out) {
   GF_ENTER(h);
-  if (max_iters < 0 || proposal < 0 || proposal > 2)
+  if (max_iters < 0 || proposal < 0 || proposal > 3)
     return gf_fail(h, GFORS_E_ARG, "bad max_iters / proposal");
   const auto t0 = std::chrono::steady_clock::now();
   const int kint = h->prm.k_int;
@@ -915,6 +932,7 @@ extern "C" gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t m
     return gf_fail(h, GFORS_E_ARG, "mode must be 0, 1 or 2");
   }
   h->n_bit_g4 = -1;                      // Bernoulli group list rebuilt
+  h->grp_version++;                      // static features rebuilt
   if ((e = cudaMemcpy(h->var_grouped + I.var_off, grouped.data(), I.npad,
                       cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->var_grouped_feat + I.var_off, grouped.data(), I.npad,
@@ -962,6 +980,7 @@ extern "C" gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, 
   for (int64_t i = 0; i < I.n; ++i) grouped[i] = 1;
   cudaError_t e;
   h->n_bit_g4 = -1;                      // Bernoulli group list rebuilt
+  h->grp_version++;                      // static features rebuilt
   if ((e = cudaMemcpy(h->var_grouped + I.var_off, grouped.data(), I.npad,
                       cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->var_grouped_feat + I.var_off, grouped.data(), I.npad,

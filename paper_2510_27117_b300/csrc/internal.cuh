@@ -273,9 +273,9 @@ struct gfors_ctx {
   float* mlp_W = nullptr;
   int64_t mlp_np = 0;
   float* feat = nullptr;            // N x 8
-  float* x_hist = nullptr;          // N x 4 ring of trigger snapshots
   float* x_trig_prev = nullptr;     // x at the previous trigger
-  int hist_count = 0;
+  float* crel = nullptr;            // N: cstd - min of cstd over the variable's group
+  long long feat_grp_version = -1;  // group tables the static features were built for
   float* p_learn = nullptr;         // N
   float* dlast = nullptr;           // tau1 * delta of the last step (N)
   float* degnorm = nullptr;         // column degree / max (N)
@@ -283,7 +283,7 @@ struct gfors_ctx {
   float* grpmax = nullptr;          // N: max_{group} x (scratch)
   float* p_learn_z = nullptr;       // N: logits of the learned proposal
   uint8_t* var_grouped_feat = nullptr;  // N: 1 if in a one-hot group / axial slab
-  int hist_ring = 0;                // triggers pushed into x_hist
+  long long grp_version = 0;        // bumped whenever groups change
 
   // CUDA graphs of one PDHG iteration pair, by parity of its first iteration
   cudaGraphExec_t g_pair = nullptr;

@@ -6,7 +6,7 @@
 // plain form kept as fallback and reference.
 //
 //   h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), z = w3 . h2 + b3,
-//   p  = clip(sigmoid(z), 1e-4, 1 - 1e-4).
+//   p  = clip(sigmoid(z), 2^-24, 1 - 2^-24).
 // Weights (not biases, not activations) are rounded to bf16 (round to
 // nearest even) when staged; arithmetic is FP32.  Gradients are taken with
 // respect to the FP32 masters, the rounding passed straight through.  The
@@ -253,10 +253,12 @@ __global__ void k_adam(int64_t np, float* __restrict__ w, const float* __restric
 }
 
 // ---- features -----------------------------------------------------------
-// 1 standardised cost, 2 column degree / max degree, 3 x_k, 4 x_k - x at the
-// previous trigger, 5 mean of x over the last (up to) 4 triggers, 6 x / max
-// of x over the variable's group (x itself when ungrouped), 7 tau1 delta of
-// the last primal step, 8 rho / rho_max.
+// 1 standardised cost (c_hat - mean) / sd over the instance, 2 column degree
+// / max degree, 3 x_k, 4 x_k - x at the previous trigger, 5 the standardised
+// cost above the cheapest member of the variable's group (one-hot group or
+// axial slab x_i**; the whole instance when ungrouped), 6 x / max of x over
+// the variable's group (x itself when ungrouped), 7 tau1 delta of the last
+// primal step, 8 rho / rho_max.
 __global__ void k_group_max(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
                             int64_t ngroups, const float* __restrict__ x,
                             float* __restrict__ gmax) {
@@ -286,7 +288,7 @@ __global__ void k_slab_max(const float* __restrict__ x, int64_t v0, int I,
 }
 
 __global__ void k_features(int64_t N, const float* __restrict__ x, const float* __restrict__ xprev_trig,
-                           const float* __restrict__ hist, int hist_count,
+                           const float* __restrict__ crel,
                            const float* __restrict__ cstd, const float* __restrict__ degn,
                            const float* __restrict__ gmax, const uint8_t* __restrict__ grouped,
                            const float* __restrict__ dlast, const uint8_t* __restrict__ live,
@@ -299,17 +301,11 @@ __global__ void k_features(int64_t N, const float* __restrict__ x, const float* 
     for (int q = 0; q < kF; ++q) f[q] = 0.0f;
   } else {
     const float xi = x[i];
-    float mean = xi;
-    if (hist_count > 0) {
-      float s = 0.0f;
-      for (int q = 0; q < hist_count; ++q) s += hist[(int64_t)q * N + i];
-      mean = s / (float)hist_count;
-    }
     f[0] = cstd[i];
     f[1] = degn[i];
     f[2] = xi;
     f[3] = xi - xprev_trig[i];
-    f[4] = mean;
+    f[4] = crel[i];
     f[5] = grouped[i] ? (gmax[i] > 0.0f ? xi / gmax[i] : 0.0f) : xi;
     f[6] = dlast[i];
     f[7] = rho_frac;
@@ -426,20 +422,23 @@ extern "C" gfors_status gfors_mlp_adam(int64_t np, float* W_dev, const float* gr
 
 // ---- solver integration ---------------------------------------------------
 static cudaError_t ensure_feature_buffers(GfCtx* h) {
-  if (h->feat) return cudaSuccess;
+  if (h->feat && h->feat_grp_version == h->grp_version) return cudaSuccess;
   const int64_t N = h->N;
-  h->feat = gf_alloc_t<float>(h, (size_t)N * kF);
-  h->x_hist = gf_alloc_t<float>(h, (size_t)N * 4);
-  h->x_trig_prev = gf_alloc_t<float>(h, N);
-  h->p_learn = gf_alloc_t<float>(h, N);
-  h->degnorm = gf_alloc_t<float>(h, N);
-  h->cstd = gf_alloc_t<float>(h, N);
-  h->grpmax = gf_alloc_t<float>(h, N);
-  if (!h->feat || !h->x_hist || !h->x_trig_prev || !h->p_learn || !h->degnorm || !h->cstd ||
-      !h->grpmax)
-    return cudaErrorMemoryAllocation;
-  // static features: standardised cost and normalised column degree
-  std::vector<float> cs(N, 0.0f), dg(N, 0.0f);
+  if (!h->feat) {
+    h->feat = gf_alloc_t<float>(h, (size_t)N * kF);
+    h->x_trig_prev = gf_alloc_t<float>(h, N);
+    h->p_learn = gf_alloc_t<float>(h, N);
+    h->degnorm = gf_alloc_t<float>(h, N);
+    h->cstd = gf_alloc_t<float>(h, N);
+    h->crel = gf_alloc_t<float>(h, N);
+    h->grpmax = gf_alloc_t<float>(h, N);
+    if (!h->feat || !h->x_trig_prev || !h->p_learn || !h->degnorm || !h->cstd || !h->crel ||
+        !h->grpmax)
+      return cudaErrorMemoryAllocation;
+  }
+  // static features: standardised cost, normalised column degree, and the
+  // standardised cost above its group's cheapest member
+  std::vector<float> cs(N, 0.0f), dg(N, 0.0f), cr(N, 0.0f);
   std::vector<float> chat(N);
   std::vector<int64_t> Tp(N + 1), Qp(N + 1);
   cudaError_t e;
@@ -461,21 +460,43 @@ static cudaError_t ensure_feature_buffers(GfCtx* h) {
       dmax = std::max(dmax, deg);
     }
     sd = sqrt(sd / (double)I.n);
+    float cmin = INFINITY;
     for (int64_t i = 0; i < I.n; ++i) {
       const int64_t v = I.var_off + i;
       cs[v] = sd > 0.0 ? (float)((chat[v] - mu) / sd) : 0.0f;
+      cmin = std::min(cmin, cs[v]);
       const int64_t deg = (Tp[v + 1] - Tp[v]) + (Qp[v + 1] - Qp[v]) + (I.qkind == 1 ? I.n : 0);
       dg[v] = (float)deg / (float)dmax;
     }
+    for (int64_t i = 0; i < I.n; ++i) cr[I.var_off + i] = cs[I.var_off + i] - cmin;
+    if ((I.group_mode == 2 || I.group_mode == 3) && I.axial_I > 0) {
+      const int64_t P = (int64_t)I.axial_I * I.axial_I;        // slab x_i** of the axial form
+      for (int64_t a = 0; a < I.axial_I; ++a) {
+        const int64_t v0 = I.var_off + a * P;
+        float m = INFINITY;
+        for (int64_t q = 0; q < P; ++q) m = std::min(m, cs[v0 + q]);
+        for (int64_t q = 0; q < P; ++q) cr[v0 + q] = cs[v0 + q] - m;
+      }
+    }
+  }
+  for (int64_t g = 0; g < h->ngroups_tot; ++g) {             // one-hot groups
+    float m = INFINITY;
+    for (int64_t t = h->h_grp_ptr[g]; t < h->h_grp_ptr[g + 1]; ++t)
+      m = std::min(m, cs[h->h_grp_idx[t]]);
+    for (int64_t t = h->h_grp_ptr[g]; t < h->h_grp_ptr[g + 1]; ++t)
+      cr[h->h_grp_idx[t]] = cs[h->h_grp_idx[t]] - m;
   }
   if ((e = cudaMemcpy(h->cstd, cs.data(), sizeof(float) * N, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(h->degnorm, dg.data(), sizeof(float) * N, cudaMemcpyHostToDevice)))
+      (e = cudaMemcpy(h->degnorm, dg.data(), sizeof(float) * N, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->crel, cr.data(), sizeof(float) * N, cudaMemcpyHostToDevice)))
     return e;
-  const float* xk = h->x[h->k_host & 1];
-  if ((e = cudaMemcpyAsync(h->x_trig_prev, xk, sizeof(float) * N, cudaMemcpyDeviceToDevice,
-                           h->stream)))
-    return e;
-  h->hist_count = 0;
+  if (h->feat_grp_version < 0) {
+    const float* xk = h->x[h->k_host & 1];
+    if ((e = cudaMemcpyAsync(h->x_trig_prev, xk, sizeof(float) * N, cudaMemcpyDeviceToDevice,
+                             h->stream)))
+      return e;
+  }
+  h->feat_grp_version = h->grp_version;
   return cudaSuccess;
 }
 
@@ -487,13 +508,6 @@ cudaError_t gf_launch_features(GfCtx* h) {
   const int64_t N = h->N;
   cudaStream_t s = h->stream;
   const float* xk = h->x[h->k_host & 1];
-  // trigger history ring (slot = count mod 4)
-  const int slot = h->hist_ring % 4;
-  if ((e = cudaMemcpyAsync(h->x_hist + (int64_t)slot * N, xk, sizeof(float) * N,
-                           cudaMemcpyDeviceToDevice, s)))
-    return e;
-  h->hist_ring++;
-  h->hist_count = std::min(4, h->hist_ring);
   if (h->ngroups_tot)
     k_group_max<<<(unsigned)((h->ngroups_tot * 32 + 255) / 256), 256, 0, s>>>(
         h->grp_ptr, h->grp_idx, h->ngroups_tot, xk, h->grpmax);
@@ -503,7 +517,7 @@ cudaError_t gf_launch_features(GfCtx* h) {
                                                   h->grpmax);
   const float rf = (float)(h->prm.rho_max > 0 ? h->rho_host / h->prm.rho_max : 0.0);
   k_features<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
-      N, xk, h->x_trig_prev, h->x_hist, h->hist_count, h->cstd, h->degnorm, h->grpmax,
+      N, xk, h->x_trig_prev, h->crel, h->cstd, h->degnorm, h->grpmax,
       h->var_grouped_feat, h->dlast, h->var_live, rf, h->feat);
   h->launches += 1 + (h->ngroups_tot ? 1 : 0);
   if ((e = cudaGetLastError())) return e;

@@ -2,7 +2,7 @@
 // 5th-generation tensor cores (tcgen05):
 //
 //   h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), z = w3 . h2 + b3,
-//   p  = clip(sigmoid(z), 1e-4, 1 - 1e-4)      (F = 8, H = 128),
+//   p  = clip(sigmoid(z), 2^-24, 1 - 2^-24)    (F = 8, H = 128),
 //
 // with the numerics of the CUDA-core kernel in k_mlp.cu: weights rounded to
 // bf16, every other quantity FP32.  The FP32 inputs of the two GEMMs (the
@@ -86,7 +86,8 @@ GF_DEV void split8_store(uint8_t* base0, uint8_t* base1, uint8_t* base2, int r, 
 
 GF_DEV float clip_sigmoid(float z) {
   const float p = 1.0f / (1.0f + expf(-z));
-  return fminf(fmaxf(p, 1e-4f), 1.0f - 1e-4f);
+  // bounds: the sampler's resolution (threshold floor(p 2^24) >= 1)
+  return fminf(fmaxf(p, 0x1p-24f), 1.0f - 0x1p-24f);
 }
 
 GF_DEV void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -87,3 +87,124 @@ def train(feat: np.ndarray, label: np.ndarray, epochs: int = 5, batch: int = 327
         hist.append(tot / cnt)
     torch.cuda.synchronize()
     return W.cpu().numpy(), hist
+
+
+def sharpen(W: np.ndarray, beta: float) -> np.ndarray:
+    """The same network sampled at temperature 1/beta: the output layer
+    (w3, b3) scaled by beta, so p = clip(sigmoid(beta z))."""
+    Wb = np.array(W, np.float32, copy=True)
+    Wb[H * F + H + H * H + H:] *= np.float32(beta)
+    return Wb
+
+
+# Training recipes of the bench workloads: small seeded instances of the
+# same family, plain runs (p = x_k) labelled by their incumbents, then Adam
+# on mean BCE, then the sampling temperature chosen on held-out instances
+# of the same family.  Seeds: training from 20000 (3D assignment) / 30000
+# (facility location), validation from 29000 / 39000; all disjoint from the
+# evaluation instances (seeds 0+).
+RECIPES = {
+    "assign3d": dict(make=lambda W, q: W.assign3d(I=32, idx=20000 + q),
+                     val=lambda W, q: W.assign3d(I=32, idx=29000 + q),
+                     prm=dict(k_b=1024, seed=0x5EED0003, x0=0.5), iters=2000, k_int=50,
+                     seeds=2, every=4,
+                     source="plain runs, 2000 iterations, best of 2 Philox seeds, features "
+                            "of every 4th trigger, axial I=32, seeds 20000+"),
+    "facility": dict(make=lambda W, q: W.facility_location(50, 500, idx=30000 + q),
+                     val=lambda W, q: W.facility_location(50, 500, idx=39000 + q),
+                     prm=dict(k_b=256, k_r=4, seed=0x5EED0004, x0=0.5), iters=2000, k_int=50,
+                     seeds=2, every=4,
+                     source="plain runs, 2000 iterations, best of 2 Philox seeds, features "
+                            "of every 4th trigger, facility location 50 x 500, seeds 30000+"),
+}
+BETAS = (1.0, 1.5, 2.0, 2.5, 3.0)
+
+
+def collect_best(instances, prm_kw: dict, iters: int, k_int: int, seeds: int, every: int = 1):
+    """As collect(), but every instance runs under `seeds` Philox seeds, the
+    features of every `every`-th trigger are recorded, and all of them are
+    labelled with the best incumbent found."""
+    feats, labels = [], []
+    for inst in instances:
+        best = None
+        for sd in range(seeds):
+            kw = dict(prm_kw)
+            kw["seed"] = prm_kw["seed"] + 17 * sd
+            prm = G.default_params(k_int=k_int, **kw)
+            h = G.load(inst, prm)
+            rec = []
+            rid = 0
+            for t in range(iters // k_int):
+                h.pdhg_steps(k_int)
+                f = h.get_features(0)
+                if t % every == 0:
+                    rec.append(f)
+                h.sample_eval(prm.k_r, rid, 0)
+                rid += prm.k_r
+            h.final_round()
+            inc = h.incumbent(0)
+            h.destroy()
+            if inc["found"] and (best is None or inc["obj"] < best[0]):
+                best = (inc["obj"], inc["x"].astype(np.float32), rec)
+        if best is not None:
+            feats.extend(best[2])
+            labels.extend([best[1]] * len(best[2]))
+    return np.concatenate(feats), np.concatenate(labels)
+
+
+def select_temperature(Wt: np.ndarray, kind: str, nval: int = 4, triggers: int = 10):
+    """Sampling temperature of the trained network: for each beta in BETAS,
+    learned-only rounds (proposal 1) on nval held-out instances for
+    `triggers` triggers; the beta with the least mean best objective (an
+    instance without a feasible candidate counts as +inf) is returned with
+    the scores."""
+    from . import workloads as W
+    R = RECIPES[kind]
+    scores = {}
+    for beta in BETAS:
+        Wb = sharpen(Wt, beta)
+        tot = 0.0
+        for q in range(nval):
+            prm = G.default_params(k_int=R["k_int"], **R["prm"])
+            h = G.load(R["val"](W, q), prm)
+            h.set_proposal(Wb)
+            for t in range(triggers):
+                h.pdhg_steps(R["k_int"])
+                h.sample_eval(prm.k_r, t * prm.k_r, 1)
+            inc = h.incumbent(0, want_x=False)
+            h.destroy()
+            tot += inc["obj"] if inc["found"] else float("inf")
+        scores[beta] = tot / nval
+    best = min(BETAS, key=lambda b: (scores[b], b))
+    return best, scores
+
+
+def train_for(kind: str, max_instances: int, budget_s: float, epochs: int = 3,
+              chunk: int = 8):
+    """Collect plain-run data on the recipe's seeded instances (until
+    max_instances or budget_s seconds), train, choose the sampling
+    temperature on held-out instances, and return (sharpened weights,
+    info)."""
+    import time
+    from . import workloads as W
+    R = RECIPES[kind]
+    t0 = time.perf_counter()
+    feats, labels, ntr = [], [], 0
+    while ntr < max_instances and time.perf_counter() - t0 < budget_s:
+        batch = [R["make"](W, ntr + q) for q in range(min(chunk, max_instances - ntr))]
+        f, y = collect_best(batch, R["prm"], R["iters"], R["k_int"], R["seeds"], R["every"])
+        feats.append(f)
+        labels.append(y)
+        ntr += len(batch)
+    t_col = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Wt, hist = train(np.concatenate(feats), np.concatenate(labels), epochs=epochs)
+    t_train = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    beta, scores = select_temperature(Wt, kind)
+    info = {"instances": ntr, "rows": int(sum(len(y) for y in labels)),
+            "collect_s": t_col, "train_s": t_train, "loss_per_epoch": hist,
+            "source": R["source"], "beta": beta,
+            "beta_val_mean_best": {str(b): v for b, v in scores.items()},
+            "select_s": time.perf_counter() - t0}
+    return sharpen(Wt, beta), info

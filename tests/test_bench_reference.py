@@ -36,6 +36,7 @@ def test_reference_line_contract():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert cb["unit"] == d["unit"] and cb["sample"]
+    assert cb["host_cores"] >= cb["cores"] and cb["cpu_count"] >= 1
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

@@ -70,7 +70,7 @@ def test_mlp_forward_many_tiles_matches_oracle():
     zo, po = O.mlp_forward(f[idx], _unpack(Wp), rb=1)
     assert np.all(np.abs(zg[idx] - zo) <= 1e-5 * (1 + np.abs(zo)))
     assert np.all(np.abs(pg[idx] - po) <= 1e-5)
-    assert np.all((pg >= 1e-4 - 1e-9) & (pg <= 1 - 1e-4 + 1e-9))
+    assert np.all((pg >= 2.0 ** -24) & (pg <= 1 - 2.0 ** -24))
 
 
 def test_mlp_gradient_matches_oracle():
@@ -128,7 +128,8 @@ def test_features_definitions():
     assert np.allclose(f2[:, 1], 1.0)           # every column has 3 nonzeros
     assert np.array_equal(f2[:, 2], x2)
     assert np.allclose(f2[:, 3], x2 - x1, atol=1e-7)
-    assert np.allclose(f2[:, 4], 0.5 * (x1.astype(np.float64) + x2), atol=1e-6)
+    # feature 5: standardised cost above the cheapest cell of its slab x_i**
+    assert np.allclose(f2[:, 4], cs - cs.reshape(6, 36).min(axis=1).repeat(36), atol=1e-5)
     slab = x2.reshape(6, 36).max(axis=1).repeat(36)
     assert np.allclose(f2[:, 5], x2 / slab, atol=1e-6)
     assert np.allclose(f2[:, 7], 0.25)
@@ -155,10 +156,10 @@ def test_learned_proposal_ablation(capsys):
     feat, lab = P.collect(train_insts, prm_kw, iters=400, k_int=20)
     Wt, hist = P.train(feat, lab, epochs=6, batch=8192, lr=2e-3, seed=1)
     assert hist[-1] < hist[0]
-    res = {0: [], 1: [], 2: []}
+    res = {0: [], 1: [], 2: [], 3: []}
     for q in range(4):
         inst = W.assign3d(I=10, idx=900 + q)
-        for mode in (0, 1, 2):
+        for mode in (0, 1, 2, 3):
             H = G.load(inst, G.default_params(k_int=20, **prm_kw))
             if mode:
                 H.set_proposal(Wt)
@@ -169,6 +170,44 @@ def test_learned_proposal_ablation(capsys):
             assert v[0] == 0 and o[0] == inc["obj"]
             res[mode].append(inc["obj"])
             H.destroy()
+    # proposal 3 draws every plain candidate and more: never worse than plain
+    assert all(b3 <= b0 for b0, b3 in zip(res[0], res[3]))
     with capsys.disabled():
         print(f"\n[ablation] loss {hist[0]:.4f} -> {hist[-1]:.4f}; best objective per "
-              f"held-out instance: plain {res[0]}, learned {res[1]}, split {res[2]}")
+              f"held-out instance: plain {res[0]}, learned {res[1]}, split {res[2]}, "
+              f"plain + learned {res[3]}")
+
+
+@pytest.mark.parametrize("name", ["setcover", "facloc"])
+def test_plain_plus_learned_rounds_bit_exact(name):
+    """Proposal 3: each round draws the candidates of proposal 0 (round id r)
+    and then k_b candidates from the network under round id r | 2^31.  With
+    every weight zero the network's p is sigmoid(0) = 1/2 exactly, so the
+    oracle reproduces the learned round; the incumbent is the oracle's
+    incumbent rule applied to the plain round, then the learned round."""
+    inst = (W.set_cover(n=500, m=60, density=0.05, idx=3) if name == "setcover"
+            else W.facility_location(nf=12, nc=40, idx=2))
+    k_b, seed, R = 96, 0x5EED0007, 13
+    H = G.load(inst, G.default_params(k_b=k_b, seed=seed, x0=0.5))
+    H.set_proposal(np.zeros(G.mlp_nparams(), np.float32))
+    rng = np.random.default_rng(5)
+    x = rng.random(inst.n).astype(np.float32)
+    H.set_iterate(0, x, x, None)
+    H.sample_eval(1, R, 3)
+    X, viol, obj = H.get_samples(0)             # the last round: the learned one
+    inc = H.incumbent(0)
+    H.destroy()
+    ev = O.Evaluator(inst)
+    Xl = O.sample(inst, np.full(inst.n, 0.5, np.float32), k_b, seed, 0, R | (1 << 31))
+    assert np.array_equal(X, Xl)
+    vl, ol = ev(Xl)
+    assert np.array_equal(viol, vl) and np.array_equal(obj, ol)
+    Xp = O.sample(inst, x, k_b, seed, 0, R)
+    vp, op = ev(Xp)
+    st = dict(found=0, obj=0, round=0, sample=-1)
+    O.incumbent_update(st, vp, op, R)
+    O.incumbent_update(st, vl, ol, R | (1 << 31))
+    assert inc["found"] == st["found"]
+    if st["found"]:
+        assert (inc["obj"], inc["round"], inc["sample"]) == (st["obj"], st["round"],
+                                                              st["sample"])

@@ -747,3 +747,32 @@ def test_fp64_evaluator_on_fractional_data():
         if kind == "outside":
             want = want + hit
         assert np.array_equal(viol, want)
+
+
+# ---------------------------------------------------------------- multi-core build
+def test_openmp_build_gives_identical_results():
+    """The multi-core oracle build (OpenMP over rows and samples, used only
+    for the CPU baseline's timing) returns exactly what the single-thread
+    reference build returns: PDHG steps, Bernoulli and one-hot sampling,
+    closure, repair and evaluation."""
+    insts = [W.set_cover(n=300, m=40, density=0.08, idx=2), W.max_cut(n=120, idx=3),
+             W.facility_location(nf=7, nc=30, idx=1),
+             W.facility_location(nf=9, nc=11, idx=2, relaxed=True)]
+    outs = []
+    for on in (False, True):
+        O.use_threads(on)
+        res = []
+        for inst in insts:
+            S = O.preprocess(inst, 5)
+            rng = np.random.default_rng(1)
+            x = rng.random(S.n)
+            y = rng.random(S.m)
+            t1, t2 = O.step_sizes(0.99, S.normQ, 0.1, S.qkind != 0)
+            res.append(O.pdhg_step(S, t1, t2, 0.1, x, x, y))
+            X = O.sample(inst, x.astype(np.float32), 96, 7, 0, 3)
+            res.append((X,) + O.Evaluator(inst)(X))
+        outs.append(res)
+    O.use_threads(False)
+    for a, b in zip(*outs):
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v)
