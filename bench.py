@@ -383,6 +383,14 @@ TRAFFIC = {
                "profiles/k_pdhg_dense_persistent_maxcut_n4096.md (one launch = 50 iterations; "
                "the one-time copy of W2 into shared memory)"),
 }
+# DRAM bytes of one PDHG iteration PER INSTANCE, captured on one instance and
+# scaled by the batch's instances (the kernels process the batch
+# block-diagonally, so traffic is proportional to the instances)
+TRAFFIC_PER_INSTANCE_ITER = {
+    "facility": (814.06e6 + 88.79e6,
+                 "profiles/pdhg_facility_1_dram.md (one instance, one iteration = 5 kernels; "
+                 "scaled by the 16 instances)"),
+}
 PDHG_KERNELS = {
     "buckets": "PDHG iteration (bucketed k_dual_* / k_primal_* kernels, long-row chunks)",
     "one_row": "PDHG iteration (k_single_primal + k_single_dual, one-row batches)",
@@ -462,9 +470,13 @@ def roofline(workload, insts, k_int, k_b, prof, peaks, src, steps, fp8=False, pa
     if dom == "pdhg":
         ms, iters = phases["pdhg"]
         ach = alg[0] * iters / (ms / 1e3) / 1e9
+        tr = TRAFFIC_PER_INSTANCE_ITER.get(workload)
         out.update({"kernel": PDHG_KERNELS[path],
                     "bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs", 6400.0),
-                    "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6400.0), "traffic": None,
+                    "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6400.0),
+                    "traffic": tr[0] * len(insts) if tr else None,
+                    "traffic_unit": "bytes per iteration (the unit of `achieved`)",
+                    "traffic_source": tr[1] if tr else None,
                     "algorithmic_per_iteration": f"{alg[1]} = {alg[0]:.4e} B",
                     "us_per_iteration": ms / iters * 1e3})
     elif dom == "eval" and workload == "maxcut_sparse":
