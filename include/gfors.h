@@ -225,6 +225,28 @@ GFORS_API gfors_status gfors_final_round(gfors_handle h);
 GFORS_API gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time_budget_s,
                        int32_t proposal, int64_t* iters_out);
 
+/* Alg. 1 as ONE CUDA-graph launch, with CheckHalt (Section 3) decided on
+ * the device: no host synchronisation between sampling triggers.  The body
+ * of a conditional while node is one trigger: k_int PDHG iterations, k_r
+ * rounds (proposal as in gfors_sample_eval), the FP64 CheckHalt sums, and a
+ * one-block kernel that evaluates CheckHalt (the indicators and stall rule
+ * of gfors_run), the iteration budget and, when target_obj (HOST,
+ * ninst int64, may be NULL) is given, whether every instance b holds a
+ * feasible incumbent with objective <= target_obj[b]; that kernel sets the
+ * loop condition.  After the graph come the iterations after the last
+ * trigger when the budget (not CheckHalt or the targets) ended the loop,
+ * then the final rounding.  With target_obj NULL the results equal
+ * gfors_run's with time_budget_s <= 0: the same iterates, candidates,
+ * incumbents and halting decisions.  *iters_out and *triggers_out (may be
+ * NULL) receive the iteration count and the triggers the graph ran.  Needs
+ * an even k_int, the iteration count at a trigger boundary, and a PDHG path
+ * without cooperative launches (not "persistent" or "cooperative" in
+ * gfors_pdhg_path); otherwise GFORS_E_UNSUPPORTED.  The graph is built on
+ * each call.  Synchronises. */
+GFORS_API gfors_status gfors_run_graph(gfors_handle h, int64_t max_iters, int32_t proposal,
+                                       const int64_t* target_obj, int64_t* iters_out,
+                                       int64_t* triggers_out);
+
 /* Incumbent of instance inst: *found = 0/1, objective on the original data
  * (*obj_i exact for integer data, *obj_f always), the round id and sample
  * index that produced it, and x_best as n bytes (0/1) into x_out (may be

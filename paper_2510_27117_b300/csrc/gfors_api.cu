@@ -83,6 +83,14 @@ __global__ void k_round_dense(const float* __restrict__ x, int64_t v0, int64_t n
   put_cand(Xs, i, i < n && x[v0 + i] > 0.5f, f8);
 }
 __global__ void k_set_round(GfDState* st, unsigned v) { st->round_id = v; }
+// proposal 3: after the plain round (which advanced the id to r + 1), the
+// network's round takes id r | 2^31; after it (id (r | 2^31) + 1) the plain
+// sequence resumes at r + 1.  Done on the device so a captured trigger
+// replays with the right ids.
+__global__ void k_round_to_learned(GfDState* st) {
+  st->round_id = (st->round_id - 1u) | 0x80000000u;
+}
+__global__ void k_round_to_plain(GfDState* st) { st->round_id &= 0x7FFFFFFFu; }
 
 __global__ void k_x0_random(float* __restrict__ x, const int32_t* __restrict__ var_inst,
                             const int64_t* __restrict__ var_off, const uint8_t* __restrict__ live,
@@ -238,6 +246,20 @@ static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
   // light pairs while more than two iterations remain
   while (h->use_graphs && nsteps - done >= 3) {
     const int p = (int)((h->k_host + 1) & 1);
+    if (h->capturing) {
+      // inside the capture of a whole trigger (no nested capture, no graph
+      // launch): the pair's two light iterations as direct launches
+      h->light_iter = true;
+      e = gf_launch_pdhg_iter(h, p);
+      if (e == cudaSuccess) e = gf_launch_pdhg_iter(h, 1 - p);
+      h->light_iter = false;
+      if (e) return e;
+      host_advance(h, h->k_host + 1);
+      host_advance(h, h->k_host + 2);
+      h->k_host += 2;
+      done += 2;
+      continue;
+    }
     if (!h->g_light2[p]) {
       cudaGraph_t g;
       if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal))) return e;
@@ -267,6 +289,16 @@ static cudaError_t enqueue_steps(GfCtx* h, int64_t nsteps) {
   // replay a captured pair of iterations while at least two remain
   while (h->use_graphs && nsteps - done >= 2) {
     const int p = (int)((h->k_host + 1) & 1);   // parity of the first iteration
+    if (h->capturing) {                          // as above, full iterations
+      e = gf_launch_pdhg_iter(h, p);
+      if (e == cudaSuccess) e = gf_launch_pdhg_iter(h, 1 - p);
+      if (e) return e;
+      host_advance(h, h->k_host + 1);
+      host_advance(h, h->k_host + 2);
+      h->k_host += 2;
+      done += 2;
+      continue;
+    }
     if (!h->g_iter2[p]) {
       cudaGraph_t g;
       if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal))) return e;
@@ -381,11 +413,11 @@ static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal, i
     for (int r = 0; r < nrounds; ++r) {
       const unsigned rid = h->host_round;
       if ((e = enqueue_round(h, xk, xk, kb, sb, se))) return gf_cuda(h, e, "sampling round");
-      k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, rid | 0x80000000u);
+      k_round_to_learned<<<1, 1, 0, h->stream>>>(h->dstate);
       h->host_round = rid | 0x80000000u;
       if ((e = enqueue_round(h, h->p_learn, xk, kb, sb, se)))
         return gf_cuda(h, e, "sampling round");
-      k_set_round<<<1, 1, 0, h->stream>>>(h->dstate, rid + 1);
+      k_round_to_plain<<<1, 1, 0, h->stream>>>(h->dstate);
       h->host_round = rid + 1;
       h->launches += 2;
     }
@@ -635,6 +667,228 @@ extern "C" gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e) return gf_cuda(h, e, "gfors_run sync");
   if (iters_out) *iters_out = h->k_host;
+  return GFORS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1 as one CUDA-graph launch: the body of a while node is one trigger
+// (k_int iterations, k_r rounds, the FP64 CheckHalt sums) and ends with the
+// halt kernel, which evaluates CheckHalt (the host loop's halt_update, same
+// FP64 formulas and stall rule), the iteration budget and the optional
+// objective targets, and sets the loop's condition.
+namespace {
+__global__ void k_trigger_round(GfDState* st, const long long* ctl, long long base, int kr) {
+  st->round_id = (unsigned)((base + ctl[0]) * (long long)kr);
+}
+
+__global__ void k_halt_step(const double* __restrict__ s_rows, const double* __restrict__ s_vars,
+                            const int32_t* __restrict__ nvar, const int32_t* __restrict__ qk,
+                            double* best, long long* last, long long* ctl,
+                            const long long* __restrict__ tgt, const GfInc* __restrict__ inc,
+                            int ninst, double tol, int window, long long max_trig,
+                            cudaGraphConditionalHandle cond) {
+  __shared__ int all_done, all_hit;
+  if (threadIdx.x == 0) {
+    all_done = 1;
+    all_hit = tgt ? 1 : 0;
+  }
+  __syncthreads();
+  const long long t = ctl[1] + 1;               // CheckHalt trigger count
+  for (int b = threadIdx.x; b < ninst; b += blockDim.x) {
+    const double* s1 = s_rows + 8 * b;
+    const double* s2 = s_vars + 8 * b;
+    double v[3];
+    v[0] = sqrt(s1[0]) / (1.0 + sqrt(s1[1]));
+    const double pobj = s2[3] + s2[4], D = s1[2] + s2[6], sx = sqrt(s2[7]);
+    v[1] = (qk[b] == 0) ? fabs(pobj - D) / (1.0 + fabs(pobj) + fabs(D)) : sx;
+    v[2] = s2[5] / (double)nvar[b];
+    bool done = true;
+    for (int q = 0; q < 3; ++q) {
+      double& bq = best[3 * b + q];
+      long long& lq = last[3 * b + q];
+      if (isinf(bq) || v[q] < bq * (1.0 - 1e-3)) {
+        bq = v[q];
+        lq = t;
+      }
+      done &= (v[q] <= tol) || (t - lq >= window);
+    }
+    if (!done) all_done = 0;
+    if (tgt && !(inc[b].found && inc[b].obj <= tgt[b])) all_hit = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl[1] = t;
+    const long long ran = ctl[0] + 1;
+    ctl[0] = ran;
+    const long long reason = all_done ? 1 : all_hit ? 2 : (ran >= max_trig ? 0 : -1);
+    ctl[2] = reason;
+    cudaGraphSetConditional(cond, reason < 0 ? 1u : 0u);
+  }
+}
+}  // namespace
+
+extern "C" gfors_status gfors_run_graph(gfors_handle h, int64_t max_iters, int32_t proposal,
+                                        const int64_t* target_obj, int64_t* iters_out,
+                                        int64_t* triggers_out) {
+  GF_ENTER(h);
+  if (max_iters < 0 || proposal < 0 || proposal > 3)
+    return gf_fail(h, GFORS_E_ARG, "bad max_iters / proposal");
+  if (!h->all_integral)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "exact evaluation needs integral data");
+  if (proposal != 0 && !h->mlp_W)
+    return gf_fail(h, GFORS_E_STATE, "learned proposal requested but none attached");
+  const int kint = h->prm.k_int, kr = h->prm.k_r;
+  if (kint % 2 != 0 || h->k_host % kint != 0)
+    return gf_fail(h, GFORS_E_UNSUPPORTED,
+                   "gfors_run_graph needs an even k_int and k at a trigger boundary");
+  if (h->persist_ok || h->coop_ok)
+    return gf_fail(h, GFORS_E_UNSUPPORTED,
+                   "gfors_run_graph: cooperative PDHG launches are not captured; use gfors_run");
+  cudaStream_t s = h->stream;
+  cudaError_t e;
+  // everything a trigger allocates, uploads or synchronises on, done first
+  if (h->single_ok && !h->sr_valid) {
+    if ((e = gf_single_init(h))) return gf_cuda(h, e, "one-row init");
+    h->sr_valid = true;
+  }
+  if (proposal != 0 && (e = gf_prepare_features(h))) return gf_cuda(h, e, "feature buffers");
+  if (!h->fused_ok && (e = gf_ensure_bit_list(h))) return gf_cuda(h, e, "sampling list");
+  const int nb = h->ninst;
+  if (!h->halt_ctl) {
+    h->halt_n = gf_alloc_t<int32_t>(h, nb);
+    h->halt_q = gf_alloc_t<int32_t>(h, nb);
+    h->halt_best = gf_alloc_t<double>(h, 3 * nb);
+    h->halt_last = gf_alloc_t<long long>(h, 3 * nb);
+    h->halt_tgt = gf_alloc_t<long long>(h, nb);
+    h->halt_ctl = gf_alloc_t<long long>(h, 3);
+    if (!h->halt_n || !h->halt_q || !h->halt_best || !h->halt_last || !h->halt_tgt ||
+        !h->halt_ctl)
+      return gf_fail(h, GFORS_E_OOM, "halt state");
+    std::vector<int32_t> nv(nb), qv(nb);
+    for (int b = 0; b < nb; ++b) {
+      nv[b] = (int32_t)h->ih[b].n;
+      qv[b] = h->ih[b].qkind;
+    }
+    if ((e = cudaMemcpyAsync(h->halt_n, nv.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice,
+                             s)) ||
+        (e = cudaMemcpyAsync(h->halt_q, qv.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice,
+                             s)) ||
+        (e = cudaStreamSynchronize(s)))
+      return gf_cuda(h, e, "halt constants");
+  }
+  const long long ntrig = (max_iters - h->k_host) / kint;
+  long long ran = 0, reason = 0;
+  if (ntrig > 0) {
+    long long ctl[3] = {0, h->h_trig, -1};
+    if ((e = cudaMemcpyAsync(h->halt_best, h->h_best.data(), sizeof(double) * 3 * nb,
+                             cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(h->halt_last, h->h_last.data(), sizeof(long long) * 3 * nb,
+                             cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(h->halt_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s)) ||
+        (target_obj && (e = cudaMemcpyAsync(h->halt_tgt, target_obj, sizeof(long long) * nb,
+                                            cudaMemcpyHostToDevice, s))) ||
+        (e = cudaStreamSynchronize(s)))
+      return gf_cuda(h, e, "halt state upload");
+    // ---- build: while (cond) { one trigger; halt kernel sets cond }
+    const long long k0 = h->k_host;
+    const int n_rho0 = h->n_rho_host;
+    const double rho0 = h->rho_host;
+    const long long l0 = h->launches;
+    const unsigned hr0 = h->host_round;
+    const bool prof0 = h->prof;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaGraphConditionalHandle hc;
+    if ((e = cudaGraphCreate(&g, 0))) return gf_cuda(h, e, "graph");
+    e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node;
+    if (!e) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hc;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    gfors_status st = GFORS_OK;
+    if (!e) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+      if (!e) {
+        h->capturing = true;
+        h->prof = false;                // no event nodes inside the body
+        cudaError_t ec = enqueue_steps(h, kint);
+        if (!ec) {
+          k_trigger_round<<<1, 1, 0, s>>>(h->dstate, h->halt_ctl, k0 / kint, kr);
+          h->launches++;
+          st = sample_rounds(h, kr, proposal, 0, h->prm.k_b);
+        }
+        if (!ec && st == GFORS_OK) ec = gf_launch_stats(h);
+        if (!ec && st == GFORS_OK) {
+          k_halt_step<<<1, 256, 0, s>>>(h->stats, h->stats2, h->halt_n, h->halt_q,
+                                        h->halt_best, h->halt_last, h->halt_ctl,
+                                        target_obj ? h->halt_tgt : nullptr, h->inc, nb,
+                                        h->prm.halt_tol, h->prm.stall_window, ntrig, hc);
+          h->launches++;
+          ec = cudaGetLastError();
+        }
+        h->capturing = false;
+        h->prof = prof0;
+        cudaGraph_t out = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(s, &out);
+        e = ec ? ec : ee;
+      }
+    }
+    const long long per_trig = h->launches - l0;
+    // the capture advanced the host mirrors by one trigger: undo
+    h->k_host = k0;
+    h->n_rho_host = n_rho0;
+    h->rho_host = rho0;
+    h->launches = l0;
+    h->host_round = hr0;
+    if (!e && st == GFORS_OK) e = cudaGraphInstantiate(&ge, g, 0);
+    if (!e && st == GFORS_OK) e = cudaGraphLaunch(ge, s);
+    long long ctl_out[3] = {0, 0, 0};
+    std::vector<double> bst(3 * nb);
+    std::vector<long long> lst(3 * nb);
+    if (!e && st == GFORS_OK) {
+      e = cudaMemcpyAsync(ctl_out, h->halt_ctl, sizeof(ctl_out), cudaMemcpyDeviceToHost, s);
+      if (!e) e = cudaMemcpyAsync(bst.data(), h->halt_best, sizeof(double) * 3 * nb,
+                                  cudaMemcpyDeviceToHost, s);
+      if (!e) e = cudaMemcpyAsync(lst.data(), h->halt_last, sizeof(long long) * 3 * nb,
+                                  cudaMemcpyDeviceToHost, s);
+      if (!e) e = cudaStreamSynchronize(s);
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    if (st != GFORS_OK) return st;
+    if (e) return gf_cuda(h, e, "gfors_run_graph");
+    if (gfors_status ds = check_device_error(h)) return ds;
+    // host mirrors after `ran` triggers
+    ran = ctl_out[0];
+    reason = ctl_out[2];
+    for (long long it = k0 + 1; it <= k0 + ran * kint; ++it) host_advance(h, it);
+    h->k_host = k0 + ran * kint;
+    h->launches += 1 + ran * per_trig;
+    h->h_trig = ctl_out[1];
+    h->h_best = bst;
+    h->h_last = lst;
+    const unsigned last_plain = (unsigned)((k0 / kint + ran) * kr - 1);
+    h->host_round = last_plain + 1;
+    h->last_round = (proposal == 3) ? (last_plain | 0x80000000u) : last_plain;
+  }
+  // CheckHalt or the targets stop Alg. 1 at once; the iteration budget runs
+  // the iterations after the last trigger, as gfors_run does
+  if (ntrig <= 0 || reason == 0) {
+    const int64_t rest = max_iters - h->k_host;
+    if (rest > 0 && (e = enqueue_steps(h, rest))) return gf_cuda(h, e, "gfors_run_graph steps");
+  }
+  gfors_status st2 = gfors_final_round(h);
+  if (st2) return st2;
+  if ((e = cudaStreamSynchronize(s))) return gf_cuda(h, e, "gfors_run_graph sync");
+  if (iters_out) *iters_out = h->k_host;
+  if (triggers_out) *triggers_out = ran;
   return GFORS_OK;
 }
 

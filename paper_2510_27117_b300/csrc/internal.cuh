@@ -284,6 +284,16 @@ struct gfors_ctx {
   float* p_learn_z = nullptr;       // N: logits of the learned proposal
   uint8_t* var_grouped_feat = nullptr;  // N: 1 if in a one-hot group / axial slab
   long long grp_version = 0;        // bumped whenever groups change
+  // device-side Alg. 1 loop (gfors_run_graph): per-instance constants and
+  // CheckHalt state of the halt kernel, the trigger graph while it is built
+  bool capturing = false;
+  int32_t* halt_n = nullptr;        // ninst: n of each instance
+  int32_t* halt_q = nullptr;        // ninst: qkind of each instance
+  double* halt_best = nullptr;      // 3 ninst
+  long long* halt_last = nullptr;   // 3 ninst
+  long long* halt_tgt = nullptr;    // ninst: target objectives
+  long long* halt_ctl = nullptr;    // [0] triggers run, [1] CheckHalt trigger count,
+                                    // [2] halt reason (0 budget, 1 CheckHalt, 2 targets)
 
   // CUDA graphs of one PDHG iteration pair, by parity of its first iteration
   cudaGraphExec_t g_pair = nullptr;
@@ -320,6 +330,7 @@ struct gfors_ctx {
   bool small_ok = false;
   struct GfSmallInst* small_tab = nullptr;
   uint16_t* small_perm = nullptr;   // N: each instance's columns by decreasing length
+  long long* small_k0 = nullptr;    // st->k snapshotted before each small launch
   size_t small_smem = 0;
   // persistent cooperative PDHG launch (dense instance, matrix in smem)
   bool persist_ok = false;
@@ -363,6 +374,8 @@ cudaError_t gf_launch_power(GfCtx* h, int which, const int64_t* Kp, const int32_
                             const double* Kv, const int64_t* Tp, const int32_t* Tr,
                             const double* Tv, int64_t mrows, double* norms, int* iters);
 cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense);
+cudaError_t gf_ensure_bit_list(GfCtx* h);
+cudaError_t gf_prepare_features(GfCtx* h);
 cudaError_t gf_launch_eval(GfCtx* h, int s0, int len);
 cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len);
 cudaError_t gf_launch_dense_score(GfCtx* h, const GfDenseQ& dq, int s0, int len);

@@ -292,9 +292,13 @@ __global__ void k_features(int64_t N, const float* __restrict__ x, const float* 
                            const float* __restrict__ cstd, const float* __restrict__ degn,
                            const float* __restrict__ gmax, const uint8_t* __restrict__ grouped,
                            const float* __restrict__ dlast, const uint8_t* __restrict__ live,
-                           float rho_frac, float* __restrict__ feat) {
+                           const GfDState* __restrict__ st, double rho_max,
+                           float* __restrict__ feat) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  // rho of the next iteration from the device state (a captured launch
+  // replays with the current penalty)
+  const float rho_frac = (float)(rho_max > 0.0 ? st->rho / rho_max : 0.0);
   float f[kF];
   if (!live[i]) {
 #pragma unroll
@@ -500,6 +504,8 @@ static cudaError_t ensure_feature_buffers(GfCtx* h) {
   return cudaSuccess;
 }
 
+cudaError_t gf_prepare_features(GfCtx* h) { return ensure_feature_buffers(h); }
+
 // Features at the current iterate; called once per sampling trigger, it also
 // pushes x_k into the trigger history.
 cudaError_t gf_launch_features(GfCtx* h) {
@@ -515,10 +521,9 @@ cudaError_t gf_launch_features(GfCtx* h) {
     if (h->ih[b].group_mode == 2 || h->ih[b].group_mode == 3)
       k_slab_max<<<h->ih[b].axial_I, 256, 0, s>>>(xk, h->ih[b].var_off, h->ih[b].axial_I,
                                                   h->grpmax);
-  const float rf = (float)(h->prm.rho_max > 0 ? h->rho_host / h->prm.rho_max : 0.0);
   k_features<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
       N, xk, h->x_trig_prev, h->crel, h->cstd, h->degnorm, h->grpmax,
-      h->var_grouped_feat, h->dlast, h->var_live, rf, h->feat);
+      h->var_grouped_feat, h->dlast, h->var_live, h->dstate, h->prm.rho_max, h->feat);
   h->launches += 1 + (h->ngroups_tot ? 1 : 0);
   if ((e = cudaGetLastError())) return e;
   // remember x_k for the next trigger's trajectory feature

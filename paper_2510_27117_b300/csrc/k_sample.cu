@@ -543,6 +543,26 @@ namespace {
 // Sample `len` candidates (samples s0 .. s0+len-1 of the current round) of
 // every instance from proposal p.  for_dense: dense-Q instances get their
 // bf16 sample-major operand instead of bits.
+
+// The list of 4-variable groups that Bernoulli draws cover (those holding a
+// variable no group sampler draws); built once after the groups change.
+// Synchronises when it builds, so callers that capture a graph build it first.
+cudaError_t gf_ensure_bit_list(GfCtx* h) {
+  if (h->n_bit_g4 >= 0) return cudaSuccess;
+  cudaError_t e;
+  const int64_t N4 = h->N / 4;
+  if ((e = cudaMemsetAsync(h->bit_count, 0, sizeof(int32_t), h->stream))) return e;
+  k_bit_list<<<(unsigned)((N4 + 255) / 256), 256, 0, h->stream>>>(h->var_grouped, N4,
+                                                                   h->bit_g4, h->bit_count);
+  int32_t cnt = 0;
+  if ((e = cudaMemcpyAsync(&cnt, h->bit_count, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return e;
+  h->n_bit_g4 = cnt;
+  return cudaSuccess;
+}
+
 cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense) {
   const gfors_params& P = h->prm;
   cudaError_t e;
@@ -560,18 +580,7 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
   }
   // Bernoulli bits only for the 4-variable groups that hold a variable no
   // group sampler draws (the list is rebuilt after the groups change)
-  if (h->n_bit_g4 < 0) {
-    const int64_t N4 = h->N / 4;
-    if ((e = cudaMemsetAsync(h->bit_count, 0, sizeof(int32_t), h->stream))) return e;
-    k_bit_list<<<(unsigned)((N4 + 255) / 256), 256, 0, h->stream>>>(h->var_grouped, N4,
-                                                                     h->bit_g4, h->bit_count);
-    int32_t cnt = 0;
-    if ((e = cudaMemcpyAsync(&cnt, h->bit_count, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             h->stream)) ||
-        (e = cudaStreamSynchronize(h->stream)))
-      return e;
-    h->n_bit_g4 = cnt;
-  }
+  if ((e = gf_ensure_bit_list(h))) return e;
   if (h->n_bit_g4 > 0) {
     const int64_t N4 = h->n_bit_g4;
     const int64_t threads = N4 * kw;

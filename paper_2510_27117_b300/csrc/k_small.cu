@@ -39,9 +39,9 @@ k_pdhg_small(const GfSmallInst* __restrict__ insts, const int64_t* __restrict__ 
              const float* __restrict__ rhat,
              const uint8_t* __restrict__ row_eq, const float* __restrict__ chat, float* x0,
              float* x1, float* __restrict__ xbar_g, float* __restrict__ y_g,
-             float* __restrict__ dlast, GfIParam* iprm, int ninst, long long k0,
-             long long nsteps, GfDState* st, const GfSched* sc, const double* normQ,
-             const int32_t* cap) {
+             float* __restrict__ dlast, GfIParam* iprm, int ninst,
+             const long long* __restrict__ k0_snap, long long nsteps, GfDState* st,
+             const GfSched* sc, const double* normQ, const int32_t* cap) {
   extern __shared__ __align__(16) uint8_t sm[];
   const int b = blockIdx.x;
   const GfSmallInst I = insts[b];
@@ -68,7 +68,11 @@ k_pdhg_small(const GfSmallInst* __restrict__ insts, const int64_t* __restrict__ 
   __shared__ double rho_s;
   __shared__ int n_rho_s;
   // ---- stage the instance
-  const long long it0 = k0 + 1;
+  // iterations completed before this launch, from the device state as
+  // snapshotted just before it (st->k itself is rewritten by block 0 at the
+  // end, possibly before later blocks start), so a captured launch replays
+  // with the current counter
+  const long long it0 = *k0_snap + 1;
   const float* xo_g = (it0 & 1) ? x0 : x1;        // x_{k0} in x[k0 & 1]
   for (int j = threadIdx.x; j <= m; j += kThreads) rp[j] = (int32_t)(Kp[I.r0 + j] - I.k0);
   for (int i = threadIdx.x; i <= n; i += kThreads) cp[i] = (int32_t)(Tp[I.v0 + i] - I.t0);
@@ -212,6 +216,8 @@ size_t small_smem(int64_t n, int64_t m, int64_t nnz, bool uniform) {
   return b;
 }
 
+__global__ void k_snap_k(const GfDState* st, long long* snap) { *snap = st->k; }
+
 }  // namespace
 
 // Eligibility and tables of the small-instance path: every instance without
@@ -265,7 +271,8 @@ bool gf_small_setup(GfCtx* h, const std::vector<uint8_t>& uniform,
     return false;
   }
   h->small_tab = gf_alloc_t<GfSmallInst>(h, tab.size());
-  if (!h->small_tab) return false;
+  h->small_k0 = gf_alloc_t<long long>(h, 1);
+  if (!h->small_tab || !h->small_k0) return false;
   if (cudaMemcpyAsync(h->small_tab, tab.data(), sizeof(GfSmallInst) * tab.size(),
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -276,13 +283,15 @@ bool gf_small_setup(GfCtx* h, const std::vector<uint8_t>& uniform,
   return true;
 }
 
-// nsteps iterations of every instance after iteration h->k_host (one launch).
+// nsteps iterations of every instance after the iterations completed so far
+// (one launch, plus the one-thread snapshot of the device counter).
 cudaError_t gf_launch_small(GfCtx* h, int64_t nsteps) {
+  k_snap_k<<<1, 1, 0, h->stream>>>(h->dstate, h->small_k0);
   k_pdhg_small<<<h->ninst, kThreads, h->small_smem, h->stream>>>(
       h->small_tab, h->Kp, h->Kc, h->Kv, h->Tp, h->Tr, h->Tv, h->small_perm, h->rhat,
       h->row_eq, h->chat,
-      h->x[0], h->x[1], h->xbar, h->y, h->dlast, h->iprm, h->ninst, h->k_host, nsteps,
+      h->x[0], h->x[1], h->xbar, h->y, h->dlast, h->iprm, h->ninst, h->small_k0, nsteps,
       h->dstate, h->sched_d, h->normQhat_d, h->cap_d);
-  h->launches++;
+  h->launches += 2;
   return cudaGetLastError();
 }

@@ -70,6 +70,7 @@ _lib.gfors_pdhg_steps.argtypes = [_H, i64]
 _lib.gfors_sample_eval.argtypes = [_H, i32, u32, i32]
 _lib.gfors_final_round.argtypes = [_H]
 _lib.gfors_run.argtypes = [_H, i64, f64, i32, _P(i64)]
+_lib.gfors_run_graph.argtypes = [_H, i64, i32, vp, _P(i64), _P(i64)]
 _lib.gfors_incumbent.argtypes = [_H, i32, _P(i32), _P(i64), _P(f64), _P(u32), _P(i32), vp]
 _lib.gfors_lp_stats.argtypes = [_H, i32, vp]
 _lib.gfors_get_scales.argtypes = [_H, i32, vp]
@@ -258,6 +259,16 @@ class Handle:
         it = i64(0)
         _check(_lib.gfors_run(self.h, max_iters, time_budget_s, proposal, C.byref(it)), self.h)
         return it.value
+
+    def run_graph(self, max_iters, proposal=0, targets=None):
+        """gfors_run_graph: Alg. 1 as one CUDA-graph launch with CheckHalt on
+        the device; targets (one int per instance) add the target stop.
+        Returns (iterations, triggers run in the graph)."""
+        it, tr = i64(0), i64(0)
+        t = None if targets is None else np.ascontiguousarray(targets, np.int64)
+        _check(_lib.gfors_run_graph(self.h, max_iters, proposal, _ptr(t), C.byref(it),
+                                    C.byref(tr)), self.h)
+        return it.value, tr.value
 
     # --- results and state
     def incumbent(self, inst=0, want_x=True):
