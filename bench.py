@@ -696,36 +696,6 @@ def _dantzig_bound(I):
     return -val
 
 
-def _gap_ok(obj, zref):
-    return obj <= zref + 0.01 * max(1.0, abs(zref))
-
-
-def _run_until(G, H, insts, prm, proposal, zref, max_trig, tsync):
-    """Alg. 1 loop on handle H (all its instances): k_int PDHG iterations
-    then k_r sampling rounds per trigger; after each trigger the incumbents
-    are read.  Returns (seconds until every instance is within 1% of zref
-    (None if never), best objectives, per-trigger trace)."""
-    import torch
-    tsync()
-    t0 = time.perf_counter()
-    rid, hit_t, trace = 0, None, []
-    best = [None] * len(insts)
-    for trig in range(max_trig):
-        H.pdhg_steps(prm.k_int)
-        H.sample_eval(prm.k_r, rid, proposal)
-        rid += prm.k_r
-        for q in range(len(insts)):
-            inc = H.incumbent(q, want_x=False)
-            best[q] = inc["obj"] if inc["found"] else None
-        el = time.perf_counter() - t0
-        trace.append((el, list(best)))
-        if zref is not None and hit_t is None and all(
-                b is not None and _gap_ok(b, z) for b, z in zip(best, zref)):
-            hit_t = el
-            break
-    return hit_t, best, trace
-
-
 def time_to_gap(args):
     """Wall time (Preprocess excluded) until the incumbent is within 1% of
     the reference value: the plain form (p = x_k, one instance per handle,
@@ -763,24 +733,50 @@ def time_to_gap(args):
         zref = [_dantzig_bound(I) for I in insts]
         desc = (f"first {len(insts)} of the 512-knapsack batch, k_int=50, k_b=4096; "
                 "reference = fractional LP bound")
+    # every arm runs Alg. 1 with CheckHalt off (fixed trigger budget) as one
+    # graph launch (gfors_run_graph): the per-instance targets stop it on the
+    # device at the first trigger after which every instance is within 1%
+    kw.update(halt_tol=0.0, stall_window=1 << 30)
     prm = G.default_params(**kw)
-    # plain form: one handle per instance, one after another
-    t_plain, best_plain, reached = 0.0, [], []
+    max_iters = max_trig * k_int
+
+    def targets(z):
+        return [int(np.floor(v + 0.01 * max(1.0, abs(v)))) for v in z]
+
+    def timed(H, prop, tg):
+        H.run_graph_prepare(prop)         # set-up, like Preprocess: not timed
+        tsync()
+        t0 = time.perf_counter()
+        it, trig = H.run_graph(max_iters, proposal=prop, targets=tg)
+        el = time.perf_counter() - t0
+        best = [H.incumbent(q, want_x=False) for q in range(len(H.insts))]
+        best = [b["obj"] if b["found"] else None for b in best]
+        hit = tg is not None and all(b is not None and b <= t for b, t in zip(best, tg))
+        return (el if hit else None), el, trig, best
+
+    # plain form: one handle per instance, one after another (Philox
+    # instance id q, as instance q of the batched handle, so the batched
+    # plain form draws the very same candidates)
+    t_plain, best_plain, reached, trig_plain = 0.0, [], [], []
     for q, I in enumerate(insts):
-        # Philox instance id q, as instance q of the batched handle: the
-        # batched plain form then draws the very same candidates
-        H = G.load(I, G.default_params(**kw, inst_base=q))
-        zq = None if zref is None else [zref[q]]
-        hit, best, trace = _run_until(G, H, [I], prm, 0, zq, max_trig, tsync)
+        kq = dict(kw, inst_base=q)
+        if zref is None:               # reference: plain's best at its full budget
+            H = G.load(I, G.default_params(**kq))
+            H.run_graph(max_iters, proposal=0)
+            zq = H.incumbent(0, want_x=False)["obj"]
+            H.destroy()
+        else:
+            zq = zref[q]
+        H = G.load(I, G.default_params(**kq))
+        hit, el, trig, best = timed(H, 0, targets([zq]))
         H.destroy()
-        if zref is None:               # reference: plain's best at full budget
-            zb = best[0]
-            hit = next(el for el, b in trace if b[0] is not None and _gap_ok(b[0], zb))
-        best_plain.append(best[0])
+        best_plain.append(zq if zref is None else best[0])
         reached.append(hit is not None)
-        t_plain += hit if hit is not None else trace[-1][0]
+        trig_plain.append(trig)
+        t_plain += hit if hit is not None else el
     if zref is None:
         zref = best_plain
+    tg_all = targets(zref)
     res = {}
     # the learned form: every round draws the plain form's candidates from
     # x_k and as many again from the network (proposal 3); split rounds
@@ -797,13 +793,16 @@ def time_to_gap(args):
         H = G.load_batch(arm_insts, prm)
         if prop:
             H.set_proposal(Wt)
-        hit, best, trace = _run_until(G, H, insts, prm, prop, zref, max_trig, tsync)
+        hit, el, trig, best = timed(H, prop, tg_all)
         H.destroy()
-        res[name] = {"s": hit, "reached": hit is not None, "best": best,
-                     "s_budget": trace[-1][0]}
-    out.update({"workload": desc, "instances": len(insts), "z_ref": zref,
+        res[name] = {"s": hit, "reached": hit is not None, "best": best, "triggers": trig,
+                     "s_run": el}
+    out.update({"workload": desc, "instances": len(insts), "z_ref": zref, "targets": tg_all,
                 "plain_s": t_plain, "plain_reached": reached, "plain_best": best_plain,
-                "max_triggers": max_trig, "training": train_info, **res})
+                "plain_triggers": trig_plain, "max_triggers": max_trig,
+                "halting": "device (gfors_run_graph: one graph launch per run, CheckHalt off, "
+                           "per-instance targets)",
+                "training": train_info, **res})
     lb = res.get("learned_batched", res.get("batched_plain"))
     out["value"] = lb["s"]
     out["speedup_vs_plain"] = (t_plain / lb["s"]) if lb["s"] else None

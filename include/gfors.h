@@ -241,11 +241,16 @@ GFORS_API gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time_
  * NULL) receive the iteration count and the triggers the graph ran.  Needs
  * an even k_int, the iteration count at a trigger boundary, and a PDHG path
  * without cooperative launches (not "persistent" or "cooperative" in
- * gfors_pdhg_path); otherwise GFORS_E_UNSUPPORTED.  The graph is built on
- * each call.  Synchronises. */
+ * gfors_pdhg_path); otherwise GFORS_E_UNSUPPORTED.  The instantiated graph
+ * is kept on the handle, one per proposal, and reused until the groups,
+ * closure, repair groups or lane counts change; the budget, the first
+ * trigger and the targets are read from device memory.  Synchronises. */
 GFORS_API gfors_status gfors_run_graph(gfors_handle h, int64_t max_iters, int32_t proposal,
                                        const int64_t* target_obj, int64_t* iters_out,
                                        int64_t* triggers_out);
+/* Build and keep that graph without running it (set-up work, e.g. before a
+ * timed run); the same conditions and errors as gfors_run_graph. */
+GFORS_API gfors_status gfors_run_graph_prepare(gfors_handle h, int32_t proposal);
 
 /* Incumbent of instance inst: *found = 0/1, objective on the original data
  * (*obj_i exact for integer data, *obj_f always), the round id and sample

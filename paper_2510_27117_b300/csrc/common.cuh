@@ -101,6 +101,30 @@ struct CSum {
   GF_DEV float value() const { return __fadd_rn(s, c); }
 };
 
+// acc += val[t] * vec[idx[t]] for t = t, t + S, t + 2S, ... < t1, added in
+// that order; U consecutive terms have their index and value loads issued,
+// then their gathers, before any is added (U independent gathers in flight
+// instead of one dependent chain), so the sum equals the plain loop's.
+template <int U>
+GF_DEV void gather_dot(CSum& acc, const int32_t* __restrict__ idx,
+                       const float* __restrict__ val, const float* __restrict__ vec,
+                       int64_t t, int64_t t1, int S) {
+  for (; t + (int64_t)(U - 1) * S < t1; t += (int64_t)U * S) {
+    int32_t c[U];
+    float v[U], g[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = idx[t + (int64_t)u * S];
+      v[u] = val[t + (int64_t)u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) g[u] = vec[c[u]];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc.add(__fmul_rn(v[u], g[u]));
+  }
+  for (; t < t1; t += S) acc.add(__fmul_rn(val[t], vec[idx[t]]));
+}
+
 // Sum-reduce a CSum over aligned groups of W lanes (W a power of two <= 32);
 // the result lands in the group's first lane.
 template <int W>

@@ -674,23 +674,27 @@ extern "C" gfors_status gfors_run(gfors_handle h, int64_t max_iters, double time
 // Alg. 1 as one CUDA-graph launch: the body of a while node is one trigger
 // (k_int iterations, k_r rounds, the FP64 CheckHalt sums) and ends with the
 // halt kernel, which evaluates CheckHalt (the host loop's halt_update, same
-// FP64 formulas and stall rule), the iteration budget and the optional
-// objective targets, and sets the loop's condition.
+// FP64 formulas and stall rule), the trigger budget and the optional
+// objective targets, and sets the loop's condition.  Everything that
+// differs between runs (budget, first trigger, targets) lives in device
+// memory, so one instantiated graph per proposal serves every run of the
+// handle until its structure changes.
 namespace {
-__global__ void k_trigger_round(GfDState* st, const long long* ctl, long long base, int kr) {
-  st->round_id = (unsigned)((base + ctl[0]) * (long long)kr);
+__global__ void k_trigger_round(GfDState* st, const long long* ctl, int kr) {
+  st->round_id = (unsigned)((ctl[4] + ctl[0]) * (long long)kr);
 }
 
 __global__ void k_halt_step(const double* __restrict__ s_rows, const double* __restrict__ s_vars,
                             const int32_t* __restrict__ nvar, const int32_t* __restrict__ qk,
                             double* best, long long* last, long long* ctl,
                             const long long* __restrict__ tgt, const GfInc* __restrict__ inc,
-                            int ninst, double tol, int window, long long max_trig,
+                            int ninst, double tol, int window,
                             cudaGraphConditionalHandle cond) {
   __shared__ int all_done, all_hit;
+  const bool use_tgt = ctl[5] != 0;
   if (threadIdx.x == 0) {
     all_done = 1;
-    all_hit = tgt ? 1 : 0;
+    all_hit = use_tgt ? 1 : 0;
   }
   __syncthreads();
   const long long t = ctl[1] + 1;               // CheckHalt trigger count
@@ -713,32 +717,28 @@ __global__ void k_halt_step(const double* __restrict__ s_rows, const double* __r
       done &= (v[q] <= tol) || (t - lq >= window);
     }
     if (!done) all_done = 0;
-    if (tgt && !(inc[b].found && inc[b].obj <= tgt[b])) all_hit = 0;
+    if (use_tgt && !(inc[b].found && inc[b].obj <= tgt[b])) all_hit = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     ctl[1] = t;
     const long long ran = ctl[0] + 1;
     ctl[0] = ran;
-    const long long reason = all_done ? 1 : all_hit ? 2 : (ran >= max_trig ? 0 : -1);
+    const long long reason = all_done ? 1 : all_hit ? 2 : (ran >= ctl[3] ? 0 : -1);
     ctl[2] = reason;
     cudaGraphSetConditional(cond, reason < 0 ? 1u : 0u);
   }
 }
 }  // namespace
 
-extern "C" gfors_status gfors_run_graph(gfors_handle h, int64_t max_iters, int32_t proposal,
-                                        const int64_t* target_obj, int64_t* iters_out,
-                                        int64_t* triggers_out) {
-  GF_ENTER(h);
-  if (max_iters < 0 || proposal < 0 || proposal > 3)
-    return gf_fail(h, GFORS_E_ARG, "bad max_iters / proposal");
+// Checks and lazy state shared by the build and the run of the graph.
+static gfors_status run_graph_ready(GfCtx* h, int32_t proposal) {
+  if (proposal < 0 || proposal > 3) return gf_fail(h, GFORS_E_ARG, "bad proposal");
   if (!h->all_integral)
     return gf_fail(h, GFORS_E_UNSUPPORTED, "exact evaluation needs integral data");
   if (proposal != 0 && !h->mlp_W)
     return gf_fail(h, GFORS_E_STATE, "learned proposal requested but none attached");
-  const int kint = h->prm.k_int, kr = h->prm.k_r;
-  if (kint % 2 != 0 || h->k_host % kint != 0)
+  if (h->prm.k_int % 2 != 0 || h->k_host % h->prm.k_int != 0)
     return gf_fail(h, GFORS_E_UNSUPPORTED,
                    "gfors_run_graph needs an even k_int and k at a trigger boundary");
   if (h->persist_ok || h->coop_ok)
@@ -760,7 +760,7 @@ extern "C" gfors_status gfors_run_graph(gfors_handle h, int64_t max_iters, int32
     h->halt_best = gf_alloc_t<double>(h, 3 * nb);
     h->halt_last = gf_alloc_t<long long>(h, 3 * nb);
     h->halt_tgt = gf_alloc_t<long long>(h, nb);
-    h->halt_ctl = gf_alloc_t<long long>(h, 3);
+    h->halt_ctl = gf_alloc_t<long long>(h, 6);
     if (!h->halt_n || !h->halt_q || !h->halt_best || !h->halt_last || !h->halt_tgt ||
         !h->halt_ctl)
       return gf_fail(h, GFORS_E_OOM, "halt state");
@@ -776,101 +776,140 @@ extern "C" gfors_status gfors_run_graph(gfors_handle h, int64_t max_iters, int32
         (e = cudaStreamSynchronize(s)))
       return gf_cuda(h, e, "halt constants");
   }
+  return GFORS_OK;
+}
+
+// Capture one trigger into the body of a while node and instantiate it
+// (cached per proposal until the handle's structure changes).
+static gfors_status run_graph_build(GfCtx* h, int32_t proposal) {
+  GfCtx::RunGraph& rg = h->run_graph[proposal];
+  if (rg.exec && rg.sv == h->struct_version && rg.gv == h->grp_version) return GFORS_OK;
+  if (rg.exec) {
+    cudaGraphExecDestroy(rg.exec);
+    rg.exec = nullptr;
+  }
+  cudaStream_t s = h->stream;
+  const int kint = h->prm.k_int, kr = h->prm.k_r;
+  const long long k0 = h->k_host;
+  const int n_rho0 = h->n_rho_host;
+  const double rho0 = h->rho_host;
+  const long long l0 = h->launches;
+  const unsigned hr0 = h->host_round;
+  const bool prof0 = h->prof;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle hc;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e) return gf_cuda(h, e, "graph");
+  e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  if (!e) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  }
+  gfors_status st = GFORS_OK;
+  if (!e) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (!e) {
+      h->capturing = true;
+      h->prof = false;                  // no event nodes inside the body
+      cudaError_t ec = enqueue_steps(h, kint);
+      if (!ec) {
+        k_trigger_round<<<1, 1, 0, s>>>(h->dstate, h->halt_ctl, kr);
+        h->launches++;
+        st = sample_rounds(h, kr, proposal, 0, h->prm.k_b);
+      }
+      if (!ec && st == GFORS_OK) ec = gf_launch_stats(h);
+      if (!ec && st == GFORS_OK) {
+        k_halt_step<<<1, 256, 0, s>>>(h->stats, h->stats2, h->halt_n, h->halt_q, h->halt_best,
+                                      h->halt_last, h->halt_ctl, h->halt_tgt, h->inc, h->ninst,
+                                      h->prm.halt_tol, h->prm.stall_window, hc);
+        h->launches++;
+        ec = cudaGetLastError();
+      }
+      h->capturing = false;
+      h->prof = prof0;
+      cudaGraph_t out = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(s, &out);
+      e = ec ? ec : ee;
+    }
+  }
+  rg.per_trig = h->launches - l0;
+  // the capture advanced the host mirrors by one trigger: undo
+  h->k_host = k0;
+  h->n_rho_host = n_rho0;
+  h->rho_host = rho0;
+  h->launches = l0;
+  h->host_round = hr0;
+  if (!e && st == GFORS_OK) e = cudaGraphInstantiate(&rg.exec, g, 0);
+  // upload now (set-up), so the first run does not pay for it
+  if (!e && st == GFORS_OK) e = cudaGraphUpload(rg.exec, s);
+  if (!e && st == GFORS_OK) e = cudaStreamSynchronize(s);
+  cudaGraphDestroy(g);
+  if (st != GFORS_OK) return st;
+  if (e) {
+    rg.exec = nullptr;
+    return gf_cuda(h, e, "gfors_run_graph build");
+  }
+  rg.sv = h->struct_version;
+  rg.gv = h->grp_version;
+  return GFORS_OK;
+}
+
+extern "C" gfors_status gfors_run_graph_prepare(gfors_handle h, int32_t proposal) {
+  GF_ENTER(h);
+  gfors_status st = run_graph_ready(h, proposal);
+  if (st) return st;
+  return run_graph_build(h, proposal);
+}
+
+extern "C" gfors_status gfors_run_graph(gfors_handle h, int64_t max_iters, int32_t proposal,
+                                        const int64_t* target_obj, int64_t* iters_out,
+                                        int64_t* triggers_out) {
+  GF_ENTER(h);
+  if (max_iters < 0) return gf_fail(h, GFORS_E_ARG, "bad max_iters");
+  gfors_status st = run_graph_ready(h, proposal);
+  if (st) return st;
+  const int kint = h->prm.k_int, kr = h->prm.k_r, nb = h->ninst;
+  cudaStream_t s = h->stream;
+  cudaError_t e;
   const long long ntrig = (max_iters - h->k_host) / kint;
   long long ran = 0, reason = 0;
   if (ntrig > 0) {
-    long long ctl[3] = {0, h->h_trig, -1};
+    if ((st = run_graph_build(h, proposal))) return st;
+    const GfCtx::RunGraph& rg = h->run_graph[proposal];
+    const long long k0 = h->k_host;
+    long long ctl[6] = {0, h->h_trig, -1, ntrig, k0 / kint, target_obj ? 1 : 0};
     if ((e = cudaMemcpyAsync(h->halt_best, h->h_best.data(), sizeof(double) * 3 * nb,
                              cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(h->halt_last, h->h_last.data(), sizeof(long long) * 3 * nb,
                              cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(h->halt_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s)) ||
         (target_obj && (e = cudaMemcpyAsync(h->halt_tgt, target_obj, sizeof(long long) * nb,
-                                            cudaMemcpyHostToDevice, s))) ||
-        (e = cudaStreamSynchronize(s)))
+                                            cudaMemcpyHostToDevice, s))))
       return gf_cuda(h, e, "halt state upload");
-    // ---- build: while (cond) { one trigger; halt kernel sets cond }
-    const long long k0 = h->k_host;
-    const int n_rho0 = h->n_rho_host;
-    const double rho0 = h->rho_host;
-    const long long l0 = h->launches;
-    const unsigned hr0 = h->host_round;
-    const bool prof0 = h->prof;
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    cudaGraphConditionalHandle hc;
-    if ((e = cudaGraphCreate(&g, 0))) return gf_cuda(h, e, "graph");
-    e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
-    cudaGraphNodeParams np = {};
-    cudaGraphNode_t node;
-    if (!e) {
-      np.type = cudaGraphNodeTypeConditional;
-      np.conditional.handle = hc;
-      np.conditional.type = cudaGraphCondTypeWhile;
-      np.conditional.size = 1;
-      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
-    }
-    gfors_status st = GFORS_OK;
-    if (!e) {
-      cudaGraph_t body = np.conditional.phGraph_out[0];
-      e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                        cudaStreamCaptureModeRelaxed);
-      if (!e) {
-        h->capturing = true;
-        h->prof = false;                // no event nodes inside the body
-        cudaError_t ec = enqueue_steps(h, kint);
-        if (!ec) {
-          k_trigger_round<<<1, 1, 0, s>>>(h->dstate, h->halt_ctl, k0 / kint, kr);
-          h->launches++;
-          st = sample_rounds(h, kr, proposal, 0, h->prm.k_b);
-        }
-        if (!ec && st == GFORS_OK) ec = gf_launch_stats(h);
-        if (!ec && st == GFORS_OK) {
-          k_halt_step<<<1, 256, 0, s>>>(h->stats, h->stats2, h->halt_n, h->halt_q,
-                                        h->halt_best, h->halt_last, h->halt_ctl,
-                                        target_obj ? h->halt_tgt : nullptr, h->inc, nb,
-                                        h->prm.halt_tol, h->prm.stall_window, ntrig, hc);
-          h->launches++;
-          ec = cudaGetLastError();
-        }
-        h->capturing = false;
-        h->prof = prof0;
-        cudaGraph_t out = nullptr;
-        cudaError_t ee = cudaStreamEndCapture(s, &out);
-        e = ec ? ec : ee;
-      }
-    }
-    const long long per_trig = h->launches - l0;
-    // the capture advanced the host mirrors by one trigger: undo
-    h->k_host = k0;
-    h->n_rho_host = n_rho0;
-    h->rho_host = rho0;
-    h->launches = l0;
-    h->host_round = hr0;
-    if (!e && st == GFORS_OK) e = cudaGraphInstantiate(&ge, g, 0);
-    if (!e && st == GFORS_OK) e = cudaGraphLaunch(ge, s);
-    long long ctl_out[3] = {0, 0, 0};
+    long long ctl_out[6] = {0, 0, 0, 0, 0, 0};
     std::vector<double> bst(3 * nb);
     std::vector<long long> lst(3 * nb);
-    if (!e && st == GFORS_OK) {
-      e = cudaMemcpyAsync(ctl_out, h->halt_ctl, sizeof(ctl_out), cudaMemcpyDeviceToHost, s);
-      if (!e) e = cudaMemcpyAsync(bst.data(), h->halt_best, sizeof(double) * 3 * nb,
-                                  cudaMemcpyDeviceToHost, s);
-      if (!e) e = cudaMemcpyAsync(lst.data(), h->halt_last, sizeof(long long) * 3 * nb,
-                                  cudaMemcpyDeviceToHost, s);
-      if (!e) e = cudaStreamSynchronize(s);
-    }
-    if (ge) cudaGraphExecDestroy(ge);
-    cudaGraphDestroy(g);
-    if (st != GFORS_OK) return st;
-    if (e) return gf_cuda(h, e, "gfors_run_graph");
+    if ((e = cudaGraphLaunch(rg.exec, s)) ||
+        (e = cudaMemcpyAsync(ctl_out, h->halt_ctl, sizeof(ctl_out), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(bst.data(), h->halt_best, sizeof(double) * 3 * nb,
+                             cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(lst.data(), h->halt_last, sizeof(long long) * 3 * nb,
+                             cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+      return gf_cuda(h, e, "gfors_run_graph");
     if (gfors_status ds = check_device_error(h)) return ds;
     // host mirrors after `ran` triggers
     ran = ctl_out[0];
     reason = ctl_out[2];
     for (long long it = k0 + 1; it <= k0 + ran * kint; ++it) host_advance(h, it);
     h->k_host = k0 + ran * kint;
-    h->launches += 1 + ran * per_trig;
+    h->launches += ran * rg.per_trig;
     h->h_trig = ctl_out[1];
     h->h_best = bst;
     h->h_last = lst;
@@ -993,6 +1032,7 @@ extern "C" gfors_status gfors_set_counters(gfors_handle h, int64_t k, double rho
   if (e) return gf_cuda(h, e, "set_counters sync");
   if ((k & 1) != (h->k_host & 1)) {       // keep x_k in x[k & 1]
     std::swap(h->x[0], h->x[1]);
+    h->struct_version++;                  // captured launches name these buffers
     for (int q = 0; q < 2; ++q)
       if (h->g_iter2[q]) { cudaGraphExecDestroy(h->g_iter2[q]); h->g_iter2[q] = nullptr; }
     for (int q = 0; q < 2; ++q)
@@ -1278,6 +1318,7 @@ extern "C" gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, in
     h->h_rg_ptr.push_back(base + grp_ptr[g + 1]);
   }
   h->nrg = (int64_t)h->h_rg_ptr.size() - 1;
+  h->struct_version++;
   h->rg_ptr = gf_alloc_t<int64_t>(h, h->h_rg_ptr.size());
   h->rg_idx = gf_alloc_t<int64_t>(h, std::max<size_t>(1, h->h_rg_idx.size()));
   if (!h->rg_ptr || !h->rg_idx) return gf_fail(h, GFORS_E_OOM, "repair groups");
@@ -1315,6 +1356,7 @@ extern "C" gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t 
     h->h_rep_ptr.push_back(base + rep_ptr[q + 1]);
   }
   h->nrep_tot = (int64_t)h->h_rep_var.size();
+  h->struct_version++;
   h->rep_var = gf_alloc_t<int64_t>(h, h->h_rep_var.size());
   h->rep_ptr = gf_alloc_t<int64_t>(h, h->h_rep_ptr.size());
   h->rep_idx = gf_alloc_t<int64_t>(h, h->h_rep_idx.size());

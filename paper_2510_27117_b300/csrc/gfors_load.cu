@@ -1122,6 +1122,12 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     }
     h->nurows = (int64_t)ur.size();
     h->nprows = (int64_t)pr.size();
+    // general rows longer than kGLong entries after the others: those get a
+    // block per (row, candidate word) in evaluation (row order does not
+    // change any count)
+    std::stable_partition(gr.begin(), gr.end(), [](const GfGRow& R) { return R.len <= kGLong; });
+    h->ngrows_short = 0;
+    for (const GfGRow& R : gr) h->ngrows_short += (R.len <= kGLong) ? 1 : 0;
     h->ngrows = (int64_t)gr.size();
     h->nochunks = (int64_t)oc.size();
     h->nqchunks = (int64_t)qc.size();
@@ -1427,6 +1433,8 @@ extern "C" void gfors_destroy(gfors_handle h) {
     if (h->g_iter2[q]) cudaGraphExecDestroy(h->g_iter2[q]);
     if (h->g_light2[q]) cudaGraphExecDestroy(h->g_light2[q]);
   }
+  for (auto& rg : h->run_graph)
+    if (rg.exec) cudaGraphExecDestroy(rg.exec);
   gf_free_all(h);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;

@@ -110,6 +110,7 @@ void apply_lanes(GfCtx* h, const int32_t* l) {
   for (size_t k = 0; k < h->rb.size() && k < 5; ++k) h->rb[k].lanes = l[k];
   for (size_t k = 0; k < h->cb.size() && k < 5; ++k) h->cb[k].lanes = l[5 + k];
   drop_graphs(h);
+  h->struct_version++;                  // a cached whole-run graph is rebuilt
 }
 
 }  // namespace

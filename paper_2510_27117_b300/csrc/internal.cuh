@@ -19,6 +19,7 @@
 // ---------------------------------------------------------------------------
 constexpr int kLongLen = 2048;     // rows/cols longer than this are chunked
 constexpr int kChunkLen = 2048;    // nnz per partial-sum chunk
+constexpr int kGLong = 256;       // general rows above this length: a block each in evaluation
 
 struct GfChunk {                    // one partial-sum chunk of a long row/col
   int32_t id;                       // row (dual) or column (primal)
@@ -225,6 +226,7 @@ struct gfors_ctx {
   int64_t nurows_cls[3] = {0, 0, 0};  // urows of each class, stored in class order
   GfPRow* prows = nullptr; int64_t nprows = 0;
   GfGRow* grows = nullptr; int64_t ngrows = 0; int32_t* gcols = nullptr; int32_t* gvals = nullptr;
+  int64_t ngrows_short = 0;         // rows [0, ngrows_short) have <= kGLong entries
   long long* cint = nullptr;        // N, original integer costs
   GfObjChunk* ochunks = nullptr; int64_t nochunks = 0;
   // sparse Q for evaluation: pairs (QIi < QIc) with w = q_ij + q_ji in
@@ -293,7 +295,15 @@ struct gfors_ctx {
   long long* halt_last = nullptr;   // 3 ninst
   long long* halt_tgt = nullptr;    // ninst: target objectives
   long long* halt_ctl = nullptr;    // [0] triggers run, [1] CheckHalt trigger count,
-                                    // [2] halt reason (0 budget, 1 CheckHalt, 2 targets)
+                                    // [2] halt reason (0 budget, 1 CheckHalt, 2 targets),
+                                    // [3] trigger budget, [4] first trigger's index,
+                                    // [5] targets on
+  long long struct_version = 0;     // bumped when the launches of a trigger change
+  struct RunGraph {                 // instantiated whole-run graph, per proposal
+    cudaGraphExec_t exec = nullptr;
+    long long sv = -1, gv = -1;     // struct_version / grp_version it was built for
+    long long per_trig = 0;         // kernel launches in one trigger
+  } run_graph[4];
 
   // CUDA graphs of one PDHG iteration pair, by parity of its first iteration
   cudaGraphExec_t g_pair = nullptr;

@@ -274,6 +274,47 @@ k_eval_grows(const GfGRow* __restrict__ rows, int64_t nrows,
   add_violations(vmask, inst, w, chunk, viol, valid);
 }
 
+// Long G rows: one 256-thread block per (row, candidate word); each thread
+// sums its entries for the 32 candidates, a warp reduction hands lane t the
+// warp's sum for candidate t, and the warps' sums are added in shared
+// memory.  Integer sums, so the counts equal the one-thread kernel's.
+__global__ void __launch_bounds__(256)
+k_eval_grows_long(const GfGRow* __restrict__ rows, const int32_t* __restrict__ gcols,
+                  const int32_t* __restrict__ gvals, const uint32_t* __restrict__ X, int kws,
+                  int len, int chunk, int32_t* __restrict__ viol) {
+  const GfGRow R = rows[blockIdx.x];
+  const int w = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long acc[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) acc[t] = 0;
+  for (int q = threadIdx.x; q < R.len; q += blockDim.x) {
+    const uint32_t m = X[(int64_t)gcols[R.t0 + q] * kws + w];
+    if (!m) continue;
+    const long long a = gvals[R.t0 + q];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] += ((m >> t) & 1u) ? a : 0ll;
+  }
+  long long mine = 0;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    long long v = acc[t];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+    if (lane == t) mine = v;
+  }
+  __shared__ long long red[8][32];
+  red[warp][lane] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    long long tot = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += red[q][lane];
+    const bool bad = R.eq ? (tot != R.rhs) : (tot < R.rhs);
+    if (bad && 32 * w + lane < len)
+      atomicAdd(&viol[(int64_t)R.inst * chunk + 32 * w + lane], 1);
+  }
+}
+
 constexpr int kQW = 4;
 
 // Weighted counts of a warp's 32 items for the 32 candidates of each of kQW
@@ -692,10 +733,18 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
         h->prows, h->nprows, h->X, h->kw, kwu, len, h->chunk, h->viol);
     h->launches++;
   }
-  if (h->ngrows) {
-    const int64_t th = h->ngrows * kwu;
+  if (h->ngrows_short) {
+    const int64_t th = h->ngrows_short * kwu;
     k_eval_grows<<<(unsigned)((th + 127) / 128), 128, 0, h->stream>>>(
-        h->grows, h->ngrows, h->gcols, h->gvals, h->X, h->kw, kwu, len, h->chunk, h->viol);
+        h->grows, h->ngrows_short, h->gcols, h->gvals, h->X, h->kw, kwu, len, h->chunk,
+        h->viol);
+    h->launches++;
+  }
+  if (h->ngrows > h->ngrows_short) {
+    dim3 grid((unsigned)(h->ngrows - h->ngrows_short), (unsigned)kwu);
+    k_eval_grows_long<<<grid, 256, 0, h->stream>>>(h->grows + h->ngrows_short, h->gcols,
+                                                   h->gvals, h->X, h->kw, len, h->chunk,
+                                                   h->viol);
     h->launches++;
   }
   if (h->nochunks) {

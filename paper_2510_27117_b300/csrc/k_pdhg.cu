@@ -43,8 +43,7 @@ k_dual_rows(const int32_t* __restrict__ rows, int32_t nrows,
     tau2 = ip[row_inst[j]].tau2;
   }
   CSum acc;
-  for (int64_t t = t0 + lane; t < t1; t += LANES)
-    acc.add(__fmul_rn(Kv[t], xbar[Kc[t]]));
+  gf::gather_dot<4>(acc, Kc, Kv, xbar, t0 + lane, t1, LANES);
   gf::csum_group_reduce<LANES>(acc);
   if (lane == 0) {
     float v = yo + tau2 * (acc.value() + rj);
@@ -93,8 +92,7 @@ k_dual_runs(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_ptr,
     eq = row_eq[j];
   }
   CSum acc;
-  for (int64_t t = t0 + lane; t < t1; t += LANES)
-    acc.add(__fmul_rn(Kv[t], xbar[Kc[t]]));
+  gf::gather_dot<4>(acc, Kc, Kv, xbar, t0 + lane, t1, LANES);
   gf::csum_group_reduce<LANES>(acc);
   if (lane == 0) {
     const float tau2 = ip[R.inst].tau2;
@@ -352,8 +350,7 @@ k_primal_cols(const int32_t* __restrict__ cols, int32_t ncols,
       ch = chat[i];
     }
     CSum acc;
-    for (int64_t t = Tp[i] + lane; t < Tp[i + 1]; t += LANES)
-      acc.add(__fmul_rn(Tv[t], y[Tr[t]]));
+    gf::gather_dot<4>(acc, Tr, Tv, y, Tp[i] + lane, Tp[i + 1], LANES);
     if (Qp) {
       for (int64_t t = Qp[i] + lane; t < Qp[i + 1]; t += LANES)
         acc.add(2.0f * __fmul_rn(Qv[t], x_old[Qc[t]]));
@@ -418,8 +415,7 @@ k_primal_runs(const GfRun* __restrict__ runs, const int64_t* __restrict__ run_pt
       for (int e = 0; e < 4; ++e)
         if (e < R.len) acc.add(__fmul_rn(v[e], g[e]));
     } else {
-      for (int64_t t = t0 + lane; t < t1; t += LANES)
-        acc.add(__fmul_rn(Tv[t], y[Tr[t]]));
+      gf::gather_dot<4>(acc, Tr, Tv, y, t0 + lane, t1, LANES);
     }
     if (Qp) {
       for (int64_t t = Qp[i] + lane; t < Qp[i + 1]; t += LANES)
@@ -454,8 +450,8 @@ k_long_partial(const GfChunk* __restrict__ ch, int32_t nch,
   const GfChunk k = ch[c];
   CSum acc;
   if (k.part == 0) {
-    for (int64_t t = k.t0 + threadIdx.x; t < k.t1; t += blockDim.x)
-      acc.add(__fmul_rn(val[t], vec[idx[t]]));
+    // chunks of kChunkLen = 8 x 256 entries: all eight gathers in flight
+    gf::gather_dot<8>(acc, idx, val, vec, k.t0 + threadIdx.x, k.t1, (int)blockDim.x);
   } else {
     for (int64_t t = k.t0 + threadIdx.x; t < k.t1; t += blockDim.x)
       acc.add(2.0f * __fmul_rn(Qv[t], xq[Qc[t]]));

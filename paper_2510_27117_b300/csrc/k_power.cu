@@ -9,6 +9,8 @@
 namespace {
 
 constexpr int kRedThreads = 256;
+constexpr int kRowChunk = 2048;    // rows per statistics chunk (the load's row chunks)
+constexpr int kStatLong = 256;     // longer rows are summed by a whole block
 
 __device__ double block_sum(double v) {
   __shared__ double sh[kRedThreads];
@@ -180,7 +182,16 @@ k_stats_rows(const int32_t* __restrict__ ch, int64_t nch, const int64_t* __restr
   if (c >= nch) return;
   const int a = ch[3 * c + 1], e = ch[3 * c + 2];
   double s0 = 0, s1 = 0, s2 = 0;
+  // rows longer than kStatLong entries are marked here and summed by the
+  // whole block below, in row order (a single thread would walk them alone)
+  __shared__ uint32_t lmask[kRowChunk / 32];
+  for (int q = threadIdx.x; q < kRowChunk / 32; q += kRedThreads) lmask[q] = 0u;
+  __syncthreads();
   for (int j = a + threadIdx.x; j < e; j += kRedThreads) {
+    if (Kp[j + 1] - Kp[j] > kStatLong) {
+      atomicOr(&lmask[(j - a) >> 5], 1u << ((j - a) & 31));
+      continue;
+    }
     double v = 0.0;
     for (int64_t t = Kp[j]; t < Kp[j + 1]; ++t) v += (double)Kv[t] * (double)x[Kc[t]];
     v += (double)r[j];
@@ -188,6 +199,25 @@ k_stats_rows(const int32_t* __restrict__ ch, int64_t nch, const int64_t* __restr
     s0 += v * v;
     s1 += (double)r[j] * (double)r[j];
     s2 += (double)r[j] * (double)y[j];
+  }
+  __syncthreads();
+  for (int q = 0; q < (e - a + 31) / 32; ++q) {
+    uint32_t m = lmask[q];                      // the same word in every thread
+    while (m) {
+      const int j = a + 32 * q + __ffs(m) - 1;
+      m &= m - 1u;
+      double v = 0.0;
+      for (int64_t t = Kp[j] + threadIdx.x; t < Kp[j + 1]; t += kRedThreads)
+        v += (double)Kv[t] * (double)x[Kc[t]];
+      v = block_sum(v);
+      if (threadIdx.x == 0) {
+        v += (double)r[j];
+        if (!row_eq[j] && v < 0.0) v = 0.0;
+        s0 += v * v;
+        s1 += (double)r[j] * (double)r[j];
+        s2 += (double)r[j] * (double)y[j];
+      }
+    }
   }
   s0 = block_sum(s0);
   s1 = block_sum(s1);

@@ -71,6 +71,7 @@ _lib.gfors_sample_eval.argtypes = [_H, i32, u32, i32]
 _lib.gfors_final_round.argtypes = [_H]
 _lib.gfors_run.argtypes = [_H, i64, f64, i32, _P(i64)]
 _lib.gfors_run_graph.argtypes = [_H, i64, i32, vp, _P(i64), _P(i64)]
+_lib.gfors_run_graph_prepare.argtypes = [_H, i32]
 _lib.gfors_incumbent.argtypes = [_H, i32, _P(i32), _P(i64), _P(f64), _P(u32), _P(i32), vp]
 _lib.gfors_lp_stats.argtypes = [_H, i32, vp]
 _lib.gfors_get_scales.argtypes = [_H, i32, vp]
@@ -269,6 +270,10 @@ class Handle:
         _check(_lib.gfors_run_graph(self.h, max_iters, proposal, _ptr(t), C.byref(it),
                                     C.byref(tr)), self.h)
         return it.value, tr.value
+
+    def run_graph_prepare(self, proposal=0):
+        """gfors_run_graph_prepare: build the whole-run graph now (set-up)."""
+        _check(_lib.gfors_run_graph_prepare(self.h, proposal), self.h)
 
     # --- results and state
     def incumbent(self, inst=0, want_x=True):

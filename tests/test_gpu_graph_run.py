@@ -127,3 +127,25 @@ def test_graph_run_unsupported_forms():
         H.run_graph(70)
     assert e.value.status == 6
     H.destroy()
+
+
+def test_graph_reused_across_calls_and_rebuilt_after_lane_change():
+    """One instantiated graph serves successive calls (the budget and the
+    first trigger come from device memory); a lane change rebuilds it.
+    Results equal the host loop's over the same sequence of calls."""
+    insts = CASES["assign3d"][0]()
+    prm = G.default_params(k_int=10, k_b=128, seed=0x5EED0011, halt_tol=0.0,
+                           stall_window=1000)
+    A = G.load_batch(insts, prm)
+    A.run(40)
+    A.run(90)
+    B = G.load_batch(insts, prm)
+    B.run_graph_prepare(0)
+    assert B.run_graph(40) == (40, 4)
+    B.set_lanes(B.get_lanes())              # same lanes, new structure version
+    assert B.run_graph(90) == (90, 5)
+    a = dict(it=90, inc=[A.incumbent(0)], x=[A.get_iterate(0)[0]], st=[A.lp_stats(0)])
+    b = dict(it=90, inc=[B.incumbent(0)], x=[B.get_iterate(0)[0]], st=[B.lp_stats(0)])
+    _same(a, b)
+    A.destroy()
+    B.destroy()
