@@ -510,8 +510,12 @@ void gf_set_slot(GfCtx* h, int parity, double rho) {
 
 // Runs of a bucket's (ascending) ids: maximal stretches of consecutive ids of
 // one instance; uniform when all have the same length (ptr differences).
-// Used instead of the id list when there are at most kMaxRuns of them.
+// Used instead of the id list when there are at most kMaxRuns of them, or
+// when they hold at least kMinRunLen ids on average (a kernel finds a run by
+// binary search over the run offsets, once per row group or block, which
+// long runs amortise).
 constexpr int kMaxRuns = 4096;
+constexpr int64_t kMinRunLen = 32;
 // Blocks of 32 sparse-Q pairs per evaluation chunk (one CUDA block of 8 warps).
 constexpr int kQChunkBlocks = 64;
 static bool make_runs(const std::vector<int32_t>& ids, const std::vector<int64_t>& ptr,
@@ -527,7 +531,11 @@ static bool make_runs(const std::vector<int32_t>& ids, const std::vector<int64_t
       if (R->len != len) R->len = -1;
       R->count++;
     } else {
-      if ((int)runs.size() == kMaxRuns) return false;
+      // many short runs: the id list serves better
+      if ((int64_t)runs.size() >= kMaxRuns &&
+          (int64_t)runs.size() * kMinRunLen > (int64_t)ids.size())
+        return false;
+      if (runs.size() >= (size_t)INT32_MAX) return false;
       runs.push_back(GfRun{id, ptr[id], 1, len, inst_of[id], 0});
     }
   }

@@ -66,7 +66,9 @@ __global__ void k_inst_sum(const double* __restrict__ partial, const int32_t* __
   }
 }
 
-// FP64 CSR product out = M vec, LANES threads per row.
+// FP64 CSR product out = M vec, LANES threads per row; rows longer than
+// kPwLong entries are left to k_spmv64_long.
+constexpr int64_t kPwLong = 256;
 template <int LANES>
 __global__ void __launch_bounds__(256)
 k_spmv64(const int64_t* __restrict__ Mp, const int32_t* __restrict__ Mc,
@@ -76,6 +78,7 @@ k_spmv64(const int64_t* __restrict__ Mp, const int32_t* __restrict__ Mc,
   const int64_t r = gid / LANES;
   const int lane = (int)(gid % LANES);
   if (r >= rows) return;
+  if (Mp[r + 1] - Mp[r] > kPwLong) return;      // the whole group skips it
   double s = 0.0;
   for (int64_t t = Mp[r] + lane; t < Mp[r + 1]; t += LANES) s += Mv[t] * vec[Mc[t]];
   if (LANES > 1) {
@@ -85,6 +88,20 @@ k_spmv64(const int64_t* __restrict__ Mp, const int32_t* __restrict__ Mc,
     for (int off = LANES / 2; off > 0; off >>= 1) s += __shfl_down_sync(mask, s, off, LANES);
   }
   if (lane == 0) out[r] = s;
+}
+
+// The long rows (ids[]) of the same product, one block each, block_sum in a
+// fixed order.
+__global__ void __launch_bounds__(kRedThreads)
+k_spmv64_long(const int64_t* __restrict__ Mp, const int32_t* __restrict__ Mc,
+              const double* __restrict__ Mv, const double* __restrict__ vec,
+              const int64_t* __restrict__ ids, double* __restrict__ out) {
+  const int64_t r = ids[blockIdx.x];
+  double s = 0.0;
+  for (int64_t t = Mp[r] + threadIdx.x; t < Mp[r + 1]; t += kRedThreads)
+    s += Mv[t] * vec[Mc[t]];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[r] = s;
 }
 
 // FP64 dense symmetric product for one dense-Q instance:
@@ -110,12 +127,14 @@ struct PwState {
 
 // Per-instance bookkeeping of one power-iteration step t (the oracle's
 // order): lambda_t = ||M v_t||^2, zn = ||M^T M v_t||; zn = 0 ends;
-// otherwise v_{t+1} = z / zn and the relative-change test ends it.
+// otherwise v_{t+1} = z / zn and the relative-change test ends it.  t is
+// the device step counter (the loop runs as one graph launch).
 __global__ void k_pw_step(PwState* __restrict__ ps, const double* __restrict__ lam,
-                          const double* __restrict__ zn2, int ninst, int t, double tol,
-                          int maxit, int* __restrict__ ndone) {
+                          const double* __restrict__ zn2, int ninst, const int* __restrict__ tc,
+                          double tol, int maxit, int* __restrict__ ndone) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ninst) return;
+  const int t = *tc;
   PwState S = ps[b];
   S.upd = 0;
   if (!S.done) {
@@ -148,6 +167,15 @@ __global__ void k_pw_normalize(double* v, const double* z,
   if (i >= N) return;
   const int b = var_inst[i];
   if (ps[b].upd) v[i] = z[i] / sqrt(zn2[b]);
+}
+
+// End of a loop step: t <- t + 1, and the loop goes on while an instance is
+// still iterating and t < maxit.
+__global__ void k_pw_next(int* tc, const int* __restrict__ ndone, int ninst, int maxit,
+                          cudaGraphConditionalHandle cond) {
+  const int t = *tc + 1;
+  *tc = t;
+  cudaGraphSetConditional(cond, (*ndone < ninst && t < maxit) ? 1u : 0u);
 }
 
 __global__ void k_scale_f32(const double* __restrict__ src, float* __restrict__ dst,
@@ -292,7 +320,31 @@ struct PowerScratch {
   double *v, *w, *z, *lam, *zn2, *partial;
   PwState* ps;
   int* ndone;
+  int* tc;                          // step counter of the graph loop
 };
+
+// ids of the lines of a CSR (ptr, lines) longer than kPwLong, on the device
+static int64_t* long_lines(GfCtx* h, const int64_t* ptr_dev, int64_t lines, int64_t* count,
+                           cudaError_t* err) {
+  *count = 0;
+  *err = cudaSuccess;
+  if (lines <= 0) return nullptr;
+  std::vector<int64_t> p(lines + 1), ids;
+  if ((*err = cudaMemcpy(p.data(), ptr_dev, sizeof(int64_t) * (lines + 1),
+                         cudaMemcpyDeviceToHost)))
+    return nullptr;
+  for (int64_t l = 0; l < lines; ++l)
+    if (p[l + 1] - p[l] > kPwLong) ids.push_back(l);
+  *count = (int64_t)ids.size();
+  if (ids.empty()) return nullptr;
+  int64_t* d = gf_alloc_t<int64_t>(h, ids.size());
+  if (!d) {
+    *err = cudaErrorMemoryAllocation;
+    return nullptr;
+  }
+  *err = cudaMemcpy(d, ids.data(), sizeof(int64_t) * ids.size(), cudaMemcpyHostToDevice);
+  return d;
+}
 
 extern "C++" cudaError_t gf_power_run(GfCtx* h, int which, const int64_t* Mp,
                                       const int32_t* Mc, const double* Mv,
@@ -313,9 +365,23 @@ extern "C++" cudaError_t gf_power_run(GfCtx* h, int which, const int64_t* Mp,
   S.partial = gf_alloc_t<double>(h, std::max(nrch, h->nvchunk) + 1);
   S.ps = gf_alloc_t<PwState>(h, nb);
   S.ndone = gf_alloc_t<int>(h, 1);
-  if (!S.v || !S.z || !S.w || !S.lam || !S.zn2 || !S.partial || !S.ps || !S.ndone)
+  S.tc = gf_alloc_t<int>(h, 1);
+  if (!S.v || !S.z || !S.w || !S.lam || !S.zn2 || !S.partial || !S.ps || !S.ndone || !S.tc)
     return cudaErrorMemoryAllocation;
   cudaError_t e;
+  // long lines of the two products (one block each)
+  int64_t nlr = 0, nlc = 0;
+  const int64_t* lr = nullptr;
+  const int64_t* lc = nullptr;
+  if (which == 0) {
+    lr = long_lines(h, Mp, mrows, &nlr, &e);
+    if (e) return e;
+    lc = long_lines(h, Tp, N, &nlc, &e);
+    if (e) return e;
+  } else if (Mp) {
+    lr = long_lines(h, Mp, N, &nlr, &e);
+    if (e) return e;
+  }
   // instances without the matrix are done from the start
   std::vector<PwState> init(nb);
   int pre_done = 0;
@@ -360,12 +426,15 @@ extern "C++" cudaError_t gf_power_run(GfCtx* h, int which, const int64_t* Mp,
         else if (rl == 4) k_spmv64<4><<<nblk, 256, 0, s>>>(Mp, Mc, Mv, in, mrows, out);
         else if (rl == 8) k_spmv64<8><<<nblk, 256, 0, s>>>(Mp, Mc, Mv, in, mrows, out);
         else k_spmv64<32><<<nblk, 256, 0, s>>>(Mp, Mc, Mv, in, mrows, out);
+        if (nlr) k_spmv64_long<<<(unsigned)nlr, kRedThreads, 0, s>>>(Mp, Mc, Mv, in, lr, out);
       } else {
         k_spmv64<4><<<(unsigned)((N * 4 + 255) / 256), 256, 0, s>>>(Tp, Tr, Tv, in, N, out);
+        if (nlc) k_spmv64_long<<<(unsigned)nlc, kRedThreads, 0, s>>>(Tp, Tr, Tv, in, lc, out);
       }
     } else {
       if (Mp) {
         k_spmv64<4><<<(unsigned)((N * 4 + 255) / 256), 256, 0, s>>>(Mp, Mc, Mv, in, N, out);
+        if (nlr) k_spmv64_long<<<(unsigned)nlr, kRedThreads, 0, s>>>(Mp, Mc, Mv, in, lr, out);
       } else {
         cudaMemsetAsync(out, 0, sizeof(double) * N, s);
       }
@@ -376,30 +445,58 @@ extern "C++" cudaError_t gf_power_run(GfCtx* h, int which, const int64_t* Mp,
       }
     }
   };
-  int host_done = pre_done;
-  for (int t = 0; t < maxit && host_done < nb; ++t) {
-    product(S.v, S.w, false);
-    if (which == 0) {
-      k_chunk_sumsq<<<(unsigned)nrch, kRedThreads, 0, s>>>(S.w, rch, nrch, S.partial);
-      k_inst_sum<<<(nb + 127) / 128, 128, 0, s>>>(S.partial, rptr, nb, 1, 1, S.lam);
-    } else {
-      k_chunk_sumsq<<<(unsigned)h->nvchunk, kRedThreads, 0, s>>>(S.w, h->vchunk, h->nvchunk,
+  // the iteration loop as ONE graph launch: a while node whose body is one
+  // step (products, reductions, bookkeeping, normalisation, counter)
+  if (pre_done < nb) {
+    if ((e = cudaMemsetAsync(S.tc, 0, sizeof(int), s))) return e;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaGraphConditionalHandle hc;
+    if ((e = cudaGraphCreate(&g, 0))) return e;
+    e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node;
+    if (!e) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hc;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (!e) e = cudaStreamBeginCaptureToGraph(s, np.conditional.phGraph_out[0], nullptr, nullptr,
+                                              0, cudaStreamCaptureModeRelaxed);
+    if (!e) {
+      product(S.v, S.w, false);
+      if (which == 0) {
+        k_chunk_sumsq<<<(unsigned)nrch, kRedThreads, 0, s>>>(S.w, rch, nrch, S.partial);
+        k_inst_sum<<<(nb + 127) / 128, 128, 0, s>>>(S.partial, rptr, nb, 1, 1, S.lam);
+      } else {
+        k_chunk_sumsq<<<(unsigned)h->nvchunk, kRedThreads, 0, s>>>(S.w, h->vchunk, h->nvchunk,
+                                                                    S.partial);
+        k_inst_sum<<<(nb + 127) / 128, 128, 0, s>>>(S.partial, h->vchunk_iptr, nb, 1, 1,
+                                                     S.lam);
+      }
+      product(S.w, S.z, true);
+      k_chunk_sumsq<<<(unsigned)h->nvchunk, kRedThreads, 0, s>>>(S.z, h->vchunk, h->nvchunk,
                                                                   S.partial);
-      k_inst_sum<<<(nb + 127) / 128, 128, 0, s>>>(S.partial, h->vchunk_iptr, nb, 1, 1, S.lam);
+      k_inst_sum<<<(nb + 127) / 128, 128, 0, s>>>(S.partial, h->vchunk_iptr, nb, 1, 1, S.zn2);
+      k_pw_step<<<(nb + 127) / 128, 128, 0, s>>>(S.ps, S.lam, S.zn2, nb, S.tc, tol, maxit,
+                                                  S.ndone);
+      k_pw_normalize<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(S.v, S.z, S.zn2, h->var_inst,
+                                                                 S.ps, N);
+      k_pw_next<<<1, 1, 0, s>>>(S.tc, S.ndone, nb, maxit, hc);
+      cudaError_t ec = cudaGetLastError();
+      cudaGraph_t out = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(s, &out);
+      e = ec ? ec : ee;
     }
-    product(S.w, S.z, true);
-    k_chunk_sumsq<<<(unsigned)h->nvchunk, kRedThreads, 0, s>>>(S.z, h->vchunk, h->nvchunk,
-                                                                S.partial);
-    k_inst_sum<<<(nb + 127) / 128, 128, 0, s>>>(S.partial, h->vchunk_iptr, nb, 1, 1, S.zn2);
-    k_pw_step<<<(nb + 127) / 128, 128, 0, s>>>(S.ps, S.lam, S.zn2, nb, t, tol, maxit, S.ndone);
-    k_pw_normalize<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(S.v, S.z, S.zn2, h->var_inst,
-                                                               S.ps, N);
-    if ((e = cudaGetLastError())) return e;
-    if ((t & 15) == 15 || t == maxit - 1) {
-      if ((e = cudaMemcpyAsync(&host_done, S.ndone, sizeof(int), cudaMemcpyDeviceToHost, s)))
-        return e;
-      if ((e = cudaStreamSynchronize(s))) return e;
-    }
+    if (!e) e = cudaGraphInstantiate(&ge, g, 0);
+    if (!e) e = cudaGraphLaunch(ge, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (ge) cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    if (e) return e;
+    h->launches += 1;
   }
   std::vector<PwState> fin(nb);
   if ((e = cudaMemcpyAsync(fin.data(), S.ps, sizeof(PwState) * nb, cudaMemcpyDeviceToHost, s)))
