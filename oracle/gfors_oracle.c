@@ -546,6 +546,60 @@ void orc_repair_min(int64_t n, int64_t ng, const int64_t* gp, const int64_t* gi,
   }
 }
 
+/* General repair after a monotone relaxation (Section 2.4.3): equality rows
+ * with 0/1 coefficients relaxed to covering rows sum_{k in R} x_k >= 1, and
+ * c >= 0, so dropping a selected variable never raises the objective.  The
+ * repair (a reading: the paper leaves it problem-specific) visits each
+ * candidate's selected variables of these rows in decreasing cost, ties to
+ * the larger index first, and drops a variable when every relaxed row that
+ * contains it keeps another selected member ("reverse delete").  The
+ * result is a minimal cover of the rows the candidate covered.  Rows are
+ * CSR (rp, ri: variable lists); they may overlap. */
+static const int64_t* g_rr_cost;
+static int cmp_rr_order(const void* a, const void* b) {
+  const int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+  if (g_rr_cost[x] != g_rr_cost[y]) return g_rr_cost[x] > g_rr_cost[y] ? -1 : 1;
+  return x > y ? -1 : (x < y ? 1 : 0);
+}
+
+void orc_repair_rows(int64_t n, int64_t nr, const int64_t* rp, const int64_t* ri,
+                     const int64_t* cost, int32_t k, uint8_t* X) {
+  /* rows of each variable (CSC of the relaxed rows) */
+  int64_t* deg = calloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t t = 0; t < rp[nr]; ++t) deg[ri[t] + 1]++;
+  for (int64_t v = 0; v < n; ++v) deg[v + 1] += deg[v];
+  int64_t* vr = malloc(sizeof(int64_t) * (size_t)(rp[nr] > 0 ? rp[nr] : 1));
+  int64_t* fill = calloc((size_t)n, sizeof(int64_t));
+  for (int64_t r = 0; r < nr; ++r)
+    for (int64_t t = rp[r]; t < rp[r + 1]; ++t) vr[deg[ri[t]] + fill[ri[t]]++] = r;
+  /* the variables of relaxed rows in decreasing cost (larger index first) */
+  int64_t nv = 0;
+  int64_t* order = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t v = 0; v < n; ++v)
+    if (deg[v + 1] > deg[v]) order[nv++] = v;
+  g_rr_cost = cost;
+  qsort(order, (size_t)nv, sizeof(int64_t), cmp_rr_order);
+  int64_t* cnt = malloc(sizeof(int64_t) * (size_t)(nr > 0 ? nr : 1));
+  for (int32_t s = 0; s < k; ++s) {
+    uint8_t* x = X + (int64_t)s * n;
+    for (int64_t r = 0; r < nr; ++r) {
+      cnt[r] = 0;
+      for (int64_t t = rp[r]; t < rp[r + 1]; ++t) cnt[r] += x[ri[t]];
+    }
+    for (int64_t q = 0; q < nv; ++q) {
+      const int64_t v = order[q];
+      if (!x[v]) continue;
+      int removable = 1;
+      for (int64_t t = deg[v]; t < deg[v + 1]; ++t)
+        if (cnt[vr[t]] < 2) { removable = 0; break; }
+      if (!removable) continue;
+      x[v] = 0;
+      for (int64_t t = deg[v]; t < deg[v + 1]; ++t) cnt[vr[t]]--;
+    }
+  }
+  free(deg); free(vr); free(fill); free(order); free(cnt);
+}
+
 /* ======================================================================
  * EvalBest, evaluation half (Section 3 and Eq. 1), on the ORIGINAL data:
  *   viol_s = #{j : A_j X_s < b_j} + #{j : B_j X_s != d_j}

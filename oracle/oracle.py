@@ -64,6 +64,7 @@ def _load(path):
     L.orc_philox_lane.argtypes = [u64, u32, u32, u32, u32, u64]
     L.orc_philox_lane.restype = u32
     L.orc_repair_min.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
+    L.orc_repair_rows.argtypes = [i64, i64, I64P, I64P, I64P, i32, U8P]
     L.orc_bernoulli_from.argtypes = [i64, i32, i32, F32P, u64, u32, u32, VP, U8P]
     L.orc_philox_lanes.argtypes = [u64, u32, u32, u32, u32, i64, U32P]
     L.orc_row_normalize.argtypes = [i64, i64, I64P, F64P, F64P, F64P]
@@ -180,6 +181,17 @@ def repair_min(X, groups, cost):
     return X
 
 
+def repair_rows(X, rows, cost):
+    """General monotone-relaxation repair: each candidate drops its selected
+    variables of the relaxed covering rows in decreasing cost (larger index
+    first) whenever every such row keeps another selected member."""
+    rp, ri = (np.ascontiguousarray(a, np.int64) for a in rows)
+    cost = np.ascontiguousarray(cost, np.int64)
+    k, n = X.shape
+    lib().orc_repair_rows(n, rp.size - 1, rp, ri, cost, k, X)
+    return X
+
+
 def closure(X, clos):
     rv, rp, ri = (np.ascontiguousarray(a, np.int64) for a in clos)
     k, n = X.shape
@@ -210,6 +222,8 @@ def sample(inst, p32, k, seed, inst_id, round_id, mode=None):
             onehot(p32, inst.groups, k, seed, inst_id, round_id, X)
     if inst.repair is not None:
         repair_min(X, inst.repair, np.asarray(inst.c, np.int64))
+    if getattr(inst, "repair_rows", None) is not None:
+        repair_rows(X, inst.repair_rows, np.asarray(inst.c, np.int64))
     if inst.closure is not None:
         closure(X, inst.closure)
     return X

@@ -35,6 +35,9 @@ class Instance:
     y <- y OR x_k for k in the list (the facility-location closure);
     ``repair`` = (grp_ptr, grp_idx) lists equality groups relaxed to
     "sum >= 1" whose candidates keep only their least-cost selected member.
+    ``repair_rows`` = (row_ptr, row_idx) lists 0/1 equality rows relaxed to
+    "sum >= 1" (possibly overlapping) whose candidates are reduced to minimal
+    covers by reverse delete in decreasing cost.
     """
 
     name: str
@@ -49,6 +52,7 @@ class Instance:
     axial_I: int = 0
     closure: Optional[Tuple[np.ndarray, np.ndarray, np.ndarray]] = None
     repair: Optional[Tuple[np.ndarray, np.ndarray]] = None
+    repair_rows: Optional[Tuple[np.ndarray, np.ndarray]] = None
     meta: dict = field(default_factory=dict)
 
     @property
@@ -188,8 +192,11 @@ def knapsack_batch(ninst: int = 512, nmin: int = 1000, nmax: int = 100000,
 # --------------------------------------------------------------------------
 def assign3d(I: int = 64, idx: int = 0, family: int = A3D, sampler: str = "axial",
              gamma: int = 1, L: Optional[int] = None) -> Instance:
-    """Axial 3D assignment; sampler 'axial' (one (j,k) per i by p) or 'alg4'
-    (the paper's customized sampler with gamma*I entries and L steps)."""
+    """Axial 3D assignment; sampler 'axial' (one (j,k) per i by p), 'alg4'
+    (the paper's customized sampler with gamma*I entries and L steps) or
+    'relaxed' (the monotone relaxation of Section 2.4.3: costs are positive,
+    so the 3I equality rows become covering rows sum >= 1 of A, candidates
+    are plain Bernoulli draws reduced to minimal covers by reverse delete)."""
     rng = _rng(family, idx)
     n = I ** 3
     c = rng.integers(1, 101, size=n).astype(np.float64)
@@ -200,6 +207,11 @@ def assign3d(I: int = 64, idx: int = 0, family: int = A3D, sampler: str = "axial
     B = _csr(rows, cols, np.ones(3 * n), (3 * I, n))
     grp_ptr = np.arange(0, n + 1, I * I, dtype=np.int64)      # rows "per i"
     grp_idx = v.copy()
+    if sampler == "relaxed":
+        inst = Instance(f"assign3d_rel_I{I}_s{idx}", n, c, A=B, b=np.ones(3 * I),
+                        repair_rows=(B.indptr.astype(np.int64), B.indices.astype(np.int64)))
+        inst.meta.update(sampler="relaxed")
+        return inst
     inst = Instance(f"assign3d_I{I}_s{idx}", n, c, B=B, d=np.ones(3 * I),
                     groups=(grp_ptr, grp_idx), axial_I=I)
     if sampler == "alg4":
