@@ -186,6 +186,24 @@ GFORS_API gfors_status gfors_set_assign3d_custom(gfors_handle h, int32_t inst, i
  * claim).  grp_ptr (ngroups + 1, grp_ptr[0] = 0) / grp_idx: disjoint groups
  * of local variable indices.  Needs integral costs; GFORS_E_UNSUPPORTED on
  * a dense-Q or fused single-row batch. */
+/* Monotone relaxation (Section 2.4.3), general repair for instance inst:
+ * the caller has relaxed equality rows with 0/1 coefficients to covering
+ * rows sum_{k in R} x_k >= 1 (rows of A; valid when costs are
+ * non-negative, so dropping a selected variable never raises the
+ * objective).  After sampling (and any group repair, before the closure),
+ * every candidate visits its selected variables of these rows in decreasing
+ * cost c_k, ties to the larger index first, and drops each one whose rows
+ * all keep another selected member ("reverse delete").  The result is a
+ * minimal cover of the rows the candidate covered, never more expensive;
+ * on disjoint rows it keeps the cheapest selected member (ties to the lower
+ * index), as gfors_set_repair_groups does.  row_ptr (nrows + 1, row_ptr[0]
+ * = 0) / row_idx: local variable indices; rows may overlap.  Once per
+ * instance (GFORS_E_STATE after), needs integral costs; GFORS_E_UNSUPPORTED
+ * on a dense-Q or fused single-row batch.  The repair is the paper's
+ * "customized repair step", read here as reverse delete. */
+GFORS_API gfors_status gfors_set_repair_rows(gfors_handle h, int32_t inst, int64_t nrows,
+                                             const int64_t* row_ptr, const int64_t* row_idx);
+
 GFORS_API gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, int64_t ngroups,
                                                const int64_t* grp_ptr, const int64_t* grp_idx);
 

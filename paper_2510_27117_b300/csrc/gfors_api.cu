@@ -1331,6 +1331,71 @@ extern "C" gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, in
   return GFORS_OK;
 }
 
+extern "C" gfors_status gfors_set_repair_rows(gfors_handle h, int32_t inst, int64_t nrows,
+                                              const int64_t* row_ptr, const int64_t* row_idx) {
+  GF_ENTER(h);
+  if (inst < 0 || inst >= h->ninst) return gf_fail(h, GFORS_E_ARG, "bad instance");
+  GfInstHost& I = h->ih[inst];
+  if (nrows <= 0) return GFORS_OK;
+  if (!row_ptr || !row_idx || row_ptr[0] != 0) return gf_fail(h, GFORS_E_ARG, "bad row arrays");
+  if (I.qkind == 1 || h->fused_ok)
+    return gf_fail(h, GFORS_E_UNSUPPORTED, "repair rows on a dense / fused instance");
+  if (!I.integral) return gf_fail(h, GFORS_E_UNSUPPORTED, "repair rows need integral costs");
+  if (I.rr_set) return gf_fail(h, GFORS_E_STATE, "repair rows already set for this instance");
+  std::vector<long long> cost((size_t)I.n);
+  if (cudaError_t e0 = cudaMemcpy(cost.data(), h->cint + I.var_off, sizeof(long long) * I.n,
+                                  cudaMemcpyDeviceToHost))
+    return gf_cuda(h, e0, "repair row costs");
+  // rows (local ids checked) and the rows of each variable
+  std::vector<std::vector<int64_t>> vr((size_t)I.n);
+  for (int64_t r = 0; r < nrows; ++r) {
+    if (row_ptr[r + 1] < row_ptr[r]) return gf_fail(h, GFORS_E_ARG, "row ptr not monotone");
+    for (int64_t t = row_ptr[r]; t < row_ptr[r + 1]; ++t)
+      if (row_idx[t] < 0 || row_idx[t] >= I.n)
+        return gf_fail(h, GFORS_E_ARG, "row index out of range");
+  }
+  if (h->h_rr_ptr.empty()) h->h_rr_ptr.push_back(0);
+  if (h->h_rr_optr.empty()) h->h_rr_optr.push_back(0);
+  if (h->h_rr_vptr.empty()) h->h_rr_vptr.push_back(0);
+  const int64_t r0 = (int64_t)h->h_rr_ptr.size() - 1;        // global id of row 0
+  for (int64_t r = 0; r < nrows; ++r) {
+    for (int64_t t = row_ptr[r]; t < row_ptr[r + 1]; ++t) {
+      h->h_rr_idx.push_back(I.var_off + row_idx[t]);
+      vr[(size_t)row_idx[t]].push_back(r0 + r);
+    }
+    h->h_rr_ptr.push_back((int64_t)h->h_rr_idx.size());
+  }
+  // the row variables in decreasing cost, ties to the larger index first
+  std::vector<int64_t> order;
+  for (int64_t v = 0; v < I.n; ++v)
+    if (!vr[(size_t)v].empty()) order.push_back(v);
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return cost[a] != cost[b] ? cost[a] > cost[b] : a > b;
+  });
+  for (int64_t v : order) {
+    h->h_rr_order.push_back(I.var_off + v);
+    for (int64_t r : vr[(size_t)v]) h->h_rr_vrow.push_back(r);
+    h->h_rr_vptr.push_back((int64_t)h->h_rr_vrow.size());
+  }
+  h->h_rr_optr.push_back((int64_t)h->h_rr_order.size());
+  h->nrr = (int64_t)h->h_rr_ptr.size() - 1;
+  h->nrr_seg = (int64_t)h->h_rr_optr.size() - 1;
+  I.rr_set = true;
+  h->struct_version++;
+  auto up = [&](int64_t*& d, const std::vector<int64_t>& v) {
+    d = gf_alloc_t<int64_t>(h, std::max<size_t>(1, v.size()));
+    return d && cudaMemcpy(d, v.data(), sizeof(int64_t) * v.size(), cudaMemcpyHostToDevice) ==
+                    cudaSuccess;
+  };
+  if (!up(h->rr_ptr, h->h_rr_ptr) || !up(h->rr_idx, h->h_rr_idx) ||
+      !up(h->rr_optr, h->h_rr_optr) || !up(h->rr_order, h->h_rr_order) ||
+      !up(h->rr_vptr, h->h_rr_vptr) || !up(h->rr_vrow, h->h_rr_vrow))
+    return gf_fail(h, GFORS_E_OOM, "repair rows");
+  h->rr_cnt = gf_alloc_t<int32_t>(h, (size_t)h->nrr * h->chunk);
+  if (!h->rr_cnt) return gf_fail(h, GFORS_E_OOM, "repair row counts");
+  return GFORS_OK;
+}
+
 extern "C" gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t nrep,
                                           const int64_t* rep_var, const int64_t* rep_ptr,
                                           const int64_t* rep_idx) {

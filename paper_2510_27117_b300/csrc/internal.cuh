@@ -126,6 +126,7 @@ struct GfInstHost {
   int64_t nrep = 0, rep_off = 0;
   bool single_row = false;          // eligible for fused sample+eval
   int dense_idx = -1;
+  bool rr_set = false;              // general repair rows attached
 };
 
 struct gfors_ctx {
@@ -194,6 +195,15 @@ struct gfors_ctx {
   int64_t* rg_ptr = nullptr;
   int64_t* rg_idx = nullptr;
   int64_t nrg = 0;
+  // general monotone-relaxation repair (reverse delete over relaxed covering
+  // rows): rows (global ids, CSR), per instance segment the row variables
+  // in decreasing cost, each with its rows; per (row, candidate) counts
+  int64_t nrr = 0, nrr_seg = 0;
+  int64_t *rr_ptr = nullptr, *rr_idx = nullptr;   // rows
+  int64_t *rr_optr = nullptr, *rr_order = nullptr;  // segments of the order
+  int64_t *rr_vptr = nullptr, *rr_vrow = nullptr;   // rows of each order position
+  int32_t* rr_cnt = nullptr;                         // nrr x chunk
+  std::vector<int64_t> h_rr_ptr, h_rr_idx, h_rr_optr, h_rr_order, h_rr_vptr, h_rr_vrow;
   long long* key_stage = nullptr;    // 3 per instance: gfors_incumbent_async
   int32_t* bit_g4 = nullptr;
   int32_t* bit_count = nullptr;

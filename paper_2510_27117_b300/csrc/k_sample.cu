@@ -64,6 +64,81 @@ k_repair_min(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi, int
   }
 }
 
+// General repair after a monotone relaxation (reverse delete over relaxed
+// covering rows).  k_rr_count: one warp per (row, candidate word), the
+// members' words in chunks of 32 transposed so that lane b counts candidate
+// b's selected members.  k_rr_delete: one warp per (instance segment, word);
+// the segment's row variables in decreasing cost, four 32-variable chunks
+// of loads in flight; for every variable some candidate selected, each lane
+// (candidate) drops it when all its rows keep another selected member, and
+// the counts follow.  Every lane follows the sequential rule of its own
+// candidate, so the result equals the one-candidate-at-a-time repair.
+__global__ void __launch_bounds__(256)
+k_rr_count(const int64_t* __restrict__ rp, const int64_t* __restrict__ ri, int64_t nr,
+           int kws, int kwu, int chunk, const uint32_t* __restrict__ X,
+           int32_t* __restrict__ cnt) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= nr * kwu) return;                       // whole warps
+  const int64_t r = wid / kwu;
+  const int w = (int)(wid % kwu);
+  const gf::TransposeLane tl = gf::transpose_lane(lane);
+  int c = 0;
+  for (int64_t t0 = rp[r]; t0 < rp[r + 1]; t0 += 32 * kRepairU) {
+    uint32_t word[kRepairU];
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) {
+      const int64_t t = t0 + 32 * u + lane;
+      word[u] = t < rp[r + 1] ? X[ri[t] * kws + w] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) c += __popc(gf::warp_transpose32(word[u], tl));
+  }
+  cnt[r * chunk + 32 * w + lane] = c;
+}
+
+__global__ void __launch_bounds__(256)
+k_rr_delete(const int64_t* __restrict__ optr, const int64_t* __restrict__ order,
+            const int64_t* __restrict__ vptr, const int64_t* __restrict__ vrow, int64_t nseg,
+            int kws, int kwu, int chunk, uint32_t* __restrict__ X, int32_t* __restrict__ cnt) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= nseg * kwu) return;                     // whole warps
+  const int64_t seg = wid / kwu;
+  const int w = (int)(wid % kwu);
+  const int64_t o0 = optr[seg], o1 = optr[seg + 1];
+  const int cand = 32 * w + lane;
+  for (int64_t p0 = o0; p0 < o1; p0 += 32 * kRepairU) {
+    int64_t v[kRepairU];
+    uint32_t m[kRepairU];
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) {
+      const int64_t p = p0 + 32 * u + lane;
+      v[u] = p < o1 ? order[p] : -1;
+      m[u] = v[u] >= 0 ? X[v[u] * kws + w] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kRepairU; ++u) {
+      uint32_t nz = __ballot_sync(0xFFFFFFFFu, m[u] != 0u);
+      while (nz) {                                   // warp-uniform
+        const int l = __ffs(nz) - 1;
+        nz &= nz - 1u;
+        const int64_t vv = __shfl_sync(0xFFFFFFFFu, v[u], l);
+        const uint32_t mm = __shfl_sync(0xFFFFFFFFu, m[u], l);
+        const int64_t p = p0 + 32 * u + l;
+        const int64_t t0 = vptr[p], t1 = vptr[p + 1];
+        bool rem = (mm >> lane) & 1u;
+        for (int64_t t = t0; t < t1; ++t)
+          if (rem && cnt[vrow[t] * chunk + cand] < 2) rem = false;
+        if (rem)
+          for (int64_t t = t0; t < t1; ++t) cnt[vrow[t] * chunk + cand] -= 1;
+        const uint32_t gone = __ballot_sync(0xFFFFFFFFu, rem);
+        if (gone && lane == 0) X[vv * kws + w] = mm & ~gone;
+      }
+    }
+  }
+}
+
 // Indices of the 4-variable groups holding a variable that no group sampler
 // draws (order irrelevant: every entry writes its own words).
 __global__ void k_bit_list(const uint8_t* __restrict__ grouped, int64_t N4,
@@ -623,6 +698,16 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
     k_repair_min<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
         h->rg_ptr, h->rg_idx, h->nrg, h->kw, kw, h->X);
     h->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (h->nrr > 0) {
+    const int64_t wc = h->nrr * kw, wd = h->nrr_seg * kw;
+    k_rr_count<<<(unsigned)((wc * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->rr_ptr, h->rr_idx, h->nrr, h->kw, kw, h->chunk, h->X, h->rr_cnt);
+    k_rr_delete<<<(unsigned)((wd * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->rr_optr, h->rr_order, h->rr_vptr, h->rr_vrow, h->nrr_seg, h->kw, kw, h->chunk, h->X,
+        h->rr_cnt);
+    h->launches += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (h->nrep_tot > 0) {

@@ -66,6 +66,7 @@ _lib.gfors_load_batch.argtypes = [i32, _P(_P(Csr)), _P(vp), _P(_P(Csr)), _P(vp),
 _lib.gfors_set_groups.argtypes = [_H, i32, i32, i64, vp, vp, i32]
 _lib.gfors_set_closure.argtypes = [_H, i32, i64, vp, vp, vp]
 _lib.gfors_set_repair_groups.argtypes = [_H, i32, i64, vp, vp]
+_lib.gfors_set_repair_rows.argtypes = [_H, i32, i64, vp, vp]
 _lib.gfors_pdhg_steps.argtypes = [_H, i64]
 _lib.gfors_sample_eval.argtypes = [_H, i32, u32, i32]
 _lib.gfors_final_round.argtypes = [_H]
@@ -348,6 +349,12 @@ class Handle:
         _check(_lib.gfors_set_repair_groups(self.h, inst, gp.size - 1, _ptr(gp), _ptr(gi)),
                self.h)
 
+    def set_repair_rows(self, inst, rows):
+        """gfors_set_repair_rows: (row_ptr, row_idx) of relaxed covering rows."""
+        rp, ri = (np.ascontiguousarray(a, np.int64) for a in rows)
+        _check(_lib.gfors_set_repair_rows(self.h, inst, rp.size - 1, _ptr(rp), _ptr(ri)),
+               self.h)
+
     def set_closure(self, inst, closure):
         rv, rp, ri = (np.ascontiguousarray(a, np.int64) for a in closure)
         _check(_lib.gfors_set_closure(self.h, inst, rv.size, _ptr(rv), _ptr(rp), _ptr(ri)),
@@ -466,6 +473,8 @@ def load_batch(insts: Sequence, prm: Optional[Params] = None, stream=None,
                 H.set_groups(q, 1, I.groups)
             if getattr(I, "repair", None) is not None:
                 H.set_repair_groups(q, I.repair)
+            if getattr(I, "repair_rows", None) is not None:
+                H.set_repair_rows(q, I.repair_rows)
             if I.closure is not None:
                 H.set_closure(q, I.closure)
     return H

@@ -657,3 +657,71 @@ def test_lp_stats_match_oracle(name):
     else:
         assert np.isnan(st[4]) and st[1] == st[5]
         assert abs(hs[1] - hs[5]) == 0.0
+
+
+# ------------------------------------------------------------ general repair
+def _covering_instance(n, nr, seed):
+    """Random overlapping 0/1 covering rows (relaxed equalities), costs >= 0."""
+    rng = np.random.default_rng(seed)
+    mem = [np.sort(rng.choice(n, size=rng.integers(2, 40), replace=False)) for _ in range(nr)]
+    rp = np.cumsum([0] + [m.size for m in mem]).astype(np.int64)
+    ri = np.concatenate(mem).astype(np.int64)
+    A = sp.csr_matrix((np.ones(ri.size), ri.astype(np.int32), rp), shape=(nr, n))
+    c = rng.integers(0, 30, size=n).astype(np.float64)
+    return W.Instance(f"cover_rel_{seed}", n, c, A=A, b=np.ones(nr), repair_rows=(rp, ri))
+
+
+@pytest.mark.parametrize("case,k_b", [("a3d6", 96), ("a3d12", 160), ("cover", 2048),
+                                      ("a3d8_batch", 128)])
+def test_repair_rows_bit_exact(case, k_b):
+    """Reverse-delete repair on the device against the oracle: relaxed 3D
+    assignments (three overlapping rows per variable), random overlapping
+    covering rows with dense draws (many members compete), a candidate
+    count with a partial word, and a batch in which one instance has no
+    repair rows."""
+    if case == "a3d6":
+        insts = [W.assign3d(I=6, idx=1, sampler="relaxed")]
+    elif case == "a3d12":
+        insts = [W.assign3d(I=12, idx=2, sampler="relaxed")]
+    elif case == "cover":
+        insts = [_covering_instance(300, 60, 5)]
+    else:
+        insts = [W.assign3d(I=8, idx=3, sampler="relaxed"), CASES["setcover"](),
+                 W.assign3d(I=8, idx=4, sampler="relaxed")]
+    gp, op = _params(k_b=k_b)
+    H = G.load_batch(insts, gp)
+    rng = np.random.default_rng(k_b)
+    ps = []
+    for q, I in enumerate(insts):
+        p = (0.3 + 0.7 * rng.random(I.n)).astype(np.float32)
+        H.set_iterate(q, p, p, None)
+        ps.append(p)
+    H.sample_eval(1, 5, 0)
+    for q, I in enumerate(insts):
+        X, viol, obj = H.get_samples(q)
+        Xo = O.sample(I, ps[q], k_b, op.seed, q, 5)
+        assert np.array_equal(X, Xo), (case, q)
+        vo, oo = O.Evaluator(I)(Xo)
+        assert np.array_equal(viol, vo) and np.array_equal(obj, oo)
+    H.destroy()
+
+
+def test_repair_rows_equal_group_repair_on_facility_location():
+    """On the relaxed facility location the customer rows are disjoint, so
+    reverse delete keeps each customer's cheapest selected facility: the
+    candidates equal those of the least-cost group repair."""
+    base = W.facility_location(nf=40, nc=30, idx=6, relaxed=True)
+    rows = base.repair
+    alt = W.facility_location(nf=40, nc=30, idx=6, relaxed=True)
+    alt.repair, alt.repair_rows = None, rows
+    gp, _ = _params(k_b=256)
+    out = []
+    for I in (base, alt):
+        H = G.load(I, gp)
+        p = (0.5 + 0.5 * np.random.default_rng(2).random(I.n)).astype(np.float32)
+        H.set_iterate(0, p, p, None)
+        H.sample_eval(1, 3, 0)
+        out.append(H.get_samples(0))
+        H.destroy()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
