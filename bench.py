@@ -397,6 +397,8 @@ PDHG_KERNELS = {
     "small": "PDHG iterations (k_pdhg_small, one block per instance)",
     "cooperative": "PDHG iterations (k_pdhg_coop, one cooperative launch)",
     "persistent": "k_pdhg_dense_persistent (PDHG, Alg. 2, dense Q GEMV)",
+    "cluster": "PDHG iterations (k_pdhg_cluster, one thread-block cluster per instance, "
+               "xbar and y exchanged in distributed shared memory)",
 }
 
 

@@ -108,12 +108,15 @@ typedef struct {
   int32_t pdhg_mode;   /* 0 auto: one persistent cooperative launch per call
                           for a single dense instance that fits shared
                           memory; one block per instance for instances whose
-                          matrix fits a block's shared memory; the fused
-                          one-row kernels for batches of one-row instances;
-                          otherwise CUDA graphs of per-iteration launches.
-                          1 per-iteration launches only.  2 as 0, plus one
-                          cooperative launch per call for sparse problems
-                          that fit the L2 cache                            */
+                          matrix fits a block's shared memory (one
+                          thread-block cluster of 16 or 8 CTAs per instance
+                          when every instance's cluster fits one wave); the
+                          fused one-row kernels for batches of one-row
+                          instances; otherwise CUDA graphs of per-iteration
+                          launches.  1 per-iteration launches only.  2 as 0,
+                          plus one cooperative launch per call for sparse
+                          problems that fit the L2 cache.  3 as 0 without
+                          the clusters (one block per instance)            */
 } gfors_params;
 
 GFORS_API void gfors_default_params(gfors_params* prm);
@@ -522,13 +525,16 @@ GFORS_API void gfors_tu_free(gfors_tu t);
  * load: bucketed row / column kernels with CUDA-graph replay, the one-row
  * streaming kernels (every instance one row, no Q), one block per instance
  * (instances that fit shared memory), one cooperative launch per call
- * (pdhg_mode 2), or the persistent dense-Q launch.  Host only. */
+ * (pdhg_mode 2), the persistent dense-Q launch, or one thread-block cluster
+ * per instance (few instances that fit shared memory; xbar and y exchanged in
+ * distributed shared memory).  Host only. */
 enum {
   GFORS_PATH_BUCKETS = 0,
   GFORS_PATH_ONE_ROW = 1,
   GFORS_PATH_SMALL = 2,
   GFORS_PATH_COOPERATIVE = 3,
-  GFORS_PATH_PERSISTENT = 4
+  GFORS_PATH_PERSISTENT = 4,
+  GFORS_PATH_CLUSTER = 5
 };
 GFORS_API gfors_status gfors_pdhg_path(gfors_handle h, int32_t* path);
 

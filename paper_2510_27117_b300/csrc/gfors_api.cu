@@ -462,6 +462,7 @@ extern "C" gfors_status gfors_dense_info(gfors_handle h, int32_t inst, int64_t o
 extern "C" gfors_status gfors_pdhg_path(gfors_handle h, int32_t* path) {
   if (!h || !path) return GFORS_E_ARG;
   *path = h->persist_ok ? GFORS_PATH_PERSISTENT
+        : (h->small_ok && h->cluster_C > 0) ? GFORS_PATH_CLUSTER
         : h->small_ok   ? GFORS_PATH_SMALL
         : h->coop_ok    ? GFORS_PATH_COOPERATIVE
         : h->single_ok  ? GFORS_PATH_ONE_ROW

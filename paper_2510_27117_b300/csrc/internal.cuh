@@ -351,6 +351,8 @@ struct gfors_ctx {
   struct GfSmallInst* small_tab = nullptr;
   uint16_t* small_perm = nullptr;   // N: each instance's columns by decreasing length
   long long* small_k0 = nullptr;    // st->k snapshotted before each small launch
+  int cluster_C = 0;                // > 0: one cluster of this many CTAs per instance
+  size_t cluster_smem = 0;
   size_t small_smem = 0;
   // persistent cooperative PDHG launch (dense instance, matrix in smem)
   bool persist_ok = false;

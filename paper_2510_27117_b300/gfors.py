@@ -230,7 +230,8 @@ class Handle:
         """Name of the kernels that run this handle's PDHG iterations."""
         v = C.c_int32(0)
         _check(_lib.gfors_pdhg_path(self.h, C.byref(v)), self.h)
-        return ("buckets", "one_row", "small", "cooperative", "persistent")[v.value]
+        return ("buckets", "one_row", "small", "cooperative", "persistent",
+                "cluster")[v.value]
 
     def sample_eval_range(self, nrounds, first_round_id, proposal, s_begin, s_end):
         _check(_lib.gfors_sample_eval_range(self.h, nrounds, first_round_id, proposal,

@@ -2,7 +2,8 @@
 node per run, CheckHalt evaluated on the device) against the host loop
 (gfors_run): identical iterates, incumbents (objective, round, candidate,
 x), CheckHalt statistics and iteration counts, on every PDHG path the graph
-captures (one-row batches, one block per instance, bucketed launches with
+captures (one-row batches, one block or one thread-block cluster per
+instance, bucketed launches with
 one-hot groups and closure, dense Q with per-iteration launches and
 tensor-core scoring), with halting by CheckHalt and by the iteration
 budget, and with the learned proposals."""
@@ -19,7 +20,9 @@ CASES = {
     "knapsack_batch": (lambda: [W.knapsack(n, idx=40 + q) for q, n in
                                 enumerate((3001, 777, 9000))], {}, "one_row"),
     "setcover_batch": (lambda: [W.set_cover(n=400, m=40, density=0.08, idx=60 + q)
-                                for q in range(3)], {}, "small"),
+                                for q in range(3)], {}, "cluster"),
+    "setcover_batch_small": (lambda: [W.set_cover(n=400, m=40, density=0.08, idx=60 + q)
+                                      for q in range(3)], dict(pdhg_mode=3), "small"),
     "assign3d": (lambda: [W.assign3d(I=24, idx=3)], {}, "buckets"),
     "facloc": (lambda: [W.facility_location(nf=30, nc=400, idx=2)], {}, "buckets"),
     "maxcut_launch": (lambda: [W.max_cut(n=300, idx=1)], dict(pdhg_mode=1, x0=-1.0),
@@ -75,7 +78,8 @@ def test_graph_run_equals_host_loop_budget(name):
     assert b["trig"] == 9
 
 
-@pytest.mark.parametrize("name", ["knapsack_batch", "setcover_batch", "facloc"])
+@pytest.mark.parametrize("name", ["knapsack_batch", "setcover_batch", "setcover_batch_small",
+                                  "facloc"])
 def test_graph_run_equals_host_loop_checkhalt(name):
     """CheckHalt ends the loop early (loose tolerance, short stall window):
     the device decides at the same trigger as the host loop."""

@@ -725,3 +725,33 @@ def test_repair_rows_equal_group_repair_on_facility_location():
         H.destroy()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("kind", ["setcover", "setcover_batch", "tiny", "assign_small"])
+def test_cluster_path_matches_one_block_path(kind):
+    """One thread-block cluster per instance (rows and columns split over
+    the CTAs, xbar and y exchanged in distributed shared memory) against one
+    block per instance (pdhg_mode 3): every row and column is summed the
+    same way, so the iterates agree exactly; calls of uneven length put
+    penalty updates inside and between launches.  'tiny' has fewer rows and
+    columns than CTAs; its rows carry several coefficient values."""
+    insts = {"setcover": lambda: [CASES["setcover"]()],
+             "setcover_batch": lambda: [W.set_cover(n=700, m=90, density=0.05, idx=70 + q)
+                                        for q in range(5)],
+             "tiny": lambda: [W.tiny_bip(n=14, m1=4, m2=1, idx=5, with_Q=False)],
+             "assign_small": lambda: [W.assign3d(I=6, idx=2)]}[kind]()
+    out = []
+    for mode, path in ((0, "cluster"), (3, "small")):
+        gp, _ = _params(k_int=10, pdhg_mode=mode)
+        H = G.load_batch(insts, gp)
+        assert H.pdhg_path() == path
+        for k in (7, 13, 5, 20):
+            H.pdhg_steps(k)
+        out.append(([H.get_iterate(q) for q in range(len(insts))],
+                    [H.get_scales(q) for q in range(len(insts))]))
+        H.destroy()
+    for (a, sa), (b, sb) in zip(zip(*out[0]), zip(*out[1])):
+        for name, u, v in zip(("x", "xbar", "x_prev", "y"), a, b):
+            bad = np.flatnonzero(u != v)
+            assert bad.size == 0, (name, bad[:10], u[bad[:5]], v[bad[:5]], u.size)
+        assert sa[6] == sb[6] and sa[7] == sb[7]
