@@ -400,6 +400,16 @@ static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal, i
     return gf_fail(h, GFORS_E_STATE, "learned proposal requested but none attached");
   cudaError_t e;
   const float* xk = h->x[h->k_host & 1];
+  // the group samplers' cumulative weights depend on p alone, which stays
+  // fixed for the whole call: each source's weights are formed once
+  struct CwCache {
+    GfCtx* h;
+    explicit CwCache(GfCtx* c) : h(c) {
+      h->cw_src[0] = h->cw_src[1] = nullptr;
+      h->cw_cache = true;
+    }
+    ~CwCache() { h->cw_cache = false; }
+  } cw_cache(h);
   if (proposal != 0 && nrounds > 0) {
     // features of this trigger, then the network's probabilities
     if ((e = gf_launch_features(h))) return gf_cuda(h, e, "features");
@@ -1212,7 +1222,9 @@ extern "C" gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t m
     h->grp_inst = gf_alloc_t<int32_t>(h, h->h_grp_inst.size());
     h->grp_local = gf_alloc_t<int32_t>(h, h->h_grp_local.size());
     h->grp_cw = gf_alloc_t<unsigned long long>(h, h->h_grp_idx.size());
-    if (!h->grp_ptr || !h->grp_idx || !h->grp_inst || !h->grp_local || !h->grp_cw)
+    h->grp_cw2 = gf_alloc_t<unsigned long long>(h, h->h_grp_idx.size());
+    if (!h->grp_ptr || !h->grp_idx || !h->grp_inst || !h->grp_local || !h->grp_cw ||
+        !h->grp_cw2)
       return gf_fail(h, GFORS_E_OOM, "group tables");
     if ((e = cudaMemcpy(h->grp_ptr, h->h_grp_ptr.data(), sizeof(int64_t) * h->h_grp_ptr.size(),
                         cudaMemcpyHostToDevice)) ||
@@ -1426,8 +1438,25 @@ extern "C" gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t 
   h->rep_var = gf_alloc_t<int64_t>(h, h->h_rep_var.size());
   h->rep_ptr = gf_alloc_t<int64_t>(h, h->h_rep_ptr.size());
   h->rep_idx = gf_alloc_t<int64_t>(h, h->h_rep_idx.size());
-  if (!h->rep_var || !h->rep_ptr || !h->rep_idx) return gf_fail(h, GFORS_E_OOM, "closure");
+  h->rep_step = gf_alloc_t<int64_t>(h, h->h_rep_var.size());
+  if (!h->rep_var || !h->rep_ptr || !h->rep_idx || !h->rep_step)
+    return gf_fail(h, GFORS_E_OOM, "closure");
+  // lists in constant steps (e.g. x_ij over j for one y_i) are generated in
+  // the kernel instead of read
+  std::vector<int64_t> step(h->h_rep_var.size(), 0);
+  for (size_t q = 0; q < step.size(); ++q) {
+    const int64_t a = h->h_rep_ptr[q], b = h->h_rep_ptr[q + 1];
+    if (b - a < 2) continue;
+    const int64_t d = h->h_rep_idx[a + 1] - h->h_rep_idx[a];
+    if (d <= 0) continue;
+    bool ok = true;
+    for (int64_t t = a + 2; t < b && ok; ++t) ok = h->h_rep_idx[t] - h->h_rep_idx[t - 1] == d;
+    if (ok) step[q] = d;
+  }
   cudaError_t e;
+  if ((e = cudaMemcpy(h->rep_step, step.data(), sizeof(int64_t) * step.size(),
+                      cudaMemcpyHostToDevice)))
+    return gf_cuda(h, e, "closure upload");
   if ((e = cudaMemcpy(h->rep_var, h->h_rep_var.data(), sizeof(int64_t) * h->h_rep_var.size(),
                       cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(h->rep_ptr, h->h_rep_ptr.data(), sizeof(int64_t) * h->h_rep_ptr.size(),

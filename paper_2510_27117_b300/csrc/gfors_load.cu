@@ -228,6 +228,7 @@ struct Stage {
   std::vector<GfURow> ur;
   std::vector<int32_t> ucols;
   std::vector<GfPRow> pr;
+  std::vector<GfPChunk> pch;
   std::vector<GfGRow> gr;
   std::vector<int32_t> gcols, gvals;
   gfors_status status = GFORS_OK;
@@ -411,6 +412,75 @@ void stage_instance(int q, GfInstHost& I, Stage& S, const gfors_params& P,
   I.single_row = (I.m1 == 1 && I.m2 == 0 && I.qkind == 0);
 }
 
+// P rows in runs (v1 in constant steps, one v2, one table; e.g. linking
+// rows x_ij <= y_i over j) become chunks of up to kPChunk rows that carry no
+// per-row data; the rest stay single rows.  Row order changes no count.
+void extract_p_runs(std::vector<GfPRow>& pr, std::vector<GfPChunk>& pch) {
+  // orient each two-variable row so that its more frequent variable (a hub
+  // such as y_i) is v2: swapping x1 and x2 swaps bits 1 and 2 of the table
+  {
+    if (pr.empty()) return;
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (const GfPRow& R : pr) {
+      lo = std::min(lo, R.v1);
+      hi = std::max(hi, R.v1);
+      if (R.v2 >= 0) {
+        lo = std::min(lo, R.v2);
+        hi = std::max(hi, R.v2);
+      }
+    }
+    std::vector<int32_t> cnt_v((size_t)((int64_t)hi - lo + 1), 0);
+    auto cnt = [&](int32_t v) -> int32_t& { return cnt_v[(size_t)(v - lo)]; };
+    for (const GfPRow& R : pr) {
+      ++cnt(R.v1);
+      if (R.v2 >= 0) ++cnt(R.v2);
+    }
+    for (GfPRow& R : pr) {
+      if (R.v2 < 0) continue;
+      const int32_t a = cnt(R.v1), b = cnt(R.v2);
+      if (a > b || (a == b && R.v1 > R.v2)) {
+        std::swap(R.v1, R.v2);
+        const uint32_t t = R.table;
+        R.table = (t & 9u) | ((t & 2u) << 1) | ((t & 4u) >> 1);
+      }
+    }
+  }
+  std::sort(pr.begin(), pr.end(), [](const GfPRow& a, const GfPRow& b) {
+    if (a.table != b.table) return a.table < b.table;
+    if (a.v2 != b.v2) return a.v2 < b.v2;
+    return a.v1 < b.v1;
+  });
+  std::vector<GfPRow> rest;
+  size_t i = 0;
+  while (i < pr.size()) {
+    const auto same = [&](size_t k) {
+      return pr[k].table == pr[i].table && pr[k].v2 == pr[i].v2;
+    };
+    size_t j = i + 1;
+    int64_t d = 0;
+    if (j < pr.size() && same(j) && pr[j].v1 > pr[i].v1) {
+      d = (int64_t)pr[j].v1 - pr[i].v1;
+      while (j < pr.size() && same(j) && (int64_t)pr[j].v1 - pr[j - 1].v1 == d) ++j;
+    }
+    if (j - i >= (size_t)kMinPRun && pr[i].v2 >= 0 && d <= INT32_MAX) {
+      for (size_t a = i; a < j; a += kPChunk) {
+        GfPChunk C{};
+        C.inst = pr[i].inst;
+        C.v1 = pr[a].v1;
+        C.v2 = pr[i].v2;
+        C.table = pr[i].table;
+        C.len = (int32_t)std::min<size_t>(kPChunk, j - a);
+        C.stride = (int32_t)d;
+        pch.push_back(C);
+      }
+    } else {
+      rest.insert(rest.end(), pr.begin() + i, pr.begin() + j);
+    }
+    i = j;
+  }
+  pr.swap(rest);
+}
+
 // Integer evaluation rows of one instance (original data): P rows (<= 2
 // nonzeros, truth table), U rows (equal coefficients: a count bound), G rows.
 void stage_eval_rows(int q, const GfInstHost& I, Stage& S) {
@@ -486,6 +556,7 @@ void stage_eval_rows(int q, const GfInstHost& I, Stage& S) {
       S.gr.push_back(R);
     }
   }
+  extract_p_runs(S.pr, S.pch);
 }
 
 }  // namespace
@@ -993,6 +1064,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     std::vector<GfURow> ur;
     std::vector<int32_t> ucols;
     std::vector<GfPRow> pr;
+    std::vector<GfPChunk> pch;
     std::vector<GfGRow> gr;
     std::vector<int32_t> gcols, gvals;
     std::vector<GfObjChunk> oc;
@@ -1008,6 +1080,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       }
       ucols.insert(ucols.end(), S.ucols.begin(), S.ucols.end());
       pr.insert(pr.end(), S.pr.begin(), S.pr.end());
+      pch.insert(pch.end(), S.pch.begin(), S.pch.end());
       for (GfGRow R : S.gr) {
         R.t0 += (int64_t)gcols.size();
         gr.push_back(R);
@@ -1130,6 +1203,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     }
     h->nurows = (int64_t)ur.size();
     h->nprows = (int64_t)pr.size();
+    h->npchunks = (int64_t)pch.size();
     // general rows longer than kGLong entries after the others: those get a
     // block per (row, candidate word) in evaluation (row order does not
     // change any count)
@@ -1142,6 +1216,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     ALLOC(h->urows, GfURow, ur.size());
     ALLOC(h->ucols, int32_t, ucols.size());
     ALLOC(h->prows, GfPRow, pr.size());
+    ALLOC(h->pchunks, GfPChunk, pch.size());
     ALLOC(h->grows, GfGRow, gr.size());
     ALLOC(h->gcols, int32_t, gcols.size());
     ALLOC(h->gvals, int32_t, gvals.size());
@@ -1179,6 +1254,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     if (!ur.empty()) UP(h->urows, ur.data(), GfURow, ur.size());
     if (!ucols.empty()) UP(h->ucols, ucols.data(), int32_t, ucols.size());
     if (!pr.empty()) UP(h->prows, pr.data(), GfPRow, pr.size());
+    if (!pch.empty()) UP(h->pchunks, pch.data(), GfPChunk, pch.size());
     if (!gr.empty()) UP(h->grows, gr.data(), GfGRow, gr.size());
     if (!gcols.empty()) UP(h->gcols, gcols.data(), int32_t, gcols.size());
     if (!gvals.empty()) UP(h->gvals, gvals.data(), int32_t, gvals.size());

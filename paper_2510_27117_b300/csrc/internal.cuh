@@ -78,6 +78,16 @@ struct GfGRow {                     // general integer row
   int32_t eq;
   int32_t pad;
 };
+struct GfPChunk {                   // run of P rows (v1 + e stride, v2), e < len, one table
+  int32_t inst;
+  int32_t v1, v2;
+  uint32_t table;
+  int32_t len;                      // <= kPChunk
+  int32_t stride;                   // > 0
+  int32_t pad[2];
+};
+constexpr int kPChunk = 256;        // rows per P-row run chunk (one warp)
+constexpr int kMinPRun = 64;        // runs at least this long are evaluated as chunks
 struct GfObjChunk {                 // linear-objective chunk: vars [v0, v1)
   int32_t inst;
   int32_t v0, v1;
@@ -214,11 +224,16 @@ struct gfors_ctx {
   int32_t* grp_inst = nullptr;      // instance of each group
   int32_t* grp_local = nullptr;     // group index within its instance
   unsigned long long* grp_cw = nullptr;  // cumulative weights (per member)
+  unsigned long long* grp_cw2 = nullptr; // a second set (two proposals in one call)
+  const float* cw_src[2] = {nullptr, nullptr};  // p whose weights each set holds
+  bool cw_cache = false;            // within one sampling call: p does not change
   std::vector<int64_t> h_grp_ptr, h_grp_idx;
   std::vector<int32_t> h_grp_inst, h_grp_local;
   bool groups_dirty = false;
   int64_t nrep_tot = 0;
   int64_t* rep_var = nullptr; int64_t* rep_ptr = nullptr; int64_t* rep_idx = nullptr;
+  int64_t* rep_step = nullptr;      // per repaired variable: list = rep_idx[ptr] + t step
+                                    // (arithmetic lists), 0 = read the list
   std::vector<int64_t> h_rep_var, h_rep_ptr, h_rep_idx;
   bool closure_dirty = false;
   int chunk = 0;                    // candidates per pass (multiple of 32)
@@ -235,6 +250,7 @@ struct gfors_ctx {
   GfURow* urows = nullptr; int64_t nurows = 0; int32_t* ucols = nullptr;
   int64_t nurows_cls[3] = {0, 0, 0};  // urows of each class, stored in class order
   GfPRow* prows = nullptr; int64_t nprows = 0;
+  GfPChunk* pchunks = nullptr; int64_t npchunks = 0;   // long runs of P rows
   GfGRow* grows = nullptr; int64_t ngrows = 0; int32_t* gcols = nullptr; int32_t* gvals = nullptr;
   int64_t ngrows_short = 0;         // rows [0, ngrows_short) have <= kGLong entries
   long long* cint = nullptr;        // N, original integer costs

@@ -238,6 +238,71 @@ k_eval_prows(const GfPRow* __restrict__ rows, int64_t nrows,
   }
 }
 
+// Runs of P rows (v1 + e stride, v2), e < len: one warp per chunk; lane l
+// takes rows l, l + 32, ..., kPRowsU of them loaded together.  The words of
+// v2 are loaded once per chunk, and each row's words are one contiguous
+// segment of X.
+constexpr int kPRowsU = 4;
+// A row's violation masks over all candidate words are formed first, and
+// the per-word aggregation runs only when some lane has a violation.
+__global__ void __launch_bounds__(256)
+k_eval_pchunks(const GfPChunk* __restrict__ chunks, int64_t nchunks,
+               const uint32_t* __restrict__ X, int kws, int kwu, int len, int chunk,
+               int32_t* __restrict__ viol) {
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;                       // uniform across the warp
+  const GfPChunk C = chunks[c];
+  const bool vec = (kws % 4) == 0;
+  const uint32_t T = C.table;
+  for (int w0 = 0; w0 < kwu; w0 += kUG) {
+    const int nw = min(kUG, kwu - w0);
+    uint32_t b[kUG];
+    load_words(X, (int64_t)C.v2, kws, w0, nw, vec, b);     // the hub: once per chunk
+    for (int e0 = 0; e0 < C.len; e0 += 32 * kPRowsU) {      // uniform across the warp
+      // the words of kPRowsU rows per lane are loaded before any is used
+      uint32_t a[kPRowsU][kUG];
+#pragma unroll
+      for (int r = 0; r < kPRowsU; ++r) {
+        const int e = e0 + 32 * r + lane;
+        if (e < C.len) {
+          load_words(X, (int64_t)C.v1 + (int64_t)e * C.stride, kws, w0, nw, vec, a[r]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kUG; ++j) a[r][j] = 0u;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kPRowsU; ++r) {
+        const int e = e0 + 32 * r + lane;
+        const bool valid = e < C.len;
+        uint32_t vm[kUG];
+        uint32_t any = 0u;
+#pragma unroll
+        for (int j = 0; j < kUG; ++j) {
+          uint32_t vmask = 0u;
+          if (valid && j < nw) {
+            const uint32_t x = a[r][j], y = b[j];
+            vmask = ((T & 1u) ? (~x & ~y) : 0u) | ((T & 2u) ? (x & ~y) : 0u) |
+                    ((T & 4u) ? (~x & y) : 0u) | ((T & 8u) ? (x & y) : 0u);
+            const int nt = len - 32 * (w0 + j);
+            if (nt < 32) vmask &= (1u << nt) - 1u;
+          }
+          vm[j] = vmask;
+          any |= vmask;
+        }
+        if (!__any_sync(0xFFFFFFFFu, any != 0u)) continue;
+#pragma unroll
+        for (int j = 0; j < kUG; ++j) {
+          if (j >= nw) break;
+          if (__any_sync(0xFFFFFFFFu, vm[j] != 0u))
+            add_violations(vm[j], C.inst, w0 + j, chunk, viol, valid);
+        }
+      }
+    }
+  }
+}
+
 // G rows: 32 per-candidate accumulators.
 __global__ void __launch_bounds__(128)
 k_eval_grows(const GfGRow* __restrict__ rows, int64_t nrows,
@@ -686,6 +751,34 @@ k_extract(const GfInc* __restrict__ inc, const int32_t* __restrict__ var_inst,
   xbest[i] = bit;
 }
 
+// The same per instance: block row b covers instance b's variables and
+// returns at once when its incumbent did not change (no per-variable reads).
+__global__ void __launch_bounds__(256)
+k_extract_inst(const GfInc* __restrict__ inc, const int64_t* __restrict__ var_off,
+               const uint8_t* __restrict__ live, const uint32_t* __restrict__ X, int kws,
+               int s0, int mode, const float* __restrict__ p, uint64_t seed, int inst_base,
+               uint8_t* __restrict__ xbest) {
+  const int b = blockIdx.y;
+  const GfInc I = inc[b];
+  if (!I.changed) return;
+  const int64_t v0 = var_off[b], n = var_off[b + 1] - v0;
+  const int sl = I.sample - s0;
+  for (int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; loc < n;
+       loc += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = v0 + loc;
+    if (!live[i]) { xbest[i] = 0; continue; }
+    uint8_t bit;
+    if (mode == 1) {
+      const uint4 u = gf::philox_call(seed, gf::kStreamBern, (uint32_t)(inst_base + b),
+                                      I.round_id, (uint32_t)I.sample, (uint64_t)(loc >> 2));
+      bit = (gf::lane_of(u, (uint32_t)(loc & 3)) >> 8) < gf::prob_threshold(p[i]);
+    } else {
+      bit = (X[i * kws + (sl >> 5)] >> (sl & 31)) & 1u;
+    }
+    xbest[i] = bit;
+  }
+}
+
 __global__ void k_extract_dense(const GfInc* __restrict__ inc, int b, int64_t v0, int64_t n,
                                 int64_t ld, const uint32_t* __restrict__ Xw, int s0,
                                 uint8_t* __restrict__ xbest) {
@@ -726,6 +819,11 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
     else
       k_eval_urows<2><<<blocks, 256, 0, h->stream>>>(rows, nr, h->ucols, h->X, h->kw, kwu, len,
                                                      h->chunk, h->viol);
+    h->launches++;
+  }
+  if (h->npchunks) {
+    k_eval_pchunks<<<(unsigned)((h->npchunks * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->pchunks, h->npchunks, h->X, h->kw, kwu, len, h->chunk, h->viol);
     h->launches++;
   }
   if (h->nprows) {
@@ -796,9 +894,21 @@ cudaError_t gf_launch_incumbent(GfCtx* h, int s0, int len, int mode, bool last_c
                                                h->inc);
   h->launches++;
   if (h->N > 0 && mode != 2) {
-    k_extract<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(
-        h->inc, h->var_inst, h->var_off_d, h->var_live, h->N, h->X, h->kw, s0, mode,
-        h->last_p, h->prm.seed, h->prm.inst_base, h->xbest);
+    int64_t span = 0;                        // the largest instance's variable range
+    for (int b = 0; b < h->ninst; ++b) {
+      const int64_t end = (b + 1 < h->ninst) ? h->ih[b + 1].var_off : h->N;
+      span = std::max(span, end - h->ih[b].var_off);
+    }
+    if (h->ninst <= 65535) {
+      const dim3 grid((unsigned)std::min<int64_t>((span + 255) / 256, 4096), (unsigned)h->ninst);
+      k_extract_inst<<<grid, 256, 0, h->stream>>>(h->inc, h->var_off_d, h->var_live, h->X,
+                                                   h->kw, s0, mode, h->last_p, h->prm.seed,
+                                                   h->prm.inst_base, h->xbest);
+    } else {
+      k_extract<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(
+          h->inc, h->var_inst, h->var_off_d, h->var_live, h->N, h->X, h->kw, s0, mode,
+          h->last_p, h->prm.seed, h->prm.inst_base, h->xbest);
+    }
     h->launches++;
   }
   for (const GfDenseQ& dq : h->dense) {

@@ -500,10 +500,11 @@ k_axial_grp(const float* __restrict__ p, int64_t v0, int I, int inst, int s0, in
 }
 
 // Closure repair (Section 2.4.3): rep_var[q] |= OR of its list, per word.
-// One block per repaired variable; thread tid owns word tid % kw.
+// One block per repaired variable; thread tid owns word tid % kw.  A list
+// in constant steps (rstep[q] > 0) is generated from its first entry.
 __global__ void k_closure(const int64_t* __restrict__ rv, const int64_t* __restrict__ rp,
-                          const int64_t* __restrict__ ri, int64_t nrep, int kws,
-                          int kw, uint32_t* __restrict__ X) {
+                          const int64_t* __restrict__ ri, const int64_t* __restrict__ rstep,
+                          int64_t nrep, int kws, int kw, uint32_t* __restrict__ X) {
   const int64_t q = blockIdx.x;
   if (q >= nrep) return;
   extern __shared__ uint32_t red[];
@@ -512,8 +513,13 @@ __global__ void k_closure(const int64_t* __restrict__ rv, const int64_t* __restr
   const int slot = threadIdx.x / kw;
   uint32_t acc = 0;
   if (slot < per) {
-    const int64_t a = rp[q], e = rp[q + 1];
-    for (int64_t t = a + slot; t < e; t += per) acc |= X[ri[t] * kws + w];
+    const int64_t a = rp[q], e = rp[q + 1], d = rstep[q];
+    if (d > 0) {
+      const int64_t v0 = ri[a];
+      for (int64_t t = slot; t < e - a; t += per) acc |= X[(v0 + t * d) * kws + w];
+    } else {
+      for (int64_t t = a + slot; t < e; t += per) acc |= X[ri[t] * kws + w];
+    }
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -666,13 +672,29 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (h->ngroups_tot > 0) {
-    k_group_cw<<<(unsigned)((h->ngroups_tot * 32 + 255) / 256), 256, 0, h->stream>>>(
-        h->grp_ptr, h->grp_idx, h->ngroups_tot, p, h->grp_cw);
+    // within one sampling call the weights of a p already formed are reused
+    unsigned long long* cw = h->grp_cw;
+    bool fresh = true;
+    if (h->cw_cache) {
+      int slot = (h->cw_src[0] == p) ? 0 : (h->cw_src[1] == p) ? 1 : -1;
+      if (slot >= 0) {
+        fresh = false;
+      } else {
+        slot = (h->cw_src[0] == nullptr) ? 0 : (h->cw_src[1] == nullptr) ? 1 : 0;
+        h->cw_src[slot] = p;
+      }
+      cw = slot ? h->grp_cw2 : h->grp_cw;
+    }
+    if (fresh) {
+      k_group_cw<<<(unsigned)((h->ngroups_tot * 32 + 255) / 256), 256, 0, h->stream>>>(
+          h->grp_ptr, h->grp_idx, h->ngroups_tot, p, cw);
+      h->launches++;
+    }
     const int64_t warps = h->ngroups_tot * kw;
     k_group_pick<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
-        h->grp_ptr, h->grp_idx, h->grp_inst, h->grp_local, h->ngroups_tot, h->grp_cw, h->kw,
-        kw, s0, len, P.seed, P.inst_base, h->dstate, h->X);
-    h->launches += 2;
+        h->grp_ptr, h->grp_idx, h->grp_inst, h->grp_local, h->ngroups_tot, cw, h->kw, kw, s0,
+        len, P.seed, P.inst_base, h->dstate, h->X);
+    h->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   for (int b = 0; b < h->ninst; ++b) {
@@ -714,7 +736,7 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
     int per = std::max(1, 256 / kw);
     int threads = per * kw;
     k_closure<<<(unsigned)h->nrep_tot, threads, sizeof(uint32_t) * threads, h->stream>>>(
-        h->rep_var, h->rep_ptr, h->rep_idx, h->nrep_tot, h->kw, kw, h->X);
+        h->rep_var, h->rep_ptr, h->rep_idx, h->rep_step, h->nrep_tot, h->kw, kw, h->X);
     h->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
