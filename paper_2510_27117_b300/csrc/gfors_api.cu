@@ -371,10 +371,11 @@ static cudaError_t enqueue_round(GfCtx* h, const float* p_a, const float* p_b, i
       gf_prof_end(h, pi, 1);
     } else {
       pi = gf_prof_begin(h, 1);
-      if ((e = gf_launch_sample(h, p, s0, len, !h->dense.empty()))) return e;
+      bool pick_obj = false;
+      if ((e = gf_launch_sample(h, p, s0, len, !h->dense.empty(), &pick_obj))) return e;
       gf_prof_end(h, pi, 1);
       pi = gf_prof_begin(h, 2);
-      if ((e = gf_launch_eval(h, s0, len))) return e;
+      if ((e = gf_launch_eval(h, s0, len, pick_obj))) return e;
       gf_prof_end(h, pi, 1);
       for (const GfDenseQ& dq : h->dense) {
         pi = gf_prof_begin(h, 3);
@@ -402,6 +403,7 @@ static gfors_status sample_rounds(GfCtx* h, int32_t nrounds, int32_t proposal, i
   const float* xk = h->x[h->k_host & 1];
   // the group samplers' cumulative weights depend on p alone, which stays
   // fixed for the whole call: each source's weights are formed once
+  if (!h->capturing && (e = gf_ensure_pick_obj(h))) return gf_cuda(h, e, "pick objective tables");
   struct CwCache {
     GfCtx* h;
     explicit CwCache(GfCtx* c) : h(c) {
@@ -763,6 +765,7 @@ static gfors_status run_graph_ready(GfCtx* h, int32_t proposal) {
     h->sr_valid = true;
   }
   if (proposal != 0 && (e = gf_prepare_features(h))) return gf_cuda(h, e, "feature buffers");
+  if ((e = gf_ensure_pick_obj(h))) return gf_cuda(h, e, "pick objective tables");
   if (!h->fused_ok && (e = gf_ensure_bit_list(h))) return gf_cuda(h, e, "sampling list");
   const int nb = h->ninst;
   if (!h->halt_ctl) {
@@ -1331,6 +1334,7 @@ extern "C" gfors_status gfors_set_repair_groups(gfors_handle h, int32_t inst, in
     h->h_rg_ptr.push_back(base + grp_ptr[g + 1]);
   }
   h->nrg = (int64_t)h->h_rg_ptr.size() - 1;
+  h->repair_version++;
   h->struct_version++;
   h->rg_ptr = gf_alloc_t<int64_t>(h, h->h_rg_ptr.size());
   h->rg_idx = gf_alloc_t<int64_t>(h, std::max<size_t>(1, h->h_rg_idx.size()));
@@ -1394,6 +1398,7 @@ extern "C" gfors_status gfors_set_repair_rows(gfors_handle h, int32_t inst, int6
   h->nrr = (int64_t)h->h_rr_ptr.size() - 1;
   h->nrr_seg = (int64_t)h->h_rr_optr.size() - 1;
   I.rr_set = true;
+  h->repair_version++;
   h->struct_version++;
   auto up = [&](int64_t*& d, const std::vector<int64_t>& v) {
     d = gf_alloc_t<int64_t>(h, std::max<size_t>(1, v.size()));
@@ -1434,6 +1439,7 @@ extern "C" gfors_status gfors_set_closure(gfors_handle h, int32_t inst, int64_t 
     h->h_rep_ptr.push_back(base + rep_ptr[q + 1]);
   }
   h->nrep_tot = (int64_t)h->h_rep_var.size();
+  h->repair_version++;
   h->struct_version++;
   h->rep_var = gf_alloc_t<int64_t>(h, h->h_rep_var.size());
   h->rep_ptr = gf_alloc_t<int64_t>(h, h->h_rep_ptr.size());

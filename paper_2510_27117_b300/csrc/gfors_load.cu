@@ -1338,6 +1338,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
   ALLOC(h->X, uint32_t, (size_t)N * h->kw);
   ALLOC(h->viol, int32_t, (size_t)ninst * h->chunk);
   ALLOC(h->obj, long long, (size_t)ninst * h->chunk);
+  ALLOC(h->objp, long long, (size_t)ninst * h->chunk);
   if (h->fused_ok) ALLOC(h->fsum, long long, (size_t)ninst * h->chunk);
   ALLOC(h->inc, GfInc, ninst);
   ALLOC(h->xbest, uint8_t, N);

@@ -227,6 +227,15 @@ struct gfors_ctx {
   unsigned long long* grp_cw2 = nullptr; // a second set (two proposals in one call)
   const float* cw_src[2] = {nullptr, nullptr};  // p whose weights each set holds
   bool cw_cache = false;            // within one sampling call: p does not change
+  // objective of one-hot picks: valid when no later repair changes a grouped
+  // variable; objective chunks over 32-variable slabs with an ungrouped
+  // variable and, per slab, the mask of its grouped lanes
+  bool pick_obj_valid = false;
+  long long repair_version = 0;     // bumped when repair groups / rows / closure change
+  long long pick_obj_rv = -1, pick_obj_gv = -1;
+  long long* objp = nullptr;        // [ninst][chunk] costs of the picks
+  GfObjChunk* ochunks_ng = nullptr; int64_t nochunks_ng = 0;
+  uint32_t* slab_gmask = nullptr;   // N / 32
   std::vector<int64_t> h_grp_ptr, h_grp_idx;
   std::vector<int32_t> h_grp_inst, h_grp_local;
   bool groups_dirty = false;
@@ -411,10 +420,16 @@ cudaError_t gf_launch_dense_gemv_q(GfCtx* h, const GfDenseQ& dq, const float* x,
 cudaError_t gf_launch_power(GfCtx* h, int which, const int64_t* Kp, const int32_t* Kc,
                             const double* Kv, const int64_t* Tp, const int32_t* Tr,
                             const double* Tv, int64_t mrows, double* norms, int* iters);
-cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense);
+// pick_obj (may be NULL): set when the one-hot picks also left their costs
+// in objp (gf_launch_eval then evaluates the other variables only)
+cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense,
+                             bool* pick_obj = nullptr);
 cudaError_t gf_ensure_bit_list(GfCtx* h);
 cudaError_t gf_prepare_features(GfCtx* h);
-cudaError_t gf_launch_eval(GfCtx* h, int s0, int len);
+cudaError_t gf_launch_eval(GfCtx* h, int s0, int len, bool pick_obj = false);
+// Whether (and the tables with which) the objective of the one-hot groups'
+// variables can come from the picks: rebuilt when groups or repairs change.
+cudaError_t gf_ensure_pick_obj(GfCtx* h);
 cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len);
 cudaError_t gf_launch_dense_score(GfCtx* h, const GfDenseQ& dq, int s0, int len);
 cudaError_t gf_launch_incumbent(GfCtx* h, int s0, int len, int mode, bool last_chunk);

@@ -459,7 +459,8 @@ __global__ void __launch_bounds__(256)
 k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
                const long long* __restrict__ cint, const long long* __restrict__ gbias,
                const uint8_t* __restrict__ gP, const uint32_t* __restrict__ X, int kws,
-               int kwu, int len, int chunk, long long* __restrict__ obj) {
+               int kwu, int len, int chunk, const uint32_t* __restrict__ gmask,
+               long long* __restrict__ obj) {
   const int64_t c = blockIdx.x;
   if (c >= nch) return;
   const GfObjChunk C = ch[c];
@@ -485,6 +486,11 @@ k_eval_obj_lin(const GfObjChunk* __restrict__ ch, int64_t nch,
           for (int j = 0; j < kQW; ++j)
             if (j < nw) mw[j] = __ldg(src + j);
         }
+      }
+      // lanes whose variable's objective came with the one-hot picks
+      if (gmask && ((gmask[v >> 5] >> lane) & 1u)) {
+#pragma unroll
+        for (int j = 0; j < kQW; ++j) mw[j] = 0u;
       }
       // item by item when at most kSparseLanes (variable, word) pairs of the
       // four words are nonzero (sparse candidates, e.g. one-hot groups)
@@ -796,14 +802,21 @@ __global__ void k_round_end(GfDState* st) { st->round_id += 1u; }
 
 // Exact evaluation of the materialised chunk (bits in h->X) of every
 // non-dense instance into viol / obj (zeroed here).
-cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
+cudaError_t gf_launch_eval(GfCtx* h, int s0, int len, bool pick_obj) {
   (void)s0;
   cudaError_t e;
   const int kwu = (len + 31) / 32;
   if ((e = cudaMemsetAsync(h->viol, 0, sizeof(int32_t) * h->ninst * h->chunk, h->stream)))
     return e;
-  if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
+  // the objective starts from the one-hot picks' costs when the sampler left them
+  if (pick_obj) {
+    if ((e = cudaMemcpyAsync(h->obj, h->objp, sizeof(long long) * h->ninst * h->chunk,
+                             cudaMemcpyDeviceToDevice, h->stream)))
+      return e;
+  } else if ((e = cudaMemsetAsync(h->obj, 0, sizeof(long long) * h->ninst * h->chunk,
+                                  h->stream))) {
     return e;
+  }
   for (int c = 0, r0 = 0; c < 3; r0 += (int)h->nurows_cls[c], ++c) {
     const int64_t nr = h->nurows_cls[c];
     if (!nr) continue;
@@ -846,10 +859,14 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len) {
     h->launches++;
   }
   if (h->nochunks) {
-    k_eval_obj_lin<<<(unsigned)h->nochunks, 256, 0, h->stream>>>(
-        h->ochunks, h->nochunks, h->clin ? h->clin : h->cint, h->cgbias, h->cgP, h->X, h->kw,
-        kwu, len, h->chunk, h->obj);
-    h->launches++;
+    const GfObjChunk* ocs = pick_obj ? h->ochunks_ng : h->ochunks;
+    const int64_t noc = pick_obj ? h->nochunks_ng : h->nochunks;
+    if (noc > 0) {
+      k_eval_obj_lin<<<(unsigned)noc, 256, 0, h->stream>>>(
+          ocs, noc, h->clin ? h->clin : h->cint, h->cgbias, h->cgP, h->X, h->kw, kwu, len,
+          h->chunk, pick_obj ? h->slab_gmask : nullptr, h->obj);
+      h->launches++;
+    }
   }
   if (h->nqchunks) {
     dim3 grid((unsigned)h->nqchunks, (unsigned)((kwu + kQW - 1) / kQW));

@@ -217,55 +217,95 @@ __global__ void k_group_cw(const int64_t* __restrict__ gp, const int64_t* __rest
   }
 }
 
-// One-hot group draw, one warp per (group, word): lane t draws sample
-// s0 + 32 w + t.  With W = total weight > 0 the pick is the first member
-// whose inclusive prefix exceeds floor(u W / 2^32) (exact 128-bit product,
-// binary search); with W = 0 it is member floor(u len / 2^32).  The
-// group's words start zeroed (one memset of the instance's range per
+// One-hot group draw, one warp per (group, word); a block takes one word of
+// kPickWarps consecutive groups: lane t draws sample s0 + 32 w + t.  With W = total weight > 0 the pick is the first
+// member whose inclusive prefix exceeds floor(u W / 2^32) (exact 128-bit
+// product, binary search); with W = 0 it is member floor(u len / 2^32).
+// The group's words start zeroed (one memset of the instance's range per
 // chunk); each distinct pick is written once with the mask of lanes that
-// chose it.
-__global__ void __launch_bounds__(256)
+// chose it.  With cost != NULL the picks' costs are also summed per
+// candidate over the block's warps (same word and instance) into objp.
+constexpr int kPickWarps = 16;
+
+__global__ void __launch_bounds__(32 * kPickWarps)
 k_group_pick(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
              const int32_t* __restrict__ ginst, const int32_t* __restrict__ glocal,
              int64_t ngroups, const unsigned long long* __restrict__ cw, int kws, int kwu,
              int s0, int len, uint64_t seed, int inst_base,
-             const GfDState* __restrict__ st, uint32_t* __restrict__ X) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= ngroups * kwu) return;
-  const int64_t g = wid / kwu;
-  const int w = (int)(wid % kwu);
-  const int64_t a = gp[g], e = gp[g + 1];
-  const int64_t glen = e - a;
-  if (glen <= 0) return;
-  const int sidx = 32 * w + lane;
+             const GfDState* __restrict__ st, uint32_t* __restrict__ X,
+             const long long* __restrict__ cost, unsigned long long* __restrict__ objp,
+             int chunk) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // block b: candidate word b mod kwu of the kPickWarps groups of block row
+  // b / kwu (the kwu blocks of one set of groups run back to back)
+  const int w = (int)(blockIdx.x % (unsigned)kwu);
+  const int64_t g0 = (int64_t)(blockIdx.x / (unsigned)kwu) * kPickWarps + warp;
+  const bool wvalid = g0 < ngroups;
+  const int64_t g = wvalid ? g0 : 0;
   int64_t pick = -1;
-  if (sidx < len) {
-    const uint32_t gl = (uint32_t)glocal[g];
-    const uint4 u4 = gf::philox_call(seed, gf::kStreamGroup, (uint32_t)(inst_base + ginst[g]),
-                                     st->round_id, (uint32_t)(s0 + sidx), gl >> 2);
-    const uint32_t u = gf::lane_of(u4, gl & 3u);
-    const unsigned long long W = cw[e - 1];
-    int64_t pos;
-    if (W == 0ull) {
-      pos = (int64_t)(((unsigned long long)u * (unsigned long long)glen) >> 32);
-    } else {
-      const unsigned long long lo = (unsigned long long)u * W;
-      const unsigned long long hi = __umul64hi((unsigned long long)u, W);
-      const unsigned long long r = (hi << 32) | (lo >> 32);
-      int64_t lo_i = 0, hi_i = glen - 1;      // first position with cw > r
-      while (lo_i < hi_i) {
-        const int64_t mid = (lo_i + hi_i) >> 1;
-        if (cw[a + mid] > r) hi_i = mid; else lo_i = mid + 1;
+  int inst = -1;
+  if (wvalid) {
+    inst = ginst[g];
+    const int64_t a = gp[g], e = gp[g + 1];
+    const int64_t glen = e - a;
+    const int sidx = 32 * w + lane;
+    if (glen > 0 && sidx < len) {
+      const uint32_t gl = (uint32_t)glocal[g];
+      const uint4 u4 = gf::philox_call(seed, gf::kStreamGroup, (uint32_t)(inst_base + inst),
+                                       st->round_id, (uint32_t)(s0 + sidx), gl >> 2);
+      const uint32_t u = gf::lane_of(u4, gl & 3u);
+      const unsigned long long W = cw[e - 1];
+      int64_t pos;
+      if (W == 0ull) {
+        pos = (int64_t)(((unsigned long long)u * (unsigned long long)glen) >> 32);
+      } else {
+        const unsigned long long lo = (unsigned long long)u * W;
+        const unsigned long long hi = __umul64hi((unsigned long long)u, W);
+        const unsigned long long r = (hi << 32) | (lo >> 32);
+        int64_t lo_i = 0, hi_i = glen - 1;      // first position with cw > r
+        while (lo_i < hi_i) {
+          const int64_t mid = (lo_i + hi_i) >> 1;
+          if (cw[a + mid] > r) hi_i = mid; else lo_i = mid + 1;
+        }
+        pos = lo_i;
       }
-      pos = lo_i;
+      pick = gi[a + pos];
     }
-    pick = gi[a + pos];
   }
   const unsigned active = __ballot_sync(0xFFFFFFFFu, pick >= 0);
   const unsigned same = __match_any_sync(0xFFFFFFFFu, pick);
   if (pick >= 0 && lane == __ffs(same & active) - 1)
     X[pick * kws + w] = same & active;
+  if (cost == nullptr) return;                  // the same for the whole grid
+  __shared__ long long red[kPickWarps][32];
+  __shared__ int key_inst[kPickWarps], key_w[kPickWarps];
+  red[warp][lane] = pick >= 0 ? cost[pick] : 0;
+  if (lane == 0) {
+    key_inst[warp] = wvalid ? inst : -1;
+    key_w[warp] = w;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // lane t: candidate 32 w + t; warps with the first warp's (instance,
+    // word) are summed here, any other warp adds its own
+    const int i0 = key_inst[0], w0 = key_w[0];
+    long long sum = 0;
+    for (int q = 0; q < kPickWarps; ++q) {
+      const int iq = key_inst[q];
+      if (iq < 0) continue;
+      const long long x = red[q][lane];
+      if (iq == i0 && key_w[q] == w0) {
+        sum += x;
+      } else {
+        const int cand = 32 * key_w[q] + lane;
+        if (x != 0 && cand < len)
+          atomicAdd(&objp[(int64_t)iq * chunk + cand], (unsigned long long)x);
+      }
+    }
+    const int cand = 32 * w0 + lane;
+    if (i0 >= 0 && sum != 0 && cand < len)
+      atomicAdd(&objp[(int64_t)i0 * chunk + cand], (unsigned long long)sum);
+  }
 }
 
 // Axial 3D assignment, one block per (instance, sample): for i = 0..I-1 the
@@ -644,7 +684,9 @@ cudaError_t gf_ensure_bit_list(GfCtx* h) {
   return cudaSuccess;
 }
 
-cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense) {
+cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for_dense,
+                             bool* pick_obj) {
+  if (pick_obj) *pick_obj = false;
   const gfors_params& P = h->prm;
   cudaError_t e;
   const int kw = (len + 31) / 32;
@@ -690,10 +732,20 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
           h->grp_ptr, h->grp_idx, h->ngroups_tot, p, cw);
       h->launches++;
     }
-    const int64_t warps = h->ngroups_tot * kw;
-    k_group_pick<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, h->stream>>>(
-        h->grp_ptr, h->grp_idx, h->grp_inst, h->grp_local, h->ngroups_tot, cw, h->kw, kw, s0,
-        len, P.seed, P.inst_base, h->dstate, h->X);
+    // the picks' costs, when no later repair changes a grouped variable
+    const bool po = pick_obj && h->pick_obj_valid && h->pick_obj_rv == h->repair_version &&
+                    h->pick_obj_gv == h->grp_version;
+    if (po) {
+      if ((e = cudaMemsetAsync(h->objp, 0, sizeof(long long) * h->ninst * h->chunk, h->stream)))
+        return e;
+      *pick_obj = true;
+    }
+    const int64_t gblocks = (h->ngroups_tot + kPickWarps - 1) / kPickWarps;
+    k_group_pick<<<(unsigned)(gblocks * kw), 32 * kPickWarps, 0,
+                   h->stream>>>(h->grp_ptr, h->grp_idx, h->grp_inst, h->grp_local,
+                                h->ngroups_tot, cw, h->kw, kw, s0, len, P.seed, P.inst_base,
+                                h->dstate, h->X, po ? (h->clin ? h->clin : h->cint) : nullptr,
+                                reinterpret_cast<unsigned long long*>(h->objp), h->chunk);
     h->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -761,5 +813,68 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
       }
     }
   }
+  return cudaSuccess;
+}
+
+// The objective of one-hot groups' variables can come from the picks when no
+// repair that runs after them (least-cost repair groups, reverse delete over
+// repair rows, the closure) changes a grouped variable, and no grouped
+// variable belongs to a dense tensor-core instance.  Then evaluation covers
+// the 32-variable slabs with an ungrouped variable (grouped lanes masked).
+cudaError_t gf_ensure_pick_obj(GfCtx* h) {
+  if (h->pick_obj_rv == h->repair_version && h->pick_obj_gv == h->grp_version)
+    return cudaSuccess;
+  h->pick_obj_valid = false;
+  h->pick_obj_rv = h->repair_version;
+  h->pick_obj_gv = h->grp_version;
+  if (h->ngroups_tot <= 0 || !h->all_integral) return cudaSuccess;
+  const int64_t N = h->N;
+  std::vector<uint32_t> gm((size_t)(N / 32), 0u);
+  for (int64_t v : h->h_grp_idx) gm[(size_t)(v >> 5)] |= 1u << (v & 31);
+  auto grouped = [&](int64_t v) { return (gm[(size_t)(v >> 5)] >> (v & 31)) & 1u; };
+  for (int64_t v : h->h_rep_var)
+    if (grouped(v)) return cudaSuccess;
+  for (int64_t v : h->h_rg_idx)
+    if (grouped(v)) return cudaSuccess;
+  for (int64_t v : h->h_rr_idx)
+    if (grouped(v)) return cudaSuccess;
+  for (int b = 0; b < h->ninst; ++b) {
+    const GfInstHost& I = h->ih[b];
+    if (I.qkind != 1) continue;
+    for (int64_t v = I.var_off; v < I.var_off + I.npad; v += 32)
+      if (gm[(size_t)(v >> 5)]) return cudaSuccess;
+  }
+  // objective chunks (<= 256 variables: these slabs are few, and denser
+  // than grouped ones) over slabs with an ungrouped lane
+  std::vector<GfObjChunk> oc;
+  for (int b = 0; b < h->ninst; ++b) {
+    const GfInstHost& I = h->ih[b];
+    if (I.qkind == 1) continue;
+    int64_t start = -1;
+    const int64_t aend = (I.n + 31) / 32 * 32;   // one step past the last slab
+    for (int64_t a = 0; a <= aend; a += 32) {
+      const bool open = a < I.n && gm[(size_t)((I.var_off + a) >> 5)] != 0xFFFFFFFFu;
+      if (open && start < 0) start = a;
+      const bool close = start >= 0 && (!open || a - start >= 256);
+      if (close) {
+        oc.push_back(GfObjChunk{b, (int32_t)(I.var_off + start),
+                                (int32_t)(I.var_off + std::min<int64_t>(a, I.n)), 0});
+        start = open ? a : -1;
+      }
+    }
+  }
+  h->ochunks_ng = gf_alloc_t<GfObjChunk>(h, std::max<size_t>(1, oc.size()));
+  h->slab_gmask = gf_alloc_t<uint32_t>(h, std::max<size_t>(1, gm.size()));
+  if (!h->ochunks_ng || !h->slab_gmask) return cudaErrorMemoryAllocation;
+  cudaError_t e;
+  if (!oc.empty() &&
+      (e = cudaMemcpy(h->ochunks_ng, oc.data(), sizeof(GfObjChunk) * oc.size(),
+                      cudaMemcpyHostToDevice)))
+    return e;
+  if (!gm.empty() && (e = cudaMemcpy(h->slab_gmask, gm.data(), sizeof(uint32_t) * gm.size(),
+                                     cudaMemcpyHostToDevice)))
+    return e;
+  h->nochunks_ng = (int64_t)oc.size();
+  h->pick_obj_valid = true;
   return cudaSuccess;
 }
