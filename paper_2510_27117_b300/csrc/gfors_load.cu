@@ -1040,6 +1040,70 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       }
       h->cb.push_back(B);
     }
+    // runs of at least 8 consecutive long columns of one length (one
+    // instance, no Q part) in slices of 32 with interleaved entries; their
+    // chunks are marked part 2 (done by the slice kernel)
+    std::vector<int4> sblk;
+    std::vector<int64_t> soff, ssrc;
+    std::vector<int32_t> slen, spb, sidx;
+    for (size_t q = 0; q < lid.size();) {
+      const int64_t i0 = lid[q];
+      const int64_t L = Tp[i0 + 1] - Tp[i0];
+      auto fits = [&](size_t k) {
+        const int64_t i = lid[k];
+        return Qp[i + 1] == Qp[i] && Tp[i + 1] - Tp[i] == L && var_inst[i] == var_inst[i0];
+      };
+      if (!fits(q)) {
+        ++q;
+        continue;
+      }
+      size_t r = q + 1;
+      while (r < lid.size() && fits(r)) ++r;
+      if (r - q >= 8 && L <= (int64_t)INT32_MAX / 32) {
+        for (size_t a = q; a < r; a += 32) {
+          const int nc = (int)std::min<size_t>(32, r - a);
+          const int sl = (int)slen.size();
+          soff.push_back((int64_t)sidx.size());
+          slen.push_back((int32_t)L);
+          for (int l = 0; l < 32; ++l) {
+            if (l < nc) {
+              spb.push_back(lptr[a + l]);
+              ssrc.push_back(Tp[lid[a + l]]);
+              for (int c = lptr[a + l]; c < lptr[a + l + 1]; ++c) ch[c].part = 2;
+            } else {
+              spb.push_back(-1);
+              ssrc.push_back(-1);
+            }
+          }
+          sidx.resize(sidx.size() + (size_t)L * 32);
+          for (int64_t e = 0; e < L; ++e)
+            for (int l = 0; l < 32; ++l)
+              sidx[(size_t)(soff[sl] + 32 * e + l)] = (l < nc) ? Tr[Tp[lid[a + l]] + e] : -1;
+          for (int64_t c = 0; c * kChunkLen < L; ++c) sblk.push_back(make_int4(sl, (int)c, nc, 0));
+        }
+      }
+      q = r;
+    }
+    h->csl.nslices = (int32_t)slen.size();
+    h->csl.nblocks = (int32_t)sblk.size();
+    if (!slen.empty()) {
+      ALLOC(h->csl.blk, int4, sblk.size());
+      ALLOC(h->csl.off, int64_t, soff.size());
+      ALLOC(h->csl.len, int32_t, slen.size());
+      ALLOC(h->csl.pbase, int32_t, spb.size());
+      ALLOC(h->csl.sidx, int32_t, sidx.size());
+      ALLOC(h->csl.sval, float, sidx.size());
+      int64_t* ssrc_d = gf_alloc_t<int64_t>(h, ssrc.size());
+      if (!ssrc_d) return gf_fail(h, GFORS_E_OOM, "column slices");
+      UP(h->csl.blk, sblk.data(), int4, sblk.size());
+      UP(h->csl.off, soff.data(), int64_t, soff.size());
+      UP(h->csl.len, slen.data(), int32_t, slen.size());
+      UP(h->csl.pbase, spb.data(), int32_t, spb.size());
+      UP(h->csl.sidx, sidx.data(), int32_t, sidx.size());
+      UP(ssrc_d, ssrc.data(), int64_t, ssrc.size());
+      GF_CK(h, gf_fill_slices(h, ssrc_d));
+      GF_CK(h, cudaStreamSynchronize(s));
+    }
     h->clong.nlong = (int32_t)lid.size();
     h->clong.nchunks = (int32_t)ch.size();
     if (!lid.empty()) {

@@ -56,6 +56,20 @@ struct GfLongSet {
   float2* partial = nullptr;        // device: (s, c) per chunk
 };
 
+// Long K^T columns of one length in slices of 32 (sliced ELL): entry e of
+// the slice's column l sits at off + 32 e + l, so that a warp reads 32
+// columns' entries (and, for columns whose rows are consecutive, the dual
+// values) contiguously.  Each block (slice, chunk c) writes the chunk
+// partials of the clong layout (kChunkLen entries per column chunk).
+struct GfColSlices {
+  int32_t nslices = 0, nblocks = 0;
+  int4* blk = nullptr;              // per block: (slice, chunk, columns, 0)
+  int64_t* off = nullptr;           // per slice: first entry
+  int32_t* len = nullptr;           // per slice: entries per column
+  int32_t* pbase = nullptr;         // [slice][32]: partial index of chunk 0 (-1: empty lane)
+  int32_t* sidx = nullptr;          // interleaved row indices (-1: empty lane)
+  float* sval = nullptr;            // interleaved scaled values
+};
 // ---------------------------------------------------------------------------
 // Evaluation structures (original, unscaled, integer data).
 // ---------------------------------------------------------------------------
@@ -193,6 +207,7 @@ struct gfors_ctx {
   // PDHG work lists
   std::vector<GfBucket> rb, cb;     // row / column buckets
   GfLongSet rlong, clong;
+  GfColSlices csl;                  // long K^T columns in slices of 32
   std::vector<GfDenseQ> dense;
 
   // sampling
@@ -430,6 +445,8 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len, bool pick_obj = false);
 // Whether (and the tables with which) the objective of the one-hot groups'
 // variables can come from the picks: rebuilt when groups or repairs change.
 cudaError_t gf_ensure_pick_obj(GfCtx* h);
+// Interleaved scaled values of the long-column slices (at load).
+cudaError_t gf_fill_slices(GfCtx* h, const int64_t* src_d);
 cudaError_t gf_launch_fused(GfCtx* h, const float* p, int s0, int len);
 cudaError_t gf_launch_dense_score(GfCtx* h, const GfDenseQ& dq, int s0, int len);
 cudaError_t gf_launch_incumbent(GfCtx* h, int s0, int len, int mode, bool last_chunk);

@@ -448,6 +448,7 @@ k_long_partial(const GfChunk* __restrict__ ch, int32_t nch,
   const int c = blockIdx.x;
   if (c >= nch) return;
   const GfChunk k = ch[c];
+  if (k.part == 2) return;                     // a column slice computes this chunk
   CSum acc;
   if (k.part == 0) {
     // chunks of kChunkLen = 8 x 256 entries: all eight gathers in flight
@@ -465,6 +466,67 @@ k_long_partial(const GfChunk* __restrict__ ch, int32_t nch,
     CSum tot;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot.merge(ss[q], sc_[q]);
     partial[c] = make_float2(tot.s, tot.c);
+  }
+}
+
+// Long K^T columns in slices of 32 (sliced ELL): block (slice, chunk c),
+// warp w takes entries e = e0 + w, e0 + w + 8, ... (four loads in flight),
+// lane l column l; the warps' compensated sums are merged in warp order and
+// written as the partial of chunk c of each column.
+__global__ void __launch_bounds__(256)
+k_long_slices(const int4* __restrict__ blk, const int64_t* __restrict__ off,
+              const int32_t* __restrict__ len, const int32_t* __restrict__ pbase,
+              const int32_t* __restrict__ sidx, const float* __restrict__ sval,
+              const float* __restrict__ vec, float2* __restrict__ partial) {
+  const int4 B = blk[blockIdx.x];
+  const int sl = B.x, c = B.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t L = len[sl], base = off[sl];
+  const int64_t e0 = (int64_t)c * kChunkLen, e1 = min(L, e0 + (int64_t)kChunkLen);
+  CSum acc;
+  for (int64_t e = e0 + warp; e < e1; e += 32) {
+    int32_t r[4];
+    float v[4], g[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t ee = e + 8 * u;
+      r[u] = -1;
+      v[u] = 0.0f;
+      if (ee < e1) {
+        r[u] = sidx[base + 32 * ee + lane];
+        v[u] = sval[base + 32 * ee + lane];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) g[u] = r[u] >= 0 ? vec[r[u]] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r[u] >= 0) acc.add(__fmul_rn(v[u], g[u]));
+  }
+  __shared__ float ss[8][32], sc_[8][32];
+  ss[warp][lane] = acc.s;
+  sc_[warp][lane] = acc.c;
+  __syncthreads();
+  if (warp == 0) {
+    CSum tot;
+    for (int q = 0; q < 8; ++q) tot.merge(ss[q][lane], sc_[q][lane]);
+    const int pb = pbase[sl * 32 + lane];
+    if (pb >= 0) partial[pb + c] = make_float2(tot.s, tot.c);
+  }
+}
+
+__global__ void k_fill_slices(const int64_t* __restrict__ src, const int64_t* __restrict__ off,
+                              const int32_t* __restrict__ len, int32_t nslices,
+                              const float* __restrict__ Tv, float* __restrict__ sval) {
+  const int sl = blockIdx.y;
+  if (sl >= nslices) return;
+  const int64_t L = len[sl];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 32 * L;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(t & 31);
+    const int64_t e = t >> 5;
+    const int64_t s0 = src[sl * 32 + l];
+    sval[off[sl] + t] = s0 >= 0 ? Tv[s0 + e] : 0.0f;
   }
 }
 
@@ -831,6 +893,12 @@ cudaError_t gf_launch_pdhg_iter(GfCtx* h, int parity) {
     if (e != cudaSuccess) return e;
   }
   if (h->clong.nlong) {
+    if (h->csl.nblocks) {
+      k_long_slices<<<h->csl.nblocks, 256, 0, h->stream>>>(
+          h->csl.blk, h->csl.off, h->csl.len, h->csl.pbase, h->csl.sidx, h->csl.sval, h->y,
+          h->clong.partial);
+      h->launches++;
+    }
     k_long_partial<<<h->clong.nchunks, 256, 0, h->stream>>>(
         h->clong.chunks, h->clong.nchunks, h->Tr, h->Tv, h->y, h->Qc, h->Qv, xo,
         h->clong.partial);
@@ -934,4 +1002,12 @@ cudaError_t gf_tune_lanes(GfCtx* h, int32_t lanes_out[10]) {
     lanes_out[5 + k] = k < (int)h->cb.size() ? h->cb[k].lanes : 0;
   }
   return e;
+}
+
+// Scaled values of the column slices from the CSC arrays (at load).
+cudaError_t gf_fill_slices(GfCtx* h, const int64_t* src_d) {
+  const dim3 grid(256, (unsigned)h->csl.nslices);
+  k_fill_slices<<<grid, 256, 0, h->stream>>>(src_d, h->csl.off, h->csl.len, h->csl.nslices,
+                                             h->Tv, h->csl.sval);
+  return cudaGetLastError();
 }

@@ -47,6 +47,9 @@ CASES = {
     # more than 2,048 customers: every facility column y_i is a long CSC
     # column (chunked partial sums plus a finalising pass)
     "facloc_long": lambda: W.facility_location(nf=6, nc=3000, idx=2),
+    # 40 long facility columns of one length: a full slice of 32 and one of 8
+    # (interleaved sliced-ELL partial sums)
+    "facloc_slices": lambda: W.facility_location(nf=40, nc=2100, idx=3),
 }
 
 
