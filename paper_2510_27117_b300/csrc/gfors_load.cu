@@ -16,6 +16,7 @@
 #include <numeric>
 #include <stdexcept>
 #include <thread>
+#include <tuple>
 
 #include <cuda_fp8.h>
 
@@ -229,6 +230,7 @@ struct Stage {
   std::vector<int32_t> ucols;
   std::vector<GfPRow> pr;
   std::vector<GfPChunk> pch;
+  std::vector<GfPSlice> psl;
   std::vector<GfGRow> gr;
   std::vector<int32_t> gcols, gvals;
   gfors_status status = GFORS_OK;
@@ -481,6 +483,53 @@ void extract_p_runs(std::vector<GfPRow>& pr, std::vector<GfPChunk>& pch) {
   pr.swap(rest);
 }
 
+// Chunks of equal table, stride and length whose hubs are consecutive and
+// whose first rows are consecutive (v1 - v2 equal; e.g. the same customer
+// range of consecutive facilities' linking rows) are put side by side in
+// slices of up to 32: lane l of a warp then reads variable v1 + l + e stride,
+// adjacent to its neighbours'.  Chunks in no slice of 8 or more stay.
+void slice_p_chunks(std::vector<GfPChunk>& pch, std::vector<GfPSlice>& psl) {
+  std::vector<size_t> ord(pch.size());
+  std::iota(ord.begin(), ord.end(), 0);
+  auto key = [&](size_t i) {
+    const GfPChunk& C = pch[i];
+    return std::make_tuple(C.table, C.stride, C.len, (int64_t)C.v1 - C.v2, C.v2);
+  };
+  std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return key(a) < key(b); });
+  std::vector<GfPChunk> rest;
+  size_t i = 0;
+  while (i < ord.size()) {
+    const GfPChunk& A = pch[ord[i]];
+    size_t j = i + 1;
+    while (j < ord.size()) {
+      const GfPChunk& B = pch[ord[j]];
+      const GfPChunk& P = pch[ord[j - 1]];
+      if (B.table != A.table || B.stride != A.stride || B.len != A.len ||
+          (int64_t)B.v1 - B.v2 != (int64_t)A.v1 - A.v2 || B.v2 != P.v2 + 1)
+        break;
+      ++j;
+    }
+    if (j - i >= 8) {
+      for (size_t a = i; a < j; a += 32) {
+        const GfPChunk& C = pch[ord[a]];
+        GfPSlice S{};
+        S.inst = C.inst;
+        S.v1 = C.v1;
+        S.v2 = C.v2;
+        S.table = C.table;
+        S.len = C.len;
+        S.stride = C.stride;
+        S.lanes = (int32_t)std::min<size_t>(32, j - a);
+        psl.push_back(S);
+      }
+    } else {
+      for (size_t a = i; a < j; ++a) rest.push_back(pch[ord[a]]);
+    }
+    i = j;
+  }
+  pch.swap(rest);
+}
+
 // Integer evaluation rows of one instance (original data): P rows (<= 2
 // nonzeros, truth table), U rows (equal coefficients: a count bound), G rows.
 void stage_eval_rows(int q, const GfInstHost& I, Stage& S) {
@@ -557,6 +606,7 @@ void stage_eval_rows(int q, const GfInstHost& I, Stage& S) {
     }
   }
   extract_p_runs(S.pr, S.pch);
+  slice_p_chunks(S.pch, S.psl);
 }
 
 }  // namespace
@@ -1129,6 +1179,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     std::vector<int32_t> ucols;
     std::vector<GfPRow> pr;
     std::vector<GfPChunk> pch;
+    std::vector<GfPSlice> psl;
     std::vector<GfGRow> gr;
     std::vector<int32_t> gcols, gvals;
     std::vector<GfObjChunk> oc;
@@ -1145,6 +1196,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
       ucols.insert(ucols.end(), S.ucols.begin(), S.ucols.end());
       pr.insert(pr.end(), S.pr.begin(), S.pr.end());
       pch.insert(pch.end(), S.pch.begin(), S.pch.end());
+      psl.insert(psl.end(), S.psl.begin(), S.psl.end());
       for (GfGRow R : S.gr) {
         R.t0 += (int64_t)gcols.size();
         gr.push_back(R);
@@ -1268,6 +1320,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     h->nurows = (int64_t)ur.size();
     h->nprows = (int64_t)pr.size();
     h->npchunks = (int64_t)pch.size();
+    h->npslices = (int64_t)psl.size();
     // general rows longer than kGLong entries after the others: those get a
     // block per (row, candidate word) in evaluation (row order does not
     // change any count)
@@ -1281,6 +1334,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     ALLOC(h->ucols, int32_t, ucols.size());
     ALLOC(h->prows, GfPRow, pr.size());
     ALLOC(h->pchunks, GfPChunk, pch.size());
+    ALLOC(h->pslices, GfPSlice, psl.size());
     ALLOC(h->grows, GfGRow, gr.size());
     ALLOC(h->gcols, int32_t, gcols.size());
     ALLOC(h->gvals, int32_t, gvals.size());
@@ -1319,6 +1373,7 @@ static gfors_status load_impl(GfCtx* h, int32_t ninst, const gfors_csr* const* A
     if (!ucols.empty()) UP(h->ucols, ucols.data(), int32_t, ucols.size());
     if (!pr.empty()) UP(h->prows, pr.data(), GfPRow, pr.size());
     if (!pch.empty()) UP(h->pchunks, pch.data(), GfPChunk, pch.size());
+    if (!psl.empty()) UP(h->pslices, psl.data(), GfPSlice, psl.size());
     if (!gr.empty()) UP(h->grows, gr.data(), GfGRow, gr.size());
     if (!gcols.empty()) UP(h->gcols, gcols.data(), int32_t, gcols.size());
     if (!gvals.empty()) UP(h->gvals, gvals.data(), int32_t, gvals.size());

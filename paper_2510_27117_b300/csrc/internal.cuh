@@ -100,6 +100,15 @@ struct GfPChunk {                   // run of P rows (v1 + e stride, v2), e < le
   int32_t stride;                   // > 0
   int32_t pad[2];
 };
+struct GfPSlice {                   // up to 32 P-row chunks side by side: lane l has
+  int32_t inst;                     // hub v2 + l and rows (v1 + l + e stride, v2 + l)
+  int32_t v1, v2;
+  uint32_t table;
+  int32_t len;
+  int32_t stride;
+  int32_t lanes;
+  int32_t pad;
+};
 constexpr int kPChunk = 256;        // rows per P-row run chunk (one warp)
 constexpr int kMinPRun = 64;        // runs at least this long are evaluated as chunks
 struct GfObjChunk {                 // linear-objective chunk: vars [v0, v1)
@@ -275,6 +284,7 @@ struct gfors_ctx {
   int64_t nurows_cls[3] = {0, 0, 0};  // urows of each class, stored in class order
   GfPRow* prows = nullptr; int64_t nprows = 0;
   GfPChunk* pchunks = nullptr; int64_t npchunks = 0;   // long runs of P rows
+  GfPSlice* pslices = nullptr; int64_t npslices = 0;   // runs side by side
   GfGRow* grows = nullptr; int64_t ngrows = 0; int32_t* gcols = nullptr; int32_t* gvals = nullptr;
   int64_t ngrows_short = 0;         // rows [0, ngrows_short) have <= kGLong entries
   long long* cint = nullptr;        // N, original integer costs

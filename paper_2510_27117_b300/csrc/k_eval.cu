@@ -303,6 +303,70 @@ k_eval_pchunks(const GfPChunk* __restrict__ chunks, int64_t nchunks,
   }
 }
 
+// Slices of P-row runs: one warp per slice, lane l the run of hub v2 + l
+// (its words loaded once) over rows v1 + l + e stride, kPRowsU rows in
+// flight; a warp's loads of one row index e are adjacent variables.
+__global__ void __launch_bounds__(256)
+k_eval_pslices(const GfPSlice* __restrict__ sl, int64_t nsl, const uint32_t* __restrict__ X,
+               int kws, int kwu, int len, int chunk, int32_t* __restrict__ viol) {
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nsl) return;                           // uniform across the warp
+  const GfPSlice S = sl[c];
+  const bool vec = (kws % 4) == 0;
+  const uint32_t T = S.table;
+  const bool lv = lane < S.lanes;
+  for (int w0 = 0; w0 < kwu; w0 += kUG) {
+    const int nw = min(kUG, kwu - w0);
+    uint32_t b[kUG];
+    if (lv) {
+      load_words(X, (int64_t)S.v2 + lane, kws, w0, nw, vec, b);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kUG; ++j) b[j] = 0u;
+    }
+    for (int e0 = 0; e0 < S.len; e0 += kPRowsU) {  // uniform across the warp
+      uint32_t a[kPRowsU][kUG];
+#pragma unroll
+      for (int r = 0; r < kPRowsU; ++r) {
+        const int e = e0 + r;
+        if (lv && e < S.len) {
+          load_words(X, (int64_t)S.v1 + lane + (int64_t)e * S.stride, kws, w0, nw, vec, a[r]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kUG; ++j) a[r][j] = 0u;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kPRowsU; ++r) {
+        const bool valid = lv && e0 + r < S.len;
+        uint32_t vm[kUG];
+        uint32_t any = 0u;
+#pragma unroll
+        for (int j = 0; j < kUG; ++j) {
+          uint32_t vmask = 0u;
+          if (valid && j < nw) {
+            const uint32_t x = a[r][j], y = b[j];
+            vmask = ((T & 1u) ? (~x & ~y) : 0u) | ((T & 2u) ? (x & ~y) : 0u) |
+                    ((T & 4u) ? (~x & y) : 0u) | ((T & 8u) ? (x & y) : 0u);
+            const int nt = len - 32 * (w0 + j);
+            if (nt < 32) vmask &= (1u << nt) - 1u;
+          }
+          vm[j] = vmask;
+          any |= vmask;
+        }
+        if (!__any_sync(0xFFFFFFFFu, any != 0u)) continue;
+#pragma unroll
+        for (int j = 0; j < kUG; ++j) {
+          if (j >= nw) break;
+          if (__any_sync(0xFFFFFFFFu, vm[j] != 0u))
+            add_violations(vm[j], S.inst, w0 + j, chunk, viol, valid);
+        }
+      }
+    }
+  }
+}
+
 // G rows: 32 per-candidate accumulators.
 __global__ void __launch_bounds__(128)
 k_eval_grows(const GfGRow* __restrict__ rows, int64_t nrows,
@@ -832,6 +896,11 @@ cudaError_t gf_launch_eval(GfCtx* h, int s0, int len, bool pick_obj) {
     else
       k_eval_urows<2><<<blocks, 256, 0, h->stream>>>(rows, nr, h->ucols, h->X, h->kw, kwu, len,
                                                      h->chunk, h->viol);
+    h->launches++;
+  }
+  if (h->npslices) {
+    k_eval_pslices<<<(unsigned)((h->npslices * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->pslices, h->npslices, h->X, h->kw, kwu, len, h->chunk, h->viol);
     h->launches++;
   }
   if (h->npchunks) {

@@ -129,7 +129,7 @@ def test_pdhg_single_step(name, mode):
                                        ("tiny", 0), ("maxcut", 0), ("assign3d", 0),
                                        ("facloc", 0), ("maxcut_csr", 0),
                                        ("maxcut_sparse", 0), ("facloc_tu", 0),
-                                       ("facloc_rel", 0)])
+                                       ("facloc_rel", 0), ("facloc_slices", 0)])
 def test_sampling_and_evaluation_bit_exact(name, mode):
     inst = CASES[name]()
     gp, op = _params(eval_mode=mode, k_b=96 if name != "maxcut" else 128)
