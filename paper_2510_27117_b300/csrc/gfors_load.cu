@@ -512,15 +512,18 @@ void slice_p_chunks(std::vector<GfPChunk>& pch, std::vector<GfPSlice>& psl) {
     if (j - i >= 8) {
       for (size_t a = i; a < j; a += 32) {
         const GfPChunk& C = pch[ord[a]];
-        GfPSlice S{};
-        S.inst = C.inst;
-        S.v1 = C.v1;
-        S.v2 = C.v2;
-        S.table = C.table;
-        S.len = C.len;
-        S.stride = C.stride;
-        S.lanes = (int32_t)std::min<size_t>(32, j - a);
-        psl.push_back(S);
+        // kPSliceRows rows per warp (more, shorter warps)
+        for (int32_t e0 = 0; e0 < C.len; e0 += kPSliceRows) {
+          GfPSlice S{};
+          S.inst = C.inst;
+          S.v1 = (int32_t)(C.v1 + (int64_t)e0 * C.stride);
+          S.v2 = C.v2;
+          S.table = C.table;
+          S.len = std::min<int32_t>(kPSliceRows, C.len - e0);
+          S.stride = C.stride;
+          S.lanes = (int32_t)std::min<size_t>(32, j - a);
+          psl.push_back(S);
+        }
       }
     } else {
       for (size_t a = i; a < j; ++a) rest.push_back(pch[ord[a]]);

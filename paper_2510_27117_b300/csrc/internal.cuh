@@ -110,6 +110,7 @@ struct GfPSlice {                   // up to 32 P-row chunks side by side: lane 
   int32_t pad;
 };
 constexpr int kPChunk = 256;        // rows per P-row run chunk (one warp)
+constexpr int kPSliceRows = 64;     // rows per warp of a slice of runs
 constexpr int kMinPRun = 64;        // runs at least this long are evaluated as chunks
 struct GfObjChunk {                 // linear-objective chunk: vars [v0, v1)
   int32_t inst;
