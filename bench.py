@@ -387,12 +387,13 @@ TRAFFIC = {
 # scaled by the batch's instances (the kernels process the batch
 # block-diagonally, so traffic is proportional to the instances)
 TRAFFIC_PER_INSTANCE_ITER = {
-    "facility": (814.06e6 + 88.79e6,
-                 "profiles/pdhg_facility_1_dram.md (one instance, one iteration = 5 kernels; "
+    "facility": (815.00e6 + 86.08e6,
+                 "profiles/pdhg_facility_1_dram.md (one instance, one iteration = 6 kernels; "
                  "scaled by the 16 instances)"),
 }
 PDHG_KERNELS = {
-    "buckets": "PDHG iteration (bucketed k_dual_* / k_primal_* kernels, long-row chunks)",
+    "buckets": "PDHG iteration (bucketed k_dual_* / k_primal_* kernels, long columns in "
+               "interleaved slices)",
     "one_row": "PDHG iteration (k_single_primal + k_single_dual, one-row batches)",
     "small": "PDHG iterations (k_pdhg_small, one block per instance)",
     "cooperative": "PDHG iterations (k_pdhg_coop, one cooperative launch)",
