@@ -672,8 +672,12 @@ def run_reference(args, rank, world):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-           "config": {"workload": ob.desc, "k_int": ob.k_int, "k_b": ob.k_b,
-                      "instances": ob.ninst},
+           # the same workload keys as the GPU arm's line
+           "config": {"workload": ob.desc, "global_batch": ob.k_b * ob.ninst * world,
+                      "n": ob.inst.n, "instances": ob.ninst, "k_int": ob.k_int,
+                      "k_b": WORKLOADS[args.workload][2], "k_r": ROUNDS[args.workload],
+                      "proposal": PROPOSAL_NAMES[PROPOSAL[args.workload]],
+                      "parallelism": f"replicas x{world}"},
            "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": ob.threads,
                             "kind": "oracle", "sample": ob.sample_text(), **host_info()},
            "e2e": {"value": v, "unit": "candidates/s", "h2d_bytes_per_step": 0,
