@@ -1226,9 +1226,27 @@ extern "C" gfors_status gfors_set_groups(gfors_handle h, int32_t inst, int32_t m
     h->grp_local = gf_alloc_t<int32_t>(h, h->h_grp_local.size());
     h->grp_cw = gf_alloc_t<unsigned long long>(h, h->h_grp_idx.size());
     h->grp_cw2 = gf_alloc_t<unsigned long long>(h, h->h_grp_idx.size());
+    h->grp_step = gf_alloc_t<int64_t>(h, h->h_grp_inst.size());
     if (!h->grp_ptr || !h->grp_idx || !h->grp_inst || !h->grp_local || !h->grp_cw ||
-        !h->grp_cw2)
+        !h->grp_cw2 || !h->grp_step)
       return gf_fail(h, GFORS_E_OOM, "group tables");
+    // member lists in constant steps (e.g. a customer's x_ij over i) are
+    // generated in the samplers instead of read
+    {
+      std::vector<int64_t> step(h->h_grp_inst.size(), 0);
+      for (size_t g = 0; g < step.size(); ++g) {
+        const int64_t a = h->h_grp_ptr[g], b = h->h_grp_ptr[g + 1];
+        if (b - a < 2) continue;
+        const int64_t d = h->h_grp_idx[a + 1] - h->h_grp_idx[a];
+        if (d <= 0) continue;
+        bool ok = true;
+        for (int64_t t = a + 2; t < b && ok; ++t) ok = h->h_grp_idx[t] - h->h_grp_idx[t - 1] == d;
+        if (ok) step[g] = d;
+      }
+      if ((e = cudaMemcpy(h->grp_step, step.data(), sizeof(int64_t) * step.size(),
+                          cudaMemcpyHostToDevice)))
+        return gf_cuda(h, e, "group upload");
+    }
     if ((e = cudaMemcpy(h->grp_ptr, h->h_grp_ptr.data(), sizeof(int64_t) * h->h_grp_ptr.size(),
                         cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->grp_idx, h->h_grp_idx.data(), sizeof(int64_t) * h->h_grp_idx.size(),

@@ -249,6 +249,8 @@ struct gfors_ctx {
   int32_t* grp_inst = nullptr;      // instance of each group
   int32_t* grp_local = nullptr;     // group index within its instance
   unsigned long long* grp_cw = nullptr;  // cumulative weights (per member)
+  int64_t* grp_step = nullptr;      // per group: members grp_idx[ptr] + t step
+                                    // (arithmetic lists), 0 = read the list
   unsigned long long* grp_cw2 = nullptr; // a second set (two proposals in one call)
   const float* cw_src[2] = {nullptr, nullptr};  // p whose weights each set holds
   bool cw_cache = false;            // within one sampling call: p does not change

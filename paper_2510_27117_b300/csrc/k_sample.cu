@@ -196,24 +196,29 @@ k_bern_bits(const float* __restrict__ p, const int32_t* __restrict__ var_inst,
 }
 
 // Cumulative weights floor(p 2^24) of each group's members (in list order),
-// one warp per group: warp-wide inclusive scans of 32-member slices.
+// one warp per group: warp-wide inclusive scans of 32-member slices.  A
+// member list in constant steps (gstep > 0) is generated from its first
+// entry.
 __global__ void k_group_cw(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
-                           int64_t ngroups, const float* __restrict__ p,
-                           unsigned long long* __restrict__ cw) {
+                           const int64_t* __restrict__ gstep, int64_t ngroups,
+                           const float* __restrict__ p, unsigned long long* __restrict__ cw) {
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (g >= ngroups) return;
+  const int64_t a = gp[g], d = gstep[g];
+  const int64_t v0 = d ? gi[a] : 0;         // d > 0 only for lists of 2 or more
   unsigned long long carry = 0;
-  for (int64_t t0 = gp[g]; t0 < gp[g + 1]; t0 += 32) {
+  for (int64_t t0 = a; t0 < gp[g + 1]; t0 += 32) {
     const int64_t t = t0 + lane;
-    unsigned long long v = (t < gp[g + 1]) ? gf::prob_threshold(p[gi[t]]) : 0ull;
+    const int64_t v = d ? v0 + (t - a) * d : (t < gp[g + 1] ? gi[t] : 0);
+    unsigned long long w = (t < gp[g + 1]) ? gf::prob_threshold(p[v]) : 0ull;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, v, off);
-      if (lane >= off) v += o;
+      unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, w, off);
+      if (lane >= off) w += o;
     }
-    if (t < gp[g + 1]) cw[t] = carry + v;
-    carry += __shfl_sync(0xFFFFFFFFu, v, 31);
+    if (t < gp[g + 1]) cw[t] = carry + w;
+    carry += __shfl_sync(0xFFFFFFFFu, w, 31);
   }
 }
 
@@ -229,6 +234,7 @@ constexpr int kPickWarps = 16;
 
 __global__ void __launch_bounds__(32 * kPickWarps)
 k_group_pick(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
+             const int64_t* __restrict__ gstep,
              const int32_t* __restrict__ ginst, const int32_t* __restrict__ glocal,
              int64_t ngroups, const unsigned long long* __restrict__ cw, int kws, int kwu,
              int s0, int len, uint64_t seed, int inst_base,
@@ -269,7 +275,8 @@ k_group_pick(const int64_t* __restrict__ gp, const int64_t* __restrict__ gi,
         }
         pos = lo_i;
       }
-      pick = gi[a + pos];
+      const int64_t d = gstep[g];
+      pick = d ? gi[a] + pos * d : gi[a + pos];
     }
   }
   const unsigned active = __ballot_sync(0xFFFFFFFFu, pick >= 0);
@@ -729,7 +736,7 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
     }
     if (fresh) {
       k_group_cw<<<(unsigned)((h->ngroups_tot * 32 + 255) / 256), 256, 0, h->stream>>>(
-          h->grp_ptr, h->grp_idx, h->ngroups_tot, p, cw);
+          h->grp_ptr, h->grp_idx, h->grp_step, h->ngroups_tot, p, cw);
       h->launches++;
     }
     // the picks' costs, when no later repair changes a grouped variable
@@ -742,7 +749,7 @@ cudaError_t gf_launch_sample(GfCtx* h, const float* p, int s0, int len, bool for
     }
     const int64_t gblocks = (h->ngroups_tot + kPickWarps - 1) / kPickWarps;
     k_group_pick<<<(unsigned)(gblocks * kw), 32 * kPickWarps, 0,
-                   h->stream>>>(h->grp_ptr, h->grp_idx, h->grp_inst, h->grp_local,
+                   h->stream>>>(h->grp_ptr, h->grp_idx, h->grp_step, h->grp_inst, h->grp_local,
                                 h->ngroups_tot, cw, h->kw, kw, s0, len, P.seed, P.inst_base,
                                 h->dstate, h->X, po ? (h->clin ? h->clin : h->cint) : nullptr,
                                 reinterpret_cast<unsigned long long*>(h->objp), h->chunk);
